@@ -1,0 +1,1076 @@
+/*
+ * sbmt_oracle.cpp -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+ *
+ * A plain, slow, single-threaded CPU statement of what the Structured
+ * Bitmap-to-Mesh Triangulation (SBMT) hot path computes: label bitmap ->
+ * boundary PSLG -> equilateral base grid -> segment/edge events (Alg. 1) ->
+ * frozen registry -> canonical key kappa(K) and single-valued lookup
+ * (Sec. 3.3.3, Assumption "frozen registry", Alg. 2, App. G) -> conforming mesh.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+ * load this library.  It shares no code, header, table or helper with the CUDA
+ * path; the two are written independently and compared output for output.
+ *
+ * Arithmetic is exact: every coordinate is an element a + b*sqrt(3) of
+ * Z[sqrt(3)] scaled by S = 6*h_den (h = h_num/h_den), held in __int128, so no
+ * geometric predicate has a tolerance (the paper's epsilon of Thm. "edge
+ * conformity under finite precision" is taken as 0).
+ *
+ * Readings of the paper that this file takes:
+ *  - pixels are unit squares centred at integer points (Sec. 3.3); outside the
+ *    image the label is OUTSIDE, larger than every pixel label; every pixel
+ *    edge between different labels is boundary, the image border included;
+ *  - boundary segments are the maximal straight runs of boundary pixel edges
+ *    between PSLG vertices (turns, junctions, pinches), each oriented with the
+ *    lower label on its left (Sec. 3.1 "input boundary as prescribed prior");
+ *  - the grid is v(i,j) = o + h*(i + j/2, (sqrt3/2) j) and the mesh holds every
+ *    grid cell meeting the closed image rectangle (Sec. 3.3);
+ *  - only the degeneracy-free parameter class is meshed: integer origin, h_num
+ *    even, h_den odd.  Then no grid vertex lies on a pixel line, no grid edge
+ *    is collinear with a pixel edge and no pixel corner lies on a grid edge, so
+ *    every Alg. 1 event of the pipeline is a proper crossing.  Alg. 1 itself
+ *    (all four branches) is implemented and exported for the paper's atoms;
+ *  - Tier-T cells (inside the regime of Lemma 3.1) take the App. G templates;
+ *    every other cut cell (Tier-G) takes the greedy triangulation of its local
+ *    PSLG (shortest exact edge first, ties by local index), Steiner-free;
+ *  - canonicalisation is over the three rotations (C3); mirror images are
+ *    distinct keys (App. G "orientation handling"); the nested-chord pair is
+ *    split by the direction of the chord nearest the cut corner;
+ *  - a triangle's label is the label of the pixel holding its centroid.
+ *
+ * parity pinned: Alg. 1 by the single-segment atoms of Fig. "lookup_table";
+ * intersection points by the printed coordinates of App. F; templates by the
+ * printed triangle lists of App. G at the printed coordinates; the mesh by
+ * closed forms and invariants (see tests/test_oracle_*.py).
+ */
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <set>
+#include <stdexcept>
+#include <vector>
+
+typedef __int128 i128;
+typedef int64_t i64;
+
+namespace {
+
+/* ------------------------------------------------------------------------- */
+/* exact numbers a + b*sqrt(3)                                                */
+/* ------------------------------------------------------------------------- */
+struct Z3 {
+  i128 a, b;
+};
+Z3 z(i128 a, i128 b = 0) { return Z3{a, b}; }
+Z3 operator+(Z3 x, Z3 y) { return Z3{x.a + y.a, x.b + y.b}; }
+Z3 operator-(Z3 x, Z3 y) { return Z3{x.a - y.a, x.b - y.b}; }
+Z3 operator*(Z3 x, Z3 y) { return Z3{x.a * y.a + 3 * x.b * y.b, x.a * y.b + x.b * y.a}; }
+Z3 times(Z3 x, i128 k) { return Z3{x.a * k, x.b * k}; }
+
+/* sign of a + b*sqrt(3); sqrt(3) is irrational so a^2 == 3 b^2 only at 0 */
+int sgn(Z3 v) {
+  int sa = (v.a > 0) - (v.a < 0), sb = (v.b > 0) - (v.b < 0);
+  if (sa == 0) return sb;
+  if (sb == 0 || sa == sb) return sa;
+  i128 l = v.a * v.a, r = 3 * v.b * v.b;
+  return l > r ? sa : sb;
+}
+int cmp(Z3 x, Z3 y) { return sgn(x - y); }
+double to_double(Z3 v) { return (double)v.a + (double)v.b * 1.7320508075688772935; }
+
+struct Pt {
+  Z3 x, y;
+};
+int orient(const Pt& p, const Pt& q, const Pt& r) {
+  return sgn((q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x));
+}
+Z3 dot(const Pt& o, const Pt& p, const Pt& q) {
+  return (p.x - o.x) * (q.x - o.x) + (p.y - o.y) * (q.y - o.y);
+}
+/* w on the closed segment uv (u != v) */
+bool on_closed_seg(const Pt& u, const Pt& v, const Pt& w) {
+  return orient(u, v, w) == 0 && sgn(dot(u, v, w)) >= 0 && sgn(dot(v, u, w)) >= 0;
+}
+/* w strictly inside the open segment uv */
+bool on_open_seg(const Pt& u, const Pt& v, const Pt& w) {
+  return orient(u, v, w) == 0 && sgn(dot(u, v, w)) > 0 && sgn(dot(v, u, w)) > 0;
+}
+
+/* floor(n / d) for n in Z[sqrt3], integer d > 0, exact */
+i64 floor_div(Z3 n, i64 d) {
+  double approx = to_double(n) / (double)d;
+  i64 k = (i64)std::floor(approx);
+  while (sgn(n - z((i128)k * d)) < 0) --k;
+  while (sgn(n - z((i128)(k + 1) * d)) >= 0) ++k;
+  return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 1 (Sec. 3.3.1): classify segment L = PQ against triangle edge e = UV.  */
+/* ------------------------------------------------------------------------- */
+enum { EV_NONE = 0, EV_CROSS = 1, EV_VERTEX = 2, EV_OVERLAP = 3 };
+struct Alg1 {
+  int kind;
+  bool u_on, v_on; /* which vertices of e lie on L (EV_VERTEX) */
+};
+/* The three branches in the paper's priority order:
+ *  1. L crosses e at one point of e's relative interior ("interior or
+ *     endpoint-on-edge")                                   -> one intersection;
+ *  2. else a vertex of e lies on L                         -> two intersections,
+ *     one for each edge incident to that vertex;
+ *  3. else L overlaps e collinearly (positive length)      -> one intersection. */
+Alg1 alg1(const Pt& U, const Pt& V, const Pt& P, const Pt& Q) {
+  Alg1 r{EV_NONE, false, false};
+  int o1 = orient(U, V, P), o2 = orient(U, V, Q);
+  int o3 = orient(P, Q, U), o4 = orient(P, Q, V);
+  bool colinear = (o1 == 0 && o2 == 0);
+  if (!colinear) {
+    bool meet = (o1 * o2 <= 0) && (o3 * o4 <= 0);
+    if (meet && o3 != 0 && o4 != 0) {
+      r.kind = EV_CROSS;
+      return r;
+    }
+  }
+  r.u_on = on_closed_seg(P, Q, U);
+  r.v_on = on_closed_seg(P, Q, V);
+  if (r.u_on || r.v_on) {
+    r.kind = EV_VERTEX;
+    return r;
+  }
+  if (colinear) {
+    /* positive-length overlap with neither U nor V covered: L lies inside e */
+    if (on_open_seg(U, V, P) || on_open_seg(U, V, Q)) r.kind = EV_OVERLAP;
+  }
+  return r;
+}
+
+/* intersection point of lines PQ and UV (not parallel), as a fraction
+ * (nx, ny) / den with den a positive integer */
+void line_meet(const Pt& P, const Pt& Q, const Pt& U, const Pt& V, Z3* nx, Z3* ny, i128* den) {
+  /* P + s (Q - P), s = cross(U - P, V - U) / cross(Q - P, V - U) */
+  Z3 dx = Q.x - P.x, dy = Q.y - P.y, ex = V.x - U.x, ey = V.y - U.y;
+  Z3 num = (U.x - P.x) * ey - (U.y - P.y) * ex;
+  Z3 dd = dx * ey - dy * ex;
+  Z3 conj{dd.a, -dd.b};
+  i128 d = (dd * conj).a; /* a^2 - 3 b^2, nonzero */
+  Z3 s_num = num * conj;  /* s = s_num / d */
+  if (d < 0) {
+    d = -d;
+    s_num = Z3{-s_num.a, -s_num.b};
+  }
+  *nx = times(P.x, d) + s_num * dx;
+  *ny = times(P.y, d) + s_num * dy;
+  *den = d;
+}
+Z3 exact_div(Z3 n, i128 d) {
+  if (n.a % d != 0 || n.b % d != 0) throw std::runtime_error("inexact event point");
+  return Z3{n.a / d, n.b / d};
+}
+
+/* ------------------------------------------------------------------------- */
+/* input image and the boundary PSLG (Sec. 3.1, Sec. 3.2)                     */
+/* ------------------------------------------------------------------------- */
+const int32_t OUTSIDE = 0x10000; /* larger than any u8/u16 label */
+
+struct Image {
+  int W, H;
+  i64 pitch;
+  int dtype; /* 1 = u8, 2 = u16 */
+  const uint8_t* data;
+  int32_t at(i64 x, i64 y) const {
+    if (x < 0 || y < 0 || x >= W || y >= H) return OUTSIDE;
+    const uint8_t* row = data + y * pitch;
+    if (dtype == 1) return row[x];
+    uint16_t v;
+    std::memcpy(&v, row + 2 * x, 2);
+    return v;
+  }
+};
+
+/* Pixel corner (cx, cy), 0 <= cx <= W, 0 <= cy <= H, sits at (cx-1/2, cy-1/2).
+ * Its four incident unit pixel edges: E to (cx+1,cy), W to (cx-1,cy), N to
+ * (cx,cy+1), S to (cx,cy-1); an edge is boundary when the two pixels it
+ * separates have different labels. */
+enum { CE_E = 1, CE_N = 2, CE_W = 4, CE_S = 8 };
+int corner_mask(const Image& im, i64 cx, i64 cy) {
+  int m = 0;
+  if (im.at(cx, cy - 1) != im.at(cx, cy)) m |= CE_E;
+  if (im.at(cx - 1, cy - 1) != im.at(cx - 1, cy)) m |= CE_W;
+  if (im.at(cx - 1, cy) != im.at(cx, cy)) m |= CE_N;
+  if (im.at(cx - 1, cy - 1) != im.at(cx, cy - 1)) m |= CE_S;
+  return m;
+}
+/* A corner is a PSLG vertex unless it has no boundary edge or exactly two
+ * collinear ones (a straight run passes through it). */
+bool is_vertex(int m) { return m != 0 && m != (CE_E | CE_W) && m != (CE_N | CE_S); }
+
+struct Segment {
+  i64 cx, cy; /* start corner (lower coordinate end) */
+  int dir;    /* 0: along +x, 1: along +y */
+  i64 len;
+  int32_t lab0, lab1; /* dir 0: below / above; dir 1: left / right */
+  int rev;            /* 1 when the oriented direction (lower label on the left) is -x / -y */
+};
+
+std::vector<Segment> extract_segments(const Image& im) {
+  std::vector<Segment> segs;
+  const i64 W = im.W, H = im.H;
+  std::vector<uint8_t> mask((size_t)(W + 1) * (H + 1));
+  for (i64 cy = 0; cy <= H; ++cy)
+    for (i64 cx = 0; cx <= W; ++cx) mask[cy * (W + 1) + cx] = (uint8_t)corner_mask(im, cx, cy);
+  auto M = [&](i64 cx, i64 cy) { return (int)mask[cy * (W + 1) + cx]; };
+  for (i64 cy = 0; cy <= H; ++cy)
+    for (i64 cx = 0; cx <= W; ++cx) {
+      int m = M(cx, cy);
+      if (!is_vertex(m)) continue;
+      if (m & CE_E) {
+        i64 x = cx + 1;
+        while (!is_vertex(M(x, cy))) ++x;
+        Segment s{cx, cy, 0, x - cx, im.at(cx, cy - 1), im.at(cx, cy), 0};
+        s.rev = (s.lab1 < s.lab0) ? 0 : 1; /* going +x the left side is above */
+        segs.push_back(s);
+      }
+      if (m & CE_N) {
+        i64 y = cy + 1;
+        while (!is_vertex(M(cx, y))) ++y;
+        Segment s{cx, cy, 1, y - cy, im.at(cx - 1, cy), im.at(cx, cy), 0};
+        s.rev = (s.lab0 < s.lab1) ? 0 : 1; /* going +y the left side is -x */
+        segs.push_back(s);
+      }
+    }
+  return segs;
+}
+
+/* ------------------------------------------------------------------------- */
+/* the equilateral base grid (Sec. 3.3)                                       */
+/* ------------------------------------------------------------------------- */
+struct Grid {
+  i64 p, q, S, ox, oy; /* h = p/q; scaled origin */
+  i64 W, H;
+  i64 xl, xr, yl, yr; /* closed image rectangle, scaled */
+  i64 j0, j1;         /* strip rows meeting it */
+  std::vector<i64> clo, chi, cbase;
+  i64 vj0, vj1;
+  std::vector<i64> vlo, vhi, vbase;
+  i64 ncells = 0, nverts = 0;
+
+  Pt vtx(i64 i, i64 j) const { return Pt{z(ox + 3 * p * (2 * i + j)), z(oy, 3 * p * j)}; }
+  Z3 ystrip(i64 j) const { return z(oy, 3 * p * j); }
+  Pt pixcorner(i64 cx, i64 cy) const { return Pt{z(6 * q * cx - 3 * q), z(6 * q * cy - 3 * q)}; }
+
+  /* lattice coordinates of the corners A, B, C of cell c = 2i+d in strip j */
+  void corners(i64 c, i64 j, i64 ci[3], i64 cj[3]) const {
+    i64 i = (c >= 0) ? c / 2 : -((-c + 1) / 2);
+    int d = (int)(c - 2 * i);
+    if (d == 0) { /* up: v(i,j), v(i+1,j), v(i,j+1) */
+      ci[0] = i, cj[0] = j, ci[1] = i + 1, cj[1] = j, ci[2] = i, cj[2] = j + 1;
+    } else { /* down: v(i+1,j), v(i+1,j+1), v(i,j+1) */
+      ci[0] = i + 1, cj[0] = j, ci[1] = i + 1, cj[1] = j + 1, ci[2] = i, cj[2] = j + 1;
+    }
+  }
+  std::array<Pt, 3> cell_pts(i64 c, i64 j) const {
+    i64 ci[3], cj[3];
+    corners(c, j, ci, cj);
+    return {vtx(ci[0], cj[0]), vtx(ci[1], cj[1]), vtx(ci[2], cj[2])};
+  }
+
+  /* separating-axis test: closed triangle meets the closed rectangle */
+  bool meets_rect(const std::array<Pt, 3>& t) const {
+    Z3 mnx = t[0].x, mxx = t[0].x, mny = t[0].y, mxy = t[0].y;
+    for (int k = 1; k < 3; ++k) {
+      if (cmp(t[k].x, mnx) < 0) mnx = t[k].x;
+      if (cmp(t[k].x, mxx) > 0) mxx = t[k].x;
+      if (cmp(t[k].y, mny) < 0) mny = t[k].y;
+      if (cmp(t[k].y, mxy) > 0) mxy = t[k].y;
+    }
+    if (cmp(mxx, z(xl)) < 0 || cmp(mnx, z(xr)) > 0) return false;
+    if (cmp(mxy, z(yl)) < 0 || cmp(mny, z(yr)) > 0) return false;
+    Pt rc[4] = {{z(xl), z(yl)}, {z(xr), z(yl)}, {z(xr), z(yr)}, {z(xl), z(yr)}};
+    for (int k = 0; k < 3; ++k) {
+      const Pt &a = t[k], &b = t[(k + 1) % 3];
+      bool all_out = true; /* triangle is CCW: its interior is left of ab */
+      for (auto& r : rc)
+        if (orient(a, b, r) >= 0) all_out = false;
+      if (all_out) return false;
+    }
+    return true;
+  }
+
+  bool has_cell(i64 c, i64 j) const {
+    if (j < j0 || j > j1) return false;
+    return c >= clo[j - j0] && c <= chi[j - j0];
+  }
+  i64 cell_id(i64 c, i64 j) const { return cbase[j - j0] + (c - clo[j - j0]); }
+  i64 vid(i64 i, i64 j) const {
+    if (j < vj0 || j > vj1 || i < vlo[j - vj0] || i > vhi[j - vj0]) throw std::runtime_error("vertex not in mesh");
+    return vbase[j - vj0] + (i - vlo[j - vj0]);
+  }
+  /* grid-edge id: 3 * (id of the lower-id endpoint) + family, family 0 = +x,
+   * 1 = 60 degrees, 2 = 120 degrees seen from that endpoint */
+  i64 edge_id(i64 i1, i64 j1_, i64 i2, i64 j2) const {
+    i64 a = vid(i1, j1_), b = vid(i2, j2);
+    if (b < a) std::swap(i1, i2), std::swap(j1_, j2), std::swap(a, b);
+    i64 di = i2 - i1, dj = j2 - j1_;
+    int fam = (dj == 0 && di == 1) ? 0 : (dj == 1 && di == 0) ? 1 : (dj == 1 && di == -1) ? 2 : -1;
+    if (fam < 0) throw std::runtime_error("not a grid edge");
+    return 3 * a + fam;
+  }
+  /* strip row containing a point whose y is never on a grid line */
+  i64 strip_of(Z3 y) const {
+    double approx = (to_double(y) - (double)oy) / (3.0 * (double)p * 1.7320508075688772935);
+    i64 j = (i64)std::floor(approx);
+    while (cmp(ystrip(j), y) > 0) --j;
+    while (cmp(ystrip(j + 1), y) <= 0) ++j;
+    return j;
+  }
+  /* cell-index range in strip j whose cells could meet x in [xa, xb] */
+  void cand_range(i64 j, double xa, double xb, i64* ca, i64* cb) const {
+    double ia = ((xa - (double)ox) / (3.0 * (double)p) - (double)j) / 2.0;
+    double ib = ((xb - (double)ox) / (3.0 * (double)p) - (double)j) / 2.0;
+    *ca = 2 * ((i64)std::floor(ia) - 2);
+    *cb = 2 * ((i64)std::ceil(ib) + 2) + 1;
+  }
+};
+
+bool build_grid(Grid& g, i64 W, i64 H, i64 p, i64 q, i64 o2x, i64 o2y) {
+  g.p = p, g.q = q, g.S = 6 * q, g.ox = 3 * q * o2x, g.oy = 3 * q * o2y, g.W = W, g.H = H;
+  g.xl = -3 * q, g.xr = 6 * q * W - 3 * q, g.yl = -3 * q, g.yr = 6 * q * H - 3 * q;
+  /* strip rows j with y_j <= yr and y_{j+1} >= yl */
+  g.j0 = g.strip_of(z(g.yl));
+  g.j1 = g.strip_of(z(g.yr));
+  i64 nrows = g.j1 - g.j0 + 1;
+  g.clo.assign(nrows, 0), g.chi.assign(nrows, -1), g.cbase.assign(nrows, 0);
+  std::map<i64, std::pair<i64, i64>> vr; /* vertex row -> [lo, hi] */
+  i64 base = 0;
+  for (i64 j = g.j0; j <= g.j1; ++j) {
+    i64 ca, cb;
+    g.cand_range(j, (double)g.xl - 6.0 * p, (double)g.xr + 6.0 * p, &ca, &cb);
+    i64 lo = 0, hi = -1;
+    bool any = false;
+    for (i64 c = ca; c <= cb; ++c) {
+      if (g.meets_rect(g.cell_pts(c, j))) {
+        if (!any) lo = c;
+        if (any && c != hi + 1) throw std::runtime_error("cell row not contiguous");
+        hi = c, any = true;
+      }
+    }
+    if (!any) throw std::runtime_error("empty cell row");
+    if (lo == ca || hi == cb) throw std::runtime_error("cell candidate range too small");
+    g.clo[j - g.j0] = lo, g.chi[j - g.j0] = hi, g.cbase[j - g.j0] = base;
+    base += hi - lo + 1;
+    for (i64 c = lo; c <= hi; ++c) {
+      i64 ci[3], cj[3];
+      g.corners(c, j, ci, cj);
+      for (int k = 0; k < 3; ++k) {
+        auto it = vr.find(cj[k]);
+        if (it == vr.end()) vr[cj[k]] = {ci[k], ci[k]};
+        else it->second.first = std::min(it->second.first, ci[k]), it->second.second = std::max(it->second.second, ci[k]);
+      }
+    }
+  }
+  g.ncells = base;
+  g.vj0 = vr.begin()->first, g.vj1 = vr.rbegin()->first;
+  i64 nv = g.vj1 - g.vj0 + 1;
+  g.vlo.assign(nv, 0), g.vhi.assign(nv, -1), g.vbase.assign(nv, 0);
+  base = 0;
+  for (i64 j = g.vj0; j <= g.vj1; ++j) {
+    auto& r = vr.at(j);
+    g.vlo[j - g.vj0] = r.first, g.vhi[j - g.vj0] = r.second, g.vbase[j - g.vj0] = base;
+    base += r.second - r.first + 1;
+  }
+  g.nverts = base;
+  /* every vertex in a row range must be a corner of some cell (no isolated vertex) */
+  std::vector<std::vector<uint8_t>> used(nv);
+  for (i64 j = g.vj0; j <= g.vj1; ++j) used[j - g.vj0].assign(g.vhi[j - g.vj0] - g.vlo[j - g.vj0] + 1, 0);
+  for (i64 j = g.j0; j <= g.j1; ++j)
+    for (i64 c = g.clo[j - g.j0]; c <= g.chi[j - g.j0]; ++c) {
+      i64 ci[3], cj[3];
+      g.corners(c, j, ci, cj);
+      for (int k = 0; k < 3; ++k) used[cj[k] - g.vj0][ci[k] - g.vlo[cj[k] - g.vj0]] = 1;
+    }
+  for (auto& row : used)
+    for (auto u : row)
+      if (!u) throw std::runtime_error("vertex row not contiguous");
+  return true;
+}
+
+/* ------------------------------------------------------------------------- */
+/* finite lookup table (App. G) in the canonical frame                        */
+/* ------------------------------------------------------------------------- */
+/* Template labels: canonical corners A', B', C'; E0..E3 are the events read
+ * counter-clockwise from A' (edge A'B', then B'C', then C'A'); P is the chain
+ * vertex inside the cell. */
+enum { LA = 0, LB = 1, LC = 2, E0 = 3, E1 = 4, E2 = 5, E3 = 6, LP = 7 };
+typedef std::array<int, 3> Tri;
+
+/* Canonical code of a Tier-T cell under rotation r:
+ *   star<<10 | n(r)<<7 | n(r+1)<<4 | n(r+2)<<1 | dir
+ * n(k) = number of events on actual edge k (0 AB, 1 BC, 2 CA); star = one chain
+ * vertex inside; dir = direction bit of the nearer of two nested chords.  The
+ * canonical rotation sigma minimises the code (ties: smallest sigma). */
+int tcode(int star, int n0, int n1, int n2, int dir) { return (star << 10) | (n0 << 7) | (n1 << 4) | (n2 << 1) | dir; }
+
+struct TplEntry {
+  int key;
+  std::vector<Tri> tri;
+};
+const std::map<int, TplEntry>& lut() {
+  static std::map<int, TplEntry> m;
+  if (!m.empty()) return m;
+  /* single segment, case (b): chord with Q1 on BC and Q2 on CA cuts corner C */
+  m[tcode(0, 0, 1, 1, 0)] = {1, {{E1, E0, LC}, {E1, LA, LB}, {E0, E1, LB}}};
+  /* (1,1) case (a): P inside, Q1 on CA, Q2 on BC (E0 = Q2, E1 = Q1) */
+  m[tcode(1, 0, 1, 1, 0)] = {2, {{E1, LP, LC}, {LP, E0, LC}, {E1, LA, LP}, {LA, LB, LP}, {E0, LP, LB}}};
+  /* (1,1) case (c): P inside, Q1 and Q2 on CA, Q1 nearer C (E0 = Q1, E1 = Q2) */
+  m[tcode(1, 0, 0, 2, 0)] = {3, {{E0, LP, LC}, {LP, E0, E1}, {E1, LA, LP}, {LB, LC, LP}, {LA, LB, LP}}};
+  /* (2,2) case (b1): Q1 on AB, Q3 on BC, Q4 and Q2 on CA (E0=Q1, E1=Q3, E2=Q4, E3=Q2) */
+  m[tcode(0, 1, 1, 2, 0)] = {4, {{E0, E3, LA}, {E0, E2, E3}, {E0, E1, E2}, {E0, LB, E1}, {E2, E1, LC}}};
+  /* (2,2) case (d3): nested chords at C, nearer chord runs BC -> CA
+   * (App. G attribution: Q1, Q2 on CA with Q1 nearer C; Q3, Q4 on BC with Q3
+   * nearer C; E0 = Q4, E1 = Q3, E2 = Q1, E3 = Q2) */
+  m[tcode(0, 0, 2, 2, 1)] = {5, {{LA, LB, E3}, {E3, LB, E0}, {E2, E3, E0}, {E2, E0, E1}, {E2, E1, LC}}};
+  /* (2,2) case (a4): the mirror image, drawn at corner A, rotated here so the
+   * cut corner is C' (paper A -> C', B -> A', C -> B'); E0 = Q2, E1 = Q1,
+   * E2 = Q3, E3 = Q4 */
+  m[tcode(0, 0, 2, 2, 0)] = {6, {{E2, E1, LC}, {E3, E1, E2}, {E1, E3, E0}, {E0, E3, LA}, {E0, LA, LB}}};
+  /* keys the paper does not list: one chain vertex P of degree 3 or 4 inside
+   * the cell, every segment incident to P -> star from P over the boundary
+   * cycle read counter-clockwise from A' */
+  const int star_counts[9][3] = {{0, 0, 3}, {0, 1, 2}, {0, 2, 1}, {1, 1, 1}, {0, 0, 4},
+                                 {0, 1, 3}, {0, 2, 2}, {0, 3, 1}, {1, 1, 2}};
+  for (int s = 0; s < 9; ++s) {
+    const int* n = star_counts[s];
+    std::vector<int> cyc;
+    int e = E0;
+    for (int k = 0; k < 3; ++k) {
+      cyc.push_back(k); /* corner A', B', C' */
+      for (int t = 0; t < n[k]; ++t) cyc.push_back(e++);
+    }
+    std::vector<Tri> tri;
+    for (size_t t = 0; t < cyc.size(); ++t) tri.push_back({cyc[t], cyc[(t + 1) % cyc.size()], LP});
+    m[tcode(1, n[0], n[1], n[2], 0)] = {7 + s, tri};
+  }
+  return m;
+}
+
+/* (m,n) class index in Thm. 3.2's list, 1-based; 0 = not applicable */
+int class_index(int m, int n) {
+  if (m > n) std::swap(m, n);
+  const int lst[8][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 1}, {1, 2}, {2, 2}, {1, 3}, {2, 3}};
+  for (int k = 0; k < 8; ++k)
+    if (lst[k][0] == m && lst[k][1] == n) return k + 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* per-cell key and Tier-T patch (Sec. 3.3.2, Sec. 3.3.3, Alg. 2)             */
+/* ------------------------------------------------------------------------- */
+/* Local numbering of a cell: 0,1,2 = corners A,B,C; then the events in CCW
+ * order from A (those on AB, then BC, then CA); then the chain vertices
+ * strictly inside (by pixel-corner id).  A chain edge is the piece of one
+ * boundary segment inside the cell, stored oriented along the segment. */
+struct LocalResult {
+  int tierG = 0, key = 0, sigma = 0, klass = 0, mask = 0;
+  std::vector<Tri> tri; /* Tier-T only, local indices */
+};
+
+LocalResult classify_local(const int nev[3], int nchain, const std::vector<std::pair<int, int>>& ce) {
+  LocalResult r;
+  const int ne = nev[0] + nev[1] + nev[2];
+  auto edge_of = [&](int v) -> int {
+    if (v < 3) return -1;
+    int k = v - 3;
+    for (int e = 0; e < 3; ++e) {
+      if (k < nev[e]) return e;
+      k -= nev[e];
+    }
+    return -2; /* chain vertex */
+  };
+  /* Alg. 1 bitmask (AB=2, BC=4, CA=8) per segment; bit 0 marks a chain vertex
+   * strictly inside the cell (the paper leaves bit value 1 unused) */
+  r.mask = nchain > 0 ? 1 : 0;
+  std::vector<int> counts;
+  for (auto& e : ce) {
+    int mb = 0;
+    for (int w : {e.first, e.second}) {
+      int k = edge_of(w);
+      if (k >= 0) mb |= 2 << k;
+    }
+    r.mask |= mb;
+    counts.push_back(__builtin_popcount(mb));
+  }
+  if (ce.size() == 1) r.klass = class_index(0, counts[0]);
+  else if (ce.size() == 2) r.klass = class_index(counts[0], counts[1]);
+
+  /* regime of Lemma 3.1: no chain vertex and one or two chords, or a single
+   * chain vertex P with every segment in the cell incident to P */
+  int star = 0, dir = 0;
+  bool tierT = false;
+  if (nchain == 0) {
+    for (auto& e : ce)
+      if (edge_of(e.first) < 0 || edge_of(e.second) < 0) throw std::runtime_error("chord end not an event");
+    tierT = (ce.size() == 1 || ce.size() == 2);
+    if (ce.size() == 2) {
+      /* corner cut off by a chord: the corner shared by the chord's two edges */
+      auto cut = [&](const std::pair<int, int>& e) {
+        int a = edge_of(e.first), b = edge_of(e.second);
+        if (a == b) throw std::runtime_error("chord with both ends on one edge");
+        return (b == (a + 1) % 3) ? b : a; /* edges k and k+1 share corner k+1 */
+      };
+      int x0 = cut(ce[0]), x1 = cut(ce[1]);
+      if (x0 == x1) { /* nested chords at corner X */
+        int X = x0, ein = (X + 2) % 3, eout = X;
+        /* on the edge ending at X the event nearer X comes later in CCW order */
+        int near = -1, best = -1;
+        for (int c = 0; c < 2; ++c)
+          for (int w : {ce[c].first, ce[c].second})
+            if (edge_of(w) == ein && w > best) best = w, near = c;
+        dir = (edge_of(ce[near].first) == ein && edge_of(ce[near].second) == eout) ? 1 : 0;
+      }
+    }
+  } else if (nchain == 1) {
+    const int P = 3 + ne;
+    tierT = !ce.empty();
+    for (auto& e : ce)
+      if (e.first != P && e.second != P) tierT = false;
+    star = 1;
+  }
+  if (!tierT) {
+    r.tierG = 1;
+    r.key = 63;
+    return r;
+  }
+  int best = -1, sigma = 0;
+  for (int rr = 0; rr < 3; ++rr) {
+    int code = tcode(star, nev[rr], nev[(rr + 1) % 3], nev[(rr + 2) % 3], dir);
+    if (best < 0 || code < best) best = code, sigma = rr;
+  }
+  auto it = lut().find(best);
+  if (it == lut().end()) throw std::runtime_error("Tier-T key missing from the table");
+  r.key = it->second.key;
+  r.sigma = sigma;
+  /* instantiate: pi maps canonical labels to local vertices, pre-composed with sigma */
+  int map[8];
+  for (int k = 0; k < 3; ++k) map[k] = (sigma + k) % 3;
+  std::vector<int> evs; /* events CCW from corner sigma */
+  for (int k = 0; k < 3; ++k) {
+    int e = (sigma + k) % 3, first = 3;
+    for (int t = 0; t < e; ++t) first += nev[t];
+    for (int t = 0; t < nev[e]; ++t) evs.push_back(first + t);
+  }
+  for (int k = 0; k < 4; ++k) map[E0 + k] = k < (int)evs.size() ? evs[k] : -1;
+  map[LP] = nchain == 1 ? 3 + ne : -1;
+  for (auto& t : it->second.tri) {
+    Tri o{map[t[0]], map[t[1]], map[t[2]]};
+    if (o[0] < 0 || o[1] < 0 || o[2] < 0) throw std::runtime_error("template label unmapped");
+    r.tri.push_back(o);
+  }
+  return r;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tier-G: greedy triangulation of the cell's local PSLG                      */
+/* ------------------------------------------------------------------------- */
+/* All local vertices lie in the convex cell.  Start from the constraint edges
+ * (boundary sub-edges of the cell and chain edges), then take every other
+ * vertex pair in order of exact squared length (ties: smaller local index
+ * pair) and keep it when its open segment holds no vertex and crosses no kept
+ * edge.  A maximal plane straight-line graph on a point set triangulates its
+ * convex hull, so the result triangulates the cell, embeds every chain edge
+ * and adds no Steiner point. */
+std::vector<Tri> greedy_triangulate(const std::vector<Pt>& v, const std::vector<std::pair<int, int>>& constraints) {
+  const int n = (int)v.size();
+  std::vector<std::vector<uint8_t>> adj(n, std::vector<uint8_t>(n, 0));
+  std::vector<std::pair<int, int>> edges;
+  for (auto& e : constraints) {
+    int a = std::min(e.first, e.second), b = std::max(e.first, e.second);
+    if (!adj[a][b]) adj[a][b] = adj[b][a] = 1, edges.push_back({a, b});
+  }
+  struct Cand {
+    Z3 len2;
+    int u, w;
+  };
+  std::vector<Cand> cand;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b)
+      if (!adj[a][b]) {
+        Z3 dx = v[b].x - v[a].x, dy = v[b].y - v[a].y;
+        cand.push_back({dx * dx + dy * dy, a, b});
+      }
+  std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) {
+    int c = cmp(x.len2, y.len2);
+    if (c != 0) return c < 0;
+    if (x.u != y.u) return x.u < y.u;
+    return x.w < y.w;
+  });
+  for (auto& c : cand) {
+    bool ok = true;
+    for (int k = 0; k < n && ok; ++k)
+      if (k != c.u && k != c.w && on_open_seg(v[c.u], v[c.w], v[k])) ok = false;
+    for (size_t t = 0; t < edges.size() && ok; ++t) {
+      int a = edges[t].first, b = edges[t].second;
+      if (a == c.u || a == c.w || b == c.u || b == c.w) continue;
+      int o1 = orient(v[c.u], v[c.w], v[a]), o2 = orient(v[c.u], v[c.w], v[b]);
+      int o3 = orient(v[a], v[b], v[c.u]), o4 = orient(v[a], v[b], v[c.w]);
+      if (o1 * o2 < 0 && o3 * o4 < 0) ok = false;
+    }
+    if (ok) adj[c.u][c.w] = adj[c.w][c.u] = 1, edges.push_back({c.u, c.w});
+  }
+  /* faces: 3-cycles holding no vertex in their interior, rotated so the
+   * smallest local index leads, counter-clockwise, listed in sorted order */
+  std::vector<Tri> tri;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      if (!adj[a][b]) continue;
+      for (int c = b + 1; c < n; ++c) {
+        if (!adj[a][c] || !adj[b][c]) continue;
+        int o = orient(v[a], v[b], v[c]);
+        if (o == 0) continue;
+        bool empty = true;
+        for (int k = 0; k < n && empty; ++k) {
+          if (k == a || k == b || k == c) continue;
+          int s1 = orient(v[a], v[b], v[k]), s2 = orient(v[b], v[c], v[k]), s3 = orient(v[c], v[a], v[k]);
+          if (s1 == o && s2 == o && s3 == o) empty = false;
+        }
+        if (empty) tri.push_back(o > 0 ? Tri{a, b, c} : Tri{a, c, b});
+      }
+    }
+  std::sort(tri.begin(), tri.end());
+  return tri;
+}
+
+/* ------------------------------------------------------------------------- */
+/* the whole mesh                                                             */
+/* ------------------------------------------------------------------------- */
+struct Event {
+  i64 edge;
+  i64 seg;
+  Pt pt;
+  Z3 t; /* position along the edge from its lower endpoint */
+};
+
+struct Mesh {
+  std::vector<double> xy;
+  std::vector<int32_t> tri;
+  std::vector<uint16_t> label, code;
+  std::vector<Segment> segs;
+  std::vector<Event> events; /* registry order */
+  i64 nverts_grid = 0, ncells = 0;
+  std::vector<i64> cut_cell, cut_code, cut_ntri, cut_nchain, cut_tierG;
+  i64 n_tierG = 0;
+};
+
+/* label of the pixel holding the centroid of (a, b, c); OUTSIDE off-image */
+int32_t centroid_label(const Grid& g, const Image& im, const Pt& a, const Pt& b, const Pt& c) {
+  /* pixel column = floor(x/S + 1/2) with x = (xa+xb+xc)/3 */
+  Z3 sx = a.x + b.x + c.x, sy = a.y + b.y + c.y;
+  i64 col = floor_div(times(sx, 2) + z(3 * g.S), 6 * g.S);
+  i64 row = floor_div(times(sy, 2) + z(3 * g.S), 6 * g.S);
+  return im.at(col, row);
+}
+
+uint16_t out_label(int32_t l) { return l == OUTSIDE ? (uint16_t)0xFFFF : (uint16_t)l; }
+
+uint16_t make_code(const LocalResult& r) {
+  return (uint16_t)((r.mask & 15) | ((r.sigma & 3) << 4) | ((r.key & 63) << 6) | ((r.klass & 15) << 12));
+}
+
+void mesh_image(const Image& im, i64 p, i64 q, i64 o2x, i64 o2y, Mesh& M) {
+  Grid g;
+  build_grid(g, im.W, im.H, p, q, o2x, o2y);
+  M.segs = extract_segments(im);
+
+  /* events and cell incidences: Alg. 1 for every segment against the edges of
+   * the cells near it */
+  std::map<std::pair<i64, i64>, Event> ev; /* (edge id, segment) */
+  std::map<i64, std::set<i64>> cell_segs;  /* cell id -> segments meeting it */
+  std::map<i64, std::vector<std::pair<i64, i64>>> cell_chain; /* cell id -> (corner id, segment) */
+  const i64 S = g.S;
+  for (size_t s = 0; s < M.segs.size(); ++s) {
+    const Segment& sg = M.segs[s];
+    Pt P = g.pixcorner(sg.cx, sg.cy);
+    Pt Q = sg.dir == 0 ? g.pixcorner(sg.cx + sg.len, sg.cy) : g.pixcorner(sg.cx, sg.cy + sg.len);
+    i64 ja = g.strip_of(P.y), jb = g.strip_of(Q.y);
+    for (i64 j = ja; j <= jb; ++j) {
+      i64 ca, cb;
+      g.cand_range(j, to_double(P.x) - 6.0 * p, to_double(Q.x) + 6.0 * p, &ca, &cb);
+      for (i64 c = ca; c <= cb; ++c) {
+        if (!g.has_cell(c, j)) continue;
+        i64 ci[3], cj[3];
+        g.corners(c, j, ci, cj);
+        auto T = g.cell_pts(c, j);
+        i64 cid = g.cell_id(c, j);
+        for (int k = 0; k < 3; ++k) {
+          int k2 = (k + 1) % 3;
+          Alg1 a = alg1(T[k], T[k2], P, Q);
+          if (a.kind == EV_NONE) continue;
+          if (a.kind != EV_CROSS) throw std::runtime_error("degenerate event in the degeneracy-free class");
+          i64 eid = g.edge_id(ci[k], cj[k], ci[k2], cj[k2]);
+          cell_segs[cid].insert((i64)s);
+          if (ev.count({eid, (i64)s})) continue;
+          Z3 nx, ny;
+          i128 den;
+          line_meet(P, Q, T[k], T[k2], &nx, &ny, &den);
+          Pt X{exact_div(nx, den), exact_div(ny, den)};
+          /* lower endpoint of the edge: horizontal edges run +x, the others +y */
+          Z3 t = (cj[k] == cj[k2]) ? X.x : X.y;
+          ev[{eid, (i64)s}] = Event{eid, (i64)s, X, t};
+        }
+        for (int end = 0; end < 2; ++end) {
+          const Pt& E = end == 0 ? P : Q;
+          int o0 = orient(T[0], T[1], E), o1 = orient(T[1], T[2], E), o2 = orient(T[2], T[0], E);
+          if (o0 > 0 && o1 > 0 && o2 > 0) {
+            i64 ecx = sg.cx + (end == 1 && sg.dir == 0 ? sg.len : 0);
+            i64 ecy = sg.cy + (end == 1 && sg.dir == 1 ? sg.len : 0);
+            cell_segs[cid].insert((i64)s);
+            cell_chain[cid].push_back({ecy * (g.W + 1) + ecx, (i64)s});
+          } else if (o0 * o1 * o2 == 0 && o0 >= 0 && o1 >= 0 && o2 >= 0) {
+            throw std::runtime_error("segment end on a grid edge in the degeneracy-free class");
+          }
+        }
+      }
+    }
+  }
+
+  /* frozen registry: events ordered by edge id, then position along the edge */
+  std::vector<Event> evs;
+  for (auto& kv : ev) evs.push_back(kv.second);
+  std::sort(evs.begin(), evs.end(), [](const Event& a, const Event& b) {
+    if (a.edge != b.edge) return a.edge < b.edge;
+    return cmp(a.t, b.t) < 0;
+  });
+  std::map<std::pair<i64, i64>, i64> ev_gid; /* (edge, seg) -> vertex id */
+  std::map<i64, std::vector<i64>> edge_events; /* edge -> registry indices */
+  const i64 NVg = g.nverts;
+  for (size_t k = 0; k < evs.size(); ++k) {
+    ev_gid[{evs[k].edge, evs[k].seg}] = NVg + (i64)k;
+    edge_events[evs[k].edge].push_back((i64)k);
+  }
+  const i64 NE = (i64)evs.size();
+
+  /* chain vertices: by cell id, then pixel-corner id */
+  std::map<i64, std::vector<i64>> cell_corners; /* cell -> sorted unique corner ids */
+  i64 NC = 0;
+  for (auto& kv : cell_chain) {
+    std::vector<i64> cs;
+    for (auto& pr : kv.second) cs.push_back(pr.first);
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    cell_corners[kv.first] = cs;
+    NC += (i64)cs.size();
+  }
+  std::map<i64, i64> chain_base;
+  {
+    i64 b = NVg + NE;
+    for (auto& kv : cell_corners) chain_base[kv.first] = b, b += (i64)kv.second.size();
+  }
+
+  /* coordinates */
+  const i64 NV = NVg + NE + NC;
+  M.xy.assign(2 * NV, 0.0);
+  auto put_xy = [&](i64 id, const Pt& pt) {
+    M.xy[2 * id] = to_double(pt.x) / (double)S;
+    M.xy[2 * id + 1] = to_double(pt.y) / (double)S;
+  };
+  for (i64 j = g.vj0; j <= g.vj1; ++j)
+    for (i64 i = g.vlo[j - g.vj0]; i <= g.vhi[j - g.vj0]; ++i) put_xy(g.vid(i, j), g.vtx(i, j));
+  for (size_t k = 0; k < evs.size(); ++k) put_xy(NVg + (i64)k, evs[k].pt);
+  for (auto& kv : cell_corners)
+    for (size_t t = 0; t < kv.second.size(); ++t) {
+      i64 cid = kv.second[t];
+      put_xy(chain_base[kv.first] + (i64)t, g.pixcorner(cid % (g.W + 1), cid / (g.W + 1)));
+    }
+
+  /* cells in id order: untouched cells keep their base triangle, cut cells
+   * are replaced by the patch of their key (Alg. 2) */
+  M.nverts_grid = NVg;
+  M.ncells = g.ncells;
+  M.tri.reserve(3 * (size_t)g.ncells + 64);
+  for (i64 j = g.j0; j <= g.j1; ++j) {
+    for (i64 c = g.clo[j - g.j0]; c <= g.chi[j - g.j0]; ++c) {
+      i64 cid = g.cell_id(c, j);
+      i64 ci[3], cj[3];
+      g.corners(c, j, ci, cj);
+      auto T = g.cell_pts(c, j);
+      i64 gid[3] = {g.vid(ci[0], cj[0]), g.vid(ci[1], cj[1]), g.vid(ci[2], cj[2])};
+      auto cs = cell_segs.find(cid);
+      if (cs == cell_segs.end()) {
+        M.tri.insert(M.tri.end(), {(int32_t)gid[0], (int32_t)gid[1], (int32_t)gid[2]});
+        M.label.push_back(out_label(centroid_label(g, im, T[0], T[1], T[2])));
+        M.code.push_back(0);
+        continue;
+      }
+      /* local PSLG of the cut cell */
+      std::vector<Pt> lv(T.begin(), T.end());
+      std::vector<i64> lg(gid, gid + 3);
+      int nev[3];
+      std::map<i64, int> seg_event_local[3];
+      for (int k = 0; k < 3; ++k) {
+        int k2 = (k + 1) % 3;
+        i64 eid = g.edge_id(ci[k], cj[k], ci[k2], cj[k2]);
+        std::vector<i64> idx;
+        auto it = edge_events.find(eid);
+        if (it != edge_events.end()) idx = it->second;
+        /* registry order runs from the lower-id endpoint; the cell reads CCW
+         * from corner k to corner k+1 */
+        if (gid[k] > gid[k2]) std::reverse(idx.begin(), idx.end());
+        nev[k] = (int)idx.size();
+        for (i64 r : idx) {
+          seg_event_local[k][evs[r].seg] = (int)lv.size();
+          lv.push_back(evs[r].pt);
+          lg.push_back(NVg + r);
+        }
+      }
+      std::map<i64, int> corner_local;
+      auto cc = cell_corners.find(cid);
+      int nchain = 0;
+      if (cc != cell_corners.end()) {
+        nchain = (int)cc->second.size();
+        for (size_t t = 0; t < cc->second.size(); ++t) {
+          i64 corner = cc->second[t];
+          corner_local[corner] = (int)lv.size();
+          lv.push_back(g.pixcorner(corner % (g.W + 1), corner / (g.W + 1)));
+          lg.push_back(chain_base[cid] + (i64)t);
+        }
+      }
+      std::vector<std::pair<int, int>> ce;
+      for (i64 s : cs->second) {
+        const Segment& sg = M.segs[s];
+        std::vector<int> ends;
+        for (int k = 0; k < 3; ++k) {
+          auto f = seg_event_local[k].find(s);
+          if (f != seg_event_local[k].end()) ends.push_back(f->second);
+        }
+        i64 c0 = sg.cy * (g.W + 1) + sg.cx;
+        i64 c1 = sg.dir == 0 ? c0 + sg.len : c0 + sg.len * (g.W + 1);
+        for (i64 corner : {c0, c1}) {
+          auto f = corner_local.find(corner);
+          if (f != corner_local.end()) ends.push_back(f->second);
+        }
+        if (ends.size() != 2) throw std::runtime_error("segment piece without two ends");
+        /* orient along the segment: forward is +x / +y unless rev */
+        const Pt &a = lv[ends[0]], &b = lv[ends[1]];
+        int ord = sg.dir == 0 ? cmp(a.x, b.x) : cmp(a.y, b.y);
+        bool a_first = sg.rev ? (ord > 0) : (ord < 0);
+        ce.push_back(a_first ? std::make_pair(ends[0], ends[1]) : std::make_pair(ends[1], ends[0]));
+      }
+      LocalResult lr = classify_local(nev, nchain, ce);
+      std::vector<Tri> tris;
+      if (lr.tierG) {
+        std::vector<std::pair<int, int>> cons = ce;
+        /* boundary sub-edges: consecutive vertices of the CCW cycle of the cell */
+        std::vector<int> cyc;
+        int e = 3;
+        for (int k = 0; k < 3; ++k) {
+          cyc.push_back(k);
+          for (int t = 0; t < nev[k]; ++t) cyc.push_back(e++);
+        }
+        for (size_t t = 0; t < cyc.size(); ++t) cons.push_back({cyc[t], cyc[(t + 1) % cyc.size()]});
+        tris = greedy_triangulate(lv, cons);
+        M.n_tierG++;
+      } else {
+        tris = lr.tri;
+      }
+      int nb = 3 + nev[0] + nev[1] + nev[2];
+      if ((int)tris.size() != 2 * nchain + nb - 2) throw std::runtime_error("patch triangle count");
+      uint16_t code = make_code(lr);
+      for (auto& t : tris) {
+        if (orient(lv[t[0]], lv[t[1]], lv[t[2]]) <= 0) throw std::runtime_error("patch triangle not CCW");
+        M.tri.insert(M.tri.end(), {(int32_t)lg[t[0]], (int32_t)lg[t[1]], (int32_t)lg[t[2]]});
+        M.label.push_back(out_label(centroid_label(g, im, lv[t[0]], lv[t[1]], lv[t[2]])));
+        M.code.push_back(code);
+      }
+      M.cut_cell.push_back(cid);
+      M.cut_code.push_back(code);
+      M.cut_ntri.push_back((i64)tris.size());
+      M.cut_nchain.push_back(nchain);
+      M.cut_tierG.push_back(lr.tierG);
+    }
+  }
+  M.events = evs;
+}
+
+/* ------------------------------------------------------------------------- */
+char g_err[512];
+template <class T>
+T* dup(const std::vector<T>& v) {
+  T* p = (T*)std::malloc(sizeof(T) * (v.size() ? v.size() : 1));
+  if (!v.empty()) std::memcpy(p, v.data(), sizeof(T) * v.size());
+  return p;
+}
+
+}  // namespace
+
+/* ------------------------------------------------------------------------- */
+/* C interface (ctypes)                                                       */
+/* ------------------------------------------------------------------------- */
+extern "C" {
+
+typedef struct {
+  int64_t n_vertices, n_triangles, n_cells, n_cut_cells, n_tierG_cells, n_vertices_grid;
+  double* xy;
+  int32_t* tri;
+  uint16_t* label;
+  uint16_t* code;
+  int64_t n_segments;
+  int32_t* seg; /* 7 per segment: cx, cy, dir, len, lab0, lab1, rev */
+  int64_t n_events;
+  int64_t* ev; /* 3 per event in registry order: edge id, segment index, vertex id */
+  int64_t* cut; /* 5 per cut cell in id order: cell id, code, ntri, nchain, tierG */
+} oracle_mesh;
+
+const char* oracle_last_error(void) { return g_err; }
+
+/* 0 on success, -1 bad arguments (incl. parameters outside the
+ * degeneracy-free class), -2 internal consistency failure */
+int oracle_mesh_bitmap(const void* data, int32_t width, int32_t height, int64_t pitch_bytes, int32_t dtype,
+                       int32_t h_num, int32_t h_den, int32_t origin2x, int32_t origin2y, oracle_mesh* out) {
+  g_err[0] = 0;
+  if (!data || !out || width < 1 || height < 1 || width > 32768 || height > 32768 || (dtype != 1 && dtype != 2) ||
+      pitch_bytes < (int64_t)width * dtype || h_num < 1 || h_den < 1 || h_num > 4096 || h_den > 64 ||
+      (h_num % 2) != 0 || (h_den % 2) != 1 || (origin2x % 2) != 0 || (origin2y % 2) != 0) {
+    std::snprintf(g_err, sizeof g_err, "invalid arguments");
+    return -1;
+  }
+  try {
+    Image im{width, height, pitch_bytes, dtype, (const uint8_t*)data};
+    Mesh M;
+    mesh_image(im, h_num, h_den, origin2x, origin2y, M);
+    std::memset(out, 0, sizeof *out);
+    out->n_vertices = (int64_t)M.xy.size() / 2;
+    out->n_triangles = (int64_t)M.label.size();
+    out->n_cells = M.ncells;
+    out->n_cut_cells = (int64_t)M.cut_cell.size();
+    out->n_tierG_cells = M.n_tierG;
+    out->n_vertices_grid = M.nverts_grid;
+    out->xy = dup(M.xy);
+    out->tri = dup(M.tri);
+    out->label = dup(M.label);
+    out->code = dup(M.code);
+    out->n_segments = (int64_t)M.segs.size();
+    std::vector<int32_t> sg;
+    for (auto& s : M.segs)
+      sg.insert(sg.end(), {(int32_t)s.cx, (int32_t)s.cy, s.dir, (int32_t)s.len, s.lab0, s.lab1, s.rev});
+    out->seg = dup(sg);
+    out->n_events = (int64_t)M.events.size();
+    std::vector<int64_t> e;
+    for (size_t k = 0; k < M.events.size(); ++k)
+      e.insert(e.end(), {M.events[k].edge, M.events[k].seg, M.nverts_grid + (int64_t)k});
+    out->ev = dup(e);
+    std::vector<int64_t> cu;
+    for (size_t k = 0; k < M.cut_cell.size(); ++k)
+      cu.insert(cu.end(), {M.cut_cell[k], M.cut_code[k], M.cut_ntri[k], M.cut_nchain[k], M.cut_tierG[k]});
+    out->cut = dup(cu);
+    return 0;
+  } catch (const std::exception& ex) {
+    std::snprintf(g_err, sizeof g_err, "%s", ex.what());
+    return -2;
+  }
+}
+
+void oracle_mesh_free(oracle_mesh* m) {
+  if (!m) return;
+  std::free(m->xy), std::free(m->tri), std::free(m->label), std::free(m->code);
+  std::free(m->seg), std::free(m->ev), std::free(m->cut);
+  std::memset(m, 0, sizeof *m);
+}
+
+/* Alg. 1 on one triangle ABC (CCW) and one segment PQ given by integer
+ * coordinates (x + xs*sqrt3, y + ys*sqrt3), 4 numbers per point.  Writes the
+ * event kind for edges AB, BC, CA (0 none, 1 crossing, 2 vertex on L,
+ * 3 overlap) and returns the bitmask AB=2, BC=4, CA=8 (a vertex on L sets both
+ * incident edges, an overlap its own edge). */
+int oracle_alg1(const int64_t* tri12, const int64_t* seg8, int32_t* kinds3) {
+  Pt T[3], P[2];
+  for (int k = 0; k < 3; ++k) T[k] = Pt{z(tri12[4 * k], tri12[4 * k + 1]), z(tri12[4 * k + 2], tri12[4 * k + 3])};
+  for (int k = 0; k < 2; ++k) P[k] = Pt{z(seg8[4 * k], seg8[4 * k + 1]), z(seg8[4 * k + 2], seg8[4 * k + 3])};
+  int mask = 0;
+  for (int k = 0; k < 3; ++k) {
+    int k2 = (k + 1) % 3;
+    Alg1 a = alg1(T[k], T[k2], P[0], P[1]);
+    kinds3[k] = a.kind;
+    if (a.kind == EV_CROSS || a.kind == EV_OVERLAP) mask |= 2 << k;
+    /* vertex k is shared by edges k-1 and k; vertex k2 by edges k and k2 */
+    if (a.kind == EV_VERTEX) {
+      if (a.u_on) mask |= (2 << k) | (2 << ((k + 2) % 3));
+      if (a.v_on) mask |= (2 << k) | (2 << k2);
+    }
+  }
+  return mask;
+}
+
+/* crossing point of segment PQ with segment UV (coordinates as in
+ * oracle_alg1), as doubles in the same units; returns 0 if lines are parallel */
+int oracle_line_meet(const int64_t* pq8, const int64_t* uv8, double* xy2) {
+  Pt a{z(pq8[0], pq8[1]), z(pq8[2], pq8[3])}, b{z(pq8[4], pq8[5]), z(pq8[6], pq8[7])};
+  Pt u{z(uv8[0], uv8[1]), z(uv8[2], uv8[3])}, v{z(uv8[4], uv8[5]), z(uv8[6], uv8[7])};
+  Z3 dd = (b.x - a.x) * (v.y - u.y) - (b.y - a.y) * (v.x - u.x);
+  if (sgn(dd) == 0) return 0;
+  Z3 nx, ny;
+  i128 den;
+  line_meet(a, b, u, v, &nx, &ny, &den);
+  xy2[0] = to_double(nx) / (double)den;
+  xy2[1] = to_double(ny) / (double)den;
+  return 1;
+}
+
+/* Key and Tier-T patch of one cell from its combinatorial description:
+ * nev[3] events on AB, BC, CA (local indices 3.. in CCW order from A), nchain
+ * chain vertices after them, n_ce chain edges as oriented local index pairs.
+ * Writes key, sigma, class, mask, tierG into info5 and up to cap triangles
+ * (local indices) into tri; returns the triangle count (0 for Tier-G),
+ * -1 on a malformed description. */
+int oracle_local_patch(const int32_t* nev3, int32_t nchain, const int32_t* ce, int32_t n_ce, int32_t* info5,
+                       int32_t* tri, int32_t cap) {
+  try {
+    int nev[3] = {nev3[0], nev3[1], nev3[2]};
+    std::vector<std::pair<int, int>> e;
+    for (int k = 0; k < n_ce; ++k) e.push_back({ce[2 * k], ce[2 * k + 1]});
+    LocalResult r = classify_local(nev, nchain, e);
+    info5[0] = r.key, info5[1] = r.sigma, info5[2] = r.klass, info5[3] = r.mask, info5[4] = r.tierG;
+    if ((int)r.tri.size() > cap) return -1;
+    for (size_t t = 0; t < r.tri.size(); ++t)
+      for (int k = 0; k < 3; ++k) tri[3 * t + k] = r.tri[t][k];
+    return (int)r.tri.size();
+  } catch (const std::exception& ex) {
+    std::snprintf(g_err, sizeof g_err, "%s", ex.what());
+    return -1;
+  }
+}
+
+/* The lookup table: for key id k (1..15) writes its canonical code and its
+ * template (labels 0..2 = A',B',C', 3..6 = E0..E3, 7 = P); returns the number
+ * of triangles, 0 if the key does not exist. */
+int oracle_template(int32_t key, int32_t* code, int32_t* tri, int32_t cap) {
+  for (auto& kv : lut())
+    if (kv.second.key == key) {
+      *code = kv.first;
+      int n = (int)kv.second.tri.size();
+      if (n > cap) return -1;
+      for (int t = 0; t < n; ++t)
+        for (int k = 0; k < 3; ++k) tri[3 * t + k] = kv.second.tri[t][k];
+      return n;
+    }
+  return 0;
+}
+
+/* Greedy Tier-G triangulation of explicit points (integer coordinates as in
+ * oracle_alg1) with constraint edges; returns the triangle count or -1. */
+int oracle_greedy(const int64_t* pts4, int32_t n, const int32_t* cons, int32_t ncons, int32_t* tri, int32_t cap) {
+  std::vector<Pt> v;
+  for (int k = 0; k < n; ++k) v.push_back(Pt{z(pts4[4 * k], pts4[4 * k + 1]), z(pts4[4 * k + 2], pts4[4 * k + 3])});
+  std::vector<std::pair<int, int>> c;
+  for (int k = 0; k < ncons; ++k) c.push_back({cons[2 * k], cons[2 * k + 1]});
+  auto t = greedy_triangulate(v, c);
+  if ((int)t.size() > cap) return -1;
+  for (size_t q = 0; q < t.size(); ++q)
+    for (int k = 0; k < 3; ++k) tri[3 * q + k] = t[q][k];
+  return (int)t.size();
+}
+
+}  // extern "C"
