@@ -1,0 +1,159 @@
+/*
+ * sbmt.h -- C interface of the GB300 library for Structured Bitmap-to-Mesh
+ * Triangulation (SBMT, arXiv 2602.19474).
+ *
+ * The library turns a label bitmap into a conforming triangle mesh: it
+ * extracts the pixel-edge boundary of the labels (the "input boundary as
+ * prescribed prior" of Sec. 3.1), overlays the regular equilateral base grid
+ * of edge h (Sec. 3.3), classifies every segment/edge incidence by Alg. 1
+ * (Sec. 3.3.1), keys each cut grid triangle by its canonical configuration
+ * kappa(K) and replaces it by the patch of the single-valued lookup table
+ * (Sec. 3.3.3, Alg. 2, App. G), and leaves every uncut grid triangle as it is.
+ * All steps run in CUDA kernels on the GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every function returns an int: SBMT_OK (0) or a negative SBMT_E* code.
+ *    No function throws, aborts or traps.
+ *  - Pixels are unit squares centred at integer points; pixel (x, y) is
+ *    data[y * pitch + x]; y grows with the row index and the mesh is
+ *    counter-clockwise in that (x, y) frame.
+ *  - Outside the image the label is OUTSIDE, larger than every pixel label.
+ *    Triangles outside the image carry label 0xFFFF in the output (so a u16
+ *    pixel label 0xFFFF cannot be told from the outside there).
+ *  - Ownership: inputs stay owned by the caller and are only read; a host
+ *    image may be reused once mesh_bitmap returns, a device image must stay
+ *    valid until mesh_query reports the mesh done.  Outputs are device memory
+ *    owned by the context, valid until mesh_release or mesh_destroy.
+ *  - Threading: calls on one context are serialised by an internal mutex;
+ *    work is ordered on the context's stream.
+ */
+#ifndef SBMT_H
+#define SBMT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SBMT_OK 0
+#define SBMT_EINVAL (-1)    /* bad argument: dims, dtype, pitch, h, origin, mode */
+#define SBMT_ENOMEM (-2)    /* device allocation failed */
+#define SBMT_EPENDING (-3)  /* mesh_query poll: work not finished yet */
+#define SBMT_ETIMEDOUT (-4) /* mesh_query: wait limit reached */
+#define SBMT_ECAPACITY (-5) /* a cell holds more boundary vertices than the per-cell limit */
+#define SBMT_EPROTO (-6)    /* requested mode is not available (SBMT_PREPROCESS) */
+#define SBMT_ECUDA (-7)     /* a CUDA call failed (message in sbmt_last_error) */
+#define SBMT_EINTERNAL (-8) /* a device-side consistency check failed */
+#define SBMT_ENOENT (-9)    /* unknown mesh handle */
+
+typedef struct sbmt_ctx sbmt_ctx;
+typedef uint64_t sbmt_mesh;
+
+enum { SBMT_U8 = 1, SBMT_U16 = 2 };
+enum { SBMT_PLAIN = 0, SBMT_PREPROCESS = 1 };
+enum { SBMT_EXPLICIT = 0 };
+enum { SBMT_KEEP_STAGES = 1 }; /* sbmt_params.flags: keep intermediate arrays for mesh_stage */
+
+/* A label image.  width, height in 1..32768; pitch_bytes >= width * dtype
+ * bytes; data is a host pointer (on_device = 0) or a device pointer of the
+ * context's device (on_device = 1). */
+typedef struct {
+  int32_t width, height;
+  int64_t pitch_bytes;
+  int32_t dtype; /* SBMT_U8 or SBMT_U16 */
+  const void* data;
+  int32_t on_device;
+} sbmt_image;
+
+/* Meshing parameters.  h = h_num / h_den pixels (Sec. 3.3's edge length);
+ * the grid origin is (origin2x / 2, origin2y / 2).  Only the
+ * degeneracy-free class is accepted: h_num even in 2..1024, h_den odd in
+ * 1..63, origin2x and origin2y even.  Under it no grid vertex lies on a
+ * pixel line and no pixel corner on a grid edge, so every Alg. 1 event is a
+ * proper crossing; other parameters return SBMT_EINVAL.  mode must be
+ * SBMT_PLAIN (the thresholds a, b, c of Alg. 3 are reserved for
+ * SBMT_PREPROCESS, which returns SBMT_EPROTO); format must be
+ * SBMT_EXPLICIT. */
+typedef struct {
+  int32_t h_num, h_den;
+  int32_t origin2x, origin2y;
+  int32_t mode;
+  double a, b, c;
+  int32_t format;
+  int32_t flags;
+} sbmt_params;
+
+/* A finished mesh (device pointers, owned by the context).
+ *  xy    2 * n_vertices doubles: lattice vertices (row-major), then the
+ *        boundary/grid-edge intersection vertices ordered by grid-edge id and
+ *        position along the edge, then the boundary vertices inside cells
+ *        ordered by cell id and pixel-corner id;
+ *  tri   3 * n_triangles vertex ids, counter-clockwise, ordered by base cell
+ *        id and then by the patch's emission order;
+ *  label per triangle: label of the pixel holding its centroid, 0xFFFF outside;
+ *  code  per triangle: bits 0-3 Alg. 1 bitmask of its cell (AB=2, BC=4,
+ *        CA=8; bit 0 = a boundary vertex inside the cell), bits 4-5 the
+ *        rotation sigma, bits 6-11 the key id (0 uncut, 1..15 table keys,
+ *        63 outside Lemma 3.1's regime), bits 12-15 the (m,n) class as its
+ *        1-based position in Thm. 3.2's list (0 = not applicable). */
+typedef struct {
+  int64_t n_vertices, n_triangles, n_cells, n_cut_cells, n_tierG_cells;
+  const double* xy;
+  const int32_t* tri;
+  const uint16_t* label;
+  const uint16_t* code;
+  int32_t status; /* SBMT_OK, or the error the device work reported */
+} sbmt_mesh_view;
+
+/* Create a context on CUDA device `device`.  pool_bytes (0 = no limit) is
+ * the amount of freed device memory the context keeps cached for reuse;
+ * cuda_stream is a cudaStream_t to order work on, or NULL for a stream the
+ * context creates and owns. */
+int mesh_create(sbmt_ctx** ctx, int device, size_t pool_bytes, void* cuda_stream);
+
+/* Mesh one image (Sec. 3.3 grid, Alg. 1 classification, Alg. 2 lookup).
+ * Enqueues the work on the context's stream and returns a handle; the
+ * call synchronises with the device twice to size its buffers.  The mesh
+ * is complete when mesh_query returns SBMT_OK. */
+int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out);
+
+/* Mesh n images; params points to n parameter sets, or to one shared by
+ * all (n_params = 1).  out receives n handles. */
+int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+               sbmt_mesh* out);
+
+/* Wait up to wait_ms milliseconds (0 = poll, < 0 = no limit) for a mesh and
+ * fill *out.  Returns SBMT_EPENDING / SBMT_ETIMEDOUT while unfinished, or
+ * the mesh's status. */
+int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out);
+
+/* Free the device memory of one mesh (waits for its work first). */
+int mesh_release(sbmt_ctx* ctx, sbmt_mesh mesh);
+
+/* Release every mesh and destroy the context. */
+int mesh_destroy(sbmt_ctx* ctx);
+
+/* Intermediate arrays of a finished mesh made with SBMT_KEEP_STAGES, copied
+ * to host memory, for checking each step on its own:
+ *  stage 1 boundary segments, 8 int32 each: corner x, corner y, direction
+ *          (0 +x, 1 +y), length, label below/left, label above/right (0xFFFF
+ *          = outside), reversed (1 when the lower label lies left of -x/-y),
+ *          0;
+ *  stage 2 grid-edge events in vertex-id order, 4 int64 each: grid-edge id,
+ *          vertex id, packed segment start corner (y * (W + 1) + x), dir;
+ *  stage 3 cut cells in id order, 5 int64 each: cell id, code, triangles,
+ *          boundary vertices inside, outside-regime flag.
+ * Writes min(n, cap) records to host_out and the total count to *n. */
+int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n);
+
+/* Message of the last failing call on this thread (never NULL). */
+const char* sbmt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBMT_H */

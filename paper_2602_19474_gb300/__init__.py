@@ -1,0 +1,252 @@
+"""GB300 (sm_103a) implementation of the data-parallel hot path of Structured
+Bitmap-to-Mesh Triangulation (arXiv 2602.19474).
+
+This module is a thin ctypes binding of the C interface in include/sbmt.h
+(same names: mesh_create, mesh_bitmap, mesh_batch, mesh_query, mesh_release,
+mesh_destroy, mesh_stage).  It only marshals arguments: every step of the
+meshing runs in the CUDA kernels of libsbmt.so.  There is no CPU fallback;
+loading fails with an error if the library has not been built.
+
+PyTorch is used for device buffers: images may be passed as CUDA tensors,
+and finished meshes are exposed as zero-copy CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as build_library
+
+SBMT_OK = 0
+SBMT_EINVAL = -1
+SBMT_ENOMEM = -2
+SBMT_EPENDING = -3
+SBMT_ETIMEDOUT = -4
+SBMT_ECAPACITY = -5
+SBMT_EPROTO = -6
+SBMT_ECUDA = -7
+SBMT_EINTERNAL = -8
+SBMT_ENOENT = -9
+SBMT_U8, SBMT_U16 = 1, 2
+SBMT_PLAIN, SBMT_PREPROCESS = 0, 1
+SBMT_EXPLICIT = 0
+SBMT_KEEP_STAGES = 1
+
+EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
+           "sbmt_last_error")
+
+
+class sbmt_image(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch_bytes", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class sbmt_params(ctypes.Structure):
+    _fields_ = [("h_num", ctypes.c_int32), ("h_den", ctypes.c_int32), ("origin2x", ctypes.c_int32),
+                ("origin2y", ctypes.c_int32), ("mode", ctypes.c_int32), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("c", ctypes.c_double), ("format", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class sbmt_mesh_view(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("n_cut_cells", ctypes.c_int64), ("n_tierG_cells", ctypes.c_int64), ("xy", ctypes.c_void_p),
+                ("tri", ctypes.c_void_p), ("label", ctypes.c_void_p), ("code", ctypes.c_void_p),
+                ("status", ctypes.c_int32)]
+
+
+class SbmtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("sbmt error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libsbmt.so (built in-tree by build_library())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libsbmt.so is not built (%s); run paper_2602_19474_gb300.build_library()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.mesh_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, vp]
+    lib.mesh_bitmap.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params),
+                                ctypes.POINTER(ctypes.c_uint64)]
+    lib.mesh_batch.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_int, ctypes.POINTER(sbmt_params),
+                               ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mesh_query.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(sbmt_mesh_view)]
+    lib.mesh_release.argtypes = [vp, ctypes.c_uint64]
+    lib.mesh_destroy.argtypes = [vp]
+    lib.mesh_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+    lib.sbmt_last_error.restype = ctypes.c_char_p
+    for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
+              "mesh_stage"):
+        getattr(lib, f).restype = ctypes.c_int
+    del i32
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != SBMT_OK:
+        raise SbmtError(rc, load().sbmt_last_error().decode())
+
+
+def _image(img) -> tuple[sbmt_image, object]:
+    """sbmt_image for a numpy array (host) or a CUDA tensor (device); returns
+    the struct and the object that keeps the memory alive."""
+    if isinstance(img, np.ndarray):
+        a = np.ascontiguousarray(img)
+        if a.ndim != 2 or a.dtype not in (np.uint8, np.uint16):
+            raise ValueError("image must be a 2-D uint8 or uint16 array")
+        return sbmt_image(a.shape[1], a.shape[0], a.strides[0], a.itemsize, a.ctypes.data, 0), a
+    import torch
+
+    t = img
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2 and t.dtype in (torch.uint8, torch.int16)
+            or isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2 and str(t.dtype) == "torch.uint16"):
+        raise ValueError("device image must be a 2-D CUDA tensor of uint8 or 16-bit integers")
+    if t.stride(1) != 1:
+        t = t.contiguous()
+    item = t.element_size()
+    return sbmt_image(t.shape[1], t.shape[0], t.stride(0) * item, item, t.data_ptr(), 1), t
+
+
+def _params(h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0, keep_stages: bool = False,
+            mode: int = SBMT_PLAIN) -> sbmt_params:
+    return sbmt_params(h_num, h_den, origin2x, origin2y, mode, 0.0, 0.0, 0.0, SBMT_EXPLICIT,
+                       SBMT_KEEP_STAGES if keep_stages else 0)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI names
+# ---------------------------------------------------------------------------
+def mesh_create(device: int = 0, pool_bytes: int = 0, stream: int | None = None) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load().mesh_create(ctypes.byref(ctx), device, pool_bytes, stream))
+    return ctx.value
+
+
+def mesh_bitmap(ctx: int, img, h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0,
+                keep_stages: bool = False, mode: int = SBMT_PLAIN) -> int:
+    im, keep = _image(img)
+    pr = _params(h_num, h_den, origin2x, origin2y, keep_stages, mode)
+    out = ctypes.c_uint64()
+    _check(load().mesh_bitmap(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False) -> list[int]:
+    n = len(imgs)
+    ims, keeps = zip(*[_image(i) for i in imgs]) if n else ((), ())
+    arr = (sbmt_image * max(n, 1))(*ims)
+    hn = list(h_num) if isinstance(h_num, (list, tuple, np.ndarray)) else [h_num]
+    hd = list(h_den) if isinstance(h_den, (list, tuple, np.ndarray)) else [h_den] * len(hn)
+    prs = (sbmt_params * len(hn))(*[_params(int(a), int(b), keep_stages=keep_stages) for a, b in zip(hn, hd)])
+    out = (ctypes.c_uint64 * max(n, 1))()
+    _check(load().mesh_batch(ctx, arr, n, prs, len(hn), out))
+    del keeps
+    return [out[k] for k in range(n)]
+
+
+def mesh_query(ctx: int, mesh: int, wait_ms: int = -1) -> sbmt_mesh_view:
+    v = sbmt_mesh_view()
+    rc = load().mesh_query(ctx, mesh, wait_ms, ctypes.byref(v))
+    if rc in (SBMT_EPENDING, SBMT_ETIMEDOUT):
+        return None
+    _check(rc)
+    return v
+
+
+def mesh_release(ctx: int, mesh: int) -> None:
+    _check(load().mesh_release(ctx, mesh))
+
+
+def mesh_destroy(ctx: int) -> None:
+    _check(load().mesh_destroy(ctx))
+
+
+def mesh_stage(ctx: int, mesh: int, stage: int) -> np.ndarray:
+    width = {1: (8, np.int32), 2: (4, np.int64), 3: (5, np.int64)}[stage]
+    n = ctypes.c_int64(0)
+    _check(load().mesh_stage(ctx, mesh, stage, None, 0, ctypes.byref(n)))
+    buf = np.zeros((max(n.value, 1), width[0]), dtype=width[1])
+    _check(load().mesh_stage(ctx, mesh, stage, buf.ctypes.data, n.value, ctypes.byref(n)))
+    return buf[: n.value]
+
+
+# ---------------------------------------------------------------------------
+# device views of a finished mesh
+# ---------------------------------------------------------------------------
+class _CudaArray:
+    """__cuda_array_interface__ wrapper so torch can view library memory."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+def view_tensors(view: sbmt_mesh_view, owner=None) -> dict:
+    """Zero-copy torch CUDA tensors of a finished mesh (valid until release)."""
+    import torch
+
+    V, T = view.n_vertices, view.n_triangles
+    out = {
+        "xy": torch.as_tensor(_CudaArray(view.xy, (V, 2), "<f8", owner), device="cuda"),
+        "tri": torch.as_tensor(_CudaArray(view.tri, (T, 3), "<i4", owner), device="cuda"),
+        "label": torch.as_tensor(_CudaArray(view.label, (T,), "<i2", owner), device="cuda"),
+        "code": torch.as_tensor(_CudaArray(view.code, (T,), "<i2", owner), device="cuda"),
+    }
+    return out
+
+
+def view_numpy(view: sbmt_mesh_view) -> dict:
+    """Host copies of a finished mesh."""
+    t = view_tensors(view)
+    return {
+        "xy": t["xy"].cpu().numpy(),
+        "tri": t["tri"].cpu().numpy(),
+        "label": t["label"].cpu().numpy().view(np.uint16),
+        "code": t["code"].cpu().numpy().view(np.uint16),
+        "n_cells": view.n_cells,
+        "n_cut_cells": view.n_cut_cells,
+        "n_tierG_cells": view.n_tierG_cells,
+    }
+
+
+class Context:
+    """Convenience owner of a context handle."""
+
+    def __init__(self, device: int = 0, pool_bytes: int = 0, stream: int | None = None):
+        self.handle = mesh_create(device, pool_bytes, stream)
+
+    def mesh(self, img, h_num, h_den=1, **kw) -> int:
+        return mesh_bitmap(self.handle, img, h_num, h_den, **kw)
+
+    def result(self, mesh: int) -> dict:
+        return view_numpy(mesh_query(self.handle, mesh, -1))
+
+    def close(self):
+        if self.handle:
+            mesh_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

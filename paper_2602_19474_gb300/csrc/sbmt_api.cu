@@ -1,0 +1,534 @@
+// sbmt_api.cu -- the C interface (include/sbmt.h): context, buffers, grid
+// tables and the ordered launch of the hot-path kernels on one stream.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sbmt.h"
+#include "sbmt_launch.h"
+
+using namespace sbmt;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(SBMT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+// grid tables of Sec. 3.3's lattice, on the host: per strip row the range of
+// cells meeting the closed image rectangle, per vertex row the range of
+// lattice vertices they use
+struct Tables {
+  std::vector<i64> clo, chi, cbase, vlo, vhi, vbase;
+  i64 j0 = 0, vj0 = 0, ncells = 0, nverts = 0;
+};
+
+int build_tables(const GridP& g, Tables& t) {
+  const i64 p = g.p, q = g.q, ox = g.ox, oy = g.oy, P6 = 6 * p;
+  const i64 xl = -3 * q, xr = 6 * q * g.W - 3 * q, yl = -3 * q, yr = 6 * q * g.H - 3 * q;
+  const i64 j0 = strip_of(g, zq(yl)), j1 = strip_of(g, zq(yr));
+  t.j0 = j0;
+  const i64 nrows = j1 - j0 + 1;
+  t.clo.resize(nrows), t.chi.resize(nrows), t.cbase.resize(nrows);
+  i64 base = 0;
+  for (i64 j = j0; j <= j1; ++j) {
+    const Zq yj = zq(oy, 3 * p * j), yj1 = zq(oy, 3 * p * (j + 1));
+    // the band of the strip inside the rectangle is [ya, yb]; an up cell is
+    // widest at ya, a down cell at yb; da, db = the slant offsets there
+    const Zq da = zcmp(yj, zq(yl)) >= 0 ? zq(0) : Zq{-3 * p * j, (yl - oy) / 3};
+    const Zq db = zcmp(yj1, zq(yr)) <= 0 ? zq(0) : Zq{3 * p * (j + 1), -(yr - oy) / 3};
+    const i64 iu_hi = zfloordiv(zq(xr - ox - 3 * p * j) - da, P6);
+    const i64 iu_lo = -zfloordiv(zq(-(xl - ox - 3 * p * j - P6)) - da, P6);
+    const i64 id_hi = zfloordiv(zq(xr - ox - 3 * p * (j + 1)) - db, P6);
+    const i64 id_lo = -zfloordiv(zq(-(xl - ox - 3 * p * (j + 3))) - db, P6);
+    i64 lo = INT64_MAX, hi = INT64_MIN;
+    if (iu_lo <= iu_hi) lo = std::min(lo, 2 * iu_lo), hi = std::max(hi, 2 * iu_hi);
+    if (id_lo <= id_hi) lo = std::min(lo, 2 * id_lo + 1), hi = std::max(hi, 2 * id_hi + 1);
+    if (lo > hi) return fail(SBMT_EINTERNAL, "empty cell row %lld", (long long)j);
+    // the union of both families must be contiguous: every even c in
+    // [lo, hi] an up cell, every odd c a down cell
+    auto fl2 = [](i64 x) { return x >> 1; };
+    auto ce2 = [](i64 x) { return -((-x) >> 1); };
+    const bool even_ok = ce2(lo) > fl2(hi) || (iu_lo <= ce2(lo) && iu_hi >= fl2(hi));
+    const bool odd_ok = ce2(lo - 1) > fl2(hi - 1) || (id_lo <= ce2(lo - 1) && id_hi >= fl2(hi - 1));
+    if (!even_ok || !odd_ok) return fail(SBMT_EINTERNAL, "cell row %lld not contiguous", (long long)j);
+    t.clo[j - j0] = lo, t.chi[j - j0] = hi, t.cbase[j - j0] = base;
+    base += hi - lo + 1;
+  }
+  t.ncells = base;
+  // vertex rows j0 .. j1 + 1: row j holds the bottom vertices of strip j and
+  // the top vertices of strip j - 1
+  t.vj0 = j0;
+  const i64 nv = nrows + 1;
+  t.vlo.assign(nv, INT64_MAX), t.vhi.assign(nv, INT64_MIN), t.vbase.resize(nv);
+  for (i64 r = 0; r < nrows; ++r) {
+    const i64 lo = t.clo[r], hi = t.chi[r];
+    // up(i): bottom i, i+1, top i; down(i): bottom i+1, top i, i+1
+    const i64 bmin = (lo & 1) ? (lo >> 1) + 1 : (lo >> 1), bmax = (hi >> 1) + 1;
+    const i64 tmin = lo >> 1, tmax = (hi & 1) ? (hi >> 1) + 1 : (hi >> 1);
+    t.vlo[r] = std::min(t.vlo[r], bmin), t.vhi[r] = std::max(t.vhi[r], bmax);
+    t.vlo[r + 1] = std::min(t.vlo[r + 1], tmin), t.vhi[r + 1] = std::max(t.vhi[r + 1], tmax);
+  }
+  for (i64 r = 1; r < nrows; ++r) {
+    // the two contributions to an inner row overlap (cells of adjacent strips share it)
+    const i64 lo = t.clo[r], hi = t.chi[r];
+    const i64 bmin = (lo & 1) ? (lo >> 1) + 1 : (lo >> 1), bmax = (hi >> 1) + 1;
+    const i64 tmin = t.clo[r - 1] >> 1, tmax = (t.chi[r - 1] & 1) ? (t.chi[r - 1] >> 1) + 1 : (t.chi[r - 1] >> 1);
+    if (bmin > tmax + 1 || tmin > bmax + 1) return fail(SBMT_EINTERNAL, "vertex row %lld split", (long long)r);
+  }
+  base = 0;
+  for (i64 r = 0; r < nv; ++r) t.vbase[r] = base, base += t.vhi[r] - t.vlo[r] + 1;
+  t.nverts = base;
+  return SBMT_OK;
+}
+
+struct MeshRec {
+  sbmt_mesh id = 0;
+  cudaEvent_t done = nullptr;
+  void* out_block = nullptr;
+  double* xy = nullptr;
+  int* tri = nullptr;
+  unsigned short* label = nullptr;
+  unsigned short* code = nullptr;
+  int64_t nv = 0, nt = 0, ncells = 0;
+  u32* h_info = nullptr;  // pinned: err, ncut, ntierg
+  int W = 0;
+  // kept intermediates (SBMT_KEEP_STAGES)
+  bool keep = false;
+  Seg* segs = nullptr;
+  u32 nseg = 0;
+  Event* ev = nullptr;
+  u32 ne = 0;
+  CutRec* recs = nullptr;
+  u32* bstat = nullptr;
+  u32* poff = nullptr;
+  u32 nbc = 0, np = 0;
+  std::vector<void*> scratch;  // device memory freed with the mesh
+};
+
+}  // namespace
+
+struct sbmt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::mutex mu;
+  std::map<sbmt_mesh, MeshRec*> meshes;
+  sbmt_mesh next = 1;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(sbmt_ctx* ctx, T** p, size_t count, std::vector<void*>& track) {
+  void* v = nullptr;
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMallocAsync(&v, bytes, ctx->stream);
+  if (e != cudaSuccess) return fail(SBMT_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  track.push_back(v);
+  *p = (T*)v;
+  return SBMT_OK;
+}
+
+void free_list(sbmt_ctx* ctx, std::vector<void*>& v) {
+  for (void* p : v) cudaFreeAsync(p, ctx->stream);
+  v.clear();
+}
+
+void destroy_mesh(sbmt_ctx* ctx, MeshRec* m) {
+  if (m->done) cudaEventSynchronize(m->done);
+  free_list(ctx, m->scratch);
+  if (m->out_block) cudaFreeAsync(m->out_block, ctx->stream);
+  if (m->done) cudaEventDestroy(m->done);
+  if (m->h_info) cudaFreeHost(m->h_info);
+  delete m;
+}
+
+int check_params(const sbmt_image* img, const sbmt_params* pr) {
+  if (!img || !pr || !img->data) return fail(SBMT_EINVAL, "null image or params");
+  if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768)
+    return fail(SBMT_EINVAL, "image size %dx%d outside 1..32768", img->width, img->height);
+  if (img->dtype != SBMT_U8 && img->dtype != SBMT_U16) return fail(SBMT_EINVAL, "dtype %d", img->dtype);
+  if (img->pitch_bytes < (int64_t)img->width * img->dtype) return fail(SBMT_EINVAL, "pitch too small");
+  if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is not available");
+  if (pr->mode != SBMT_PLAIN || pr->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "mode/format");
+  if (pr->h_num < 2 || pr->h_num > 1024 || (pr->h_num & 1) || pr->h_den < 1 || pr->h_den > 63 ||
+      !(pr->h_den & 1))
+    return fail(SBMT_EINVAL, "h = %d/%d outside the degeneracy-free class (even h_num <= 1024, odd h_den < 64)",
+                pr->h_num, pr->h_den);
+  if ((pr->origin2x & 1) || (pr->origin2y & 1) || pr->origin2x < -65536 || pr->origin2x > 65536 ||
+      pr->origin2y < -65536 || pr->origin2y > 65536)
+    return fail(SBMT_EINVAL, "origin must be integer pixels within +-32768");
+  return SBMT_OK;
+}
+
+int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
+  int rc = check_params(img, pr);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  CK(cudaSetDevice(ctx->device));
+  GridP g{};
+  g.W = img->width, g.H = img->height;
+  g.p = pr->h_num, g.q = pr->h_den, g.S = 6 * g.q;
+  g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
+  Tables tb;
+  if ((rc = build_tables(g, tb))) return rc;
+  if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
+    return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
+  MeshRec* m = new MeshRec();
+  m->W = g.W;
+  m->keep = (pr->flags & SBMT_KEEP_STAGES) != 0;
+  std::vector<void*> tmp;  // scratch freed at the end of the call (unless kept)
+  auto bail = [&](int code) {
+    free_list(ctx, tmp);
+    destroy_mesh(ctx, m);
+    return code;
+  };
+  if (cudaMallocHost(&m->h_info, 8 * sizeof(u32)) != cudaSuccess) return bail(fail(SBMT_ENOMEM, "pinned info"));
+  std::memset(m->h_info, 0, 8 * sizeof(u32));
+  // image on the device
+  const unsigned char* dimg;
+  i64 pitch;
+  if (img->on_device) {
+    dimg = (const unsigned char*)img->data;
+    pitch = img->pitch_bytes;
+  } else {
+    unsigned char* d;
+    pitch = (i64)img->width * img->dtype;
+    if ((rc = dalloc(ctx, &d, (size_t)pitch * img->height, tmp))) return bail(rc);
+    if (cudaMemcpy2DAsync(d, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
+      return bail(fail(SBMT_ECUDA, "image upload"));
+    dimg = d;
+  }
+  // tables
+  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
+  i64* dt;
+  if ((rc = dalloc(ctx, &dt, 3 * nrows + 3 * nvr, tmp))) return bail(rc);
+  {
+    std::vector<i64> all;
+    all.insert(all.end(), tb.clo.begin(), tb.clo.end());
+    all.insert(all.end(), tb.chi.begin(), tb.chi.end());
+    all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
+    all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
+    all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
+    all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
+    if (cudaMemcpyAsync(dt, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, st))
+      return bail(fail(SBMT_ECUDA, "tables upload"));
+    if (cudaStreamSynchronize(st)) return bail(fail(SBMT_ECUDA, "tables upload sync"));
+  }
+  g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
+  g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
+  g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
+  g.ncells = tb.ncells, g.nverts = tb.nverts;
+
+  // counters: [0] nvtx (u64), [1] totals pairs, [2] totals events, then u32s
+  unsigned long long* cnt64;
+  if ((rc = dalloc(ctx, &cnt64, 8, tmp))) return bail(rc);
+  u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, pad...
+  CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
+  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2;
+
+  // K1a
+  const int W = g.W, H = g.H;
+  const int wpr = (W + 1 + 31) / 32, wpc = (H + 1 + 31) / 32;
+  u32 *vrow, *vcol;
+  if ((rc = dalloc(ctx, &vrow, (size_t)wpr * (H + 1), tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &vcol, (size_t)wpc * (W + 1), tmp))) return bail(rc);
+  launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st);
+  unsigned long long h64[4];
+  CK(cudaMemcpyAsync(h64, cnt64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const u64 NC = h64[0];
+  // K1b: every vertex starts at most two runs (+x and +y)
+  const u32 seg_cap = (u32)std::max<u64>(2 * NC, 1);
+  Seg* segs;
+  if ((rc = dalloc(ctx, &segs, seg_cap, tmp))) return bail(rc);
+  launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st);
+  // K2 count
+  const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
+  const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
+  u32 *pcnt, *ecnt;
+  if ((rc = dalloc(ctx, &pcnt, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &ecnt, nbe + 1, tmp))) return bail(rc);
+  CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
+  CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
+  launch_traverse_count(g, segs, nseg, seg_cap, pcnt, ecnt, cnt64 + 1, err, st);
+  CK(cudaMemcpyAsync(h64, cnt64, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  u32 h32[4];
+  CK(cudaMemcpyAsync(h32, cnt32, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h32[1]) return bail(fail(SBMT_EINTERNAL, "device check failed during traversal (0x%x)", h32[1]));
+  const u32 nsegs = h32[0];
+  if (nsegs > seg_cap) return bail(fail(SBMT_EINTERNAL, "segment count %u above bound %u", nsegs, seg_cap));
+  const u64 NP = h64[1], NE = h64[2];
+  const u64 NVg = (u64)tb.nverts;
+  const u64 V = NVg + NE + NC, T = (u64)tb.ncells + 2 * NC + 2 * NE;
+  if (V >= (1ull << 31) || T >= (1ull << 31) || NP >= (1ull << 32))
+    return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T));
+  // buckets
+  u32 *poff, *eoff, *pcur, *ecur;
+  if ((rc = dalloc(ctx, &poff, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &eoff, nbe + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &pcur, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &ecur, nbe + 1, tmp))) return bail(rc);
+  launch_scan(pcnt, 1, poff, nbc, st);
+  launch_scan(ecnt, 1, eoff, nbe, st);
+  CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  Pair *pairs, *sorted;
+  Event* ev;
+  CutRec* recs;
+  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist;
+  std::vector<void*>& keep = m->keep ? m->scratch : tmp;
+  if ((rc = dalloc(ctx, &pairs, NP, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &sorted, NP, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &ev, NE, keep))) return bail(rc);
+  if ((rc = dalloc(ctx, &recs, NP, keep))) return bail(rc);
+  if ((rc = dalloc(ctx, &bstat, 4 * (size_t)nbc + 4, keep))) return bail(rc);
+  if ((rc = dalloc(ctx, &extra_scan, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &chain_scan, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &cut_scan, nbc + 1, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &glist, NP, tmp))) return bail(rc);
+  if (m->keep) {
+    // keep the segments and bucket offsets too: move them to the mesh
+    for (auto it = tmp.begin(); it != tmp.end(); ++it)
+      if (*it == (void*)segs || *it == (void*)poff) {
+        m->scratch.push_back(*it);
+        *it = nullptr;
+      }
+    tmp.erase(std::remove(tmp.begin(), tmp.end(), nullptr), tmp.end());
+  }
+  // outputs
+  const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
+  const size_t off_tri = (bxy + 255) & ~(size_t)255, off_lab = (off_tri + btri + 255) & ~(size_t)255;
+  const size_t off_code = (off_lab + blab + 255) & ~(size_t)255, total = off_code + bcode + 256;
+  if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
+    return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
+  m->xy = (double*)m->out_block;
+  m->tri = (int*)((char*)m->out_block + off_tri);
+  m->label = (unsigned short*)((char*)m->out_block + off_lab);
+  m->code = (unsigned short*)((char*)m->out_block + off_code);
+  m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
+  // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
+  launch_traverse_emit(g, segs, nseg, seg_cap, pcur, ecur, pairs, ev, err, st);
+  launch_rank_events(g, ev, eoff, nbe, (u32)NVg, m->xy, st);
+  launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st);
+  launch_scan(bstat + 1, 4, extra_scan, nbc, st);
+  launch_scan(bstat + 2, 4, chain_scan, nbc, st);
+  launch_scan(bstat + 0, 4, cut_scan, nbc, st);
+  launch_emit(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
+              (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, err, st);
+  launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, (u32)NVg, (u32)NE, m->tri,
+               m->label, m->code, m->xy, err, st);
+  launch_lattice_xy(g, m->xy, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(m->h_info + 1, cut_scan + nbc, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(m->h_info + 2, nglist, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  if (m->keep) {
+    // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
+    m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bstat = bstat;
+    m->poff = poff, m->nbc = nbc, m->np = (u32)NP;
+  }
+  free_list(ctx, tmp);
+  if (cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(SBMT_ECUDA, "event create"));
+  CK(cudaEventRecord(m->done, st));
+  m->id = ctx->next++;
+  ctx->meshes[m->id] = m;
+  *out = m->id;
+  return SBMT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbmt_last_error(void) { return g_last_error.c_str(); }
+
+int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream) {
+  if (!out) return fail(SBMT_EINVAL, "null ctx pointer");
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(SBMT_ECUDA, "no CUDA device");
+  if (device < 0 || device >= n) return fail(SBMT_EINVAL, "device %d of %d", device, n);
+  CK(cudaSetDevice(device));
+  sbmt_ctx* ctx = new sbmt_ctx();
+  ctx->device = device;
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return fail(SBMT_ECUDA, "stream create");
+    }
+    ctx->own_stream = true;
+  }
+  // keep freed stream-ordered memory cached for the next call
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    u64 thr = pool_bytes ? (u64)pool_bytes : ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = ctx;
+  return SBMT_OK;
+}
+
+int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return mesh_one(ctx, img, params, out);
+}
+
+int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+               sbmt_mesh* out) {
+  if (!ctx || !imgs || !params || !out || n < 0 || (n_params != 1 && n_params != n))
+    return fail(SBMT_EINVAL, "bad batch arguments");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (int k = 0; k < n; ++k) {
+    const int rc = mesh_one(ctx, imgs + k, params + (n_params == 1 ? 0 : k), out + k);
+    if (rc) {
+      for (int u = 0; u < k; ++u) {
+        auto it = ctx->meshes.find(out[u]);
+        if (it != ctx->meshes.end()) destroy_mesh(ctx, it->second), ctx->meshes.erase(it);
+      }
+      return rc;
+    }
+  }
+  return SBMT_OK;
+}
+
+int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) {
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  MeshRec* m;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->meshes.find(mesh);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh %llu", (unsigned long long)mesh);
+    m = it->second;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    const cudaError_t q = cudaEventQuery(m->done);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return fail(SBMT_ECUDA, "mesh work failed: %s", cudaGetErrorString(q));
+    if (wait_ms == 0) return SBMT_EPENDING;
+    if (wait_ms > 0 &&
+        std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(wait_ms))
+      return SBMT_ETIMEDOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  std::memset(out, 0, sizeof *out);
+  out->n_vertices = m->nv, out->n_triangles = m->nt, out->n_cells = m->ncells;
+  out->n_cut_cells = m->h_info[1], out->n_tierG_cells = m->h_info[2];
+  out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;
+  const u32 e = m->h_info[0];
+  out->status = e == 0 ? SBMT_OK : (e & ERR_CAPACITY) ? SBMT_ECAPACITY : SBMT_EINTERNAL;
+  if (out->status) fail(out->status, "device reported error bits 0x%x", e);
+  return out->status;
+}
+
+int mesh_release(sbmt_ctx* ctx, sbmt_mesh mesh) {
+  if (!ctx) return fail(SBMT_EINVAL, "null ctx");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->meshes.find(mesh);
+  if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+  destroy_mesh(ctx, it->second);
+  ctx->meshes.erase(it);
+  return SBMT_OK;
+}
+
+int mesh_destroy(sbmt_ctx* ctx) {
+  if (!ctx) return fail(SBMT_EINVAL, "null ctx");
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto& kv : ctx->meshes) destroy_mesh(ctx, kv.second);
+    ctx->meshes.clear();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+  return SBMT_OK;
+}
+
+int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n) {
+  if (!ctx || !n) return fail(SBMT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->meshes.find(mesh);
+  if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+  MeshRec* m = it->second;
+  if (!m->keep) return fail(SBMT_EINVAL, "mesh made without SBMT_KEEP_STAGES");
+  CK(cudaEventSynchronize(m->done));
+  if (stage == 1) {
+    std::vector<Seg> s(m->nseg);
+    CK(cudaMemcpy(s.data(), m->segs, s.size() * sizeof(Seg), cudaMemcpyDeviceToHost));
+    *n = (int64_t)s.size();
+    int32_t* o = (int32_t*)host_out;
+    for (int64_t k = 0; k < std::min<int64_t>(cap, *n); ++k) {
+      const Seg& x = s[k];
+      const int32_t rec[8] = {x.cx, x.cy, seg_dir(x), seg_len(x), (int32_t)(x.lab & 0xFFFF),
+                              (int32_t)(x.lab >> 16), seg_rev(x), 0};
+      std::memcpy(o + 8 * k, rec, sizeof rec);
+    }
+    return SBMT_OK;
+  }
+  if (stage == 2) {
+    std::vector<Event> e(m->ne);
+    std::vector<Seg> s(m->nseg);
+    CK(cudaMemcpy(e.data(), m->ev, e.size() * sizeof(Event), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.data(), m->segs, s.size() * sizeof(Seg), cudaMemcpyDeviceToHost));
+    std::sort(e.begin(), e.end(), [](const Event& a, const Event& b) { return a.gid < b.gid; });
+    *n = (int64_t)e.size();
+    int64_t* o = (int64_t*)host_out;
+    for (int64_t k = 0; k < std::min<int64_t>(cap, *n); ++k) {
+      const Seg& x = s[e[k].seg];
+      const int64_t rec[4] = {(int64_t)e[k].edge, (int64_t)e[k].gid, (int64_t)x.cy * (m->W + 1) + x.cx,
+                              (int64_t)seg_dir(x)};
+      std::memcpy(o + 4 * k, rec, sizeof rec);
+    }
+    return SBMT_OK;
+  }
+  if (stage == 3) {
+    std::vector<CutRec> r(m->np);
+    std::vector<u32> bs(4 * (size_t)m->nbc), po(m->nbc + 1);
+    CK(cudaMemcpy(r.data(), m->recs, r.size() * sizeof(CutRec), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bs.data(), m->bstat, bs.size() * sizeof(u32), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(po.data(), m->poff, po.size() * sizeof(u32), cudaMemcpyDeviceToHost));
+    int64_t k = 0;
+    int64_t* o = (int64_t*)host_out;
+    for (u32 b = 0; b < m->nbc; ++b)
+      for (u32 u = 0; u < bs[4 * b]; ++u, ++k) {
+        const CutRec& c = r[po[b] + u];
+        if (k < cap) {
+          const int64_t rec[5] = {(int64_t)c.cell, (int64_t)(c.code & 0xFFFF), (int64_t)c.ntri, (int64_t)c.nchain,
+                                  (int64_t)((c.code >> 16) & 1)};
+          std::memcpy(o + 5 * k, rec, sizeof rec);
+        }
+      }
+    *n = k;
+    return SBMT_OK;
+  }
+  return fail(SBMT_EINVAL, "unknown stage %d", stage);
+}
+
+}  // extern "C"

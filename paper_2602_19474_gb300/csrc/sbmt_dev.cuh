@@ -1,0 +1,199 @@
+// sbmt_dev.cuh -- device-side definitions shared by the SBMT kernels.
+//
+// Geometry is exact.  With h = p/q and S = 6q, every point the method
+// touches (grid vertices, pixel corners, boundary/grid-edge crossings) has
+// coordinates (a + b*sqrt3)/S with integers a, b (Sec. 3.3 grid
+// v(i,j) = o + h(i + j/2, (sqrt3/2) j); pixel corners at half-integers).  The
+// kernels keep such numbers as Zq{a, b} in 64-bit integers and decide every
+// predicate by an exact sign test; no tolerance is ever used.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define SBMT_DEV __device__ __forceinline__
+#define SBMT_HD __host__ __device__ __forceinline__
+
+namespace sbmt {
+
+typedef long long i64;
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u32 NONE = 0xFFFFFFFFu;
+constexpr int OUTSIDE = 0x10000;  // label outside the image: above every pixel label
+constexpr int CB_LOG = 10;        // base cells per cell bucket (2^10)
+constexpr int EB_LOG = 11;        // grid-edge ids per event bucket (2^11)
+
+// device error bits (reported through mesh_query)
+enum : u32 {
+  ERR_TRAVERSAL = 1u,  // a segment left the cell set / inconsistent walk
+  ERR_CAPACITY = 2u,   // a Tier-G cell exceeded the per-cell vertex limit
+  ERR_COUNT = 4u,      // a patch did not have the expected triangle count
+  ERR_SEGBUF = 8u,     // segment buffer too small (retried by the host)
+};
+
+// ---------------------------------------------------------------------------
+// exact numbers a + b*sqrt(3)
+// ---------------------------------------------------------------------------
+struct Zq {
+  i64 a, b;
+};
+SBMT_HD Zq zq(i64 a, i64 b = 0) { return Zq{a, b}; }
+SBMT_HD Zq operator+(Zq x, Zq y) { return Zq{x.a + y.a, x.b + y.b}; }
+SBMT_HD Zq operator-(Zq x, Zq y) { return Zq{x.a - y.a, x.b - y.b}; }
+SBMT_HD Zq operator*(Zq x, Zq y) { return Zq{x.a * y.a + 3 * x.b * y.b, x.a * y.b + x.b * y.a}; }
+// sign of a + b sqrt3: when a and b disagree in sign compare a^2 with 3 b^2
+SBMT_HD int zsign(Zq v) {
+  if (v.b == 0) return (v.a > 0) - (v.a < 0);
+  if (v.a == 0) return (v.b > 0) - (v.b < 0);
+  if ((v.a > 0) == (v.b > 0)) return v.a > 0 ? 1 : -1;
+  i64 l = v.a * v.a, r = 3 * v.b * v.b;
+  if (v.a > 0) return l > r ? 1 : -1;
+  return r > l ? 1 : -1;
+}
+SBMT_HD int zcmp(Zq x, Zq y) { return zsign(x - y); }
+SBMT_HD double zdouble(Zq v) { return (double)v.a + (double)v.b * 1.7320508075688772935; }
+
+// floor(v / d) for d > 0, exact
+SBMT_HD i64 zfloordiv(Zq v, i64 d) {
+  i64 k = (i64)floor(zdouble(v) / (double)d);
+  while (zsign(v - zq(k * d)) < 0) --k;
+  while (zsign(v - zq((k + 1) * d)) >= 0) ++k;
+  return k;
+}
+SBMT_HD i64 ifloordiv(i64 a, i64 d) {  // d > 0
+  i64 q = a / d;
+  if ((a % d != 0) && (a < 0)) --q;
+  return q;
+}
+
+// 2-D point with exact coordinates (K-local points fit in 32 bits)
+struct Pq {
+  Zq x, y;
+};
+SBMT_HD int orient3(const Pq& p, const Pq& q, const Pq& r) {
+  return zsign((q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x));
+}
+
+// ---------------------------------------------------------------------------
+// records
+// ---------------------------------------------------------------------------
+// boundary segment: a maximal straight run of boundary pixel edges between
+// two PSLG vertices, starting at its lower corner (cx, cy)
+struct Seg {
+  int cx, cy;
+  u32 ldr;  // length | dir << 30 (0 = +x, 1 = +y) | rev << 31 (oriented -x / -y)
+  u32 lab;  // label below/left | label above/right << 16 (0xFFFF = outside)
+};
+SBMT_HD int seg_len(const Seg& s) { return (int)(s.ldr & 0x3FFFFFFFu); }
+SBMT_HD int seg_dir(const Seg& s) { return (int)((s.ldr >> 30) & 1u); }
+SBMT_HD int seg_rev(const Seg& s) { return (int)(s.ldr >> 31); }
+
+// a segment's visit of one base cell; ev_in / ev_out are the events where the
+// walk (from the lower end, along +x / +y) enters / leaves the cell, NONE
+// when the walk starts / ends inside it
+struct Pair {
+  u32 cell, seg, ev_in, ev_out;
+};
+
+// a crossing of a boundary segment with a grid edge; xa..yb are the exact
+// global scaled coordinates, gid the vertex id once the registry is frozen
+struct Event {
+  u32 edge, seg, gid, pad;
+  int xa, xb, ya, yb;
+};
+
+// one cut cell
+struct CutRec {
+  u32 cell, pair_lo, npairs, code;  // code: bits 0-15 pattern code, bit 16 outside-regime
+  u32 ntri, nchain, tri_off, chain_base;
+};
+
+// ---------------------------------------------------------------------------
+// grid (Sec. 3.3): strip rows j, cells c = 2i (up) / 2i+1 (down) per row
+// ---------------------------------------------------------------------------
+struct GridP {
+  int W, H;
+  i64 p, q, S, ox, oy;  // h = p/q, S = 6q, origin scaled by S
+  int j0, nrows;        // strip rows meeting the image rectangle
+  int vj0, nvrows;      // lattice vertex rows used
+  const i64* clo;       // per strip row: first cell index c
+  const i64* chi;       // per strip row: last cell index c
+  const i64* cbase;     // per strip row: id of its first cell
+  const i64* vlo;       // per vertex row: first i
+  const i64* vhi;
+  const i64* vbase;     // per vertex row: id of its first vertex
+  i64 ncells, nverts;
+};
+
+SBMT_DEV u32 vid(const GridP& g, i64 i, i64 j) {
+  int r = (int)(j - g.vj0);
+  return (u32)(g.vbase[r] + (i - g.vlo[r]));
+}
+SBMT_DEV bool cell_in(const GridP& g, i64 c, i64 j) {
+  if (j < g.j0 || j >= g.j0 + g.nrows) return false;
+  int r = (int)(j - g.j0);
+  return c >= g.clo[r] && c <= g.chi[r];
+}
+SBMT_DEV u32 cell_id(const GridP& g, i64 c, i64 j) {
+  int r = (int)(j - g.j0);
+  return (u32)(g.cbase[r] + (c - g.clo[r]));
+}
+// strip row of a cell id (binary search over the row bases)
+SBMT_DEV int cell_row(const GridP& g, u32 cid) {
+  int lo = 0, hi = g.nrows - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.cbase[mid] <= (i64)cid) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// lattice indices of corners A, B, C of cell c in strip j; A is the corner
+// with least (y, x), then counter-clockwise
+SBMT_DEV void cell_corners(i64 c, i64 j, i64* ci, i64* cj) {
+  i64 i = c >> 1;  // floor(c / 2)
+  if ((c & 1) == 0) {
+    ci[0] = i, cj[0] = j, ci[1] = i + 1, cj[1] = j, ci[2] = i, cj[2] = j + 1;
+  } else {
+    ci[0] = i + 1, cj[0] = j, ci[1] = i + 1, cj[1] = j + 1, ci[2] = i, cj[2] = j + 1;
+  }
+}
+// grid-edge ids of the cell's edges AB, BC, CA: 3 * (lower endpoint id) + family
+// (0 horizontal, 1 sixty degrees, 2 one hundred twenty degrees)
+SBMT_DEV void cell_edges(const GridP& g, i64 c, i64 j, u32* e) {
+  i64 i = c >> 1;
+  if ((c & 1) == 0) {
+    e[0] = 3u * vid(g, i, j) + 0u;
+    e[1] = 3u * vid(g, i + 1, j) + 2u;
+    e[2] = 3u * vid(g, i, j) + 1u;
+  } else {
+    e[0] = 3u * vid(g, i + 1, j) + 1u;
+    e[1] = 3u * vid(g, i, j + 1) + 0u;
+    e[2] = 3u * vid(g, i + 1, j) + 2u;
+  }
+}
+// scaled coordinates of lattice vertex v(i, j)
+SBMT_DEV Pq lattice_pt(const GridP& g, i64 i, i64 j) {
+  return Pq{zq(g.ox + 3 * g.p * (2 * i + j)), zq(g.oy, 3 * g.p * j)};
+}
+SBMT_DEV Pq corner_pt(const GridP& g, i64 cx, i64 cy) {
+  return Pq{zq(6 * g.q * cx - 3 * g.q), zq(6 * g.q * cy - 3 * g.q)};
+}
+// strip row holding a point of height y (never on a grid line)
+SBMT_HD i64 strip_of(const GridP& g, Zq y) {
+  // y_j = oy + 3 p j sqrt3
+  i64 j = (i64)floor((zdouble(y) - (double)g.oy) / (3.0 * (double)g.p * 1.7320508075688772935));
+  while (zcmp(zq(g.oy, 3 * g.p * j), y) > 0) --j;
+  while (zcmp(zq(g.oy, 3 * g.p * (j + 1)), y) <= 0) ++j;
+  return j;
+}
+
+// image access with the OUTSIDE label beyond the border
+template <typename T>
+SBMT_DEV int pix(const unsigned char* img, i64 pitch, int W, int H, i64 x, i64 y) {
+  if (x < 0 || y < 0 || x >= W || y >= H) return OUTSIDE;
+  return (int)((const T*)(img + y * pitch))[x];
+}
+
+}  // namespace sbmt
