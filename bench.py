@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the SBMT hot path (bitmap -> conforming mesh) on GB300.
+
+One step = one call of the whole path through the C interface on one
+synthetic bitmap: boundary extraction, grid traversal and bucketing, event
+registry, classification / canonical key / lookup, emission of the mesh.
+The default workload is an 8192 x 8192 uint16 16-label Voronoi map (4096
+seeds, 5 x 5 majority filter) meshed with h = 2 px.
+
+Prints one JSON line (rank 0).  Under torchrun every rank meshes its own copy
+of the workload (independent images, no collective on the data path) and
+the time is the maximum over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload voronoi8192|ellipses2048|disk64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_19474_gb300 import synth  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+WORKLOADS = {
+    "voronoi8192": dict(gen=lambda: synth.voronoi_labels(), h=(2, 1),
+                        desc="8192x8192 u16, 16 labels on the Voronoi cells of 4096 uniform seeds, 5x5 majority "
+                             "filter, h=2 px"),
+    "ellipses2048": dict(gen=lambda: synth.ellipses(), h=(4, 1),
+                         desc="2048x2048 u8, union of 200 filled ellipses (semi-axes 10-150 px), h=4 px"),
+    "disk64": dict(gen=lambda: synth.disk(), h=(2, 1), desc="64x64 u8 filled disk r=20 (1257 px), h=2 px"),
+}
+
+
+def cache_path(name: str) -> str:
+    d = os.environ.get("SBMT_CACHE", "/tmp/sbmt_bench_cache")
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, name + ".npy")
+
+
+def load_workload(name: str, rank: int, barrier) -> np.ndarray:
+    p = cache_path(name)
+    if rank == 0 and not os.path.exists(p):
+        img = WORKLOADS[name]["gen"]()
+        tmp = p + ".tmp.%d.npy" % os.getpid()
+        np.save(tmp, img)
+        os.replace(tmp, p)
+    barrier()
+    return np.load(p)
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except Exception:
+        pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(img: np.ndarray, h: tuple, side: int) -> tuple:
+    """The CPU oracle on the top-left side x side crop (single thread)."""
+    import oracle
+
+    crop = np.ascontiguousarray(img[:side, :side])
+    t0 = time.perf_counter()
+    m = oracle.mesh_bitmap(crop, h[0], h[1])
+    dt = time.perf_counter() - t0
+    return m["n_triangles"], dt
+
+
+def reference_arm(args, rank: int, world: int):
+    """The oracle, as it stands, on the host cores: same metric and config."""
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    img = load_workload(args.workload, 0, lambda: None)
+    H, W = img.shape
+    # calibrate: choose a crop that keeps the whole run within ~2 minutes
+    n0, t0 = oracle_sample(img, wl["h"], min(256, W, H))
+    per_px = t0 / (min(256, W, H) ** 2)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    side = int(min(W, H, max(64, math.sqrt(budget / max(per_px, 1e-12)))))
+    side = max(32, side - side % 32)
+    for _ in range(args.warmup):
+        oracle_sample(img, wl["h"], side)
+    tris, secs = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = oracle_sample(img, wl["h"], side)
+        tris += n
+        secs += dt
+    value = tris / secs
+    print(json.dumps({
+        "impl": "reference", "metric": "output triangles/sec", "value": value, "unit": "triangles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": args.workload + ": " + wl["desc"], "sample": "%dx%d crop" % (side, side)},
+        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+                         "sample": "top-left %dx%d crop of the workload per step" % (side, side)},
+        "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# algorithmic bytes per launch of each kernel (per-unit figures x units)
+def kernel_bytes(name: str, v, img_bytes: int, W: int, H: int) -> float:
+    T, V = v.n_triangles, v.n_vertices
+    if name == "k_corner_bits":
+        return img_bytes + 4.0 * (((W + 32) // 32) * (H + 1) + ((H + 32) // 32) * (W + 1))
+    if name == "k_segments":
+        return 4.0 * (((W + 32) // 32) * (H + 1) + ((H + 32) // 32) * (W + 1)) + 16.0 * v.n_segments
+    if name == "k_emit":
+        return 16.0 * (T - v.n_tierG_triangles)
+    if name == "k_tierg":
+        return 16.0 * v.n_tierG_triangles
+    if name == "k_lattice_xy":
+        return 16.0 * v.n_lattice_vertices
+    if name == "k_rank":
+        return 16.0 * v.n_events
+    return 0.0
+
+
+def our_arm(args, rank: int, world: int, dist):
+    import torch
+
+    import paper_2602_19474_gb300 as sb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    img = load_workload(args.workload, rank, barrier)
+    H, W = img.shape
+    hn, hd = wl["h"]
+    st = torch.cuda.current_stream(dev)
+    ctx = sb.mesh_create(local, 0, st.cuda_stream)
+    dimg = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).to(dev)
+
+    def step(src):
+        m = sb.mesh_bitmap(ctx, src, hn, hd)
+        v = sb.mesh_query(ctx, m, -1)
+        sb.mesh_release(ctx, m)
+        return v
+
+    for _ in range(args.warmup):
+        v = step(dimg)
+    torch.cuda.synchronize()
+    # device-resident timed region
+    sb.mesh_profile(ctx, True)
+    sb.mesh_profile_read(ctx, reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        v = step(dimg)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = sb.mesh_profile_read(ctx, reset=True)
+    sb.mesh_profile(ctx, False)
+    T = v.n_triangles
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * T / (ms_max * 1e-3)
+
+    # end to end: host image from pinned memory in, whole mesh back to pinned host memory
+    pin_img = torch.empty(img.shape, dtype=torch.int16 if img.dtype == np.uint16 else torch.uint8).pin_memory()
+    pin_img.numpy()[...] = img.view(np.int16) if img.dtype == np.uint16 else img
+    host_img = pin_img.numpy().view(img.dtype)
+    out_xy = torch.empty((v.n_vertices, 2), dtype=torch.float64).pin_memory()
+    out_tri = torch.empty((T, 3), dtype=torch.int32).pin_memory()
+    out_lab = torch.empty((T,), dtype=torch.int16).pin_memory()
+    out_code = torch.empty((T,), dtype=torch.int16).pin_memory()
+
+    def e2e_step():
+        m = sb.mesh_bitmap(ctx, host_img, hn, hd)
+        vv = sb.mesh_query(ctx, m, -1)
+        t = sb.view_tensors(vv)
+        out_xy.copy_(t["xy"], non_blocking=True)
+        out_tri.copy_(t["tri"], non_blocking=True)
+        out_lab.copy_(t["label"], non_blocking=True)
+        out_code.copy_(t["code"], non_blocking=True)
+        st.synchronize()
+        sb.mesh_release(ctx, m)
+
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = world * T / (ms_e2e * 1e-3)
+    h2d = img.nbytes
+    d2h = 16 * v.n_vertices + 16 * T
+
+    if rank != 0:
+        sb.mesh_destroy(ctx)
+        return
+    peak, peak_kind = measured_peak()
+    launches = sum(n for (_, n) in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dn) = dom
+    dbytes = kernel_bytes(dname, v, img.nbytes, W, H)
+    achieved = dbytes / (dms / dn * 1e-3) / 1e9 if dn and dbytes else None
+    path_bytes = img.nbytes + 16.0 * T + 16.0 * v.n_vertices
+    path_gbs = path_bytes / (ms * 1e-3) / 1e9
+    share = {k: round(a / max(1e-9, sum(x for x, _ in prof.values())), 4) for k, (a, _) in prof.items()}
+    # CPU baseline: the oracle as it stands, one core, on a bounded crop
+    side = min(2048, W, H)
+    n_cpu, t_cpu = oracle_sample(img, (hn, hd), side)
+    out = {
+        "metric": "output triangles/sec", "value": value, "unit": "triangles/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "image": [W, H], "h": hn / hd,
+                   "triangles_per_step": T, "vertices_per_step": v.n_vertices,
+                   "l2": "inputs larger than L2: %d MB image and %d MB mesh per step" % (img.nbytes >> 20,
+                                                                                    (16 * (T + v.n_vertices)) >> 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "bitmaps_per_s": world / (ms_max * 1e-3),
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": dbytes,
+                     "ms_per_launch": dms / dn if dn else None},
+        "roofline_path": {"achieved": path_gbs, "peak": peak, "unit": "GB/s", "frac": path_gbs / peak,
+                          "algorithmic_bytes_per_step": path_bytes},
+        "kernel_share": share,
+        "cpu_baseline": {"value": n_cpu / t_cpu, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+                         "sample": "top-left %dx%d crop of the workload, one thread" % (side, side)},
+        "e2e": {"value": e2e_value, "unit": "triangles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    sb.mesh_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="voronoi8192", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist_
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist_.init_process_group("nccl")
+        dist = dist_
+    our_arm(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

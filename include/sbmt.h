@@ -101,6 +101,11 @@ typedef struct {
  *        1-based position in Thm. 3.2's list (0 = not applicable). */
 typedef struct {
   int64_t n_vertices, n_triangles, n_cells, n_cut_cells, n_tierG_cells;
+  int64_t n_segments;        /* boundary segments (maximal runs) */
+  int64_t n_events;          /* boundary/grid-edge crossing vertices */
+  int64_t n_inside_vertices; /* boundary vertices inside cells */
+  int64_t n_lattice_vertices;
+  int64_t n_tierG_triangles; /* triangles of cells outside the table's regime */
   const double* xy;
   const int32_t* tri;
   const uint16_t* label;
@@ -148,6 +153,17 @@ int mesh_destroy(sbmt_ctx* ctx);
  *          boundary vertices inside, outside-regime flag.
  * Writes min(n, cap) records to host_out and the total count to *n. */
 int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n);
+
+/* Per-kernel device time, for tracing and roofline accounting (no
+ * counterpart in the paper, which reports no timings).  With enable != 0
+ * every kernel launch of the context is bracketed by two CUDA events on the
+ * context's stream.  mesh_profile_read waits for the recorded events and
+ * writes, for each of the *n kernels of the hot path (at most cap), its
+ * name (static string), accumulated milliseconds and launch count; reset
+ * != 0 clears the totals. */
+int mesh_profile(sbmt_ctx* ctx, int enable);
+int mesh_profile_read(sbmt_ctx* ctx, int reset, int cap, const char** names, double* ms, int64_t* launches,
+                      int* n);
 
 /* Message of the last failing call on this thread (never NULL). */
 const char* sbmt_last_error(void);

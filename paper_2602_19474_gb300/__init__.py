@@ -36,7 +36,7 @@ SBMT_EXPLICIT = 0
 SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
-           "sbmt_last_error")
+           "mesh_profile", "mesh_profile_read", "sbmt_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -53,7 +53,9 @@ class sbmt_params(ctypes.Structure):
 
 class sbmt_mesh_view(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_cells", ctypes.c_int64),
-                ("n_cut_cells", ctypes.c_int64), ("n_tierG_cells", ctypes.c_int64), ("xy", ctypes.c_void_p),
+                ("n_cut_cells", ctypes.c_int64), ("n_tierG_cells", ctypes.c_int64), ("n_segments", ctypes.c_int64),
+                ("n_events", ctypes.c_int64), ("n_inside_vertices", ctypes.c_int64),
+                ("n_lattice_vertices", ctypes.c_int64), ("n_tierG_triangles", ctypes.c_int64), ("xy", ctypes.c_void_p),
                 ("tri", ctypes.c_void_p), ("label", ctypes.c_void_p), ("code", ctypes.c_void_p),
                 ("status", ctypes.c_int32)]
 
@@ -90,9 +92,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mesh_release.argtypes = [vp, ctypes.c_uint64]
     lib.mesh_destroy.argtypes = [vp]
     lib.mesh_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp, i64, ctypes.POINTER(i64)]
+    lib.mesh_profile.argtypes = [vp, ctypes.c_int]
+    lib.mesh_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                      ctypes.POINTER(ctypes.c_int)]
     lib.sbmt_last_error.restype = ctypes.c_char_p
     for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
-              "mesh_stage"):
+              "mesh_stage", "mesh_profile", "mesh_profile_read"):
         getattr(lib, f).restype = ctypes.c_int
     del i32
     _lib = lib
@@ -188,6 +194,21 @@ def mesh_stage(ctx: int, mesh: int, stage: int) -> np.ndarray:
     return buf[: n.value]
 
 
+def mesh_profile(ctx: int, enable: bool) -> None:
+    _check(load().mesh_profile(ctx, 1 if enable else 0))
+
+
+def mesh_profile_read(ctx: int, reset: bool = False) -> dict:
+    """{kernel name: (milliseconds, launches)} accumulated while tracing."""
+    cap = 32
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int64 * cap)()
+    n = ctypes.c_int(0)
+    _check(load().mesh_profile_read(ctx, 1 if reset else 0, cap, names, ms, cnt, ctypes.byref(n)))
+    return {names[k].decode(): (ms[k], cnt[k]) for k in range(min(n.value, cap))}
+
+
 # ---------------------------------------------------------------------------
 # device views of a finished mesh
 # ---------------------------------------------------------------------------
@@ -225,6 +246,11 @@ def view_numpy(view: sbmt_mesh_view) -> dict:
         "n_cells": view.n_cells,
         "n_cut_cells": view.n_cut_cells,
         "n_tierG_cells": view.n_tierG_cells,
+        "n_segments": view.n_segments,
+        "n_events": view.n_events,
+        "n_inside_vertices": view.n_inside_vertices,
+        "n_lattice_vertices": view.n_lattice_vertices,
+        "n_tierG_triangles": view.n_tierG_triangles,
     }
 
 

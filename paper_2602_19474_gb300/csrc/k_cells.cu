@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
                                               const u32* poff, const u32* bstat, const u32* extra_scan,
                                               const u32* chain_scan, u32 NVg, u32 NE, int* tri,
                                               unsigned short* label, unsigned short* code, double* xy, u32* glist,
-                                              u32* nglist, u32* err) {
+                                              u32* nglist, u32* ngtri, u32* err) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
@@ -540,6 +540,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       recs[rec0 + r] = rec;
       const u32 slot = atomicAdd(nglist, 1u);
       glist[slot] = rec0 + r;
+      atomicAdd(ngtri, rec.ntri);
       continue;
     }
     const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
@@ -880,11 +881,11 @@ void launch_scan(const u32* in, int stride, u32* out, u32 n, cudaStream_t st) {
 void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                  const Seg* segs, const Event* events, CutRec* recs, const u32* poff, const u32* bstat,
                  const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* err,
-                 cudaStream_t st) {
+                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* ngtri,
+                 u32* err, cudaStream_t st) {
   if (nbc == 0) return;
   k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, poff, bstat, extra_scan,
-                              chain_scan, NVg, NE, tri, label, code, xy, glist, nglist, err);
+                              chain_scan, NVg, NE, tri, label, code, xy, glist, nglist, ngtri, err);
 }
 
 void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,

@@ -111,8 +111,8 @@ struct MeshRec {
   int* tri = nullptr;
   unsigned short* label = nullptr;
   unsigned short* code = nullptr;
-  int64_t nv = 0, nt = 0, ncells = 0;
-  u32* h_info = nullptr;  // pinned: err, ncut, ntierg
+  int64_t nv = 0, nt = 0, ncells = 0, nseg_total = 0, ne_total = 0, nc_total = 0, nvg = 0;
+  u32* h_info = nullptr;  // pinned: err, ncut, ntierg, tierg triangles
   int W = 0;
   // kept intermediates (SBMT_KEEP_STAGES)
   bool keep = false;
@@ -129,6 +129,12 @@ struct MeshRec {
 
 }  // namespace
 
+// kernels of the hot path, in launch order (for the per-kernel timing)
+enum { KN_CORNER, KN_SEG, KN_TCOUNT, KN_SCAN, KN_TEMIT, KN_RANK, KN_CLASSIFY, KN_EMIT, KN_TIERG, KN_XY, KN_COUNT };
+const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_traverse_count", "k_scan",
+                                            "k_traverse_emit", "k_rank", "k_classify", "k_emit", "k_tierg",
+                                            "k_lattice_xy"};
+
 struct sbmt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -136,9 +142,64 @@ struct sbmt_ctx {
   std::mutex mu;
   std::map<sbmt_mesh, MeshRec*> meshes;
   sbmt_mesh next = 1;
+  // tracing: events around each kernel launch, resolved lazily
+  bool prof = false;
+  struct Mark {
+    int k;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Mark> pending;
+  double prof_ms[KN_COUNT] = {};
+  int64_t prof_n[KN_COUNT] = {};
 };
 
 namespace {
+
+cudaEvent_t pool_event(sbmt_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_collect(sbmt_ctx* c) {
+  for (auto& mk : c->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(mk.b) == cudaSuccess && cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
+      c->prof_ms[mk.k] += ms;
+      c->prof_n[mk.k] += 1;
+    }
+    c->ev_pool.push_back(mk.a), c->ev_pool.push_back(mk.b);
+  }
+  c->pending.clear();
+}
+
+// brackets one kernel launch with events on the context stream when tracing
+struct ProfScope {
+  sbmt_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr;
+  ProfScope(sbmt_ctx* c_, int k_) : c(c_), k(k_) {
+    if (c->prof && (a = pool_event(c))) cudaEventRecord(a, c->stream);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({k, a, b});
+    if (c->pending.size() > 8192) prof_collect(c);
+  }
+};
+#define TRACE(kn, call)          \
+  do {                           \
+    ProfScope ps_(ctx, kn);      \
+    call;                        \
+  } while (0)
 
 template <typename T>
 int dalloc(sbmt_ctx* ctx, T** p, size_t count, std::vector<void*>& track) {
@@ -247,7 +308,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = dalloc(ctx, &cnt64, 8, tmp))) return bail(rc);
   u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, pad...
   CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
-  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2;
+  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3;
 
   // K1a
   const int W = g.W, H = g.H;
@@ -255,7 +316,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   u32 *vrow, *vcol;
   if ((rc = dalloc(ctx, &vrow, (size_t)wpr * (H + 1), tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &vcol, (size_t)wpc * (W + 1), tmp))) return bail(rc);
-  launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st);
+  TRACE(KN_CORNER, launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st));
   unsigned long long h64[4];
   CK(cudaMemcpyAsync(h64, cnt64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -264,7 +325,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   const u32 seg_cap = (u32)std::max<u64>(2 * NC, 1);
   Seg* segs;
   if ((rc = dalloc(ctx, &segs, seg_cap, tmp))) return bail(rc);
-  launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st);
+  TRACE(KN_SEG, launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st));
   // K2 count
   const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
   const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
@@ -273,7 +334,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = dalloc(ctx, &ecnt, nbe + 1, tmp))) return bail(rc);
   CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
   CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
-  launch_traverse_count(g, segs, nseg, seg_cap, pcnt, ecnt, cnt64 + 1, err, st);
+  TRACE(KN_TCOUNT, launch_traverse_count(g, segs, nseg, seg_cap, pcnt, ecnt, cnt64 + 1, err, st));
   CK(cudaMemcpyAsync(h64, cnt64, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   u32 h32[4];
   CK(cudaMemcpyAsync(h32, cnt32, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -292,8 +353,8 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = dalloc(ctx, &eoff, nbe + 1, tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &pcur, nbc + 1, tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &ecur, nbe + 1, tmp))) return bail(rc);
-  launch_scan(pcnt, 1, poff, nbc, st);
-  launch_scan(ecnt, 1, eoff, nbe, st);
+  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, st));
+  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, st));
   CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   Pair *pairs, *sorted;
@@ -330,22 +391,23 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   m->label = (unsigned short*)((char*)m->out_block + off_lab);
   m->code = (unsigned short*)((char*)m->out_block + off_code);
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
+  m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
-  launch_traverse_emit(g, segs, nseg, seg_cap, pcur, ecur, pairs, ev, err, st);
-  launch_rank_events(g, ev, eoff, nbe, (u32)NVg, m->xy, st);
-  launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st);
-  launch_scan(bstat + 1, 4, extra_scan, nbc, st);
-  launch_scan(bstat + 2, 4, chain_scan, nbc, st);
-  launch_scan(bstat + 0, 4, cut_scan, nbc, st);
-  launch_emit(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
-              (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, err, st);
-  launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, (u32)NVg, (u32)NE, m->tri,
-               m->label, m->code, m->xy, err, st);
-  launch_lattice_xy(g, m->xy, st);
+  TRACE(KN_TEMIT, launch_traverse_emit(g, segs, nseg, seg_cap, pcur, ecur, pairs, ev, err, st));
+  TRACE(KN_RANK, launch_rank_events(g, ev, eoff, nbe, (u32)NVg, m->xy, st));
+  TRACE(KN_CLASSIFY, launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 1, 4, extra_scan, nbc, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 2, 4, chain_scan, nbc, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 0, 4, cut_scan, nbc, st));
+  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
+              (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, err, st));
+  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, (u32)NVg, (u32)NE, m->tri,
+               m->label, m->code, m->xy, err, st));
+  TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(m->h_info + 1, cut_scan + nbc, sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(m->h_info + 2, nglist, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(m->h_info + 2, nglist, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st));
   if (m->keep) {
     // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
     m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bstat = bstat;
@@ -441,6 +503,8 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
   std::memset(out, 0, sizeof *out);
   out->n_vertices = m->nv, out->n_triangles = m->nt, out->n_cells = m->ncells;
   out->n_cut_cells = m->h_info[1], out->n_tierG_cells = m->h_info[2];
+  out->n_segments = m->nseg_total, out->n_events = m->ne_total, out->n_inside_vertices = m->nc_total;
+  out->n_lattice_vertices = m->nvg, out->n_tierG_triangles = m->h_info[3];
   out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;
   const u32 e = m->h_info[0];
   out->status = e == 0 ? SBMT_OK : (e & ERR_CAPACITY) ? SBMT_ECAPACITY : SBMT_EINTERNAL;
@@ -465,9 +529,34 @@ int mesh_destroy(sbmt_ctx* ctx) {
     for (auto& kv : ctx->meshes) destroy_mesh(ctx, kv.second);
     ctx->meshes.clear();
     cudaStreamSynchronize(ctx->stream);
+    prof_collect(ctx);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
+  return SBMT_OK;
+}
+
+int mesh_profile(sbmt_ctx* ctx, int enable) {
+  if (!ctx) return fail(SBMT_EINVAL, "null ctx");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->prof = enable != 0;
+  return SBMT_OK;
+}
+
+int mesh_profile_read(sbmt_ctx* ctx, int reset, int cap, const char** names, double* ms, int64_t* launches,
+                      int* n) {
+  if (!ctx || !n) return fail(SBMT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  prof_collect(ctx);
+  *n = KN_COUNT;
+  for (int k = 0; k < KN_COUNT && k < cap; ++k) {
+    if (names) names[k] = kKernelNames[k];
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
+  if (reset)
+    for (int k = 0; k < KN_COUNT; ++k) ctx->prof_ms[k] = 0, ctx->prof_n[k] = 0;
   return SBMT_OK;
 }
 

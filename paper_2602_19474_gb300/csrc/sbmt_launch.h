@@ -44,8 +44,8 @@ void launch_scan(const u32* in, int stride, u32* out, u32 n, cudaStream_t st);
 void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                  const Seg* segs, const Event* events, CutRec* recs, const u32* poff, const u32* bstat,
                  const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* err,
-                 cudaStream_t st);
+                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* ngtri,
+                 u32* err, cudaStream_t st);
 
 // K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.
 void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,

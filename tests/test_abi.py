@@ -35,7 +35,7 @@ def test_struct_layouts_match_header():
     # sizes of the C structs on LP64 (int32/int64/double/pointer alignment)
     assert ctypes.sizeof(sb.sbmt_image) == 40
     assert ctypes.sizeof(sb.sbmt_params) == 56
-    assert ctypes.sizeof(sb.sbmt_mesh_view) == 80
+    assert ctypes.sizeof(sb.sbmt_mesh_view) == 120
 
 
 def test_null_arguments_are_rejected(lib):
