@@ -137,8 +137,9 @@ def reference_arm(args, rank: int, world: int):
     # calibrate: choose a crop that keeps the whole run within ~2 minutes
     n0, t0 = oracle_sample(img, wl["h"], min(256, W, H))
     per_px = t0 / (min(256, W, H) ** 2)
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    side = int(min(W, H, max(64, math.sqrt(budget / max(per_px, 1e-12)))))
+    # the cost per pixel grows with the crop (map lookups); keep a 3x margin
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    side = int(min(W, H, max(64, math.sqrt(budget / max(3.0 * per_px, 1e-12)))))
     side = max(32, side - side % 32)
     for _ in range(args.warmup):
         oracle_sample(img, wl["h"], side)

@@ -15,6 +15,7 @@
 // it crosses nothing.  Uncut cells keep their base triangle (A, B, C).
 #include <algorithm>
 
+#include "sbmt_cell.cuh"
 #include "sbmt_launch.h"
 
 namespace sbmt {
@@ -72,63 +73,6 @@ SBMT_DEV int thm32_class(int m, int n) {
   for (int k = 0; k < 8; ++k)
     if (lst[k] == m * 4 + n) return k + 1;
   return 0;
-}
-
-// ---------------------------------------------------------------------------
-// cell geometry
-// ---------------------------------------------------------------------------
-struct CellGeo {
-  i64 c, j;
-  i64 ci[3], cj[3];
-  u32 edge[3];
-  int down;
-};
-SBMT_DEV CellGeo cell_geo(const GridP& g, u32 cid, int r) {
-  CellGeo cg;
-  cg.j = g.j0 + r;
-  cg.c = g.clo[r] + ((i64)cid - g.cbase[r]);
-  cell_corners(cg.c, cg.j, cg.ci, cg.cj);
-  cell_edges(g, cg.c, cg.j, cg.edge);
-  cg.down = (int)(cg.c & 1);
-  return cg;
-}
-SBMT_DEV int local_edge(const CellGeo& cg, u32 e) {
-  return cg.edge[0] == e ? 0 : cg.edge[1] == e ? 1 : cg.edge[2] == e ? 2 : -1;
-}
-// a number increasing counter-clockwise along local edge k (corner k -> k+1):
-// up cells run AB +x, BC +y, CA -y; down cells AB +y, BC -x, CA -y
-SBMT_DEV Zq ccw_pos(int down, int k, const Event& e) {
-  if (k == 2) return zq(-e.ya, -e.yb);
-  if (down == 0) return k == 0 ? zq(e.xa, e.xb) : zq(e.ya, e.yb);
-  return k == 0 ? zq(e.ya, e.yb) : zq(-e.xa, -e.xb);
-}
-SBMT_DEV u32 corner_id(const GridP& g, const Seg& s, int upper) {
-  i64 cx = s.cx, cy = s.cy;
-  if (upper) {
-    if (seg_dir(s) == 0) cx += seg_len(s);
-    else cy += seg_len(s);
-  }
-  return (u32)(cy * (g.W + 1) + cx);
-}
-SBMT_DEV Pq corner_of_id(const GridP& g, u32 id) {
-  return corner_pt(g, (i64)(id % (u32)(g.W + 1)), (i64)(id / (u32)(g.W + 1)));
-}
-
-// label of the pixel holding the centroid of three global points
-template <typename T>
-SBMT_DEV unsigned short centroid_label(const GridP& g, const unsigned char* img, i64 pitch, const Pq& a,
-                                       const Pq& b, const Pq& c) {
-  const Zq sx = a.x + b.x + c.x, sy = a.y + b.y + c.y;
-  // pixel column floor(x/S + 1/2) with x = sx / 3
-  const i64 col = zfloordiv(Zq{2 * sx.a + 3 * g.S, 2 * sx.b}, 6 * g.S);
-  const i64 row = zfloordiv(Zq{2 * sy.a + 3 * g.S, 2 * sy.b}, 6 * g.S);
-  const int l = pix<T>(img, pitch, g.W, g.H, col, row);
-  return l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
-}
-SBMT_DEV unsigned short label_of(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pq& a,
-                                 const Pq& b, const Pq& c) {
-  return dtype == 1 ? centroid_label<unsigned char>(g, img, pitch, a, b, c)
-                    : centroid_label<unsigned short>(g, img, pitch, a, b, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -233,103 +177,67 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
   return r;
 }
 
-// ---------------------------------------------------------------------------
-// block helpers
-// ---------------------------------------------------------------------------
-// exclusive scan of one value per thread over a block of 256 threads
-SBMT_DEV u32 block_exscan256(u32 v, u32* total, u32* sh /* 8 words */) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  u32 x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sh[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    u32 s = lane < 8 ? sh[lane] : 0u;
-    for (int o = 1; o < 8; o <<= 1) {
-      const u32 y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < 8) sh[lane] = s;
-  }
-  __syncthreads();
-  const u32 before = (w ? sh[w - 1] : 0u) + x - v;
-  *total = sh[7];
-  __syncthreads();
-  return before;
-}
-
-constexpr int KCAP = 2048;
-
+// K3: one block per cell bucket (1024 consecutive cell ids).  The bucket's
+// pairs are counting-sorted by cell in shared memory (histogram, scan,
+// scatter), the cut cells compacted, and each cut cell classified.
 __global__ void __launch_bounds__(256) k_classify(GridP g, const Pair* pairs, Pair* sorted, const u32* poff,
                                                   const Seg* segs, const Event* ev, CutRec* recs, u32* bstat,
                                                   u32* err) {
-  __shared__ unsigned long long s_key[KCAP];
+  constexpr int NB = 1 << CB_LOG;
+  __shared__ u32 s_cnt[NB], s_off[NB], s_cur[NB];
+  __shared__ unsigned short s_cut[NB];
   __shared__ u32 s_sh[8];
   __shared__ u32 s_stat[4];
   const u32 b = blockIdx.x, lo = poff[b], n = poff[b + 1] - lo;
+  const i64 c0 = (i64)b << CB_LOG;
   if (threadIdx.x < 4) s_stat[threadIdx.x] = 0;
   if (n == 0) {
     if (threadIdx.x < 4) bstat[4 * b + threadIdx.x] = 0;
     return;
   }
-  // 1. order the bucket's pairs by (cell, segment): rank sort
-  const bool cached = n <= (u32)KCAP;
-  if (cached)
-    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-      const Pair p = pairs[lo + i];
-      s_key[i] = ((unsigned long long)p.cell << 32) | p.seg;
+  for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0;
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[pairs[lo + i].cell - c0], 1u);
+  __syncthreads();
+  // offsets of each cell's pairs and the index of each cut cell's record
+  u32 ncut;
+  {
+    const int k0 = threadIdx.x * 4;
+    u32 v[4], s = 0, c = 0;
+    for (int u = 0; u < 4; ++u) v[u] = s_cnt[k0 + u], s += v[u], c += v[u] ? 1u : 0u;
+    u32 tot;
+    u32 run = block_exscan256(s, &tot, s_sh);
+    u32 crun = block_exscan256(c, &ncut, s_sh);
+    for (int u = 0; u < 4; ++u) {
+      s_off[k0 + u] = run, s_cur[k0 + u] = run, run += v[u];
+      if (v[u]) s_cut[crun++] = (unsigned short)(k0 + u);
     }
+  }
   __syncthreads();
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
     const Pair p = pairs[lo + i];
-    const unsigned long long ki = ((unsigned long long)p.cell << 32) | p.seg;
-    u32 rank = 0;
-    for (u32 k = 0; k < n; ++k) {
-      unsigned long long kk;
-      if (cached) kk = s_key[k];
-      else {
-        const Pair q = pairs[lo + k];
-        kk = ((unsigned long long)q.cell << 32) | q.seg;
-      }
-      rank += kk < ki ? 1u : 0u;
-    }
-    sorted[lo + rank] = p;
+    const u32 slot = atomicAdd(&s_cur[p.cell - c0], 1u);
+    sorted[lo + slot] = p;
   }
   __syncthreads();
-  // 2. one record per cell: a pair starts a cell when its cell differs from
-  //    the previous pair's
-  u32 carry = 0, st_cut = 0, st_extra = 0, st_chain = 0, st_g = 0;
+  u32 st_extra = 0, st_chain = 0, st_g = 0;
   int row = -1;
-  for (u32 base = 0; base < n; base += blockDim.x) {
-    const u32 i = base + threadIdx.x;
-    bool start = false;
-    Pair p{};
-    if (i < n) {
-      p = sorted[lo + i];
-      start = (i == 0) || (sorted[lo + i - 1].cell != p.cell);
-    }
-    u32 tot;
-    const u32 idx = block_exscan256(start ? 1u : 0u, &tot, s_sh);
-    if (start) {
-      u32 np = 1;
-      while (i + np < n && sorted[lo + i + np].cell == p.cell) ++np;
-      if (row < 0 || !(g.cbase[row] <= (i64)p.cell && (row + 1 == g.nrows || g.cbase[row + 1] > (i64)p.cell)))
-        row = cell_row(g, p.cell);
-      const CellGeo cg = cell_geo(g, p.cell, row);
-      const Klass k = classify_cell(g, cg, sorted + lo + i, np, segs, ev, err);
-      CutRec rec{p.cell, lo + i, np, k.code | (k.tierG ? (1u << 16) : 0u), k.ntri, k.nchain, 0u, 0u};
-      recs[lo + carry + idx] = rec;
-      st_cut += 1, st_extra += k.ntri - 1, st_chain += k.nchain, st_g += k.tierG ? 1u : 0u;
-    }
-    carry += tot;
+  for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
+    const int k = s_cut[r];
+    const u32 cid = (u32)(c0 + k);
+    if (row < 0 || !(g.cbase[row] <= (i64)cid && (row + 1 == g.nrows || g.cbase[row + 1] > (i64)cid)))
+      row = cell_row(g, cid);
+    const CellGeo cg = cell_geo(g, cid, row);
+    const Klass kl = classify_cell(g, cg, sorted + lo + s_off[k], s_cnt[k], segs, ev, err);
+    recs[lo + r] = CutRec{cid, lo + s_off[k], s_cnt[k], kl.code | (kl.tierG ? (1u << 16) : 0u), kl.ntri, kl.nchain,
+                          0u, 0u};
+    st_extra += kl.ntri - 1, st_chain += kl.nchain, st_g += kl.tierG ? 1u : 0u;
   }
-  atomicAdd(&s_stat[0], st_cut);
   atomicAdd(&s_stat[1], st_extra);
   atomicAdd(&s_stat[2], st_chain);
   atomicAdd(&s_stat[3], st_g);
+  __syncthreads();
+  if (threadIdx.x == 0) s_stat[0] = ncut;
   __syncthreads();
   if (threadIdx.x < 4) bstat[4 * b + threadIdx.x] = s_stat[threadIdx.x];
 }
@@ -512,23 +420,44 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   __syncthreads();
   const u32 T0_ = (u32)c0 + extra_scan[b];
   const u32 CB0 = NVg + NE + chain_scan[b];
-  // uncut cells: the base triangle (A, B, C), untouched
-  int row = cell_row(g, (u32)c0);
+  // uncut cells: the base triangle (A, B, C), untouched.  Per strip row the
+  // corner ids are row base + i, the centroid's pixel row is tabulated, and
+  // its pixel column is an integer floor.
+  __shared__ int s_row0;
+  if (threadIdx.x == 0) s_row0 = cell_row(g, (u32)c0);
+  __syncthreads();
+  int r = -1;
+  i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0, jr = 0;
+  int lr0 = 0, lr1 = 0;
+  const i64 twoS = 2 * g.S;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     if (s_cnt[k] != 1u) continue;
-    const u32 cid = (u32)(c0 + k);
-    int r = row;
-    while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;
-    const i64 j = g.j0 + r, c = g.clo[r] + ((i64)cid - g.cbase[r]);
-    i64 ci[3], cj[3];
-    cell_corners(c, j, ci, cj);
-    const u32 o = T0_ + s_off[k];
-    Pq pt[3];
-    for (int u = 0; u < 3; ++u) {
-      tri[3 * (i64)o + u] = (int)vid(g, ci[u], cj[u]);
-      pt[u] = lattice_pt(g, ci[u], cj[u]);
+    const i64 cid = c0 + k;
+    if (r < 0 || cid >= cb_r + (g.chi[r] - clo_r + 1)) {
+      if (r < 0) r = s_row0;
+      while (r + 1 < g.nrows && g.cbase[r + 1] <= cid) ++r;
+      clo_r = g.clo[r], cb_r = g.cbase[r], jr = g.j0 + r;
+      vb0 = g.vbase[r] - g.vlo[r], vb1 = g.vbase[r + 1] - g.vlo[r + 1];
+      lr0 = g.lrow[2 * r], lr1 = g.lrow[2 * r + 1];
     }
-    label[o] = label_of(g, img, pitch, dtype, pt[0], pt[1], pt[2]);
+    const i64 c = clo_r + (cid - cb_r), i = c >> 1;
+    const u32 o = T0_ + s_off[k];
+    int v0, v1, v2, prow;
+    i64 xc;
+    if ((c & 1) == 0) {
+      v0 = (int)(vb0 + i), v1 = (int)(vb0 + i + 1), v2 = (int)(vb1 + i);
+      xc = g.ox + 3 * g.p * (2 * i + jr + 1), prow = lr0;
+    } else {
+      v0 = (int)(vb0 + i + 1), v1 = (int)(vb1 + i + 1), v2 = (int)(vb1 + i);
+      xc = g.ox + 3 * g.p * (2 * i + jr + 2), prow = lr1;
+    }
+    const i64 pcol = ifloordiv(2 * xc + g.S, twoS);
+    const int l = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
+                             : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
+    tri[3 * (i64)o] = v0;
+    tri[3 * (i64)o + 1] = v1;
+    tri[3 * (i64)o + 2] = v2;
+    label[o] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
     code[o] = 0;
   }
   // cut cells
@@ -546,306 +475,6 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
     emit_tier_t(g, cg, rec, sorted + rec.pair_lo, segs, ev, img, pitch, dtype, tri, label, code, xy, err);
   }
-}
-
-// ---------------------------------------------------------------------------
-// K4-G: one warp per Tier-G cell
-// ---------------------------------------------------------------------------
-constexpr int GN = 64;                  // local vertices per cell
-constexpr int GWARPS = 4;               // warps per block
-constexpr int GCAND = GN * (GN - 1) / 2;
-constexpr int GCANDP = 2048;            // power of two >= GCAND
-constexpr int GEDGE = 3 * GN;
-constexpr int GTRI = 2 * GN;
-
-struct GShared {
-  int xa[GN], xb[GN], ya[GN], yb[GN];  // cell-local exact coordinates
-  u32 gid[GN];
-  u32 corner[GN];
-  u64 adj[GN];
-  unsigned short cand[GCANDP];
-  unsigned short edge[GEDGE];
-  u32 tri[GTRI];
-  int n, nedge, ntri, ok;
-};
-
-SBMT_DEV Pq lpt(const GShared& s, int k) { return Pq{zq(s.xa[k], s.xb[k]), zq(s.ya[k], s.yb[k])}; }
-SBMT_DEV Zq len2(const GShared& s, int u, int v) {
-  const Zq dx = zq(s.xa[v] - s.xa[u], s.xb[v] - s.xb[u]), dy = zq(s.ya[v] - s.ya[u], s.yb[v] - s.yb[u]);
-  return dx * dx + dy * dy;
-}
-// candidate order: exact squared length, then (u, v)
-SBMT_DEV bool cand_less(const GShared& s, unsigned short x, unsigned short y) {
-  if (x == 0xFFFFu) return false;
-  if (y == 0xFFFFu) return true;
-  const int c = zcmp(len2(s, x >> 8, x & 255), len2(s, y >> 8, y & 255));
-  if (c != 0) return c < 0;
-  return x < y;
-}
-SBMT_DEV Zq dot3(const Pq& o, const Pq& p, const Pq& q) { return (p.x - o.x) * (q.x - o.x) + (p.y - o.y) * (q.y - o.y); }
-
-// build the cell's local boundary graph (lane 0): corners, events in
-// counter-clockwise order, inside vertices by corner id, constraint edges
-SBMT_DEV void build_local_g(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
-                            const Event* ev, GShared& s) {
-  const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
-  s.ok = 1;
-  s.nedge = 0;
-  for (int k = 0; k < GN; ++k) s.adj[k] = 0;
-  for (int k = 0; k < 3; ++k) {
-    const Pq p = lattice_pt(g, cg.ci[k], cg.cj[k]);
-    s.xa[k] = (int)(p.x.a - A.x.a), s.xb[k] = (int)(p.x.b - A.x.b);
-    s.ya[k] = (int)(p.y.a - A.y.a), s.yb[k] = (int)(p.y.b - A.y.b);
-    s.gid[k] = vid(g, cg.ci[k], cg.cj[k]);
-    s.corner[k] = NONE;
-  }
-  // events, sorted by (edge, position); their slots hold the event index
-  int ne = 0;
-  for (u32 k = 0; k < rec.npairs; ++k) {
-    const Pair pr = P[k];
-    for (int end = 0; end < 2; ++end) {
-      const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
-      if (e == NONE) continue;
-      if (3 + ne >= GN) {
-        s.ok = 0;
-        return;
-      }
-      if (local_edge(cg, ev[e].edge) < 0) {
-        s.ok = 0;
-        return;
-      }
-      s.corner[3 + ne] = e;  // temporarily: event index
-      ++ne;
-    }
-  }
-  for (int a = 1; a < ne; ++a)
-    for (int b = a; b > 0; --b) {
-      const Event x = ev[s.corner[3 + b]], y = ev[s.corner[3 + b - 1]];
-      const int kx = local_edge(cg, x.edge), ky = local_edge(cg, y.edge);
-      const bool sw = kx < ky || (kx == ky && zcmp(ccw_pos(cg.down, kx, x), ccw_pos(cg.down, ky, y)) < 0);
-      if (!sw) break;
-      const u32 t = s.corner[3 + b];
-      s.corner[3 + b] = s.corner[3 + b - 1], s.corner[3 + b - 1] = t;
-    }
-  int nev[3] = {0, 0, 0};
-  for (int k = 0; k < ne; ++k) {
-    const Event e = ev[s.corner[3 + k]];
-    nev[local_edge(cg, e.edge)]++;
-    s.xa[3 + k] = (int)(e.xa - A.x.a), s.xb[3 + k] = (int)(e.xb - A.x.b);
-    s.ya[3 + k] = (int)(e.ya - A.y.a), s.yb[3 + k] = (int)(e.yb - A.y.b);
-    s.gid[3 + k] = e.gid;
-  }
-  // inside vertices: distinct corner ids, ascending
-  int n = 3 + ne;
-  for (u32 k = 0; k < rec.npairs; ++k) {
-    const Pair pr = P[k];
-    for (int end = 0; end < 2; ++end) {
-      if ((end == 0 ? pr.ev_in : pr.ev_out) != NONE) continue;
-      const u32 id = corner_id(g, segs[pr.seg], end);
-      int pos = 3 + ne;
-      while (pos < n && s.corner[pos] < id) ++pos;
-      if (pos < n && s.corner[pos] == id) continue;
-      if (n >= GN) {
-        s.ok = 0;
-        return;
-      }
-      for (int t = n; t > pos; --t) s.corner[t] = s.corner[t - 1];
-      s.corner[pos] = id;
-      ++n;
-    }
-  }
-  if ((u32)(n - 3 - ne) != rec.nchain) {
-    s.ok = 0;
-    return;
-  }
-  for (int k = 3 + ne; k < n; ++k) {
-    const Pq p = corner_of_id(g, s.corner[k]);
-    s.xa[k] = (int)(p.x.a - A.x.a), s.xb[k] = (int)(p.x.b - A.x.b);
-    s.ya[k] = (int)(p.y.a - A.y.a), s.yb[k] = (int)(p.y.b - A.y.b);
-    s.gid[k] = rec.chain_base + (u32)(k - 3 - ne);
-  }
-  s.n = n;
-  auto add_edge = [&](int u, int v) {
-    if (u > v) {
-      int t = u;
-      u = v, v = t;
-    }
-    if ((s.adj[u] >> v) & 1ull) return;
-    s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
-    s.edge[s.nedge++] = (unsigned short)((u << 8) | v);
-  };
-  // boundary cycle A, events on AB, B, events on BC, C, events on CA
-  {
-    int cyc[GN], nc = 0, e = 3;
-    for (int k = 0; k < 3; ++k) {
-      cyc[nc++] = k;
-      for (int t = 0; t < nev[k]; ++t) cyc[nc++] = e++;
-    }
-    for (int k = 0; k < nc; ++k) add_edge(cyc[k], cyc[(k + 1) % nc]);
-  }
-  // chain pieces
-  for (u32 k = 0; k < rec.npairs; ++k) {
-    const Pair pr = P[k];
-    int ends[2];
-    for (int end = 0; end < 2; ++end) {
-      const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
-      int loc = -1;
-      if (e != NONE) {
-        for (int t = 0; t < ne; ++t)
-          if (s.corner[3 + t] == e) loc = 3 + t;
-      } else {
-        const u32 id = corner_id(g, segs[pr.seg], end);
-        for (int t = 3 + ne; t < n; ++t)
-          if (s.corner[t] == id) loc = t;
-      }
-      ends[end] = loc;
-    }
-    if (ends[0] < 0 || ends[1] < 0) {
-      s.ok = 0;
-      return;
-    }
-    add_edge(ends[0], ends[1]);
-  }
-  // the chain vertices' coordinates are written by their cell
-}
-
-__global__ void __launch_bounds__(32 * GWARPS) k_tierg(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                                       const Pair* sorted, const Seg* segs, const Event* ev,
-                                                       const CutRec* recs, const u32* glist, const u32* nglist,
-                                                       u32 NVg, u32 NE, int* tri, unsigned short* label,
-                                                       unsigned short* code, double* xy, u32* err) {
-  __shared__ GShared sm[GWARPS];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  GShared& s = sm[w];
-  const u32 total = *nglist;
-  for (u32 item = blockIdx.x * GWARPS + w; item < total; item += gridDim.x * GWARPS) {
-    const CutRec rec = recs[glist[item]];
-    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
-    if (lane == 0) build_local_g(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
-    __syncwarp();
-    if (!s.ok) {
-      if (lane == 0) atomicOr(err, ERR_CAPACITY);
-      __syncwarp();
-      continue;
-    }
-    const int n = s.n;
-    const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
-    // candidate pairs not joined by a constraint edge
-    int m = 0;
-    for (int u = 0; u < n; ++u)
-      for (int vb = u + 1; vb < n; vb += 32) {
-        const int v = vb + lane;
-        const bool ok = v < n && !((s.adj[u] >> v) & 1ull);
-        const u32 bal = __ballot_sync(0xffffffffu, ok);
-        if (ok) s.cand[m + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)((u << 8) | v);
-        m += __popc(bal);
-      }
-    int M = 1;
-    while (M < m) M <<= 1;
-    for (int k = m + lane; k < M; k += 32) s.cand[k] = 0xFFFFu;
-    __syncwarp();
-    // bitonic sort of the candidates
-    for (int kk = 2; kk <= M; kk <<= 1)
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int i = lane; i < M; i += 32) {
-          const int l = i ^ jj;
-          if (l > i) {
-            const unsigned short x = s.cand[i], y = s.cand[l];
-            const bool up = (i & kk) == 0;
-            if (up ? cand_less(s, y, x) : cand_less(s, x, y)) s.cand[i] = y, s.cand[l] = x;
-          }
-        }
-        __syncwarp();
-      }
-    // greedy: keep a pair when its open segment holds no vertex and crosses
-    // no kept edge
-    const int nb = 3 + (int)(rec.ntri + 2 - 2 * rec.nchain - 3);  // boundary vertices
-    const int max_edges = 3 * n - nb - 3;
-    for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
-      const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
-      const Pq pu = lpt(s, u), pv = lpt(s, v);
-      bool bad = false;
-      for (int k = lane; k < n; k += 32) {
-        if (k == u || k == v) continue;
-        const Pq pk = lpt(s, k);
-        if (orient3(pu, pv, pk) == 0 && zsign(dot3(pu, pv, pk)) > 0 && zsign(dot3(pv, pu, pk)) > 0) bad = true;
-      }
-      const int ned = s.nedge;
-      for (int k = lane; k < ned && !bad; k += 32) {
-        const int a = s.edge[k] >> 8, bb = s.edge[k] & 255;
-        if (a == u || a == v || bb == u || bb == v) continue;
-        const Pq pa = lpt(s, a), pb = lpt(s, bb);
-        const int o1 = orient3(pu, pv, pa), o2 = orient3(pu, pv, pb);
-        const int o3 = orient3(pa, pb, pu), o4 = orient3(pa, pb, pv);
-        if (o1 * o2 < 0 && o3 * o4 < 0) bad = true;
-      }
-      if (!__any_sync(0xffffffffu, bad)) {
-        if (lane == 0) {
-          s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
-          s.edge[s.nedge] = (unsigned short)((u << 8) | v);
-          s.nedge = s.nedge + 1;
-        }
-      }
-      __syncwarp();
-    }
-    // faces: 3-cycles with no vertex strictly inside
-    if (lane == 0) s.ntri = 0;
-    __syncwarp();
-    for (int u = lane; u < n; u += 32) {
-      for (u64 vs = s.adj[u] & ~((2ull << u) - 1ull); vs; vs &= vs - 1) {
-        const int v = __ffsll((long long)vs) - 1;
-        for (u64 ws = s.adj[u] & s.adj[v] & ~((2ull << v) - 1ull); ws; ws &= ws - 1) {
-          const int x = __ffsll((long long)ws) - 1;
-          const Pq a = lpt(s, u), b = lpt(s, v), c = lpt(s, x);
-          const int o = orient3(a, b, c);
-          if (o == 0) continue;
-          bool empty = true;
-          for (int k = 0; k < n && empty; ++k) {
-            if (k == u || k == v || k == x) continue;
-            const Pq pk = lpt(s, k);
-            if (orient3(a, b, pk) == o && orient3(b, c, pk) == o && orient3(c, a, pk) == o) empty = false;
-          }
-          if (!empty) continue;
-          const int slot = atomicAdd(&s.ntri, 1);
-          if (slot < GTRI) s.tri[slot] = o > 0 ? ((u32)u << 16 | (u32)v << 8 | (u32)x) : ((u32)u << 16 | (u32)x << 8 | (u32)v);
-        }
-      }
-    }
-    __syncwarp();
-    const int nt = min(s.ntri, GTRI);
-    if (lane == 0) {
-      if ((u32)s.ntri != rec.ntri) atomicOr(err, ERR_COUNT);
-      for (int a = 1; a < nt; ++a)
-        for (int b = a; b > 0 && s.tri[b] < s.tri[b - 1]; --b) {
-          const u32 t = s.tri[b];
-          s.tri[b] = s.tri[b - 1], s.tri[b - 1] = t;
-        }
-    }
-    __syncwarp();
-    const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
-    for (int k = lane; k < nt && k < (int)rec.ntri; k += 32) {
-      const int a = (int)(s.tri[k] >> 16), b = (int)((s.tri[k] >> 8) & 255u), c = (int)(s.tri[k] & 255u);
-      const u32 o = rec.tri_off + (u32)k;
-      tri[3 * (i64)o] = (int)s.gid[a];
-      tri[3 * (i64)o + 1] = (int)s.gid[b];
-      tri[3 * (i64)o + 2] = (int)s.gid[c];
-      const Pq pa = lpt(s, a), pb = lpt(s, b), pc = lpt(s, c);
-      const Pq ga{pa.x + A.x, pa.y + A.y}, gb{pb.x + A.x, pb.y + A.y}, gc{pc.x + A.x, pc.y + A.y};
-      label[o] = label_of(g, img, pitch, dtype, ga, gb, gc);
-      code[o] = cd;
-    }
-    // coordinates of the cell's inside vertices
-    const int nin = (int)rec.nchain;
-    for (int k = lane; k < nin; k += 32) {
-      const int loc = n - nin + k;
-      const u32 id = s.gid[loc];
-      xy[2 * (i64)id] = zdouble(zq(s.xa[loc] + A.x.a, s.xb[loc] + A.x.b)) / (double)g.S;
-      xy[2 * (i64)id + 1] = zdouble(zq(s.ya[loc] + A.y.a, s.yb[loc] + A.y.b)) / (double)g.S;
-    }
-    __syncwarp();
-  }
-  (void)NVg;
-  (void)NE;
 }
 
 __global__ void k_lattice_xy(GridP g, double* xy) {
@@ -886,14 +515,6 @@ void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
   if (nbc == 0) return;
   k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, poff, bstat, extra_scan,
                               chain_scan, NVg, NE, tri, label, code, xy, glist, nglist, ngtri, err);
-}
-
-void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32 NVg, u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err,
-                  cudaStream_t st) {
-  k_tierg<<<152 * 4, 32 * GWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, glist, nglist, NVg, NE,
-                                           tri, label, code, xy, err);
 }
 
 void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {

@@ -1,0 +1,414 @@
+// k_tierg.cu -- K4-G: cells outside the regime of Lemma 3.1 ("Tier-G").
+//
+// At grid edges h of a few pixels the pixel staircase puts several boundary
+// vertices, or several chords, into one base triangle, outside the paper's
+// finite table (Lemma 3.1 needs segments longer than the grid edge,
+// Sec. 3.2).  Such a cell is triangulated by a deterministic Steiner-free
+// rule: its local boundary graph (the cell's boundary split at the crossing
+// events, plus the pieces of boundary segments inside it) is completed
+// greedily -- every other vertex pair in order of exact squared length, ties
+// by local index pair, kept when its open segment holds no vertex and crosses
+// no kept edge.  A maximal plane straight-line graph on a point set
+// triangulates its convex hull, so the result tiles the cell and embeds every
+// boundary piece.  The faces are the 3-cycles with no vertex inside, listed
+// with the smallest local index first, counter-clockwise, in sorted order.
+//
+// Cells with at most TN vertices (all of them at h = 2 px) run one thread
+// each; larger cells run one warp each with the state in shared memory.  The
+// same templated code serves both (G = 1 or 32 lanes).
+#include "sbmt_cell.cuh"
+#include "sbmt_launch.h"
+
+namespace sbmt {
+
+namespace {
+
+constexpr int TN = 14;  // thread path: local vertices per cell
+constexpr int WN = 64;  // warp path
+constexpr int WWARPS = 4;
+
+SBMT_DEV constexpr int pow2_at_least(int x) {
+  int m = 1;
+  while (m < x) m <<= 1;
+  return m;
+}
+
+template <int N>
+struct GStore {
+  static constexpr int NCAND = N * (N - 1) / 2;
+  static constexpr int NCANDP = pow2_at_least(NCAND);
+  int xa[N], xb[N], ya[N], yb[N];  // cell-local exact coordinates (a + b sqrt3)
+  u32 gid[N];
+  u32 ref[N];  // event index (events) or pixel-corner id (inside vertices) while building
+  u64 adj[N];
+  unsigned short edge[3 * N];
+  unsigned short cand[NCANDP];
+  u32 tri[2 * N];
+  int n, nev, nedge, ntri, ok;
+};
+
+template <int G>
+SBMT_DEV bool g_any(bool v) {
+  if constexpr (G == 1) return v;
+  else return __any_sync(0xffffffffu, v);
+}
+template <int G>
+SBMT_DEV void g_sync() {
+  if constexpr (G == 32) __syncwarp();
+}
+
+template <int N>
+SBMT_DEV Pq lpt(const GStore<N>& s, int k) {
+  return Pq{zq(s.xa[k], s.xb[k]), zq(s.ya[k], s.yb[k])};
+}
+template <int N>
+SBMT_DEV Zq len2(const GStore<N>& s, int u, int v) {
+  const Zq dx = zq((i64)s.xa[v] - s.xa[u], (i64)s.xb[v] - s.xb[u]);
+  const Zq dy = zq((i64)s.ya[v] - s.ya[u], (i64)s.yb[v] - s.yb[u]);
+  return dx * dx + dy * dy;
+}
+// candidate order: exact squared length, then the packed pair (u << 8 | v)
+template <int N>
+SBMT_DEV bool cand_less(const GStore<N>& s, unsigned short x, unsigned short y) {
+  if (x == 0xFFFFu) return false;
+  if (y == 0xFFFFu) return true;
+  const int c = zcmp(len2(s, x >> 8, x & 255), len2(s, y >> 8, y & 255));
+  if (c != 0) return c < 0;
+  return x < y;
+}
+SBMT_DEV Zq dot3(const Pq& o, const Pq& p, const Pq& q) {
+  return (p.x - o.x) * (q.x - o.x) + (p.y - o.y) * (q.y - o.y);
+}
+
+// Build the local boundary graph (one thread): corners A, B, C; the events
+// on AB, BC, CA in counter-clockwise order; the inside vertices by pixel-
+// corner id; constraint edges = boundary cycle + one piece per pair.
+template <int N>
+SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
+                          const Event* ev, GStore<N>& s) {
+  s.ok = 0;
+  s.nedge = 0;
+  const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
+  for (int k = 0; k < 3; ++k) {
+    const Pq p = lattice_pt(g, cg.ci[k], cg.cj[k]);
+    s.xa[k] = (int)(p.x.a - A.x.a), s.xb[k] = (int)(p.x.b - A.x.b);
+    s.ya[k] = (int)(p.y.a - A.y.a), s.yb[k] = (int)(p.y.b - A.y.b);
+    s.gid[k] = vid(g, cg.ci[k], cg.cj[k]);
+    s.ref[k] = NONE;
+  }
+  // events: gather once, keyed by (local edge, counter-clockwise position)
+  int ne = 0;
+  int ek[N];
+  for (u32 k = 0; k < rec.npairs; ++k) {
+    const Pair pr = P[k];
+    for (int end = 0; end < 2; ++end) {
+      const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
+      if (e == NONE) continue;
+      if (3 + ne >= N) return;
+      const Event x = ev[e];
+      const int le = local_edge(cg, x.edge);
+      if (le < 0) return;
+      const int t = 3 + ne;
+      s.ref[t] = e, ek[t] = le, s.gid[t] = x.gid;
+      s.xa[t] = x.xa, s.xb[t] = x.xb, s.ya[t] = x.ya, s.yb[t] = x.yb;  // global for now
+      ++ne;
+    }
+  }
+  for (int a = 4; a < 3 + ne; ++a)
+    for (int b = a; b > 3; --b) {
+      const Zq pb = ccw_pos_xy(cg.down, ek[b], zq(s.xa[b], s.xb[b]), zq(s.ya[b], s.yb[b]));
+      const Zq pa = ccw_pos_xy(cg.down, ek[b - 1], zq(s.xa[b - 1], s.xb[b - 1]), zq(s.ya[b - 1], s.yb[b - 1]));
+      if (!(ek[b] < ek[b - 1] || (ek[b] == ek[b - 1] && zcmp(pb, pa) < 0))) break;
+      int ti = ek[b];
+      ek[b] = ek[b - 1], ek[b - 1] = ti;
+      u32 tu = s.ref[b];
+      s.ref[b] = s.ref[b - 1], s.ref[b - 1] = tu;
+      tu = s.gid[b], s.gid[b] = s.gid[b - 1], s.gid[b - 1] = tu;
+      ti = s.xa[b], s.xa[b] = s.xa[b - 1], s.xa[b - 1] = ti;
+      ti = s.xb[b], s.xb[b] = s.xb[b - 1], s.xb[b - 1] = ti;
+      ti = s.ya[b], s.ya[b] = s.ya[b - 1], s.ya[b - 1] = ti;
+      ti = s.yb[b], s.yb[b] = s.yb[b - 1], s.yb[b - 1] = ti;
+    }
+  int nev[3] = {0, 0, 0};
+  for (int t = 3; t < 3 + ne; ++t) {
+    nev[ek[t]]++;
+    s.xa[t] -= (int)A.x.a, s.xb[t] -= (int)A.x.b, s.ya[t] -= (int)A.y.a, s.yb[t] -= (int)A.y.b;
+  }
+  // inside vertices: distinct pixel-corner ids, ascending
+  int n = 3 + ne;
+  for (u32 k = 0; k < rec.npairs; ++k) {
+    const Pair pr = P[k];
+    if (pr.ev_in != NONE && pr.ev_out != NONE) continue;
+    const Seg sg = segs[pr.seg];
+    for (int end = 0; end < 2; ++end) {
+      if ((end == 0 ? pr.ev_in : pr.ev_out) != NONE) continue;
+      const u32 id = corner_id(g, sg, end);
+      int pos = 3 + ne;
+      while (pos < n && s.ref[pos] < id) ++pos;
+      if (pos < n && s.ref[pos] == id) continue;
+      if (n >= N) return;
+      for (int t = n; t > pos; --t) s.ref[t] = s.ref[t - 1];
+      s.ref[pos] = id;
+      ++n;
+    }
+  }
+  if ((u32)(n - 3 - ne) != rec.nchain) return;
+  for (int k = 3 + ne; k < n; ++k) {
+    const Pq p = corner_of_id(g, s.ref[k]);
+    s.xa[k] = (int)(p.x.a - A.x.a), s.xb[k] = (int)(p.x.b - A.x.b);
+    s.ya[k] = (int)(p.y.a - A.y.a), s.yb[k] = (int)(p.y.b - A.y.b);
+    s.gid[k] = rec.chain_base + (u32)(k - 3 - ne);
+  }
+  s.n = n, s.nev = ne;
+  for (int k = 0; k < n; ++k) s.adj[k] = 0;
+  bool room = true;
+  auto add_edge = [&](int u, int v) {
+    if (u > v) {
+      const int t = u;
+      u = v, v = t;
+    }
+    if ((s.adj[u] >> v) & 1ull) return;
+    if (s.nedge >= 3 * N) {
+      room = false;
+      return;
+    }
+    s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
+    s.edge[s.nedge++] = (unsigned short)((u << 8) | v);
+  };
+  {  // boundary cycle A, events on AB, B, events on BC, C, events on CA
+    int prev = 0, e = 3, first = 0;
+    for (int k = 0; k < 3; ++k) {
+      if (k) add_edge(prev, k), prev = k;
+      for (int t = 0; t < nev[k]; ++t) add_edge(prev, e), prev = e++;
+    }
+    add_edge(prev, first);
+  }
+  for (u32 k = 0; k < rec.npairs; ++k) {  // boundary pieces
+    const Pair pr = P[k];
+    int loc[2] = {-1, -1};
+    for (int end = 0; end < 2; ++end) {
+      const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
+      if (e != NONE) {
+        for (int t = 3; t < 3 + ne; ++t)
+          if (s.ref[t] == e) loc[end] = t;
+      } else {
+        const u32 id = corner_id(g, segs[pr.seg], end);
+        for (int t = 3 + ne; t < n; ++t)
+          if (s.ref[t] == id) loc[end] = t;
+      }
+    }
+    if (loc[0] < 0 || loc[1] < 0) return;
+    add_edge(loc[0], loc[1]);
+  }
+  s.ok = room ? 1 : 0;
+}
+
+// The greedy completion and face listing by a group of G lanes (G = 1: one
+// thread; G = 32: a warp with the store in shared memory).
+template <int G, int N>
+SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb) {
+  const int n = s.n;
+  // candidate pairs not joined by a constraint edge
+  int m = 0;
+  if constexpr (G == 1) {
+    for (int u = 0; u < n; ++u)
+      for (int v = u + 1; v < n; ++v)
+        if (!((s.adj[u] >> v) & 1ull)) s.cand[m++] = (unsigned short)((u << 8) | v);
+    // insertion sort by (exact length, pair)
+    for (int a = 1; a < m; ++a) {
+      const unsigned short x = s.cand[a];
+      int b = a;
+      while (b > 0 && cand_less(s, x, s.cand[b - 1])) s.cand[b] = s.cand[b - 1], --b;
+      s.cand[b] = x;
+    }
+  } else {
+    for (int u = 0; u < n; ++u)
+      for (int vb = u + 1; vb < n; vb += 32) {
+        const int v = vb + lane;
+        const bool ok = v < n && !((s.adj[u] >> v) & 1ull);
+        const u32 bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) s.cand[m + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)((u << 8) | v);
+        m += __popc(bal);
+      }
+    int M = 1;
+    while (M < m) M <<= 1;
+    for (int k = m + lane; k < M; k += 32) s.cand[k] = 0xFFFFu;
+    __syncwarp();
+    for (int kk = 2; kk <= M; kk <<= 1)
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = lane; i < M; i += 32) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const unsigned short x = s.cand[i], y = s.cand[l];
+            const bool up = (i & kk) == 0;
+            if (up ? cand_less(s, y, x) : cand_less(s, x, y)) s.cand[i] = y, s.cand[l] = x;
+          }
+        }
+        __syncwarp();
+      }
+  }
+  // keep a pair when its open segment holds no vertex and crosses no kept edge
+  const int max_edges = 3 * n - nb - 3;
+  for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
+    const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
+    const Pq pu = lpt(s, u), pv = lpt(s, v);
+    bool bad = false;
+    for (int k = lane; k < n && !bad; k += G) {
+      if (k == u || k == v) continue;
+      const Pq pk = lpt(s, k);
+      if (orient3(pu, pv, pk) == 0 && zsign(dot3(pu, pv, pk)) > 0 && zsign(dot3(pv, pu, pk)) > 0) bad = true;
+    }
+    const int ned = s.nedge;
+    for (int k = lane; k < ned && !bad; k += G) {
+      const int a = s.edge[k] >> 8, b = s.edge[k] & 255;
+      if (a == u || a == v || b == u || b == v) continue;
+      const Pq pa = lpt(s, a), pb = lpt(s, b);
+      const int o1 = orient3(pu, pv, pa), o2 = orient3(pu, pv, pb);
+      if (o1 * o2 >= 0) continue;
+      const int o3 = orient3(pa, pb, pu), o4 = orient3(pa, pb, pv);
+      if (o3 * o4 < 0) bad = true;
+    }
+    if (!g_any<G>(bad) && lane == 0) {
+      s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
+      s.edge[s.nedge] = (unsigned short)((u << 8) | v);
+      s.nedge = s.nedge + 1;
+    }
+    g_sync<G>();
+  }
+  // faces: 3-cycles with no vertex strictly inside
+  if (lane == 0) s.ntri = 0;
+  g_sync<G>();
+  for (int u = lane; u < n; u += G) {
+    for (u64 vs = s.adj[u] & ~((2ull << u) - 1ull); vs; vs &= vs - 1) {
+      const int v = __ffsll((long long)vs) - 1;
+      for (u64 ws = s.adj[u] & s.adj[v] & ~((2ull << v) - 1ull); ws; ws &= ws - 1) {
+        const int x = __ffsll((long long)ws) - 1;
+        const Pq a = lpt(s, u), b = lpt(s, v), c = lpt(s, x);
+        const int o = orient3(a, b, c);
+        if (o == 0) continue;
+        bool empty = true;
+        for (int k = 0; k < n && empty; ++k) {
+          if (k == u || k == v || k == x) continue;
+          const Pq pk = lpt(s, k);
+          if (orient3(a, b, pk) == o && orient3(b, c, pk) == o && orient3(c, a, pk) == o) empty = false;
+        }
+        if (!empty) continue;
+        int slot;
+        if constexpr (G == 1) slot = s.ntri++;
+        else slot = atomicAdd(&s.ntri, 1);
+        if (slot < 2 * N)
+          s.tri[slot] = o > 0 ? ((u32)u << 16 | (u32)v << 8 | (u32)x) : ((u32)u << 16 | (u32)x << 8 | (u32)v);
+      }
+    }
+  }
+  g_sync<G>();
+  if (lane == 0) {
+    const int nt = min(s.ntri, 2 * N);
+    for (int a = 1; a < nt; ++a)
+      for (int b = a; b > 0 && s.tri[b] < s.tri[b - 1]; --b) {
+        const u32 t = s.tri[b];
+        s.tri[b] = s.tri[b - 1], s.tri[b - 1] = t;
+      }
+  }
+  g_sync<G>();
+}
+
+template <int G, int N>
+SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const CellGeo& cg,
+                          const CutRec& rec, const GStore<N>& s, int lane, int* tri, unsigned short* label,
+                          unsigned short* code, double* xy, u32* err) {
+  const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
+  const int nt = min(s.ntri, 2 * N);
+  if (lane == 0 && (u32)s.ntri != rec.ntri) atomicOr(err, ERR_COUNT);
+  const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
+  for (int k = lane; k < nt && k < (int)rec.ntri; k += G) {
+    const int a = (int)(s.tri[k] >> 16), b = (int)((s.tri[k] >> 8) & 255u), c = (int)(s.tri[k] & 255u);
+    const u32 o = rec.tri_off + (u32)k;
+    tri[3 * (i64)o] = (int)s.gid[a];
+    tri[3 * (i64)o + 1] = (int)s.gid[b];
+    tri[3 * (i64)o + 2] = (int)s.gid[c];
+    const Pq pa = lpt(s, a), pb = lpt(s, b), pc = lpt(s, c);
+    label[o] = label_of(g, img, pitch, dtype, Pq{pa.x + A.x, pa.y + A.y}, Pq{pb.x + A.x, pb.y + A.y},
+                        Pq{pc.x + A.x, pc.y + A.y});
+    code[o] = cd;
+  }
+  // coordinates of the cell's inside vertices
+  const int nin = (int)rec.nchain;
+  const double invS = 1.0 / (double)g.S;
+  for (int k = lane; k < nin; k += G) {
+    const int loc = s.n - nin + k;
+    double2 v;
+    v.x = zdouble(zq((i64)s.xa[loc] + A.x.a, (i64)s.xb[loc] + A.x.b)) * invS;
+    v.y = zdouble(zq((i64)s.ya[loc] + A.y.a, (i64)s.yb[loc] + A.y.b)) * invS;
+    reinterpret_cast<double2*>(xy)[s.gid[loc]] = v;
+  }
+}
+
+// the number of local vertices of a Tier-G cell: ntri = 2 n_in + n_b - 2
+SBMT_DEV int local_count(const CutRec& rec) { return (int)(rec.ntri + 2 - rec.nchain); }
+SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 * rec.nchain); }
+
+// one thread per small Tier-G cell; larger cells are passed to the warp kernel
+__global__ void __launch_bounds__(128) k_tierg_thread(GridP g, const unsigned char* img, i64 pitch, int dtype,
+                                                      const Pair* sorted, const Seg* segs, const Event* ev,
+                                                      const CutRec* recs, const u32* glist, const u32* nglist,
+                                                      u32* wlist, u32* nwlist, int* tri, unsigned short* label,
+                                                      unsigned short* code, double* xy, u32* err) {
+  const u32 total = *nglist;
+  for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+    const u32 ri = glist[item];
+    const CutRec rec = recs[ri];
+    if (local_count(rec) > TN) {
+      wlist[atomicAdd(nwlist, 1u)] = ri;
+      continue;
+    }
+    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
+    GStore<TN> s;
+    build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
+    if (!s.ok) {
+      atomicOr(err, ERR_CAPACITY);
+      continue;
+    }
+    greedy_faces<1, TN>(s, 0, boundary_count(rec));
+    write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, err);
+  }
+}
+
+__global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsigned char* img, i64 pitch, int dtype,
+                                                            const Pair* sorted, const Seg* segs, const Event* ev,
+                                                            const CutRec* recs, const u32* wlist, const u32* nwlist,
+                                                            int* tri, unsigned short* label, unsigned short* code,
+                                                            double* xy, u32* err) {
+  __shared__ GStore<WN> sm[WWARPS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  GStore<WN>& s = sm[w];
+  const u32 total = *nwlist;
+  for (u32 item = blockIdx.x * WWARPS + w; item < total; item += gridDim.x * WWARPS) {
+    const CutRec rec = recs[wlist[item]];
+    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
+    if (lane == 0) build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
+    __syncwarp();
+    if (!s.ok) {
+      if (lane == 0) atomicOr(err, ERR_CAPACITY);
+      __syncwarp();
+      continue;
+    }
+    greedy_faces<32, WN>(s, lane, boundary_count(rec));
+    write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, err);
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+                  const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
+                  u32* wlist, u32* nwlist, int* tri, unsigned short* label, unsigned short* code, double* xy,
+                  u32* err, cudaStream_t st) {
+  k_tierg_thread<<<152 * 8, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, glist, nglist, wlist,
+                                         nwlist, tri, label, code, xy, err);
+  k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
+                                                tri, label, code, xy, err);
+}
+
+}  // namespace sbmt

@@ -16,6 +16,7 @@
 // (Sec. 3.3.3): by grid-edge id, then by position along the edge, so that
 // both cells sharing an edge name each crossing vertex identically with no
 // atomics and no tolerance.
+#include "sbmt_cell.cuh"
 #include "sbmt_launch.h"
 
 namespace sbmt {
@@ -209,47 +210,58 @@ __global__ void k_traverse_emit(GridP g, const Seg* segs, const u32* nseg, u32 c
   }
 }
 
-constexpr int RCAP = 1024;
-
 SBMT_DEV Zq event_t(const Event& e) {
   // horizontal grid edges run +x from their lower endpoint, slanted ones +y
   return (e.edge % 3u == 0u) ? zq(e.xa, e.xb) : zq(e.ya, e.yb);
 }
 
-__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eoff, u32 NVg, double* xy) {
-  __shared__ u32 s_e[RCAP];
-  __shared__ i64 s_a[RCAP], s_b[RCAP];
-  const u32 lo = eoff[blockIdx.x], hi = eoff[blockIdx.x + 1], n = hi - lo;
+// The registry: one block per event bucket (2048 consecutive grid-edge ids).
+// Events are counting-sorted by edge in shared memory; an event's vertex id
+// is NVg + (events on lower edge ids) + (events on its edge nearer the
+// edge's lower endpoint), compared exactly.
+__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, u32* elist, const u32* eoff, u32 NVg,
+                                              double* xy) {
+  constexpr int NEB = 1 << EB_LOG;
+  __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
+  __shared__ u32 s_sh[8];
+  const u32 lo = eoff[blockIdx.x], n = eoff[blockIdx.x + 1] - lo;
   if (n == 0) return;
-  const bool cached = n <= (u32)RCAP;
-  if (cached) {
-    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-      const Event e = ev[lo + i];
-      const Zq t = event_t(e);
-      s_e[i] = e.edge, s_a[i] = t.a, s_b[i] = t.b;
-    }
+  const u32 e0 = blockIdx.x << EB_LOG;
+  for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[ev[lo + i].edge - e0], 1u);
+  __syncthreads();
+  {
+    constexpr int PER = NEB / 256;
+    const int k0 = threadIdx.x * PER;
+    u32 s = 0;
+    for (int u = 0; u < PER; ++u) s += s_cnt[k0 + u];
+    u32 tot;
+    u32 run = block_exscan256(s, &tot, s_sh);
+    for (int u = 0; u < PER; ++u) s_off[k0 + u] = run, s_cur[k0 + u] = run, run += s_cnt[k0 + u];
+  }
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+    const u32 slot = atomicAdd(&s_cur[ev[lo + i].edge - e0], 1u);
+    elist[lo + slot] = i;
   }
   __syncthreads();
   const double invS = 1.0 / (double)g.S;
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
     const Event ei = ev[lo + i];
     const Zq ti = event_t(ei);
-    u32 rank = 0;
-    for (u32 k = 0; k < n; ++k) {
-      u32 ek;
-      Zq tk;
-      if (cached) {
-        ek = s_e[k], tk = zq(s_a[k], s_b[k]);
-      } else {
-        const Event e = ev[lo + k];
-        ek = e.edge, tk = event_t(e);
-      }
-      rank += (ek < ei.edge || (ek == ei.edge && zcmp(tk, ti) < 0)) ? 1u : 0u;
+    const u32 k = ei.edge - e0, first = s_off[k], cnt = s_cnt[k];
+    u32 rank = first;
+    for (u32 q = 0; q < cnt; ++q) {
+      const u32 j = elist[lo + first + q];
+      if (j != i && zcmp(event_t(ev[lo + j]), ti) < 0) ++rank;
     }
     const u32 gid = NVg + lo + rank;
     ev[lo + i].gid = gid;
-    xy[2 * (i64)gid] = zdouble(zq(ei.xa, ei.xb)) * invS;
-    xy[2 * (i64)gid + 1] = zdouble(zq(ei.ya, ei.yb)) * invS;
+    double2 v;
+    v.x = zdouble(zq(ei.xa, ei.xb)) * invS;
+    v.y = zdouble(zq(ei.ya, ei.yb)) * invS;
+    reinterpret_cast<double2*>(xy)[gid] = v;
   }
 }
 
@@ -269,10 +281,10 @@ void launch_traverse_emit(const GridP& g, const Seg* segs, const u32* nseg, u32 
   k_traverse_emit<<<grd, blk, 0, st>>>(g, segs, nseg, seg_cap, pcur, ecur, pairs, events, err);
 }
 
-void launch_rank_events(const GridP& g, Event* events, const u32* eoff, u32 nbe, u32 NVg, double* xy,
+void launch_rank_events(const GridP& g, Event* events, u32* elist, const u32* eoff, u32 nbe, u32 NVg, double* xy,
                         cudaStream_t st) {
   if (nbe == 0) return;
-  k_rank<<<nbe, 256, 0, st>>>(g, events, eoff, NVg, xy);
+  k_rank<<<nbe, 256, 0, st>>>(g, events, elist, eoff, NVg, xy);
 }
 
 }  // namespace sbmt

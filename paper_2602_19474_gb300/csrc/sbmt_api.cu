@@ -41,6 +41,7 @@ int fail(int code, const char* fmt, ...) {
 // lattice vertices they use
 struct Tables {
   std::vector<i64> clo, chi, cbase, vlo, vhi, vbase;
+  std::vector<int> lrow;  // per strip row: pixel rows of up-cell and down-cell centroids
   i64 j0 = 0, vj0 = 0, ncells = 0, nverts = 0;
 };
 
@@ -50,9 +51,13 @@ int build_tables(const GridP& g, Tables& t) {
   const i64 j0 = strip_of(g, zq(yl)), j1 = strip_of(g, zq(yr));
   t.j0 = j0;
   const i64 nrows = j1 - j0 + 1;
-  t.clo.resize(nrows), t.chi.resize(nrows), t.cbase.resize(nrows);
+  t.clo.resize(nrows), t.chi.resize(nrows), t.cbase.resize(nrows), t.lrow.resize(2 * nrows);
   i64 base = 0;
   for (i64 j = j0; j <= j1; ++j) {
+    // centroid heights oy + (3pj + p) sqrt3 (up) and oy + (3pj + 2p) sqrt3
+    // (down); pixel row = floor(y / S + 1/2)
+    t.lrow[2 * (j - j0)] = (int)zfloordiv(Zq{2 * oy + g.S, 2 * (3 * p * j + p)}, 2 * g.S);
+    t.lrow[2 * (j - j0) + 1] = (int)zfloordiv(Zq{2 * oy + g.S, 2 * (3 * p * j + 2 * p)}, 2 * g.S);
     const Zq yj = zq(oy, 3 * p * j), yj1 = zq(oy, 3 * p * (j + 1));
     // the band of the strip inside the rectangle is [ya, yb]; an up cell is
     // widest at ya, a down cell at yb; da, db = the slant offsets there
@@ -285,7 +290,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   // tables
   const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
   i64* dt;
-  if ((rc = dalloc(ctx, &dt, 3 * nrows + 3 * nvr, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &dt, 3 * nrows + 3 * nvr + nrows, tmp))) return bail(rc);
   {
     std::vector<i64> all;
     all.insert(all.end(), tb.clo.begin(), tb.clo.end());
@@ -294,6 +299,9 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
     all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
     all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
     all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
+    const size_t nl = all.size();
+    all.resize(nl + nrows);
+    std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
     if (cudaMemcpyAsync(dt, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, st))
       return bail(fail(SBMT_ECUDA, "tables upload"));
     if (cudaStreamSynchronize(st)) return bail(fail(SBMT_ECUDA, "tables upload sync"));
@@ -301,14 +309,15 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
   g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
   g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
+  g.lrow = (const int*)(dt + 3 * nrows + 3 * nvr);
   g.ncells = tb.ncells, g.nverts = tb.nverts;
 
   // counters: [0] nvtx (u64), [1] totals pairs, [2] totals events, then u32s
   unsigned long long* cnt64;
   if ((rc = dalloc(ctx, &cnt64, 8, tmp))) return bail(rc);
-  u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, pad...
+  u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, ngtri, nwlist
   CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
-  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3;
+  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3, *nwlist = cnt32 + 4;
 
   // K1a
   const int W = g.W, H = g.H;
@@ -360,7 +369,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist;
+  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist, *wlist, *elist;
   std::vector<void*>& keep = m->keep ? m->scratch : tmp;
   if ((rc = dalloc(ctx, &pairs, NP, tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &sorted, NP, tmp))) return bail(rc);
@@ -371,6 +380,8 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = dalloc(ctx, &chain_scan, nbc + 1, tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &cut_scan, nbc + 1, tmp))) return bail(rc);
   if ((rc = dalloc(ctx, &glist, NP, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &wlist, NP, tmp))) return bail(rc);
+  if ((rc = dalloc(ctx, &elist, NE, tmp))) return bail(rc);
   if (m->keep) {
     // keep the segments and bucket offsets too: move them to the mesh
     for (auto it = tmp.begin(); it != tmp.end(); ++it)
@@ -394,15 +405,15 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
   TRACE(KN_TEMIT, launch_traverse_emit(g, segs, nseg, seg_cap, pcur, ecur, pairs, ev, err, st));
-  TRACE(KN_RANK, launch_rank_events(g, ev, eoff, nbe, (u32)NVg, m->xy, st));
+  TRACE(KN_RANK, launch_rank_events(g, ev, elist, eoff, nbe, (u32)NVg, m->xy, st));
   TRACE(KN_CLASSIFY, launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st));
   TRACE(KN_SCAN, launch_scan(bstat + 1, 4, extra_scan, nbc, st));
   TRACE(KN_SCAN, launch_scan(bstat + 2, 4, chain_scan, nbc, st));
   TRACE(KN_SCAN, launch_scan(bstat + 0, 4, cut_scan, nbc, st));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
               (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, err, st));
-  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, (u32)NVg, (u32)NE, m->tri,
-               m->label, m->code, m->xy, err, st));
+  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, wlist, nwlist,
+                               m->tri, m->label, m->code, m->xy, err, st));
   TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));

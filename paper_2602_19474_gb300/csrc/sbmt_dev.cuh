@@ -42,12 +42,15 @@ SBMT_HD Zq zq(i64 a, i64 b = 0) { return Zq{a, b}; }
 SBMT_HD Zq operator+(Zq x, Zq y) { return Zq{x.a + y.a, x.b + y.b}; }
 SBMT_HD Zq operator-(Zq x, Zq y) { return Zq{x.a - y.a, x.b - y.b}; }
 SBMT_HD Zq operator*(Zq x, Zq y) { return Zq{x.a * y.a + 3 * x.b * y.b, x.a * y.b + x.b * y.a}; }
-// sign of a + b sqrt3: when a and b disagree in sign compare a^2 with 3 b^2
+// sign of a + b sqrt3: when a and b disagree in sign compare a^2 with 3 b^2.
+// The components of a cell-local determinant can reach ~1e15 (points on
+// rational pixel lines against lattice rows at y ~ 3pj sqrt3), so the squares
+// are taken in 128 bits.
 SBMT_HD int zsign(Zq v) {
   if (v.b == 0) return (v.a > 0) - (v.a < 0);
   if (v.a == 0) return (v.b > 0) - (v.b < 0);
   if ((v.a > 0) == (v.b > 0)) return v.a > 0 ? 1 : -1;
-  i64 l = v.a * v.a, r = 3 * v.b * v.b;
+  const __int128 l = (__int128)v.a * v.a, r = 3 * ((__int128)v.b * v.b);
   if (v.a > 0) return l > r ? 1 : -1;
   return r > l ? 1 : -1;
 }
@@ -123,6 +126,7 @@ struct GridP {
   const i64* vlo;       // per vertex row: first i
   const i64* vhi;
   const i64* vbase;     // per vertex row: id of its first vertex
+  const int* lrow;      // per strip row: pixel row of up-cell / down-cell centroids
   i64 ncells, nverts;
 };
 

@@ -27,7 +27,7 @@ void launch_traverse_emit(const GridP& g, const Seg* segs, const u32* nseg, u32 
 
 // frozen registry: rank events by (grid-edge id, position) inside each event
 // bucket, assign vertex ids NVg + rank, write their coordinates.
-void launch_rank_events(const GridP& g, Event* events, const u32* eoff, u32 nbe, u32 NVg, double* xy,
+void launch_rank_events(const GridP& g, Event* events, u32* elist, const u32* eoff, u32 nbe, u32 NVg, double* xy,
                         cudaStream_t st);
 
 // K3: sort each cell bucket's pairs by cell, classify every cut cell (key,
@@ -47,11 +47,13 @@ void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
                  unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* ngtri,
                  u32* err, cudaStream_t st);
 
-// K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.
+// K4-G: greedy Steiner-free triangulation of every queued Tier-G cell (one
+// thread per small cell; cells above the thread limit go to a warp each
+// through wlist).
 void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32 NVg, u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err,
-                  cudaStream_t st);
+                  u32* wlist, u32* nwlist, int* tri, unsigned short* label, unsigned short* code, double* xy,
+                  u32* err, cudaStream_t st);
 
 // coordinates of the lattice vertices
 void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st);

@@ -90,3 +90,20 @@ def test_paper_regime_no_tier_g():
     img = synth.disk(size=48, cx=24, cy=24, r=15)
     g, o = run_both(img, 2, 3)
     assert g["n_tierG_cells"] == 0
+
+
+def test_voronoi8192_full_size_windows():
+    """The 8192^2 16-label workload in the bench's launch configuration
+    (device-resident u16 image, h = 2): counts equal to the oracle's, exact
+    area identities at full size, and oracle parity on windows spread over
+    the image (interior, near each border, a corner)."""
+    from gpu_util import assert_window_matches_crop, exact_area_checks
+
+    img = synth.voronoi_labels()
+    g = gpu_mesh(img, 2, 1, on_device=True)
+    assert len(g["tri"]) == 42948064 and g["n_cut_cells"] == 1179109 and g["n_tierG_cells"] == 234192
+    exact_area_checks(img, g, 2.0)
+    n = 0
+    for x0, y0 in [(0, 0), (3000, 2000), (7808, 4100), (5000, 7808), (100, 6000), (4096, 4096)]:
+        n += assert_window_matches_crop(img, g, 2, 1, x0, y0, 384, 384)
+    assert n > 300000
