@@ -242,31 +242,6 @@ __global__ void __launch_bounds__(256) k_classify(GridP g, const Pair* pairs, Pa
   if (threadIdx.x < 4) bstat[4 * b + threadIdx.x] = s_stat[threadIdx.x];
 }
 
-// exclusive scan over n strided values, one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_scan(const u32* in, int stride, u32* out, u32 n) {
-  __shared__ u32 sh[1024];
-  const u32 t = threadIdx.x;
-  const u32 chunk = (n + 1023) / 1024;
-  const u32 a = min(n, t * chunk), e = min(n, a + chunk);
-  u32 s = 0;
-  for (u32 i = a; i < e; ++i) s += in[(u64)i * stride];
-  sh[t] = s;
-  __syncthreads();
-  for (u32 o = 1; o < 1024; o <<= 1) {
-    const u32 v = t >= o ? sh[t - o] : 0u;
-    __syncthreads();
-    sh[t] += v;
-    __syncthreads();
-  }
-  u32 run = sh[t] - s;
-  for (u32 i = a; i < e; ++i) {
-    const u32 v = in[(u64)i * stride];
-    out[i] = run;
-    run += v;
-  }
-  if (t == 1023) out[n] = sh[1023];
-}
-
 // ---------------------------------------------------------------------------
 // K4: emission
 // ---------------------------------------------------------------------------
@@ -375,11 +350,10 @@ SBMT_DEV void emit_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 }
 
 __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                              const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
-                                              const u32* poff, const u32* bstat, const u32* extra_scan,
-                                              const u32* chain_scan, u32 NVg, u32 NE, int* tri,
-                                              unsigned short* label, unsigned short* code, double* xy, u32* glist,
-                                              u32* nglist, u32* ngtri, u32* err) {
+                                              CutRec* recs, const u32* poff, const u32* bstat,
+                                              const u32* extra_scan, const u32* chain_scan, u32 NVg, u32 NE,
+                                              int* tri, unsigned short* label, unsigned short* code, u32* tlist,
+                                              u32* ntlist, u32* glist, u32* nglist, u32* ngtri) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
@@ -430,6 +404,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0, jr = 0;
   int lr0 = 0, lr1 = 0;
   const i64 twoS = 2 * g.S;
+  const float inv2S = 1.0f / (float)twoS;
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     if (s_cnt[k] != 1u) continue;
     const i64 cid = c0 + k;
@@ -451,7 +426,11 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       v0 = (int)(vb0 + i + 1), v1 = (int)(vb1 + i + 1), v2 = (int)(vb1 + i);
       xc = g.ox + 3 * g.p * (2 * i + jr + 2), prow = lr1;
     }
-    const i64 pcol = ifloordiv(2 * xc + g.S, twoS);
+    // pixel column floor((2 xc + S) / 2S) in 32 bits: a float estimate, corrected
+    const int num = (int)(2 * xc + g.S), den = (int)twoS;
+    int pcol = (int)floorf((float)num * inv2S);
+    while (pcol * den > num) --pcol;
+    while ((pcol + 1) * den <= num) ++pcol;
     const int l = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
                              : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
     tri[3 * (i64)o] = v0;
@@ -460,38 +439,47 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     label[o] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
     code[o] = 0;
   }
-  // cut cells
+  // cut cells: record their output ranges and queue them by kind
   for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
     CutRec rec = recs[rec0 + r];
     rec.tri_off = T0_ + s_off[rec.cell - c0];
     rec.chain_base = CB0 + s_cb[r];
+    recs[rec0 + r] = rec;
     if (rec.code & (1u << 16)) {
-      recs[rec0 + r] = rec;
-      const u32 slot = atomicAdd(nglist, 1u);
-      glist[slot] = rec0 + r;
+      glist[atomicAdd(nglist, 1u)] = rec0 + r;
       atomicAdd(ngtri, rec.ntri);
-      continue;
+    } else {
+      tlist[atomicAdd(ntlist, 1u)] = rec0 + r;
     }
+  }
+}
+
+// Tier-T patches, one thread per queued cell
+__global__ void __launch_bounds__(128) k_tiert(GridP g, const unsigned char* img, i64 pitch, int dtype,
+                                               const Pair* sorted, const Seg* segs, const Event* ev,
+                                               const CutRec* recs, const u32* tlist, const u32* ntlist, int* tri,
+                                               unsigned short* label, unsigned short* code, double* xy, u32* err) {
+  const u32 total = *ntlist;
+  for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+    const CutRec rec = recs[tlist[item]];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
     emit_tier_t(g, cg, rec, sorted + rec.pair_lo, segs, ev, img, pitch, dtype, tri, label, code, xy, err);
   }
 }
 
-__global__ void k_lattice_xy(GridP g, double* xy) {
+// lattice vertex coordinates: one block per vertex row
+__global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy) {
+  const int r = blockIdx.x;
+  const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
   const double invS = 1.0 / (double)g.S;
-  for (i64 id = (i64)blockIdx.x * blockDim.x + threadIdx.x; id < g.nverts; id += (i64)gridDim.x * blockDim.x) {
-    int lo = 0, hi = g.nvrows - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (g.vbase[mid] <= id) lo = mid;
-      else hi = mid - 1;
-    }
-    const i64 j = g.vj0 + lo, i = g.vlo[lo] + (id - g.vbase[lo]);
-    const Pq p = lattice_pt(g, i, j);
+  const double y = zdouble(zq(g.oy, 3 * g.p * j)) * invS;
+  const i64 x0 = g.ox + 3 * g.p * (2 * lo + j), dx = 6 * g.p;
+  double2* out = reinterpret_cast<double2*>(xy) + base;
+  for (i64 k = threadIdx.x; k < n; k += blockDim.x) {
     double2 v;
-    v.x = zdouble(p.x) * invS;
-    v.y = zdouble(p.y) * invS;
-    reinterpret_cast<double2*>(xy)[id] = v;
+    v.x = (double)(x0 + dx * k) * invS;
+    v.y = y;
+    out[k] = v;
   }
 }
 
@@ -503,24 +491,25 @@ void launch_classify(const GridP& g, const Pair* pairs, Pair* sorted, const u32*
   k_classify<<<nbc, 256, 0, st>>>(g, pairs, sorted, poff, segs, events, recs, bstat, err);
 }
 
-void launch_scan(const u32* in, int stride, u32* out, u32 n, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(in, stride, out, n);
+void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* poff,
+                 const u32* bstat, const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
+                 unsigned short* label, unsigned short* code, u32* tlist, u32* ntlist, u32* glist, u32* nglist,
+                 u32* ngtri, cudaStream_t st) {
+  if (nbc == 0) return;
+  k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, poff, bstat, extra_scan, chain_scan, NVg, NE, tri, label,
+                              code, tlist, ntlist, glist, nglist, ngtri);
 }
 
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                 const Seg* segs, const Event* events, CutRec* recs, const u32* poff, const u32* bstat,
-                 const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* ngtri,
-                 u32* err, cudaStream_t st) {
-  if (nbc == 0) return;
-  k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, poff, bstat, extra_scan,
-                              chain_scan, NVg, NE, tri, label, code, xy, glist, nglist, ngtri, err);
+void launch_tiert(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+                  const Seg* segs, const Event* events, const CutRec* recs, const u32* tlist, const u32* ntlist,
+                  int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err, cudaStream_t st) {
+  k_tiert<<<152 * 16, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, tlist, ntlist, tri, label,
+                                    code, xy, err);
 }
 
 void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {
   if (g.nverts == 0) return;
-  const unsigned grd = (unsigned)std::min<i64>((g.nverts + 255) / 256, 152 * 32);
-  k_lattice_xy<<<grd, 256, 0, st>>>(g, xy);
+  k_lattice_xy<<<g.nvrows, 256, 0, st>>>(g, xy);
 }
 
 }  // namespace sbmt

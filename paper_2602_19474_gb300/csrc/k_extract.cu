@@ -32,30 +32,89 @@ SBMT_DEV int corner_mask(const unsigned char* img, i64 pitch, int W, int H, int 
 }
 SBMT_DEV bool vertex_mask(int m) { return m != 0 && m != (BE_E | BE_W) && m != (BE_N | BE_S); }
 
+// 8 consecutive pixels of row y starting at column x0 (x0 a multiple of 8),
+// OUTSIDE beyond the image; one vector load when the row is in range and
+// aligned
 template <typename T>
-__global__ void __launch_bounds__(1024) k_corner_bits(const unsigned char* img, i64 pitch, int W, int H, u32* vrow,
-                                                      int wpr, u32* vcol, int wpc, unsigned long long* nvtx) {
+SBMT_DEV void load8(const unsigned char* img, i64 pitch, int W, int H, int x0, int y, int* out) {
+  if (y < 0 || y >= H) {
+    for (int k = 0; k < 8; ++k) out[k] = OUTSIDE;
+    return;
+  }
+  const unsigned char* row = img + (i64)y * pitch;
+  const T* p = (const T*)row + x0;
+  if (x0 + 8 <= W && (((uintptr_t)p) & (8 * sizeof(T) - 1)) == 0) {
+    if (sizeof(T) == 2) {
+      const uint4 v = *(const uint4*)p;
+      const u32 w[4] = {v.x, v.y, v.z, v.w};
+      for (int k = 0; k < 4; ++k) out[2 * k] = (int)(w[k] & 0xFFFFu), out[2 * k + 1] = (int)(w[k] >> 16);
+    } else {
+      const uint2 v = *(const uint2*)p;
+      const u32 w[2] = {v.x, v.y};
+      for (int k = 0; k < 2; ++k)
+        for (int b = 0; b < 4; ++b) out[4 * k + b] = (int)((w[k] >> (8 * b)) & 0xFFu);
+    }
+    return;
+  }
+  for (int k = 0; k < 8; ++k) out[k] = (x0 + k < W) ? (int)p[k] : OUTSIDE;
+}
+
+// K1a: a block covers 32 corner rows x 256 corner columns; each thread takes
+// 8 consecutive corners of 4 rows.  Vertex flags go to shared memory as one
+// byte per (row, 8 corners), then out as row words and transposed column words.
+template <typename T>
+__global__ void __launch_bounds__(256) k_corner_bits(const unsigned char* img, i64 pitch, int W, int H, u32* vrow,
+                                                     int wpr, u32* vcol, int wpc, unsigned long long* nvtx) {
   __shared__ unsigned char fl[32][33];
   __shared__ unsigned int cnt;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int cx = blockIdx.x * 32 + tx, cy = blockIdx.y * 32 + ty;
-  if (tx == 0 && ty == 0) cnt = 0;
-  bool v = false;
-  if (cx <= W && cy <= H) v = vertex_mask(corner_mask<T>(img, pitch, W, H, cx, cy));
-  const u32 row_bits = __ballot_sync(0xffffffffu, v);
-  fl[ty][tx] = v ? 1 : 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * 256 + lane * 8;  // first corner column of this thread
+  const int r0 = blockIdx.y * 32;
+  if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  if (tx == 0 && cy <= H) {
-    vrow[(i64)cy * wpr + blockIdx.x] = row_bits;
-    atomicAdd(&cnt, (unsigned)__popc(row_bits));
+  u32 mycnt = 0;
+  for (int rr = 0; rr < 4; ++rr) {
+    const int r = w * 4 + rr, cy = r0 + r;
+    int lo[9], hi[9];  // pixel rows cy-1 and cy, columns x0-1 .. x0+7
+    load8<T>(img, pitch, W, H, x0, cy - 1, lo + 1);
+    load8<T>(img, pitch, W, H, x0, cy, hi + 1);
+    // the pixel left of x0 is the previous lane's last one
+    int pl = __shfl_up_sync(0xffffffffu, lo[8], 1), ph = __shfl_up_sync(0xffffffffu, hi[8], 1);
+    if (lane == 0) {
+      const bool in = x0 - 1 >= 0 && x0 - 1 < W;
+      pl = (in && cy - 1 >= 0 && cy - 1 < H) ? (int)((const T*)(img + (i64)(cy - 1) * pitch))[x0 - 1] : OUTSIDE;
+      ph = (in && cy >= 0 && cy < H) ? (int)((const T*)(img + (i64)cy * pitch))[x0 - 1] : OUTSIDE;
+    }
+    lo[0] = pl, hi[0] = ph;
+    u32 bits = 0;
+    for (int k = 0; k < 8; ++k) {
+      // corner (x0 + k, cy): a = (cx-1, cy-1), b = (cx, cy-1), c = (cx-1, cy), d = (cx, cy)
+      const int a = lo[k], b = lo[k + 1], c = hi[k], d = hi[k + 1];
+      const int m = (b != d ? BE_E : 0) | (a != c ? BE_W : 0) | (c != d ? BE_N : 0) | (a != b ? BE_S : 0);
+      const bool v = vertex_mask(m) && x0 + k <= W && cy <= H;
+      bits |= (v ? 1u : 0u) << k;
+    }
+    fl[r][lane] = (unsigned char)bits;
+    mycnt += __popc(bits);
   }
-  // transposed read: this warp gathers corner column blockIdx.x * 32 + ty
-  const bool v2 = fl[tx][ty] != 0;
-  const u32 col_bits = __ballot_sync(0xffffffffu, v2);
-  const int ccol = blockIdx.x * 32 + ty;
-  if (tx == 0 && ccol <= W) vcol[(i64)ccol * wpc + blockIdx.y] = col_bits;
+  atomicAdd(&cnt, mycnt);
   __syncthreads();
-  if (tx == 0 && ty == 0 && cnt) atomicAdd(nvtx, (unsigned long long)cnt);
+  // row words: row r, word k of the block = groups 4k .. 4k+3
+  {
+    const int r = threadIdx.x >> 3, k = threadIdx.x & 7, cy = r0 + r;
+    const u32 word = (u32)fl[r][4 * k] | ((u32)fl[r][4 * k + 1] << 8) | ((u32)fl[r][4 * k + 2] << 16) |
+                     ((u32)fl[r][4 * k + 3] << 24);
+    const int wx = blockIdx.x * 8 + k;
+    if (cy <= H && wx < wpr) vrow[(i64)cy * wpr + wx] = word;
+  }
+  // column words: corner column c of the block, rows r0 .. r0+31
+  {
+    const int c = threadIdx.x, cx = blockIdx.x * 256 + c;
+    u32 word = 0;
+    for (int r = 0; r < 32; ++r) word |= (u32)((fl[r][c >> 3] >> (c & 7)) & 1u) << r;
+    if (cx <= W) vcol[(i64)cx * wpc + blockIdx.y] = word;
+  }
+  if (threadIdx.x == 0 && cnt) atomicAdd(nvtx, (unsigned long long)cnt);
 }
 
 // first set bit at index >= from in a packed bit-plane line of nwords words;
@@ -123,7 +182,7 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
 
 void launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
                         u32* vcol, int wpc, unsigned long long* nvtx, cudaStream_t st) {
-  dim3 blk(32, 32), grd((W + 1 + 31) / 32, (H + 1 + 31) / 32);
+  dim3 blk(256), grd((W + 1 + 255) / 256, (H + 1 + 31) / 32);
   if (dtype == 1)
     k_corner_bits<unsigned char><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx);
   else

@@ -44,6 +44,7 @@ struct GStore {
   unsigned short edge[3 * N];
   unsigned short cand[NCANDP];
   u32 tri[2 * N];
+  float fx[N], fy[N];  // rounded coordinates, only to order candidate lengths quickly
   int n, nev, nedge, ntri, ok;
 };
 
@@ -79,6 +80,63 @@ SBMT_DEV bool cand_less(const GStore<N>& s, unsigned short x, unsigned short y) 
 SBMT_DEV Zq dot3(const Pq& o, const Pq& p, const Pq& q) {
   return (p.x - o.x) * (q.x - o.x) + (p.y - o.y) * (q.y - o.y);
 }
+
+// Same order as cand_less, decided in single precision when the two lengths
+// are far apart and exactly otherwise.  Coordinates are rounded from their
+// exact values (error below |coordinate| 2^-24), so a key's error stays far
+// below tol for cells of extent E (scaled units).
+template <int N>
+SBMT_DEV bool cand_less_fast(const GStore<N>& s, unsigned short x, unsigned short y, float tolc) {
+  const int xu = x >> 8, xv = x & 255, yu = y >> 8, yv = y & 255;
+  const float dx0 = s.fx[xv] - s.fx[xu], dy0 = s.fy[xv] - s.fy[xu];
+  const float dx1 = s.fx[yv] - s.fx[yu], dy1 = s.fy[yv] - s.fy[yu];
+  const float kx = dx0 * dx0 + dy0 * dy0, ky = dx1 * dx1 + dy1 * dy1;
+  const float tol = 1e-5f * (kx + ky) + tolc;
+  if (kx < ky - tol) return true;
+  if (kx > ky + tol) return false;
+  return cand_less(s, x, y);
+}
+
+// orientation of (u, v, w) computed exactly on demand
+template <int N>
+struct OriDirect {
+  const GStore<N>* s;
+  SBMT_DEV int operator()(int u, int v, int w) const { return orient3(lpt(*s, u), lpt(*s, v), lpt(*s, w)); }
+};
+
+// orientation of every vertex triple computed once (exactly) into two bit
+// sets indexed by the sorted triple; a permutation of the triple flips the
+// sign with its parity
+template <int N>
+struct OriTable {
+  static constexpr int NT = N * (N - 1) * (N - 2) / 6;
+  static constexpr int NW = (NT + 63) / 64;
+  u64 pos[NW], zero[NW];
+  SBMT_DEV static int idx(int a, int b, int c) { return c * (c - 1) * (c - 2) / 6 + b * (b - 1) / 2 + a; }
+  SBMT_DEV void build(const GStore<N>& s) {
+    for (int k = 0; k < NW; ++k) pos[k] = 0, zero[k] = 0;
+    for (int c = 2; c < s.n; ++c) {
+      const Pq pc = lpt(s, c);
+      for (int b = 1; b < c; ++b) {
+        const Pq pb = lpt(s, b);
+        for (int a = 0; a < b; ++a) {
+          const int o = orient3(lpt(s, a), pb, pc), t = idx(a, b, c);
+          if (o == 0) zero[t >> 6] |= 1ull << (t & 63);
+          else if (o > 0) pos[t >> 6] |= 1ull << (t & 63);
+        }
+      }
+    }
+  }
+  SBMT_DEV int operator()(int u, int v, int w) const {
+    int sg = 1, t;
+    if (u > v) t = u, u = v, v = t, sg = -sg;
+    if (v > w) t = v, v = w, w = t, sg = -sg;
+    if (u > v) t = u, u = v, v = t, sg = -sg;
+    const int i = idx(u, v, w);
+    if ((zero[i >> 6] >> (i & 63)) & 1ull) return 0;
+    return ((pos[i >> 6] >> (i & 63)) & 1ull) ? sg : -sg;
+  }
+};
 
 // Build the local boundary graph (one thread): corners A, B, C; the events
 // on AB, BC, CA in counter-clockwise order; the inside vertices by pixel-
@@ -160,7 +218,11 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
     s.gid[k] = rec.chain_base + (u32)(k - 3 - ne);
   }
   s.n = n, s.nev = ne;
-  for (int k = 0; k < n; ++k) s.adj[k] = 0;
+  for (int k = 0; k < n; ++k) {
+    s.adj[k] = 0;
+    s.fx[k] = (float)zdouble(zq(s.xa[k], s.xb[k]));
+    s.fy[k] = (float)zdouble(zq(s.ya[k], s.yb[k]));
+  }
   bool room = true;
   auto add_edge = [&](int u, int v) {
     if (u > v) {
@@ -205,8 +267,8 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 
 // The greedy completion and face listing by a group of G lanes (G = 1: one
 // thread; G = 32: a warp with the store in shared memory).
-template <int G, int N>
-SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb) {
+template <int G, int N, class O>
+SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float tolc) {
   const int n = s.n;
   // candidate pairs not joined by a constraint edge
   int m = 0;
@@ -218,7 +280,7 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb) {
     for (int a = 1; a < m; ++a) {
       const unsigned short x = s.cand[a];
       int b = a;
-      while (b > 0 && cand_less(s, x, s.cand[b - 1])) s.cand[b] = s.cand[b - 1], --b;
+      while (b > 0 && cand_less_fast(s, x, s.cand[b - 1], tolc)) s.cand[b] = s.cand[b - 1], --b;
       s.cand[b] = x;
     }
   } else {
@@ -251,21 +313,19 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb) {
   const int max_edges = 3 * n - nb - 3;
   for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
     const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
-    const Pq pu = lpt(s, u), pv = lpt(s, v);
     bool bad = false;
     for (int k = lane; k < n && !bad; k += G) {
-      if (k == u || k == v) continue;
-      const Pq pk = lpt(s, k);
-      if (orient3(pu, pv, pk) == 0 && zsign(dot3(pu, pv, pk)) > 0 && zsign(dot3(pv, pu, pk)) > 0) bad = true;
+      if (k == u || k == v || ori(u, v, k) != 0) continue;
+      const Pq pu = lpt(s, u), pv = lpt(s, v), pk = lpt(s, k);
+      if (zsign(dot3(pu, pv, pk)) > 0 && zsign(dot3(pv, pu, pk)) > 0) bad = true;
     }
     const int ned = s.nedge;
     for (int k = lane; k < ned && !bad; k += G) {
       const int a = s.edge[k] >> 8, b = s.edge[k] & 255;
       if (a == u || a == v || b == u || b == v) continue;
-      const Pq pa = lpt(s, a), pb = lpt(s, b);
-      const int o1 = orient3(pu, pv, pa), o2 = orient3(pu, pv, pb);
+      const int o1 = ori(u, v, a), o2 = ori(u, v, b);
       if (o1 * o2 >= 0) continue;
-      const int o3 = orient3(pa, pb, pu), o4 = orient3(pa, pb, pv);
+      const int o3 = ori(a, b, u), o4 = ori(a, b, v);
       if (o3 * o4 < 0) bad = true;
     }
     if (!g_any<G>(bad) && lane == 0) {
@@ -283,14 +343,12 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb) {
       const int v = __ffsll((long long)vs) - 1;
       for (u64 ws = s.adj[u] & s.adj[v] & ~((2ull << v) - 1ull); ws; ws &= ws - 1) {
         const int x = __ffsll((long long)ws) - 1;
-        const Pq a = lpt(s, u), b = lpt(s, v), c = lpt(s, x);
-        const int o = orient3(a, b, c);
+        const int o = ori(u, v, x);
         if (o == 0) continue;
         bool empty = true;
         for (int k = 0; k < n && empty; ++k) {
           if (k == u || k == v || k == x) continue;
-          const Pq pk = lpt(s, k);
-          if (orient3(a, b, pk) == o && orient3(b, c, pk) == o && orient3(c, a, pk) == o) empty = false;
+          if (ori(u, v, k) == o && ori(v, x, k) == o && ori(x, u, k) == o) empty = false;
         }
         if (!empty) continue;
         int slot;
@@ -369,7 +427,10 @@ __global__ void __launch_bounds__(128) k_tierg_thread(GridP g, const unsigned ch
       atomicOr(err, ERR_CAPACITY);
       continue;
     }
-    greedy_faces<1, TN>(s, 0, boundary_count(rec));
+    OriTable<TN> ot;
+    ot.build(s);
+    const float E = (float)(6 * g.p);
+    greedy_faces<1, TN>(s, 0, boundary_count(rec), ot, 1e-4f * E * E);
     write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, err);
   }
 }
@@ -393,7 +454,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
       __syncwarp();
       continue;
     }
-    greedy_faces<32, WN>(s, lane, boundary_count(rec));
+    greedy_faces<32, WN>(s, lane, boundary_count(rec), OriDirect<WN>{&s}, 0.f);
     write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, err);
     __syncwarp();
   }

@@ -29,184 +29,190 @@ SBMT_DEV bool vid_ok(const GridP& g, i64 i, i64 j) {
   return i >= g.vlo[r] && i <= g.vhi[r];
 }
 
-// Walk one segment from its lower end along +x / +y, calling f.cell(c, j)
-// for every cell entered and f.cross(edge, x, y) for every crossing, in order.
-template <class F>
-SBMT_DEV void walk_segment(const GridP& g, const Seg& s, F& f) {
-  const i64 p = g.p, q = g.q, ox = g.ox, oy = g.oy, P6 = 6 * p;
-  const i64 L = seg_len(s);
-  if (seg_dir(s) == 0) {
-    const i64 Y = 6 * q * s.cy - 3 * q;
-    const i64 X0 = 6 * q * s.cx - 3 * q, X1 = X0 + 6 * q * L;
-    const i64 j = strip_of(g, zq(Y));
+// Closed-form walk of one segment.  The walk runs from the segment's lower
+// end along +x / +y; pair k is the k-th cell it visits and crossing k the
+// k-th grid edge it crosses (between pair k and pair k + 1).  Both are O(1)
+// for any k, so a segment can be walked in independent chunks.
+struct SegWalk {
+  i64 X, Y, X0, X1, Y0, Y1, U;  // scaled end coordinates; U = (Y - oy) / 3 for horizontal runs
+  i64 j, j1, c0;                // strip (first strip) and first cell index
+  int dir, s0;                  // vertical: the first strip's slanted crossing lies above the start
+  u32 ncross;
+};
+
+SBMT_DEV i64 strip_ab(const GridP& g, i64 X, i64 j) { return ifloordiv(X - g.ox - 3 * g.p * j, 6 * g.p); }
+
+// slanted crossing of x = X inside strip j: its height, grid edge and the
+// cell above it (the cell below is up(ab, j) = 2 ab)
+SBMT_DEV void strip_slant(const GridP& g, i64 X, i64 j, Zq* ys, i64* ei, i64* ej, int* fam, i64* upper) {
+  const i64 p = g.p, ab = strip_ab(g, X, j), xab = g.ox + 3 * p * (2 * ab + j);
+  if (X - xab < 3 * p) {  // left of the apex: the 60-degree edge from v(ab, j)
+    *ys = zq(g.oy, 3 * p * j + (X - xab));
+    *ei = ab, *ej = j, *fam = 1, *upper = 2 * ab - 1;
+  } else {  // right of it: the 120-degree edge from v(ab + 1, j)
+    *ys = zq(g.oy, 3 * p * j + (xab + 6 * p - X));
+    *ei = ab + 1, *ej = j, *fam = 2, *upper = 2 * ab + 1;
+  }
+}
+
+SBMT_DEV SegWalk seg_setup(const GridP& g, const Seg& s) {
+  SegWalk w;
+  const i64 q = g.q, P6 = 6 * g.p, L = seg_len(s);
+  w.dir = seg_dir(s);
+  if (w.dir == 0) {
+    w.Y = 6 * q * s.cy - 3 * q;
+    w.X0 = 6 * q * s.cx - 3 * q, w.X1 = w.X0 + 6 * q * L;
+    w.j = strip_of(g, zq(w.Y));
     // at height Y the 60-degree lines sit at ox + 6p i + U sqrt3 and the
-    // 120-degree lines at ox + 6p (k + j) - U sqrt3, U = (Y - oy) / 3; the
-    // cell index is the number of lines of both families left of x
-    const i64 U = (Y - oy) / 3;
-    i64 c = zfloordiv(zq(X0 - ox, -U), P6) + zfloordiv(zq(X0 - ox - P6 * j, U), P6);
-    const i64 cend = zfloordiv(zq(X1 - ox, -U), P6) + zfloordiv(zq(X1 - ox - P6 * j, U), P6);
-    if (!f.cell(c, j)) return;
-    while (c < cend) {
-      const i64 i = c >> 1;
-      if (!vid_ok(g, i + 1, j)) return f.fail();
-      u32 e;
-      Zq px;
-      if ((c & 1) == 0) {  // up(i, j) is left through its 120-degree edge from v(i+1, j)
-        e = 3u * vid(g, i + 1, j) + 2u;
-        px = zq(ox + P6 * (i + 1 + j), -U);
-      } else {  // down(i, j) is left through the 60-degree edge from v(i+1, j)
-        e = 3u * vid(g, i + 1, j) + 1u;
-        px = zq(ox + P6 * (i + 1), U);
-      }
-      if (!f.cross(e, px, zq(Y))) return;
-      ++c;
-      if (!f.cell(c, j)) return;
+    // 120-degree lines at ox + 6p (k + j) - U sqrt3; the cell index is the
+    // number of lines of both families left of x
+    w.U = (w.Y - g.oy) / 3;
+    w.c0 = zfloordiv(zq(w.X0 - g.ox, -w.U), P6) + zfloordiv(zq(w.X0 - g.ox - P6 * w.j, w.U), P6);
+    const i64 c1 = zfloordiv(zq(w.X1 - g.ox, -w.U), P6) + zfloordiv(zq(w.X1 - g.ox - P6 * w.j, w.U), P6);
+    w.ncross = (u32)(c1 - w.c0);
+    return w;
+  }
+  w.X = 6 * q * s.cx - 3 * q;
+  w.Y0 = 6 * q * s.cy - 3 * q, w.Y1 = w.Y0 + 6 * q * L;
+  w.j = strip_of(g, zq(w.Y0)), w.j1 = strip_of(g, zq(w.Y1));
+  Zq ys;
+  i64 ei, ej, up;
+  int fam;
+  strip_slant(g, w.X, w.j, &ys, &ei, &ej, &fam, &up);
+  w.s0 = zcmp(ys, zq(w.Y0)) > 0 ? 1 : 0;
+  strip_slant(g, w.X, w.j1, &ys, &ei, &ej, &fam, &up);
+  const int e1 = zcmp(ys, zq(w.Y1)) < 0 ? 1 : 0;
+  // virtual sequence S_j0, H_j0+1, S_j0+1, ..., S_j1; the first and last
+  // slanted crossings count only when they lie inside (Y0, Y1)
+  w.ncross = (u32)(2 * (w.j1 - w.j) + 1 - (1 - w.s0) - (1 - e1));
+  return w;
+}
+
+// cell (c, j) of pair k
+SBMT_DEV void walk_cell(const GridP& g, const SegWalk& w, u32 k, i64* c, i64* j) {
+  if (w.dir == 0) {
+    *c = w.c0 + k, *j = w.j;
+    return;
+  }
+  const i64 v = (i64)k - 1 + (w.s0 ? 0 : 1);  // virtual crossing just before the cell
+  if (v < 0) {
+    *j = w.j, *c = 2 * strip_ab(g, w.X, w.j);
+  } else if ((v & 1) == 0) {
+    Zq ys;
+    i64 ei, ej, up;
+    int fam;
+    *j = w.j + v / 2;
+    strip_slant(g, w.X, *j, &ys, &ei, &ej, &fam, &up);
+    *c = up;
+  } else {
+    *j = w.j + (v + 1) / 2;
+    *c = 2 * strip_ab(g, w.X, *j);
+  }
+}
+
+// grid edge (lattice index of its lower endpoint, family) and point of crossing k
+SBMT_DEV void walk_cross(const GridP& g, const SegWalk& w, u32 k, i64* ei, i64* ej, int* fam, Zq* px, Zq* py) {
+  const i64 P6 = 6 * g.p;
+  if (w.dir == 0) {
+    const i64 c = w.c0 + k, i = c >> 1;
+    *ei = i + 1, *ej = w.j, *py = zq(w.Y);
+    if ((c & 1) == 0) {  // up(i, j) is left through its 120-degree edge from v(i+1, j)
+      *fam = 2, *px = zq(g.ox + P6 * (i + 1 + w.j), -w.U);
+    } else {  // down(i, j) through the 60-degree edge from v(i+1, j)
+      *fam = 1, *px = zq(g.ox + P6 * (i + 1), w.U);
     }
     return;
   }
-  const i64 X = 6 * q * s.cx - 3 * q;
-  const i64 Y0 = 6 * q * s.cy - 3 * q, Y1 = Y0 + 6 * q * L;
-  i64 j = strip_of(g, zq(Y0));
-  const i64 U0 = (Y0 - oy) / 3;
-  i64 c = zfloordiv(zq(X - ox, -U0), P6) + zfloordiv(zq(X - ox - P6 * j, U0), P6);
-  if (!f.cell(c, j)) return;
-  while (true) {
-    // at the bottom of strip j the line x = X is inside up(ab, j); it leaves
-    // that cell through the 60-degree edge from v(ab, j) left of the apex,
-    // or the 120-degree edge from v(ab+1, j) right of it
-    const i64 ab = ifloordiv(X - ox - 3 * p * j, P6);
-    const i64 xab = ox + 3 * p * (2 * ab + j);
-    Zq ys;
-    u32 e;
-    i64 upper;
-    if (X - xab < 3 * p) {
-      if (!vid_ok(g, ab, j)) return f.fail();
-      ys = zq(oy, 3 * p * j + (X - xab));
-      e = 3u * vid(g, ab, j) + 1u;
-      upper = 2 * ab - 1;
+  const i64 v = (i64)k + (w.s0 ? 0 : 1);
+  *px = zq(w.X);
+  if ((v & 1) == 0) {
+    i64 up;
+    strip_slant(g, w.X, w.j + v / 2, py, ei, ej, fam, &up);
+  } else {
+    const i64 jj = w.j + (v + 1) / 2;  // the horizontal edge on top of strip jj - 1
+    *ej = jj, *ei = strip_ab(g, w.X, jj), *fam = 0, *py = zq(g.oy, 3 * g.p * jj);
+  }
+}
+
+__global__ void k_seg_count(GridP g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs) {
+  const u32 n = min(*nseg, cap);
+  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x)
+    npairs[s] = s < n ? seg_setup(g, segs[s]).ncross + 1u : 0u;
+}
+
+constexpr u32 CH = 32;  // pairs per thread in the chunked walks
+
+// Chunked walk over the global pair index range.  Count pass (EMIT false):
+// histogram of pairs per cell bucket and of crossings per event bucket.
+// Emit pass: each crossing's event at its fixed index (segment event base
+// + k), its index into the event bucket, each pair into its cell bucket.
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u32* pbase, u32 cap, u32 NP,
+                                              u32* pbk, u32* ebk, Pair* pairs, Event* ev, u32* eidx, u32* err) {
+  const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  const u64 p0 = t * CH;
+  if (p0 >= NP) return;
+  const u32 p1 = (u32)((p0 + CH < (u64)NP) ? p0 + CH : (u64)NP);
+  // the segment holding pair p0: last s with pbase[s] <= p0
+  u32 lo = 0, hi = cap;
+  while (lo < hi) {
+    const u32 mid = (lo + hi + 1) >> 1;
+    if (pbase[mid] <= (u32)p0) lo = mid;
+    else hi = mid - 1;
+  }
+  u32 s = lo, k = (u32)p0 - pbase[s];
+  SegWalk w = seg_setup(g, segs[s]);
+  u32 pb = NONE, pn = 0, eb = NONE, en = 0;
+  for (u32 p = (u32)p0; p < p1; ++p, ++k) {
+    if (k > w.ncross) {
+      ++s, k = 0;
+      w = seg_setup(g, segs[s]);
+    }
+    i64 c, j;
+    walk_cell(g, w, k, &c, &j);
+    if (!cell_in(g, c, j)) {
+      atomicOr(err, ERR_TRAVERSAL);
+      return;
+    }
+    const u32 cid = cell_id(g, c, j);
+    const u32 ebase = pbase[s] - s;
+    if (k < w.ncross) {
+      i64 ei, ej;
+      int fam;
+      Zq px, py;
+      walk_cross(g, w, k, &ei, &ej, &fam, &px, &py);
+      if (!vid_ok(g, ei, ej)) {
+        atomicOr(err, ERR_TRAVERSAL);
+        return;
+      }
+      const u32 e = 3u * vid(g, ei, ej) + (u32)fam;
+      if (EMIT) {
+        ev[ebase + k] = Event{e, s, 0u, 0u, (int)px.a, (int)px.b, (int)py.a, (int)py.b};
+        eidx[atomicAdd(ebk + (e >> EB_LOG), 1u)] = ebase + k;
+      } else {
+        const u32 b = e >> EB_LOG;
+        if (b != eb) {
+          if (en) atomicAdd(ebk + eb, en);
+          eb = b, en = 0;
+        }
+        ++en;
+      }
+    }
+    if (EMIT) {
+      pairs[atomicAdd(pbk + (cid >> CB_LOG), 1u)] =
+          Pair{cid, s, k > 0 ? ebase + k - 1 : NONE, k < w.ncross ? ebase + k : NONE};
     } else {
-      if (!vid_ok(g, ab + 1, j)) return f.fail();
-      ys = zq(oy, 3 * p * j + (xab + P6 - X));
-      e = 3u * vid(g, ab + 1, j) + 2u;
-      upper = 2 * ab + 1;
+      const u32 b = cid >> CB_LOG;
+      if (b != pb) {
+        if (pn) atomicAdd(pbk + pb, pn);
+        pb = b, pn = 0;
+      }
+      ++pn;
     }
-    if (zcmp(ys, zq(Y0)) > 0) {
-      if (zcmp(ys, zq(Y1)) >= 0) return;
-      if (c != 2 * ab) return f.fail();
-      if (!f.cross(e, zq(X), ys)) return;
-      c = upper;
-      if (!f.cell(c, j)) return;
-    } else if (c != upper) {
-      return f.fail();
-    }
-    // the horizontal edge on top of strip j, from v(ih, j+1)
-    const Zq yt = zq(oy, 3 * p * (j + 1));
-    if (zcmp(yt, zq(Y1)) >= 0) return;
-    const i64 ih = ifloordiv(X - ox - 3 * p * (j + 1), P6);
-    if (c != 2 * ih + 1 || !vid_ok(g, ih, j + 1)) return f.fail();
-    e = 3u * vid(g, ih, j + 1) + 0u;
-    if (!f.cross(e, zq(X), yt)) return;
-    ++j;
-    c = 2 * ih;
-    if (!f.cell(c, j)) return;
   }
-}
-
-struct CountF {
-  const GridP* g;
-  u32 *pcnt, *ecnt, *err;
-  u32 pb, pn, eb, en;
-  unsigned long long np, ne;
-  SBMT_DEV bool cell(i64 c, i64 j) {
-    if (!cell_in(*g, c, j)) {
-      fail();
-      return false;
-    }
-    const u32 b = cell_id(*g, c, j) >> CB_LOG;
-    if (b != pb) {
-      if (pn) atomicAdd(pcnt + pb, pn);
-      pb = b, pn = 0;
-    }
-    ++pn, ++np;
-    return true;
-  }
-  SBMT_DEV bool cross(u32 e, Zq, Zq) {
-    const u32 b = e >> EB_LOG;
-    if (b != eb) {
-      if (en) atomicAdd(ecnt + eb, en);
-      eb = b, en = 0;
-    }
-    ++en, ++ne;
-    return true;
-  }
-  SBMT_DEV void fail() { atomicOr(err, ERR_TRAVERSAL); }
-  SBMT_DEV void flush() {
-    if (pn) atomicAdd(pcnt + pb, pn);
-    if (en) atomicAdd(ecnt + eb, en);
-  }
-};
-
-struct EmitF {
-  const GridP* g;
-  u32 *pcur, *ecur, *err;
-  Pair* pairs;
-  Event* ev;
-  u32 seg, cur, ev_in;
-  SBMT_DEV bool cell(i64 c, i64 j) {
-    if (!cell_in(*g, c, j)) {
-      fail();
-      return false;
-    }
-    cur = cell_id(*g, c, j);
-    return true;
-  }
-  SBMT_DEV bool cross(u32 e, Zq px, Zq py) {
-    const u32 slot = atomicAdd(ecur + (e >> EB_LOG), 1u);
-    ev[slot] = Event{e, seg, 0u, 0u, (int)px.a, (int)px.b, (int)py.a, (int)py.b};
-    const u32 ps = atomicAdd(pcur + (cur >> CB_LOG), 1u);
-    pairs[ps] = Pair{cur, seg, ev_in, slot};
-    ev_in = slot;
-    return true;
-  }
-  SBMT_DEV void fail() {
-    atomicOr(err, ERR_TRAVERSAL);
-    cur = NONE;
-  }
-  SBMT_DEV void finish() {
-    if (cur == NONE) return;
-    const u32 ps = atomicAdd(pcur + (cur >> CB_LOG), 1u);
-    pairs[ps] = Pair{cur, seg, ev_in, NONE};
-  }
-};
-
-__global__ void k_traverse_count(GridP g, const Seg* segs, const u32* nseg, u32 cap, u32* pcnt, u32* ecnt,
-                                 unsigned long long* totals, u32* err) {
-  const u32 n = min(*nseg, cap);
-  unsigned long long np = 0, ne = 0;
-  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    CountF f{&g, pcnt, ecnt, err, NONE, 0u, NONE, 0u, 0ull, 0ull};
-    walk_segment(g, segs[s], f);
-    f.flush();
-    np += f.np, ne += f.ne;
-  }
-  // warp-reduce the totals before the global atomics
-  for (int o = 16; o; o >>= 1) {
-    np += __shfl_down_sync(0xffffffffu, np, o);
-    ne += __shfl_down_sync(0xffffffffu, ne, o);
-  }
-  if ((threadIdx.x & 31) == 0 && (np | ne)) {
-    atomicAdd(totals + 0, np);
-    atomicAdd(totals + 1, ne);
-  }
-}
-
-__global__ void k_traverse_emit(GridP g, const Seg* segs, const u32* nseg, u32 cap, u32* pcur, u32* ecur,
-                                Pair* pairs, Event* ev, u32* err) {
-  const u32 n = min(*nseg, cap);
-  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    EmitF f{&g, pcur, ecur, err, pairs, ev, s, NONE, NONE};
-    walk_segment(g, segs[s], f);
-    f.finish();
+  if (!EMIT) {
+    if (pn) atomicAdd(pbk + pb, pn);
+    if (en) atomicAdd(ebk + eb, en);
   }
 }
 
@@ -219,8 +225,8 @@ SBMT_DEV Zq event_t(const Event& e) {
 // Events are counting-sorted by edge in shared memory; an event's vertex id
 // is NVg + (events on lower edge ids) + (events on its edge nearer the
 // edge's lower endpoint), compared exactly.
-__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, u32* elist, const u32* eoff, u32 NVg,
-                                              double* xy) {
+__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
+                                              u32 NVg, double* xy) {
   constexpr int NEB = 1 << EB_LOG;
   __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
   __shared__ u32 s_sh[8];
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, u32* elist, co
   const u32 e0 = blockIdx.x << EB_LOG;
   for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
   __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[ev[lo + i].edge - e0], 1u);
+  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[ev[eidx[lo + i]].edge - e0], 1u);
   __syncthreads();
   {
     constexpr int PER = NEB / 256;
@@ -242,22 +248,23 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, u32* elist, co
   }
   __syncthreads();
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-    const u32 slot = atomicAdd(&s_cur[ev[lo + i].edge - e0], 1u);
-    elist[lo + slot] = i;
+    const u32 slot = atomicAdd(&s_cur[ev[eidx[lo + i]].edge - e0], 1u);
+    elist[lo + slot] = eidx[lo + i];
   }
   __syncthreads();
   const double invS = 1.0 / (double)g.S;
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-    const Event ei = ev[lo + i];
+    const u32 me = eidx[lo + i];
+    const Event ei = ev[me];
     const Zq ti = event_t(ei);
     const u32 k = ei.edge - e0, first = s_off[k], cnt = s_cnt[k];
     u32 rank = first;
     for (u32 q = 0; q < cnt; ++q) {
       const u32 j = elist[lo + first + q];
-      if (j != i && zcmp(event_t(ev[lo + j]), ti) < 0) ++rank;
+      if (j != me && zcmp(event_t(ev[j]), ti) < 0) ++rank;
     }
     const u32 gid = NVg + lo + rank;
-    ev[lo + i].gid = gid;
+    ev[me].gid = gid;
     double2 v;
     v.x = zdouble(zq(ei.xa, ei.xb)) * invS;
     v.y = zdouble(zq(ei.ya, ei.yb)) * invS;
@@ -267,24 +274,26 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, u32* elist, co
 
 }  // namespace
 
-void launch_traverse_count(const GridP& g, const Seg* segs, const u32* nseg, u32 seg_cap, u32* pcnt, u32* ecnt,
-                           unsigned long long* totals, u32* err, cudaStream_t st) {
-  const int blk = 256;
-  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((seg_cap + blk - 1) / blk, 152u * 64u));
-  k_traverse_count<<<grd, blk, 0, st>>>(g, segs, nseg, seg_cap, pcnt, ecnt, totals, err);
+void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st) {
+  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
+  k_seg_count<<<grd, 256, 0, st>>>(g, segs, nseg, cap, npairs);
 }
 
-void launch_traverse_emit(const GridP& g, const Seg* segs, const u32* nseg, u32 seg_cap, u32* pcur, u32* ecur,
-                          Pair* pairs, Event* events, u32* err, cudaStream_t st) {
-  const int blk = 256;
-  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((seg_cap + blk - 1) / blk, 152u * 64u));
-  k_traverse_emit<<<grd, blk, 0, st>>>(g, segs, nseg, seg_cap, pcur, ecur, pairs, events, err);
+void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, u32 cap, u32 NP, u32* pbk, u32* ebk,
+                 Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st) {
+  const u64 threads = (NP + CH - 1) / CH;
+  if (threads == 0) return;
+  const unsigned grd = (unsigned)((threads + 255) / 256);
+  if (emit)
+    k_walk<true><<<grd, 256, 0, st>>>(g, segs, pbase, cap, NP, pbk, ebk, pairs, events, eidx, err);
+  else
+    k_walk<false><<<grd, 256, 0, st>>>(g, segs, pbase, cap, NP, pbk, ebk, pairs, events, eidx, err);
 }
 
-void launch_rank_events(const GridP& g, Event* events, u32* elist, const u32* eoff, u32 nbe, u32 NVg, double* xy,
-                        cudaStream_t st) {
+void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
+                        u32 NVg, double* xy, cudaStream_t st) {
   if (nbe == 0) return;
-  k_rank<<<nbe, 256, 0, st>>>(g, events, elist, eoff, NVg, xy);
+  k_rank<<<nbe, 256, 0, st>>>(g, events, eidx, elist, eoff, NVg, xy);
 }
 
 }  // namespace sbmt

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <string>
@@ -135,10 +136,23 @@ struct MeshRec {
 }  // namespace
 
 // kernels of the hot path, in launch order (for the per-kernel timing)
-enum { KN_CORNER, KN_SEG, KN_TCOUNT, KN_SCAN, KN_TEMIT, KN_RANK, KN_CLASSIFY, KN_EMIT, KN_TIERG, KN_XY, KN_COUNT };
-const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_traverse_count", "k_scan",
-                                            "k_traverse_emit", "k_rank", "k_classify", "k_emit", "k_tierg",
-                                            "k_lattice_xy"};
+enum {
+  KN_CORNER,
+  KN_SEG,
+  KN_TCOUNT,
+  KN_SCAN,
+  KN_TEMIT,
+  KN_RANK,
+  KN_CLASSIFY,
+  KN_EMIT,
+  KN_TIERT,
+  KN_TIERG,
+  KN_XY,
+  KN_COUNT
+};
+const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_walk_count", "k_scan",
+                                            "k_walk_emit", "k_rank", "k_classify", "k_emit", "k_tiert",
+                                            "k_tierg", "k_lattice_xy"};
 
 struct sbmt_ctx {
   int device = 0;
@@ -157,6 +171,20 @@ struct sbmt_ctx {
   std::vector<Mark> pending;
   double prof_ms[KN_COUNT] = {};
   int64_t prof_n[KN_COUNT] = {};
+  // grid tables per (W, H, h, origin), kept on the device
+  struct TableEntry {
+    Tables host;
+    i64* dev = nullptr;
+    uint64_t last_use = 0;
+  };
+  std::map<std::array<i64, 6>, TableEntry> tables;
+  uint64_t tick = 0;
+  // per-call scratch: bump allocation in stream-ordered chunks
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t chunk_used = 0, call_bytes = 0;
+  // pinned slots for the per-mesh status words
+  std::vector<u32*> pinned_slabs;
+  std::vector<u32*> pinned_free;
 };
 
 namespace {
@@ -206,6 +234,96 @@ struct ProfScope {
     call;                        \
   } while (0)
 
+// scratch arena: every call bumps through the context's chunks; a call that
+// needed more than one chunk leaves a single chunk of its total size for the
+// next call (frees and allocations are ordered on the context stream)
+template <typename T>
+int aalloc(sbmt_ctx* ctx, T** p, size_t count) {
+  const size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~(size_t)255;
+  ctx->call_bytes += bytes;
+  if (ctx->chunks.empty() || ctx->chunk_used + bytes > ctx->chunks.back().second) {
+    const size_t want = std::max<size_t>(bytes, ctx->chunks.empty() ? ((size_t)64 << 20) : 2 * ctx->chunks.back().second);
+    void* v = nullptr;
+    cudaError_t e = cudaMallocAsync(&v, want, ctx->stream);
+    if (e != cudaSuccess) return fail(SBMT_ENOMEM, "scratch chunk of %zu bytes: %s", want, cudaGetErrorString(e));
+    ctx->chunks.push_back({(char*)v, want});
+    ctx->chunk_used = 0;
+  }
+  *p = (T*)(ctx->chunks.back().first + ctx->chunk_used);
+  ctx->chunk_used += bytes;
+  return SBMT_OK;
+}
+void arena_begin(sbmt_ctx* ctx) {
+  ctx->call_bytes = 0;
+  ctx->chunk_used = 0;
+  // keep only the first chunk's position: reuse from the start
+  while (ctx->chunks.size() > 1) {
+    cudaFreeAsync(ctx->chunks.back().first, ctx->stream);
+    ctx->chunks.pop_back();
+  }
+}
+void arena_end(sbmt_ctx* ctx) {
+  if (ctx->chunks.size() <= 1) return;
+  const size_t total = ctx->call_bytes + ((size_t)16 << 20);
+  for (auto& c : ctx->chunks) cudaFreeAsync(c.first, ctx->stream);
+  ctx->chunks.clear();
+  void* v = nullptr;
+  if (cudaMallocAsync(&v, total, ctx->stream) == cudaSuccess) ctx->chunks.push_back({(char*)v, total});
+}
+
+u32* pinned_slot(sbmt_ctx* ctx) {
+  if (ctx->pinned_free.empty()) {
+    u32* slab = nullptr;
+    if (cudaMallocHost(&slab, 1024 * 8 * sizeof(u32)) != cudaSuccess) return nullptr;
+    ctx->pinned_slabs.push_back(slab);
+    for (int k = 1023; k >= 0; --k) ctx->pinned_free.push_back(slab + 8 * k);
+  }
+  u32* p = ctx->pinned_free.back();
+  ctx->pinned_free.pop_back();
+  std::memset(p, 0, 8 * sizeof(u32));
+  return p;
+}
+
+// grid tables for one configuration, built once and kept on the device
+int get_tables(sbmt_ctx* ctx, const GridP& g, const Tables** host, const i64** dev) {
+  const std::array<i64, 6> key{g.W, g.H, g.p, g.q, g.ox, g.oy};
+  auto it = ctx->tables.find(key);
+  if (it == ctx->tables.end()) {
+    if (ctx->tables.size() >= 64) {  // evict the least recently used entry
+      auto old = ctx->tables.begin();
+      for (auto jt = ctx->tables.begin(); jt != ctx->tables.end(); ++jt)
+        if (jt->second.last_use < old->second.last_use) old = jt;
+      cudaFreeAsync(old->second.dev, ctx->stream);
+      ctx->tables.erase(old);
+    }
+    sbmt_ctx::TableEntry te;
+    int rc = build_tables(g, te.host);
+    if (rc) return rc;
+    const Tables& tb = te.host;
+    const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
+    std::vector<i64> all;
+    all.insert(all.end(), tb.clo.begin(), tb.clo.end());
+    all.insert(all.end(), tb.chi.begin(), tb.chi.end());
+    all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
+    all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
+    all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
+    all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
+    const size_t nl = all.size();
+    all.resize(nl + nrows);
+    std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
+    if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), ctx->stream) != cudaSuccess)
+      return fail(SBMT_ENOMEM, "table allocation");
+    if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, ctx->stream) ||
+        cudaStreamSynchronize(ctx->stream))
+      return fail(SBMT_ECUDA, "table upload");
+    it = ctx->tables.emplace(key, std::move(te)).first;
+  }
+  it->second.last_use = ++ctx->tick;
+  *host = &it->second.host;
+  *dev = it->second.dev;
+  return SBMT_OK;
+}
+
 template <typename T>
 int dalloc(sbmt_ctx* ctx, T** p, size_t count, std::vector<void*>& track) {
   void* v = nullptr;
@@ -226,8 +344,8 @@ void destroy_mesh(sbmt_ctx* ctx, MeshRec* m) {
   if (m->done) cudaEventSynchronize(m->done);
   free_list(ctx, m->scratch);
   if (m->out_block) cudaFreeAsync(m->out_block, ctx->stream);
-  if (m->done) cudaEventDestroy(m->done);
-  if (m->h_info) cudaFreeHost(m->h_info);
+  if (m->done) ctx->ev_pool.push_back(m->done);
+  if (m->h_info) ctx->pinned_free.push_back(m->h_info);
   delete m;
 }
 
@@ -258,21 +376,24 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   g.W = img->width, g.H = img->height;
   g.p = pr->h_num, g.q = pr->h_den, g.S = 6 * g.q;
   g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
-  Tables tb;
-  if ((rc = build_tables(g, tb))) return rc;
+  const Tables* tbp;
+  const i64* dt;
+  if ((rc = get_tables(ctx, g, &tbp, &dt))) return rc;
+  const Tables& tb = *tbp;
   if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
     return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
   MeshRec* m = new MeshRec();
   m->W = g.W;
   m->keep = (pr->flags & SBMT_KEEP_STAGES) != 0;
-  std::vector<void*> tmp;  // scratch freed at the end of the call (unless kept)
+  std::vector<void*> tmp;  // device memory freed at the end of the call
+  arena_begin(ctx);
   auto bail = [&](int code) {
     free_list(ctx, tmp);
+    arena_end(ctx);
     destroy_mesh(ctx, m);
     return code;
   };
-  if (cudaMallocHost(&m->h_info, 8 * sizeof(u32)) != cudaSuccess) return bail(fail(SBMT_ENOMEM, "pinned info"));
-  std::memset(m->h_info, 0, 8 * sizeof(u32));
+  if (!(m->h_info = pinned_slot(ctx))) return bail(fail(SBMT_ENOMEM, "pinned info"));
   // image on the device
   const unsigned char* dimg;
   i64 pitch;
@@ -282,30 +403,12 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   } else {
     unsigned char* d;
     pitch = (i64)img->width * img->dtype;
-    if ((rc = dalloc(ctx, &d, (size_t)pitch * img->height, tmp))) return bail(rc);
+    if ((rc = aalloc(ctx, &d, (size_t)pitch * img->height))) return bail(rc);
     if (cudaMemcpy2DAsync(d, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
       return bail(fail(SBMT_ECUDA, "image upload"));
     dimg = d;
   }
-  // tables
   const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
-  i64* dt;
-  if ((rc = dalloc(ctx, &dt, 3 * nrows + 3 * nvr + nrows, tmp))) return bail(rc);
-  {
-    std::vector<i64> all;
-    all.insert(all.end(), tb.clo.begin(), tb.clo.end());
-    all.insert(all.end(), tb.chi.begin(), tb.chi.end());
-    all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
-    all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
-    all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
-    all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
-    const size_t nl = all.size();
-    all.resize(nl + nrows);
-    std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
-    if (cudaMemcpyAsync(dt, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, st))
-      return bail(fail(SBMT_ECUDA, "tables upload"));
-    if (cudaStreamSynchronize(st)) return bail(fail(SBMT_ECUDA, "tables upload sync"));
-  }
   g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
   g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
   g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
@@ -314,17 +417,18 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
 
   // counters: [0] nvtx (u64), [1] totals pairs, [2] totals events, then u32s
   unsigned long long* cnt64;
-  if ((rc = dalloc(ctx, &cnt64, 8, tmp))) return bail(rc);
+  if ((rc = aalloc(ctx, &cnt64, 8))) return bail(rc);
   u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, ngtri, nwlist
   CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
   u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3, *nwlist = cnt32 + 4;
+  u32* ntlist = cnt32 + 5;
 
   // K1a
   const int W = g.W, H = g.H;
   const int wpr = (W + 1 + 31) / 32, wpc = (H + 1 + 31) / 32;
   u32 *vrow, *vcol;
-  if ((rc = dalloc(ctx, &vrow, (size_t)wpr * (H + 1), tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &vcol, (size_t)wpc * (W + 1), tmp))) return bail(rc);
+  if ((rc = aalloc(ctx, &vrow, (size_t)wpr * (H + 1)))) return bail(rc);
+  if ((rc = aalloc(ctx, &vcol, (size_t)wpc * (W + 1)))) return bail(rc);
   TRACE(KN_CORNER, launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st));
   unsigned long long h64[4];
   CK(cudaMemcpyAsync(h64, cnt64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -333,64 +437,64 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   // K1b: every vertex starts at most two runs (+x and +y)
   const u32 seg_cap = (u32)std::max<u64>(2 * NC, 1);
   Seg* segs;
-  if ((rc = dalloc(ctx, &segs, seg_cap, tmp))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &segs, seg_cap, m->scratch) : aalloc(ctx, &segs, seg_cap))) return bail(rc);
   TRACE(KN_SEG, launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st));
-  // K2 count
+  // K2: pairs per segment in closed form and their scan -> fixed pair and
+  // event indices of every segment
   const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
   const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
-  u32 *pcnt, *ecnt;
-  if ((rc = dalloc(ctx, &pcnt, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &ecnt, nbe + 1, tmp))) return bail(rc);
-  CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
-  CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
-  TRACE(KN_TCOUNT, launch_traverse_count(g, segs, nseg, seg_cap, pcnt, ecnt, cnt64 + 1, err, st));
-  CK(cudaMemcpyAsync(h64, cnt64, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  u32 *npairs, *pbase, *sscr;
+  const size_t scr_words = std::max({scan_scratch_words(seg_cap), scan_scratch_words(nbc), scan_scratch_words(nbe)});
+  if ((rc = aalloc(ctx, &npairs, seg_cap))) return bail(rc);
+  if ((rc = aalloc(ctx, &pbase, (size_t)seg_cap + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &sscr, scr_words + 1))) return bail(rc);
+  TRACE(KN_TCOUNT, launch_seg_count(g, segs, nseg, seg_cap, npairs, st));
+  TRACE(KN_SCAN, launch_scan(npairs, 1, pbase, seg_cap, sscr, st));
   u32 h32[4];
   CK(cudaMemcpyAsync(h32, cnt32, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h32 + 3, pbase + seg_cap, sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (h32[1]) return bail(fail(SBMT_EINTERNAL, "device check failed during traversal (0x%x)", h32[1]));
+  if (h32[1]) return bail(fail(SBMT_EINTERNAL, "device check failed during extraction (0x%x)", h32[1]));
   const u32 nsegs = h32[0];
   if (nsegs > seg_cap) return bail(fail(SBMT_EINTERNAL, "segment count %u above bound %u", nsegs, seg_cap));
-  const u64 NP = h64[1], NE = h64[2];
+  const u64 NP = h32[3], NE = NP - nsegs;
   const u64 NVg = (u64)tb.nverts;
   const u64 V = NVg + NE + NC, T = (u64)tb.ncells + 2 * NC + 2 * NE;
-  if (V >= (1ull << 31) || T >= (1ull << 31) || NP >= (1ull << 32))
+  if (V >= (1ull << 31) || T >= (1ull << 31) || NP >= (1ull << 31))
     return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T));
-  // buckets
-  u32 *poff, *eoff, *pcur, *ecur;
-  if ((rc = dalloc(ctx, &poff, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &eoff, nbe + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &pcur, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &ecur, nbe + 1, tmp))) return bail(rc);
-  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, st));
-  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, st));
+  // buckets: pairs by cell id, events by grid-edge id
+  u32 *pcnt, *ecnt, *poff, *eoff, *pcur, *ecur;
+  if ((rc = aalloc(ctx, &pcnt, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &ecnt, nbe + 1))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &poff, nbc + 1, m->scratch) : aalloc(ctx, &poff, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &eoff, nbe + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &pcur, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &ecur, nbe + 1))) return bail(rc);
+  CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
+  CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
+  TRACE(KN_TCOUNT, launch_walk(false, g, segs, pbase, seg_cap, (u32)NP, pcnt, ecnt, nullptr, nullptr, nullptr, err, st));
+  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
+  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
   CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist, *wlist, *elist;
-  std::vector<void*>& keep = m->keep ? m->scratch : tmp;
-  if ((rc = dalloc(ctx, &pairs, NP, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &sorted, NP, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &ev, NE, keep))) return bail(rc);
-  if ((rc = dalloc(ctx, &recs, NP, keep))) return bail(rc);
-  if ((rc = dalloc(ctx, &bstat, 4 * (size_t)nbc + 4, keep))) return bail(rc);
-  if ((rc = dalloc(ctx, &extra_scan, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &chain_scan, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &cut_scan, nbc + 1, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &glist, NP, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &wlist, NP, tmp))) return bail(rc);
-  if ((rc = dalloc(ctx, &elist, NE, tmp))) return bail(rc);
-  if (m->keep) {
-    // keep the segments and bucket offsets too: move them to the mesh
-    for (auto it = tmp.begin(); it != tmp.end(); ++it)
-      if (*it == (void*)segs || *it == (void*)poff) {
-        m->scratch.push_back(*it);
-        *it = nullptr;
-      }
-    tmp.erase(std::remove(tmp.begin(), tmp.end(), nullptr), tmp.end());
-  }
+  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist, *wlist, *elist, *eidx, *tlist;
+
+  if ((rc = aalloc(ctx, &pairs, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &sorted, NP))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &ev, NE, m->scratch) : aalloc(ctx, &ev, NE))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &recs, NP, m->scratch) : aalloc(ctx, &recs, NP))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &bstat, 4 * (size_t)nbc + 4, m->scratch) : aalloc(ctx, &bstat, 4 * (size_t)nbc + 4))) return bail(rc);
+  if ((rc = aalloc(ctx, &extra_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &chain_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &cut_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &glist, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &wlist, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &tlist, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &elist, NE))) return bail(rc);
+  if ((rc = aalloc(ctx, &eidx, NE))) return bail(rc);
   // outputs
   const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
   const size_t off_tri = (bxy + 255) & ~(size_t)255, off_lab = (off_tri + btri + 255) & ~(size_t)255;
@@ -404,14 +508,16 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
-  TRACE(KN_TEMIT, launch_traverse_emit(g, segs, nseg, seg_cap, pcur, ecur, pairs, ev, err, st));
-  TRACE(KN_RANK, launch_rank_events(g, ev, elist, eoff, nbe, (u32)NVg, m->xy, st));
+  TRACE(KN_TEMIT, launch_walk(true, g, segs, pbase, seg_cap, (u32)NP, pcur, ecur, pairs, ev, eidx, err, st));
+  TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
   TRACE(KN_CLASSIFY, launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 1, 4, extra_scan, nbc, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 2, 4, chain_scan, nbc, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 0, 4, cut_scan, nbc, st));
-  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
-              (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, err, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 1, 4, extra_scan, nbc, sscr, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 2, 4, chain_scan, nbc, sscr, st));
+  TRACE(KN_SCAN, launch_scan(bstat + 0, 4, cut_scan, nbc, sscr, st));
+  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
+                             (u32)NE, m->tri, m->label, m->code, tlist, ntlist, glist, nglist, ngtri, st));
+  TRACE(KN_TIERT, launch_tiert(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, tlist, ntlist, m->tri, m->label,
+                               m->code, m->xy, err, st));
   TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, wlist, nwlist,
                                m->tri, m->label, m->code, m->xy, err, st));
   TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
@@ -425,8 +531,8 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
     m->poff = poff, m->nbc = nbc, m->np = (u32)NP;
   }
   free_list(ctx, tmp);
-  if (cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming) != cudaSuccess)
-    return bail(fail(SBMT_ECUDA, "event create"));
+  arena_end(ctx);
+  if (!(m->done = pool_event(ctx))) return bail(fail(SBMT_ECUDA, "event create"));
   CK(cudaEventRecord(m->done, st));
   m->id = ctx->next++;
   ctx->meshes[m->id] = m;
@@ -542,6 +648,10 @@ int mesh_destroy(sbmt_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     prof_collect(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto& c : ctx->chunks) cudaFreeAsync(c.first, ctx->stream);
+    for (auto& kv : ctx->tables) cudaFreeAsync(kv.second.dev, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    for (u32* slab : ctx->pinned_slabs) cudaFreeHost(slab);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;

@@ -44,30 +44,40 @@ SBMT_HD Zq operator-(Zq x, Zq y) { return Zq{x.a - y.a, x.b - y.b}; }
 SBMT_HD Zq operator*(Zq x, Zq y) { return Zq{x.a * y.a + 3 * x.b * y.b, x.a * y.b + x.b * y.a}; }
 // sign of a + b sqrt3: when a and b disagree in sign compare a^2 with 3 b^2.
 // The components of a cell-local determinant can reach ~1e15 (points on
-// rational pixel lines against lattice rows at y ~ 3pj sqrt3), so the squares
-// are taken in 128 bits.
+// rational pixel lines against lattice rows at y ~ 3pj sqrt3), so large
+// squares are taken in 128 bits; below 1.7e9 they fit in 64.
 SBMT_HD int zsign(Zq v) {
   if (v.b == 0) return (v.a > 0) - (v.a < 0);
   if (v.a == 0) return (v.b > 0) - (v.b < 0);
   if ((v.a > 0) == (v.b > 0)) return v.a > 0 ? 1 : -1;
-  const __int128 l = (__int128)v.a * v.a, r = 3 * ((__int128)v.b * v.b);
-  if (v.a > 0) return l > r ? 1 : -1;
-  return r > l ? 1 : -1;
+  const i64 aa = v.a < 0 ? -v.a : v.a, bb = v.b < 0 ? -v.b : v.b;
+  bool a_wins;
+  if (aa < 1700000000ll && bb < 1700000000ll) {
+    a_wins = aa * aa > 3 * (bb * bb);
+  } else {
+    const __int128 l = (__int128)aa * aa, r = 3 * ((__int128)bb * bb);
+    a_wins = l > r;
+  }
+  return a_wins ? (v.a > 0 ? 1 : -1) : (v.b > 0 ? 1 : -1);
 }
 SBMT_HD int zcmp(Zq x, Zq y) { return zsign(x - y); }
 SBMT_HD double zdouble(Zq v) { return (double)v.a + (double)v.b * 1.7320508075688772935; }
 
-// floor(v / d) for d > 0, exact
+// floor(a / d) for d > 0: a float estimate corrected exactly (|a / d| < 2^30)
+SBMT_HD i64 ifloordiv(i64 a, i64 d) {
+  i64 k = (i64)floorf((float)a / (float)d);
+  while (k * d > a) --k;
+  while ((k + 1) * d <= a) ++k;
+  return k;
+}
+
+// floor(v / d) for d > 0, exact: a float estimate of a + b sqrt3, then the
+// exact sign of v - k d decides
 SBMT_HD i64 zfloordiv(Zq v, i64 d) {
-  i64 k = (i64)floor(zdouble(v) / (double)d);
+  i64 k = (i64)floorf(((float)v.a + (float)v.b * 1.7320508f) / (float)d);
   while (zsign(v - zq(k * d)) < 0) --k;
   while (zsign(v - zq((k + 1) * d)) >= 0) ++k;
   return k;
-}
-SBMT_HD i64 ifloordiv(i64 a, i64 d) {  // d > 0
-  i64 q = a / d;
-  if ((a % d != 0) && (a < 0)) --q;
-  return q;
 }
 
 // 2-D point with exact coordinates (K-local points fit in 32 bits)
@@ -187,7 +197,7 @@ SBMT_DEV Pq corner_pt(const GridP& g, i64 cx, i64 cy) {
 // strip row holding a point of height y (never on a grid line)
 SBMT_HD i64 strip_of(const GridP& g, Zq y) {
   // y_j = oy + 3 p j sqrt3
-  i64 j = (i64)floor((zdouble(y) - (double)g.oy) / (3.0 * (double)g.p * 1.7320508075688772935));
+  i64 j = (i64)floorf(((float)(y.a - g.oy) + (float)y.b * 1.7320508f) / (3.0f * (float)g.p * 1.7320508f));
   while (zcmp(zq(g.oy, 3 * g.p * j), y) > 0) --j;
   while (zcmp(zq(g.oy, 3 * g.p * (j + 1)), y) <= 0) ++j;
   return j;

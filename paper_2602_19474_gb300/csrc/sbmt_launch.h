@@ -16,19 +16,22 @@ void launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, i
 void launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
                      const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, cudaStream_t st);
 
-// K2 count pass: per segment, the cells it visits and the grid edges it
-// crosses, histogrammed into cell buckets and event buckets.
-void launch_traverse_count(const GridP& g, const Seg* segs, const u32* nseg, u32 seg_cap, u32* pcnt, u32* ecnt,
-                           unsigned long long* totals, u32* err, cudaStream_t st);
+// K2: number of pairs (cells visited = crossings + 1) of every segment, in
+// closed form; slots beyond the segment count get 0.
+void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
 
-// K2 emit pass: writes pairs and events into their buckets.
-void launch_traverse_emit(const GridP& g, const Seg* segs, const u32* nseg, u32 seg_cap, u32* pcur, u32* ecur,
-                          Pair* pairs, Event* events, u32* err, cudaStream_t st);
+// K2 walks, chunked over the global pair index (pbase = exclusive scan of
+// npairs).  Count pass (emit = false): pairs per cell bucket into pbk and
+// crossings per event bucket into ebk.  Emit pass: pbk / ebk are bucket
+// cursors; writes every event at its fixed index, its index into eidx, and
+// every pair into its cell bucket.
+void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, u32 cap, u32 NP, u32* pbk, u32* ebk,
+                 Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st);
 
-// frozen registry: rank events by (grid-edge id, position) inside each event
-// bucket, assign vertex ids NVg + rank, write their coordinates.
-void launch_rank_events(const GridP& g, Event* events, u32* elist, const u32* eoff, u32 nbe, u32 NVg, double* xy,
-                        cudaStream_t st);
+// frozen registry: rank the events of each event bucket (listed in eidx) by
+// (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
+void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
+                        u32 NVg, double* xy, cudaStream_t st);
 
 // K3: sort each cell bucket's pairs by cell, classify every cut cell (key,
 // sigma, class, Tier-T / Tier-G, triangle and inside-vertex counts).
@@ -36,16 +39,22 @@ void launch_classify(const GridP& g, const Pair* pairs, Pair* sorted, const u32*
                      const Event* events, CutRec* recs, u32* bstat, u32* err, cudaStream_t st);
 
 // exclusive scan of n u32 values with stride `stride` into out (n + 1
-// entries, out[n] = total), single block
-void launch_scan(const u32* in, int stride, u32* out, u32 n, cudaStream_t st);
+// entries, out[n] = total); inputs above 65536 values need scratch of
+// scan_scratch_words(n) words
+size_t scan_scratch_words(u32 n);
+void launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
 
-// K4: emit every uncut cell's base triangle and every Tier-T patch; queue
-// the Tier-G cells.
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                 const Seg* segs, const Event* events, CutRec* recs, const u32* poff, const u32* bstat,
-                 const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist, u32* ngtri,
-                 u32* err, cudaStream_t st);
+// K4: emit every uncut cell's base triangle, give each cut cell its output
+// range, queue the cut cells by kind (Tier-T into tlist, Tier-G into glist).
+void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* poff,
+                 const u32* bstat, const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
+                 unsigned short* label, unsigned short* code, u32* tlist, u32* ntlist, u32* glist, u32* nglist,
+                 u32* ngtri, cudaStream_t st);
+
+// K4-T: the App. G patch of every queued Tier-T cell (Alg. 2).
+void launch_tiert(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+                  const Seg* segs, const Event* events, const CutRec* recs, const u32* tlist, const u32* ntlist,
+                  int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err, cudaStream_t st);
 
 // K4-G: greedy Steiner-free triangulation of every queued Tier-G cell (one
 // thread per small cell; cells above the thread limit go to a warp each

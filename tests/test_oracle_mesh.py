@@ -189,3 +189,18 @@ def test_greedy_keeps_chain_constraints():
     edges = {tuple(sorted(e)) for t in tri for e in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0]))}
     assert {(3, 4), (4, 5), (5, 6)} <= edges
     assert len(tri) == 2 * 4 + 3 - 2
+
+
+def test_patches_depend_only_on_their_neighbourhood():
+    """Cor. "lookup-driven parallel retriangulation": every patch is a function
+    of its cell's local configuration, so meshing any crop on the same lattice
+    (grid origin moved by the crop offset) reproduces the full mesh's
+    triangles away from the crop border, vertex order, label and code
+    included."""
+    from gpu_util import assert_window_matches_crop
+
+    img = synth.voronoi_labels(size=700, nseeds=120, nlabels=9)
+    for hn in (2, 4):
+        m = oracle.mesh_bitmap(img, hn, 1)
+        for x0, y0 in [(0, 0), (150, 260), (316, 316)]:
+            assert assert_window_matches_crop(img, m, hn, 1, x0, y0, 384, 384) > 1000
