@@ -165,6 +165,35 @@ int mesh_profile(sbmt_ctx* ctx, int enable);
 int mesh_profile_read(sbmt_ctx* ctx, int reset, int cap, const char** names, double* ms, int64_t* launches,
                       int* n);
 
+/* Boundary extraction without any device allocation (no counterpart in the
+ * paper: an interface for callers that may not allocate device memory, such
+ * as a host application that gives the library a fixed device budget, or a
+ * latency-critical path where an allocation could block or fail).
+ *
+ * Extracts the boundary segments of one device-resident image -- the first
+ * step of mesh_bitmap -- on the calling thread's current CUDA device and
+ * enqueues the work on cuda_stream (NULL = the legacy default stream).
+ *  d_image     device image, width x height in 1..4096 (larger images return
+ *              SBMT_EINVAL), pitch_bytes >= width * dtype, dtype SBMT_U8 or
+ *              SBMT_U16;
+ *  d_segments  device output, room for `capacity` records of 4 int32 each:
+ *              corner x, corner y, length | direction << 30 (0 +x, 1 +y) |
+ *              reversed << 31, label below/left | label above/right << 16
+ *              (0xFFFF outside the image); records come in no fixed order;
+ *  d_count     device u32 receiving the number of segments (it may exceed
+ *              capacity, then only `capacity` records are written).
+ * Working memory is one 8 MiB array of static device storage held by every
+ * GPU that loads the library until the process exits; the call allocates
+ * and frees nothing.  The first call on a device looks up the array's device
+ * address (make it before any stream capture).  Every call shares the
+ * array, so calls whose work overlaps on the GPU race: order them on one
+ * stream or synchronise between them.  Returns SBMT_OK once the work is
+ * enqueued; the message of a failing call is in sbmt_static_last_error(). */
+int sbmt_extract_segments_static(const void* d_image, int32_t width, int32_t height, int64_t pitch_bytes,
+                                 int32_t dtype, void* d_segments, uint32_t capacity, uint32_t* d_count,
+                                 void* cuda_stream);
+const char* sbmt_static_last_error(void);
+
 /* Message of the last failing call on this thread (never NULL). */
 const char* sbmt_last_error(void);
 
