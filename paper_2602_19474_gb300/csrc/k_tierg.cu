@@ -23,7 +23,7 @@ namespace sbmt {
 
 namespace {
 
-constexpr int TN = 14;  // thread path: local vertices per cell
+constexpr int TN = 12;  // thread path: local vertices per cell (16-bit vertex sets)
 constexpr int WN = 64;  // warp path
 constexpr int WWARPS = 4;
 
@@ -371,6 +371,123 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
   g_sync<G>();
 }
 
+// The same greedy rule for one thread, on vertex sets.  For every pair u < v
+// two 16-bit sets record the vertices strictly left of the directed line
+// u -> v and those on it; each triple's orientation is decided once, in
+// single precision when the determinant is clear of its rounding bound and
+// exactly otherwise.  A candidate is blocked by a collinear vertex between
+// its ends or by a kept edge with one end on each side whose own line
+// separates the candidate's ends; a 3-cycle is a face when no vertex lies on
+// the inner side of all three of its edges.
+template <int N>
+SBMT_DEV int ori_filtered(const GStore<N>& s, int a, int b, int c, float tol) {
+  const float dx1 = s.fx[b] - s.fx[a], dy1 = s.fy[b] - s.fy[a];
+  const float dx2 = s.fx[c] - s.fx[a], dy2 = s.fy[c] - s.fy[a];
+  const float d = dx1 * dy2 - dy1 * dx2;
+  if (d > tol) return 1;
+  if (d < -tol) return -1;
+  return orient3(lpt(s, a), lpt(s, b), lpt(s, c));
+}
+
+template <int N>
+SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
+  static_assert(N <= 16, "vertex sets are 16 bits wide");
+  constexpr int NPAIR = N * (N - 1) / 2;
+  const int n = s.n;
+  unsigned short Lm[NPAIR], Zm[NPAIR];
+  auto pid = [](int u, int v) { return v * (v - 1) / 2 + u; };  // u < v
+  for (int k = 0; k < n * (n - 1) / 2; ++k) Lm[k] = 0, Zm[k] = 0;
+  for (int c = 2; c < n; ++c)
+    for (int b = 1; b < c; ++b)
+      for (int a = 0; a < b; ++a) {
+        const int o = ori_filtered(s, a, b, c, tolo);
+        // ori(a,b,c) = ori(b,c,a) = -ori(a,c,b)
+        if (o > 0) {
+          Lm[pid(a, b)] |= (unsigned short)(1u << c);
+          Lm[pid(b, c)] |= (unsigned short)(1u << a);
+        } else if (o < 0) {
+          Lm[pid(a, c)] |= (unsigned short)(1u << b);
+        } else {
+          Zm[pid(a, b)] |= (unsigned short)(1u << c);
+          Zm[pid(a, c)] |= (unsigned short)(1u << b);
+          Zm[pid(b, c)] |= (unsigned short)(1u << a);
+        }
+      }
+  const unsigned valid = (1u << n) - 1u;
+  auto Zset = [&](int u, int v) -> unsigned { return u < v ? Zm[pid(u, v)] : Zm[pid(v, u)]; };
+  auto Lset = [&](int u, int v) -> unsigned {
+    return u < v ? (unsigned)Lm[pid(u, v)] : (valid & ~((unsigned)Lm[pid(v, u)] | Zm[pid(v, u)]));
+  };
+  auto ori = [&](int u, int v, int w) -> int {
+    if ((Zset(u, v) >> w) & 1u) return 0;
+    return ((Lset(u, v) >> w) & 1u) ? 1 : -1;
+  };
+  // candidates in order of exact length, then (u, v)
+  int m = 0;
+  for (int u = 0; u < n; ++u)
+    for (int v = u + 1; v < n; ++v)
+      if (!((s.adj[u] >> v) & 1ull)) s.cand[m++] = (unsigned short)((u << 8) | v);
+  for (int a = 1; a < m; ++a) {
+    const unsigned short x = s.cand[a];
+    int b = a;
+    while (b > 0 && cand_less_fast(s, x, s.cand[b - 1], tolc)) s.cand[b] = s.cand[b - 1], --b;
+    s.cand[b] = x;
+  }
+  const int max_edges = 3 * n - nb - 3;
+  for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
+    const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
+    bool bad = false;
+    const unsigned zu = Zset(u, v);
+    for (unsigned zc = zu & ~((1u << u) | (1u << v)); zc && !bad; zc &= zc - 1) {
+      const int k = __ffs(zc) - 1;
+      const Pq pu = lpt(s, u), pv = lpt(s, v), pk = lpt(s, k);
+      if (zsign(dot3(pu, pv, pk)) > 0 && zsign(dot3(pv, pu, pk)) > 0) bad = true;
+    }
+    if (!bad) {
+      // the complement of L and Z holds u and v themselves: drop them
+      const unsigned lu = Lset(u, v), ru = valid & ~(lu | zu | (1u << u) | (1u << v));
+      for (unsigned as = lu; as && !bad; as &= as - 1) {
+        const int a = __ffs(as) - 1;
+        for (unsigned bs = (unsigned)s.adj[a] & ru; bs && !bad; bs &= bs - 1) {
+          const int b = __ffs(bs) - 1;
+          if (ori(a, b, u) * ori(a, b, v) < 0) bad = true;
+        }
+      }
+    }
+    if (!bad) {
+      s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
+      s.edge[s.nedge++] = (unsigned short)((u << 8) | v);
+    }
+  }
+  s.ntri = 0;
+  for (int u = 0; u < n; ++u)
+    for (unsigned vs = (unsigned)s.adj[u] & ~((2u << u) - 1u); vs; vs &= vs - 1) {
+      const int v = __ffs(vs) - 1;
+      for (unsigned ws = (unsigned)(s.adj[u] & s.adj[v]) & ~((2u << v) - 1u); ws; ws &= ws - 1) {
+        const int w = __ffs(ws) - 1;
+        const int o = ori(u, v, w);
+        if (o == 0) continue;
+        unsigned inside;
+        if (o > 0) {
+          inside = Lset(u, v) & Lset(v, w) & Lset(w, u);
+        } else {
+          inside = (valid & ~(Lset(u, v) | Zset(u, v))) & (valid & ~(Lset(v, w) | Zset(v, w))) &
+                   (valid & ~(Lset(w, u) | Zset(w, u)));
+        }
+        if (inside & ~((1u << u) | (1u << v) | (1u << w))) continue;
+        if (s.ntri < 2 * N)
+          s.tri[s.ntri] = o > 0 ? ((u32)u << 16 | (u32)v << 8 | (u32)w) : ((u32)u << 16 | (u32)w << 8 | (u32)v);
+        ++s.ntri;
+      }
+    }
+  const int nt = min(s.ntri, 2 * N);
+  for (int a = 1; a < nt; ++a)
+    for (int b = a; b > 0 && s.tri[b] < s.tri[b - 1]; --b) {
+      const u32 t = s.tri[b];
+      s.tri[b] = s.tri[b - 1], s.tri[b - 1] = t;
+    }
+}
+
 template <int G, int N>
 SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const CellGeo& cg,
                           const CutRec& rec, const GStore<N>& s, int lane, int* tri, unsigned short* label,
@@ -427,10 +544,9 @@ __global__ void __launch_bounds__(128) k_tierg_thread(GridP g, const unsigned ch
       atomicOr(err, ERR_CAPACITY);
       continue;
     }
-    OriTable<TN> ot;
-    ot.build(s);
-    const float E = (float)(6 * g.p);
-    greedy_faces<1, TN>(s, 0, boundary_count(rec), ot, 1e-4f * E * E);
+    // cell-local coordinates are bounded by the cell extent M = 6p scaled units
+    const float M = (float)(6 * g.p);
+    greedy_faces_sets<TN>(s, boundary_count(rec), 1e-4f * M * M, 8e-6f * M * M);
     write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, err);
   }
 }
