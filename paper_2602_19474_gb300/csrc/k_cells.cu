@@ -177,29 +177,27 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
   return r;
 }
 
-// K3: one block per cell bucket (1024 consecutive cell ids).  The bucket's
+// K3a: one block per cell bucket (1024 consecutive cell ids).  The bucket's
 // pairs are counting-sorted by cell in shared memory (histogram, scan,
-// scatter), the cut cells compacted, and each cut cell classified.
-__global__ void __launch_bounds__(256) k_classify(GridP g, const Pair* pairs, Pair* sorted, const u32* poff,
-                                                  const Seg* segs, const Event* ev, CutRec* recs, u32* bstat,
-                                                  u32* err) {
+// scatter); each cut cell gets a record, in cell order, in a dense range of
+// recs drawn from a counter (bbase[b], bcut[b] records).
+__global__ void __launch_bounds__(256) k_sort(const Pair* pairs, Pair* sorted, const u32* poff, CutRec* recs,
+                                              u32* nrec, u32* bcut, u32* bbase) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB], s_off[NB], s_cur[NB];
   __shared__ unsigned short s_cut[NB];
   __shared__ u32 s_sh[8];
-  __shared__ u32 s_stat[4];
+  __shared__ u32 s_base;
   const u32 b = blockIdx.x, lo = poff[b], n = poff[b + 1] - lo;
   const i64 c0 = (i64)b << CB_LOG;
-  if (threadIdx.x < 4) s_stat[threadIdx.x] = 0;
   if (n == 0) {
-    if (threadIdx.x < 4) bstat[4 * b + threadIdx.x] = 0;
+    if (threadIdx.x == 0) bcut[b] = 0, bbase[b] = 0;
     return;
   }
   for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0;
   __syncthreads();
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[pairs[lo + i].cell - c0], 1u);
   __syncthreads();
-  // offsets of each cell's pairs and the index of each cut cell's record
   u32 ncut;
   {
     const int k0 = threadIdx.x * 4;
@@ -213,50 +211,73 @@ __global__ void __launch_bounds__(256) k_classify(GridP g, const Pair* pairs, Pa
       if (v[u]) s_cut[crun++] = (unsigned short)(k0 + u);
     }
   }
+  if (threadIdx.x == 0) s_base = atomicAdd(nrec, ncut);
   __syncthreads();
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
     const Pair p = pairs[lo + i];
     const u32 slot = atomicAdd(&s_cur[p.cell - c0], 1u);
     sorted[lo + slot] = p;
   }
-  __syncthreads();
-  u32 st_extra = 0, st_chain = 0, st_g = 0;
-  int row = -1;
+  const u32 base = s_base;
   for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
     const int k = s_cut[r];
-    const u32 cid = (u32)(c0 + k);
-    if (row < 0 || !(g.cbase[row] <= (i64)cid && (row + 1 == g.nrows || g.cbase[row + 1] > (i64)cid)))
-      row = cell_row(g, cid);
-    const CellGeo cg = cell_geo(g, cid, row);
-    const Klass kl = classify_cell(g, cg, sorted + lo + s_off[k], s_cnt[k], segs, ev, err);
-    recs[lo + r] = CutRec{cid, lo + s_off[k], s_cnt[k], kl.code | (kl.tierG ? (1u << 16) : 0u), kl.ntri, kl.nchain,
-                          0u, 0u};
-    st_extra += kl.ntri - 1, st_chain += kl.nchain, st_g += kl.tierG ? 1u : 0u;
+    recs[base + r] = CutRec{(u32)(c0 + k), lo + s_off[k], s_cnt[k], 0u, 0u, 0u, 0u, 0u};
   }
-  atomicAdd(&s_stat[1], st_extra);
-  atomicAdd(&s_stat[2], st_chain);
-  atomicAdd(&s_stat[3], st_g);
-  __syncthreads();
-  if (threadIdx.x == 0) s_stat[0] = ncut;
-  __syncthreads();
-  if (threadIdx.x < 4) bstat[4 * b + threadIdx.x] = s_stat[threadIdx.x];
+  if (threadIdx.x == 0) bcut[b] = ncut, bbase[b] = base;
 }
 
 // ---------------------------------------------------------------------------
-// K4: emission
+// Tier-T patches (Alg. 2 "instantiate by a single map")
 // ---------------------------------------------------------------------------
-// Tier-T patch: events in counter-clockwise order from A, the template of the
-// key read through sigma (Alg. 2 "instantiate by a single map")
-SBMT_DEV void emit_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
-                          const Event* ev, const unsigned char* img, i64 pitch, int dtype, int* tri,
-                          unsigned short* label, unsigned short* code, double* xy, u32* err) {
-  // local vertices: 0..2 corners, then up to 4 events, then P
-  Pq pt[8];
-  u32 gid[8];
-  for (int k = 0; k < 3; ++k) {
-    pt[k] = lattice_pt(g, cg.ci[k], cg.cj[k]);
-    gid[k] = vid(g, cg.ci[k], cg.cj[k]);
+// The local triangle list of the key's template read through sigma: labels
+// 0..2 are the corners A, B, C, 3.. the events in counter-clockwise order
+// from A, 7 the inside vertex P.  Everything follows from key and sigma: the
+// key's canonical code holds the event count of each canonical edge, and
+// canonical edge s is edge (sigma + s) mod 3 of the cell.
+SBMT_DEV int tier_t_tris(int key, int sigma, unsigned char (*t)[3]) {
+  const u32 kc = c_key_code[key - 1];
+  const int ncan[3] = {(int)((kc >> 7) & 7u), (int)((kc >> 4) & 7u), (int)((kc >> 1) & 7u)};
+  int nin[3];
+  for (int s = 0; s < 3; ++s) nin[(sigma + s) % 3] = ncan[s];
+  // canonical label -> local label
+  int map[8];
+  for (int k = 0; k < 3; ++k) map[k] = (sigma + k) % 3;
+  int tt = 0;
+  for (int s = 0; s < 3; ++s) {
+    const int e = (sigma + s) % 3;
+    int first = 3;
+    for (int u = 0; u < e; ++u) first += nin[u];
+    for (int u = 0; u < nin[e]; ++u) map[3 + tt++] = first + u;
   }
+  for (int k = tt; k < 4; ++k) map[3 + k] = 0;
+  map[TP] = 7;
+  if (key <= 6) {
+    const int nt = key == 1 ? 3 : 5;
+    for (int k = 0; k < nt; ++k)
+      for (int u = 0; u < 3; ++u) t[k][u] = (unsigned char)map[c_tpl[key - 1][k][u]];
+    return nt;
+  }
+  // star from P over the boundary cycle read counter-clockwise from A'
+  int cyc[8], nc = 0, ev_i = 0;
+  for (int s = 0; s < 3; ++s) {
+    cyc[nc++] = s;
+    for (int u = 0; u < ncan[s]; ++u) cyc[nc++] = T0 + ev_i++;
+  }
+  for (int k = 0; k < nc; ++k) {
+    t[k][0] = (unsigned char)map[cyc[k]];
+    t[k][1] = (unsigned char)map[cyc[(k + 1) % nc]];
+    t[k][2] = 7;
+  }
+  return nc;
+}
+
+// From the cell's pairs: the events in counter-clockwise order from A (their
+// vertex ids staged), the patch triangles' labels (staged), and the pixel
+// corner of P (returned; NONE without P).
+SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
+                          const Event* ev, const unsigned char* img, i64 pitch, int dtype, TStage* out, u32* err) {
+  Pq pt[8];
+  for (int k = 0; k < 3; ++k) pt[k] = lattice_pt(g, cg.ci[k], cg.cj[k]);
   u32 evs[4];
   int evk[4];
   Zq evp[4];
@@ -272,12 +293,12 @@ SBMT_DEV void emit_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       }
       if (ne >= 4) {
         atomicOr(err, ERR_COUNT);
-        return;
+        return NONE;
       }
       const int le = local_edge(cg, ev[e].edge);
       if (le < 0) {
         atomicOr(err, ERR_TRAVERSAL);
-        return;
+        return NONE;
       }
       evs[ne] = e, evk[ne] = le, evp[ne] = ccw_pos(cg.down, le, ev[e]);
       ++ne;
@@ -295,74 +316,75 @@ SBMT_DEV void emit_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       Zq tp = evp[b];
       evp[b] = evp[b - 1], evp[b - 1] = tp;
     }
-  for (int k = 0; k < ne; ++k) {
-    const Event e = ev[evs[k]];
-    pt[3 + k] = Pq{zq(e.xa, e.xb), zq(e.ya, e.yb)};
-    gid[3 + k] = e.gid;
-  }
-  const int key = (int)((rec.code >> 6) & 63u), sigma = (int)((rec.code >> 4) & 3u);
-  const int P_ = 3 + ne;
-  if (rec.nchain == 1) {
-    pt[P_] = corner_of_id(g, pcorner);
-    gid[P_] = rec.chain_base;
-    xy[2 * (i64)rec.chain_base] = zdouble(pt[P_].x) / (double)g.S;
-    xy[2 * (i64)rec.chain_base + 1] = zdouble(pt[P_].y) / (double)g.S;
-  }
-  // canonical label -> local vertex
-  int map[8];
-  for (int k = 0; k < 3; ++k) map[k] = (sigma + k) % 3;
-  int nin[3] = {0, 0, 0};
-  for (int k = 0; k < ne; ++k) nin[evk[k]]++;
-  int t = 0;
-  for (int s = 0; s < 3; ++s) {
-    const int e = (sigma + s) % 3;
-    int first = 3;
-    for (int u = 0; u < e; ++u) first += nin[u];
-    for (int u = 0; u < nin[e]; ++u) map[3 + t++] = first + u;
-  }
-  for (int k = t; k < 4; ++k) map[3 + k] = -1;
-  map[TP] = rec.nchain == 1 ? P_ : -1;
-  const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
-  u32 out = rec.tri_off;
-  auto put = [&](int la, int lb, int lc) {
-    const int a = map[la], b = map[lb], c = map[lc];
-    tri[3 * (i64)out] = (int)gid[a];
-    tri[3 * (i64)out + 1] = (int)gid[b];
-    tri[3 * (i64)out + 2] = (int)gid[c];
-    label[out] = label_of(g, img, pitch, dtype, pt[a], pt[b], pt[c]);
-    code[out] = cd;
-    ++out;
-  };
-  if (key <= 6) {
-    const int nt = key == 1 ? 3 : 5;
-    for (int k = 0; k < nt; ++k) put(c_tpl[key - 1][k][0], c_tpl[key - 1][k][1], c_tpl[key - 1][k][2]);
-  } else {
-    // star from P over the boundary cycle read counter-clockwise from A'
-    int cyc[8], nc = 0, ev_i = 0;
-    for (int s = 0; s < 3; ++s) {
-      cyc[nc++] = s;
-      const int e = (sigma + s) % 3;
-      for (int u = 0; u < nin[e]; ++u) cyc[nc++] = T0 + ev_i++;
+  TStage st;
+  for (int k = 0; k < 4; ++k) {
+    if (k < ne) {
+      const Event e = ev[evs[k]];
+      pt[3 + k] = Pq{zq(e.xa, e.xb), zq(e.ya, e.yb)};
+      st.ev[k] = e.gid;
+    } else {
+      pt[3 + k] = pt[0];
+      st.ev[k] = NONE;
     }
-    for (int k = 0; k < nc; ++k) put(cyc[k], cyc[(k + 1) % nc], TP);
   }
-  if (out != rec.tri_off + rec.ntri) atomicOr(err, ERR_COUNT);
+  pt[7] = rec.nchain == 1 ? corner_of_id(g, pcorner) : pt[0];
+  const int key = (int)((rec.code >> 6) & 63u), sigma = (int)((rec.code >> 4) & 3u);
+  unsigned char t[8][3];
+  const int nt = tier_t_tris(key, sigma, t);
+  if ((u32)nt != rec.ntri) atomicOr(err, ERR_COUNT);
+  for (int k = 0; k < 8; ++k)
+    st.lab[k] = k < nt ? label_of(g, img, pitch, dtype, pt[t[k][0]], pt[t[k][1]], pt[t[k][2]]) : (unsigned short)0;
+  *out = st;
+  return rec.nchain == 1 ? pcorner : NONE;
 }
 
+// K3b: one thread per cut cell (dense): classification (key, sigma, class,
+// Tier-T / Tier-G, triangle and inside-vertex counts) added to the bucket's
+// totals, and for a Tier-T cell its staged patch.
+__global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
+                                                  const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
+                                                  const u32* nrec, u32* bextra, u32* bchain, TStage* stg, u32* err) {
+  const u32 total = *nrec;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    CutRec rec = recs[i];
+    const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
+    const Pair* P = sorted + rec.pair_lo;
+    const Klass kl = classify_cell(g, cg, P, rec.npairs, segs, ev, err);
+    rec.code = kl.code | (kl.tierG ? (1u << 16) : 0u);
+    rec.ntri = kl.ntri, rec.nchain = kl.nchain;
+    // until emission, a Tier-T record keeps P's pixel corner in tri_off
+    if (!kl.tierG) rec.tri_off = stage_tier_t(g, cg, rec, P, segs, ev, img, pitch, dtype, stg + i, err);
+    recs[i] = rec;
+    const u32 b = rec.cell >> CB_LOG;
+    atomicAdd(&bextra[b], kl.ntri - 1);
+    if (kl.nchain) atomicAdd(&bchain[b], kl.nchain);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: emission, one block per cell bucket
+// ---------------------------------------------------------------------------
+// Every uncut cell writes its base triangle; every Tier-T cell its staged
+// patch at its offset, with P's id and coordinates; every Tier-G cell gets
+// its output range and is queued.  The bucket's whole triangle range is
+// written by one block.
 __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                              CutRec* recs, const u32* poff, const u32* bstat,
-                                              const u32* extra_scan, const u32* chain_scan, u32 NVg, u32 NE,
-                                              int* tri, unsigned short* label, unsigned short* code, u32* tlist,
-                                              u32* ntlist, u32* glist, u32* nglist, u32* ngtri) {
+                                              CutRec* recs, const u32* bcut, const u32* bbase,
+                                              const u32* extra_scan, const u32* chain_scan, const TStage* stg,
+                                              u32 NVg, u32 NE, int* tri, unsigned short* label,
+                                              unsigned short* code, double* xy, u32* glist, u32* nglist,
+                                              u32* ngtri) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
   __shared__ u32 s_cb[NB];
   __shared__ u32 s_sh[8];
+  __shared__ int s_row0;
   const u32 b = blockIdx.x;
   const i64 c0 = (i64)b << CB_LOG;
   const int nc = (int)min((i64)NB, g.ncells - c0);
-  const u32 ncut = bstat[4 * b], rec0 = poff[b];
+  const u32 ncut = bcut[b], rec0 = bbase[b];
+  if (threadIdx.x == 0) s_row0 = cell_row_near(g, (u32)c0);
   for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = k < nc ? 1u : 0u;
   __syncthreads();
   for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
@@ -394,12 +416,10 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   __syncthreads();
   const u32 T0_ = (u32)c0 + extra_scan[b];
   const u32 CB0 = NVg + NE + chain_scan[b];
+  const int row0 = s_row0;
   // uncut cells: the base triangle (A, B, C), untouched.  Per strip row the
   // corner ids are row base + i, the centroid's pixel row is tabulated, and
   // its pixel column is an integer floor.
-  __shared__ int s_row0;
-  if (threadIdx.x == 0) s_row0 = cell_row(g, (u32)c0);
-  __syncthreads();
   int r = -1;
   i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0, jr = 0;
   int lr0 = 0, lr1 = 0;
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     if (s_cnt[k] != 1u) continue;
     const i64 cid = c0 + k;
     if (r < 0 || cid >= cb_r + (g.chi[r] - clo_r + 1)) {
-      if (r < 0) r = s_row0;
+      if (r < 0) r = row0;
       while (r + 1 < g.nrows && g.cbase[r + 1] <= cid) ++r;
       clo_r = g.clo[r], cb_r = g.cbase[r], jr = g.j0 + r;
       vb0 = g.vbase[r] - g.vlo[r], vb1 = g.vbase[r + 1] - g.vlo[r + 1];
@@ -439,31 +459,44 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     label[o] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
     code[o] = 0;
   }
-  // cut cells: record their output ranges and queue them by kind
-  for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
-    CutRec rec = recs[rec0 + r];
-    rec.tri_off = T0_ + s_off[rec.cell - c0];
-    rec.chain_base = CB0 + s_cb[r];
-    recs[rec0 + r] = rec;
+  // cut cells
+  int row = row0;
+  const double invS = 1.0 / (double)g.S;
+  for (u32 rr = threadIdx.x; rr < ncut; rr += blockDim.x) {
+    CutRec rec = recs[rec0 + rr];
+    const u32 off = T0_ + s_off[rec.cell - c0], cb = CB0 + s_cb[rr];
     if (rec.code & (1u << 16)) {
-      glist[atomicAdd(nglist, 1u)] = rec0 + r;
+      rec.tri_off = off, rec.chain_base = cb;
+      recs[rec0 + rr] = rec;
+      glist[atomicAdd(nglist, 1u)] = rec0 + rr;
       atomicAdd(ngtri, rec.ntri);
-    } else {
-      tlist[atomicAdd(ntlist, 1u)] = rec0 + r;
+      continue;
     }
-  }
-}
-
-// Tier-T patches, one thread per queued cell
-__global__ void __launch_bounds__(128) k_tiert(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                               const Pair* sorted, const Seg* segs, const Event* ev,
-                                               const CutRec* recs, const u32* tlist, const u32* ntlist, int* tri,
-                                               unsigned short* label, unsigned short* code, double* xy, u32* err) {
-  const u32 total = *ntlist;
-  for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
-    const CutRec rec = recs[tlist[item]];
-    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
-    emit_tier_t(g, cg, rec, sorted + rec.pair_lo, segs, ev, img, pitch, dtype, tri, label, code, xy, err);
+    row = advance_row(g, row, rec.cell);
+    const CellGeo cg = cell_geo(g, rec.cell, row);
+    const TStage st = stg[rec0 + rr];
+    u32 gid[8];
+    for (int k = 0; k < 3; ++k) gid[k] = vid(g, cg.ci[k], cg.cj[k]);
+    for (int k = 0; k < 4; ++k) gid[3 + k] = st.ev[k];
+    gid[7] = cb;
+    unsigned char t[8][3];
+    const int nt = tier_t_tris((int)((rec.code >> 6) & 63u), (int)((rec.code >> 4) & 3u), t);
+    const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
+    for (int k = 0; k < nt; ++k) {
+      const u32 o = off + (u32)k;
+      tri[3 * (i64)o] = (int)gid[t[k][0]];
+      tri[3 * (i64)o + 1] = (int)gid[t[k][1]];
+      tri[3 * (i64)o + 2] = (int)gid[t[k][2]];
+      label[o] = st.lab[k];
+      code[o] = cd;
+    }
+    if (rec.nchain == 1) {
+      const Pq p = corner_of_id(g, rec.tri_off);
+      double2 v;
+      v.x = zdouble(p.x) * invS;
+      v.y = zdouble(p.y) * invS;
+      reinterpret_cast<double2*>(xy)[cb] = v;
+    }
   }
 }
 
@@ -485,26 +518,26 @@ __global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy) {
 
 }  // namespace
 
-void launch_classify(const GridP& g, const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, const Seg* segs,
-                     const Event* events, CutRec* recs, u32* bstat, u32* err, cudaStream_t st) {
+void launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
+                 u32* bbase, cudaStream_t st) {
   if (nbc == 0) return;
-  k_classify<<<nbc, 256, 0, st>>>(g, pairs, sorted, poff, segs, events, recs, bstat, err);
+  k_sort<<<nbc, 256, 0, st>>>(pairs, sorted, poff, recs, nrec, bcut, bbase);
 }
 
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* poff,
-                 const u32* bstat, const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, u32* tlist, u32* ntlist, u32* glist, u32* nglist,
+void launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+                     const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
+                     TStage* stg, u32* err, cudaStream_t st) {
+  k_cutcells<<<152 * 24, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, nrec, bextra, bchain, stg,
+                                       err);
+}
+
+void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
+                 const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
+                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
                  u32* ngtri, cudaStream_t st) {
   if (nbc == 0) return;
-  k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, poff, bstat, extra_scan, chain_scan, NVg, NE, tri, label,
-                              code, tlist, ntlist, glist, nglist, ngtri);
-}
-
-void launch_tiert(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, const CutRec* recs, const u32* tlist, const u32* ntlist,
-                  int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err, cudaStream_t st) {
-  k_tiert<<<152 * 16, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, tlist, ntlist, tri, label,
-                                    code, xy, err);
+  k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, NVg, NE, tri,
+                              label, code, xy, glist, nglist, ngtri);
 }
 
 void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {

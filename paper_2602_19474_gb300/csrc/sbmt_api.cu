@@ -127,9 +127,9 @@ struct MeshRec {
   Event* ev = nullptr;
   u32 ne = 0;
   CutRec* recs = nullptr;
-  u32* bstat = nullptr;
-  u32* poff = nullptr;
-  u32 nbc = 0, np = 0;
+  u32* bcut = nullptr;
+  u32* bbase = nullptr;
+  u32 nbc = 0;
   std::vector<void*> scratch;  // device memory freed with the mesh
 };
 
@@ -143,15 +143,15 @@ enum {
   KN_SCAN,
   KN_TEMIT,
   KN_RANK,
-  KN_CLASSIFY,
+  KN_SORT,
+  KN_CUTCELLS,
   KN_EMIT,
-  KN_TIERT,
   KN_TIERG,
   KN_XY,
   KN_COUNT
 };
 const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_walk_count", "k_scan",
-                                            "k_walk_emit", "k_rank", "k_classify", "k_emit", "k_tiert",
+                                            "k_walk_emit", "k_rank", "k_sort", "k_cutcells", "k_emit",
                                             "k_tierg", "k_lattice_xy"};
 
 struct sbmt_ctx {
@@ -421,7 +421,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, ngtri, nwlist
   CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
   u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3, *nwlist = cnt32 + 4;
-  u32* ntlist = cnt32 + 5;
+  u32* nrec = cnt32 + 5;
 
   // K1a
   const int W = g.W, H = g.H;
@@ -466,7 +466,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   u32 *pcnt, *ecnt, *poff, *eoff, *pcur, *ecur;
   if ((rc = aalloc(ctx, &pcnt, nbc + 1))) return bail(rc);
   if ((rc = aalloc(ctx, &ecnt, nbe + 1))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &poff, nbc + 1, m->scratch) : aalloc(ctx, &poff, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &poff, nbc + 1))) return bail(rc);
   if ((rc = aalloc(ctx, &eoff, nbe + 1))) return bail(rc);
   if ((rc = aalloc(ctx, &pcur, nbc + 1))) return bail(rc);
   if ((rc = aalloc(ctx, &ecur, nbe + 1))) return bail(rc);
@@ -480,19 +480,22 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bstat, *extra_scan, *chain_scan, *cut_scan, *glist, *wlist, *elist, *eidx, *tlist;
+  u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *wlist, *elist, *eidx;
+  TStage* stg;
 
   if ((rc = aalloc(ctx, &pairs, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &sorted, NP))) return bail(rc);
   if ((rc = m->keep ? dalloc(ctx, &ev, NE, m->scratch) : aalloc(ctx, &ev, NE))) return bail(rc);
   if ((rc = m->keep ? dalloc(ctx, &recs, NP, m->scratch) : aalloc(ctx, &recs, NP))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &bstat, 4 * (size_t)nbc + 4, m->scratch) : aalloc(ctx, &bstat, 4 * (size_t)nbc + 4))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &bcut, nbc + 1, m->scratch) : aalloc(ctx, &bcut, nbc + 1))) return bail(rc);
+  if ((rc = m->keep ? dalloc(ctx, &bbase, nbc + 1, m->scratch) : aalloc(ctx, &bbase, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &bextra, 2 * ((size_t)nbc + 1)))) return bail(rc);
+  bchain = bextra + nbc + 1;
   if ((rc = aalloc(ctx, &extra_scan, nbc + 1))) return bail(rc);
   if ((rc = aalloc(ctx, &chain_scan, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &cut_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(ctx, &stg, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &glist, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &wlist, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &tlist, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &elist, NE))) return bail(rc);
   if ((rc = aalloc(ctx, &eidx, NE))) return bail(rc);
   // outputs
@@ -510,25 +513,25 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
   TRACE(KN_TEMIT, launch_walk(true, g, segs, pbase, seg_cap, (u32)NP, pcur, ecur, pairs, ev, eidx, err, st));
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
-  TRACE(KN_CLASSIFY, launch_classify(g, pairs, sorted, poff, nbc, segs, ev, recs, bstat, err, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 1, 4, extra_scan, nbc, sscr, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 2, 4, chain_scan, nbc, sscr, st));
-  TRACE(KN_SCAN, launch_scan(bstat + 0, 4, cut_scan, nbc, sscr, st));
-  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, poff, bstat, extra_scan, chain_scan, nbc, (u32)NVg,
-                             (u32)NE, m->tri, m->label, m->code, tlist, ntlist, glist, nglist, ngtri, st));
-  TRACE(KN_TIERT, launch_tiert(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, tlist, ntlist, m->tri, m->label,
-                               m->code, m->xy, err, st));
+  CK(cudaMemsetAsync(bextra, 0, 2 * ((size_t)nbc + 1) * sizeof(u32), st));
+  TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
+  TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
+                                     err, st));
+  TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
+  TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
+  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
+                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, st));
   TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, wlist, nwlist,
                                m->tri, m->label, m->code, m->xy, err, st));
   TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(m->h_info + 1, cut_scan + nbc, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(m->h_info + 1, nrec, sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(m->h_info + 2, nglist, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st));
   if (m->keep) {
     // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
-    m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bstat = bstat;
-    m->poff = poff, m->nbc = nbc, m->np = (u32)NP;
+    m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bcut = bcut;
+    m->bbase = bbase, m->nbc = nbc;
   }
   free_list(ctx, tmp);
   arena_end(ctx);
@@ -719,15 +722,17 @@ int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t
     return SBMT_OK;
   }
   if (stage == 3) {
-    std::vector<CutRec> r(m->np);
-    std::vector<u32> bs(4 * (size_t)m->nbc), po(m->nbc + 1);
+    std::vector<u32> bs(m->nbc), po(m->nbc);
+    CK(cudaMemcpy(bs.data(), m->bcut, bs.size() * sizeof(u32), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(po.data(), m->bbase, po.size() * sizeof(u32), cudaMemcpyDeviceToHost));
+    u64 nr = 0;
+    for (u32 b = 0; b < m->nbc; ++b) nr = std::max<u64>(nr, (u64)po[b] + bs[b]);
+    std::vector<CutRec> r(nr);
     CK(cudaMemcpy(r.data(), m->recs, r.size() * sizeof(CutRec), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(bs.data(), m->bstat, bs.size() * sizeof(u32), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(po.data(), m->poff, po.size() * sizeof(u32), cudaMemcpyDeviceToHost));
     int64_t k = 0;
     int64_t* o = (int64_t*)host_out;
     for (u32 b = 0; b < m->nbc; ++b)
-      for (u32 u = 0; u < bs[4 * b]; ++u, ++k) {
+      for (u32 u = 0; u < bs[b]; ++u, ++k) {
         const CutRec& c = r[po[b] + u];
         if (k < cap) {
           const int64_t rec[5] = {(int64_t)c.cell, (int64_t)(c.code & 0xFFFF), (int64_t)c.ntri, (int64_t)c.nchain,

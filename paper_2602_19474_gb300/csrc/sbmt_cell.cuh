@@ -21,6 +21,19 @@ SBMT_DEV CellGeo cell_geo(const GridP& g, u32 cid, int r) {
   cg.down = (int)(cg.c & 1);
   return cg;
 }
+// strip row of cell id cid: a proportional estimate, corrected
+SBMT_DEV int cell_row_near(const GridP& g, u32 cid) {
+  int r = (int)((float)cid * ((float)g.nrows / (float)g.ncells));
+  r = max(0, min(g.nrows - 1, r));
+  while (r > 0 && g.cbase[r] > (i64)cid) --r;
+  while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;
+  return r;
+}
+// from strip row r, the strip row of a cell id at or after that row's first cell
+SBMT_DEV int advance_row(const GridP& g, int r, u32 cid) {
+  while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;
+  return r;
+}
 SBMT_DEV int local_edge(const CellGeo& cg, u32 e) {
   return cg.edge[0] == e ? 0 : cg.edge[1] == e ? 1 : cg.edge[2] == e ? 2 : -1;
 }

@@ -116,10 +116,21 @@ struct Event {
   int xa, xb, ya, yb;
 };
 
-// one cut cell
+// one cut cell.  tri_off / chain_base: the cell's first output triangle and
+// first inside vertex, stored for Tier-G cells at emission; between
+// classification and emission a Tier-T record keeps in tri_off the pixel
+// corner of its inside vertex P (NONE without one).
 struct CutRec {
   u32 cell, pair_lo, npairs, code;  // code: bits 0-15 pattern code, bit 16 outside-regime
   u32 ntri, nchain, tri_off, chain_base;
+};
+
+// a Tier-T patch between classification and emission: the vertex ids of the
+// cell's events in counter-clockwise order from A, and the label of each
+// patch triangle
+struct __align__(16) TStage {
+  u32 ev[4];
+  unsigned short lab[8];
 };
 
 // ---------------------------------------------------------------------------

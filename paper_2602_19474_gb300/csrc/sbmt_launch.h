@@ -33,10 +33,18 @@ void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, u
 void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
                         u32 NVg, double* xy, cudaStream_t st);
 
-// K3: sort each cell bucket's pairs by cell, classify every cut cell (key,
-// sigma, class, Tier-T / Tier-G, triangle and inside-vertex counts).
-void launch_classify(const GridP& g, const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, const Seg* segs,
-                     const Event* events, CutRec* recs, u32* bstat, u32* err, cudaStream_t st);
+// K3a: sort each cell bucket's pairs by cell into sorted; one record per cut
+// cell, in cell order, in a dense range of recs drawn from *nrec (bucket b:
+// bcut[b] records from bbase[b]).
+void launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
+                 u32* bbase, cudaStream_t st);
+
+// K3b: classify every cut cell (key, sigma, class, Tier-T / Tier-G, triangle
+// and inside-vertex counts, added per bucket into bextra / bchain) and stage
+// the patch of every Tier-T cell in stg (same index as its record).
+void launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+                     const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
+                     TStage* stg, u32* err, cudaStream_t st);
 
 // exclusive scan of n u32 values with stride `stride` into out (n + 1
 // entries, out[n] = total); inputs above 65536 values need scratch of
@@ -44,17 +52,13 @@ void launch_classify(const GridP& g, const Pair* pairs, Pair* sorted, const u32*
 size_t scan_scratch_words(u32 n);
 void launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
 
-// K4: emit every uncut cell's base triangle, give each cut cell its output
-// range, queue the cut cells by kind (Tier-T into tlist, Tier-G into glist).
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* poff,
-                 const u32* bstat, const u32* extra_scan, const u32* chain_scan, u32 nbc, u32 NVg, u32 NE, int* tri,
-                 unsigned short* label, unsigned short* code, u32* tlist, u32* ntlist, u32* glist, u32* nglist,
+// K4: per cell bucket, emit every uncut cell's base triangle and every
+// Tier-T cell's staged patch (Alg. 2) with its inside vertex; give each
+// Tier-G cell its output range and queue it into glist.
+void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
+                 const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
+                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
                  u32* ngtri, cudaStream_t st);
-
-// K4-T: the App. G patch of every queued Tier-T cell (Alg. 2).
-void launch_tiert(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, const CutRec* recs, const u32* tlist, const u32* ntlist,
-                  int* tri, unsigned short* label, unsigned short* code, double* xy, u32* err, cudaStream_t st);
 
 // K4-G: greedy Steiner-free triangulation of every queued Tier-G cell (one
 // thread per small cell; cells above the thread limit go to a warp each
