@@ -29,7 +29,7 @@ namespace {
 enum { TA = 0, TB = 1, TC = 2, T0 = 3, T1 = 4, T2 = 5, T3 = 6, TP = 7 };
 constexpr int NKEYS = 15;
 // canonical code star<<10 | n(A'B')<<7 | n(B'C')<<4 | n(C'A')<<1 | dir of keys 1..15
-__constant__ unsigned short c_key_code[NKEYS] = {
+constexpr unsigned short kKeyCode[NKEYS] = {
     (0 << 10) | (0 << 7) | (1 << 4) | (1 << 1) | 0,  // 1 single segment (b)
     (1 << 10) | (0 << 7) | (1 << 4) | (1 << 1) | 0,  // 2 (1,1) (a)
     (1 << 10) | (0 << 7) | (0 << 4) | (2 << 1) | 0,  // 3 (1,1) (c)
@@ -47,7 +47,7 @@ __constant__ unsigned short c_key_code[NKEYS] = {
     (1 << 10) | (1 << 7) | (1 << 4) | (2 << 1),
 };
 // templates of the paper's keys 1..6, in App. G's order
-__constant__ unsigned char c_tpl[6][5][3] = {
+constexpr unsigned char kTpl[6][5][3] = {
     // single segment (b): Q1 on B'C' (E0), Q2 on C'A' (E1)
     {{T1, T0, TC}, {T1, TA, TB}, {T0, T1, TB}, {0, 0, 0}, {0, 0, 0}},
     // (1,1) (a): Q2 on B'C' (E0), Q1 on C'A' (E1), P inside
@@ -63,16 +63,75 @@ __constant__ unsigned char c_tpl[6][5][3] = {
     {{T2, T1, TC}, {T3, T1, T2}, {T1, T3, T0}, {T0, T3, TA}, {T0, TA, TB}},
 };
 
+// The registry as the kernels read it: the key codes, and per (key, sigma)
+// the patch's triangles in local labels (0..2 the corners A, B, C; 3.. the
+// events in counter-clockwise order from A; 7 the inside vertex P), three
+// 3-bit labels per triangle, triangle k in bits 9k..9k+8.  The template is
+// read through sigma (Alg. 2 "instantiate by a single map"): canonical
+// corner k is corner (sigma + k) mod 3, canonical edge s is edge
+// (sigma + s) mod 3, and the key's code holds the event count of each
+// canonical edge.
+struct KeyTable {
+  unsigned short code[NKEYS];
+  unsigned long long tris[NKEYS * 3];
+};
+constexpr KeyTable make_key_table() {
+  KeyTable t{};
+  for (int k = 0; k < NKEYS; ++k) t.code[k] = kKeyCode[k];
+  for (int key = 1; key <= NKEYS; ++key)
+    for (int sigma = 0; sigma < 3; ++sigma) {
+      const unsigned kc = kKeyCode[key - 1];
+      const int ncan[3] = {(int)((kc >> 7) & 7u), (int)((kc >> 4) & 7u), (int)((kc >> 1) & 7u)};
+      int nin[3] = {0, 0, 0};
+      for (int s = 0; s < 3; ++s) nin[(sigma + s) % 3] = ncan[s];
+      int map[8] = {0, 0, 0, 0, 0, 0, 0, 7};
+      for (int k = 0; k < 3; ++k) map[k] = (sigma + k) % 3;
+      int tt = 0;
+      for (int s = 0; s < 3; ++s) {
+        const int e = (sigma + s) % 3;
+        int first = 3;
+        for (int u = 0; u < e; ++u) first += nin[u];
+        for (int u = 0; u < nin[e]; ++u) map[3 + tt++] = first + u;
+      }
+      unsigned long long w = 0;
+      auto put = [&](int k, int a, int b, int c) {
+        w |= (unsigned long long)(map[a] | map[b] << 3 | map[c] << 6) << (9 * k);
+      };
+      if (key <= 6) {
+        const int nt = key == 1 ? 3 : 5;
+        for (int k = 0; k < nt; ++k) put(k, kTpl[key - 1][k][0], kTpl[key - 1][k][1], kTpl[key - 1][k][2]);
+      } else {
+        // star from P over the boundary cycle read counter-clockwise from A'
+        int cyc[8] = {}, nc = 0, ev_i = 0;
+        for (int s = 0; s < 3; ++s) {
+          cyc[nc++] = s;
+          for (int u = 0; u < ncan[s]; ++u) cyc[nc++] = T0 + ev_i++;
+        }
+        for (int k = 0; k < nc; ++k) put(k, cyc[k], cyc[(k + 1) % nc], TP);
+      }
+      t.tris[(key - 1) * 3 + sigma] = w;
+    }
+  return t;
+}
+__device__ const KeyTable g_keys = make_key_table();
+
+// local labels of triangle k of a packed patch
+SBMT_DEV int tri_label(unsigned long long w, int k, int u) { return (int)((w >> (9 * k + 3 * u)) & 7u); }
+
 SBMT_DEV int thm32_class(int m, int n) {
   // 1-based position of the sorted pair in Thm. 3.2's list, 0 if absent
-  if (m > n) {
-    int t = m;
-    m = n, n = t;
+  const int lo = m < n ? m : n, hi = m < n ? n : m;
+  switch (lo * 4 + hi) {
+    case 0 * 4 + 1: return 1;
+    case 0 * 4 + 2: return 2;
+    case 0 * 4 + 3: return 3;
+    case 1 * 4 + 1: return 4;
+    case 1 * 4 + 2: return 5;
+    case 2 * 4 + 2: return 6;
+    case 1 * 4 + 3: return 7;
+    case 2 * 4 + 3: return 8;
+    default: return 0;
   }
-  const int lst[8] = {0 * 4 + 1, 0 * 4 + 2, 0 * 4 + 3, 1 * 4 + 1, 1 * 4 + 2, 2 * 4 + 2, 1 * 4 + 3, 2 * 4 + 3};
-  for (int k = 0; k < 8; ++k)
-    if (lst[k] == m * 4 + n) return k + 1;
-  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -85,16 +144,18 @@ struct Klass {
 
 SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u32 np, const Seg* segs,
                              const Event* ev, u32* err) {
-  int nev[3] = {0, 0, 0};
+  int n0 = 0, n1 = 0, n2 = 0;  // events on AB, BC, CA
   u32 mask = 0, nchain = 0;
   bool all_one_inside = true;
-  int pin[2] = {-1, -1}, pout[2] = {-1, -1};  // local edges of the walk-order ends (Tier-T chords)
-  u32 ein_ev[2] = {NONE, NONE}, eout_ev[2] = {NONE, NONE};
-  int prev[2] = {0, 0}, mcount[2] = {0, 0};
+  // the first two pairs (Tier-T chords): local edges of the walk-order ends,
+  // their events, the segment's orientation, the pair's event count
+  int pin0 = -1, pout0 = -1, pin1 = -1, pout1 = -1, rev0 = 0, rev1 = 0, m0 = 0, m1 = 0;
+  u32 ein0 = NONE, eout0 = NONE, ein1 = NONE, eout1 = NONE;
   for (u32 k = 0; k < np; ++k) {
     const Pair pr = P[k];
     const Seg s = segs[pr.seg];
-    int inside = 0, m = 0;
+    int inside = 0, m = 0, lin = -1, lout = -1;
+#pragma unroll
     for (int end = 0; end < 2; ++end) {
       const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
       if (e != NONE) {
@@ -103,10 +164,11 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
           atomicOr(err, ERR_TRAVERSAL);
           continue;
         }
-        nev[le]++;
+        n0 += le == 0, n1 += le == 1, n2 += le == 2;
         mask |= 2u << le;
         ++m;
-        if (k < 2) (end == 0 ? pin[k] : pout[k]) = le;
+        if (end == 0) lin = le;
+        else lout = le;
         continue;
       }
       ++inside;
@@ -122,15 +184,14 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
       if (!seen) ++nchain;
     }
     if (inside != 1) all_one_inside = false;
-    if (k < 2) {
-      ein_ev[k] = pr.ev_in, eout_ev[k] = pr.ev_out, prev[k] = seg_rev(s), mcount[k] = m;
-    }
+    if (k == 0) pin0 = lin, pout0 = lout, ein0 = pr.ev_in, eout0 = pr.ev_out, rev0 = seg_rev(s), m0 = m;
+    else if (k == 1) pin1 = lin, pout1 = lout, ein1 = pr.ev_in, eout1 = pr.ev_out, rev1 = seg_rev(s), m1 = m;
   }
   Klass r;
   r.nchain = nchain;
-  r.ntri = 2 * nchain + 1 + (u32)(nev[0] + nev[1] + nev[2]);
+  r.ntri = 2 * nchain + 1 + (u32)(n0 + n1 + n2);
   if (nchain) mask |= 1u;
-  const int klass = np == 1 ? thm32_class(0, mcount[0]) : np == 2 ? thm32_class(mcount[0], mcount[1]) : 0;
+  const int klass = np == 1 ? thm32_class(0, m0) : np == 2 ? thm32_class(m0, m1) : 0;
   const bool chords = nchain == 0 && (np == 1 || np == 2);
   const bool star = nchain == 1 && all_one_inside && np >= 2 && np <= 4;
   if (!chords && !star) {
@@ -140,33 +201,32 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
   }
   int dir = 0;
   if (chords && np == 2) {
-    int X[2];
-    for (int k = 0; k < 2; ++k) X[k] = (pout[k] == (pin[k] + 1) % 3) ? pout[k] : pin[k];
-    if (X[0] == X[1]) {
+    const int X0 = (pout0 == (pin0 + 1) % 3) ? pout0 : pin0;
+    const int X1 = (pout1 == (pin1 + 1) % 3) ? pout1 : pin1;
+    if (X0 == X1) {
       // nested chords at corner X: the chord nearer X meets the edge ending
       // at X later in counter-clockwise order
-      const int ein = (X[0] + 2) % 3, eout = X[0];
-      Zq pos[2];
-      for (int k = 0; k < 2; ++k) {
-        const u32 e = pin[k] == ein ? ein_ev[k] : eout_ev[k];
-        pos[k] = ccw_pos(cg.down, ein, ev[e]);
-      }
-      const int near = zcmp(pos[0], pos[1]) > 0 ? 0 : 1;
+      const int ein = (X0 + 2) % 3, eout = X0;
+      const Zq pos0 = ccw_pos(cg.down, ein, ev[pin0 == ein ? ein0 : eout0]);
+      const Zq pos1 = ccw_pos(cg.down, ein, ev[pin1 == ein ? ein1 : eout1]);
+      const bool near0 = zcmp(pos0, pos1) > 0;
+      const int pi = near0 ? pin0 : pin1, po = near0 ? pout0 : pout1, rv = near0 ? rev0 : rev1;
       // the chord's own direction: the walk runs in -> out, reversed if rev
-      const int first = prev[near] ? pout[near] : pin[near];
-      const int second = prev[near] ? pin[near] : pout[near];
+      const int first = rv ? po : pi, second = rv ? pi : po;
       dir = (first == ein && second == eout) ? 1 : 0;
     }
   }
+  // canonical rotation: the least code over the three rotations
   const int st = star ? 1 : 0;
-  int best = -1, sigma = 0;
-  for (int rr = 0; rr < 3; ++rr) {
-    const int code = (st << 10) | (nev[rr] << 7) | (nev[(rr + 1) % 3] << 4) | (nev[(rr + 2) % 3] << 1) | dir;
-    if (best < 0 || code < best) best = code, sigma = rr;
-  }
+  const int cr0 = (st << 10) | (n0 << 7) | (n1 << 4) | (n2 << 1) | dir;
+  const int cr1 = (st << 10) | (n1 << 7) | (n2 << 4) | (n0 << 1) | dir;
+  const int cr2 = (st << 10) | (n2 << 7) | (n0 << 4) | (n1 << 1) | dir;
+  int best = cr0, sigma = 0;
+  if (cr1 < best) best = cr1, sigma = 1;
+  if (cr2 < best) best = cr2, sigma = 2;
   int key = 0;
   for (int k = 0; k < NKEYS; ++k)
-    if (c_key_code[k] == best) key = k + 1;
+    if (g_keys.code[k] == best) key = k + 1;
   if (key == 0) {  // structure in the regime but no table entry: treat as Tier-G
     r.tierG = true;
     r.code = (mask & 15u) | (63u << 6) | ((u32)klass << 12);
@@ -227,64 +287,24 @@ __global__ void __launch_bounds__(256) k_sort(const Pair* pairs, Pair* sorted, c
 }
 
 // ---------------------------------------------------------------------------
-// Tier-T patches (Alg. 2 "instantiate by a single map")
+// Tier-T patches (Alg. 2)
 // ---------------------------------------------------------------------------
-// The local triangle list of the key's template read through sigma: labels
-// 0..2 are the corners A, B, C, 3.. the events in counter-clockwise order
-// from A, 7 the inside vertex P.  Everything follows from key and sigma: the
-// key's canonical code holds the event count of each canonical edge, and
-// canonical edge s is edge (sigma + s) mod 3 of the cell.
-SBMT_DEV int tier_t_tris(int key, int sigma, unsigned char (*t)[3]) {
-  const u32 kc = c_key_code[key - 1];
-  const int ncan[3] = {(int)((kc >> 7) & 7u), (int)((kc >> 4) & 7u), (int)((kc >> 1) & 7u)};
-  int nin[3];
-  for (int s = 0; s < 3; ++s) nin[(sigma + s) % 3] = ncan[s];
-  // canonical label -> local label
-  int map[8];
-  for (int k = 0; k < 3; ++k) map[k] = (sigma + k) % 3;
-  int tt = 0;
-  for (int s = 0; s < 3; ++s) {
-    const int e = (sigma + s) % 3;
-    int first = 3;
-    for (int u = 0; u < e; ++u) first += nin[u];
-    for (int u = 0; u < nin[e]; ++u) map[3 + tt++] = first + u;
-  }
-  for (int k = tt; k < 4; ++k) map[3 + k] = 0;
-  map[TP] = 7;
-  if (key <= 6) {
-    const int nt = key == 1 ? 3 : 5;
-    for (int k = 0; k < nt; ++k)
-      for (int u = 0; u < 3; ++u) t[k][u] = (unsigned char)map[c_tpl[key - 1][k][u]];
-    return nt;
-  }
-  // star from P over the boundary cycle read counter-clockwise from A'
-  int cyc[8], nc = 0, ev_i = 0;
-  for (int s = 0; s < 3; ++s) {
-    cyc[nc++] = s;
-    for (int u = 0; u < ncan[s]; ++u) cyc[nc++] = T0 + ev_i++;
-  }
-  for (int k = 0; k < nc; ++k) {
-    t[k][0] = (unsigned char)map[cyc[k]];
-    t[k][1] = (unsigned char)map[cyc[(k + 1) % nc]];
-    t[k][2] = 7;
-  }
-  return nc;
-}
-
 // From the cell's pairs: the events in counter-clockwise order from A (their
-// vertex ids staged), the patch triangles' labels (staged), and the pixel
-// corner of P (returned; NONE without P).
+// vertex ids staged), the labels of the patch's triangles (staged), and the
+// pixel corner of P (returned; NONE without P).  Points are kept relative to
+// corner A, where they fit 32 bits.
 SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
                           const Event* ev, const unsigned char* img, i64 pitch, int dtype, TStage* out, u32* err) {
-  Pq pt[8];
-  for (int k = 0; k < 3; ++k) pt[k] = lattice_pt(g, cg.ci[k], cg.cj[k]);
-  u32 evs[4];
-  int evk[4];
-  Zq evp[4];
+  // events as (local edge, counter-clockwise position, index); absent ones
+  // carry edge 3 and sort last
+  u32 e_[4] = {NONE, NONE, NONE, NONE};
+  int k_[4] = {3, 3, 3, 3};
+  Zq p_[4] = {zq(0), zq(0), zq(0), zq(0)};
   int ne = 0;
   u32 pcorner = NONE;
   for (u32 k = 0; k < rec.npairs; ++k) {
     const Pair pr = P[k];
+#pragma unroll
     for (int end = 0; end < 2; ++end) {
       const u32 e = end == 0 ? pr.ev_in : pr.ev_out;
       if (e == NONE) {
@@ -295,45 +315,73 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
         atomicOr(err, ERR_COUNT);
         return NONE;
       }
-      const int le = local_edge(cg, ev[e].edge);
+      const Event x = ev[e];
+      const int le = local_edge(cg, x.edge);
       if (le < 0) {
         atomicOr(err, ERR_TRAVERSAL);
         return NONE;
       }
-      evs[ne] = e, evk[ne] = le, evp[ne] = ccw_pos(cg.down, le, ev[e]);
+      const Zq pos = ccw_pos(cg.down, le, x);
+      // slot ne, written through fixed indices
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t == ne) e_[t] = e, k_[t] = le, p_[t] = pos;
       ++ne;
     }
   }
-  // order events by (edge, counter-clockwise position)
-  for (int a = 1; a < ne; ++a)
-    for (int b = a; b > 0; --b) {
-      const bool sw = evk[b] < evk[b - 1] || (evk[b] == evk[b - 1] && zcmp(evp[b], evp[b - 1]) < 0);
-      if (!sw) break;
-      u32 te = evs[b];
-      evs[b] = evs[b - 1], evs[b - 1] = te;
-      int tk = evk[b];
-      evk[b] = evk[b - 1], evk[b - 1] = tk;
-      Zq tp = evp[b];
-      evp[b] = evp[b - 1], evp[b - 1] = tp;
+  // sorting network on four by (edge, position)
+  auto cswap = [&](int a, int b) {
+    const bool sw = k_[b] < k_[a] || (k_[b] == k_[a] && k_[a] < 3 && zcmp(p_[b], p_[a]) < 0);
+    if (sw) {
+      const u32 te = e_[a];
+      e_[a] = e_[b], e_[b] = te;
+      const int tk = k_[a];
+      k_[a] = k_[b], k_[b] = tk;
+      const Zq tp = p_[a];
+      p_[a] = p_[b], p_[b] = tp;
     }
+  };
+  cswap(0, 1), cswap(2, 3), cswap(0, 2), cswap(1, 3), cswap(1, 2);
+  const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
+  int4 lp[8];  // (x.a, x.b, y.a, y.b) relative to A
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const Pq q = lattice_pt(g, cg.ci[k], cg.cj[k]);
+    lp[k] = make_int4((int)(q.x.a - A.x.a), (int)(q.x.b - A.x.b), (int)(q.y.a - A.y.a), (int)(q.y.b - A.y.b));
+  }
   TStage st;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (k < ne) {
-      const Event e = ev[evs[k]];
-      pt[3 + k] = Pq{zq(e.xa, e.xb), zq(e.ya, e.yb)};
-      st.ev[k] = e.gid;
+    if (e_[k] != NONE) {
+      const Event x = ev[e_[k]];
+      lp[3 + k] = make_int4((int)(x.xa - A.x.a), (int)(x.xb - A.x.b), (int)(x.ya - A.y.a), (int)(x.yb - A.y.b));
+      st.ev[k] = x.gid;
     } else {
-      pt[3 + k] = pt[0];
+      lp[3 + k] = lp[0];
       st.ev[k] = NONE;
     }
   }
-  pt[7] = rec.nchain == 1 ? corner_of_id(g, pcorner) : pt[0];
+  if (rec.nchain == 1) {
+    const Pq q = corner_of_id(g, pcorner);
+    lp[7] = make_int4((int)(q.x.a - A.x.a), (int)(q.x.b - A.x.b), (int)(q.y.a - A.y.a), (int)(q.y.b - A.y.b));
+  } else {
+    lp[7] = lp[0];
+  }
   const int key = (int)((rec.code >> 6) & 63u), sigma = (int)((rec.code >> 4) & 3u);
-  unsigned char t[8][3];
-  const int nt = tier_t_tris(key, sigma, t);
-  if ((u32)nt != rec.ntri) atomicOr(err, ERR_COUNT);
-  for (int k = 0; k < 8; ++k)
-    st.lab[k] = k < nt ? label_of(g, img, pitch, dtype, pt[t[k][0]], pt[t[k][1]], pt[t[k][2]]) : (unsigned short)0;
+  const unsigned long long w = g_keys.tris[(key - 1) * 3 + sigma];
+  const int nt = (int)rec.ntri;
+  const Zq Sx = zq(3 * A.x.a, 3 * A.x.b), Sy = zq(3 * A.y.a, 3 * A.y.b);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    unsigned short l = 0;
+    if (k < nt) {
+      const int4 a = lp[tri_label(w, k, 0)], b = lp[tri_label(w, k, 1)], c = lp[tri_label(w, k, 2)];
+      const Zq sx = Sx + zq((i64)a.x + b.x + c.x, (i64)a.y + b.y + c.y);
+      const Zq sy = Sy + zq((i64)a.z + b.z + c.z, (i64)a.w + b.w + c.w);
+      l = label_at_sum(g, img, pitch, dtype, sx, sy);
+    }
+    st.lab[k] = l;
+  }
   *out = st;
   return rec.nchain == 1 ? pcorner : NONE;
 }
@@ -475,18 +523,28 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     row = advance_row(g, row, rec.cell);
     const CellGeo cg = cell_geo(g, rec.cell, row);
     const TStage st = stg[rec0 + rr];
-    u32 gid[8];
-    for (int k = 0; k < 3; ++k) gid[k] = vid(g, cg.ci[k], cg.cj[k]);
-    for (int k = 0; k < 4; ++k) gid[3 + k] = st.ev[k];
-    gid[7] = cb;
-    unsigned char t[8][3];
-    const int nt = tier_t_tris((int)((rec.code >> 6) & 63u), (int)((rec.code >> 4) & 3u), t);
+    const unsigned long long w = g_keys.tris[(((rec.code >> 6) & 63u) - 1) * 3 + ((rec.code >> 4) & 3u)];
+    const u32 ga = vid(g, cg.ci[0], cg.cj[0]), gb = vid(g, cg.ci[1], cg.cj[1]), gc = vid(g, cg.ci[2], cg.cj[2]);
+    auto gid = [&](int l) -> u32 {
+      switch (l) {
+        case 0: return ga;
+        case 1: return gb;
+        case 2: return gc;
+        case 3: return st.ev[0];
+        case 4: return st.ev[1];
+        case 5: return st.ev[2];
+        case 6: return st.ev[3];
+        default: return cb;
+      }
+    };
     const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
-    for (int k = 0; k < nt; ++k) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      if (k >= (int)rec.ntri) break;
       const u32 o = off + (u32)k;
-      tri[3 * (i64)o] = (int)gid[t[k][0]];
-      tri[3 * (i64)o + 1] = (int)gid[t[k][1]];
-      tri[3 * (i64)o + 2] = (int)gid[t[k][2]];
+      tri[3 * (i64)o] = (int)gid(tri_label(w, k, 0));
+      tri[3 * (i64)o + 1] = (int)gid(tri_label(w, k, 1));
+      tri[3 * (i64)o + 2] = (int)gid(tri_label(w, k, 2));
       label[o] = st.lab[k];
       code[o] = cd;
     }

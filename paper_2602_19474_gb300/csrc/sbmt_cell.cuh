@@ -57,21 +57,25 @@ SBMT_DEV Pq corner_of_id(const GridP& g, u32 id) {
   return corner_pt(g, (i64)(id % (u32)(g.W + 1)), (i64)(id / (u32)(g.W + 1)));
 }
 
-// label of the pixel holding the centroid of three global points
+// label of the pixel holding the point (sx / 3, sy / 3), sx and sy the sums of
+// a triangle's three global coordinates: its centroid.  Pixel k spans
+// [k - 1/2, k + 1/2) in pixel units, so the column is floor(x/S + 1/2).
 template <typename T>
-SBMT_DEV unsigned short centroid_label(const GridP& g, const unsigned char* img, i64 pitch, const Pq& a,
-                                       const Pq& b, const Pq& c) {
-  const Zq sx = a.x + b.x + c.x, sy = a.y + b.y + c.y;
-  // pixel column floor(x/S + 1/2) with x = sx / 3
+SBMT_DEV unsigned short centroid_label_sum(const GridP& g, const unsigned char* img, i64 pitch, const Zq& sx,
+                                           const Zq& sy) {
   const i64 col = zfloordiv(Zq{2 * sx.a + 3 * g.S, 2 * sx.b}, 6 * g.S);
   const i64 row = zfloordiv(Zq{2 * sy.a + 3 * g.S, 2 * sy.b}, 6 * g.S);
   const int l = pix<T>(img, pitch, g.W, g.H, col, row);
   return l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
 }
+SBMT_DEV unsigned short label_at_sum(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Zq& sx,
+                                     const Zq& sy) {
+  return dtype == 1 ? centroid_label_sum<unsigned char>(g, img, pitch, sx, sy)
+                    : centroid_label_sum<unsigned short>(g, img, pitch, sx, sy);
+}
 SBMT_DEV unsigned short label_of(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pq& a,
                                  const Pq& b, const Pq& c) {
-  return dtype == 1 ? centroid_label<unsigned char>(g, img, pitch, a, b, c)
-                    : centroid_label<unsigned short>(g, img, pitch, a, b, c);
+  return label_at_sum(g, img, pitch, dtype, a.x + b.x + c.x, a.y + b.y + c.y);
 }
 
 // exclusive scan of one value per thread over a block of 256 threads

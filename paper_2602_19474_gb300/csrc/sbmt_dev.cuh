@@ -71,10 +71,18 @@ SBMT_HD i64 ifloordiv(i64 a, i64 d) {
   return k;
 }
 
-// floor(v / d) for d > 0, exact: a float estimate of a + b sqrt3, then the
-// exact sign of v - k d decides
+// floor(v / d) for d > 0, exact.  A single-precision estimate x of
+// (a + b sqrt3) / d is off by at most 2.4e-7 (|a| + 2|b|) / d (rounding of
+// the two conversions, the constant, the product, the sum and the quotient,
+// each 2^-24 relative); when x is farther than that from an integer its
+// floor is the answer, else the exact sign of v - k d decides.
 SBMT_HD i64 zfloordiv(Zq v, i64 d) {
-  i64 k = (i64)floorf(((float)v.a + (float)v.b * 1.7320508f) / (float)d);
+  const float x = ((float)v.a + (float)v.b * 1.7320508f) / (float)d;
+  i64 k = (i64)floorf(x);
+  const float fr = x - (float)k;
+  const float tol =
+      4e-7f * ((float)(v.a < 0 ? -v.a : v.a) + 2.0f * (float)(v.b < 0 ? -v.b : v.b)) / (float)d + 1e-6f;
+  if (fr > tol && fr < 1.0f - tol) return k;
   while (zsign(v - zq(k * d)) < 0) --k;
   while (zsign(v - zq((k + 1) * d)) >= 0) ++k;
   return k;
