@@ -23,7 +23,7 @@ namespace sbmt {
 
 namespace {
 
-constexpr int TN = 12;  // thread path: local vertices per cell (16-bit vertex sets)
+constexpr int TN = TIERG_TN;  // thread path: local vertices per cell (16-bit vertex sets)
 constexpr int WN = 64;  // warp path
 constexpr int WWARPS = 4;
 
@@ -523,21 +523,52 @@ SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, i
 SBMT_DEV int local_count(const CutRec& rec) { return (int)(rec.ntri + 2 - rec.nchain); }
 SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 * rec.nchain); }
 
-// one thread per small Tier-G cell; larger cells are passed to the warp kernel
+// Tier-G cells ordered by local vertex count, largest first, so that the
+// lanes of a warp run cells of one size; cells above TN vertices go to the
+// warp kernel.  gcnt[n] holds the number of queued cells with n vertices
+// (n > TN pooled at index TN + 1).
+__global__ void __launch_bounds__(256) k_gorder(const CutRec* recs, const u32* glist, const u32* nglist,
+                                                const u32* gcnt, u32* gcur, u32* olist, u32* nolist, u32* wlist,
+                                                u32* nwlist) {
+  __shared__ u32 s_base[TN + 2];
+  if (threadIdx.x == 0) {
+    u32 run = 0;
+    for (int n = TN; n >= 0; --n) s_base[n] = run, run += gcnt[n];
+    s_base[TN + 1] = 0;
+    if (blockIdx.x == 0) *nolist = run;
+  }
+  __syncthreads();
+  const u32 total = *nglist;
+  const int lane = threadIdx.x & 31;
+  for (u32 i0 = blockIdx.x * blockDim.x; i0 < total; i0 += gridDim.x * blockDim.x) {
+    const u32 i = i0 + threadIdx.x;
+    const bool valid = i < total;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    if (!valid) continue;
+    const u32 ri = glist[i];
+    const int n = local_count(recs[ri]);
+    const int key = n > TN ? TN + 1 : n;
+    // one atomic per distinct size in the warp
+    const unsigned peers = __match_any_sync(vmask, key);
+    const int leader = __ffs(peers) - 1;
+    u32 at = 0;
+    if (lane == leader) at = atomicAdd(key > TN ? nwlist : &gcur[key], (u32)__popc(peers));
+    at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
+    if (key > TN) wlist[at] = ri;
+    else olist[s_base[key] + at] = ri;
+  }
+}
+
+// one thread per Tier-G cell of at most TN vertices, in the order above
 __global__ void __launch_bounds__(128) k_tierg_thread(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                                       const Pair* sorted, const Seg* segs, const Event* ev,
-                                                      const CutRec* recs, const u32* glist, const u32* nglist,
-                                                      u32* wlist, u32* nwlist, int* tri, unsigned short* label,
-                                                      unsigned short* code, double* xy, u32* err) {
-  const u32 total = *nglist;
+                                                      const CutRec* recs, const u32* olist, const u32* nolist,
+                                                      int* tri, unsigned short* label, unsigned short* code,
+                                                      double* xy, u32* err) {
+  const u32 total = *nolist;
   for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
-    const u32 ri = glist[item];
-    const CutRec rec = recs[ri];
-    if (local_count(rec) > TN) {
-      wlist[atomicAdd(nwlist, 1u)] = ri;
-      continue;
-    }
-    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
+    const CutRec rec = recs[olist[item]];
+    const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
     GStore<TN> s;
     build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
     if (!s.ok) {
@@ -580,10 +611,14 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
 
 void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* wlist, u32* nwlist, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32* err, cudaStream_t st) {
-  k_tierg_thread<<<152 * 8, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, glist, nglist, wlist,
-                                         nwlist, tri, label, code, xy, err);
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
+                  unsigned short* code, double* xy, u32* err, cudaStream_t st) {
+  // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
+  u32* gcur = gcnt + (TN + 2);
+  u32* nolist = gcnt + 2 * (TN + 2);
+  k_gorder<<<152 * 2, 256, 0, st>>>(recs, glist, nglist, gcnt, gcur, olist, nolist, wlist, nwlist);
+  k_tierg_thread<<<152 * 12, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist, nolist, tri,
+                                          label, code, xy, err);
   k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
                                                 tri, label, code, xy, err);
 }

@@ -140,27 +140,31 @@ __global__ void k_seg_count(GridP g, const Seg* segs, const u32* nseg, u32 cap, 
     npairs[s] = s < n ? seg_setup(g, segs[s]).ncross + 1u : 0u;
 }
 
-constexpr u32 CH = 32;  // pairs per thread in the chunked walks
+constexpr u32 CH = 8;  // pairs per thread in the chunked walks
+
+// first segment of every chunk of CH pairs: chunk c starts in the segment s
+// with pbase[s] <= c CH < pbase[s + 1] (every segment has at least one pair)
+__global__ void k_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart) {
+  const u32 n = min(*nseg, cap);
+  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const u32 a = pbase[s], b = pbase[s + 1];
+    for (u32 c = (a + CH - 1) / CH; c * CH < b; ++c) cstart[c] = s;
+  }
+}
 
 // Chunked walk over the global pair index range.  Count pass (EMIT false):
 // histogram of pairs per cell bucket and of crossings per event bucket.
 // Emit pass: each crossing's event at its fixed index (segment event base
 // + k), its index into the event bucket, each pair into its cell bucket.
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u32* pbase, u32 cap, u32 NP,
-                                              u32* pbk, u32* ebk, Pair* pairs, Event* ev, u32* eidx, u32* err) {
+__global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u32* pbase, const u32* cstart,
+                                              u32 NP, u32* pbk, u32* ebk, Pair* pairs, Event* ev, u32* eidx,
+                                              u32* err) {
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   const u64 p0 = t * CH;
   if (p0 >= NP) return;
   const u32 p1 = (u32)((p0 + CH < (u64)NP) ? p0 + CH : (u64)NP);
-  // the segment holding pair p0: last s with pbase[s] <= p0
-  u32 lo = 0, hi = cap;
-  while (lo < hi) {
-    const u32 mid = (lo + hi + 1) >> 1;
-    if (pbase[mid] <= (u32)p0) lo = mid;
-    else hi = mid - 1;
-  }
-  u32 s = lo, k = (u32)p0 - pbase[s];
+  u32 s = cstart[t], k = (u32)p0 - pbase[s];
   SegWalk w = seg_setup(g, segs[s]);
   u32 pb = NONE, pn = 0, eb = NONE, en = 0;
   for (u32 p = (u32)p0; p < p1; ++p, ++k) {
@@ -222,16 +226,46 @@ SBMT_DEV Zq event_t(const Event& e) {
 }
 
 // The registry: one block per event bucket (2048 consecutive grid-edge ids).
-// Events are counting-sorted by edge in shared memory; an event's vertex id
-// is NVg + (events on lower edge ids) + (events on its edge nearer the
-// edge's lower endpoint), compared exactly.
+// An event's vertex id is NVg + (events on lower edge ids) + (events on its
+// edge nearer the edge's lower endpoint), compared exactly.  A bucket of at
+// most 256 events ranks each event against the others held in shared
+// memory; a larger one counting-sorts its events by edge first.
 __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
                                               u32 NVg, double* xy) {
   constexpr int NEB = 1 << EB_LOG;
   __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
   __shared__ u32 s_sh[8];
+  __shared__ u32 s_edge[256];
+  __shared__ int s_ta[256], s_tb[256];
   const u32 lo = eoff[blockIdx.x], n = eoff[blockIdx.x + 1] - lo;
   if (n == 0) return;
+  const double invS = 1.0 / (double)g.S;
+  if (n <= 256) {
+    const u32 i = threadIdx.x;
+    u32 me = 0;
+    Event x{};
+    if (i < n) {
+      me = eidx[lo + i];
+      x = ev[me];
+      const bool horiz = x.edge % 3u == 0u;
+      s_edge[i] = x.edge, s_ta[i] = horiz ? x.xa : x.ya, s_tb[i] = horiz ? x.xb : x.yb;
+    }
+    __syncthreads();
+    if (i >= n) return;
+    const Zq ti = zq(s_ta[i], s_tb[i]);
+    u32 rank = 0;
+    for (u32 q = 0; q < n; ++q) {
+      const u32 eq = s_edge[q];
+      if (eq < x.edge || (eq == x.edge && q != i && zcmp(zq(s_ta[q], s_tb[q]), ti) < 0)) ++rank;
+    }
+    const u32 gid = NVg + lo + rank;
+    ev[me].gid = gid;
+    double2 v;
+    v.x = zdouble(zq(x.xa, x.xb)) * invS;
+    v.y = zdouble(zq(x.ya, x.yb)) * invS;
+    reinterpret_cast<double2*>(xy)[gid] = v;
+    return;
+  }
   const u32 e0 = blockIdx.x << EB_LOG;
   for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
   __syncthreads();
@@ -252,7 +286,6 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
     elist[lo + slot] = eidx[lo + i];
   }
   __syncthreads();
-  const double invS = 1.0 / (double)g.S;
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
     const u32 me = eidx[lo + i];
     const Event ei = ev[me];
@@ -279,15 +312,22 @@ void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap,
   k_seg_count<<<grd, 256, 0, st>>>(g, segs, nseg, cap, npairs);
 }
 
-void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, u32 cap, u32 NP, u32* pbk, u32* ebk,
-                 Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st) {
-  const u64 threads = (NP + CH - 1) / CH;
+void launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st) {
+  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
+  k_chunk_map<<<grd, 256, 0, st>>>(pbase, nseg, cap, cstart);
+}
+
+size_t walk_chunks(u32 NP) { return (NP + CH - 1) / CH; }
+
+void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
+                 u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st) {
+  const u64 threads = walk_chunks(NP);
   if (threads == 0) return;
   const unsigned grd = (unsigned)((threads + 255) / 256);
   if (emit)
-    k_walk<true><<<grd, 256, 0, st>>>(g, segs, pbase, cap, NP, pbk, ebk, pairs, events, eidx, err);
+    k_walk<true><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
   else
-    k_walk<false><<<grd, 256, 0, st>>>(g, segs, pbase, cap, NP, pbk, ebk, pairs, events, eidx, err);
+    k_walk<false><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
 }
 
 void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,

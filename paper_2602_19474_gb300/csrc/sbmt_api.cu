@@ -472,7 +472,10 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = aalloc(ctx, &ecur, nbe + 1))) return bail(rc);
   CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
   CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
-  TRACE(KN_TCOUNT, launch_walk(false, g, segs, pbase, seg_cap, (u32)NP, pcnt, ecnt, nullptr, nullptr, nullptr, err, st));
+  u32* cstart;
+  if ((rc = aalloc(ctx, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
+  TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
+  TRACE(KN_TCOUNT, launch_walk(false, g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, nullptr, nullptr, nullptr, err, st));
   TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
   TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
   CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
@@ -480,7 +483,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *wlist, *elist, *eidx;
+  u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx, *gcnt;
   TStage* stg;
 
   if ((rc = aalloc(ctx, &pairs, NP))) return bail(rc);
@@ -496,6 +499,8 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   if ((rc = aalloc(ctx, &stg, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &glist, NP))) return bail(rc);
   if ((rc = aalloc(ctx, &wlist, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &olist, NP))) return bail(rc);
+  if ((rc = aalloc(ctx, &gcnt, 3 * (TIERG_TN + 2)))) return bail(rc);
   if ((rc = aalloc(ctx, &elist, NE))) return bail(rc);
   if ((rc = aalloc(ctx, &eidx, NE))) return bail(rc);
   // outputs
@@ -511,18 +516,19 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
-  TRACE(KN_TEMIT, launch_walk(true, g, segs, pbase, seg_cap, (u32)NP, pcur, ecur, pairs, ev, eidx, err, st));
+  TRACE(KN_TEMIT, launch_walk(true, g, segs, pbase, cstart, (u32)NP, pcur, ecur, pairs, ev, eidx, err, st));
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
   CK(cudaMemsetAsync(bextra, 0, 2 * ((size_t)nbc + 1) * sizeof(u32), st));
+  CK(cudaMemsetAsync(gcnt, 0, 3 * (TIERG_TN + 2) * sizeof(u32), st));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
                                      err, st));
   TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
   TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
-                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, st));
-  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, wlist, nwlist,
-                               m->tri, m->label, m->code, m->xy, err, st));
+                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, st));
+  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist,
+                               nwlist, m->tri, m->label, m->code, m->xy, err, st));
   TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));

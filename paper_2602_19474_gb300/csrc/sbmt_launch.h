@@ -21,12 +21,15 @@ void launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int 
 void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
 
 // K2 walks, chunked over the global pair index (pbase = exclusive scan of
-// npairs).  Count pass (emit = false): pairs per cell bucket into pbk and
-// crossings per event bucket into ebk.  Emit pass: pbk / ebk are bucket
-// cursors; writes every event at its fixed index, its index into eidx, and
-// every pair into its cell bucket.
-void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, u32 cap, u32 NP, u32* pbk, u32* ebk,
-                 Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st);
+// npairs; cstart = first segment of every chunk, from launch_chunk_map over
+// walk_chunks(NP) chunks).  Count pass (emit = false): pairs per cell bucket
+// into pbk and crossings per event bucket into ebk.  Emit pass: pbk / ebk are
+// bucket cursors; writes every event at its fixed index, its index into eidx,
+// and every pair into its cell bucket.
+size_t walk_chunks(u32 NP);
+void launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st);
+void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
+                 u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st);
 
 // frozen registry: rank the events of each event bucket (listed in eidx) by
 // (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
@@ -58,15 +61,17 @@ void launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaS
 void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
                  u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, cudaStream_t st);
+                 u32* ngtri, u32* gcnt, cudaStream_t st);
 
-// K4-G: greedy Steiner-free triangulation of every queued Tier-G cell (one
-// thread per small cell; cells above the thread limit go to a warp each
-// through wlist).
+// K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.  The
+// cells are first ordered by local vertex count, largest first, into olist
+// (gcnt: zeroed, 3 * (TIERG_TN + 2) words; its first TIERG_TN + 2 are the
+// per-count totals k_emit gathered); one thread per cell of at most
+// TIERG_TN vertices, one warp per larger cell (through wlist).
 void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* wlist, u32* nwlist, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32* err, cudaStream_t st);
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
+                  unsigned short* code, double* xy, u32* err, cudaStream_t st);
 
 // coordinates of the lattice vertices
 void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st);
