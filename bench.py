@@ -12,7 +12,18 @@ of the workload (independent images, no collective on the data path) and
 the time is the maximum over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload voronoi8192|ellipses2048|disk64]
+                  [--workload voronoi8192|ellipses2048|disk64|noise512]
+
+noise512 is the batched workload: one step meshes 512 thresholded-noise
+bitmaps (sides log-uniform in [128, 2048], h = 2 px) with one mesh_batch
+call; the line also reports the same images meshed by a loop of
+mesh_bitmap calls and checks that both give the same meshes.
+
+serving is the latency study: requests arrive as a Poisson process at each
+rate of --rates, each one a square noise bitmap from a pool of 128 (sides
+log-uniform in [256, 4096], h drawn from {2, 4, 8}), served first come first
+served by --workers host threads with one context and stream each; the line
+gives p50 / p99 latency (arrival to mesh ready) per rate.
 """
 from __future__ import annotations
 
@@ -44,6 +55,13 @@ WORKLOADS = {
 }
 
 
+BATCH_WORKLOADS = {
+    "noise512": dict(n=512, lo=128, hi=2048, h=(2, 1),
+                     desc="512 u8 bitmaps, W and H log-uniform in [128, 2048], Gaussian-filtered N(0,1) noise "
+                          "(sigma 4-32 px) > 0, h=2 px, one mesh_batch call per step"),
+}
+
+
 def cache_path(name: str) -> str:
     d = os.environ.get("SBMT_CACHE", "/tmp/sbmt_bench_cache")
     os.makedirs(d, exist_ok=True)
@@ -59,6 +77,39 @@ def load_workload(name: str, rank: int, barrier) -> np.ndarray:
         os.replace(tmp, p)
     barrier()
     return np.load(p)
+
+
+def load_batch(name: str) -> list:
+    p = cache_path(name).replace(".npy", ".npz")
+    if not os.path.exists(p):
+        # independent images: generated on all host cores (spawned before any GPU use)
+        import multiprocessing as mp
+
+        b = BATCH_WORKLOADS[name]
+        specs = synth.noise_batch_specs(n=b["n"], lo=b["lo"], hi=b["hi"])
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            imgs = pool.map(synth.noise_batch_item, specs, chunksize=4)
+        tmp = p + ".tmp.%d.npz" % os.getpid()
+        np.savez(tmp, *imgs)
+        os.replace(tmp, p)
+    with np.load(p) as z:
+        return [z["arr_%d" % k] for k in range(len(z.files))]
+
+
+def load_serving_pool() -> list:
+    p = cache_path("serving_pool").replace(".npy", ".npz")
+    if not os.path.exists(p):
+        import multiprocessing as mp
+
+        specs = synth.serving_specs()
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            imgs = pool.map(synth.serving_image, specs, chunksize=1)
+        tmp = p + ".tmp.%d.npz" % os.getpid()
+        np.savez(tmp, *imgs, hs=np.array([sp[2] for sp in specs]))
+        os.replace(tmp, p)
+    with np.load(p) as z:
+        hs = [int(x) for x in z["hs"]]
+        return [(z["arr_%d" % k], hs[k]) for k in range(len(hs))]
 
 
 def measured_peak():
@@ -279,10 +330,14 @@ def our_arm(args, rank: int, world: int, dist):
         return
     peak, peak_kind = measured_peak()
     launches = sum(n for (_, n) in prof.values())
+    # the dominant stage by device time; a stage is one launch of its kernel
+    # per step (plus, for k_scan and k_tierg, small helper launches timed
+    # with it), so its time per step is its time per launch
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dname, (dms, dn) = dom
     dbytes = kernel_bytes(dname, v, img.nbytes, W, H)
-    achieved = dbytes / (dms / dn * 1e-3) / 1e9 if dn and dbytes else None
+    per_launch_ms = dms / args.steps
+    achieved = dbytes / (per_launch_ms * 1e-3) / 1e9 if dbytes else None
     path_bytes = img.nbytes + 16.0 * T + 16.0 * v.n_vertices
     path_gbs = path_bytes / (ms * 1e-3) / 1e9
     share = {k: round(a / max(1e-9, sum(x for x, _ in prof.values())), 4) for k, (a, _) in prof.items()}
@@ -302,7 +357,7 @@ def our_arm(args, rank: int, world: int, dist):
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": dbytes,
-                     "ms_per_launch": dms / dn if dn else None},
+                     "ms_per_launch": per_launch_ms},
         "roofline_path": {"achieved": path_gbs, "peak": peak, "unit": "GB/s", "frac": path_gbs / peak,
                           "algorithmic_bytes_per_step": path_bytes},
         "kernel_share": share,
@@ -316,18 +371,207 @@ def our_arm(args, rank: int, world: int, dist):
     sb.mesh_destroy(ctx)
 
 
+def batch_arm(args, rank: int, world: int, dist):
+    """The batched workload: every step meshes the whole batch with one
+    mesh_batch call (images on several streams at once); a loop of
+    mesh_bitmap calls over the same device-resident images is timed beside
+    it, and the two must give the same meshes."""
+    import torch
+
+    import paper_2602_19474_gb300 as sb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b = BATCH_WORKLOADS[args.workload]
+    hn, hd = b["h"]
+    imgs = load_batch(args.workload)
+    st = torch.cuda.current_stream(dev)
+    ctx = sb.mesh_create(local, 0, st.cuda_stream)
+    dimgs = [torch.from_numpy(i).to(dev) for i in imgs]
+    px = sum(i.size for i in imgs)
+
+    def digest(views):
+        # per-mesh device checksums of connectivity, labels and codes
+        out = []
+        for v in views:
+            t = sb.view_tensors(v)
+            out.append((v.n_triangles, int(t["tri"].long().sum()), int(t["label"].long().sum()),
+                        int(t["code"].long().sum())))
+        return out
+
+    def batch_step(check=False):
+        ids = sb.mesh_batch(ctx, dimgs, hn, hd)
+        views = [sb.mesh_query(ctx, m, -1) for m in ids]
+        tris = (sum(v.n_triangles for v in views), sum(v.n_vertices for v in views))
+        d = digest(views) if check else None
+        for m in ids:
+            sb.mesh_release(ctx, m)
+        return tris, d
+
+    def loop_step(check=False):
+        ids = [sb.mesh_bitmap(ctx, x, hn, hd) for x in dimgs]
+        views = [sb.mesh_query(ctx, m, -1) for m in ids]
+        tris = (sum(v.n_triangles for v in views), sum(v.n_vertices for v in views))
+        d = digest(views) if check else None
+        for m in ids:
+            sb.mesh_release(ctx, m)
+        return tris, d
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier_sync()
+        e0.record(st)
+        for _ in range(steps):
+            tris = fn()[0]
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, tris
+
+    def barrier_sync():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    _, d_batch = batch_step(check=True)
+    _, d_loop = loop_step(check=True)
+    identical = d_batch == d_loop
+    for _ in range(max(0, args.warmup - 1)):
+        batch_step()
+    clk = ClockSampler(local)
+    clk.start()
+    ms, (T, V) = timed(batch_step, args.steps)
+    clocks = clk.stop()
+    loop_steps = max(1, min(3, args.steps))
+    ms_loop, _ = timed(loop_step, loop_steps)
+    if rank != 0:
+        sb.mesh_destroy(ctx)
+        return
+    peak, peak_kind = measured_peak()
+    path_bytes = float(px) + 16.0 * T + 16.0 * V
+    out = {
+        "metric": "output triangles/sec", "value": world * T / (ms * 1e-3), "unit": "triangles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + b["desc"], "images": len(imgs), "pixels": px,
+                   "h": hn / hd, "triangles_per_step": T, "vertices_per_step": V,
+                   "l2": "inputs and outputs larger than L2 (%d MB of images, ~%d MB of meshes per step)"
+                         % (px >> 20, int(24 * T) >> 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "bitmaps_per_s": world * len(imgs) / (ms * 1e-3),
+        "loop": {"ms_per_step": ms_loop, "bitmaps_per_s": world * len(imgs) / (ms_loop * 1e-3),
+                 "what": "the same images, one mesh_bitmap call each on one stream"},
+        "batch_over_loop": ms_loop / ms,
+        "identical_to_loop": identical,
+        "roofline_path": {"achieved": path_bytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": path_bytes / (ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                          "algorithmic_bytes_per_step": path_bytes},
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    sb.mesh_destroy(ctx)
+
+
+def serving_arm(args, rank: int, world: int):
+    """Open-loop serving: Poisson arrivals at each rate, FIFO over worker
+    threads (one context and stream each); latency = mesh ready - arrival."""
+    import queue
+
+    import torch
+
+    import paper_2602_19474_gb300 as sb
+
+    if rank != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pool = load_serving_pool()
+    dimgs = [(torch.from_numpy(img).to(dev), h) for img, h in pool]
+    torch.cuda.synchronize()
+    rates = [float(r) for r in args.rates.split(",")]
+    rng = np.random.default_rng(260219474 + 5)
+    ctxs = [sb.mesh_create(local) for _ in range(args.workers)]
+
+    def serve(rate: float, n: int) -> list:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+        picks = rng.integers(0, len(dimgs), n)
+        q = queue.Queue()
+        for i in range(n):
+            q.put(i)
+        lat = [0.0] * n
+        t0 = time.perf_counter() + 0.01
+
+        def worker(c):
+            torch.cuda.set_device(local)
+            while True:
+                try:
+                    i = q.get_nowait()
+                except queue.Empty:
+                    return
+                wait = t0 + arrivals[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                img, h = dimgs[picks[i]]
+                m = sb.mesh_bitmap(c, img, h, 1)
+                sb.mesh_query(c, m, -1)
+                lat[i] = time.perf_counter() - (t0 + arrivals[i])
+                sb.mesh_release(c, m)
+
+        ths = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        return lat
+
+    serve(200.0, max(8, args.warmup * 8))  # warm the contexts (table caches, scratch arenas)
+    res = []
+    for r in rates:
+        lat = serve(r, args.requests + args.warm_requests)[args.warm_requests:]
+        ms = np.array(lat) * 1e3
+        res.append({"rate_per_s": r, "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                    "mean_ms": float(ms.mean()), "requests": len(ms)})
+    for c in ctxs:
+        sb.mesh_destroy(c)
+    out = {
+        "metric": "p99 latency", "value": res[-1]["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": "serving: pool of 128 square u8 noise bitmaps, side log-uniform in [256, 4096], "
+                               "h from {2, 4, 8}, Poisson arrivals, FIFO over %d worker threads" % args.workers,
+                   "rates_per_s": rates, "requests_per_rate": args.requests,
+                   "warmup_requests_per_rate": args.warm_requests},
+        "latency": res,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="voronoi8192", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="voronoi8192",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + ["serving"])
+    ap.add_argument("--rates", default="100,200,500,1000,2000,5000,10000,20000",
+                    help="serving: arrival rates per second")
+    ap.add_argument("--requests", type=int, default=400, help="serving: measured requests per rate")
+    ap.add_argument("--warm-requests", type=int, default=50, help="serving: unmeasured requests per rate")
+    ap.add_argument("--workers", type=int, default=4, help="serving: worker threads (one context each)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "serving":
+        serving_arm(args, rank, world)
         return
     dist = None
     if world > 1:
@@ -337,7 +581,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist_.init_process_group("nccl")
         dist = dist_
-    our_arm(args, rank, world, dist)
+    if args.workload in BATCH_WORKLOADS:
+        batch_arm(args, rank, world, dist)
+    else:
+        our_arm(args, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
                                               const u32* extra_scan, const u32* chain_scan, const TStage* stg,
                                               u32 NVg, u32 NE, int* tri, unsigned short* label,
                                               unsigned short* code, double* xy, u32* glist, u32* nglist,
-                                              u32* ngtri) {
+                                              u32* ngtri, u32* gcnt) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
@@ -516,8 +516,18 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     if (rec.code & (1u << 16)) {
       rec.tri_off = off, rec.chain_base = cb;
       recs[rec0 + rr] = rec;
-      glist[atomicAdd(nglist, 1u)] = rec0 + rr;
-      atomicAdd(ngtri, rec.ntri);
+      // queue it: one atomic per warp for the list and the triangle count,
+      // one per distinct size for the per-size counts (n = ntri + 2 - n_i)
+      const unsigned act = __activemask();
+      const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
+      const u32 t = __reduce_add_sync(act, rec.ntri);
+      u32 at = 0;
+      if (lane == lead) at = atomicAdd(nglist, (u32)__popc(act)), atomicAdd(ngtri, t);
+      at = __shfl_sync(act, at, lead) + (u32)__popc(act & ((1u << lane) - 1u));
+      glist[at] = rec0 + rr;
+      const u32 n = rec.ntri + 2 - rec.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
+      const unsigned peers = __match_any_sync(act, key);
+      if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[key], (u32)__popc(peers));
       continue;
     }
     row = advance_row(g, row, rec.cell);
@@ -576,31 +586,35 @@ __global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy) {
 
 }  // namespace
 
-void launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
+int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
                  u32* bbase, cudaStream_t st) {
-  if (nbc == 0) return;
+  if (nbc == 0) return 0;
   k_sort<<<nbc, 256, 0, st>>>(pairs, sorted, poff, recs, nrec, bcut, bbase);
+  return 1;
 }
 
-void launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
                      TStage* stg, u32* err, cudaStream_t st) {
   k_cutcells<<<152 * 24, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, nrec, bextra, bchain, stg,
                                        err);
+  return 1;
 }
 
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
+int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
                  u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, cudaStream_t st) {
-  if (nbc == 0) return;
+                 u32* ngtri, u32* gcnt, cudaStream_t st) {
+  if (nbc == 0) return 0;
   k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, NVg, NE, tri,
-                              label, code, xy, glist, nglist, ngtri);
+                              label, code, xy, glist, nglist, ngtri, gcnt);
+  return 1;
 }
 
-void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {
-  if (g.nverts == 0) return;
+int launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {
+  if (g.nverts == 0) return 0;
   k_lattice_xy<<<g.nvrows, 256, 0, st>>>(g, xy);
+  return 1;
 }
 
 }  // namespace sbmt

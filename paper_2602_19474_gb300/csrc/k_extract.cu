@@ -132,22 +132,34 @@ SBMT_DEV int next_set(const u32* line, int nwords, int from) {
 
 SBMT_DEV u32 lab16(int l) { return l == OUTSIDE ? 0xFFFFu : (u32)l; }
 
+// K1b: one thread per 32-corner word of a row bit-plane; every vertex starts
+// its +x and +y runs.  Output slots are taken one atomic per warp.
 template <typename T>
 __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, const u32* vrow, int wpr,
                            const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err) {
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (i64)(H + 1) * wpr) return;
-  const int cy = (int)(t / wpr), w = (int)(t % wpr);
-  const u32 bits = vrow[t];
-  if (!bits) return;
-  int cnt = 0;
+  const bool in = t < (i64)(H + 1) * wpr;
+  const int cy = in ? (int)(t / wpr) : 0, w = in ? (int)(t % wpr) : 0;
+  const u32 bits = in ? vrow[t] : 0u;
+  u32 cnt = 0;
   for (u32 b = bits; b; b &= b - 1) {
     const int cx = (w << 5) + __ffs(b) - 1;
     const int m = corner_mask<T>(img, pitch, W, H, cx, cy);
     cnt += ((m & BE_E) != 0) + ((m & BE_N) != 0);
   }
+  // warp-wide exclusive scan of the counts and one atomic for the warp
+  const int lane = threadIdx.x & 31;
+  u32 x = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const u32 wtot = __shfl_sync(0xffffffffu, x, 31);
+  u32 wbase = 0;
+  if (lane == 31 && wtot) wbase = atomicAdd(nseg, wtot);
+  wbase = __shfl_sync(0xffffffffu, wbase, 31);
   if (!cnt) return;
-  u32 slot = atomicAdd(nseg, (u32)cnt);
+  u32 slot = wbase + x - cnt;
   for (u32 b = bits; b; b &= b - 1) {
     const int cx = (w << 5) + __ffs(b) - 1;
     const int m = corner_mask<T>(img, pitch, W, H, cx, cy);
@@ -180,16 +192,17 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
 
 }  // namespace
 
-void launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
+int launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
                         u32* vcol, int wpc, unsigned long long* nvtx, cudaStream_t st) {
   dim3 blk(256), grd((W + 1 + 255) / 256, (H + 1 + 31) / 32);
   if (dtype == 1)
     k_corner_bits<unsigned char><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx);
   else
     k_corner_bits<unsigned short><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx);
+  return 1;
 }
 
-void launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
+int launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
                      const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, cudaStream_t st) {
   const i64 n = (i64)(H + 1) * wpr;
   const int blk = 256;
@@ -198,6 +211,7 @@ void launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int 
     k_segments<unsigned char><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, segs, cap, nseg, err);
   else
     k_segments<unsigned short><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, segs, cap, nseg, err);
+  return 1;
 }
 
 }  // namespace sbmt

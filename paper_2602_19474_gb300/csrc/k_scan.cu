@@ -74,16 +74,17 @@ __global__ void __launch_bounds__(256) k_tile_scan(const u32* in, int stride, u3
 
 size_t scan_scratch_words(u32 n) { return n <= 16384 ? 0 : (size_t)((n + TILE - 1) / TILE) + 1; }
 
-void launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st) {
+int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st) {
   if (n <= 16384 || scratch == nullptr) {
     k_scan_small<<<1, 1024, 0, st>>>(in, stride, out, n);
-    return;
+    return 1;
   }
   const u32 tiles = (n + TILE - 1) / TILE;
   k_tile_sums<<<tiles, 256, 0, st>>>(in, stride, n, scratch);
   // scan of the tile sums in place (tiles <= 65536 for any n < 2^27)
   k_scan_small<<<1, 1024, 0, st>>>(scratch, 1, scratch, tiles);
   k_tile_scan<<<tiles, 256, 0, st>>>(in, stride, n, scratch, out);
+  return 3;
 }
 
 }  // namespace sbmt

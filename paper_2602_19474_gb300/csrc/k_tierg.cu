@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
 
 }  // namespace
 
-void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
                   unsigned short* code, double* xy, u32* err, cudaStream_t st) {
@@ -621,6 +621,7 @@ void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype
                                           label, code, xy, err);
   k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
                                                 tri, label, code, xy, err);
+  return 3;
 }
 
 }  // namespace sbmt

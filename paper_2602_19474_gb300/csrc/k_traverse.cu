@@ -142,6 +142,18 @@ __global__ void k_seg_count(GridP g, const Seg* segs, const u32* nseg, u32 cap, 
 
 constexpr u32 CH = 8;  // pairs per thread in the chunked walks
 
+// atomicAdd(&cur[key], 1) for each active lane, one atomic per distinct key
+// among them (neighbouring lanes mostly fill the same bucket)
+SBMT_DEV u32 warp_inc(u32* cur, u32 key) {
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, key);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  u32 at = 0;
+  if (lane == leader) at = atomicAdd(cur + key, (u32)__popc(peers));
+  at = __shfl_sync(peers, at, leader);
+  return at + (u32)__popc(peers & ((1u << lane) - 1u));
+}
+
 // first segment of every chunk of CH pairs: chunk c starts in the segment s
 // with pbase[s] <= c CH < pbase[s + 1] (every segment has at least one pair)
 __global__ void k_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart) {
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u3
       const u32 e = 3u * vid(g, ei, ej) + (u32)fam;
       if (EMIT) {
         ev[ebase + k] = Event{e, s, 0u, 0u, (int)px.a, (int)px.b, (int)py.a, (int)py.b};
-        eidx[atomicAdd(ebk + (e >> EB_LOG), 1u)] = ebase + k;
+        eidx[warp_inc(ebk, e >> EB_LOG)] = ebase + k;
       } else {
         const u32 b = e >> EB_LOG;
         if (b != eb) {
@@ -203,8 +215,7 @@ __global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u3
       }
     }
     if (EMIT) {
-      pairs[atomicAdd(pbk + (cid >> CB_LOG), 1u)] =
-          Pair{cid, s, k > 0 ? ebase + k - 1 : NONE, k < w.ncross ? ebase + k : NONE};
+      pairs[warp_inc(pbk, cid >> CB_LOG)] = Pair{cid, s, k > 0 ? ebase + k - 1 : NONE, k < w.ncross ? ebase + k : NONE};
     } else {
       const u32 b = cid >> CB_LOG;
       if (b != pb) {
@@ -307,33 +318,37 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
 
 }  // namespace
 
-void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st) {
+int launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st) {
   const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
   k_seg_count<<<grd, 256, 0, st>>>(g, segs, nseg, cap, npairs);
+  return 1;
 }
 
-void launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st) {
+int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st) {
   const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
   k_chunk_map<<<grd, 256, 0, st>>>(pbase, nseg, cap, cstart);
+  return 1;
 }
 
 size_t walk_chunks(u32 NP) { return (NP + CH - 1) / CH; }
 
-void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
+int launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
                  u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st) {
   const u64 threads = walk_chunks(NP);
-  if (threads == 0) return;
+  if (threads == 0) return 0;
   const unsigned grd = (unsigned)((threads + 255) / 256);
   if (emit)
     k_walk<true><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
   else
     k_walk<false><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
+  return 1;
 }
 
-void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
+int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
                         u32 NVg, double* xy, cudaStream_t st) {
-  if (nbe == 0) return;
+  if (nbe == 0) return 0;
   k_rank<<<nbe, 256, 0, st>>>(g, events, eidx, elist, eoff, NVg, xy);
+  return 1;
 }
 
 }  // namespace sbmt

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -154,21 +155,39 @@ const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_wa
                                             "k_walk_emit", "k_rank", "k_sort", "k_cutcells", "k_emit",
                                             "k_tierg", "k_lattice_xy"};
 
-struct sbmt_ctx {
-  int device = 0;
+// One stream of work: the context's own stream, or one of the extra streams
+// a batch spreads its images over.  Each lane has its own scratch arena and
+// its own tracing events, so lanes run on separate host threads.
+struct Lane {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  std::mutex mu;
-  std::map<sbmt_mesh, MeshRec*> meshes;
-  sbmt_mesh next = 1;
+  // per-call scratch: bump allocation in stream-ordered chunks
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t chunk_used = 0, call_bytes = 0;
   // tracing: events around each kernel launch, resolved lazily
-  bool prof = false;
   struct Mark {
-    int k;
+    int k, kernels;
     cudaEvent_t a, b;
   };
   std::vector<cudaEvent_t> ev_pool;
   std::vector<Mark> pending;
+};
+
+// images a batch meshes at once, each on its own lane
+constexpr int kBatchLanes = 6;
+
+struct sbmt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;   // one API call at a time
+  std::mutex reg;  // meshes, ids, events, pinned slots, tables: shared by the lanes of a batch
+  std::map<sbmt_mesh, MeshRec*> meshes;
+  sbmt_mesh next = 1;
+  Lane main;
+  std::vector<Lane*> extra;
+  bool in_batch = false;  // lanes share the tables: no eviction while set
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
   double prof_ms[KN_COUNT] = {};
   int64_t prof_n[KN_COUNT] = {};
   // grid tables per (W, H, h, origin), kept on the device
@@ -179,9 +198,6 @@ struct sbmt_ctx {
   };
   std::map<std::array<i64, 6>, TableEntry> tables;
   uint64_t tick = 0;
-  // per-call scratch: bump allocation in stream-ordered chunks
-  std::vector<std::pair<char*, size_t>> chunks;
-  size_t chunk_used = 0, call_bytes = 0;
   // pinned slots for the per-mesh status words
   std::vector<u32*> pinned_slabs;
   std::vector<u32*> pinned_free;
@@ -189,88 +205,102 @@ struct sbmt_ctx {
 
 namespace {
 
-cudaEvent_t pool_event(sbmt_ctx* c) {
-  if (!c->ev_pool.empty()) {
-    cudaEvent_t e = c->ev_pool.back();
-    c->ev_pool.pop_back();
+cudaEvent_t take_event(std::vector<cudaEvent_t>& pool) {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
     return e;
   }
   cudaEvent_t e = nullptr;
   cudaEventCreate(&e);
   return e;
 }
+// a context-level event (mesh completion); callers hold ctx->reg
+cudaEvent_t pool_event(sbmt_ctx* c) { return take_event(c->ev_pool); }
 
-void prof_collect(sbmt_ctx* c) {
-  for (auto& mk : c->pending) {
+void prof_collect_lane(sbmt_ctx* c, Lane* L) {
+  for (auto& mk : L->pending) {
     float ms = 0.f;
     if (cudaEventSynchronize(mk.b) == cudaSuccess && cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
       c->prof_ms[mk.k] += ms;
-      c->prof_n[mk.k] += 1;
+      c->prof_n[mk.k] += mk.kernels;
     }
-    c->ev_pool.push_back(mk.a), c->ev_pool.push_back(mk.b);
+    L->ev_pool.push_back(mk.a), L->ev_pool.push_back(mk.b);
   }
-  c->pending.clear();
+  L->pending.clear();
+}
+void prof_collect(sbmt_ctx* c) {
+  prof_collect_lane(c, &c->main);
+  for (Lane* L : c->extra) prof_collect_lane(c, L);
 }
 
-// brackets one kernel launch with events on the context stream when tracing
+// brackets one kernel launch with events on the lane's stream when tracing
 struct ProfScope {
-  sbmt_ctx* c;
-  int k;
+  Lane* L;
+  int k, kernels = 0;
   cudaEvent_t a = nullptr;
-  ProfScope(sbmt_ctx* c_, int k_) : c(c_), k(k_) {
-    if (c->prof && (a = pool_event(c))) cudaEventRecord(a, c->stream);
+  ProfScope(sbmt_ctx* c, Lane* L_, int k_) : L(L_), k(k_) {
+    if (c->prof && (a = take_event(L->ev_pool))) cudaEventRecord(a, L->stream);
   }
   ~ProfScope() {
     if (!a) return;
-    cudaEvent_t b = pool_event(c);
-    cudaEventRecord(b, c->stream);
-    c->pending.push_back({k, a, b});
-    if (c->pending.size() > 8192) prof_collect(c);
+    cudaEvent_t b = take_event(L->ev_pool);
+    cudaEventRecord(b, L->stream);
+    L->pending.push_back({k, kernels, a, b});
   }
 };
-#define TRACE(kn, call)          \
-  do {                           \
-    ProfScope ps_(ctx, kn);      \
-    call;                        \
+#define TRACE(kn, call)            \
+  do {                             \
+    ProfScope ps_(ctx, lane, kn);  \
+    ps_.kernels = (call);          \
   } while (0)
 
-// scratch arena: every call bumps through the context's chunks; a call that
+// scratch arena: every call bumps through the lane's chunks; a call that
 // needed more than one chunk leaves a single chunk of its total size for the
-// next call (frees and allocations are ordered on the context stream)
+// next call (frees and allocations are ordered on the lane's stream)
 template <typename T>
-int aalloc(sbmt_ctx* ctx, T** p, size_t count) {
+int aalloc(Lane* L, T** p, size_t count) {
   const size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~(size_t)255;
-  ctx->call_bytes += bytes;
-  if (ctx->chunks.empty() || ctx->chunk_used + bytes > ctx->chunks.back().second) {
-    const size_t want = std::max<size_t>(bytes, ctx->chunks.empty() ? ((size_t)64 << 20) : 2 * ctx->chunks.back().second);
+  L->call_bytes += bytes;
+  if (L->chunks.empty() || L->chunk_used + bytes > L->chunks.back().second) {
+    const size_t want = std::max<size_t>(bytes, L->chunks.empty() ? ((size_t)64 << 20) : 2 * L->chunks.back().second);
     void* v = nullptr;
-    cudaError_t e = cudaMallocAsync(&v, want, ctx->stream);
+    cudaError_t e = cudaMallocAsync(&v, want, L->stream);
     if (e != cudaSuccess) return fail(SBMT_ENOMEM, "scratch chunk of %zu bytes: %s", want, cudaGetErrorString(e));
-    ctx->chunks.push_back({(char*)v, want});
-    ctx->chunk_used = 0;
+    L->chunks.push_back({(char*)v, want});
+    L->chunk_used = 0;
   }
-  *p = (T*)(ctx->chunks.back().first + ctx->chunk_used);
-  ctx->chunk_used += bytes;
+  *p = (T*)(L->chunks.back().first + L->chunk_used);
+  L->chunk_used += bytes;
   return SBMT_OK;
 }
-void arena_begin(sbmt_ctx* ctx) {
-  ctx->call_bytes = 0;
-  ctx->chunk_used = 0;
+void arena_begin(Lane* L) {
+  L->call_bytes = 0;
+  L->chunk_used = 0;
   // keep only the first chunk's position: reuse from the start
-  while (ctx->chunks.size() > 1) {
-    cudaFreeAsync(ctx->chunks.back().first, ctx->stream);
-    ctx->chunks.pop_back();
+  while (L->chunks.size() > 1) {
+    cudaFreeAsync(L->chunks.back().first, L->stream);
+    L->chunks.pop_back();
   }
 }
-void arena_end(sbmt_ctx* ctx) {
-  if (ctx->chunks.size() <= 1) return;
-  const size_t total = ctx->call_bytes + ((size_t)16 << 20);
-  for (auto& c : ctx->chunks) cudaFreeAsync(c.first, ctx->stream);
-  ctx->chunks.clear();
+void arena_end(Lane* L) {
+  if (L->chunks.size() <= 1) return;
+  const size_t total = L->call_bytes + ((size_t)16 << 20);
+  for (auto& c : L->chunks) cudaFreeAsync(c.first, L->stream);
+  L->chunks.clear();
   void* v = nullptr;
-  if (cudaMallocAsync(&v, total, ctx->stream) == cudaSuccess) ctx->chunks.push_back({(char*)v, total});
+  if (cudaMallocAsync(&v, total, L->stream) == cudaSuccess) L->chunks.push_back({(char*)v, total});
+}
+void lane_release(Lane* L) {
+  for (auto& c : L->chunks) cudaFreeAsync(c.first, L->stream);
+  L->chunks.clear();
+  cudaStreamSynchronize(L->stream);
+  for (cudaEvent_t e : L->ev_pool) cudaEventDestroy(e);
+  L->ev_pool.clear();
+  if (L->own_stream) cudaStreamDestroy(L->stream);
 }
 
+// callers hold ctx->reg
 u32* pinned_slot(sbmt_ctx* ctx) {
   if (ctx->pinned_free.empty()) {
     u32* slab = nullptr;
@@ -284,16 +314,19 @@ u32* pinned_slot(sbmt_ctx* ctx) {
   return p;
 }
 
-// grid tables for one configuration, built once and kept on the device
-int get_tables(sbmt_ctx* ctx, const GridP& g, const Tables** host, const i64** dev) {
+// grid tables for one configuration, built once and kept on the device.
+// Callers hold ctx->reg.  An evicted entry may still be read by work in
+// flight on any lane, so eviction waits for the device first.
+int get_tables(sbmt_ctx* ctx, Lane* lane, const GridP& g, const Tables** host, const i64** dev) {
   const std::array<i64, 6> key{g.W, g.H, g.p, g.q, g.ox, g.oy};
   auto it = ctx->tables.find(key);
   if (it == ctx->tables.end()) {
-    if (ctx->tables.size() >= 64) {  // evict the least recently used entry
+    if (ctx->tables.size() >= 1024 && !ctx->in_batch) {  // evict the least recently used entry
       auto old = ctx->tables.begin();
       for (auto jt = ctx->tables.begin(); jt != ctx->tables.end(); ++jt)
         if (jt->second.last_use < old->second.last_use) old = jt;
-      cudaFreeAsync(old->second.dev, ctx->stream);
+      cudaDeviceSynchronize();
+      cudaFree(old->second.dev);
       ctx->tables.erase(old);
     }
     sbmt_ctx::TableEntry te;
@@ -311,10 +344,10 @@ int get_tables(sbmt_ctx* ctx, const GridP& g, const Tables** host, const i64** d
     const size_t nl = all.size();
     all.resize(nl + nrows);
     std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
-    if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), ctx->stream) != cudaSuccess)
+    if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), lane->stream) != cudaSuccess)
       return fail(SBMT_ENOMEM, "table allocation");
-    if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, ctx->stream) ||
-        cudaStreamSynchronize(ctx->stream))
+    if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, lane->stream) ||
+        cudaStreamSynchronize(lane->stream))
       return fail(SBMT_ECUDA, "table upload");
     it = ctx->tables.emplace(key, std::move(te)).first;
   }
@@ -325,25 +358,27 @@ int get_tables(sbmt_ctx* ctx, const GridP& g, const Tables** host, const i64** d
 }
 
 template <typename T>
-int dalloc(sbmt_ctx* ctx, T** p, size_t count, std::vector<void*>& track) {
+int dalloc(Lane* L, T** p, size_t count, std::vector<void*>& track) {
   void* v = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMallocAsync(&v, bytes, ctx->stream);
+  cudaError_t e = cudaMallocAsync(&v, bytes, L->stream);
   if (e != cudaSuccess) return fail(SBMT_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
   track.push_back(v);
   *p = (T*)v;
   return SBMT_OK;
 }
 
-void free_list(sbmt_ctx* ctx, std::vector<void*>& v) {
-  for (void* p : v) cudaFreeAsync(p, ctx->stream);
+void free_list(cudaStream_t st, std::vector<void*>& v) {
+  for (void* p : v) cudaFreeAsync(p, st);
   v.clear();
 }
 
-void destroy_mesh(sbmt_ctx* ctx, MeshRec* m) {
+// frees a mesh's memory, ordered on st after the mesh's own work; callers
+// hold ctx->reg
+void destroy_mesh(sbmt_ctx* ctx, MeshRec* m, cudaStream_t st) {
   if (m->done) cudaEventSynchronize(m->done);
-  free_list(ctx, m->scratch);
-  if (m->out_block) cudaFreeAsync(m->out_block, ctx->stream);
+  free_list(st, m->scratch);
+  if (m->out_block) cudaFreeAsync(m->out_block, st);
   if (m->done) ctx->ev_pool.push_back(m->done);
   if (m->h_info) ctx->pinned_free.push_back(m->h_info);
   delete m;
@@ -367,10 +402,11 @@ int check_params(const sbmt_image* img, const sbmt_params* pr) {
   return SBMT_OK;
 }
 
-int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
+// the whole path for one image, enqueued on one lane
+int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
   int rc = check_params(img, pr);
   if (rc) return rc;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = lane->stream;
   CK(cudaSetDevice(ctx->device));
   GridP g{};
   g.W = img->width, g.H = img->height;
@@ -378,7 +414,10 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
   const Tables* tbp;
   const i64* dt;
-  if ((rc = get_tables(ctx, g, &tbp, &dt))) return rc;
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    if ((rc = get_tables(ctx, lane, g, &tbp, &dt))) return rc;
+  }
   const Tables& tb = *tbp;
   if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
     return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
@@ -386,14 +425,19 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   m->W = g.W;
   m->keep = (pr->flags & SBMT_KEEP_STAGES) != 0;
   std::vector<void*> tmp;  // device memory freed at the end of the call
-  arena_begin(ctx);
+  arena_begin(lane);
   auto bail = [&](int code) {
-    free_list(ctx, tmp);
-    arena_end(ctx);
-    destroy_mesh(ctx, m);
+    free_list(st, tmp);
+    arena_end(lane);
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    destroy_mesh(ctx, m, st);
     return code;
   };
-  if (!(m->h_info = pinned_slot(ctx))) return bail(fail(SBMT_ENOMEM, "pinned info"));
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->h_info = pinned_slot(ctx);
+  }
+  if (!m->h_info) return bail(fail(SBMT_ENOMEM, "pinned info"));
   // image on the device
   const unsigned char* dimg;
   i64 pitch;
@@ -403,7 +447,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   } else {
     unsigned char* d;
     pitch = (i64)img->width * img->dtype;
-    if ((rc = aalloc(ctx, &d, (size_t)pitch * img->height))) return bail(rc);
+    if ((rc = aalloc(lane, &d, (size_t)pitch * img->height))) return bail(rc);
     if (cudaMemcpy2DAsync(d, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
       return bail(fail(SBMT_ECUDA, "image upload"));
     dimg = d;
@@ -417,7 +461,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
 
   // counters: [0] nvtx (u64), [1] totals pairs, [2] totals events, then u32s
   unsigned long long* cnt64;
-  if ((rc = aalloc(ctx, &cnt64, 8))) return bail(rc);
+  if ((rc = aalloc(lane, &cnt64, 8))) return bail(rc);
   u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, ngtri, nwlist
   CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
   u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3, *nwlist = cnt32 + 4;
@@ -427,8 +471,8 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   const int W = g.W, H = g.H;
   const int wpr = (W + 1 + 31) / 32, wpc = (H + 1 + 31) / 32;
   u32 *vrow, *vcol;
-  if ((rc = aalloc(ctx, &vrow, (size_t)wpr * (H + 1)))) return bail(rc);
-  if ((rc = aalloc(ctx, &vcol, (size_t)wpc * (W + 1)))) return bail(rc);
+  if ((rc = aalloc(lane, &vrow, (size_t)wpr * (H + 1)))) return bail(rc);
+  if ((rc = aalloc(lane, &vcol, (size_t)wpc * (W + 1)))) return bail(rc);
   TRACE(KN_CORNER, launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st));
   unsigned long long h64[4];
   CK(cudaMemcpyAsync(h64, cnt64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -437,7 +481,7 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   // K1b: every vertex starts at most two runs (+x and +y)
   const u32 seg_cap = (u32)std::max<u64>(2 * NC, 1);
   Seg* segs;
-  if ((rc = m->keep ? dalloc(ctx, &segs, seg_cap, m->scratch) : aalloc(ctx, &segs, seg_cap))) return bail(rc);
+  if ((rc = m->keep ? dalloc(lane, &segs, seg_cap, m->scratch) : aalloc(lane, &segs, seg_cap))) return bail(rc);
   TRACE(KN_SEG, launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st));
   // K2: pairs per segment in closed form and their scan -> fixed pair and
   // event indices of every segment
@@ -445,9 +489,9 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
   u32 *npairs, *pbase, *sscr;
   const size_t scr_words = std::max({scan_scratch_words(seg_cap), scan_scratch_words(nbc), scan_scratch_words(nbe)});
-  if ((rc = aalloc(ctx, &npairs, seg_cap))) return bail(rc);
-  if ((rc = aalloc(ctx, &pbase, (size_t)seg_cap + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &sscr, scr_words + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &npairs, seg_cap))) return bail(rc);
+  if ((rc = aalloc(lane, &pbase, (size_t)seg_cap + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &sscr, scr_words + 1))) return bail(rc);
   TRACE(KN_TCOUNT, launch_seg_count(g, segs, nseg, seg_cap, npairs, st));
   TRACE(KN_SCAN, launch_scan(npairs, 1, pbase, seg_cap, sscr, st));
   u32 h32[4];
@@ -464,16 +508,16 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
     return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T));
   // buckets: pairs by cell id, events by grid-edge id
   u32 *pcnt, *ecnt, *poff, *eoff, *pcur, *ecur;
-  if ((rc = aalloc(ctx, &pcnt, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &ecnt, nbe + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &poff, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &eoff, nbe + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &pcur, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &ecur, nbe + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &pcnt, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &ecnt, nbe + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &poff, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &eoff, nbe + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &pcur, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &ecur, nbe + 1))) return bail(rc);
   CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
   CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
   u32* cstart;
-  if ((rc = aalloc(ctx, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
   TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
   TRACE(KN_TCOUNT, launch_walk(false, g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, nullptr, nullptr, nullptr, err, st));
   TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
@@ -486,23 +530,23 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
   u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx, *gcnt;
   TStage* stg;
 
-  if ((rc = aalloc(ctx, &pairs, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &sorted, NP))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &ev, NE, m->scratch) : aalloc(ctx, &ev, NE))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &recs, NP, m->scratch) : aalloc(ctx, &recs, NP))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &bcut, nbc + 1, m->scratch) : aalloc(ctx, &bcut, nbc + 1))) return bail(rc);
-  if ((rc = m->keep ? dalloc(ctx, &bbase, nbc + 1, m->scratch) : aalloc(ctx, &bbase, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &bextra, 2 * ((size_t)nbc + 1)))) return bail(rc);
+  if ((rc = aalloc(lane, &pairs, NP))) return bail(rc);
+  if ((rc = aalloc(lane, &sorted, NP))) return bail(rc);
+  if ((rc = m->keep ? dalloc(lane, &ev, NE, m->scratch) : aalloc(lane, &ev, NE))) return bail(rc);
+  if ((rc = m->keep ? dalloc(lane, &recs, NP, m->scratch) : aalloc(lane, &recs, NP))) return bail(rc);
+  if ((rc = m->keep ? dalloc(lane, &bcut, nbc + 1, m->scratch) : aalloc(lane, &bcut, nbc + 1))) return bail(rc);
+  if ((rc = m->keep ? dalloc(lane, &bbase, nbc + 1, m->scratch) : aalloc(lane, &bbase, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &bextra, 2 * ((size_t)nbc + 1)))) return bail(rc);
   bchain = bextra + nbc + 1;
-  if ((rc = aalloc(ctx, &extra_scan, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &chain_scan, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(ctx, &stg, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &glist, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &wlist, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &olist, NP))) return bail(rc);
-  if ((rc = aalloc(ctx, &gcnt, 3 * (TIERG_TN + 2)))) return bail(rc);
-  if ((rc = aalloc(ctx, &elist, NE))) return bail(rc);
-  if ((rc = aalloc(ctx, &eidx, NE))) return bail(rc);
+  if ((rc = aalloc(lane, &extra_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &chain_scan, nbc + 1))) return bail(rc);
+  if ((rc = aalloc(lane, &stg, NP))) return bail(rc);
+  if ((rc = aalloc(lane, &glist, NP))) return bail(rc);
+  if ((rc = aalloc(lane, &wlist, NP))) return bail(rc);
+  if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
+  if ((rc = aalloc(lane, &gcnt, 3 * (TIERG_TN + 2)))) return bail(rc);
+  if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
+  if ((rc = aalloc(lane, &eidx, NE))) return bail(rc);
   // outputs
   const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
   const size_t off_tri = (bxy + 255) & ~(size_t)255, off_lab = (off_tri + btri + 255) & ~(size_t)255;
@@ -539,10 +583,15 @@ int mesh_one(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_m
     m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bcut = bcut;
     m->bbase = bbase, m->nbc = nbc;
   }
-  free_list(ctx, tmp);
-  arena_end(ctx);
-  if (!(m->done = pool_event(ctx))) return bail(fail(SBMT_ECUDA, "event create"));
+  free_list(st, tmp);
+  arena_end(lane);
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->done = pool_event(ctx);
+  }
+  if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
   CK(cudaEventRecord(m->done, st));
+  std::lock_guard<std::mutex> lk(ctx->reg);
   m->id = ctx->next++;
   ctx->meshes[m->id] = m;
   *out = m->id;
@@ -570,8 +619,9 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
       delete ctx;
       return fail(SBMT_ECUDA, "stream create");
     }
-    ctx->own_stream = true;
+    ctx->main.own_stream = true;
   }
+  ctx->main.stream = ctx->stream;
   // keep freed stream-ordered memory cached for the next call
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -585,7 +635,7 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  return mesh_one(ctx, img, params, out);
+  return mesh_one(ctx, &ctx->main, img, params, out);
 }
 
 int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
@@ -593,15 +643,82 @@ int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* 
   if (!ctx || !imgs || !params || !out || n < 0 || (n_params != 1 && n_params != n))
     return fail(SBMT_EINVAL, "bad batch arguments");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  for (int k = 0; k < n; ++k) {
-    const int rc = mesh_one(ctx, imgs + k, params + (n_params == 1 ? 0 : k), out + k);
-    if (rc) {
-      for (int u = 0; u < k; ++u) {
-        auto it = ctx->meshes.find(out[u]);
-        if (it != ctx->meshes.end()) destroy_mesh(ctx, it->second), ctx->meshes.erase(it);
-      }
-      return rc;
+  CK(cudaSetDevice(ctx->device));
+  const int K = std::min(n, kBatchLanes);
+  while ((int)ctx->extra.size() < K - 1) {
+    Lane* L = new Lane();
+    if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete L;
+      return fail(SBMT_ECUDA, "stream create");
     }
+    L->own_stream = true;
+    ctx->extra.push_back(L);
+  }
+  std::vector<Lane*> lanes{&ctx->main};
+  for (int k = 0; k < K - 1; ++k) lanes.push_back(ctx->extra[k]);
+  // the extra lanes start after the work already on the context stream
+  cudaEvent_t start;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    start = pool_event(ctx);
+  }
+  CK(cudaEventRecord(start, ctx->stream));
+  for (int k = 1; k < K; ++k) CK(cudaStreamWaitEvent(lanes[k]->stream, start, 0));
+  // largest images first, each lane taking the next image when it is free
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (i64)imgs[a].width * imgs[a].height > (i64)imgs[b].width * imgs[b].height;
+  });
+  std::vector<char> made(n, 0);
+  std::atomic<int> next{0};
+  std::atomic<int> first_rc{0};
+  std::mutex msg_mu;
+  std::string msg;
+  ctx->in_batch = true;
+  auto work = [&](Lane* L) {
+    cudaSetDevice(ctx->device);
+    for (int i; (i = next.fetch_add(1)) < n;) {
+      if (first_rc.load()) break;
+      const int k = order[i];
+      const int rc = mesh_one(ctx, L, imgs + k, params + (n_params == 1 ? 0 : k), out + k);
+      if (rc) {
+        std::lock_guard<std::mutex> ml(msg_mu);
+        if (!first_rc.load()) first_rc = rc, msg = sbmt_last_error();
+        break;
+      }
+      made[k] = 1;
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int k = 1; k < K; ++k) threads.emplace_back(work, lanes[k]);
+  work(lanes[0]);
+  for (auto& t : threads) t.join();
+  ctx->in_batch = false;
+  // later work on the context stream sees every mesh of the batch
+  for (int k = 1; k < K; ++k) {
+    cudaEvent_t e;
+    {
+      std::lock_guard<std::mutex> rl(ctx->reg);
+      e = pool_event(ctx);
+    }
+    CK(cudaEventRecord(e, lanes[k]->stream));
+    CK(cudaStreamWaitEvent(ctx->stream, e, 0));
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    ctx->ev_pool.push_back(e);
+  }
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    ctx->ev_pool.push_back(start);
+  }
+  if (first_rc.load()) {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    for (int k = 0; k < n; ++k) {
+      if (!made[k]) continue;
+      auto it = ctx->meshes.find(out[k]);
+      if (it != ctx->meshes.end()) destroy_mesh(ctx, it->second, ctx->stream), ctx->meshes.erase(it);
+    }
+    return fail(first_rc.load(), "%s", msg.c_str());
   }
   return SBMT_OK;
 }
@@ -641,9 +758,10 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
 int mesh_release(sbmt_ctx* ctx, sbmt_mesh mesh) {
   if (!ctx) return fail(SBMT_EINVAL, "null ctx");
   std::lock_guard<std::mutex> lk(ctx->mu);
+  std::lock_guard<std::mutex> rl(ctx->reg);
   auto it = ctx->meshes.find(mesh);
   if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
-  destroy_mesh(ctx, it->second);
+  destroy_mesh(ctx, it->second, ctx->stream);
   ctx->meshes.erase(it);
   return SBMT_OK;
 }
@@ -652,16 +770,16 @@ int mesh_destroy(sbmt_ctx* ctx) {
   if (!ctx) return fail(SBMT_EINVAL, "null ctx");
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    for (auto& kv : ctx->meshes) destroy_mesh(ctx, kv.second);
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    for (auto& kv : ctx->meshes) destroy_mesh(ctx, kv.second, ctx->stream);
     ctx->meshes.clear();
-    cudaStreamSynchronize(ctx->stream);
+    cudaDeviceSynchronize();
     prof_collect(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    for (auto& c : ctx->chunks) cudaFreeAsync(c.first, ctx->stream);
     for (auto& kv : ctx->tables) cudaFreeAsync(kv.second.dev, ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
+    for (Lane* L : ctx->extra) lane_release(L), delete L;
+    lane_release(&ctx->main);
     for (u32* slab : ctx->pinned_slabs) cudaFreeHost(slab);
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
   return SBMT_OK;

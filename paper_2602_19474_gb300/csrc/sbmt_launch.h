@@ -1,5 +1,6 @@
 // sbmt_launch.h -- host-side launchers of the SBMT kernels (one per step of
-// the hot path), called by the C interface in sbmt_api.cu.
+// the hot path), called by the C interface in sbmt_api.cu.  Each returns the
+// number of kernels it launched.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -9,16 +10,16 @@ namespace sbmt {
 
 // K1a: vertex flags of every pixel corner, bit-packed per corner row (vrow)
 // and per corner column (vcol); counts the PSLG vertices into *nvtx.
-void launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
+int launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
                         u32* vcol, int wpc, unsigned long long* nvtx, cudaStream_t st);
 
 // K1b: maximal boundary runs between PSLG vertices, compacted into segs.
-void launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
+int launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
                      const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, cudaStream_t st);
 
 // K2: number of pairs (cells visited = crossings + 1) of every segment, in
 // closed form; slots beyond the segment count get 0.
-void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
+int launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
 
 // K2 walks, chunked over the global pair index (pbase = exclusive scan of
 // npairs; cstart = first segment of every chunk, from launch_chunk_map over
@@ -27,25 +28,25 @@ void launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap,
 // bucket cursors; writes every event at its fixed index, its index into eidx,
 // and every pair into its cell bucket.
 size_t walk_chunks(u32 NP);
-void launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st);
-void launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
+int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st);
+int launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
                  u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st);
 
 // frozen registry: rank the events of each event bucket (listed in eidx) by
 // (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
-void launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
+int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
                         u32 NVg, double* xy, cudaStream_t st);
 
 // K3a: sort each cell bucket's pairs by cell into sorted; one record per cut
 // cell, in cell order, in a dense range of recs drawn from *nrec (bucket b:
 // bcut[b] records from bbase[b]).
-void launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
+int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
                  u32* bbase, cudaStream_t st);
 
 // K3b: classify every cut cell (key, sigma, class, Tier-T / Tier-G, triangle
 // and inside-vertex counts, added per bucket into bextra / bchain) and stage
 // the patch of every Tier-T cell in stg (same index as its record).
-void launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
                      TStage* stg, u32* err, cudaStream_t st);
 
@@ -53,12 +54,12 @@ void launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dt
 // entries, out[n] = total); inputs above 65536 values need scratch of
 // scan_scratch_words(n) words
 size_t scan_scratch_words(u32 n);
-void launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
+int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
 
 // K4: per cell bucket, emit every uncut cell's base triangle and every
 // Tier-T cell's staged patch (Alg. 2) with its inside vertex; give each
 // Tier-G cell its output range and queue it into glist.
-void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
+int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
                  u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
                  u32* ngtri, u32* gcnt, cudaStream_t st);
@@ -68,12 +69,12 @@ void launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
 // (gcnt: zeroed, 3 * (TIERG_TN + 2) words; its first TIERG_TN + 2 are the
 // per-count totals k_emit gathered); one thread per cell of at most
 // TIERG_TN vertices, one warp per larger cell (through wlist).
-void launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
+int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
                   unsigned short* code, double* xy, u32* err, cudaStream_t st);
 
 // coordinates of the lattice vertices
-void launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st);
+int launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st);
 
 }  // namespace sbmt

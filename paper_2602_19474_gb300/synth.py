@@ -169,12 +169,18 @@ def noise_batch_specs(n: int = 512, lo: int = 128, hi: int = 2048, seed_k: int =
     return [(int(w[i]), int(h[i]), float(s[i]), i) for i in range(n)]
 
 
+def noise_batch_item(spec, seed_k: int = 4) -> np.ndarray:
+    """One bitmap of the batch from its (width, height, sigma, index) spec."""
+    w, h, s, i = spec
+    return noise_bitmap(rng_for(seed_k, salt=1 + i), w, h, s)
+
+
 def noise_batch(n: int = 512, lo: int = 128, hi: int = 2048, seed_k: int = 4, first: int | None = None):
     """The batch of thresholded-noise bitmaps (optionally only the first few)."""
     specs = noise_batch_specs(n, lo, hi, seed_k)
     if first is not None:
         specs = specs[:first]
-    return [noise_bitmap(rng_for(seed_k, salt=1 + i), w, h, s) for (w, h, s, i) in specs]
+    return [noise_batch_item(sp, seed_k) for sp in specs]
 
 
 def serving_specs(n: int = 128, lo: int = 256, hi: int = 4096, seed_k: int = 5):
