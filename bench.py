@@ -112,6 +112,43 @@ def load_serving_pool() -> list:
         return [(z["arr_%d" % k], hs[k]) for k in range(len(hs))]
 
 
+# stage -> source files whose hash the committed DRAM capture records
+STAGE_SOURCES = {
+    "k_corner_bits": ["k_extract.cu"], "k_segments": ["k_extract.cu"], "k_walk_count": ["k_traverse.cu"],
+    "k_walk_emit": ["k_traverse.cu"], "k_rank": ["k_traverse.cu"], "k_sort": ["k_cells.cu"],
+    "k_cutcells": ["k_cells.cu"], "k_emit": ["k_cells.cu"], "k_tierg": ["k_tierg.cu"],
+    "k_lattice_xy": ["k_cells.cu"], "k_scan": ["k_scan.cu"],
+}
+
+
+def stage_source_hash(stage: str) -> str | None:
+    import hashlib
+
+    files = STAGE_SOURCES.get(stage)
+    if not files:
+        return None
+    hsh = hashlib.sha256()
+    for f in files + ["sbmt_dev.cuh", "sbmt_cell.cuh"]:
+        with open(os.path.join(ROOT, "paper_2602_19474_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def committed_traffic(workload: str, stage: str):
+    """DRAM bytes per launch of a stage from the committed ncu capture, or
+    None when there is none or the stage's source changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic_%s.md" % workload)
+    try:
+        rows = [ln.strip().strip("|").split("|") for ln in open(p) if ln.startswith("| k_")]
+    except OSError:
+        return None
+    for r in rows:
+        r = [c.strip() for c in r]
+        if len(r) >= 4 and r[0] == stage and r[3] == stage_source_hash(stage):
+            return float(r[2])
+    return None
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -355,7 +392,8 @@ def our_arm(args, rank: int, world: int, dist):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "bitmaps_per_s": world / (ms_max * 1e-3),
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": committed_traffic(args.workload, dname),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": dbytes,
                      "ms_per_launch": per_launch_ms},
         "roofline_path": {"achieved": path_gbs, "peak": peak, "unit": "GB/s", "frac": path_gbs / peak,
