@@ -16,6 +16,8 @@
 // Cells with at most TN vertices (all of them at h = 2 px) run one thread
 // each; larger cells run one warp each with the state in shared memory.  The
 // same templated code serves both (G = 1 or 32 lanes).
+#include <type_traits>
+
 #include "sbmt_cell.cuh"
 #include "sbmt_launch.h"
 
@@ -24,6 +26,7 @@ namespace sbmt {
 namespace {
 
 constexpr int TN = TIERG_TN;  // thread path: local vertices per cell (16-bit vertex sets)
+constexpr int TG_BLOCKS_PER_SM = 24;  // thread path: as many 64-thread blocks as fit (latency bound)
 constexpr int WN = 64;  // warp path
 constexpr int WWARPS = 4;
 
@@ -33,20 +36,35 @@ SBMT_DEV constexpr int pow2_at_least(int x) {
   return m;
 }
 
+// The state of one Tier-G cell.  The thread path (N <= 16) keeps it in
+// local memory and small -- 16-bit vertex sets, no edge list; the warp path
+// (N = 64) keeps it in shared memory.  Cell-local coordinates keep full 32-bit
+// components: a value near the cell can have components of order the image
+// size (a point on a slanted grid edge has x = a + b sqrt3 with both large).
 template <int N>
 struct GStore {
+  static constexpr bool SMALL = N <= 16;
   static constexpr int NCAND = N * (N - 1) / 2;
-  static constexpr int NCANDP = pow2_at_least(NCAND);
+  static constexpr int NCANDP = SMALL ? NCAND : pow2_at_least(NCAND);
+  using Adj = typename std::conditional<SMALL, unsigned short, u64>::type;
   int xa[N], xb[N], ya[N], yb[N];  // cell-local exact coordinates (a + b sqrt3)
   u32 gid[N];
   u32 ref[N];  // event index (events) or pixel-corner id (inside vertices) while building
-  u64 adj[N];
-  unsigned short edge[3 * N];
+  Adj adj[N];
+  unsigned short edge[SMALL ? 1 : 3 * N];  // kept edges, warp path only
   unsigned short cand[NCANDP];
   u32 tri[2 * N];
-  float fx[N], fy[N];  // rounded coordinates, only to order candidate lengths quickly
+  float fx[N], fy[N];  // the values rounded once from double, for the fast filters
   int n, nev, nedge, ntri, ok;
 };
+template <int N>
+SBMT_DEV float sfx(const GStore<N>& s, int k) {
+  return s.fx[k];
+}
+template <int N>
+SBMT_DEV float sfy(const GStore<N>& s, int k) {
+  return s.fy[k];
+}
 
 template <int G>
 SBMT_DEV bool g_any(bool v) {
@@ -88,8 +106,8 @@ SBMT_DEV Zq dot3(const Pq& o, const Pq& p, const Pq& q) {
 template <int N>
 SBMT_DEV bool cand_less_fast(const GStore<N>& s, unsigned short x, unsigned short y, float tolc) {
   const int xu = x >> 8, xv = x & 255, yu = y >> 8, yv = y & 255;
-  const float dx0 = s.fx[xv] - s.fx[xu], dy0 = s.fy[xv] - s.fy[xu];
-  const float dx1 = s.fx[yv] - s.fx[yu], dy1 = s.fy[yv] - s.fy[yu];
+  const float dx0 = sfx(s, xv) - sfx(s, xu), dy0 = sfy(s, xv) - sfy(s, xu);
+  const float dx1 = sfx(s, yv) - sfx(s, yu), dy1 = sfy(s, yv) - sfy(s, yu);
   const float kx = dx0 * dx0 + dy0 * dy0, ky = dx1 * dx1 + dy1 * dy1;
   const float tol = 1e-5f * (kx + ky) + tolc;
   if (kx < ky - tol) return true;
@@ -168,7 +186,8 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       if (le < 0) return;
       const int t = 3 + ne;
       s.ref[t] = e, ek[t] = le, s.gid[t] = x.gid;
-      s.xa[t] = x.xa, s.xb[t] = x.xb, s.ya[t] = x.ya, s.yb[t] = x.yb;  // global for now
+      s.xa[t] = (int)(x.xa - A.x.a), s.xb[t] = (int)(x.xb - A.x.b);
+      s.ya[t] = (int)(x.ya - A.y.a), s.yb[t] = (int)(x.yb - A.y.b);
       ++ne;
     }
   }
@@ -188,10 +207,7 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       ti = s.yb[b], s.yb[b] = s.yb[b - 1], s.yb[b - 1] = ti;
     }
   int nev[3] = {0, 0, 0};
-  for (int t = 3; t < 3 + ne; ++t) {
-    nev[ek[t]]++;
-    s.xa[t] -= (int)A.x.a, s.xb[t] -= (int)A.x.b, s.ya[t] -= (int)A.y.a, s.yb[t] -= (int)A.y.b;
-  }
+  for (int t = 3; t < 3 + ne; ++t) nev[ek[t]]++;
   // inside vertices: distinct pixel-corner ids, ascending
   int n = 3 + ne;
   for (u32 k = 0; k < rec.npairs; ++k) {
@@ -235,7 +251,8 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       return;
     }
     s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
-    s.edge[s.nedge++] = (unsigned short)((u << 8) | v);
+    if constexpr (!GStore<N>::SMALL) s.edge[s.nedge] = (unsigned short)((u << 8) | v);
+    ++s.nedge;
   };
   {  // boundary cycle A, events on AB, B, events on BC, C, events on CA
     int prev = 0, e = 3, first = 0;
@@ -381,8 +398,9 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
 // the inner side of all three of its edges.
 template <int N>
 SBMT_DEV int ori_filtered(const GStore<N>& s, int a, int b, int c, float tol) {
-  const float dx1 = s.fx[b] - s.fx[a], dy1 = s.fy[b] - s.fy[a];
-  const float dx2 = s.fx[c] - s.fx[a], dy2 = s.fy[c] - s.fy[a];
+  const float fxa = sfx(s, a), fya = sfy(s, a);
+  const float dx1 = sfx(s, b) - fxa, dy1 = sfy(s, b) - fya;
+  const float dx2 = sfx(s, c) - fxa, dy2 = sfy(s, c) - fya;
   const float d = dx1 * dy2 - dy1 * dx2;
   if (d > tol) return 1;
   if (d < -tol) return -1;
@@ -456,7 +474,7 @@ SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
     }
     if (!bad) {
       s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
-      s.edge[s.nedge++] = (unsigned short)((u << 8) | v);
+      ++s.nedge;
     }
   }
   s.ntri = 0;
@@ -560,7 +578,7 @@ __global__ void __launch_bounds__(256) k_gorder(const CutRec* recs, const u32* g
 }
 
 // one thread per Tier-G cell of at most TN vertices, in the order above
-__global__ void __launch_bounds__(128) k_tierg_thread(GridP g, const unsigned char* img, i64 pitch, int dtype,
+__global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                                       const Pair* sorted, const Seg* segs, const Event* ev,
                                                       const CutRec* recs, const u32* olist, const u32* nolist,
                                                       int* tri, unsigned short* label, unsigned short* code,
@@ -617,8 +635,14 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
   k_gorder<<<152 * 2, 256, 0, st>>>(recs, glist, nglist, gcnt, gcur, olist, nolist, wlist, nwlist);
-  k_tierg_thread<<<152 * 12, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist, nolist, tri,
-                                          label, code, xy, err);
+  // each thread keeps a cell's state in local memory: give L1 the most room
+  static const bool carve = [] {
+    cudaFuncSetAttribute(k_tierg_thread, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    return true;
+  }();
+  (void)carve;
+  k_tierg_thread<<<152 * TG_BLOCKS_PER_SM, 64, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist,
+                                                        nolist, tri, label, code, xy, err);
   k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
                                                 tri, label, code, xy, err);
   return 3;

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <array>
 #include <atomic>
@@ -173,8 +174,16 @@ struct Lane {
   std::vector<Mark> pending;
 };
 
-// images a batch meshes at once, each on its own lane
-constexpr int kBatchLanes = 6;
+// images a batch meshes at once, each on its own lane (SBMT_BATCH_LANES
+// overrides, 1..32)
+int batch_lanes() {
+  static const int n = [] {
+    const char* e = std::getenv("SBMT_BATCH_LANES");
+    const int v = e ? std::atoi(e) : 0;
+    return v >= 1 && v <= 32 ? v : 12;
+  }();
+  return n;
+}
 
 struct sbmt_ctx {
   int device = 0;
@@ -194,6 +203,7 @@ struct sbmt_ctx {
   struct TableEntry {
     Tables host;
     i64* dev = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded after the upload
     uint64_t last_use = 0;
   };
   std::map<std::array<i64, 6>, TableEntry> tables;
@@ -315,41 +325,64 @@ u32* pinned_slot(sbmt_ctx* ctx) {
 }
 
 // grid tables for one configuration, built once and kept on the device.
-// Callers hold ctx->reg.  An evicted entry may still be read by work in
-// flight on any lane, so eviction waits for the device first.
+// The host build and the upload run outside ctx->reg, so the lanes of a
+// batch build different tables at once; a lane that finds an entry another
+// lane is still uploading waits for its event.  An evicted entry may still be
+// read by work in flight on any lane, so eviction waits for the device, and
+// is put off while a batch runs.
 int get_tables(sbmt_ctx* ctx, Lane* lane, const GridP& g, const Tables** host, const i64** dev) {
   const std::array<i64, 6> key{g.W, g.H, g.p, g.q, g.ox, g.oy};
-  auto it = ctx->tables.find(key);
-  if (it == ctx->tables.end()) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    auto it = ctx->tables.find(key);
+    if (it != ctx->tables.end()) {
+      it->second.last_use = ++ctx->tick;
+      *host = &it->second.host;
+      *dev = it->second.dev;
+      if (cudaStreamWaitEvent(lane->stream, it->second.ready, 0) != cudaSuccess)
+        return fail(SBMT_ECUDA, "table wait");
+      return SBMT_OK;
+    }
     if (ctx->tables.size() >= 1024 && !ctx->in_batch) {  // evict the least recently used entry
       auto old = ctx->tables.begin();
       for (auto jt = ctx->tables.begin(); jt != ctx->tables.end(); ++jt)
         if (jt->second.last_use < old->second.last_use) old = jt;
       cudaDeviceSynchronize();
       cudaFree(old->second.dev);
+      cudaEventDestroy(old->second.ready);
       ctx->tables.erase(old);
     }
-    sbmt_ctx::TableEntry te;
-    int rc = build_tables(g, te.host);
-    if (rc) return rc;
-    const Tables& tb = te.host;
-    const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
-    std::vector<i64> all;
-    all.insert(all.end(), tb.clo.begin(), tb.clo.end());
-    all.insert(all.end(), tb.chi.begin(), tb.chi.end());
-    all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
-    all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
-    all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
-    all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
-    const size_t nl = all.size();
-    all.resize(nl + nrows);
-    std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
-    if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), lane->stream) != cudaSuccess)
-      return fail(SBMT_ENOMEM, "table allocation");
-    if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, lane->stream) ||
-        cudaStreamSynchronize(lane->stream))
-      return fail(SBMT_ECUDA, "table upload");
-    it = ctx->tables.emplace(key, std::move(te)).first;
+  }
+  sbmt_ctx::TableEntry te;
+  int rc = build_tables(g, te.host);
+  if (rc) return rc;
+  const Tables& tb = te.host;
+  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
+  std::vector<i64> all;
+  all.insert(all.end(), tb.clo.begin(), tb.clo.end());
+  all.insert(all.end(), tb.chi.begin(), tb.chi.end());
+  all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
+  all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
+  all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
+  all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
+  const size_t nl = all.size();
+  all.resize(nl + nrows);
+  std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
+  (void)nvr;
+  if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), lane->stream) != cudaSuccess)
+    return fail(SBMT_ENOMEM, "table allocation");
+  // from pageable memory the copy has read `all` when the call returns
+  if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, lane->stream) ||
+      cudaEventCreateWithFlags(&te.ready, cudaEventDisableTiming) || cudaEventRecord(te.ready, lane->stream))
+    return fail(SBMT_ECUDA, "table upload");
+  std::lock_guard<std::mutex> lk(ctx->reg);
+  auto ins = ctx->tables.try_emplace(key, std::move(te));
+  auto it = ins.first;
+  if (!ins.second) {
+    // another lane built the same tables meanwhile: use those
+    cudaFreeAsync(te.dev, lane->stream);
+    cudaEventDestroy(te.ready);
+    if (cudaStreamWaitEvent(lane->stream, it->second.ready, 0) != cudaSuccess) return fail(SBMT_ECUDA, "table wait");
   }
   it->second.last_use = ++ctx->tick;
   *host = &it->second.host;
@@ -414,10 +447,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
   const Tables* tbp;
   const i64* dt;
-  {
-    std::lock_guard<std::mutex> lk(ctx->reg);
-    if ((rc = get_tables(ctx, lane, g, &tbp, &dt))) return rc;
-  }
+  if ((rc = get_tables(ctx, lane, g, &tbp, &dt))) return rc;
   const Tables& tb = *tbp;
   if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
     return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
@@ -644,7 +674,7 @@ int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* 
     return fail(SBMT_EINVAL, "bad batch arguments");
   std::lock_guard<std::mutex> lk(ctx->mu);
   CK(cudaSetDevice(ctx->device));
-  const int K = std::min(n, kBatchLanes);
+  const int K = std::min(n, batch_lanes());
   while ((int)ctx->extra.size() < K - 1) {
     Lane* L = new Lane();
     if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -776,7 +806,7 @@ int mesh_destroy(sbmt_ctx* ctx) {
     cudaDeviceSynchronize();
     prof_collect(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    for (auto& kv : ctx->tables) cudaFreeAsync(kv.second.dev, ctx->stream);
+    for (auto& kv : ctx->tables) cudaFreeAsync(kv.second.dev, ctx->stream), cudaEventDestroy(kv.second.ready);
     for (Lane* L : ctx->extra) lane_release(L), delete L;
     lane_release(&ctx->main);
     for (u32* slab : ctx->pinned_slabs) cudaFreeHost(slab);
