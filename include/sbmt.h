@@ -154,6 +154,32 @@ int mesh_destroy(sbmt_ctx* ctx);
  * Writes min(n, cap) records to host_out and the total count to *n. */
 int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n);
 
+/* Quality measures of a finished mesh, computed on the device from its
+ * output (the measures of the paper's experiments, Sec. 4: Tables "mesh
+ * quality", "comparison", "aspect-ratio statistics", Fig. "minimum angle
+ * histograms").  Angles, areas and aspect ratios in double precision from
+ * the output coordinates, in pixel units:
+ *  min_angle_deg  smallest interior angle over all triangles;
+ *  min_area       smallest triangle area;
+ *  slivers        triangles whose smallest angle is below 5 degrees;
+ *  equilateral    triangles whose longest and shortest squared edges differ
+ *                 by at most 1e-9 of the longest (the edge-length test);
+ *  area_mean, area_var  mean and population variance of the areas;
+ *  ar_median, ar_p95, ar_max  AR = longest edge / shortest altitude; the
+ *                 percentiles are nearest-rank (the ceil(p T)-th smallest)
+ *                 of AR rounded to single precision, the maximum in double;
+ *  angle_hist     smallest angles in 2-degree bins [0,2) ... [58,60].
+ * Waits for the mesh; synchronises with the device a few times. */
+typedef struct {
+  int64_t triangles;
+  double min_angle_deg, min_area;
+  int64_t slivers, equilateral;
+  double area_mean, area_var;
+  double ar_median, ar_p95, ar_max;
+  int64_t angle_hist[30];
+} sbmt_quality;
+int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out);
+
 /* Per-kernel device time, for tracing and roofline accounting (no
  * counterpart in the paper, which reports no timings).  With enable != 0
  * every kernel launch of the context is bracketed by two CUDA events on the

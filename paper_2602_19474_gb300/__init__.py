@@ -36,7 +36,7 @@ SBMT_EXPLICIT = 0
 SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
-           "mesh_profile", "mesh_profile_read", "sbmt_last_error")
+           "mesh_profile", "mesh_profile_read", "mesh_quality", "sbmt_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -58,6 +58,13 @@ class sbmt_mesh_view(ctypes.Structure):
                 ("n_lattice_vertices", ctypes.c_int64), ("n_tierG_triangles", ctypes.c_int64), ("xy", ctypes.c_void_p),
                 ("tri", ctypes.c_void_p), ("label", ctypes.c_void_p), ("code", ctypes.c_void_p),
                 ("status", ctypes.c_int32)]
+
+
+class sbmt_quality(ctypes.Structure):
+    _fields_ = [("triangles", ctypes.c_int64), ("min_angle_deg", ctypes.c_double), ("min_area", ctypes.c_double),
+                ("slivers", ctypes.c_int64), ("equilateral", ctypes.c_int64), ("area_mean", ctypes.c_double),
+                ("area_var", ctypes.c_double), ("ar_median", ctypes.c_double), ("ar_p95", ctypes.c_double),
+                ("ar_max", ctypes.c_double), ("angle_hist", ctypes.c_int64 * 30)]
 
 
 class SbmtError(RuntimeError):
@@ -96,9 +103,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mesh_profile_read.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                       ctypes.POINTER(ctypes.c_int)]
+    lib.mesh_quality.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_quality)]
     lib.sbmt_last_error.restype = ctypes.c_char_p
     for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
-              "mesh_stage", "mesh_profile", "mesh_profile_read"):
+              "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality"):
         getattr(lib, f).restype = ctypes.c_int
     del i32
     _lib = lib
@@ -192,6 +200,15 @@ def mesh_stage(ctx: int, mesh: int, stage: int) -> np.ndarray:
     buf = np.zeros((max(n.value, 1), width[0]), dtype=width[1])
     _check(load().mesh_stage(ctx, mesh, stage, buf.ctypes.data, n.value, ctypes.byref(n)))
     return buf[: n.value]
+
+
+def mesh_quality(ctx: int, mesh: int) -> dict:
+    """Quality measures of a finished mesh, computed on the device."""
+    q = sbmt_quality()
+    _check(load().mesh_quality(ctx, mesh, ctypes.byref(q)))
+    out = {k: getattr(q, k) for k, _ in sbmt_quality._fields_ if k != "angle_hist"}
+    out["angle_hist"] = [int(x) for x in q.angle_hist]
+    return out
 
 
 def mesh_profile(ctx: int, enable: bool) -> None:

@@ -568,17 +568,25 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   }
 }
 
-// lattice vertex coordinates: one block per vertex row
-__global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy) {
+// lattice vertex coordinates.  Vertex v(i, j) has x = (ox + 3p m) / S with
+// m = 2i + j, so every row reads its x values from one table over the m the
+// image uses (the double arithmetic is done once per m, not per vertex;
+// this part has little FP64 throughput); one block per vertex row.
+__global__ void __launch_bounds__(256) k_lattice_tab(GridP g, double* tab, i64 m0, i64 nm) {
+  const double invS = 1.0 / (double)g.S;
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += (i64)gridDim.x * blockDim.x)
+    tab[k] = (double)(g.ox + 3 * g.p * (m0 + k)) * invS;
+}
+
+__global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy, const double* tab, i64 m0) {
   const int r = blockIdx.x;
   const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
-  const double invS = 1.0 / (double)g.S;
-  const double y = zdouble(zq(g.oy, 3 * g.p * j)) * invS;
-  const i64 x0 = g.ox + 3 * g.p * (2 * lo + j), dx = 6 * g.p;
+  const double y = zdouble(zq(g.oy, 3 * g.p * j)) * (1.0 / (double)g.S);
+  const double* tx = tab + (2 * lo + j - m0);
   double2* out = reinterpret_cast<double2*>(xy) + base;
   for (i64 k = threadIdx.x; k < n; k += blockDim.x) {
     double2 v;
-    v.x = (double)(x0 + dx * k) * invS;
+    v.x = tx[2 * k];
     v.y = y;
     out[k] = v;
   }
@@ -611,10 +619,11 @@ int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, 
   return 1;
 }
 
-int launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st) {
+int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st) {
   if (g.nverts == 0) return 0;
-  k_lattice_xy<<<g.nvrows, 256, 0, st>>>(g, xy);
-  return 1;
+  k_lattice_tab<<<(unsigned)std::min<i64>((nm + 255) / 256, 1024), 256, 0, st>>>(g, tab, m0, nm);
+  k_lattice_xy<<<g.nvrows, 256, 0, st>>>(g, xy, tab, m0);
+  return 2;
 }
 
 }  // namespace sbmt

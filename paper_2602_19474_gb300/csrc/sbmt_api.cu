@@ -2,6 +2,7 @@
 // tables and the ordered launch of the hot-path kernels on one stream.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -603,7 +604,16 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
                              (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, st));
   TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist,
                                nwlist, m->tri, m->label, m->code, m->xy, err, st));
-  TRACE(KN_XY, launch_lattice_xy(g, m->xy, st));
+  // x of lattice vertex v(i, j) is indexed by m = 2i + j
+  i64 m_lo = 0, m_hi = -1;
+  for (i64 r = 0; r < nvr; ++r) {
+    const i64 a = 2 * tb.vlo[r] + tb.vj0 + r, b = 2 * tb.vhi[r] + tb.vj0 + r;
+    if (r == 0 || a < m_lo) m_lo = a;
+    if (r == 0 || b > m_hi) m_hi = b;
+  }
+  double* xtab;
+  if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
+  TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(m->h_info + 1, nrec, sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -812,6 +822,99 @@ int mesh_destroy(sbmt_ctx* ctx) {
     for (u32* slab : ctx->pinned_slabs) cudaFreeHost(slab);
   }
   delete ctx;
+  return SBMT_OK;
+}
+
+int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out) {
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  MeshRec* m;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    auto it = ctx->meshes.find(mesh);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+    m = it->second;
+  }
+  CK(cudaSetDevice(ctx->device));
+  std::memset(out, 0, sizeof *out);
+  const u64 T = (u64)m->nt;
+  out->triangles = (int64_t)T;
+  if (T == 0) return SBMT_OK;
+  Lane* lane = &ctx->main;
+  cudaStream_t st = lane->stream;
+  CK(cudaStreamWaitEvent(st, m->done, 0));
+  constexpr int NBLK = 152 * 8;
+  arena_begin(lane);
+  float* ar;
+  unsigned long long* mm;
+  double* part;
+  u32* hist;
+  int rc;
+  if ((rc = aalloc(lane, &ar, T)) || (rc = aalloc(lane, &mm, 8)) || (rc = aalloc(lane, &part, 2 * NBLK)) ||
+      (rc = aalloc(lane, &hist, 32 + 2 * 4096))) {
+    arena_end(lane);
+    return rc;
+  }
+  unsigned long long* cnt = mm + 3;
+  u32* h0 = hist + 32;
+  u32* h1 = h0 + 4096;
+  const unsigned long long init[5] = {0x7FF0000000000000ull, 0x7FF0000000000000ull, 0ull, 0ull, 0ull};
+  std::vector<double> hpart(2 * NBLK);
+  unsigned long long hmm[5];
+  u32 hh[32];
+  CK(cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(hist, 0, 32 * sizeof(u32), st));
+  launch_quality(m->xy, m->tri, T, ar, mm, cnt, part, NBLK, hist, st);
+  CK(cudaMemcpyAsync(hmm, mm, sizeof hmm, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hpart.data(), part, hpart.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  auto dbl = [](unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+  };
+  out->min_angle_deg = dbl(hmm[0]), out->min_area = dbl(hmm[1]), out->ar_max = dbl(hmm[2]);
+  out->slivers = (int64_t)hmm[3], out->equilateral = (int64_t)hmm[4];
+  double sa = 0.0, sa2 = 0.0;
+  for (int b = 0; b < NBLK; ++b) sa += hpart[2 * b], sa2 += hpart[2 * b + 1];
+  out->area_mean = sa / (double)T;
+  out->area_var = std::max(0.0, sa2 / (double)T - out->area_mean * out->area_mean);
+  for (int k = 0; k < 30; ++k) out->angle_hist[k] = hh[k];
+  // nearest-rank percentiles: a radix select over the float bits in three
+  // levels, both ranks at once
+  u64 rank[2] = {(T + 1) / 2, (u64)std::ceil(0.95 * (double)T)};
+  rank[1] = std::max<u64>(1, std::min<u64>(rank[1], T));
+  u32 pre[2] = {0, 0};
+  const int lo_of[3] = {20, 10, 0}, width_of[3] = {12, 10, 10};
+  std::vector<u32> a0(4096), a1(4096);
+  for (int lev = 0; lev < 3; ++lev) {
+    const int lo = lo_of[lev], width = width_of[lev], nb = 1 << width;
+    CK(cudaMemsetAsync(h0, 0, 2 * 4096 * sizeof(u32), st));
+    launch_select_hist(ar, T, lo, width, pre[0], pre[1], lo + width, h0, h1, st);
+    CK(cudaMemcpyAsync(a0.data(), h0, nb * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(a1.data(), h1, nb * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < 2; ++r) {
+      const std::vector<u32>& h = r == 0 ? a0 : a1;
+      u64 cum = 0;
+      int bin = nb - 1;
+      for (int k = 0; k < nb; ++k) {
+        if (cum + h[k] >= rank[r]) {
+          bin = k;
+          break;
+        }
+        cum += h[k];
+      }
+      rank[r] -= cum;
+      pre[r] = (pre[r] << width) | (u32)bin;
+    }
+  }
+  float f[2];
+  std::memcpy(&f[0], &pre[0], 4);
+  std::memcpy(&f[1], &pre[1], 4);
+  out->ar_median = f[0], out->ar_p95 = f[1];
+  arena_end(lane);
   return SBMT_OK;
 }
 

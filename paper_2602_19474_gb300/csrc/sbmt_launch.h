@@ -74,7 +74,16 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
                   unsigned short* code, double* xy, u32* err, cudaStream_t st);
 
-// coordinates of the lattice vertices
-int launch_lattice_xy(const GridP& g, double* xy, cudaStream_t st);
+// quality measures: per-triangle pass (mm: min angle, min area, max AR as
+// double bits; cnt: slivers, equilateral; part: per-block area sums; ar:
+// AR per triangle as float) and one level of the radix select of two ranks
+int launch_quality(const double* xy, const int* tri, u64 T, float* ar, unsigned long long* mm,
+                   unsigned long long* cnt, double* part, int nblocks, u32* hist, cudaStream_t st);
+int launch_select_hist(const float* v, u64 T, int lo, int width, u32 pre0, u32 pre1, int above, u32* h0, u32* h1,
+                       cudaStream_t st);
+
+// coordinates of the lattice vertices; tab: scratch of nm doubles for the x
+// values (ox + 3p m) / S, m0 <= m < m0 + nm covering 2i + j of every vertex
+int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st);
 
 }  // namespace sbmt

@@ -36,6 +36,39 @@ def disk(size: int = 64, cx: float = 32, cy: float = 32, r: float = 20) -> np.nd
     return (((xx - cx) ** 2 + (yy - cy) ** 2) <= r * r).astype(np.uint8)
 
 
+def star(size: int = 256, points: int = 5, r_out: float = 100.0, r_in: float = 40.0, rot: float = 0.3) -> np.ndarray:
+    """Filled five-pointed star (a stand-in for the paper's synthetic star):
+    foreground where the pixel centre lies inside the polygon whose vertices
+    alternate between radius r_out and r_in about the image centre."""
+    c = (size - 1) / 2.0
+    ang = rot + np.arange(2 * points) * math.pi / points
+    rad = np.where(np.arange(2 * points) % 2 == 0, r_out, r_in)
+    px, py = c + rad * np.cos(ang), c + rad * np.sin(ang)
+    yy, xx = np.mgrid[0:size, 0:size].astype(float)
+    inside = np.zeros((size, size), bool)
+    j = len(px) - 1
+    for i in range(len(px)):  # even-odd rule over the polygon's edges
+        cond = (py[i] > yy) != (py[j] > yy)
+        xint = (px[j] - px[i]) * (yy - py[i]) / np.where(py[j] != py[i], py[j] - py[i], 1.0) + px[i]
+        inside ^= cond & (xx < xint)
+        j = i
+    return inside.astype(np.uint8)
+
+
+def blob(size: int = 256, seed_k: int = 6, n: int = 7) -> np.ndarray:
+    """A smooth blob (a stand-in for the paper's droplet): the union of n
+    overlapping disks with seeded centres near the image centre."""
+    rng = rng_for(seed_k)
+    c = size / 2.0
+    yy, xx = np.mgrid[0:size, 0:size].astype(float)
+    img = np.zeros((size, size), bool)
+    for _ in range(n):
+        cx, cy = c + rng.uniform(-0.2, 0.2) * size, c + rng.uniform(-0.2, 0.2) * size
+        r = rng.uniform(0.12, 0.25) * size
+        img |= (xx - cx) ** 2 + (yy - cy) ** 2 <= r * r
+    return img.astype(np.uint8)
+
+
 def ellipses(size: int = 2048, n: int = 200, seed_k: int = 2, amin: float = 10.0, amax: float = 150.0) -> np.ndarray:
     """Union of n filled ellipses: centres uniform over the image, semi-axes
     uniform in [amin, amax], rotation uniform in [0, pi)."""
