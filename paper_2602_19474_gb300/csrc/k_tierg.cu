@@ -13,9 +13,10 @@
 // boundary piece.  The faces are the 3-cycles with no vertex inside, listed
 // with the smallest local index first, counter-clockwise, in sorted order.
 //
-// Cells with at most TN vertices (all of them at h = 2 px) run one thread
-// each; larger cells run one warp each with the state in shared memory.  The
-// same templated code serves both (G = 1 or 32 lanes).
+// The cells are first ordered by vertex count, largest first.  Cells with at
+// most TN vertices (nearly all of them at h = 2 px) run one thread each, on
+// per-pair vertex sets (orientations decided once per triple); larger cells
+// run one warp each with the state in shared memory.
 #include <type_traits>
 
 #include "sbmt_cell.cuh"
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
   const u32 total = *nwlist;
   for (u32 item = blockIdx.x * WWARPS + w; item < total; item += gridDim.x * WWARPS) {
     const CutRec rec = recs[wlist[item]];
-    const CellGeo cg = cell_geo(g, rec.cell, cell_row(g, rec.cell));
+    const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
     if (lane == 0) build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
     __syncwarp();
     if (!s.ok) {

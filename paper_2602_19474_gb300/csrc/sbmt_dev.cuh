@@ -173,16 +173,6 @@ SBMT_DEV u32 cell_id(const GridP& g, i64 c, i64 j) {
   int r = (int)(j - g.j0);
   return (u32)(g.cbase[r] + (c - g.clo[r]));
 }
-// strip row of a cell id (binary search over the row bases)
-SBMT_DEV int cell_row(const GridP& g, u32 cid) {
-  int lo = 0, hi = g.nrows - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (g.cbase[mid] <= (i64)cid) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 // lattice indices of corners A, B, C of cell c in strip j; A is the corner
 // with least (y, x), then counter-clockwise
 SBMT_DEV void cell_corners(i64 c, i64 j, i64* ci, i64* cj) {
