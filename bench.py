@@ -114,8 +114,8 @@ def load_serving_pool() -> list:
 
 # stage -> source files whose hash the committed DRAM capture records
 STAGE_SOURCES = {
-    "k_corner_bits": ["k_extract.cu"], "k_segments": ["k_extract.cu"], "k_walk_count": ["k_traverse.cu"],
-    "k_walk_emit": ["k_traverse.cu"], "k_rank": ["k_traverse.cu"], "k_sort": ["k_cells.cu"],
+    "k_corner_bits": ["k_extract.cu"], "k_segments": ["k_extract.cu"], "k_seg_count": ["k_traverse.cu"],
+    "k_walk": ["k_traverse.cu"], "k_rank": ["k_traverse.cu"], "k_sort": ["k_cells.cu"],
     "k_cutcells": ["k_cells.cu"], "k_emit": ["k_cells.cu"], "k_tierg": ["k_tierg.cu"],
     "k_lattice_xy": ["k_cells.cu"], "k_scan": ["k_scan.cu"],
 }

@@ -164,14 +164,13 @@ __global__ void k_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cst
   }
 }
 
-// Chunked walk over the global pair index range.  Count pass (EMIT false):
-// histogram of pairs per cell bucket and of crossings per event bucket.
-// Emit pass: each crossing's event at its fixed index (segment event base
-// + k), its index into the event bucket, each pair into its cell bucket.
-template <bool EMIT>
+// Chunked walk over the global pair index range, done once: every pair is
+// written at its global index (raw), every event at its fixed index (segment
+// event base + k), and the pairs per cell bucket and events per event bucket
+// are counted (one atomic per run of equal buckets).  k_scatter then places
+// pairs and event indices into their buckets.
 __global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u32* pbase, const u32* cstart,
-                                              u32 NP, u32* pbk, u32* ebk, Pair* pairs, Event* ev, u32* eidx,
-                                              u32* err) {
+                                              u32 NP, u32* pbk, u32* ebk, Pair* raw, Event* ev, u32* err) {
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   const u64 p0 = t * CH;
   if (p0 >= NP) return;
@@ -202,32 +201,37 @@ __global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u3
         return;
       }
       const u32 e = 3u * vid(g, ei, ej) + (u32)fam;
-      if (EMIT) {
-        ev[ebase + k] = Event{e, s, 0u, 0u, (int)px.a, (int)px.b, (int)py.a, (int)py.b};
-        eidx[warp_inc(ebk, e >> EB_LOG)] = ebase + k;
-      } else {
-        const u32 b = e >> EB_LOG;
-        if (b != eb) {
-          if (en) atomicAdd(ebk + eb, en);
-          eb = b, en = 0;
-        }
-        ++en;
+      ev[ebase + k] = Event{e, s, 0u, 0u, (int)px.a, (int)px.b, (int)py.a, (int)py.b};
+      const u32 b = e >> EB_LOG;
+      if (b != eb) {
+        if (en) atomicAdd(ebk + eb, en);
+        eb = b, en = 0;
       }
+      ++en;
     }
-    if (EMIT) {
-      pairs[warp_inc(pbk, cid >> CB_LOG)] = Pair{cid, s, k > 0 ? ebase + k - 1 : NONE, k < w.ncross ? ebase + k : NONE};
-    } else {
-      const u32 b = cid >> CB_LOG;
-      if (b != pb) {
-        if (pn) atomicAdd(pbk + pb, pn);
-        pb = b, pn = 0;
-      }
-      ++pn;
+    raw[p] = Pair{cid, s, k > 0 ? ebase + k - 1 : NONE, k < w.ncross ? ebase + k : NONE};
+    const u32 b = cid >> CB_LOG;
+    if (b != pb) {
+      if (pn) atomicAdd(pbk + pb, pn);
+      pb = b, pn = 0;
     }
+    ++pn;
   }
-  if (!EMIT) {
-    if (pn) atomicAdd(pbk + pb, pn);
-    if (en) atomicAdd(ebk + eb, en);
+  if (pn) atomicAdd(pbk + pb, pn);
+  if (en) atomicAdd(ebk + eb, en);
+}
+
+// pairs into their cell buckets and event indices into their event buckets
+// (pcur / ecur: bucket cursors, the exclusive scans of the counts)
+__global__ void __launch_bounds__(256) k_scatter(const Pair* raw, u32 NP, const Event* ev, u32 NE, u32* pcur,
+                                                 u32* ecur, Pair* pairs, u32* eidx) {
+  const u32 n = max(NP, NE);
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < NP) {
+      const Pair pr = raw[i];
+      pairs[warp_inc(pcur, pr.cell >> CB_LOG)] = pr;
+    }
+    if (i < NE) eidx[warp_inc(ecur, ev[i].edge >> EB_LOG)] = i;
   }
 }
 
@@ -332,15 +336,21 @@ int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cu
 
 size_t walk_chunks(u32 NP) { return (NP + CH - 1) / CH; }
 
-int launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
-                 u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st) {
+int launch_walk(const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk, u32* ebk,
+                Pair* raw, Event* events, u32* err, cudaStream_t st) {
   const u64 threads = walk_chunks(NP);
   if (threads == 0) return 0;
   const unsigned grd = (unsigned)((threads + 255) / 256);
-  if (emit)
-    k_walk<true><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
-  else
-    k_walk<false><<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, pairs, events, eidx, err);
+  k_walk<<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, raw, events, err);
+  return 1;
+}
+
+int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pcur, u32* ecur, Pair* pairs,
+                   u32* eidx, cudaStream_t st) {
+  const u32 n = std::max(NP, NE);
+  if (n == 0) return 0;
+  const unsigned grd = (unsigned)std::min<u64>((n + 255) / 256, 152u * 16u);
+  k_scatter<<<grd, 256, 0, st>>>(raw, NP, events, NE, pcur, ecur, pairs, eidx);
   return 1;
 }
 

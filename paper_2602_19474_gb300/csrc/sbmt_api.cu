@@ -153,8 +153,8 @@ enum {
   KN_XY,
   KN_COUNT
 };
-const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_walk_count", "k_scan",
-                                            "k_walk_emit", "k_rank", "k_sort", "k_cutcells", "k_emit",
+const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_seg_count", "k_scan",
+                                            "k_walk", "k_rank", "k_sort", "k_cutcells", "k_emit",
                                             "k_tierg", "k_lattice_xy"};
 
 // One stream of work: the context's own stream, or one of the extra streams
@@ -547,23 +547,27 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if ((rc = aalloc(lane, &ecur, nbe + 1))) return bail(rc);
   CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
   CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
-  u32* cstart;
-  if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
-  TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
-  TRACE(KN_TCOUNT, launch_walk(false, g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, nullptr, nullptr, nullptr, err, st));
-  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
-  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
-  CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
   u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx, *gcnt;
   TStage* stg;
-
+  u32* cstart;
+  if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
   if ((rc = aalloc(lane, &pairs, NP))) return bail(rc);
   if ((rc = aalloc(lane, &sorted, NP))) return bail(rc);
   if ((rc = m->keep ? dalloc(lane, &ev, NE, m->scratch) : aalloc(lane, &ev, NE))) return bail(rc);
+  if ((rc = aalloc(lane, &eidx, NE))) return bail(rc);
+  // K2: one walk (pairs in their global order, in the sorted buffer for now;
+  // events at their fixed indices; bucket counts), then the bucket scans and
+  // the scatter into buckets
+  TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
+  TRACE(KN_TEMIT, launch_walk(g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, sorted, ev, err, st));
+  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
+  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
+  CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  TRACE(KN_TEMIT, launch_scatter(sorted, (u32)NP, ev, (u32)NE, pcur, ecur, pairs, eidx, st));
   if ((rc = m->keep ? dalloc(lane, &recs, NP, m->scratch) : aalloc(lane, &recs, NP))) return bail(rc);
   if ((rc = m->keep ? dalloc(lane, &bcut, nbc + 1, m->scratch) : aalloc(lane, &bcut, nbc + 1))) return bail(rc);
   if ((rc = m->keep ? dalloc(lane, &bbase, nbc + 1, m->scratch) : aalloc(lane, &bbase, nbc + 1))) return bail(rc);
@@ -577,7 +581,6 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &gcnt, 3 * (TIERG_TN + 2)))) return bail(rc);
   if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
-  if ((rc = aalloc(lane, &eidx, NE))) return bail(rc);
   // outputs
   const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
   const size_t off_tri = (bxy + 255) & ~(size_t)255, off_lab = (off_tri + btri + 255) & ~(size_t)255;
@@ -590,8 +593,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   m->code = (unsigned short*)((char*)m->out_block + off_code);
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
-  // K2 emit, registry, K3, scans, K4, K4-G, lattice coordinates
-  TRACE(KN_TEMIT, launch_walk(true, g, segs, pbase, cstart, (u32)NP, pcur, ecur, pairs, ev, eidx, err, st));
+  // registry, K3, scans, K4, K4-G, lattice coordinates
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
   CK(cudaMemsetAsync(bextra, 0, 2 * ((size_t)nbc + 1) * sizeof(u32), st));
   CK(cudaMemsetAsync(gcnt, 0, 3 * (TIERG_TN + 2) * sizeof(u32), st));

@@ -21,16 +21,19 @@ int launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H
 // closed form; slots beyond the segment count get 0.
 int launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
 
-// K2 walks, chunked over the global pair index (pbase = exclusive scan of
+// K2 walk, chunked over the global pair index (pbase = exclusive scan of
 // npairs; cstart = first segment of every chunk, from launch_chunk_map over
-// walk_chunks(NP) chunks).  Count pass (emit = false): pairs per cell bucket
-// into pbk and crossings per event bucket into ebk.  Emit pass: pbk / ebk are
-// bucket cursors; writes every event at its fixed index, its index into eidx,
-// and every pair into its cell bucket.
+// walk_chunks(NP) chunks): every pair at its global index in raw, every event
+// at its fixed index, pairs per cell bucket counted into pbk and events per
+// event bucket into ebk.  launch_scatter then moves the pairs into their cell
+// buckets and the event indices into their event buckets (pcur / ecur: the
+// buckets' cursors, starting at the exclusive scans of pbk / ebk).
 size_t walk_chunks(u32 NP);
 int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st);
-int launch_walk(bool emit, const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
-                 u32* ebk, Pair* pairs, Event* events, u32* eidx, u32* err, cudaStream_t st);
+int launch_walk(const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk, u32* ebk,
+                Pair* raw, Event* events, u32* err, cudaStream_t st);
+int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pcur, u32* ecur, Pair* pairs,
+                   u32* eidx, cudaStream_t st);
 
 // frozen registry: rank the events of each event bucket (listed in eidx) by
 // (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
