@@ -149,6 +149,23 @@ def committed_traffic(workload: str, stage: str):
     return None
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank processes the same amount)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -315,12 +332,8 @@ def our_arm(args, rank: int, world: int, dist):
     prof = sb.mesh_profile_read(ctx, reset=True)
     sb.mesh_profile(ctx, False)
     T = v.n_triangles
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * T / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = job_rate(world, T, ms_max)
 
     # end to end: host image from pinned memory in, whole mesh back to pinned host memory
     pin_img = torch.empty(img.shape, dtype=torch.int16 if img.dtype == np.uint16 else torch.uint8).pin_memory()
@@ -353,12 +366,8 @@ def our_arm(args, rank: int, world: int, dist):
     e1.record(st)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * T / (ms_e2e * 1e-3)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
+    e2e_value = job_rate(world, T, ms_e2e)
     h2d = img.nbytes
     d2h = 16 * v.n_vertices + 16 * T
 
@@ -464,12 +473,7 @@ def batch_arm(args, rank: int, world: int, dist):
             tris = fn()[0]
         e1.record(st)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, tris
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev), tris
 
     def barrier_sync():
         if dist is not None:
@@ -493,7 +497,7 @@ def batch_arm(args, rank: int, world: int, dist):
     peak, peak_kind = measured_peak()
     path_bytes = float(px) + 16.0 * T + 16.0 * V
     out = {
-        "metric": "output triangles/sec", "value": world * T / (ms * 1e-3), "unit": "triangles/s",
+        "metric": "output triangles/sec", "value": job_rate(world, T, ms), "unit": "triangles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload + ": " + b["desc"], "images": len(imgs), "pixels": px,
