@@ -70,7 +70,51 @@ __global__ void __launch_bounds__(256) k_tile_scan(const u32* in, int stride, u3
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) out[n] = run;
 }
 
+// one block of 1024 threads per array: exclusive scans of up to two arrays
+// of at most SCAN_ONE values each (total at out[n]), the result written to
+// out and, when given, to out2 as well (bucket cursors)
+struct ScanJob {
+  const u32* in;
+  u32* out;
+  u32* out2;
+  u32 n;
+};
+__global__ void __launch_bounds__(1024) k_scan_jobs(ScanJob a, ScanJob b) {
+  __shared__ u32 sh[1024];
+  const ScanJob j = blockIdx.x == 0 ? a : b;
+  const u32 t = threadIdx.x, n = j.n;
+  const u32 chunk = (n + 1023) / 1024;
+  const u32 lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  u32 s = 0;
+  for (u32 i = lo; i < hi; ++i) s += j.in[i];
+  sh[t] = s;
+  __syncthreads();
+  for (u32 o = 1; o < 1024; o <<= 1) {
+    const u32 v = t >= o ? sh[t - o] : 0u;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  u32 run = sh[t] - s;
+  for (u32 i = lo; i < hi; ++i) {
+    const u32 v = j.in[i];
+    j.out[i] = run;
+    if (j.out2) j.out2[i] = run;
+    run += v;
+  }
+  if (t == 1023) {
+    j.out[n] = sh[1023];
+    if (j.out2) j.out2[n] = sh[1023];
+  }
+}
+
 }  // namespace
+
+int launch_scan_pair(const u32* in_a, u32* out_a, u32* out2_a, u32 n_a, const u32* in_b, u32* out_b, u32* out2_b,
+                     u32 n_b, cudaStream_t st) {
+  k_scan_jobs<<<in_b ? 2 : 1, 1024, 0, st>>>(ScanJob{in_a, out_a, out2_a, n_a}, ScanJob{in_b, out_b, out2_b, n_b});
+  return 1;
+}
 
 size_t scan_scratch_words(u32 n) { return n <= 16384 ? 0 : (size_t)((n + TILE - 1) / TILE) + 1; }
 

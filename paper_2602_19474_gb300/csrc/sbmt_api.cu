@@ -490,13 +490,26 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   g.lrow = (const int*)(dt + 3 * nrows + 3 * nvr);
   g.ncells = tb.ncells, g.nverts = tb.nverts;
 
-  // counters: [0] nvtx (u64), [1] totals pairs, [2] totals events, then u32s
-  unsigned long long* cnt64;
-  if ((rc = aalloc(lane, &cnt64, 8))) return bail(rc);
-  u32* cnt32 = (u32*)(cnt64 + 4);  // nseg, err, nglist, ngtri, nwlist
-  CK(cudaMemsetAsync(cnt64, 0, 8 * sizeof(unsigned long long), st));
-  u32 *nseg = cnt32 + 0, *err = cnt32 + 1, *nglist = cnt32 + 2, *ngtri = cnt32 + 3, *nwlist = cnt32 + 4;
-  u32* nrec = cnt32 + 5;
+  // every counter of the call, zeroed by one memset: the vertex count (u64),
+  // the u32 counters (err, cut cells, Tier-G cells and their triangles next
+  // to each other: the mesh's status words), the bucket counts of pairs and
+  // events, the buckets' extra triangles and inside vertices, the Tier-G
+  // per-size counts
+  const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
+  const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
+  const size_t zwords = 16 + (nbc + 1) + (nbe + 1) + 2 * ((size_t)nbc + 1) + 3 * (TIERG_TN + 2);
+  u32* zero;
+  if ((rc = aalloc(lane, &zero, zwords))) return bail(rc);
+  CK(cudaMemsetAsync(zero, 0, zwords * sizeof(u32), st));
+  unsigned long long* cnt64 = (unsigned long long*)zero;
+  u32* cnt32 = zero + 8;
+  u32 *nseg = cnt32 + 0, *nwlist = cnt32 + 1, *err = cnt32 + 2, *nrec = cnt32 + 3, *nglist = cnt32 + 4,
+      *ngtri = cnt32 + 5;
+  u32* pcnt = zero + 16;
+  u32* ecnt = pcnt + nbc + 1;
+  u32* bextra = ecnt + nbe + 1;
+  u32* bchain = bextra + nbc + 1;
+  u32* gcnt = bchain + nbc + 1;
 
   // K1a
   const int W = g.W, H = g.H;
@@ -516,8 +529,6 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   TRACE(KN_SEG, launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st));
   // K2: pairs per segment in closed form and their scan -> fixed pair and
   // event indices of every segment
-  const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
-  const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
   u32 *npairs, *pbase, *sscr;
   const size_t scr_words = std::max({scan_scratch_words(seg_cap), scan_scratch_words(nbc), scan_scratch_words(nbe)});
   if ((rc = aalloc(lane, &npairs, seg_cap))) return bail(rc);
@@ -529,7 +540,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   CK(cudaMemcpyAsync(h32, cnt32, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h32 + 3, pbase + seg_cap, sizeof(u32), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (h32[1]) return bail(fail(SBMT_EINTERNAL, "device check failed during extraction (0x%x)", h32[1]));
+  if (h32[2]) return bail(fail(SBMT_EINTERNAL, "device check failed during extraction (0x%x)", h32[2]));
   const u32 nsegs = h32[0];
   if (nsegs > seg_cap) return bail(fail(SBMT_EINTERNAL, "segment count %u above bound %u", nsegs, seg_cap));
   const u64 NP = h32[3], NE = NP - nsegs;
@@ -538,19 +549,15 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if (V >= (1ull << 31) || T >= (1ull << 31) || NP >= (1ull << 31))
     return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T));
   // buckets: pairs by cell id, events by grid-edge id
-  u32 *pcnt, *ecnt, *poff, *eoff, *pcur, *ecur;
-  if ((rc = aalloc(lane, &pcnt, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &ecnt, nbe + 1))) return bail(rc);
+  u32 *poff, *eoff, *pcur, *ecur;
   if ((rc = aalloc(lane, &poff, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &eoff, nbe + 1))) return bail(rc);
   if ((rc = aalloc(lane, &pcur, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &ecur, nbe + 1))) return bail(rc);
-  CK(cudaMemsetAsync(pcnt, 0, (nbc + 1) * sizeof(u32), st));
-  CK(cudaMemsetAsync(ecnt, 0, (nbe + 1) * sizeof(u32), st));
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bcut, *bbase, *bextra, *bchain, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx, *gcnt;
+  u32 *bcut, *bbase, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx;
   TStage* stg;
   u32* cstart;
   if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
@@ -563,23 +570,24 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   // the scatter into buckets
   TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
   TRACE(KN_TEMIT, launch_walk(g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, sorted, ev, err, st));
-  TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
-  TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
-  CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  if (nbc <= SCAN_ONE && nbe <= SCAN_ONE) {
+    TRACE(KN_SCAN, launch_scan_pair(pcnt, poff, pcur, nbc, ecnt, eoff, ecur, nbe, st));
+  } else {
+    TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
+    TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
+    CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
+  }
   TRACE(KN_TEMIT, launch_scatter(sorted, (u32)NP, ev, (u32)NE, pcur, ecur, pairs, eidx, st));
   if ((rc = m->keep ? dalloc(lane, &recs, NP, m->scratch) : aalloc(lane, &recs, NP))) return bail(rc);
   if ((rc = m->keep ? dalloc(lane, &bcut, nbc + 1, m->scratch) : aalloc(lane, &bcut, nbc + 1))) return bail(rc);
   if ((rc = m->keep ? dalloc(lane, &bbase, nbc + 1, m->scratch) : aalloc(lane, &bbase, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &bextra, 2 * ((size_t)nbc + 1)))) return bail(rc);
-  bchain = bextra + nbc + 1;
   if ((rc = aalloc(lane, &extra_scan, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &chain_scan, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &stg, NP))) return bail(rc);
   if ((rc = aalloc(lane, &glist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &wlist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &gcnt, 3 * (TIERG_TN + 2)))) return bail(rc);
   if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
   // outputs
   const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
@@ -595,13 +603,15 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // registry, K3, scans, K4, K4-G, lattice coordinates
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
-  CK(cudaMemsetAsync(bextra, 0, 2 * ((size_t)nbc + 1) * sizeof(u32), st));
-  CK(cudaMemsetAsync(gcnt, 0, 3 * (TIERG_TN + 2) * sizeof(u32), st));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
                                      err, st));
-  TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
-  TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
+  if (nbc <= SCAN_ONE) {
+    TRACE(KN_SCAN, launch_scan_pair(bextra, extra_scan, nullptr, nbc, bchain, chain_scan, nullptr, nbc, st));
+  } else {
+    TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
+    TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
+  }
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
                              (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, st));
   TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist,
@@ -617,9 +627,8 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
   TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(m->h_info + 0, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(m->h_info + 1, nrec, sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(m->h_info + 2, nglist, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  // the status words: err, cut cells, Tier-G cells, Tier-G triangles
+  CK(cudaMemcpyAsync(m->h_info, err, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
   if (m->keep) {
     // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
     m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bcut = bcut;

@@ -57,6 +57,12 @@ int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dty
 // entries, out[n] = total); inputs above 65536 values need scratch of
 // scan_scratch_words(n) words
 size_t scan_scratch_words(u32 n);
+// exclusive scans of one or two arrays (in_b = nullptr for one) of at most
+// SCAN_ONE values each in one launch, the results also copied to out2 when
+// given (nullptr otherwise)
+constexpr u32 SCAN_ONE = 1u << 14;
+int launch_scan_pair(const u32* in_a, u32* out_a, u32* out2_a, u32 n_a, const u32* in_b, u32* out_b, u32* out2_b,
+                     u32 n_b, cudaStream_t st);
 int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
 
 // K4: per cell bucket, emit every uncut cell's base triangle and every
