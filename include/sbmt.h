@@ -54,7 +54,7 @@ typedef uint64_t sbmt_mesh;
 
 enum { SBMT_U8 = 1, SBMT_U16 = 2 };
 enum { SBMT_PLAIN = 0, SBMT_PREPROCESS = 1 };
-enum { SBMT_EXPLICIT = 0 };
+enum { SBMT_EXPLICIT = 0, SBMT_COMPACT = 1 };
 enum { SBMT_KEEP_STAGES = 1 }; /* sbmt_params.flags: keep intermediate arrays for mesh_stage */
 
 /* A label image.  width, height in 1..32768; pitch_bytes >= width * dtype
@@ -75,8 +75,10 @@ typedef struct {
  * pixel line and no pixel corner on a grid edge, so every Alg. 1 event is a
  * proper crossing; other parameters return SBMT_EINVAL.  mode must be
  * SBMT_PLAIN (the thresholds a, b, c of Alg. 3 are reserved for
- * SBMT_PREPROCESS, which returns SBMT_EPROTO); format must be
- * SBMT_EXPLICIT. */
+ * SBMT_PREPROCESS, which returns SBMT_EPROTO).  format selects the storage
+ * of the mesh (see sbmt_mesh_view): SBMT_EXPLICIT lists every triangle;
+ * SBMT_COMPACT keeps the untouched base mesh implicit -- the paper's
+ * "preserve the base mesh" (Sec. 1, Sec. 3.3) as a storage format. */
 typedef struct {
   int32_t h_num, h_den;
   int32_t origin2x, origin2y;
@@ -111,6 +113,26 @@ typedef struct {
   const uint16_t* label;
   const uint16_t* code;
   int32_t status; /* SBMT_OK, or the error the device work reported */
+  /* SBMT_COMPACT meshes (format = SBMT_COMPACT; NULL / 0 otherwise):
+   *  xy         2 * (n_vertices - n_lattice_vertices) doubles: the vertices
+   *             after the lattice (ids n_lattice_vertices and up); lattice
+   *             vertex coordinates are v(i, j) = o + h (i + j/2, sqrt3/2 j);
+   *  cell_label per base cell: label of its triangle (A, B, C) when the cell
+   *             is uncut (cell_code 0), 0xFFFF when cut;
+   *  cell_code  per base cell: its pattern code (0 = uncut);
+   *  patch_cell the cut cell ids, increasing (n_cut_cells of them);
+   *  patch_off  n_cut_cells + 1 offsets: cut cell k's triangles are patch
+   *             triangles patch_off[k] .. patch_off[k + 1] - 1;
+   *  tri, label, code  the n_patch_triangles patch triangles, in cut-cell
+   *             order, as in the explicit format.
+   * Expanding them cell by cell (uncut cells emit (A, B, C)) gives the
+   * explicit mesh exactly. */
+  int32_t format;
+  int64_t n_patch_triangles;
+  const uint16_t* cell_label;
+  const uint16_t* cell_code;
+  const uint32_t* patch_cell;
+  const uint32_t* patch_off;
 } sbmt_mesh_view;
 
 /* Create a context on CUDA device `device`.  pool_bytes (0 = no limit) is
@@ -169,6 +191,7 @@ int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t
  *                 percentiles are nearest-rank (the ceil(p T)-th smallest)
  *                 of AR rounded to single precision, the maximum in double;
  *  angle_hist     smallest angles in 2-degree bins [0,2) ... [58,60].
+ * Needs a mesh in the SBMT_EXPLICIT format (SBMT_EINVAL otherwise).
  * Waits for the mesh; synchronises with the device a few times. */
 typedef struct {
   int64_t triangles;

@@ -32,7 +32,7 @@ SBMT_EINTERNAL = -8
 SBMT_ENOENT = -9
 SBMT_U8, SBMT_U16 = 1, 2
 SBMT_PLAIN, SBMT_PREPROCESS = 0, 1
-SBMT_EXPLICIT = 0
+SBMT_EXPLICIT, SBMT_COMPACT = 0, 1
 SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
@@ -57,7 +57,9 @@ class sbmt_mesh_view(ctypes.Structure):
                 ("n_events", ctypes.c_int64), ("n_inside_vertices", ctypes.c_int64),
                 ("n_lattice_vertices", ctypes.c_int64), ("n_tierG_triangles", ctypes.c_int64), ("xy", ctypes.c_void_p),
                 ("tri", ctypes.c_void_p), ("label", ctypes.c_void_p), ("code", ctypes.c_void_p),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("format", ctypes.c_int32), ("n_patch_triangles", ctypes.c_int64),
+                ("cell_label", ctypes.c_void_p), ("cell_code", ctypes.c_void_p), ("patch_cell", ctypes.c_void_p),
+                ("patch_off", ctypes.c_void_p)]
 
 
 class sbmt_quality(ctypes.Structure):
@@ -139,8 +141,8 @@ def _image(img) -> tuple[sbmt_image, object]:
 
 
 def _params(h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0, keep_stages: bool = False,
-            mode: int = SBMT_PLAIN) -> sbmt_params:
-    return sbmt_params(h_num, h_den, origin2x, origin2y, mode, 0.0, 0.0, 0.0, SBMT_EXPLICIT,
+            mode: int = SBMT_PLAIN, format: int = SBMT_EXPLICIT) -> sbmt_params:
+    return sbmt_params(h_num, h_den, origin2x, origin2y, mode, 0.0, 0.0, 0.0, format,
                        SBMT_KEEP_STAGES if keep_stages else 0)
 
 
@@ -154,22 +156,23 @@ def mesh_create(device: int = 0, pool_bytes: int = 0, stream: int | None = None)
 
 
 def mesh_bitmap(ctx: int, img, h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0,
-                keep_stages: bool = False, mode: int = SBMT_PLAIN) -> int:
+                keep_stages: bool = False, mode: int = SBMT_PLAIN, format: int = SBMT_EXPLICIT) -> int:
     im, keep = _image(img)
-    pr = _params(h_num, h_den, origin2x, origin2y, keep_stages, mode)
+    pr = _params(h_num, h_den, origin2x, origin2y, keep_stages, mode, format)
     out = ctypes.c_uint64()
     _check(load().mesh_bitmap(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
     del keep
     return out.value
 
 
-def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False) -> list[int]:
+def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False, format: int = SBMT_EXPLICIT) -> list[int]:
     n = len(imgs)
     ims, keeps = zip(*[_image(i) for i in imgs]) if n else ((), ())
     arr = (sbmt_image * max(n, 1))(*ims)
     hn = list(h_num) if isinstance(h_num, (list, tuple, np.ndarray)) else [h_num]
     hd = list(h_den) if isinstance(h_den, (list, tuple, np.ndarray)) else [h_den] * len(hn)
-    prs = (sbmt_params * len(hn))(*[_params(int(a), int(b), keep_stages=keep_stages) for a, b in zip(hn, hd)])
+    prs = (sbmt_params * len(hn))(*[_params(int(a), int(b), keep_stages=keep_stages, format=format)
+                                       for a, b in zip(hn, hd)])
     out = (ctypes.c_uint64 * max(n, 1))()
     _check(load().mesh_batch(ctx, arr, n, prs, len(hn), out))
     del keeps
@@ -242,24 +245,47 @@ def view_tensors(view: sbmt_mesh_view, owner=None) -> dict:
     """Zero-copy torch CUDA tensors of a finished mesh (valid until release)."""
     import torch
 
+    def dev(ptr, shape, typestr):
+        return torch.as_tensor(_CudaArray(ptr, shape, typestr, owner), device="cuda")
+
+    if view.format == SBMT_COMPACT:
+        V, T, C, K = view.n_vertices - view.n_lattice_vertices, view.n_patch_triangles, view.n_cells, view.n_cut_cells
+        return {
+            "xy": dev(view.xy, (V, 2), "<f8"),
+            "tri": dev(view.tri, (T, 3), "<i4"),
+            "label": dev(view.label, (T,), "<i2"),
+            "code": dev(view.code, (T,), "<i2"),
+            "cell_label": dev(view.cell_label, (C,), "<i2"),
+            "cell_code": dev(view.cell_code, (C,), "<i2"),
+            "patch_cell": dev(view.patch_cell, (K,), "<i4"),
+            "patch_off": dev(view.patch_off, (K + 1,), "<i4"),
+        }
     V, T = view.n_vertices, view.n_triangles
-    out = {
-        "xy": torch.as_tensor(_CudaArray(view.xy, (V, 2), "<f8", owner), device="cuda"),
-        "tri": torch.as_tensor(_CudaArray(view.tri, (T, 3), "<i4", owner), device="cuda"),
-        "label": torch.as_tensor(_CudaArray(view.label, (T,), "<i2", owner), device="cuda"),
-        "code": torch.as_tensor(_CudaArray(view.code, (T,), "<i2", owner), device="cuda"),
+    return {
+        "xy": dev(view.xy, (V, 2), "<f8"),
+        "tri": dev(view.tri, (T, 3), "<i4"),
+        "label": dev(view.label, (T,), "<i2"),
+        "code": dev(view.code, (T,), "<i2"),
     }
-    return out
 
 
 def view_numpy(view: sbmt_mesh_view) -> dict:
     """Host copies of a finished mesh."""
     t = view_tensors(view)
-    return {
+    out = {
         "xy": t["xy"].cpu().numpy(),
         "tri": t["tri"].cpu().numpy(),
         "label": t["label"].cpu().numpy().view(np.uint16),
         "code": t["code"].cpu().numpy().view(np.uint16),
+    }
+    if view.format == SBMT_COMPACT:
+        out.update(cell_label=t["cell_label"].cpu().numpy().view(np.uint16),
+                   cell_code=t["cell_code"].cpu().numpy().view(np.uint16),
+                   patch_cell=t["patch_cell"].cpu().numpy().view(np.uint32),
+                   patch_off=t["patch_off"].cpu().numpy().view(np.uint32),
+                   n_triangles=view.n_triangles, n_vertices=view.n_vertices, n_patch_triangles=view.n_patch_triangles)
+    out.update({
+        "format": view.format,
         "n_cells": view.n_cells,
         "n_cut_cells": view.n_cut_cells,
         "n_tierG_cells": view.n_tierG_cells,
@@ -268,7 +294,8 @@ def view_numpy(view: sbmt_mesh_view) -> dict:
         "n_inside_vertices": view.n_inside_vertices,
         "n_lattice_vertices": view.n_lattice_vertices,
         "n_tierG_triangles": view.n_tierG_triangles,
-    }
+    })
+    return out
 
 
 class Context:

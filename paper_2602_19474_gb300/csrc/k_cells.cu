@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
                                               const u32* extra_scan, const u32* chain_scan, const TStage* stg,
                                               u32 NVg, u32 NE, int* tri, unsigned short* label,
                                               unsigned short* code, double* xy, u32* glist, u32* nglist,
-                                              u32* ngtri, u32* gcnt) {
+                                              u32* ngtri, u32* gcnt, CompactOut cp) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
@@ -501,10 +501,15 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     while ((pcol + 1) * den <= num) ++pcol;
     const int l = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
                              : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
+    const unsigned short lab = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
+    if (cp.on) {  // the base triangle stays implicit: its cell's label and code
+      cp.cell_label[cid] = lab, cp.cell_code[cid] = 0;
+      continue;
+    }
     tri[3 * (i64)o] = v0;
     tri[3 * (i64)o + 1] = v1;
     tri[3 * (i64)o + 2] = v2;
-    label[o] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
+    label[o] = lab;
     code[o] = 0;
   }
   // cut cells
@@ -512,7 +517,16 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   const double invS = 1.0 / (double)g.S;
   for (u32 rr = threadIdx.x; rr < ncut; rr += blockDim.x) {
     CutRec rec = recs[rec0 + rr];
-    const u32 off = T0_ + s_off[rec.cell - c0], cb = CB0 + s_cb[rr];
+    const u32 kl = rec.cell - (u32)c0, cb = CB0 + s_cb[rr];
+    u32 off = T0_ + s_off[kl];
+    if (cp.on) {
+      // patch triangles before this cell: those of earlier buckets, then the
+      // bucket's earlier cut cells (their extra triangles plus one each)
+      const u32 gi = cp.cut_scan[b] + rr;
+      off = extra_scan[b] + cp.cut_scan[b] + rr + (s_off[kl] - kl);
+      cp.patch_cell[gi] = rec.cell, cp.patch_off[gi] = off;
+      cp.cell_label[rec.cell] = 0xFFFF, cp.cell_code[rec.cell] = (unsigned short)(rec.code & 0xFFFFu);
+    }
     if (rec.code & (1u << 16)) {
       rec.tri_off = off, rec.chain_base = cb;
       recs[rec0 + rr] = rec;
@@ -563,9 +577,11 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       double2 v;
       v.x = zdouble(p.x) * invS;
       v.y = zdouble(p.y) * invS;
-      reinterpret_cast<double2*>(xy)[cb] = v;
+      reinterpret_cast<double2*>(xy)[cb - cp.xy0] = v;
     }
   }
+  if (cp.on && b == gridDim.x - 1 && threadIdx.x == 0)
+    cp.patch_off[cp.cut_scan[gridDim.x]] = extra_scan[gridDim.x] + cp.cut_scan[gridDim.x];
 }
 
 // lattice vertex coordinates.  Vertex v(i, j) has x = (ox + 3p m) / S with
@@ -612,10 +628,10 @@ int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dty
 int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
                  u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, u32* gcnt, cudaStream_t st) {
+                 u32* ngtri, u32* gcnt, const CompactOut& cp, cudaStream_t st) {
   if (nbc == 0) return 0;
   k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, NVg, NE, tri,
-                              label, code, xy, glist, nglist, ngtri, gcnt);
+                              label, code, xy, glist, nglist, ngtri, gcnt, cp);
   return 1;
 }
 

@@ -510,7 +510,7 @@ SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
 template <int G, int N>
 SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const CellGeo& cg,
                           const CutRec& rec, const GStore<N>& s, int lane, int* tri, unsigned short* label,
-                          unsigned short* code, double* xy, u32* err) {
+                          unsigned short* code, double* xy, u32 xy0, u32* err) {
   const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
   const int nt = min(s.ntri, 2 * N);
   if (lane == 0 && (u32)s.ntri != rec.ntri) atomicOr(err, ERR_COUNT);
@@ -534,7 +534,7 @@ SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, i
     double2 v;
     v.x = zdouble(zq((i64)s.xa[loc] + A.x.a, (i64)s.xb[loc] + A.x.b)) * invS;
     v.y = zdouble(zq((i64)s.ya[loc] + A.y.a, (i64)s.yb[loc] + A.y.b)) * invS;
-    reinterpret_cast<double2*>(xy)[s.gid[loc]] = v;
+    reinterpret_cast<double2*>(xy)[s.gid[loc] - xy0] = v;
   }
 }
 
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned cha
                                                       const Pair* sorted, const Seg* segs, const Event* ev,
                                                       const CutRec* recs, const u32* olist, const u32* nolist,
                                                       int* tri, unsigned short* label, unsigned short* code,
-                                                      double* xy, u32* err) {
+                                                      double* xy, u32 xy0, u32* err) {
   const u32 total = *nolist;
   for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
     const CutRec rec = recs[olist[item]];
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned cha
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
     const float M = (float)(6 * g.p);
     greedy_faces_sets<TN>(s, boundary_count(rec), 1e-4f * M * M, 8e-6f * M * M);
-    write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, err);
+    write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, xy0, err);
   }
 }
 
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
                                                             const Pair* sorted, const Seg* segs, const Event* ev,
                                                             const CutRec* recs, const u32* wlist, const u32* nwlist,
                                                             int* tri, unsigned short* label, unsigned short* code,
-                                                            double* xy, u32* err) {
+                                                            double* xy, u32 xy0, u32* err) {
   __shared__ GStore<WN> sm[WWARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   GStore<WN>& s = sm[w];
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
       continue;
     }
     greedy_faces<32, WN>(s, lane, boundary_count(rec), OriDirect<WN>{&s}, 0.f);
-    write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, err);
+    write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, xy0, err);
     __syncwarp();
   }
 }
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
-                  unsigned short* code, double* xy, u32* err, cudaStream_t st) {
+                  unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st) {
   // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
@@ -643,9 +643,9 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
   }();
   (void)carve;
   k_tierg_thread<<<152 * TG_BLOCKS_PER_SM, 64, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist,
-                                                        nolist, tri, label, code, xy, err);
+                                                        nolist, tri, label, code, xy, xy0, err);
   k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
-                                                tri, label, code, xy, err);
+                                                tri, label, code, xy, xy0, err);
   return 3;
 }
 

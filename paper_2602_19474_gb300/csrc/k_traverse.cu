@@ -246,7 +246,7 @@ SBMT_DEV Zq event_t(const Event& e) {
 // most 256 events ranks each event against the others held in shared
 // memory; a larger one counting-sorts its events by edge first.
 __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
-                                              u32 NVg, double* xy) {
+                                              u32 NVg, double* xy, u32 xy0) {
   constexpr int NEB = 1 << EB_LOG;
   __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
   __shared__ u32 s_sh[8];
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
     double2 v;
     v.x = zdouble(zq(x.xa, x.xb)) * invS;
     v.y = zdouble(zq(x.ya, x.yb)) * invS;
-    reinterpret_cast<double2*>(xy)[gid] = v;
+    reinterpret_cast<double2*>(xy)[gid - xy0] = v;
     return;
   }
   const u32 e0 = blockIdx.x << EB_LOG;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
     double2 v;
     v.x = zdouble(zq(ei.xa, ei.xb)) * invS;
     v.y = zdouble(zq(ei.ya, ei.yb)) * invS;
-    reinterpret_cast<double2*>(xy)[gid] = v;
+    reinterpret_cast<double2*>(xy)[gid - xy0] = v;
   }
 }
 
@@ -355,9 +355,9 @@ int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pc
 }
 
 int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, cudaStream_t st) {
+                        u32 NVg, double* xy, u32 xy0, cudaStream_t st) {
   if (nbe == 0) return 0;
-  k_rank<<<nbe, 256, 0, st>>>(g, events, eidx, elist, eoff, NVg, xy);
+  k_rank<<<nbe, 256, 0, st>>>(g, events, eidx, elist, eoff, NVg, xy, xy0);
   return 1;
 }
 

@@ -121,6 +121,12 @@ struct MeshRec {
   unsigned short* label = nullptr;
   unsigned short* code = nullptr;
   int64_t nv = 0, nt = 0, ncells = 0, nseg_total = 0, ne_total = 0, nc_total = 0, nvg = 0;
+  // SBMT_COMPACT: per-cell labels and codes, the cut cells' patch list
+  int format = SBMT_EXPLICIT;
+  unsigned short* cell_label = nullptr;
+  unsigned short* cell_code = nullptr;
+  u32* patch_cell = nullptr;
+  u32* patch_off = nullptr;
   u32* h_info = nullptr;  // pinned: err, ncut, ntierg, tierg triangles
   int W = 0;
   // kept intermediates (SBMT_KEEP_STAGES)
@@ -425,7 +431,8 @@ int check_params(const sbmt_image* img, const sbmt_params* pr) {
   if (img->dtype != SBMT_U8 && img->dtype != SBMT_U16) return fail(SBMT_EINVAL, "dtype %d", img->dtype);
   if (img->pitch_bytes < (int64_t)img->width * img->dtype) return fail(SBMT_EINVAL, "pitch too small");
   if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is not available");
-  if (pr->mode != SBMT_PLAIN || pr->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "mode/format");
+  if (pr->mode != SBMT_PLAIN || (pr->format != SBMT_EXPLICIT && pr->format != SBMT_COMPACT))
+    return fail(SBMT_EINVAL, "mode/format");
   if (pr->h_num < 2 || pr->h_num > 1024 || (pr->h_num & 1) || pr->h_den < 1 || pr->h_den > 63 ||
       !(pr->h_den & 1))
     return fail(SBMT_EINVAL, "h = %d/%d outside the degeneracy-free class (even h_num <= 1024, odd h_den < 64)",
@@ -589,20 +596,39 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if ((rc = aalloc(lane, &wlist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
-  // outputs
-  const size_t bxy = 16 * V, btri = 12 * T, blab = 2 * T, bcode = 2 * T;
-  const size_t off_tri = (bxy + 255) & ~(size_t)255, off_lab = (off_tri + btri + 255) & ~(size_t)255;
-  const size_t off_code = (off_lab + blab + 255) & ~(size_t)255, total = off_code + bcode + 256;
+  // outputs.  The compact format stores the vertices after the lattice, the
+  // per-cell label and code, and the patch triangles of the cut cells (at
+  // most the extra triangles plus one per cut cell, and cut cells <= pairs).
+  const bool compact = pr->format == SBMT_COMPACT;
+  m->format = pr->format;
+  const u64 nxy = compact ? V - NVg : V, ntr = compact ? (T - (u64)tb.ncells) + NP : T;
+  const size_t bxy = 16 * nxy, btri = 12 * ntr, blab = 2 * ntr, bcode = 2 * ntr;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_tri = up(bxy), off_lab = up(off_tri + btri), off_code = up(off_lab + blab);
+  const size_t off_cl = up(off_code + bcode), off_cc = up(off_cl + (compact ? 2 * (size_t)tb.ncells : 0));
+  const size_t off_pc = up(off_cc + (compact ? 2 * (size_t)tb.ncells : 0));
+  const size_t off_po = up(off_pc + (compact ? 4 * NP : 0));
+  const size_t total = off_po + (compact ? 4 * (NP + 1) : 0) + 256;
   if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
     return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
-  m->xy = (double*)m->out_block;
-  m->tri = (int*)((char*)m->out_block + off_tri);
-  m->label = (unsigned short*)((char*)m->out_block + off_lab);
-  m->code = (unsigned short*)((char*)m->out_block + off_code);
+  char* ob = (char*)m->out_block;
+  m->xy = (double*)ob;
+  m->tri = (int*)(ob + off_tri);
+  m->label = (unsigned short*)(ob + off_lab);
+  m->code = (unsigned short*)(ob + off_code);
+  CompactOut cp{0, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+  u32* cut_scan = nullptr;
+  if (compact) {
+    m->cell_label = (unsigned short*)(ob + off_cl), m->cell_code = (unsigned short*)(ob + off_cc);
+    m->patch_cell = (u32*)(ob + off_pc), m->patch_off = (u32*)(ob + off_po);
+    if ((rc = aalloc(lane, &cut_scan, nbc + 1))) return bail(rc);
+    cp = CompactOut{1, (u32)NVg, m->cell_label, m->cell_code, m->patch_cell, m->patch_off, cut_scan};
+    if (nbc == 0) CK(cudaMemsetAsync(m->patch_off, 0, sizeof(u32), st));
+  }
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // registry, K3, scans, K4, K4-G, lattice coordinates
-  TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, st));
+  TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
                                      err, st));
@@ -612,10 +638,18 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
     TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
     TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
   }
+  if (compact) {
+    if (nbc <= SCAN_ONE) {
+      TRACE(KN_SCAN, launch_scan_pair(bcut, cut_scan, nullptr, nbc, nullptr, nullptr, nullptr, 0, st));
+    } else {
+      TRACE(KN_SCAN, launch_scan(bcut, 1, cut_scan, nbc, sscr, st));
+    }
+  }
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
-                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, st));
+                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, cp,
+                             st));
   TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist,
-                               nwlist, m->tri, m->label, m->code, m->xy, err, st));
+                               nwlist, m->tri, m->label, m->code, m->xy, cp.xy0, err, st));
   // x of lattice vertex v(i, j) is indexed by m = 2i + j
   i64 m_lo = 0, m_hi = -1;
   for (i64 r = 0; r < nvr; ++r) {
@@ -625,7 +659,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   }
   double* xtab;
   if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
-  TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
+  if (!compact) TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
   CK(cudaGetLastError());
   // the status words: err, cut cells, Tier-G cells, Tier-G triangles
   CK(cudaMemcpyAsync(m->h_info, err, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -800,6 +834,12 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
   out->n_segments = m->nseg_total, out->n_events = m->ne_total, out->n_inside_vertices = m->nc_total;
   out->n_lattice_vertices = m->nvg, out->n_tierG_triangles = m->h_info[3];
   out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;
+  out->format = m->format;
+  if (m->format == SBMT_COMPACT) {
+    out->n_patch_triangles = (m->nt - m->ncells) + (int64_t)m->h_info[1];
+    out->cell_label = m->cell_label, out->cell_code = m->cell_code;
+    out->patch_cell = m->patch_cell, out->patch_off = m->patch_off;
+  }
   const u32 e = m->h_info[0];
   out->status = e == 0 ? SBMT_OK : (e & ERR_CAPACITY) ? SBMT_ECAPACITY : SBMT_EINTERNAL;
   if (out->status) fail(out->status, "device reported error bits 0x%x", e);
@@ -846,6 +886,7 @@ int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out) {
     if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
     m = it->second;
   }
+  if (m->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "quality needs the explicit format");
   CK(cudaSetDevice(ctx->device));
   std::memset(out, 0, sizeof *out);
   const u64 T = (u64)m->nt;

@@ -134,6 +134,19 @@ struct CutRec {
   u32 ntri, nchain, tri_off, chain_base;
 };
 
+// where emission writes: the compact format keeps the uncut cells as one
+// label and one code per base cell, lists the cut cells' patches, and stores
+// coordinates only for the vertices after the lattice (ids from xy0 up)
+struct CompactOut {
+  int on;                     // 0: explicit format (the other fields unused)
+  u32 xy0;                    // id of the first vertex stored in xy
+  unsigned short* cell_label;
+  unsigned short* cell_code;
+  u32* patch_cell;            // per cut cell (in cell order): its id
+  u32* patch_off;             // per cut cell: its first patch triangle; then the total
+  const u32* cut_scan;        // exclusive scan of the cut cells per bucket
+};
+
 // a Tier-T patch between classification and emission: the vertex ids of the
 // cell's events in counter-clockwise order from A, and the label of each
 // patch triangle

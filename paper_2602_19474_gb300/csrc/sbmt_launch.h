@@ -38,7 +38,7 @@ int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pc
 // frozen registry: rank the events of each event bucket (listed in eidx) by
 // (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
 int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, cudaStream_t st);
+                        u32 NVg, double* xy, u32 xy0, cudaStream_t st);
 
 // K3a: sort each cell bucket's pairs by cell into sorted; one record per cut
 // cell, in cell order, in a dense range of recs drawn from *nrec (bucket b:
@@ -71,7 +71,7 @@ int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaSt
 int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
                  u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, u32* gcnt, cudaStream_t st);
+                 u32* ngtri, u32* gcnt, const CompactOut& cp, cudaStream_t st);
 
 // K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.  The
 // cells are first ordered by local vertex count, largest first, into olist
@@ -81,7 +81,7 @@ int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, 
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                   const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
-                  unsigned short* code, double* xy, u32* err, cudaStream_t st);
+                  unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st);
 
 // quality measures: per-triangle pass (mm: min angle, min area, max AR as
 // double bits; cnt: slivers, equilateral; part: per-block area sums; ar:

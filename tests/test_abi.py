@@ -31,11 +31,33 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
-def test_struct_layouts_match_header():
-    # sizes of the C structs on LP64 (int32/int64/double/pointer alignment)
-    assert ctypes.sizeof(sb.sbmt_image) == 40
-    assert ctypes.sizeof(sb.sbmt_params) == 56
-    assert ctypes.sizeof(sb.sbmt_mesh_view) == 120
+def test_struct_layouts_match_header(tmp_path):
+    # every field's offset and every struct's size, as the C compiler lays
+    # out include/sbmt.h, against the ctypes declarations of the binding
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = (sb.sbmt_image, sb.sbmt_params, sb.sbmt_mesh_view, sb.sbmt_quality)
+    lines = []
+    for st in structs:
+        n = st.__name__
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (n, n))
+        for f, _ in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (n, f, n, f))
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include "sbmt.h"\nint main(void) {\n%s\nreturn 0;\n}\n' % "\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[n + "." + f]) == getattr(st, f).offset, (n, f)
 
 
 def test_null_arguments_are_rejected(lib):
