@@ -412,6 +412,31 @@ def our_arm(args, rank: int, world: int, dist):
     torch.cuda.synchronize()
     barrier()
     ms_ce = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
+    # projection of a scalar pixel field onto the mesh (per-triangle means and
+    # bilinear vertex values): a smooth synthetic intensity of the image's size
+    m = sb.mesh_bitmap(ctx, dimg, hn, hd)
+    vp = sb.mesh_query(ctx, m, -1)
+    yy = torch.arange(H, device=dev, dtype=torch.float32)[:, None]
+    xx = torch.arange(W, device=dev, dtype=torch.float32)[None, :]
+    field = (torch.sin(xx / 37.0) * torch.cos(yy / 53.0) + dimg.to(torch.float32) * 0.125).contiguous()
+    tv = torch.empty(vp.n_triangles, dtype=torch.float32, device=dev)
+    vv = torch.empty(vp.n_vertices, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sb.mesh_project(ctx, m, field, tv, vv)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        sb.mesh_project(ctx, m, field, tv, vv)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / args.steps
+    sb.mesh_release(ctx, m)
+    del field
+    pbytes = 12.0 * T + 16.0 * vp.n_vertices + 4.0 * W * H + 4.0 * T + 4.0 * vp.n_vertices
+    projection = {"what": "mean of a float pixel field over every triangle (exact pixel overlaps) and its bilinear "
+                          "value at every vertex, on the step's mesh; two kernels per call",
+                  "ms_per_call": ms_p, "triangles_per_s": T / (ms_p * 1e-3),
+                  "algorithmic_bytes_per_call": pbytes, "achieved_gbs": pbytes / (ms_p * 1e-3) / 1e9}
     compact = {"what": "the same mesh in the compact format (uncut cells as a label per base cell, cut cells' "
                        "patches listed); triangles/s counts the triangles the mesh represents",
                "ms_per_step": ms_c, "value": job_rate(world, T, ms_c), "patch_triangles": vc.n_patch_triangles,
@@ -459,6 +484,7 @@ def our_arm(args, rank: int, world: int, dist):
                          "sample": "top-left %dx%d crop of the workload, one thread" % (side, side)},
         "e2e": {"value": e2e_value, "unit": "triangles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "compact_format": compact,
+        "projection": dict(projection, peak=peak, frac=projection["achieved_gbs"] / peak),
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -52,7 +52,7 @@ extern "C" {
 typedef struct sbmt_ctx sbmt_ctx;
 typedef uint64_t sbmt_mesh;
 
-enum { SBMT_U8 = 1, SBMT_U16 = 2 };
+enum { SBMT_U8 = 1, SBMT_U16 = 2, SBMT_F32 = 4 }; /* SBMT_F32: fields for mesh_project only */
 enum { SBMT_PLAIN = 0, SBMT_PREPROCESS = 1 };
 enum { SBMT_EXPLICIT = 0, SBMT_COMPACT = 1 };
 enum { SBMT_KEEP_STAGES = 1 }; /* sbmt_params.flags: keep intermediate arrays for mesh_stage */
@@ -202,6 +202,28 @@ typedef struct {
   int64_t angle_hist[30];
 } sbmt_quality;
 int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out);
+
+/* Projection of a scalar pixel field onto a finished mesh (Sec. 3.3: the
+ * bitmap's scalar fields are projected onto each triangle; Sec. 3.6 and
+ * App. C: the interpolation stage, constant work per triangle).
+ *  field         a width x height image of the meshed size with dtype
+ *                SBMT_F32 (4-byte floats), host or device (see sbmt_image;
+ *                a host field is copied first);
+ *  tri_value     device, n_triangles floats, or NULL: per triangle T the
+ *                mean of the piecewise-constant pixel field over T,
+ *                (1/|T|) sum_p f_p |T n p|, pixel (x, y) the unit square
+ *                centred at (x, y); 0 for triangles outside the image;
+ *  vertex_value  device, n_vertices floats, or NULL: the bilinear
+ *                interpolation of the field between pixel centres at each
+ *                vertex, the point clamped to [0, W-1] x [0, H-1].
+ * Single precision, double for thin triangles (longest edge L with
+ * L (L + 1) > 64 |T|): a triangle's mean is within a few 2^-24
+ * L (L + 1) / |T| of the field's range over its pixels.  Both buffers are
+ * caller-owned.  The work is enqueued on the context's stream after the
+ * mesh; mesh_query on the mesh then also waits for it.  Explicit meshes
+ * only: SBMT_EINVAL for a compact mesh, a field of another size or dtype,
+ * or a mesh of 2^32 triangles or more. */
+int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* tri_value, float* vertex_value);
 
 /* Per-kernel device time, for tracing and roofline accounting (no
  * counterpart in the paper, which reports no timings).  With enable != 0

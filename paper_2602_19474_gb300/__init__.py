@@ -30,13 +30,13 @@ SBMT_EPROTO = -6
 SBMT_ECUDA = -7
 SBMT_EINTERNAL = -8
 SBMT_ENOENT = -9
-SBMT_U8, SBMT_U16 = 1, 2
+SBMT_U8, SBMT_U16, SBMT_F32 = 1, 2, 4
 SBMT_PLAIN, SBMT_PREPROCESS = 0, 1
 SBMT_EXPLICIT, SBMT_COMPACT = 0, 1
 SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
-           "mesh_profile", "mesh_profile_read", "mesh_quality", "sbmt_last_error")
+           "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "sbmt_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -106,9 +106,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                       ctypes.POINTER(ctypes.c_int)]
     lib.mesh_quality.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_quality)]
+    lib.mesh_project.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_image), vp, vp]
     lib.sbmt_last_error.restype = ctypes.c_char_p
     for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
-              "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality"):
+              "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project"):
         getattr(lib, f).restype = ctypes.c_int
     del i32
     _lib = lib
@@ -212,6 +213,41 @@ def mesh_quality(ctx: int, mesh: int) -> dict:
     out = {k: getattr(q, k) for k, _ in sbmt_quality._fields_ if k != "angle_hist"}
     out["angle_hist"] = [int(x) for x in q.angle_hist]
     return out
+
+
+def _field(field) -> tuple[sbmt_image, object]:
+    """sbmt_image (SBMT_F32) for a float32 numpy array or CUDA tensor."""
+    if isinstance(field, np.ndarray):
+        a = np.ascontiguousarray(field, dtype=np.float32)
+        if a.ndim != 2:
+            raise ValueError("the field must be 2-D")
+        return sbmt_image(a.shape[1], a.shape[0], a.strides[0], SBMT_F32, a.ctypes.data, 0), a
+    import torch
+
+    t = field
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 2 and t.dtype == torch.float32):
+        raise ValueError("a device field must be a 2-D float32 CUDA tensor")
+    if t.stride(1) != 1:
+        t = t.contiguous()
+    return sbmt_image(t.shape[1], t.shape[0], t.stride(0) * 4, SBMT_F32, t.data_ptr(), 1), t
+
+
+def mesh_project(ctx: int, mesh: int, field, tri_value=None, vertex_value=None) -> None:
+    """Project a float32 pixel field onto a finished mesh: per-triangle means
+    into ``tri_value`` and bilinear vertex values into ``vertex_value`` (float32
+    CUDA tensors of n_triangles / n_vertices elements, or None).  Enqueued on
+    the context's stream; mesh_query on the mesh waits for it."""
+    fi, keep = _field(field)
+
+    def ptr(t):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous()):
+            raise ValueError("outputs must be contiguous float32 CUDA tensors")
+        return t.data_ptr()
+
+    _check(load().mesh_project(ctx, mesh, ctypes.byref(fi), ptr(tri_value), ptr(vertex_value)))
+    del keep
 
 
 def mesh_profile(ctx: int, enable: bool) -> None:

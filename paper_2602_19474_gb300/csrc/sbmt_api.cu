@@ -128,7 +128,7 @@ struct MeshRec {
   u32* patch_cell = nullptr;
   u32* patch_off = nullptr;
   u32* h_info = nullptr;  // pinned: err, ncut, ntierg, tierg triangles
-  int W = 0;
+  int W = 0, H = 0;
   // kept intermediates (SBMT_KEEP_STAGES)
   bool keep = false;
   Seg* segs = nullptr;
@@ -460,7 +460,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
     return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
   MeshRec* m = new MeshRec();
-  m->W = g.W;
+  m->W = g.W, m->H = g.H;
   m->keep = (pr->flags & SBMT_KEEP_STAGES) != 0;
   std::vector<void*> tmp;  // device memory freed at the end of the call
   arena_begin(lane);
@@ -967,6 +967,54 @@ int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out) {
   std::memcpy(&f[1], &pre[1], 4);
   out->ar_median = f[0], out->ar_p95 = f[1];
   arena_end(lane);
+  return SBMT_OK;
+}
+
+int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* tri_value, float* vertex_value) {
+  if (!ctx || !field) return fail(SBMT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  MeshRec* m;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    auto it = ctx->meshes.find(mesh);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+    m = it->second;
+  }
+  if (m->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "projection needs the explicit format");
+  if (field->dtype != SBMT_F32 || field->width != m->W || field->height != m->H || !field->data)
+    return fail(SBMT_EINVAL, "field must be a %dx%d SBMT_F32 image", m->W, m->H);
+  if (field->pitch_bytes < 4 * (int64_t)field->width || (field->pitch_bytes & 3))
+    return fail(SBMT_EINVAL, "field pitch");
+  if ((u64)m->nt >= (1ull << 32)) return fail(SBMT_EINVAL, "mesh too large to project");
+  if (!tri_value && !vertex_value) return SBMT_OK;
+  CK(cudaSetDevice(ctx->device));
+  Lane* lane = &ctx->main;
+  cudaStream_t st = lane->stream;
+  CK(cudaStreamWaitEvent(st, m->done, 0));
+  arena_begin(lane);
+  const float* f = (const float*)field->data;
+  i64 pitch = field->pitch_bytes;
+  if (!field->on_device) {
+    float* d;
+    int rc;
+    pitch = 4 * (i64)field->width;
+    if ((rc = aalloc(lane, &d, (size_t)field->width * field->height))) {
+      arena_end(lane);
+      return rc;
+    }
+    if (cudaMemcpy2DAsync(d, pitch, field->data, field->pitch_bytes, pitch, field->height, cudaMemcpyHostToDevice,
+                          st) != cudaSuccess) {
+      arena_end(lane);
+      return fail(SBMT_ECUDA, "field upload");
+    }
+    f = d;
+  }
+  launch_project(m->xy, m->tri, (u64)m->nt, (u64)m->nv, f, pitch, m->W, m->H, tri_value, vertex_value, st);
+  const cudaError_t e = cudaGetLastError();
+  arena_end(lane);
+  if (e != cudaSuccess) return fail(SBMT_ECUDA, "projection launch: %s", cudaGetErrorString(e));
+  // the mesh's completion now includes the projection
+  CK(cudaEventRecord(m->done, st));
   return SBMT_OK;
 }
 
