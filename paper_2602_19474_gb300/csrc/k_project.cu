@@ -87,13 +87,15 @@ SBMT_DEV DF quot(DF a, DF b) { return a / b; }
 
 // integral of min(x - t, 0) dy along the segment p -> q, in the form
 // dy * I with I the mean of min(., 0) over the segment's linear x - t
+// (branch-free: with lo <= hi the ends' values, the segment lies left of t
+// when hi <= 0, and otherwise only the triangle of height -min(lo, 0) over
+// the part of length -min(lo, 0) / (hi - lo) counts; that is 0 when lo >= 0)
 template <typename R>
 SBMT_DEV R left_integral(R px, R py, R qx, R qy, R t) {
   const R a = px - t, b = qx - t, dy = qy - py;
-  if (a <= R(0) && b <= R(0)) return R(0.5f) * (a + b) * dy;
-  if (a > R(0) && b > R(0)) return R(0);
-  const R neg = a <= R(0) ? a : b;  // the end left of t; |b - a| >= |neg| > 0
-  return -quot(neg * neg * dy, R(2) * fabs(b - a));
+  const R lo = fmin(a, b), hi = fmax(a, b), n = fmin(lo, R(0));
+  const R cross = -quot(n * n * dy, R(2) * fmax(hi - lo, R(1e-30f)));
+  return hi > R(0) ? cross : R(0.5f) * (a + b) * dy;
 }
 
 // the part of edge p -> q with lo <= y <= hi, end points and whether it is
@@ -105,10 +107,8 @@ struct Sub {
   bool in;
 };
 template <typename R>
-SBMT_DEV Sub<R> band_part(R px, R py, R qx, R qy, R lo, R hi) {
-  const R dy = qy - py;
+SBMT_DEV Sub<R> band_part(R px, R py, R qx, R qy, R dy, R inv, R lo, R hi) {
   if (dy == R(0)) return Sub<R>{px, py, qx, qy, lo <= py && py <= hi};
-  const R inv = quot(R(1), dy);
   const R s0 = (lo - py) * inv, s1 = (hi - py) * inv;
   const R u0 = fmax(R(0), fmin(s0, s1)), u1 = fmin(R(1), fmax(s0, s1));
   if (u1 <= u0) return Sub<R>{px, py, px, py, false};
@@ -125,12 +125,16 @@ SBMT_DEV Sub<R> band_part(R px, R py, R qx, R qy, R lo, R hi) {
 template <typename R>
 SBMT_DEV float tri_mean(R bx, R by, R qx, R qy, R X0, R Y0, int c0, int c1, int r0, int r1, const float* f,
                         i64 fpitch) {
+  // the edges' rises and their reciprocals, once per triangle
+  const R d0 = by, d1 = qy - by, d2 = -qy;
+  const R i0 = d0 == R(0) ? R(0) : quot(R(1), d0), i1 = d1 == R(0) ? R(0) : quot(R(1), d1);
+  const R i2 = d2 == R(0) ? R(0) : quot(R(1), d2);
   R s(0), tot(0);
   for (int r = r0; r <= r1; ++r) {
     const R lo = Y0 + R((float)(r - r0)), hi = lo + R(1);
-    const Sub<R> e0 = band_part<R>(R(0), R(0), bx, by, lo, hi);
-    const Sub<R> e1 = band_part<R>(bx, by, qx, qy, lo, hi);
-    const Sub<R> e2 = band_part<R>(qx, qy, R(0), R(0), lo, hi);
+    const Sub<R> e0 = band_part<R>(R(0), R(0), bx, by, d0, i0, lo, hi);
+    const Sub<R> e1 = band_part<R>(bx, by, qx, qy, d1, i1, lo, hi);
+    const Sub<R> e2 = band_part<R>(qx, qy, R(0), R(0), d2, i2, lo, hi);
     if (!(e0.in || e1.in || e2.in)) continue;
     R xlo(3e38f), xhi(-3e38f);
     if (e0.in) xlo = fmin(xlo, fmin(e0.px, e0.qx)), xhi = fmax(xhi, fmax(e0.px, e0.qx));
@@ -188,6 +192,12 @@ SBMT_DEV Split split(double x) {
   return bits < 0 ? Split{-(int)ip, -d, -e} : Split{(int)ip, d, e};
 }
 
+// a vertex split once by the vertex pass, read by the triangle pass (16 B)
+struct SplitV {
+  int X, Y;
+  float dx, dy;
+};
+
 // pixel index floor(x + 1/2) of a split coordinate
 SBMT_DEV int pixel_of(Split s) { return s.X + (int)floorf(s.d + 0.5f); }
 
@@ -205,8 +215,8 @@ constexpr float COND_F32 = 128.f;
 constexpr int PT_ITER = 8;
 constexpr int QCAP = PT_ITER * 256;
 
-__global__ void __launch_bounds__(256, 4) k_project_tri(const double* xy, const int* tri, u64 T, const float* f,
-                                                        i64 fpitch, int W, int H, float* out) {
+__global__ void __launch_bounds__(256, 4) k_project_tri(const double* xy, const int* tri, const SplitV* sv, u64 T,
+                                                        const float* f, i64 fpitch, int W, int H, float* out) {
   __shared__ u32 s_q[QCAP];
   __shared__ int s_n;
   if (threadIdx.x == 0) s_n = 0;
@@ -214,10 +224,12 @@ __global__ void __launch_bounds__(256, 4) k_project_tri(const double* xy, const 
   for (int it = 0; it < PT_ITER; ++it) {
     const u64 t = ((u64)blockIdx.x * PT_ITER + it) * blockDim.x + threadIdx.x;
     if (t >= T) break;
-    const double2 a = reinterpret_cast<const double2*>(xy)[tri[3 * t]];
-    const double2 b = reinterpret_cast<const double2*>(xy)[tri[3 * t + 1]];
-    const double2 c = reinterpret_cast<const double2*>(xy)[tri[3 * t + 2]];
-    const Split ax = split(a.x), ay = split(a.y), bx = split(b.x), by = split(b.y), cx = split(c.x), cy = split(c.y);
+    const int4 va = __ldg(reinterpret_cast<const int4*>(sv) + tri[3 * t]);
+    const int4 vb = __ldg(reinterpret_cast<const int4*>(sv) + tri[3 * t + 1]);
+    const int4 vc = __ldg(reinterpret_cast<const int4*>(sv) + tri[3 * t + 2]);
+    const Split ax{va.x, __int_as_float(va.z), 0.f}, ay{va.y, __int_as_float(va.w), 0.f};
+    const Split bx{vb.x, __int_as_float(vb.z), 0.f}, by{vb.y, __int_as_float(vb.w), 0.f};
+    const Split cx{vc.x, __int_as_float(vc.z), 0.f}, cy{vc.y, __int_as_float(vc.w), 0.f};
     // centroid inside the image rectangle: 3 x_c in (-3/2, 3W - 3/2), the
     // integer parts summed exactly, the fractions in float
     const int IX = ax.X + bx.X + cx.X, IY = ay.X + by.X + cy.X;
@@ -265,12 +277,16 @@ __global__ void __launch_bounds__(256, 4) k_project_tri(const double* xy, const 
   }
 }
 
+// the vertex pass: every vertex split once into sv (when given) and its
+// bilinear value into out (when given)
 __global__ void __launch_bounds__(256) k_project_vert(const double* xy, u64 V, const float* f, i64 fpitch, int W,
-                                                      int H, float* out) {
+                                                      int H, float* out, SplitV* sv) {
   for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < V; k += (u64)gridDim.x * blockDim.x) {
     const double2 p = reinterpret_cast<const double2*>(xy)[k];
     // clamp x = X + d to [0, W - 1] with d in [0, 1): i0 = X, u = d
     Split sx = split(p.x), sy = split(p.y);
+    if (sv) sv[k] = SplitV{sx.X, sy.X, sx.d, sy.d};
+    if (!out) continue;
     if (sx.d < 0.f) sx.X -= 1, sx.d += 1.f;
     if (sy.d < 0.f) sy.X -= 1, sy.d += 1.f;
     if (sx.X < 0) sx.X = 0, sx.d = 0.f;
@@ -289,18 +305,21 @@ __global__ void __launch_bounds__(256) k_project_vert(const double* xy, u64 V, c
 
 }  // namespace
 
+size_t project_scratch_bytes(u64 V) { return sizeof(SplitV) * (size_t)V; }
+
 int launch_project(const double* xy, const int* tri, u64 T, u64 V, const float* f, i64 fpitch, int W, int H,
-                   float* tri_value, float* vertex_value, cudaStream_t st) {
+                   float* tri_value, float* vertex_value, void* scratch, cudaStream_t st) {
   if (T >= (1ull << 32)) return -1;
   int n = 0;
-  if (tri_value && T) {
-    const u64 blocks = (T + QCAP - 1) / QCAP;
-    k_project_tri<<<(unsigned)blocks, 256, 0, st>>>(xy, tri, T, f, fpitch, W, H, tri_value);
+  SplitV* sv = tri_value && T ? (SplitV*)scratch : nullptr;
+  if ((vertex_value || sv) && V) {
+    const u64 blocks = std::min<u64>((V + 255) / 256, 152ull * 16);
+    k_project_vert<<<(unsigned)blocks, 256, 0, st>>>(xy, V, f, fpitch, W, H, vertex_value, sv);
     ++n;
   }
-  if (vertex_value && V) {
-    const u64 blocks = std::min<u64>((V + 255) / 256, 152ull * 16);
-    k_project_vert<<<(unsigned)blocks, 256, 0, st>>>(xy, V, f, fpitch, W, H, vertex_value);
+  if (sv) {
+    const u64 blocks = (T + QCAP - 1) / QCAP;
+    k_project_tri<<<(unsigned)blocks, 256, 0, st>>>(xy, tri, sv, T, f, fpitch, W, H, tri_value);
     ++n;
   }
   return n;

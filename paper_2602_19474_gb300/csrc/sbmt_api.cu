@@ -1009,7 +1009,15 @@ int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* 
     }
     f = d;
   }
-  launch_project(m->xy, m->tri, (u64)m->nt, (u64)m->nv, f, pitch, m->W, m->H, tri_value, vertex_value, st);
+  unsigned char* scratch = nullptr;
+  if (tri_value) {
+    int rc;
+    if ((rc = aalloc(lane, &scratch, project_scratch_bytes((u64)m->nv)))) {
+      arena_end(lane);
+      return rc;
+    }
+  }
+  launch_project(m->xy, m->tri, (u64)m->nt, (u64)m->nv, f, pitch, m->W, m->H, tri_value, vertex_value, scratch, st);
   const cudaError_t e = cudaGetLastError();
   arena_end(lane);
   if (e != cudaSuccess) return fail(SBMT_ECUDA, "projection launch: %s", cudaGetErrorString(e));

@@ -93,9 +93,12 @@ int launch_select_hist(const float* v, u64 T, int lo, int width, u32 pre0, u32 p
 
 // projection of a float pixel field (row pitch fpitch bytes): per-triangle
 // means into tri_value and bilinear vertex values into vertex_value (either
-// may be null); returns the number of kernels launched, -1 if T >= 2^32
+// may be null); scratch holds project_scratch_bytes(V) bytes (16-byte
+// aligned) for the vertices' split coordinates; returns the number of
+// kernels launched, -1 if T >= 2^32
+size_t project_scratch_bytes(u64 V);
 int launch_project(const double* xy, const int* tri, u64 T, u64 V, const float* f, i64 fpitch, int W, int H,
-                   float* tri_value, float* vertex_value, cudaStream_t st);
+                   float* tri_value, float* vertex_value, void* scratch, cudaStream_t st);
 
 // coordinates of the lattice vertices; tab: scratch of nm doubles for the x
 // values (ox + 3p m) / S, m0 <= m < m0 + nm covering 2i + j of every vertex
