@@ -28,6 +28,7 @@ gives p50 / p99 latency (arrival to mesh ready) per rate.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -317,6 +318,10 @@ def our_arm(args, rank: int, world: int, dist):
     for _ in range(args.warmup):
         v = step(dimg)
     torch.cuda.synchronize()
+    # no garbage-collection pauses inside the timed regions (each step waits
+    # on the host between its launches, so host pauses show in its time)
+    gc.collect()
+    gc.disable()
     # device-resident timed region
     sb.mesh_profile(ctx, True)
     sb.mesh_profile_read(ctx, reset=True)

@@ -85,19 +85,6 @@ SBMT_DEV DF fmax(DF x, DF y) { return x < y ? y : x; }
 SBMT_DEV float quot(float a, float b) { return __fdividef(a, b); }
 SBMT_DEV DF quot(DF a, DF b) { return a / b; }
 
-// integral of min(x - t, 0) dy along the segment p -> q, in the form
-// dy * I with I the mean of min(., 0) over the segment's linear x - t
-// (branch-free: with lo <= hi the ends' values, the segment lies left of t
-// when hi <= 0, and otherwise only the triangle of height -min(lo, 0) over
-// the part of length -min(lo, 0) / (hi - lo) counts; that is 0 when lo >= 0)
-template <typename R>
-SBMT_DEV R left_integral(R px, R py, R qx, R qy, R t) {
-  const R a = px - t, b = qx - t, dy = qy - py;
-  const R lo = fmin(a, b), hi = fmax(a, b), n = fmin(lo, R(0));
-  const R cross = -quot(n * n * dy, R(2) * fmax(hi - lo, R(1e-30f)));
-  return hi > R(0) ? cross : R(0.5f) * (a + b) * dy;
-}
-
 // the part of edge p -> q with lo <= y <= hi, end points and whether it is
 // there (a horizontal edge inside the band is kept whole: it bounds the
 // band's polygon but adds nothing to the integrals)
@@ -114,6 +101,31 @@ SBMT_DEV Sub<R> band_part(R px, R py, R qx, R qy, R dy, R inv, R lo, R hi) {
   if (u1 <= u0) return Sub<R>{px, py, px, py, false};
   const R dx = qx - px;
   return Sub<R>{px + u0 * dx, py + u0 * dy, px + u1 * dx, py + u1 * dy, true};
+}
+
+// One edge's part inside a row band, set up for the integral of
+// min(x - t, 0) dy along it as a function of the column line x = t: with
+// xmin <= xmax its ends' x, the whole part lies left of t when t >= xmax,
+// giving (cx - t) dy with cx its mid x; otherwise only the part left of t
+// counts, a triangle of height xmin - t (when negative) over a length
+// (t - xmin) / (xmax - xmin) of the part: -(min(xmin - t, 0))^2 k with
+// k = dy / (2 (xmax - xmin)).  A horizontal or absent part has dy = 0.
+template <typename R>
+struct Row {
+  R xmin, xmax, cx, dy, k;
+  SBMT_DEV R left(R t) const {
+    const R n = fmin(xmin - t, R(0));
+    return t < xmax ? -(n * n * k) : (cx - t) * dy;
+  }
+};
+template <typename R>
+SBMT_DEV Row<R> row_edge(const Sub<R>& e) {
+  Row<R> g;
+  g.xmin = fmin(e.px, e.qx), g.xmax = fmax(e.px, e.qx);
+  g.cx = R(0.5f) * (e.px + e.qx);
+  g.dy = e.in ? e.qy - e.py : R(0);
+  g.k = quot(g.dy, R(2) * fmax(g.xmax - g.xmin, R(1e-30f)));
+  return g;
 }
 
 // the weighted sum over the pixels (c0..c1) x (r0..r1), divided by the sum
@@ -140,9 +152,9 @@ SBMT_DEV float tri_mean(R bx, R by, R qx, R qy, R X0, R Y0, int c0, int c1, int 
     if (e0.in) xlo = fmin(xlo, fmin(e0.px, e0.qx)), xhi = fmax(xhi, fmax(e0.px, e0.qx));
     if (e1.in) xlo = fmin(xlo, fmin(e1.px, e1.qx)), xhi = fmax(xhi, fmax(e1.px, e1.qx));
     if (e2.in) xlo = fmin(xlo, fmin(e2.px, e2.qx)), xhi = fmax(xhi, fmax(e2.px, e2.qx));
+    const Row<R> g0 = row_edge(e0), g1 = row_edge(e1), g2 = row_edge(e2);
     // the polygon's area: the integral of x dy over its edges on the triangle
-    const R whole = R(0.5f) * ((e0.px + e0.qx) * (e0.qy - e0.py) + (e1.px + e1.qx) * (e1.qy - e1.py) +
-                               (e2.px + e2.qx) * (e2.qy - e2.py));
+    const R whole = g0.cx * g0.dy + g1.cx * g1.dy + g2.cx * g2.dy;
     const float* row = reinterpret_cast<const float*>((const char*)f + r * fpitch);
     R prev(0);
     for (int cc = c0; cc <= c1; ++cc) {
@@ -153,8 +165,7 @@ SBMT_DEV float tri_mean(R bx, R by, R qx, R qy, R X0, R Y0, int c0, int c1, int 
       } else if (t <= xlo) {
         next = R(0);
       } else {
-        next = left_integral<R>(e0.px, e0.py, e0.qx, e0.qy, t) + left_integral<R>(e1.px, e1.py, e1.qx, e1.qy, t) +
-               left_integral<R>(e2.px, e2.py, e2.qx, e2.qy, t);
+        next = g0.left(t) + g1.left(t) + g2.left(t);
       }
       const R piece = next - prev;
       prev = next;
