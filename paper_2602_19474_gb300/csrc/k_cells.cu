@@ -388,10 +388,13 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 
 // K3b: one thread per cut cell (dense): classification (key, sigma, class,
 // Tier-T / Tier-G, triangle and inside-vertex counts) added to the bucket's
-// totals, and for a Tier-T cell its staged patch.
+// totals, for a Tier-T cell its staged patch, and a Tier-G cell queued
+// (glist; the queued triangles in ngtri; per-size counts in gcnt, sizes
+// above TIERG_TN pooled at TIERG_TN + 1).
 __global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                                   const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
-                                                  const u32* nrec, u32* bextra, u32* bchain, TStage* stg, u32* err) {
+                                                  const u32* nrec, u32* bextra, u32* bchain, TStage* stg,
+                                                  u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err) {
   const u32 total = *nrec;
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     CutRec rec = recs[i];
@@ -406,6 +409,20 @@ __global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* 
     const u32 b = rec.cell >> CB_LOG;
     atomicAdd(&bextra[b], kl.ntri - 1);
     if (kl.nchain) atomicAdd(&bchain[b], kl.nchain);
+    if (kl.tierG) {
+      // one atomic per warp for the list and the triangle count, one per
+      // distinct size for the per-size counts (n = ntri + 2 - n_i)
+      const unsigned act = __activemask();
+      const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
+      const u32 t = __reduce_add_sync(act, kl.ntri);
+      u32 at = 0;
+      if (lane == lead) at = atomicAdd(nglist, (u32)__popc(act)), atomicAdd(ngtri, t);
+      at = __shfl_sync(act, at, lead) + (u32)__popc(act & ((1u << lane) - 1u));
+      glist[at] = i;
+      const u32 n = kl.ntri + 2 - kl.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
+      const unsigned peers = __match_any_sync(act, key);
+      if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[key], (u32)__popc(peers));
+    }
   }
 }
 
@@ -413,15 +430,15 @@ __global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* 
 // K4: emission, one block per cell bucket
 // ---------------------------------------------------------------------------
 // Every uncut cell writes its base triangle; every Tier-T cell its staged
-// patch at its offset, with P's id and coordinates; every Tier-G cell gets
-// its output range and is queued.  The bucket's whole triangle range is
-// written by one block.
+// patch at its offset, with P's id and coordinates.  Tier-G cells are left
+// to the Tier-G kernels, which run beside this one and take their output
+// ranges from the same scans.  The bucket's other triangles are written by
+// one block.
 __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                               CutRec* recs, const u32* bcut, const u32* bbase,
                                               const u32* extra_scan, const u32* chain_scan, const TStage* stg,
                                               u32 NVg, u32 NE, int* tri, unsigned short* label,
-                                              unsigned short* code, double* xy, u32* glist, u32* nglist,
-                                              u32* ngtri, u32* gcnt, CompactOut cp) {
+                                              unsigned short* code, double* xy, CompactOut cp) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
@@ -527,23 +544,7 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       cp.patch_cell[gi] = rec.cell, cp.patch_off[gi] = off;
       cp.cell_label[rec.cell] = 0xFFFF, cp.cell_code[rec.cell] = (unsigned short)(rec.code & 0xFFFFu);
     }
-    if (rec.code & (1u << 16)) {
-      rec.tri_off = off, rec.chain_base = cb;
-      recs[rec0 + rr] = rec;
-      // queue it: one atomic per warp for the list and the triangle count,
-      // one per distinct size for the per-size counts (n = ntri + 2 - n_i)
-      const unsigned act = __activemask();
-      const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
-      const u32 t = __reduce_add_sync(act, rec.ntri);
-      u32 at = 0;
-      if (lane == lead) at = atomicAdd(nglist, (u32)__popc(act)), atomicAdd(ngtri, t);
-      at = __shfl_sync(act, at, lead) + (u32)__popc(act & ((1u << lane) - 1u));
-      glist[at] = rec0 + rr;
-      const u32 n = rec.ntri + 2 - rec.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
-      const unsigned peers = __match_any_sync(act, key);
-      if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[key], (u32)__popc(peers));
-      continue;
-    }
+    if (rec.code & (1u << 16)) continue;  // Tier-G
     row = advance_row(g, row, rec.cell);
     const CellGeo cg = cell_geo(g, rec.cell, row);
     const TStage st = stg[rec0 + rr];
@@ -619,19 +620,19 @@ int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRe
 
 int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* err, cudaStream_t st) {
+                     TStage* stg, u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st) {
   k_cutcells<<<152 * 24, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, nrec, bextra, bchain, stg,
-                                       err);
+                                       glist, nglist, ngtri, gcnt, err);
   return 1;
 }
 
 int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
-                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, u32* gcnt, const CompactOut& cp, cudaStream_t st) {
+                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, const CompactOut& cp,
+                 cudaStream_t st) {
   if (nbc == 0) return 0;
   k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, NVg, NE, tri,
-                              label, code, xy, glist, nglist, ngtri, gcnt, cp);
+                              label, code, xy, cp);
   return 1;
 }
 

@@ -546,9 +546,15 @@ SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 *
 // lanes of a warp run cells of one size; cells above TN vertices go to the
 // warp kernel.  gcnt[n] holds the number of queued cells with n vertices
 // (n > TN pooled at index TN + 1).
-__global__ void __launch_bounds__(256) k_gorder(const CutRec* recs, const u32* glist, const u32* nglist,
-                                                const u32* gcnt, u32* gcur, u32* olist, u32* nolist, u32* wlist,
-                                                u32* nwlist) {
+// Each queued cell also gets its output range here, from the scans that the
+// emission kernel uses: its triangles follow those of its bucket's earlier
+// cells (one each when uncut, ntri each when cut) and its inside vertices
+// those of its bucket's earlier cut cells.  In the compact format only the
+// cut cells' triangles are listed.
+__global__ void __launch_bounds__(256) k_gorder(CutRec* recs, const u32* glist, const u32* nglist, const u32* gcnt,
+                                                u32* gcur, u32* olist, u32* nolist, u32* wlist, u32* nwlist,
+                                                const u32* bbase, const u32* extra_scan, const u32* chain_scan,
+                                                const u32* cut_scan, u32 CB0) {
   __shared__ u32 s_base[TN + 2];
   if (threadIdx.x == 0) {
     u32 run = 0;
@@ -565,7 +571,16 @@ __global__ void __launch_bounds__(256) k_gorder(const CutRec* recs, const u32* g
     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
     if (!valid) continue;
     const u32 ri = glist[i];
-    const int n = local_count(recs[ri]);
+    const CutRec rec = recs[ri];
+    const u32 b = rec.cell >> CB_LOG, rec0 = bbase[b];
+    u32 pt = 0, pc = 0;
+    for (u32 k = rec0; k < ri; ++k) {
+      const CutRec o = recs[k];
+      pt += o.ntri - 1, pc += o.nchain;
+    }
+    recs[ri].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + (ri - rec0) + pt : rec.cell + extra_scan[b] + pt;
+    recs[ri].chain_base = CB0 + chain_scan[b] + pc;
+    const int n = local_count(rec);
     const int key = n > TN ? TN + 1 : n;
     // one atomic per distinct size in the warp
     const unsigned peers = __match_any_sync(vmask, key);
@@ -629,13 +644,15 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
 }  // namespace
 
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
+                  const Seg* segs, const Event* events, CutRec* recs, const u32* glist, const u32* nglist,
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* bbase, const u32* extra_scan,
+                  const u32* chain_scan, const u32* cut_scan, u32 CB0, int* tri, unsigned short* label,
                   unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st) {
   // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
-  k_gorder<<<152 * 2, 256, 0, st>>>(recs, glist, nglist, gcnt, gcur, olist, nolist, wlist, nwlist);
+  k_gorder<<<152 * 2, 256, 0, st>>>(recs, glist, nglist, gcnt, gcur, olist, nolist, wlist, nwlist, bbase, extra_scan,
+                                    chain_scan, cut_scan, CB0);
   // each thread keeps a cell's state in local memory: give L1 the most room
   static const bool carve = [] {
     cudaFuncSetAttribute(k_tierg_thread, cudaFuncAttributePreferredSharedMemoryCarveout, 0);

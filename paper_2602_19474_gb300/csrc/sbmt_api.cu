@@ -169,6 +169,10 @@ const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_se
 struct Lane {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the Tier-G kernels run on a second stream beside the emission kernel,
+  // forked from and joined back into the lane's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   // per-call scratch: bump allocation in stream-ordered chunks
   std::vector<std::pair<char*, size_t>> chunks;
   size_t chunk_used = 0, call_bytes = 0;
@@ -254,23 +258,25 @@ void prof_collect(sbmt_ctx* c) {
 // brackets one kernel launch with events on the lane's stream when tracing
 struct ProfScope {
   Lane* L;
+  cudaStream_t s;
   int k, kernels = 0;
   cudaEvent_t a = nullptr;
-  ProfScope(sbmt_ctx* c, Lane* L_, int k_) : L(L_), k(k_) {
-    if (c->prof && (a = take_event(L->ev_pool))) cudaEventRecord(a, L->stream);
+  ProfScope(sbmt_ctx* c, Lane* L_, int k_, cudaStream_t s_) : L(L_), s(s_), k(k_) {
+    if (c->prof && (a = take_event(L->ev_pool))) cudaEventRecord(a, s);
   }
   ~ProfScope() {
     if (!a) return;
     cudaEvent_t b = take_event(L->ev_pool);
-    cudaEventRecord(b, L->stream);
+    cudaEventRecord(b, s);
     L->pending.push_back({k, kernels, a, b});
   }
 };
-#define TRACE(kn, call)            \
-  do {                             \
-    ProfScope ps_(ctx, lane, kn);  \
-    ps_.kernels = (call);          \
+#define TRACE_ON(kn, strm, call)           \
+  do {                                     \
+    ProfScope ps_(ctx, lane, kn, strm);    \
+    ps_.kernels = (call);                  \
   } while (0)
+#define TRACE(kn, call) TRACE_ON(kn, lane->stream, call)
 
 // scratch arena: every call bumps through the lane's chunks; a call that
 // needed more than one chunk leaves a single chunk of its total size for the
@@ -315,6 +321,25 @@ void lane_release(Lane* L) {
   for (cudaEvent_t e : L->ev_pool) cudaEventDestroy(e);
   L->ev_pool.clear();
   if (L->own_stream) cudaStreamDestroy(L->stream);
+  if (L->side) cudaStreamSynchronize(L->side), cudaStreamDestroy(L->side);
+  if (L->fork) cudaEventDestroy(L->fork);
+  if (L->join) cudaEventDestroy(L->join);
+}
+
+// the lane's second stream, made on first use (highest priority: the Tier-G
+// kernels' largest cells are the long pole of the call)
+int lane_side(Lane* L) {
+  if (L->side) return SBMT_OK;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithPriority(&L->side, cudaStreamNonBlocking, hi) != cudaSuccess) {
+    L->side = nullptr;
+    return fail(SBMT_ECUDA, "side stream");
+  }
+  if (cudaEventCreateWithFlags(&L->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&L->join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(SBMT_ECUDA, "fork/join events");
+  return SBMT_OK;
 }
 
 // callers hold ctx->reg
@@ -631,7 +656,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
-                                     err, st));
+                                     glist, nglist, ngtri, gcnt, err, st));
   if (nbc <= SCAN_ONE) {
     TRACE(KN_SCAN, launch_scan_pair(bextra, extra_scan, nullptr, nbc, bchain, chain_scan, nullptr, nbc, st));
   } else {
@@ -645,11 +670,18 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
       TRACE(KN_SCAN, launch_scan(bcut, 1, cut_scan, nbc, sscr, st));
     }
   }
+  // Tier-G beside the emission: both read the scans and the records, and
+  // write disjoint parts of the output
+  if ((rc = lane_side(lane))) return bail(rc);
+  CK(cudaEventRecord(lane->fork, st));
+  CK(cudaStreamWaitEvent(lane->side, lane->fork, 0));
+  TRACE_ON(KN_TIERG, lane->side,
+           launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist, nwlist,
+                        bbase, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
+                        m->label, m->code, m->xy, cp.xy0, err, lane->side));
+  CK(cudaEventRecord(lane->join, lane->side));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
-                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, glist, nglist, ngtri, gcnt, cp,
-                             st));
-  TRACE(KN_TIERG, launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist,
-                               nwlist, m->tri, m->label, m->code, m->xy, cp.xy0, err, st));
+                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, cp, st));
   // x of lattice vertex v(i, j) is indexed by m = 2i + j
   i64 m_lo = 0, m_hi = -1;
   for (i64 r = 0; r < nvr; ++r) {
@@ -660,6 +692,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   double* xtab;
   if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
   if (!compact) TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
+  CK(cudaStreamWaitEvent(st, lane->join, 0));
   CK(cudaGetLastError());
   // the status words: err, cut cells, Tier-G cells, Tier-G triangles
   CK(cudaMemcpyAsync(m->h_info, err, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));

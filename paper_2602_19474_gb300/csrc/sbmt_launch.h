@@ -51,7 +51,7 @@ int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRe
 // the patch of every Tier-T cell in stg (same index as its record).
 int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* err, cudaStream_t st);
+                     TStage* stg, u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st);
 
 // exclusive scan of n u32 values with stride `stride` into out (n + 1
 // entries, out[n] = total); inputs above 65536 values need scratch of
@@ -66,21 +66,24 @@ int launch_scan_pair(const u32* in_a, u32* out_a, u32* out2_a, u32 n_a, const u3
 int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
 
 // K4: per cell bucket, emit every uncut cell's base triangle and every
-// Tier-T cell's staged patch (Alg. 2) with its inside vertex; give each
-// Tier-G cell its output range and queue it into glist.
+// Tier-T cell's staged patch (Alg. 2) with its inside vertex (Tier-G cells
+// are skipped: k_cutcells queued them, the Tier-G kernels place them).
 int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
                  const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
-                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, u32* glist, u32* nglist,
-                 u32* ngtri, u32* gcnt, const CompactOut& cp, cudaStream_t st);
+                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, const CompactOut& cp,
+                 cudaStream_t st);
 
 // K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.  The
 // cells are first ordered by local vertex count, largest first, into olist
 // (gcnt: zeroed, 3 * (TIERG_TN + 2) words; its first TIERG_TN + 2 are the
-// per-count totals k_emit gathered); one thread per cell of at most
-// TIERG_TN vertices, one warp per larger cell (through wlist).
+// per-count totals k_cutcells gathered), each cell's output range taken from
+// the scans (cut_scan for the compact format, else null; CB0 = the first
+// inside-vertex id); one thread per cell of at most TIERG_TN vertices, one
+// warp per larger cell (through wlist).
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, const CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, int* tri, unsigned short* label,
+                  const Seg* segs, const Event* events, CutRec* recs, const u32* glist, const u32* nglist,
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* bbase, const u32* extra_scan,
+                  const u32* chain_scan, const u32* cut_scan, u32 CB0, int* tri, unsigned short* label,
                   unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st);
 
 // quality measures: per-triangle pass (mm: min angle, min area, max AR as
