@@ -469,7 +469,9 @@ int check_params(const sbmt_image* img, const sbmt_params* pr) {
 }
 
 // the whole path for one image, enqueued on one lane
-int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
+// fork: run the Tier-G kernels on the lane's second stream beside the
+// emission (single meshes; a batch's lanes already fill the device)
+int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out, bool fork) {
   int rc = check_params(img, pr);
   if (rc) return rc;
   cudaStream_t st = lane->stream;
@@ -672,14 +674,18 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   }
   // Tier-G beside the emission: both read the scans and the records, and
   // write disjoint parts of the output
-  if ((rc = lane_side(lane))) return bail(rc);
-  CK(cudaEventRecord(lane->fork, st));
-  CK(cudaStreamWaitEvent(lane->side, lane->fork, 0));
-  TRACE_ON(KN_TIERG, lane->side,
+  cudaStream_t gst = st;
+  if (fork) {
+    if ((rc = lane_side(lane))) return bail(rc);
+    CK(cudaEventRecord(lane->fork, st));
+    CK(cudaStreamWaitEvent(lane->side, lane->fork, 0));
+    gst = lane->side;
+  }
+  TRACE_ON(KN_TIERG, gst,
            launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist, nwlist,
                         bbase, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
-                        m->label, m->code, m->xy, cp.xy0, err, lane->side));
-  CK(cudaEventRecord(lane->join, lane->side));
+                        m->label, m->code, m->xy, cp.xy0, err, gst));
+  if (fork) CK(cudaEventRecord(lane->join, lane->side));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
                              (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, cp, st));
   // x of lattice vertex v(i, j) is indexed by m = 2i + j
@@ -692,7 +698,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   double* xtab;
   if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
   if (!compact) TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
-  CK(cudaStreamWaitEvent(st, lane->join, 0));
+  if (fork) CK(cudaStreamWaitEvent(st, lane->join, 0));
   CK(cudaGetLastError());
   // the status words: err, cut cells, Tier-G cells, Tier-G triangles
   CK(cudaMemcpyAsync(m->h_info, err, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -753,7 +759,7 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  return mesh_one(ctx, &ctx->main, img, params, out);
+  return mesh_one(ctx, &ctx->main, img, params, out, true);
 }
 
 int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
@@ -799,7 +805,7 @@ int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* 
     for (int i; (i = next.fetch_add(1)) < n;) {
       if (first_rc.load()) break;
       const int k = order[i];
-      const int rc = mesh_one(ctx, L, imgs + k, params + (n_params == 1 ? 0 : k), out + k);
+      const int rc = mesh_one(ctx, L, imgs + k, params + (n_params == 1 ? 0 : k), out + k, false);
       if (rc) {
         std::lock_guard<std::mutex> ml(msg_mu);
         if (!first_rc.load()) first_rc = rc, msg = sbmt_last_error();
