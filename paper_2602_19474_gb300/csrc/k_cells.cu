@@ -388,13 +388,13 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 
 // K3b: one thread per cut cell (dense): classification (key, sigma, class,
 // Tier-T / Tier-G, triangle and inside-vertex counts) added to the bucket's
-// totals, for a Tier-T cell its staged patch, and a Tier-G cell queued
-// (glist; the queued triangles in ngtri; per-size counts in gcnt, sizes
-// above TIERG_TN pooled at TIERG_TN + 1).
+// totals, for a Tier-T cell its staged patch, and a Tier-G cell counted
+// (cells in ngcell, triangles in ngtri, cells per local vertex count in
+// gcnt, counts above TIERG_TN pooled at TIERG_TN + 1).
 __global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                                   const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
                                                   const u32* nrec, u32* bextra, u32* bchain, TStage* stg,
-                                                  u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err) {
+                                                  u32* ngcell, u32* ngtri, u32* gcnt, u32* err) {
   const u32 total = *nrec;
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     CutRec rec = recs[i];
@@ -410,15 +410,12 @@ __global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* 
     atomicAdd(&bextra[b], kl.ntri - 1);
     if (kl.nchain) atomicAdd(&bchain[b], kl.nchain);
     if (kl.tierG) {
-      // one atomic per warp for the list and the triangle count, one per
+      // one atomic per warp for the cell and triangle counts, one per
       // distinct size for the per-size counts (n = ntri + 2 - n_i)
       const unsigned act = __activemask();
       const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
       const u32 t = __reduce_add_sync(act, kl.ntri);
-      u32 at = 0;
-      if (lane == lead) at = atomicAdd(nglist, (u32)__popc(act)), atomicAdd(ngtri, t);
-      at = __shfl_sync(act, at, lead) + (u32)__popc(act & ((1u << lane) - 1u));
-      glist[at] = i;
+      if (lane == lead) atomicAdd(ngcell, (u32)__popc(act)), atomicAdd(ngtri, t);
       const u32 n = kl.ntri + 2 - kl.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
       const unsigned peers = __match_any_sync(act, key);
       if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[key], (u32)__popc(peers));
@@ -620,9 +617,9 @@ int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRe
 
 int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st) {
+                     TStage* stg, u32* ngcell, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st) {
   k_cutcells<<<152 * 24, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, nrec, bextra, bchain, stg,
-                                       glist, nglist, ngtri, gcnt, err);
+                                       ngcell, ngtri, gcnt, err);
   return 1;
 }
 

@@ -544,16 +544,16 @@ SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 *
 
 // Tier-G cells ordered by local vertex count, largest first, so that the
 // lanes of a warp run cells of one size; cells above TN vertices go to the
-// warp kernel.  gcnt[n] holds the number of queued cells with n vertices
-// (n > TN pooled at index TN + 1).
-// Each queued cell also gets its output range here, from the scans that the
-// emission kernel uses: its triangles follow those of its bucket's earlier
-// cells (one each when uncut, ntri each when cut) and its inside vertices
-// those of its bucket's earlier cut cells.  In the compact format only the
-// cut cells' triangles are listed.
-__global__ void __launch_bounds__(256) k_gorder(CutRec* recs, const u32* glist, const u32* nglist, const u32* gcnt,
-                                                u32* gcur, u32* olist, u32* nolist, u32* wlist, u32* nwlist,
-                                                const u32* bbase, const u32* extra_scan, const u32* chain_scan,
+// warp kernel.  gcnt[n] holds the number of Tier-G cells with n vertices
+// (n > TN pooled at index TN + 1).  One warp per cell bucket scans the
+// bucket's records (in cell order) and gives each Tier-G cell its output
+// range from the scans the emission kernel uses: its triangles follow those
+// of the bucket's earlier cells (one each when uncut, ntri each when cut)
+// and its inside vertices those of the bucket's earlier cut cells.  In the
+// compact format only the cut cells' triangles are listed.
+__global__ void __launch_bounds__(256) k_gorder(CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
+                                                const u32* gcnt, u32* gcur, u32* olist, u32* nolist, u32* wlist,
+                                                u32* nwlist, const u32* extra_scan, const u32* chain_scan,
                                                 const u32* cut_scan, u32 CB0) {
   __shared__ u32 s_base[TN + 2];
   if (threadIdx.x == 0) {
@@ -563,33 +563,41 @@ __global__ void __launch_bounds__(256) k_gorder(CutRec* recs, const u32* glist, 
     if (blockIdx.x == 0) *nolist = run;
   }
   __syncthreads();
-  const u32 total = *nglist;
   const int lane = threadIdx.x & 31;
-  for (u32 i0 = blockIdx.x * blockDim.x; i0 < total; i0 += gridDim.x * blockDim.x) {
-    const u32 i = i0 + threadIdx.x;
-    const bool valid = i < total;
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-    if (!valid) continue;
-    const u32 ri = glist[i];
-    const CutRec rec = recs[ri];
-    const u32 b = rec.cell >> CB_LOG, rec0 = bbase[b];
-    u32 pt = 0, pc = 0;
-    for (u32 k = rec0; k < ri; ++k) {
-      const CutRec o = recs[k];
-      pt += o.ntri - 1, pc += o.nchain;
+  const u32 nwarps = gridDim.x * (blockDim.x >> 5);
+  for (u32 b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nbc; b += nwarps) {
+    const u32 n = bcut[b], rec0 = bbase[b];
+    u32 ct = 0, cc = 0;  // the bucket's earlier records: sum of (ntri - 1), of nchain
+    for (u32 base = 0; base < n; base += 32) {
+      const u32 r = base + (u32)lane;
+      const bool valid = r < n;
+      CutRec rec{};
+      if (valid) rec = recs[rec0 + r];
+      const u32 vt = valid ? rec.ntri - 1u : 0u, vc = valid ? rec.nchain : 0u;
+      u32 it = vt, ic = vc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, it, o), c = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) it += t, ic += c;
+      }
+      const u32 pt = ct + it - vt, pc = cc + ic - vc;
+      ct += __shfl_sync(0xffffffffu, it, 31), cc += __shfl_sync(0xffffffffu, ic, 31);
+      const bool tg = valid && (rec.code & (1u << 16));
+      const unsigned tmask = __ballot_sync(0xffffffffu, tg);
+      if (!tg) continue;
+      recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
+      recs[rec0 + r].chain_base = CB0 + chain_scan[b] + pc;
+      const int nv = local_count(rec);
+      const int key = nv > TN ? TN + 1 : nv;
+      // one atomic per distinct size in the warp
+      const unsigned peers = __match_any_sync(tmask, key);
+      const int leader = __ffs(peers) - 1;
+      u32 at = 0;
+      if (lane == leader) at = atomicAdd(key > TN ? nwlist : &gcur[key], (u32)__popc(peers));
+      at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
+      if (key > TN) wlist[at] = rec0 + r;
+      else olist[s_base[key] + at] = rec0 + r;
     }
-    recs[ri].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + (ri - rec0) + pt : rec.cell + extra_scan[b] + pt;
-    recs[ri].chain_base = CB0 + chain_scan[b] + pc;
-    const int n = local_count(rec);
-    const int key = n > TN ? TN + 1 : n;
-    // one atomic per distinct size in the warp
-    const unsigned peers = __match_any_sync(vmask, key);
-    const int leader = __ffs(peers) - 1;
-    u32 at = 0;
-    if (lane == leader) at = atomicAdd(key > TN ? nwlist : &gcur[key], (u32)__popc(peers));
-    at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
-    if (key > TN) wlist[at] = ri;
-    else olist[s_base[key] + at] = ri;
   }
 }
 
@@ -644,14 +652,16 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
 }  // namespace
 
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* bbase, const u32* extra_scan,
-                  const u32* chain_scan, const u32* cut_scan, u32 CB0, int* tri, unsigned short* label,
-                  unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st) {
+                  const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
+                  const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
+                  u32 xy0, u32* err, cudaStream_t st) {
   // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
-  k_gorder<<<152 * 2, 256, 0, st>>>(recs, glist, nglist, gcnt, gcur, olist, nolist, wlist, nwlist, bbase, extra_scan,
+  if (nbc == 0) return 0;
+  const u32 gblocks = std::min<u32>((nbc + 7) / 8, 152 * 8);
+  k_gorder<<<gblocks, 256, 0, st>>>(recs, bcut, bbase, nbc, gcnt, gcur, olist, nolist, wlist, nwlist, extra_scan,
                                     chain_scan, cut_scan, CB0);
   // each thread keeps a cell's state in local memory: give L1 the most room
   static const bool carve = [] {

@@ -591,7 +591,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   Pair *pairs, *sorted;
   Event* ev;
   CutRec* recs;
-  u32 *bcut, *bbase, *extra_scan, *chain_scan, *glist, *olist, *wlist, *elist, *eidx;
+  u32 *bcut, *bbase, *extra_scan, *chain_scan, *olist, *wlist, *elist, *eidx;
   TStage* stg;
   u32* cstart;
   if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
@@ -619,7 +619,6 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if ((rc = aalloc(lane, &extra_scan, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &chain_scan, nbc + 1))) return bail(rc);
   if ((rc = aalloc(lane, &stg, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &glist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &wlist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
   if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
@@ -658,7 +657,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
-                                     glist, nglist, ngtri, gcnt, err, st));
+                                     nglist, ngtri, gcnt, err, st));
   if (nbc <= SCAN_ONE) {
     TRACE(KN_SCAN, launch_scan_pair(bextra, extra_scan, nullptr, nbc, bchain, chain_scan, nullptr, nbc, st));
   } else {
@@ -682,8 +681,8 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
     gst = lane->side;
   }
   TRACE_ON(KN_TIERG, gst,
-           launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, glist, nglist, gcnt, olist, wlist, nwlist,
-                        bbase, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
+           launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, bcut, bbase, nbc, gcnt, olist, wlist,
+                        nwlist, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
                         m->label, m->code, m->xy, cp.xy0, err, gst));
   if (fork) CK(cudaEventRecord(lane->join, lane->side));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,

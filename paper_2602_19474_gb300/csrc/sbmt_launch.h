@@ -51,7 +51,7 @@ int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRe
 // the patch of every Tier-T cell in stg (same index as its record).
 int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
                      const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* glist, u32* nglist, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st);
+                     TStage* stg, u32* ngcell, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st);
 
 // exclusive scan of n u32 values with stride `stride` into out (n + 1
 // entries, out[n] = total); inputs above 65536 values need scratch of
@@ -81,10 +81,10 @@ int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, 
 // inside-vertex id); one thread per cell of at most TIERG_TN vertices, one
 // warp per larger cell (through wlist).
 int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, CutRec* recs, const u32* glist, const u32* nglist,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* bbase, const u32* extra_scan,
-                  const u32* chain_scan, const u32* cut_scan, u32 CB0, int* tri, unsigned short* label,
-                  unsigned short* code, double* xy, u32 xy0, u32* err, cudaStream_t st);
+                  const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
+                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
+                  const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
+                  u32 xy0, u32* err, cudaStream_t st);
 
 // quality measures: per-triangle pass (mm: min angle, min area, max AR as
 // double bits; cnt: slivers, equilateral; part: per-block area sums; ar:
