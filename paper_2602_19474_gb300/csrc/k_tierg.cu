@@ -116,12 +116,13 @@ SBMT_DEV bool cand_less_fast(const GStore<N>& s, unsigned short x, unsigned shor
   return cand_less(s, x, y);
 }
 
-// orientation of (u, v, w) computed exactly on demand
+// cand_less_fast with the sort's padding entries (0xFFFF) last
 template <int N>
-struct OriDirect {
-  const GStore<N>* s;
-  SBMT_DEV int operator()(int u, int v, int w) const { return orient3(lpt(*s, u), lpt(*s, v), lpt(*s, w)); }
-};
+SBMT_DEV bool cand_less_sent(const GStore<N>& s, unsigned short x, unsigned short y, float tolc) {
+  if (x == 0xFFFFu) return false;
+  if (y == 0xFFFFu) return true;
+  return cand_less_fast(s, x, y, tolc);
+}
 
 // orientation of every vertex triple computed once (exactly) into two bit
 // sets indexed by the sorted triple; a permutation of the triple flips the
@@ -321,7 +322,7 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
           if (l > i) {
             const unsigned short x = s.cand[i], y = s.cand[l];
             const bool up = (i & kk) == 0;
-            if (up ? cand_less(s, y, x) : cand_less(s, x, y)) s.cand[i] = y, s.cand[l] = x;
+            if (up ? cand_less_sent(s, y, x, tolc) : cand_less_sent(s, x, y, tolc)) s.cand[i] = y, s.cand[l] = x;
           }
         }
         __syncwarp();
@@ -407,6 +408,14 @@ SBMT_DEV int ori_filtered(const GStore<N>& s, int a, int b, int c, float tol) {
   if (d < -tol) return -1;
   return orient3(lpt(s, a), lpt(s, b), lpt(s, c));
 }
+
+// orientation decided in single precision when clear, exactly otherwise
+template <int N>
+struct OriFiltered {
+  const GStore<N>* s;
+  float tol;
+  SBMT_DEV int operator()(int u, int v, int w) const { return ori_filtered(*s, u, v, w, tol); }
+};
 
 template <int N>
 SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
@@ -643,7 +652,9 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
       __syncwarp();
       continue;
     }
-    greedy_faces<32, WN>(s, lane, boundary_count(rec), OriDirect<WN>{&s}, 0.f);
+    // cell-local coordinates are bounded by the cell extent M = 6p scaled units
+    const float M = (float)(6 * g.p);
+    greedy_faces<32, WN>(s, lane, boundary_count(rec), OriFiltered<WN>{&s, 8e-6f * M * M}, 1e-4f * M * M);
     write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, xy0, err);
     __syncwarp();
   }
@@ -655,7 +666,7 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
                   const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
                   const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32 xy0, u32* err, cudaStream_t st) {
+                  u32 xy0, u32* err, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order, cudaEvent_t ev_warp) {
   // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
@@ -671,8 +682,15 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
   (void)carve;
   k_tierg_thread<<<152 * TG_BLOCKS_PER_SM, 64, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist,
                                                         nolist, tri, label, code, xy, xy0, err);
-  k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist, nwlist,
-                                                tri, label, code, xy, xy0, err);
+  // the warp kernel on its own stream when given one, beside the thread kernel
+  if (st2) {
+    if (cudaEventRecord(ev_order, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_order, 0) != cudaSuccess) return -1;
+  }
+  k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist,
+                                                            nwlist, tri, label, code, xy, xy0, err);
+  if (st2) {
+    if (cudaEventRecord(ev_warp, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_warp, 0) != cudaSuccess) return -1;
+  }
   return 3;
 }
 

@@ -171,8 +171,8 @@ struct Lane {
   bool own_stream = false;
   // the Tier-G kernels run on a second stream beside the emission kernel,
   // forked from and joined back into the lane's stream
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr, side2 = nullptr;  // side2: the Tier-G warp kernel
+  cudaEvent_t fork = nullptr, join = nullptr, order = nullptr, warp = nullptr;
   // per-call scratch: bump allocation in stream-ordered chunks
   std::vector<std::pair<char*, size_t>> chunks;
   size_t chunk_used = 0, call_bytes = 0;
@@ -322,23 +322,27 @@ void lane_release(Lane* L) {
   L->ev_pool.clear();
   if (L->own_stream) cudaStreamDestroy(L->stream);
   if (L->side) cudaStreamSynchronize(L->side), cudaStreamDestroy(L->side);
-  if (L->fork) cudaEventDestroy(L->fork);
-  if (L->join) cudaEventDestroy(L->join);
+  if (L->side2) cudaStreamSynchronize(L->side2), cudaStreamDestroy(L->side2);
+  for (cudaEvent_t e : {L->fork, L->join, L->order, L->warp})
+    if (e) cudaEventDestroy(e);
 }
 
-// the lane's second stream, made on first use (highest priority: the Tier-G
-// kernels' largest cells are the long pole of the call)
+// the lane's second and third streams, made on first use (highest priority:
+// the Tier-G kernels' largest cells are the long pole of the call)
 int lane_side(Lane* L) {
-  if (L->side) return SBMT_OK;
+  if (L->side && L->side2) return SBMT_OK;
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  if (cudaStreamCreateWithPriority(&L->side, cudaStreamNonBlocking, hi) != cudaSuccess) {
-    L->side = nullptr;
-    return fail(SBMT_ECUDA, "side stream");
-  }
-  if (cudaEventCreateWithFlags(&L->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&L->join, cudaEventDisableTiming) != cudaSuccess)
-    return fail(SBMT_ECUDA, "fork/join events");
+  for (cudaStream_t* s : {&L->side, &L->side2})
+    if (!*s && cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, hi) != cudaSuccess) {
+      *s = nullptr;
+      return fail(SBMT_ECUDA, "side stream");
+    }
+  for (cudaEvent_t* e : {&L->fork, &L->join, &L->order, &L->warp})
+    if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+      *e = nullptr;
+      return fail(SBMT_ECUDA, "fork/join events");
+    }
   return SBMT_OK;
 }
 
@@ -680,10 +684,13 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
     CK(cudaStreamWaitEvent(lane->side, lane->fork, 0));
     gst = lane->side;
   }
+  int ntg = 0;
   TRACE_ON(KN_TIERG, gst,
-           launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, bcut, bbase, nbc, gcnt, olist, wlist,
+           ntg = launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, bcut, bbase, nbc, gcnt, olist, wlist,
                         nwlist, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
-                        m->label, m->code, m->xy, cp.xy0, err, gst));
+                        m->label, m->code, m->xy, cp.xy0, err, gst, fork ? lane->side2 : nullptr, lane->order,
+                        lane->warp));
+  if (ntg < 0) return bail(fail(SBMT_ECUDA, "Tier-G stream events"));
   if (fork) CK(cudaEventRecord(lane->join, lane->side));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
                              (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, cp, st));

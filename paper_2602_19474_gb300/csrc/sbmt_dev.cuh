@@ -23,7 +23,7 @@ constexpr u32 NONE = 0xFFFFFFFFu;
 constexpr int OUTSIDE = 0x10000;  // label outside the image: above every pixel label
 constexpr int CB_LOG = 10;        // base cells per cell bucket (2^10)
 constexpr int EB_LOG = 11;        // grid-edge ids per event bucket (2^11)
-constexpr int TIERG_TN = 12;      // Tier-G cells up to this many local vertices run one thread each
+constexpr int TIERG_TN = 9;      // Tier-G cells up to this many local vertices run one thread each
 
 // device error bits (reported through mesh_query)
 enum : u32 {
