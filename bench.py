@@ -12,7 +12,7 @@ of the workload (independent images, no collective on the data path) and
 the time is the maximum over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload voronoi8192|ellipses2048|disk64|noise512]
+                  [--workload voronoi8192|voronoi4096|ellipses2048|disk64|noise512]
 
 noise512 is the batched workload: one step meshes 512 thresholded-noise
 bitmaps (sides log-uniform in [128, 2048], h = 2 px) with one mesh_batch
@@ -50,6 +50,9 @@ WORKLOADS = {
     "voronoi8192": dict(gen=lambda: synth.voronoi_labels(), h=(2, 1),
                         desc="8192x8192 u16, 16 labels on the Voronoi cells of 4096 uniform seeds, 5x5 majority "
                              "filter, h=2 px"),
+    "voronoi4096": dict(gen=lambda: synth.voronoi_labels(size=4096, nseeds=1024), h=(2, 1),
+                        desc="4096x4096 u16, 16 labels on the Voronoi cells of 1024 uniform seeds, 5x5 majority "
+                             "filter, h=2 px (a quarter of voronoi8192, for detailed profiles)"),
     "ellipses2048": dict(gen=lambda: synth.ellipses(), h=(4, 1),
                          desc="2048x2048 u8, union of 200 filled ellipses (semi-axes 10-150 px), h=4 px"),
     "disk64": dict(gen=lambda: synth.disk(), h=(2, 1), desc="64x64 u8 filled disk r=20 (1257 px), h=2 px"),
