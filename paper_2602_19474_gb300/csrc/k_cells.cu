@@ -481,14 +481,24 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
   const int row0 = s_row0;
   // uncut cells: the base triangle (A, B, C), untouched.  Per strip row the
   // corner ids are row base + i, the centroid's pixel row is tabulated, and
-  // its pixel column is an integer floor.
+  // its pixel column is an integer floor.  A thread's four cells (the block
+  // has 256 threads for 1024 cells) are set up first with their pixel loads
+  // issued, then written, so that the loads are in flight together.
+  static_assert(NB == 4 * 256, "four cells per thread");
   int r = -1;
   i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0, jr = 0;
   int lr0 = 0, lr1 = 0;
   const i64 twoS = 2 * g.S;
   const float inv2S = 1.0f / (float)twoS;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-    if (s_cnt[k] != 1u) continue;
+  int tv0[4], tv1[4], tv2[4], traw[4];
+  u32 to[4];
+  bool tuc[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = (int)threadIdx.x + j * 256;
+    tuc[j] = k < nc && s_cnt[k] == 1u;
+    traw[j] = OUTSIDE, tv0[j] = tv1[j] = tv2[j] = 0, to[j] = 0;
+    if (!tuc[j]) continue;
     const i64 cid = c0 + k;
     if (r < 0 || cid >= cb_r + (g.chi[r] - clo_r + 1)) {
       if (r < 0) r = row0;
@@ -498,14 +508,14 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       lr0 = g.lrow[2 * r], lr1 = g.lrow[2 * r + 1];
     }
     const i64 c = clo_r + (cid - cb_r), i = c >> 1;
-    const u32 o = T0_ + s_off[k];
-    int v0, v1, v2, prow;
+    to[j] = T0_ + s_off[k];
+    int prow;
     i64 xc;
     if ((c & 1) == 0) {
-      v0 = (int)(vb0 + i), v1 = (int)(vb0 + i + 1), v2 = (int)(vb1 + i);
+      tv0[j] = (int)(vb0 + i), tv1[j] = (int)(vb0 + i + 1), tv2[j] = (int)(vb1 + i);
       xc = g.ox + 3 * g.p * (2 * i + jr + 1), prow = lr0;
     } else {
-      v0 = (int)(vb0 + i + 1), v1 = (int)(vb1 + i + 1), v2 = (int)(vb1 + i);
+      tv0[j] = (int)(vb0 + i + 1), tv1[j] = (int)(vb1 + i + 1), tv2[j] = (int)(vb1 + i);
       xc = g.ox + 3 * g.p * (2 * i + jr + 2), prow = lr1;
     }
     // pixel column floor((2 xc + S) / 2S) in 32 bits: a float estimate, corrected
@@ -513,16 +523,22 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
     int pcol = (int)floorf((float)num * inv2S);
     while (pcol * den > num) --pcol;
     while ((pcol + 1) * den <= num) ++pcol;
-    const int l = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
-                             : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
-    const unsigned short lab = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
+    traw[j] = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
+                         : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!tuc[j]) continue;
+    const unsigned short lab = traw[j] == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)traw[j];
     if (cp.on) {  // the base triangle stays implicit: its cell's label and code
+      const i64 cid = c0 + (int)threadIdx.x + j * 256;
       cp.cell_label[cid] = lab, cp.cell_code[cid] = 0;
       continue;
     }
-    tri[3 * (i64)o] = v0;
-    tri[3 * (i64)o + 1] = v1;
-    tri[3 * (i64)o + 2] = v2;
+    const u32 o = to[j];
+    tri[3 * (i64)o] = tv0[j];
+    tri[3 * (i64)o + 1] = tv1[j];
+    tri[3 * (i64)o + 2] = tv2[j];
     label[o] = lab;
     code[o] = 0;
   }
