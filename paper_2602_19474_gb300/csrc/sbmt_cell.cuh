@@ -23,7 +23,7 @@ SBMT_DEV CellGeo cell_geo(const GridP& g, u32 cid, int r) {
 }
 // strip row of cell id cid: a proportional estimate, corrected
 SBMT_DEV int cell_row_near(const GridP& g, u32 cid) {
-  int r = (int)((float)cid * ((float)g.nrows / (float)g.ncells));
+  int r = (int)((float)cid * ((float)g.nrows / i2f(g.ncells)));
   r = max(0, min(g.nrows - 1, r));
   while (r > 0 && g.cbase[r] > (i64)cid) --r;
   while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;

@@ -64,9 +64,30 @@ SBMT_HD int zsign(Zq v) {
 SBMT_HD int zcmp(Zq x, Zq y) { return zsign(x - y); }
 SBMT_HD double zdouble(Zq v) { return (double)v.a + (double)v.b * 1.7320508075688772935; }
 
+// Conversions between 64-bit integers and float on the 32-bit path: this
+// part runs 64-bit conversions at its double-precision rate, a small
+// fraction of the single-precision one.  A value within 32 bits converts in
+// one instruction; a larger one as two halves joined by an FMA (one more
+// rounding).  floor_i64 takes the 32-bit path below 2e9.
+SBMT_HD float i2f(i64 v) {
+#ifdef __CUDA_ARCH__
+  const int lo = (int)v;
+  if ((i64)lo == v) return (float)lo;
+  return fmaf((float)(int)(v >> 32), 4294967296.0f, (float)(unsigned)v);
+#else
+  return (float)v;
+#endif
+}
+SBMT_HD i64 floor_i64(float x) {
+#ifdef __CUDA_ARCH__
+  if (fabsf(x) < 2.0e9f) return (i64)(int)floorf(x);
+#endif
+  return (i64)floorf(x);
+}
+
 // floor(a / d) for d > 0: a float estimate corrected exactly (|a / d| < 2^30)
 SBMT_HD i64 ifloordiv(i64 a, i64 d) {
-  i64 k = (i64)floorf((float)a / (float)d);
+  i64 k = floor_i64(i2f(a) / i2f(d));
   while (k * d > a) --k;
   while ((k + 1) * d <= a) ++k;
   return k;
@@ -75,14 +96,16 @@ SBMT_HD i64 ifloordiv(i64 a, i64 d) {
 // floor(v / d) for d > 0, exact.  A single-precision estimate x of
 // (a + b sqrt3) / d is off by at most 2.4e-7 (|a| + 2|b|) / d (rounding of
 // the two conversions, the constant, the product, the sum and the quotient,
-// each 2^-24 relative); when x is farther than that from an integer its
-// floor is the answer, else the exact sign of v - k d decides.
+// each 2^-24 relative), and by at most 3.0e-7 (|a| + 2|b|) / d when a or b
+// needs more than 32 bits (one more rounding in its conversion, i2f); when
+// x is farther than 4e-7 (|a| + 2|b|) / d from an integer its floor is the
+// answer, else the exact sign of v - k d decides.
 SBMT_HD i64 zfloordiv(Zq v, i64 d) {
-  const float x = ((float)v.a + (float)v.b * 1.7320508f) / (float)d;
-  i64 k = (i64)floorf(x);
-  const float fr = x - (float)k;
-  const float tol =
-      4e-7f * ((float)(v.a < 0 ? -v.a : v.a) + 2.0f * (float)(v.b < 0 ? -v.b : v.b)) / (float)d + 1e-6f;
+  const float fd = i2f(d);
+  const float x = (i2f(v.a) + i2f(v.b) * 1.7320508f) / fd;
+  i64 k = floor_i64(x);
+  const float fr = x - i2f(k);
+  const float tol = 4e-7f * (i2f(v.a < 0 ? -v.a : v.a) + 2.0f * i2f(v.b < 0 ? -v.b : v.b)) / fd + 1e-6f;
   if (fr > tol && fr < 1.0f - tol) return k;
   while (zsign(v - zq(k * d)) < 0) --k;
   while (zsign(v - zq((k + 1) * d)) >= 0) ++k;
@@ -220,7 +243,7 @@ SBMT_DEV Pq corner_pt(const GridP& g, i64 cx, i64 cy) {
 // strip row holding a point of height y (never on a grid line)
 SBMT_HD i64 strip_of(const GridP& g, Zq y) {
   // y_j = oy + 3 p j sqrt3
-  i64 j = (i64)floorf(((float)(y.a - g.oy) + (float)y.b * 1.7320508f) / (3.0f * (float)g.p * 1.7320508f));
+  i64 j = floor_i64((i2f(y.a - g.oy) + i2f(y.b) * 1.7320508f) / (3.0f * (float)g.p * 1.7320508f));
   while (zcmp(zq(g.oy, 3 * g.p * j), y) > 0) --j;
   while (zcmp(zq(g.oy, 3 * g.p * (j + 1)), y) <= 0) ++j;
   return j;
