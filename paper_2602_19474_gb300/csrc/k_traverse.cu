@@ -245,28 +245,35 @@ SBMT_DEV Zq event_t(const Event& e) {
 // edge nearer the edge's lower endpoint), compared exactly.  A bucket of at
 // most 256 events ranks each event against the others held in shared
 // memory; a larger one counting-sorts its events by edge first.
-__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
-                                              u32 NVg, double* xy, u32 xy0) {
-  constexpr int NEB = 1 << EB_LOG;
-  __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
-  __shared__ u32 s_sh[8];
-  __shared__ u32 s_edge[256];
-  __shared__ int s_ta[256], s_tb[256];
+// The registry, small buckets (at most RANK_SMALL events, nearly all of
+// them): a 64-thread block per bucket, each event ranked by a count over
+// the bucket's events held in shared memory.
+constexpr u32 RANK_SMALL = 256;
+__global__ void __launch_bounds__(64) k_rank_small(GridP g, Event* ev, const u32* eidx, const u32* eoff, u32 NVg,
+                                                   double* xy, u32 xy0) {
+  __shared__ u32 s_edge[RANK_SMALL];
+  __shared__ int s_ta[RANK_SMALL], s_tb[RANK_SMALL];
   const u32 lo = eoff[blockIdx.x], n = eoff[blockIdx.x + 1] - lo;
-  if (n == 0) return;
+  if (n == 0 || n > RANK_SMALL) return;
   const double invS = 1.0 / (double)g.S;
-  if (n <= 256) {
-    const u32 i = threadIdx.x;
-    u32 me = 0;
-    Event x{};
+  u32 me[RANK_SMALL / 64];
+  Event xs[RANK_SMALL / 64];
+#pragma unroll
+  for (int u = 0; u < (int)(RANK_SMALL / 64); ++u) {
+    const u32 i = threadIdx.x + 64u * u;
     if (i < n) {
-      me = eidx[lo + i];
-      x = ev[me];
-      const bool horiz = x.edge % 3u == 0u;
-      s_edge[i] = x.edge, s_ta[i] = horiz ? x.xa : x.ya, s_tb[i] = horiz ? x.xb : x.yb;
+      me[u] = eidx[lo + i];
+      xs[u] = ev[me[u]];
+      const bool horiz = xs[u].edge % 3u == 0u;
+      s_edge[i] = xs[u].edge, s_ta[i] = horiz ? xs[u].xa : xs[u].ya, s_tb[i] = horiz ? xs[u].xb : xs[u].yb;
     }
-    __syncthreads();
-    if (i >= n) return;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < (int)(RANK_SMALL / 64); ++u) {
+    const u32 i = threadIdx.x + 64u * u;
+    if (i >= n) break;
+    const Event& x = xs[u];
     const Zq ti = zq(s_ta[i], s_tb[i]);
     u32 rank = 0;
     for (u32 q = 0; q < n; ++q) {
@@ -274,49 +281,65 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
       if (eq < x.edge || (eq == x.edge && q != i && zcmp(zq(s_ta[q], s_tb[q]), ti) < 0)) ++rank;
     }
     const u32 gid = NVg + lo + rank;
-    ev[me].gid = gid;
+    ev[me[u]].gid = gid;
     double2 v;
     v.x = zdouble(zq(x.xa, x.xb)) * invS;
     v.y = zdouble(zq(x.ya, x.yb)) * invS;
     reinterpret_cast<double2*>(xy)[gid - xy0] = v;
-    return;
   }
-  const u32 e0 = blockIdx.x << EB_LOG;
-  for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[ev[eidx[lo + i]].edge - e0], 1u);
-  __syncthreads();
-  {
-    constexpr int PER = NEB / 256;
-    const int k0 = threadIdx.x * PER;
-    u32 s = 0;
-    for (int u = 0; u < PER; ++u) s += s_cnt[k0 + u];
-    u32 tot;
-    u32 run = block_exscan256(s, &tot, s_sh);
-    for (int u = 0; u < PER; ++u) s_off[k0 + u] = run, s_cur[k0 + u] = run, run += s_cnt[k0 + u];
-  }
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-    const u32 slot = atomicAdd(&s_cur[ev[eidx[lo + i]].edge - e0], 1u);
-    elist[lo + slot] = eidx[lo + i];
-  }
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-    const u32 me = eidx[lo + i];
-    const Event ei = ev[me];
-    const Zq ti = event_t(ei);
-    const u32 k = ei.edge - e0, first = s_off[k], cnt = s_cnt[k];
-    u32 rank = first;
-    for (u32 q = 0; q < cnt; ++q) {
-      const u32 j = elist[lo + first + q];
-      if (j != me && zcmp(event_t(ev[j]), ti) < 0) ++rank;
+}
+
+// The registry, large buckets (grid-edge buckets along the image border
+// collect thousands of events): a counting sort of the bucket's events by
+// grid edge, then each event ranked among those of its own edge.  A short
+// grid walks over all buckets and skips the small ones.
+__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
+                                              u32 nbe, u32 NVg, double* xy, u32 xy0) {
+  constexpr int NEB = 1 << EB_LOG;
+  __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
+  __shared__ u32 s_sh[8];
+  const double invS = 1.0 / (double)g.S;
+  for (u32 b = blockIdx.x; b < nbe; b += gridDim.x) {
+    const u32 lo = eoff[b], n = eoff[b + 1] - lo;
+    if (n <= RANK_SMALL) continue;
+    const u32 e0 = b << EB_LOG;
+    for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[ev[eidx[lo + i]].edge - e0], 1u);
+    __syncthreads();
+    {
+      constexpr int PER = NEB / 256;
+      const int k0 = threadIdx.x * PER;
+      u32 s = 0;
+      for (int u = 0; u < PER; ++u) s += s_cnt[k0 + u];
+      u32 tot;
+      u32 run = block_exscan256(s, &tot, s_sh);
+      for (int u = 0; u < PER; ++u) s_off[k0 + u] = run, s_cur[k0 + u] = run, run += s_cnt[k0 + u];
     }
-    const u32 gid = NVg + lo + rank;
-    ev[me].gid = gid;
-    double2 v;
-    v.x = zdouble(zq(ei.xa, ei.xb)) * invS;
-    v.y = zdouble(zq(ei.ya, ei.yb)) * invS;
-    reinterpret_cast<double2*>(xy)[gid - xy0] = v;
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+      const u32 slot = atomicAdd(&s_cur[ev[eidx[lo + i]].edge - e0], 1u);
+      elist[lo + slot] = eidx[lo + i];
+    }
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+      const u32 me = eidx[lo + i];
+      const Event ei = ev[me];
+      const Zq ti = event_t(ei);
+      const u32 k = ei.edge - e0, first = s_off[k], cnt = s_cnt[k];
+      u32 rank = first;
+      for (u32 q = 0; q < cnt; ++q) {
+        const u32 j = elist[lo + first + q];
+        if (j != me && zcmp(event_t(ev[j]), ti) < 0) ++rank;
+      }
+      const u32 gid = NVg + lo + rank;
+      ev[me].gid = gid;
+      double2 v;
+      v.x = zdouble(zq(ei.xa, ei.xb)) * invS;
+      v.y = zdouble(zq(ei.ya, ei.yb)) * invS;
+      reinterpret_cast<double2*>(xy)[gid - xy0] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -357,8 +380,9 @@ int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pc
 int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
                         u32 NVg, double* xy, u32 xy0, cudaStream_t st) {
   if (nbe == 0) return 0;
-  k_rank<<<nbe, 256, 0, st>>>(g, events, eidx, elist, eoff, NVg, xy, xy0);
-  return 1;
+  k_rank_small<<<nbe, 64, 0, st>>>(g, events, eidx, eoff, NVg, xy, xy0);
+  k_rank<<<152 * 2, 256, 0, st>>>(g, events, eidx, elist, eoff, nbe, NVg, xy, xy0);
+  return 2;
 }
 
 }  // namespace sbmt
