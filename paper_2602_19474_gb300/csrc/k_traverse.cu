@@ -257,15 +257,14 @@ __global__ void __launch_bounds__(64) k_rank_small(GridP g, Event* ev, const u32
   if (n == 0 || n > RANK_SMALL) return;
   const double invS = 1.0 / (double)g.S;
   u32 me[RANK_SMALL / 64];
-  Event xs[RANK_SMALL / 64];
 #pragma unroll
   for (int u = 0; u < (int)(RANK_SMALL / 64); ++u) {
     const u32 i = threadIdx.x + 64u * u;
     if (i < n) {
       me[u] = eidx[lo + i];
-      xs[u] = ev[me[u]];
-      const bool horiz = xs[u].edge % 3u == 0u;
-      s_edge[i] = xs[u].edge, s_ta[i] = horiz ? xs[u].xa : xs[u].ya, s_tb[i] = horiz ? xs[u].xb : xs[u].yb;
+      const Event x = ev[me[u]];
+      const bool horiz = x.edge % 3u == 0u;
+      s_edge[i] = x.edge, s_ta[i] = horiz ? x.xa : x.ya, s_tb[i] = horiz ? x.xb : x.yb;
     }
   }
   __syncthreads();
@@ -273,14 +272,15 @@ __global__ void __launch_bounds__(64) k_rank_small(GridP g, Event* ev, const u32
   for (int u = 0; u < (int)(RANK_SMALL / 64); ++u) {
     const u32 i = threadIdx.x + 64u * u;
     if (i >= n) break;
-    const Event& x = xs[u];
+    const u32 xe = s_edge[i];
     const Zq ti = zq(s_ta[i], s_tb[i]);
     u32 rank = 0;
     for (u32 q = 0; q < n; ++q) {
       const u32 eq = s_edge[q];
-      if (eq < x.edge || (eq == x.edge && q != i && zcmp(zq(s_ta[q], s_tb[q]), ti) < 0)) ++rank;
+      if (eq < xe || (eq == xe && q != i && zcmp(zq(s_ta[q], s_tb[q]), ti) < 0)) ++rank;
     }
     const u32 gid = NVg + lo + rank;
+    const Event x = ev[me[u]];
     ev[me[u]].gid = gid;
     double2 v;
     v.x = zdouble(zq(x.xa, x.xb)) * invS;
@@ -378,10 +378,18 @@ int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pc
 }
 
 int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, u32 xy0, cudaStream_t st) {
+                        u32 NVg, double* xy, u32 xy0, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
+                        cudaEvent_t ev_b) {
   if (nbe == 0) return 0;
+  // the large buckets on st2 beside the small ones when given (disjoint buckets)
+  if (st2) {
+    if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess) return -1;
+  }
+  k_rank<<<152 * 2, 256, 0, st2 ? st2 : st>>>(g, events, eidx, elist, eoff, nbe, NVg, xy, xy0);
   k_rank_small<<<nbe, 64, 0, st>>>(g, events, eidx, eoff, NVg, xy, xy0);
-  k_rank<<<152 * 2, 256, 0, st>>>(g, events, eidx, elist, eoff, nbe, NVg, xy, xy0);
+  if (st2) {
+    if (cudaEventRecord(ev_b, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return -1;
+  }
   return 2;
 }
 

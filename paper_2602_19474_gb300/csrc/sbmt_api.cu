@@ -658,7 +658,11 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
   m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
   // registry, K3, scans, K4, K4-G, lattice coordinates
-  TRACE(KN_RANK, launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st));
+  if (fork && (rc = lane_side(lane))) return bail(rc);
+  int nrk = 0;
+  TRACE(KN_RANK, nrk = launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st,
+                                          fork ? lane->side : nullptr, lane->fork, lane->join));
+  if (nrk < 0) return bail(fail(SBMT_ECUDA, "registry stream events"));
   TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
   TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
                                      nglist, ngtri, gcnt, err, st));

@@ -37,8 +37,12 @@ int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pc
 
 // frozen registry: rank the events of each event bucket (listed in eidx) by
 // (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
+// With st2 the few large buckets are ranked there beside the small ones
+// (ev_a, ev_b fork and join); returns the kernels launched, -1 when an
+// event call failed.
 int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, u32 xy0, cudaStream_t st);
+                        u32 NVg, double* xy, u32 xy0, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
+                        cudaEvent_t ev_b);
 
 // K3a: sort each cell bucket's pairs by cell into sorted; one record per cut
 // cell, in cell order, in a dense range of recs drawn from *nrec (bucket b:
