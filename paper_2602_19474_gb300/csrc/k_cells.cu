@@ -391,7 +391,7 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 // totals, for a Tier-T cell its staged patch, and a Tier-G cell counted
 // (cells in ngcell, triangles in ngtri, cells per local vertex count in
 // gcnt, counts above TIERG_TN pooled at TIERG_TN + 1).
-__global__ void __launch_bounds__(128) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
+__global__ void __launch_bounds__(128, 8) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
                                                   const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
                                                   const u32* nrec, u32* bextra, u32* bchain, TStage* stg,
                                                   u32* ngcell, u32* ngtri, u32* gcnt, u32* err) {
