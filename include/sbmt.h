@@ -43,7 +43,7 @@ extern "C" {
 #define SBMT_ENOMEM (-2)    /* device allocation failed */
 #define SBMT_EPENDING (-3)  /* mesh_query poll: work not finished yet */
 #define SBMT_ETIMEDOUT (-4) /* mesh_query: wait limit reached */
-#define SBMT_ECAPACITY (-5) /* a cell holds more boundary vertices than the per-cell limit */
+#define SBMT_ECAPACITY (-5) /* a cell holds more boundary vertices than the per-cell limit (mesh_stage 4 lists them) */
 #define SBMT_EPROTO (-6)    /* requested mode is not available (SBMT_PREPROCESS) */
 #define SBMT_ECUDA (-7)     /* a CUDA call failed (message in sbmt_last_error) */
 #define SBMT_EINTERNAL (-8) /* a device-side consistency check failed */
@@ -164,7 +164,8 @@ int mesh_release(sbmt_ctx* ctx, sbmt_mesh mesh);
 int mesh_destroy(sbmt_ctx* ctx);
 
 /* Intermediate arrays of a finished mesh made with SBMT_KEEP_STAGES, copied
- * to host memory, for checking each step on its own:
+ * to host memory, for checking each step on its own (stage 4 is kept for
+ * every mesh):
  *  stage 1 boundary segments, 8 int32 each: corner x, corner y, direction
  *          (0 +x, 1 +y), length, label below/left, label above/right (0xFFFF
  *          = outside), reversed (1 when the lower label lies left of -x/-y),
@@ -172,7 +173,11 @@ int mesh_destroy(sbmt_ctx* ctx);
  *  stage 2 grid-edge events in vertex-id order, 4 int64 each: grid-edge id,
  *          vertex id, packed segment start corner (y * (W + 1) + x), dir;
  *  stage 3 cut cells in id order, 5 int64 each: cell id, code, triangles,
- *          boundary vertices inside, outside-regime flag.
+ *          boundary vertices inside, outside-regime flag;
+ *  stage 4 the cells whose local boundary graph has more vertices than the
+ *          per-cell limit of the Tier-G rule (64), the reason for the status
+ *          SBMT_ECAPACITY: their ids in increasing order, 1 int64 each, the
+ *          first 1024 of them; *n is their total number.
  * Writes min(n, cap) records to host_out and the total count to *n. */
 int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n);
 

@@ -198,12 +198,12 @@ def mesh_destroy(ctx: int) -> None:
 
 
 def mesh_stage(ctx: int, mesh: int, stage: int) -> np.ndarray:
-    width = {1: (8, np.int32), 2: (4, np.int64), 3: (5, np.int64)}[stage]
+    width = {1: (8, np.int32), 2: (4, np.int64), 3: (5, np.int64), 4: (1, np.int64)}[stage]
     n = ctypes.c_int64(0)
     _check(load().mesh_stage(ctx, mesh, stage, None, 0, ctypes.byref(n)))
     buf = np.zeros((max(n.value, 1), width[0]), dtype=width[1])
     _check(load().mesh_stage(ctx, mesh, stage, buf.ctypes.data, n.value, ctypes.byref(n)))
-    return buf[: n.value]
+    return buf[: min(n.value, 1024) if stage == 4 else n.value]
 
 
 def mesh_quality(ctx: int, mesh: int) -> dict:

@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned cha
                                                       const Pair* sorted, const Seg* segs, const Event* ev,
                                                       const CutRec* recs, const u32* olist, const u32* nolist,
                                                       int* tri, unsigned short* label, unsigned short* code,
-                                                      double* xy, u32 xy0, u32* err) {
+                                                      double* xy, u32 xy0, u32* err, u32* nover, u32* over) {
   const u32 total = *nolist;
   for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
     const CutRec rec = recs[olist[item]];
@@ -624,6 +624,8 @@ __global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned cha
     build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
     if (!s.ok) {
       atomicOr(err, ERR_CAPACITY);
+      const u32 slot = atomicAdd(nover, 1u);
+      if (slot < OVER_CAP) over[slot] = rec.cell;
       continue;
     }
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
@@ -637,7 +639,8 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
                                                             const Pair* sorted, const Seg* segs, const Event* ev,
                                                             const CutRec* recs, const u32* wlist, const u32* nwlist,
                                                             int* tri, unsigned short* label, unsigned short* code,
-                                                            double* xy, u32 xy0, u32* err) {
+                                                            double* xy, u32 xy0, u32* err, u32* nover,
+                                                            u32* over) {
   __shared__ GStore<WN> sm[WWARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   GStore<WN>& s = sm[w];
@@ -648,7 +651,11 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsig
     if (lane == 0) build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
     __syncwarp();
     if (!s.ok) {
-      if (lane == 0) atomicOr(err, ERR_CAPACITY);
+      if (lane == 0) {
+        atomicOr(err, ERR_CAPACITY);
+        const u32 slot = atomicAdd(nover, 1u);
+        if (slot < OVER_CAP) over[slot] = rec.cell;
+      }
       __syncwarp();
       continue;
     }
@@ -666,7 +673,8 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
                   const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
                   const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32 xy0, u32* err, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order, cudaEvent_t ev_warp) {
+                  u32 xy0, u32* err, u32* nover, u32* over, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
+                  cudaEvent_t ev_warp) {
   // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
   u32* gcur = gcnt + (TN + 2);
   u32* nolist = gcnt + 2 * (TN + 2);
@@ -681,13 +689,13 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
   }();
   (void)carve;
   k_tierg_thread<<<152 * TG_BLOCKS_PER_SM, 64, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist,
-                                                        nolist, tri, label, code, xy, xy0, err);
+                                                        nolist, tri, label, code, xy, xy0, err, nover, over);
   // the warp kernel on its own stream when given one, beside the thread kernel
   if (st2) {
     if (cudaEventRecord(ev_order, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_order, 0) != cudaSuccess) return -1;
   }
   k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist,
-                                                            nwlist, tri, label, code, xy, xy0, err);
+                                                            nwlist, tri, label, code, xy, xy0, err, nover, over);
   if (st2) {
     if (cudaEventRecord(ev_warp, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_warp, 0) != cudaSuccess) return -1;
   }

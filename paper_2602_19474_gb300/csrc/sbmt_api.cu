@@ -127,7 +127,8 @@ struct MeshRec {
   unsigned short* cell_code = nullptr;
   u32* patch_cell = nullptr;
   u32* patch_off = nullptr;
-  u32* h_info = nullptr;  // pinned: err, ncut, ntierg, tierg triangles
+  u32* h_info = nullptr;  // pinned: err, ncut, ntierg, tierg triangles, cells over the Tier-G limit
+  u32* over_cells = nullptr;  // device: ids of the cells over the Tier-G limit (OVER_CAP at most)
   int W = 0, H = 0;
   // kept intermediates (SBMT_KEEP_STAGES)
   bool keep = false;
@@ -542,7 +543,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   unsigned long long* cnt64 = (unsigned long long*)zero;
   u32* cnt32 = zero + 8;
   u32 *nseg = cnt32 + 0, *nwlist = cnt32 + 1, *err = cnt32 + 2, *nrec = cnt32 + 3, *nglist = cnt32 + 4,
-      *ngtri = cnt32 + 5;
+      *ngtri = cnt32 + 5, *nover = cnt32 + 6;
   u32* pcnt = zero + 16;
   u32* ecnt = pcnt + nbc + 1;
   u32* bextra = ecnt + nbe + 1;
@@ -638,7 +639,8 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   const size_t off_cl = up(off_code + bcode), off_cc = up(off_cl + (compact ? 2 * (size_t)tb.ncells : 0));
   const size_t off_pc = up(off_cc + (compact ? 2 * (size_t)tb.ncells : 0));
   const size_t off_po = up(off_pc + (compact ? 4 * NP : 0));
-  const size_t total = off_po + (compact ? 4 * (NP + 1) : 0) + 256;
+  const size_t off_ov = up(off_po + (compact ? 4 * (NP + 1) : 0));
+  const size_t total = off_ov + 4 * (size_t)OVER_CAP + 256;
   if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
     return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
   char* ob = (char*)m->out_block;
@@ -646,6 +648,7 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   m->tri = (int*)(ob + off_tri);
   m->label = (unsigned short*)(ob + off_lab);
   m->code = (unsigned short*)(ob + off_code);
+  m->over_cells = (u32*)(ob + off_ov);
   CompactOut cp{0, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
   u32* cut_scan = nullptr;
   if (compact) {
@@ -692,8 +695,8 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   TRACE_ON(KN_TIERG, gst,
            ntg = launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, bcut, bbase, nbc, gcnt, olist, wlist,
                         nwlist, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
-                        m->label, m->code, m->xy, cp.xy0, err, gst, fork ? lane->side2 : nullptr, lane->order,
-                        lane->warp));
+                        m->label, m->code, m->xy, cp.xy0, err, nover, m->over_cells, gst,
+                        fork ? lane->side2 : nullptr, lane->order, lane->warp));
   if (ntg < 0) return bail(fail(SBMT_ECUDA, "Tier-G stream events"));
   if (fork) CK(cudaEventRecord(lane->join, lane->side));
   TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
@@ -710,8 +713,9 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   if (!compact) TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
   if (fork) CK(cudaStreamWaitEvent(st, lane->join, 0));
   CK(cudaGetLastError());
-  // the status words: err, cut cells, Tier-G cells, Tier-G triangles
-  CK(cudaMemcpyAsync(m->h_info, err, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  // the status words: err, cut cells, Tier-G cells, Tier-G triangles, cells
+  // over the Tier-G limit
+  CK(cudaMemcpyAsync(m->h_info, err, 5 * sizeof(u32), cudaMemcpyDeviceToHost, st));
   if (m->keep) {
     // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
     m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bcut = bcut;
@@ -1104,6 +1108,17 @@ int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t
   auto it = ctx->meshes.find(mesh);
   if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
   MeshRec* m = it->second;
+  if (stage == 4) {  // cells over the Tier-G limit, for every mesh
+    CK(cudaEventSynchronize(m->done));
+    const u32 cnt = m->h_info[4], kept = std::min<u32>(cnt, OVER_CAP);
+    std::vector<u32> ids(kept);
+    if (kept) CK(cudaMemcpy(ids.data(), m->over_cells, kept * sizeof(u32), cudaMemcpyDeviceToHost));
+    std::sort(ids.begin(), ids.end());
+    *n = (int64_t)cnt;
+    int64_t* o = (int64_t*)host_out;
+    for (int64_t k = 0; k < std::min<int64_t>(cap, (int64_t)kept); ++k) o[k] = (int64_t)ids[k];
+    return SBMT_OK;
+  }
   if (!m->keep) return fail(SBMT_EINVAL, "mesh made without SBMT_KEEP_STAGES");
   CK(cudaEventSynchronize(m->done));
   if (stage == 1) {

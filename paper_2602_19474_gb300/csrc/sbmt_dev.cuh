@@ -24,11 +24,12 @@ constexpr int OUTSIDE = 0x10000;  // label outside the image: above every pixel 
 constexpr int CB_LOG = 10;        // base cells per cell bucket (2^10)
 constexpr int EB_LOG = 11;        // grid-edge ids per event bucket (2^11)
 constexpr int TIERG_TN = 9;      // Tier-G cells up to this many local vertices run one thread each
+constexpr u32 OVER_CAP = 1024;   // ids of cells over the Tier-G vertex limit kept per mesh
 
 // device error bits (reported through mesh_query)
 enum : u32 {
   ERR_TRAVERSAL = 1u,  // a segment left the cell set / inconsistent walk
-  ERR_CAPACITY = 2u,   // a Tier-G cell exceeded the per-cell vertex limit
+  ERR_CAPACITY = 2u,   // a Tier-G cell exceeded the per-cell vertex limit (ids listed, OVER_CAP at most)
   ERR_COUNT = 4u,      // a patch did not have the expected triangle count
   ERR_SEGBUF = 8u,     // segment buffer too small (retried by the host)
 };

@@ -83,7 +83,9 @@ int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, 
 // per-count totals k_cutcells gathered), each cell's output range taken from
 // the scans (cut_scan for the compact format, else null; CB0 = the first
 // inside-vertex id); one thread per cell of at most TIERG_TN vertices, one
-// warp per larger cell (through wlist).  With st2 the warp kernel runs there,
+// warp per larger cell (through wlist).  A cell over the per-cell limit
+// sets ERR_CAPACITY, counts itself in *nover and lists its id in over
+// (OVER_CAP at most).  With st2 the warp kernel runs there,
 // after ev_order (recorded on st after the ordering), and st waits for it
 // through ev_warp; without, everything runs on st.  Returns the kernels
 // launched, or -1 when an event call failed.
@@ -91,8 +93,8 @@ int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype,
                   const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
                   u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
                   const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32 xy0, u32* err, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
-                  cudaEvent_t ev_warp);
+                  u32 xy0, u32* err, u32* nover, u32* over, cudaStream_t st, cudaStream_t st2,
+                  cudaEvent_t ev_order, cudaEvent_t ev_warp);
 
 // quality measures: per-triangle pass (mm: min angle, min area, max AR as
 // double bits; cnt: slivers, equilateral; part: per-block area sums; ar:
