@@ -236,6 +236,29 @@ def oracle_sample(img: np.ndarray, h: tuple, side: int) -> tuple:
     return m["n_triangles"], dt
 
 
+def _oracle_image(args):
+    """One bitmap through the oracle (a worker of the batch CPU baseline)."""
+    import oracle
+
+    img, hn, hd = args
+    return oracle.mesh_bitmap(img, hn, hd)["n_triangles"]
+
+
+def oracle_batch_sample(imgs, h: tuple, n: int) -> tuple:
+    """The oracle over the first n bitmaps of a batch on every host core, one
+    bitmap per task (spawned workers): (triangles, bitmaps, seconds, cores)."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    sample = [(np.ascontiguousarray(x), h[0], h[1]) for x in imgs[:n]]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_image, sample[:cores])  # workers up and the library loaded
+        t0 = time.perf_counter()
+        tris = sum(pool.map(_oracle_image, sample, chunksize=1))
+        dt = time.perf_counter() - t0
+    return tris, len(sample), dt, cores
+
+
 def reference_arm(args, rank: int, world: int):
     """The oracle, as it stands, on the host cores: same metric and config."""
     if rank != 0:
@@ -592,6 +615,7 @@ def batch_arm(args, rank: int, world: int, dist):
         return
     peak, peak_kind = measured_peak()
     path_bytes = float(px) + 16.0 * T + 16.0 * V
+    ntri_cpu, nimg_cpu, t_cpu, cores = oracle_batch_sample(imgs, (hn, hd), 128)
     out = {
         "metric": "output triangles/sec", "value": job_rate(world, T, ms), "unit": "triangles/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -609,6 +633,10 @@ def batch_arm(args, rank: int, world: int, dist):
         "roofline_path": {"achieved": path_bytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                           "frac": path_bytes / (ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                           "algorithmic_bytes_per_step": path_bytes},
+        "cpu_baseline": {"value": ntri_cpu / t_cpu, "unit": "triangles/s", "cores": cores, "kind": "oracle",
+                         "bitmaps_per_s": nimg_cpu / t_cpu,
+                         "sample": "the first %d bitmaps of the batch, one per task over %d host cores"
+                                   % (nimg_cpu, cores)},
         "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
