@@ -124,40 +124,6 @@ SBMT_DEV bool cand_less_sent(const GStore<N>& s, unsigned short x, unsigned shor
   return cand_less_fast(s, x, y, tolc);
 }
 
-// orientation of every vertex triple computed once (exactly) into two bit
-// sets indexed by the sorted triple; a permutation of the triple flips the
-// sign with its parity
-template <int N>
-struct OriTable {
-  static constexpr int NT = N * (N - 1) * (N - 2) / 6;
-  static constexpr int NW = (NT + 63) / 64;
-  u64 pos[NW], zero[NW];
-  SBMT_DEV static int idx(int a, int b, int c) { return c * (c - 1) * (c - 2) / 6 + b * (b - 1) / 2 + a; }
-  SBMT_DEV void build(const GStore<N>& s) {
-    for (int k = 0; k < NW; ++k) pos[k] = 0, zero[k] = 0;
-    for (int c = 2; c < s.n; ++c) {
-      const Pq pc = lpt(s, c);
-      for (int b = 1; b < c; ++b) {
-        const Pq pb = lpt(s, b);
-        for (int a = 0; a < b; ++a) {
-          const int o = orient3(lpt(s, a), pb, pc), t = idx(a, b, c);
-          if (o == 0) zero[t >> 6] |= 1ull << (t & 63);
-          else if (o > 0) pos[t >> 6] |= 1ull << (t & 63);
-        }
-      }
-    }
-  }
-  SBMT_DEV int operator()(int u, int v, int w) const {
-    int sg = 1, t;
-    if (u > v) t = u, u = v, v = t, sg = -sg;
-    if (v > w) t = v, v = w, w = t, sg = -sg;
-    if (u > v) t = u, u = v, v = t, sg = -sg;
-    const int i = idx(u, v, w);
-    if ((zero[i >> 6] >> (i & 63)) & 1ull) return 0;
-    return ((pos[i >> 6] >> (i & 63)) & 1ull) ? sg : -sg;
-  }
-};
-
 // Build the local boundary graph (one thread): corners A, B, C; the events
 // on AB, BC, CA in counter-clockwise order; the inside vertices by pixel-
 // corner id; constraint edges = boundary cycle + one piece per pair.
