@@ -79,6 +79,10 @@ def _load():
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         lib.oracle_template.restype = ctypes.c_int
         lib.oracle_template.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+        lib.oracle_base_mesh.restype = ctypes.c_int
+        lib.oracle_base_mesh.argtypes = [ctypes.c_int32] * 6 + [ctypes.POINTER(ctypes.c_int64)] * 2 + [
+            ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_greedy.restype = ctypes.c_int
         lib.oracle_greedy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_int32]
@@ -191,3 +195,21 @@ def greedy(points, constraints):
     if n < 0:
         raise OracleError("greedy failed")
     return tri[: 3 * n].reshape(-1, 3).copy()
+
+
+def base_mesh(width: int, height: int, h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0):
+    """The base mesh T0 (Sec. 3.3): lattice vertex coordinates (V, 2) in
+    vertex-id order and the cells' corners A, B, C (C, 3) in cell-id order."""
+    lib = _load()
+    nv, nc = ctypes.c_int64(0), ctypes.c_int64(0)
+    xy = ctypes.POINTER(ctypes.c_double)()
+    tri = ctypes.POINTER(ctypes.c_int32)()
+    rc = lib.oracle_base_mesh(width, height, h_num, h_den, origin2x, origin2y, ctypes.byref(nv), ctypes.byref(nc),
+                              ctypes.byref(xy), ctypes.byref(tri))
+    if rc != 0:
+        raise OracleError("oracle_base_mesh failed (%d): %s" % (rc, lib.oracle_last_error().decode()))
+    try:
+        return (_copy(xy, 2 * nv.value, np.float64).reshape(-1, 2), _copy(tri, 3 * nc.value, np.int32).reshape(-1, 3))
+    finally:
+        lib.oracle_free(ctypes.cast(xy, ctypes.c_void_p))
+        lib.oracle_free(ctypes.cast(tri, ctypes.c_void_p))

@@ -1073,4 +1073,44 @@ int oracle_greedy(const int64_t* pts4, int32_t n, const int32_t* cons, int32_t n
   return (int)t.size();
 }
 
+/* The base mesh T0 of Sec. 3.3 (the lattice cells meeting the closed image
+ * rectangle, no boundary embedded), the input of the preprocessing of
+ * Alg. 3: lattice vertex coordinates (2 doubles each, vertex-id order) and
+ * the cells' corners A, B, C (3 vertex ids each, cell-id order).  Free the
+ * two arrays with oracle_free. */
+int oracle_base_mesh(int32_t width, int32_t height, int32_t h_num, int32_t h_den, int32_t origin2x, int32_t origin2y,
+                     int64_t* nverts, int64_t* ncells, double** xy, int32_t** tri) {
+  g_err[0] = 0;
+  if (!nverts || !ncells || !xy || !tri || width < 1 || height < 1 || h_num < 1 || h_den < 1 || (h_num % 2) != 0 ||
+      (h_den % 2) != 1 || (origin2x % 2) != 0 || (origin2y % 2) != 0) {
+    std::snprintf(g_err, sizeof g_err, "invalid arguments");
+    return -1;
+  }
+  try {
+    Grid g;
+    build_grid(g, width, height, h_num, h_den, origin2x, origin2y);
+    std::vector<double> v;
+    for (i64 j = g.vj0; j <= g.vj1; ++j)
+      for (i64 i = g.vlo[j - g.vj0]; i <= g.vhi[j - g.vj0]; ++i) {
+        const Pt q = g.vtx(i, j);
+        v.push_back(to_double(q.x) / (double)g.S), v.push_back(to_double(q.y) / (double)g.S);
+      }
+    std::vector<int32_t> t;
+    for (i64 j = g.j0; j <= g.j1; ++j)
+      for (i64 c = g.clo[j - g.j0]; c <= g.chi[j - g.j0]; ++c) {
+        i64 ci[3], cj[3];
+        g.corners(c, j, ci, cj);
+        for (int k = 0; k < 3; ++k) t.push_back((int32_t)g.vid(ci[k], cj[k]));
+      }
+    *nverts = g.nverts, *ncells = g.ncells;
+    *xy = dup(v), *tri = dup(t);
+    return 0;
+  } catch (const std::exception& ex) {
+    std::snprintf(g_err, sizeof g_err, "%s", ex.what());
+    return -2;
+  }
+}
+
+void oracle_free(void* p) { free(p); }
+
 }  // extern "C"

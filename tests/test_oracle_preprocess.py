@@ -1,0 +1,128 @@
+"""Pins of the preprocessing oracle (Alg. 3): the thresholds' scale and
+admissible range, a single pixel worked by hand, a constant image whose
+border distances have a closed form, and on label images: every snap to the
+nearest boundary point (a k-d tree query), every repelled vertex at distance
+c from the boundary (dense sampling of the boundary), every elimination
+within b, and the re-fanned mesh's triangle count and orientation."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import preprocess as P
+from paper_2602_19474_gb300 import synth
+
+TRIPLET = (0.26, 0.125, 0.183)  # App. I's first admissible triplet
+
+
+def test_thresholds_scale_and_admissible_range():
+    A, B, C = P.thresholds_px(*TRIPLET, h=2.0)
+    s = 2.0 / math.sqrt(0.45)
+    assert abs(A - 0.26 * s) < 1e-15 and abs(B - 0.125 * s) < 1e-15 and abs(C - 0.183 * s) < 1e-15
+    with pytest.raises(P.NotAdmissible):  # c >= a / sqrt(2): the paper's (0.24, 0.115, 0.17)
+        P.thresholds_px(0.24, 0.115, 0.17, h=2.0)
+    with pytest.raises(P.NotAdmissible):  # b >= a / 2
+        P.thresholds_px(0.26, 0.13, 0.1, h=2.0)
+    with pytest.raises(P.NotAdmissible):  # a >= h / 2
+        P.thresholds_px(0.4, 0.1, 0.1, h=2.0)
+
+
+def test_single_pixel_by_hand():
+    # one pixel [-1/2, 1/2]^2; lattice vertex v(0,0) at the origin is 1/sqrt(2)
+    # from all four corners, inside the snapping radius 0.775: it snaps, the
+    # tie going to corner (0, 0) at (-1/2, -1/2)
+    img = np.ones((1, 1), np.uint8)
+    r = P.preprocess(img, 2, 1, *TRIPLET)
+    xy0, _ = oracle.base_mesh(1, 1, 2, 1)
+    k = int(np.nonzero((xy0 == [0.0, 0.0]).all(1))[0][0])
+    assert r["status"][k] == 1 and r["snap"][k] == 0
+    assert tuple(r["xy"][k]) == (-0.5, -0.5)
+    pid, ppos = P.boundary_points(img)
+    assert list(pid) == [0, 1, 2, 3] and np.array_equal(ppos, [[-0.5, -0.5], [0.5, -0.5], [-0.5, 0.5], [0.5, 0.5]])
+
+
+def test_constant_image_border_in_closed_form():
+    H, W = 9, 13
+    img = np.full((H, W), 3, np.uint8)
+    A, B, C = P.thresholds_px(*TRIPLET, h=2.0)
+    xy0, _ = oracle.base_mesh(W, H, 2, 1)
+    r = P.preprocess(img, 2, 1, *TRIPLET)
+    corners = np.array([[-0.5, -0.5], [W - 0.5, -0.5], [-0.5, H - 0.5], [W - 0.5, H - 0.5]])
+    lo, hi = np.array([-0.5, -0.5]), np.array([W - 0.5, H - 0.5])
+    for k, v in enumerate(xy0):
+        dc = np.sqrt(((corners - v) ** 2).sum(1))
+        if dc.min() < A:  # snaps to the nearest image corner
+            assert r["status"][k] == 1 and np.array_equal(r["xy"][k], corners[np.argmin(dc)])
+            continue
+        inside = (v > lo).all() and (v < hi).all()
+        if inside:  # nearest point of the border: the nearest side
+            ds = np.array([v[0] - lo[0], hi[0] - v[0], v[1] - lo[1], hi[1] - v[1]])
+            s = int(np.argmin(ds))
+            q = v.copy()
+            q[s // 2] = lo[s // 2] if s % 2 == 0 else hi[s // 2]
+            d = ds[s]
+        else:
+            q = np.clip(v, lo, hi)
+            d = float(np.sqrt(((v - q) ** 2).sum()))
+        if d < C:
+            assert r["status"][k] == 2
+            assert np.allclose(r["xy"][k], q + C * (v - q) / d, rtol=0, atol=1e-12)
+        else:
+            assert r["status"][k] == 0 and np.array_equal(r["xy"][k], v)
+
+
+def _sampled_boundary(img, step=1e-3):
+    _, seg = P.boundary_edges(img)
+    t = np.arange(0.0, 1.0 + step / 2, step)
+    pts = seg[:, None, 0, :] + t[None, :, None] * (seg[:, None, 1, :] - seg[:, None, 0, :])
+    return pts.reshape(-1, 2)
+
+
+@pytest.mark.parametrize("name,img,hn,hd", [
+    ("disk", synth.disk(), 2, 1),
+    ("voronoi", synth.voronoi_labels(size=96, nseeds=12), 2, 1),
+    ("noise_third", synth.noise_bitmap(synth.rng_for(17), 40, 32, 2.0), 2, 3),
+])
+def test_steps_on_label_images(name, img, hn, hd):
+    from scipy.spatial import cKDTree
+
+    h = hn / hd
+    A, B, C = P.thresholds_px(*TRIPLET, h=h)
+    xy0, cells = oracle.base_mesh(img.shape[1], img.shape[0], hn, hd)
+    r = P.preprocess(img, hn, hd, *TRIPLET)
+    V = len(xy0)
+    pid, ppos = P.boundary_points(img)
+    # Step 1: a snap is to the nearest boundary point, closer than a
+    d, _ = cKDTree(ppos).query(xy0)
+    snapped = r["status"] == 1
+    assert np.array_equal(snapped, d < A)
+    assert np.allclose(np.sqrt(((r["xy"][:V][snapped] - xy0[snapped]) ** 2).sum(1)), d[snapped], rtol=0, atol=1e-12)
+    # Step 2: a repelled vertex was closer than c to the boundary and ends at
+    # distance c from it (dense samples of the boundary pixel edges)
+    tree = cKDTree(_sampled_boundary(img))
+    before, _ = tree.query(xy0)
+    after, _ = tree.query(r["xy"][:V])
+    rep = r["status"] == 2
+    kept = r["status"] == 0
+    assert (before[rep] < C + 1e-3).all() and (before[kept] >= C - 1e-3).all()
+    assert np.abs(after[rep] - C).max() <= 2e-3
+    # Step 3: every elimination point is within b of its edge (after Steps 1-2)
+    for p, u, w in r["eliminations"]:
+        q = ppos[np.searchsorted(pid, p)]
+        a_, b_ = r["xy"][u], r["xy"][w]
+        t = np.clip(np.dot(q - a_, b_ - a_) / np.dot(b_ - a_, b_ - a_), 0, 1)
+        assert np.linalg.norm(q - (a_ + t * (b_ - a_))) < B
+    # re-fanned mesh: one more triangle per cell beside an eliminated edge,
+    # every triangle counter-clockwise
+    edges = {}
+    for c_ in cells:
+        for k in range(3):
+            e = (min(c_[k], c_[(k + 1) % 3]), max(c_[k], c_[(k + 1) % 3]))
+            edges[e] = edges.get(e, 0) + 1
+    extra = sum(edges[(min(u, w), max(u, w))] for _, u, w in r["eliminations"])
+    assert len(r["tri"]) == len(cells) + extra
+    assert len(r["xy"]) == V + len(r["eliminations"])
+    p3 = r["xy"][r["tri"]]
+    area = (p3[:, 1, 0] - p3[:, 0, 0]) * (p3[:, 2, 1] - p3[:, 0, 1]) - (p3[:, 1, 1] - p3[:, 0, 1]) * (p3[:, 2, 0] - p3[:, 0, 0])
+    assert (area > 0).all()
