@@ -44,7 +44,7 @@ extern "C" {
 #define SBMT_EPENDING (-3)  /* mesh_query poll: work not finished yet */
 #define SBMT_ETIMEDOUT (-4) /* mesh_query: wait limit reached */
 #define SBMT_ECAPACITY (-5) /* a cell holds more boundary vertices than the per-cell limit (mesh_stage 4 lists them) */
-#define SBMT_EPROTO (-6)    /* requested mode is not available (SBMT_PREPROCESS) */
+#define SBMT_EPROTO (-6)    /* requested mode is not available (SBMT_PREPROCESS in mesh_bitmap) */
 #define SBMT_ECUDA (-7)     /* a CUDA call failed (message in sbmt_last_error) */
 #define SBMT_EINTERNAL (-8) /* a device-side consistency check failed */
 #define SBMT_ENOENT (-9)    /* unknown mesh handle */
@@ -74,8 +74,10 @@ typedef struct {
  * 1..63, origin2x and origin2y even.  Under it no grid vertex lies on a
  * pixel line and no pixel corner on a grid edge, so every Alg. 1 event is a
  * proper crossing; other parameters return SBMT_EINVAL.  mode must be
- * SBMT_PLAIN (the thresholds a, b, c of Alg. 3 are reserved for
- * SBMT_PREPROCESS, which returns SBMT_EPROTO).  format selects the storage
+ * SBMT_PLAIN for mesh_bitmap and mesh_batch (SBMT_PREPROCESS returns
+ * SBMT_EPROTO there: the template retriangulation of Alg. 3's Region III is
+ * not built) and SBMT_PREPROCESS for mesh_preprocess, which reads the
+ * thresholds a, b, c.  format selects the storage
  * of the mesh (see sbmt_mesh_view): SBMT_EXPLICIT lists every triangle;
  * SBMT_COMPACT keeps the untouched base mesh implicit -- the paper's
  * "preserve the base mesh" (Sec. 1, Sec. 3.3) as a storage format. */
@@ -146,6 +148,59 @@ int mesh_create(sbmt_ctx** ctx, int device, size_t pool_bytes, void* cuda_stream
  * call synchronises with the device twice to size its buffers.  The mesh
  * is complete when mesh_query returns SBMT_OK. */
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out);
+
+/* Geometric preprocessing of the base mesh (Alg. 3, Steps 1-3): the mesh T
+ * that Alg. 3's template retriangulation starts from.  params->mode must be
+ * SBMT_PREPROCESS and params->format SBMT_EXPLICIT.  The thresholds a, b, c
+ * are relative to the reference edge length sqrt(0.45) px of the paper's
+ * experiments (Sec. 4, App. I: a = 0.26, b = 0.125, c = 0.183 is
+ * admissible), so in pixels they are a h / sqrt(0.45) etc.; they must lie
+ * in the admissible range b < a/2, c < a/sqrt2 (Eq. "admissible range") and
+ * a < h/2, else SBMT_EINVAL.  Boundary points are the PSLG vertices, the
+ * pixel corners with id y (W + 1) + x; boundary segments are the boundary
+ * pixel edges.
+ *  Step 1  a lattice vertex moves onto the boundary point nearest to it when
+ *          that point is closer than a (ties: the smaller id);
+ *  Step 2  a vertex that did not snap moves away from the nearest point q of
+ *          the boundary segments (ties: the smaller pixel-edge id, horizontal
+ *          edge (m, k) between pixels (m, k-1) and (m, k) has id k W + m,
+ *          vertical edge (m, k) between (m-1, k) and (m, k) has id
+ *          (H + 1) W + k (W + 1) + m) along q -> v to distance c, when q is
+ *          closer than c;
+ *  Step 3  a boundary point p closer than b to an edge e of the moved mesh,
+ *          neither end of e at p, is a candidate (p, e).  It applies when e
+ *          is p's smallest candidate edge (by smaller end id, then larger)
+ *          and no smaller point is a candidate on an edge of the triangles
+ *          beside e.  p becomes vertex n_lattice_vertices + (its rank by id
+ *          among the applied points), and each triangle (u, w, x) beside
+ *          e = u w becomes (u, p, x) and (p, w, x).
+ * Steps 1 and 2 read the lattice positions; every distance test is a
+ * double-precision comparison of squared distances.  The result is an
+ * explicit mesh (mesh_query): the lattice vertices in id order (moved),
+ * then the inserted points; the cells in id order, a split cell's two
+ * halves in place of it; labels from the centroids as for mesh_bitmap;
+ * code 0 everywhere; n_cut_cells counts the split cells.  mesh_quality and
+ * mesh_project accept it.  Synchronises with the device once. */
+int mesh_preprocess(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out);
+
+/* Records of a preprocessed mesh (waits for it):
+ *  status  per lattice vertex (device, n_lattice_vertices bytes): 0 kept,
+ *          1 snapped (Step 1), 2 repelled (Step 2);
+ *  snap    per lattice vertex (device, int32): the corner id snapped to, -1;
+ *  elim    per applied Step 3 candidate, by point id (device, 3 int32):
+ *          the point's corner id and the removed edge's ends u < w;
+ *  n_points the boundary points; n_candidate_points those with a candidate;
+ *  a_px, b_px, c_px the thresholds in pixels.
+ * SBMT_EINVAL for a mesh not made by mesh_preprocess. */
+typedef struct {
+  int64_t n_lattice_vertices, n_points;
+  int64_t n_snapped, n_repelled, n_candidate_points, n_eliminated, n_split_cells;
+  double a_px, b_px, c_px;
+  const uint8_t* status;
+  const int32_t* snap;
+  const int32_t* elim;
+} sbmt_pre_info;
+int mesh_preprocess_info(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_pre_info* out);
 
 /* Mesh n images; params points to n parameter sets, or to one shared by
  * all (n_params = 1).  out receives n handles. */

@@ -36,7 +36,8 @@ SBMT_EXPLICIT, SBMT_COMPACT = 0, 1
 SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
-           "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "sbmt_last_error")
+           "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
+           "mesh_preprocess_info", "sbmt_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -67,6 +68,14 @@ class sbmt_quality(ctypes.Structure):
                 ("slivers", ctypes.c_int64), ("equilateral", ctypes.c_int64), ("area_mean", ctypes.c_double),
                 ("area_var", ctypes.c_double), ("ar_median", ctypes.c_double), ("ar_p95", ctypes.c_double),
                 ("ar_max", ctypes.c_double), ("angle_hist", ctypes.c_int64 * 30)]
+
+
+class sbmt_pre_info(ctypes.Structure):
+    _fields_ = [("n_lattice_vertices", ctypes.c_int64), ("n_points", ctypes.c_int64), ("n_snapped", ctypes.c_int64),
+                ("n_repelled", ctypes.c_int64), ("n_candidate_points", ctypes.c_int64),
+                ("n_eliminated", ctypes.c_int64), ("n_split_cells", ctypes.c_int64), ("a_px", ctypes.c_double),
+                ("b_px", ctypes.c_double), ("c_px", ctypes.c_double), ("status", ctypes.c_void_p),
+                ("snap", ctypes.c_void_p), ("elim", ctypes.c_void_p)]
 
 
 class SbmtError(RuntimeError):
@@ -107,9 +116,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_int)]
     lib.mesh_quality.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_quality)]
     lib.mesh_project.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_image), vp, vp]
+    lib.mesh_preprocess.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params),
+                                    ctypes.POINTER(ctypes.c_uint64)]
+    lib.mesh_preprocess_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_pre_info)]
     lib.sbmt_last_error.restype = ctypes.c_char_p
     for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
-              "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project"):
+              "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
+              "mesh_preprocess_info"):
         getattr(lib, f).restype = ctypes.c_int
     del i32
     _lib = lib
@@ -164,6 +177,43 @@ def mesh_bitmap(ctx: int, img, h_num: int, h_den: int = 1, origin2x: int = 0, or
     _check(load().mesh_bitmap(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
     del keep
     return out.value
+
+
+def mesh_preprocess(ctx: int, img, h_num: int, h_den: int = 1, a: float = 0.26, b: float = 0.125, c: float = 0.183,
+                    origin2x: int = 0, origin2y: int = 0) -> int:
+    """Alg. 3's preprocessed mesh of one image (thresholds relative to the
+    reference edge sqrt(0.45) px); a handle for mesh_query and
+    mesh_preprocess_info."""
+    im, keep = _image(img)
+    pr = sbmt_params(h_num, h_den, origin2x, origin2y, SBMT_PREPROCESS, float(a), float(b), float(c), SBMT_EXPLICIT, 0)
+    out = ctypes.c_uint64()
+    _check(load().mesh_preprocess(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def mesh_preprocess_info(ctx: int, mesh: int) -> sbmt_pre_info:
+    v = sbmt_pre_info()
+    _check(load().mesh_preprocess_info(ctx, mesh, ctypes.byref(v)))
+    return v
+
+
+def pre_info_numpy(info: sbmt_pre_info) -> dict:
+    """Host copies of a preprocessed mesh's records (status, snap, elim)."""
+    import torch
+
+    def dev(ptr, shape, typestr):
+        return torch.as_tensor(_CudaArray(ptr, shape, typestr, None), device="cuda").cpu().numpy()
+
+    V, E = info.n_lattice_vertices, info.n_eliminated
+    return {
+        "status": dev(info.status, (V,), "|u1") if V else np.zeros(0, np.uint8),
+        "snap": dev(info.snap, (V,), "<i4") if V else np.zeros(0, np.int32),
+        "elim": dev(info.elim, (E, 3), "<i4") if E else np.zeros((0, 3), np.int32),
+        "n_points": info.n_points, "n_snapped": info.n_snapped, "n_repelled": info.n_repelled,
+        "n_candidate_points": info.n_candidate_points, "n_split_cells": info.n_split_cells,
+        "thresholds_px": (info.a_px, info.b_px, info.c_px),
+    }
 
 
 def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False, format: int = SBMT_EXPLICIT) -> list[int]:

@@ -1,0 +1,480 @@
+// k_preprocess.cu -- geometric preprocessing of the base mesh (Alg. 3,
+// Steps 1-3).
+//
+// The base mesh T0 (the lattice cells meeting the image rectangle, Sec. 3.3)
+// and the boundary go in; the preprocessed mesh T comes out.
+//  - Region I (Steps 1 and 2, which commute): a lattice vertex snaps onto the
+//    nearest boundary point closer than a; a vertex that did not snap and is
+//    closer than c to the boundary moves away from its nearest boundary point
+//    q along q -> v to distance c.  Both read the positions of T0.
+//  - Region II (Step 3): a boundary point p closer than b to an edge e of T
+//    (neither end of e at p) is a candidate (p, e).  It applies when e is p's
+//    smallest candidate edge (smaller end id, then larger) and no smaller
+//    point has a candidate on an edge of the triangles beside e; it inserts
+//    p and splits each triangle (u, w, x) beside e = uw into (u, p, x) and
+//    (p, w, x) (Fig. "b threshold split").
+// Boundary points are the PSLG vertices (pixel corners, id y (W + 1) + x),
+// boundary segments the boundary pixel edges.  The thresholds arrive in
+// pixels.
+//
+// Every decision is the plain double-precision evaluation of its formula,
+// each operation rounded once (the _rn intrinsics keep the compiler from
+// fusing them).  This part runs FP64 at a small fraction of its FP32 rate,
+// so candidates are screened first: by integer tests (corner flags, pixel
+// labels) and in single precision with a margin that covers the rounding
+// of the coordinates to float.  Only survivors reach the double test.
+#include <algorithm>
+
+#include "sbmt_cell.cuh"
+#include "sbmt_launch.h"
+
+namespace sbmt {
+
+// a boundary point's smallest candidate edge (Step 3) and the cells beside it
+struct PreCand {
+  u32 u, w;            // the edge's ends, u < w
+  u32 cell[2];         // the cells beside it, NONE where absent
+  u32 cv[2][3];        // their corners A, B, C
+  unsigned char k[2];  // the edge's local index in each cell (AB 0, BC 1, CA 2)
+  unsigned char n;     // cells found (0: no candidate)
+};
+
+size_t pre_cand_bytes(u32 np) { return (size_t)std::max<u32>(np, 1) * sizeof(PreCand); }
+
+namespace {
+
+constexpr double SQRT3D = 1.7320508075688772935;
+
+SBMT_DEV double dadd(double a, double b) { return __dadd_rn(a, b); }
+SBMT_DEV double dsub(double a, double b) { return __dsub_rn(a, b); }
+SBMT_DEV double dmul(double a, double b) { return __dmul_rn(a, b); }
+SBMT_DEV double d2of(double dx, double dy) { return dadd(dmul(dx, dx), dmul(dy, dy)); }
+
+// y of lattice row j in pixels, (oy + 3 p j sqrt3) / S
+SBMT_DEV double row_y(const GridP& g, i64 j) {
+  return __ddiv_rn(dadd((double)g.oy, dmul((double)(3 * g.p * j), SQRT3D)), (double)g.S);
+}
+
+SBMT_DEV bool corner_flag(const PreArgs& a, int cx, int cy) {
+  return (a.vrow[(i64)cy * a.wpr + (cx >> 5)] >> (cx & 31)) & 1u;
+}
+
+// squared distance from p to the segment u -> w: the projection parameter
+// clamped to [0, 1], then the offset
+SBMT_DEV double seg_d2(double px, double py, double2 u, double2 w) {
+  const double ex = dsub(w.x, u.x), ey = dsub(w.y, u.y);
+  const double qx = dsub(px, u.x), qy = dsub(py, u.y);
+  const double t = fmin(fmax(__ddiv_rn(dadd(dmul(qx, ex), dmul(qy, ey)), d2of(ex, ey)), 0.0), 1.0);
+  return d2of(dsub(qx, dmul(t, ex)), dsub(qy, dmul(t, ey)));
+}
+SBMT_DEV float seg_d2f(float px, float py, float2 u, float2 w) {
+  const float ex = w.x - u.x, ey = w.y - u.y, qx = px - u.x, qy = py - u.y;
+  const float t = fminf(fmaxf((qx * ex + qy * ey) / (ex * ex + ey * ey), 0.f), 1.f);
+  const float dx = qx - t * ex, dy = qy - t * ey;
+  return dx * dx + dy * dy;
+}
+
+// Step 3's candidate test of the point (px, py) against the edge u w
+SBMT_DEV bool is_cand(const PreArgs& a, double px, double py, float pxf, float pyf, u32 u, u32 w) {
+  if (seg_d2f(pxf, pyf, a.xyf[u], a.xyf[w]) >= a.bscr2) return false;
+  const double2* xy = reinterpret_cast<const double2*>(a.xy);
+  const double2 du = xy[u], dw = xy[w];
+  if ((du.x == px && du.y == py) || (dw.x == px && dw.y == py)) return false;
+  return seg_d2(px, py, du, dw) < a.B2;
+}
+
+// pixel index of the centroid coordinate ((c0 + c1) + c2) / 3: the floor of
+// it plus 1/2.  The float estimate decides unless it lies within its error
+// bound of an integer; then the double evaluation does.
+SBMT_DEV int cen_floor(double c0, double c1, double c2, float f0, float f1, float f2) {
+  const float s = ((f0 + f1) + f2) * (1.0f / 3.0f) + 0.5f;
+  const float M = fmaxf(fmaxf(fabsf(f0), fabsf(f1)), fabsf(f2));
+  const float eps = (M + 1.0f) * 0x1p-19f;
+  const float fl = floorf(s);
+  if (s - fl > eps && (fl + 1.0f) - s > eps) return (int)fl;
+  return (int)floor(dadd(__ddiv_rn(dadd(dadd(c0, c1), c2), 3.0), 0.5));
+}
+
+template <typename T>
+SBMT_DEV unsigned short pre_label(const PreArgs& a, int col, int row) {
+  const int l = pix<T>(a.img, a.pitch, a.g.W, a.g.H, col, row);
+  return l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
+}
+
+template <typename T>
+SBMT_DEV unsigned short moved_label(const PreArgs& a, const double2* pd, const float2* pf) {
+  const int col = cen_floor(pd[0].x, pd[1].x, pd[2].x, pf[0].x, pf[1].x, pf[2].x);
+  const int row = cen_floor(pd[0].y, pd[1].y, pd[2].y, pf[0].y, pf[1].y, pf[2].y);
+  return pre_label<T>(a, col, row);
+}
+
+// x table over m = 2i + j (the x of v(i, j) depends on m only) and the pixel
+// rows of the centroids of unmoved up and down cells, per strip row
+__global__ void __launch_bounds__(256) k_pre_rows(PreArgs a) {
+  const GridP& g = a.g;
+  const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  for (i64 k = t0; k < a.nm; k += stride) {
+    const double x = __ddiv_rn((double)(g.ox + 3 * g.p * (a.m0 + k)), (double)g.S);
+    a.tab[k] = x;
+    a.tabf[k] = __double2float_rn(x);
+  }
+  for (i64 r = t0; r < g.nrows; r += stride) {
+    const i64 j = g.j0 + r;
+    const double y0 = row_y(g, j), y1 = row_y(g, j + 1);
+    // up cells have two corners on row j, down cells two on row j + 1
+    a.prow[2 * r] = (int)floor(dadd(__ddiv_rn(dadd(dadd(y0, y0), y1), 3.0), 0.5));
+    a.prow[2 * r + 1] = (int)floor(dadd(__ddiv_rn(dadd(dadd(y0, y1), y1), 3.0), 0.5));
+  }
+}
+
+// Region I: Steps 1 and 2 for every lattice vertex, one block per vertex row
+template <typename T>
+__global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
+  const GridP& g = a.g;
+  const int r = blockIdx.x, W = g.W, H = g.H;
+  const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
+  const double y = row_y(g, j);
+  const float yf = __double2float_rn(y);
+  const float Af = a.ascr, Cf = a.cscr;
+  const double A2 = dmul(a.A, a.A), C2 = dmul(a.C, a.C);
+  double2* xy = reinterpret_cast<double2*>(a.xy);
+  u32 nsnap = 0, nrep = 0;
+  for (i64 k = threadIdx.x; k < n; k += blockDim.x) {
+    const i64 mi = 2 * (lo + k) + j - a.m0;
+    const double x = a.tab[mi];
+    const float xf = a.tabf[mi];
+    double2 out = make_double2(x, y);
+    float2 outf = make_float2(xf, yf);
+    unsigned char st = 0;
+    int sc = -1;
+    // Step 1: the boundary point nearest to v, if closer than a; corners are
+    // visited in increasing id, so a tie keeps the smaller
+    {
+      const int x0 = max(0, (int)ceilf(xf + 0.5f - Af)), x1 = min(W, (int)floorf(xf + 0.5f + Af));
+      const int y0 = max(0, (int)ceilf(yf + 0.5f - Af)), y1 = min(H, (int)floorf(yf + 0.5f + Af));
+      double best = 0.0;
+      int bx = -1, by = -1;
+      for (int cy = y0; cy <= y1; ++cy)
+        for (int cx = x0; cx <= x1; ++cx) {
+          if (!corner_flag(a, cx, cy)) continue;
+          const double d2 = d2of(dsub(x, (double)cx - 0.5), dsub(y, (double)cy - 0.5));
+          if (bx < 0 || d2 < best) best = d2, bx = cx, by = cy;
+        }
+      if (bx >= 0 && best < A2) {
+        out = make_double2((double)bx - 0.5, (double)by - 0.5);
+        outf = make_float2((float)bx - 0.5f, (float)by - 0.5f);
+        st = 1, sc = by * (W + 1) + bx;
+      }
+    }
+    // Step 2: the nearest point q of the boundary pixel edges (ties to the
+    // smaller edge id), if closer than c: v moves to q + c (v - q) / |v - q|.
+    // An edge within c of v lies between two pixels of the box around v.
+    if (st == 0) {
+      const int m0 = max(-1, (int)ceilf(xf - Cf - 0.5f)), m1 = min(W, (int)floorf(xf + Cf + 0.5f));
+      const int k0 = max(-1, (int)ceilf(yf - Cf - 0.5f)), k1 = min(H, (int)floorf(yf + Cf + 0.5f));
+      double best = 0.0, bqx = 0.0, bqy = 0.0;
+      i64 bid = -1;
+      for (int kk = k0; kk <= k1; ++kk)
+        for (int m = m0; m <= m1; ++m) {
+          const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
+          // horizontal edge (m, kk): y = kk - 1/2 between pixels (m, kk - 1) and (m, kk)
+          if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
+            const double qx = fmin(fmax(x, (double)m - 0.5), (double)m + 0.5), qy = (double)kk - 0.5;
+            const double d2 = d2of(dsub(x, qx), dsub(y, qy));
+            const i64 id = (i64)kk * W + m;
+            if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
+          }
+          // vertical edge (m, kk): x = m - 1/2 between pixels (m - 1, kk) and (m, kk)
+          if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
+            const double qx = (double)m - 0.5, qy = fmin(fmax(y, (double)kk - 0.5), (double)kk + 0.5);
+            const double d2 = d2of(dsub(x, qx), dsub(y, qy));
+            const i64 id = (i64)(H + 1) * W + (i64)kk * (W + 1) + m;
+            if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
+          }
+        }
+      if (bid >= 0 && best < C2) {
+        const double t = __ddiv_rn(a.C, __dsqrt_rn(best));
+        out = make_double2(dadd(bqx, dmul(t, dsub(x, bqx))), dadd(bqy, dmul(t, dsub(y, bqy))));
+        outf = make_float2(__double2float_rn(out.x), __double2float_rn(out.y));
+        st = 2;
+      }
+    }
+    xy[base + k] = out;
+    a.xyf[base + k] = outf;
+    a.status[base + k] = st;
+    a.snap[base + k] = sc;
+    nsnap += st == 1, nrep += st == 2;
+  }
+  nsnap = __reduce_add_sync(0xFFFFFFFFu, nsnap);
+  nrep = __reduce_add_sync(0xFFFFFFFFu, nrep);
+  if ((threadIdx.x & 31) == 0) {
+    if (nsnap) atomicAdd(a.cnt + 3, nsnap);
+    if (nrep) atomicAdd(a.cnt + 4, nrep);
+  }
+}
+
+// population counts of a bit-plane; with wpr > 0 the plane has rows of wpr
+// words and only the bits of corner columns 0..W count
+__global__ void __launch_bounds__(256) k_popc(const u32* words, u64 n, int wpr, int W, u32* out) {
+  for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (u64)gridDim.x * blockDim.x) {
+    u32 b = words[w];
+    if (wpr > 0) {
+      const int c0 = 32 * (int)(w % (u64)wpr);
+      if (W - c0 < 31) b &= (2u << (W - c0)) - 1u;
+    }
+    out[w] = __popc(b);
+  }
+}
+
+// the boundary points in corner-id order
+__global__ void __launch_bounds__(256) k_pre_points(PreArgs a, u64 nw, const u32* wscan) {
+  const int W = a.g.W;
+  for (u64 w = (u64)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x) {
+    u32 b = a.vrow[w];
+    const int cy = (int)(w / (u64)a.wpr), c0 = 32 * (int)(w % (u64)a.wpr);
+    u32 o = wscan[w];
+    while (b) {
+      const int cx = c0 + __ffs(b) - 1;
+      b &= b - 1;
+      if (cx > W || o >= a.np) break;
+      a.plist[o++] = (u32)cy * (u32)(W + 1) + (u32)cx;
+    }
+  }
+}
+
+// Step 3, first pass: every boundary point's smallest candidate edge and
+// the cells beside it.  A candidate edge's moved ends lie within a of their
+// lattice positions, so its lattice segment lies within a + b of p: the
+// cells visited are those whose lattice extent meets p's box of that
+// half-width.
+__global__ void __launch_bounds__(128) k_pre_cand(PreArgs a) {
+  const GridP& g = a.g;
+  const u64 V = (u64)g.nverts;
+  const float R = a.reach;
+  u32 found = 0;
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
+    const u32 p = a.plist[t];
+    const int cx = (int)(p % (u32)(g.W + 1)), cy = (int)(p / (u32)(g.W + 1));
+    const double px = (double)cx - 0.5, py = (double)cy - 0.5;
+    const float pxf = (float)cx - 0.5f, pyf = (float)cy - 0.5f;
+    PreCand c;
+    c.u = c.w = NONE, c.cell[0] = c.cell[1] = NONE, c.k[0] = c.k[1] = 0, c.n = 0;
+    u64 best = ~0ull;
+    // strip rows: row jj spans the lattice row coordinate [jj, jj + 1]
+    const float ilo = (pyf - R - a.oyf) / a.rowh, ihi = (pyf + R - a.oyf) / a.rowh;
+    const int jlo = max(g.j0, (int)floorf(ilo - 1e-6f * fabsf(ilo) - 0.01f));
+    const int jhi = min(g.j0 + g.nrows - 1, (int)floorf(ihi + 1e-6f * fabsf(ihi) + 0.01f));
+    for (int jj = jlo; jj <= jhi; ++jj) {
+      const int r = jj - g.j0;
+      // cell cc of the row spans 2u in [cc, cc + 2], u = (x - ox) / h - jj / 2
+      const float ulo = 2.0f * ((pxf - R - a.oxf) / a.hf) - (float)jj;
+      const float uhi = 2.0f * ((pxf + R - a.oxf) / a.hf) - (float)jj;
+      const i64 c0 = max(g.clo[r], (i64)floorf(ulo - 2.0f - 1e-6f * fabsf(ulo) - 0.01f));
+      const i64 c1 = min(g.chi[r], (i64)floorf(uhi + 1e-6f * fabsf(uhi) + 0.01f));
+      for (i64 cc = c0; cc <= c1; ++cc) {
+        i64 ci[3], cj[3];
+        cell_corners(cc, jj, ci, cj);
+        u32 v[3];
+        float2 f[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) v[e] = vid(g, ci[e], cj[e]), f[e] = a.xyf[v[e]];
+        // the cell's moved bounding box against p's b-box
+        const float bx0 = fminf(fminf(f[0].x, f[1].x), f[2].x), bx1 = fmaxf(fmaxf(f[0].x, f[1].x), f[2].x);
+        const float by0 = fminf(fminf(f[0].y, f[1].y), f[2].y), by1 = fmaxf(fmaxf(f[0].y, f[1].y), f[2].y);
+        if (bx0 > pxf + a.bscr || bx1 < pxf - a.bscr || by0 > pyf + a.bscr || by1 < pyf - a.bscr) continue;
+        const u32 cid = cell_id(g, cc, jj);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const u32 u = v[e], w = v[e == 2 ? 0 : e + 1];
+          if (!is_cand(a, px, py, pxf, pyf, u, w)) continue;
+          const u32 lo = min(u, w), hi = max(u, w);
+          const u64 key = (u64)lo * V + hi;
+          if (key < best) {
+            best = key, c.u = lo, c.w = hi, c.n = 1;
+            c.cell[0] = cid, c.k[0] = (unsigned char)e, c.cell[1] = NONE;
+            c.cv[0][0] = v[0], c.cv[0][1] = v[1], c.cv[0][2] = v[2];
+          } else if (key == best && c.n == 1) {
+            c.n = 2, c.cell[1] = cid, c.k[1] = (unsigned char)e;
+            c.cv[1][0] = v[0], c.cv[1][1] = v[1], c.cv[1][2] = v[2];
+          }
+        }
+      }
+    }
+    a.cand[t] = c;
+    found += c.n != 0;
+  }
+  found = __reduce_add_sync(0xFFFFFFFFu, found);
+  if ((threadIdx.x & 31) == 0 && found) atomicAdd(a.cnt + 5, found);
+}
+
+// Step 3, second pass: p applies unless a smaller point has a candidate on
+// an edge of a cell beside p's edge.  Such a point lies within b of the
+// bounding box of those cells' moved corners.
+__global__ void __launch_bounds__(128) k_pre_apply(PreArgs a) {
+  const GridP& g = a.g;
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
+    const PreCand c = a.cand[t];
+    if (c.n == 0) {
+      a.appl[t] = 0;
+      continue;
+    }
+    const u32 p = a.plist[t];
+    const int pcx = (int)(p % (u32)(g.W + 1)), pcy = (int)(p / (u32)(g.W + 1));
+    float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
+    for (int s = 0; s < c.n; ++s)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const float2 f = a.xyf[c.cv[s][e]];
+        bx0 = fminf(bx0, f.x), bx1 = fmaxf(bx1, f.x), by0 = fminf(by0, f.y), by1 = fmaxf(by1, f.y);
+      }
+    const int x0 = max(0, (int)ceilf(bx0 - a.bscr + 0.5f)), x1 = min(g.W, (int)floorf(bx1 + a.bscr + 0.5f));
+    const int y0 = max(0, (int)ceilf(by0 - a.bscr + 0.5f)), y1 = min(pcy, (int)floorf(by1 + a.bscr + 0.5f));
+    bool ok = true;
+    for (int cy = y0; cy <= y1 && ok; ++cy) {
+      const int xe = cy == pcy ? min(x1, pcx - 1) : x1;  // ids below p only
+      for (int cx = x0; cx <= xe && ok; ++cx) {
+        if (!corner_flag(a, cx, cy)) continue;
+        const double qx = (double)cx - 0.5, qy = (double)cy - 0.5;
+        const float qxf = (float)cx - 0.5f, qyf = (float)cy - 0.5f;
+        for (int s = 0; s < c.n && ok; ++s)
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            if (ok && is_cand(a, qx, qy, qxf, qyf, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
+      }
+    }
+    a.appl[t] = ok ? 1u : 0u;
+    if (ok)
+      for (int s = 0; s < c.n; ++s) atomicOr(a.sbit + (c.cell[s] >> 5), 1u << (c.cell[s] & 31));
+  }
+}
+
+// output triangle index of cell cid: its id plus the split cells before it
+SBMT_DEV u64 out_index(const PreArgs& a, u32 cid) {
+  return (u64)cid + a.wpre[cid >> 5] + __popc(a.sbit[cid >> 5] & ((1u << (cid & 31)) - 1u));
+}
+
+// the preprocessed mesh: every cell that is not split, as its triangle
+// (A, B, C), labelled by its centroid -- exactly for a cell with three
+// unmoved corners (the column in integers, the row from the per-row table)
+template <typename T>
+__global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
+  const GridP& g = a.g;
+  const u64 nc = (u64)g.ncells;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const double2* xy = reinterpret_cast<const double2*>(a.xy);
+  for (u64 w0 = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < nc; w0 += stride) {
+    int r = 0;
+    if (lane == 0) r = cell_row_near(g, (u32)w0);
+    r = __shfl_sync(0xFFFFFFFFu, r, 0);
+    const u64 cid = w0 + lane;
+    if (cid >= nc) continue;
+    while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;
+    const u32 sw = a.sbit[cid >> 5];
+    if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
+    const u64 o = cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
+    const i64 jr = g.j0 + r, c = g.clo[r] + ((i64)cid - g.cbase[r]), i = c >> 1;
+    i64 ci[3], cj[3];
+    cell_corners(c, jr, ci, cj);
+    u32 v[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) v[e] = vid(g, ci[e], cj[e]);
+    unsigned short lab;
+    if ((a.status[v[0]] | a.status[v[1]] | a.status[v[2]]) == 0) {
+      // pixel column floor((2 xc + S) / 2S) of the centroid x = xc / S
+      const int num = (int)(2 * (g.ox + 3 * g.p * (2 * i + jr + 1 + (c & 1))) + g.S), den = (int)(2 * g.S);
+      int col = (int)floorf((float)num / (float)den);
+      while (col * den > num) --col;
+      while ((col + 1) * den <= num) ++col;
+      lab = pre_label<T>(a, col, a.prow[2 * r + (c & 1)]);
+    } else {
+      double2 pd[3];
+      float2 pf[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) pd[e] = xy[v[e]], pf[e] = a.xyf[v[e]];
+      lab = moved_label<T>(a, pd, pf);
+    }
+    a.tri[3 * o] = (int)v[0], a.tri[3 * o + 1] = (int)v[1], a.tri[3 * o + 2] = (int)v[2];
+    a.label[o] = lab, a.code[o] = 0;
+  }
+}
+
+// the applied points: vertex V + rank at the corner, the elimination
+// record, and the two halves of each split cell
+template <typename T>
+__global__ void __launch_bounds__(128) k_pre_split(PreArgs a) {
+  const GridP& g = a.g;
+  double2* xy = reinterpret_cast<double2*>(a.xy);
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
+    if (!a.appl[t]) continue;
+    const PreCand c = a.cand[t];
+    const u32 p = a.plist[t], rank = a.ascan[t], q = (u32)g.nverts + rank;
+    const int cx = (int)(p % (u32)(g.W + 1)), cy = (int)(p / (u32)(g.W + 1));
+    const double2 pq = make_double2((double)cx - 0.5, (double)cy - 0.5);
+    const float2 pqf = make_float2((float)cx - 0.5f, (float)cy - 0.5f);
+    xy[q] = pq;
+    a.elim[3 * (u64)rank] = (int)p, a.elim[3 * (u64)rank + 1] = (int)c.u, a.elim[3 * (u64)rank + 2] = (int)c.w;
+    for (int s = 0; s < c.n; ++s) {
+      const u32 cell = c.cell[s];
+      const int k = c.k[s];
+      const u32 u = c.cv[s][k], w = c.cv[s][(k + 1) % 3], x = c.cv[s][(k + 2) % 3];
+      const u64 o = out_index(a, cell);
+      const double2 du = xy[u], dw = xy[w], dx = xy[x];
+      const float2 fu = a.xyf[u], fw = a.xyf[w], fx = a.xyf[x];
+      // (u, p, x), then (p, w, x)
+      a.tri[3 * o] = (int)u, a.tri[3 * o + 1] = (int)q, a.tri[3 * o + 2] = (int)x;
+      a.tri[3 * o + 3] = (int)q, a.tri[3 * o + 4] = (int)w, a.tri[3 * o + 5] = (int)x;
+      const double2 d0[3] = {du, pq, dx}, d1[3] = {pq, dw, dx};
+      const float2 f0[3] = {fu, pqf, fx}, f1[3] = {pqf, fw, fx};
+      a.label[o] = moved_label<T>(a, d0, f0);
+      a.label[o + 1] = moved_label<T>(a, d1, f1);
+      a.code[o] = 0, a.code[o + 1] = 0;
+    }
+  }
+}
+
+// status words: the eliminations and split cells, from the scans' totals
+__global__ void k_pre_totals(PreArgs a, u64 nsw) {
+  a.cnt[1] = a.ascan[a.np];
+  a.cnt[2] = a.wpre[nsw];
+}
+
+unsigned grid_for(u64 n, int threads, unsigned cap) {
+  return (unsigned)std::max<u64>(1, std::min<u64>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr, cudaStream_t st) {
+  int n = 0;
+  const GridP& g = a.g;
+  k_pre_rows<<<grid_for((u64)std::max<i64>(a.nm, g.nrows), 256, 1024), 256, 0, st>>>(a), ++n;
+  if (a.dtype == 1) k_pre_vertex<unsigned char><<<g.nvrows, 256, 0, st>>>(a);
+  else k_pre_vertex<unsigned short><<<g.nvrows, 256, 0, st>>>(a);
+  ++n;
+  // the boundary points, in corner-id order
+  k_popc<<<grid_for(nw, 256, 152 * 8), 256, 0, st>>>(a.vrow, nw, a.wpr, g.W, wpop), ++n;
+  n += launch_scan(wpop, 1, wscan, (u32)nw, scr, st);
+  k_pre_points<<<grid_for(nw, 256, 152 * 8), 256, 0, st>>>(a, nw, wscan), ++n;
+  // Step 3
+  const u64 nsw = ((u64)g.ncells + 31) / 32;
+  if (cudaMemsetAsync(a.sbit, 0, (nsw + 1) * sizeof(u32), st) != cudaSuccess) return -1;
+  k_pre_cand<<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a), ++n;
+  k_pre_apply<<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a), ++n;
+  n += launch_scan(a.appl, 1, a.ascan, a.np, scr, st);
+  k_popc<<<grid_for(nsw, 256, 152 * 8), 256, 0, st>>>(a.sbit, nsw, 0, 0, a.spop), ++n;
+  n += launch_scan(a.spop, 1, a.wpre, (u32)nsw, scr, st);
+  // the preprocessed mesh
+  if (a.dtype == 1) {
+    k_pre_emit<unsigned char><<<grid_for(g.ncells, 256, 152 * 16), 256, 0, st>>>(a);
+    k_pre_split<unsigned char><<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a);
+  } else {
+    k_pre_emit<unsigned short><<<grid_for(g.ncells, 256, 152 * 16), 256, 0, st>>>(a);
+    k_pre_split<unsigned short><<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a);
+  }
+  n += 2;
+  k_pre_totals<<<1, 1, 0, st>>>(a, nsw), ++n;
+  return n;
+}
+
+}  // namespace sbmt

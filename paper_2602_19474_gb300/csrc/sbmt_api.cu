@@ -141,6 +141,15 @@ struct MeshRec {
   u32* bbase = nullptr;
   u32 nbc = 0;
   std::vector<void*> scratch;  // device memory freed with the mesh
+  // preprocessed meshes (Alg. 3): the counts are known once the work is done
+  // (h_info: err, eliminations, split cells, snapped, repelled, points with
+  // a candidate)
+  bool pre = false, settled = false;
+  unsigned char* pstatus = nullptr;
+  int* psnap = nullptr;
+  int* pelim = nullptr;
+  double thr[3] = {0, 0, 0};
+  int64_t npts = 0;
 };
 
 }  // namespace
@@ -158,11 +167,12 @@ enum {
   KN_EMIT,
   KN_TIERG,
   KN_XY,
+  KN_PRE,
   KN_COUNT
 };
 const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_seg_count", "k_scan",
                                             "k_walk", "k_rank", "k_sort", "k_cutcells", "k_emit",
-                                            "k_tierg", "k_lattice_xy"};
+                                            "k_tierg", "k_lattice_xy", "k_preprocess"};
 
 // One stream of work: the context's own stream, or one of the extra streams
 // a batch spreads its images over.  Each lane has its own scratch arena and
@@ -454,15 +464,20 @@ void destroy_mesh(sbmt_ctx* ctx, MeshRec* m, cudaStream_t st) {
   delete m;
 }
 
-int check_params(const sbmt_image* img, const sbmt_params* pr) {
+int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false) {
   if (!img || !pr || !img->data) return fail(SBMT_EINVAL, "null image or params");
   if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768)
     return fail(SBMT_EINVAL, "image size %dx%d outside 1..32768", img->width, img->height);
   if (img->dtype != SBMT_U8 && img->dtype != SBMT_U16) return fail(SBMT_EINVAL, "dtype %d", img->dtype);
   if (img->pitch_bytes < (int64_t)img->width * img->dtype) return fail(SBMT_EINVAL, "pitch too small");
-  if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is not available");
-  if (pr->mode != SBMT_PLAIN || (pr->format != SBMT_EXPLICIT && pr->format != SBMT_COMPACT))
-    return fail(SBMT_EINVAL, "mode/format");
+  if (pre) {
+    if (pr->mode != SBMT_PREPROCESS || pr->format != SBMT_EXPLICIT)
+      return fail(SBMT_EINVAL, "mesh_preprocess takes mode SBMT_PREPROCESS and the explicit format");
+  } else {
+    if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is not available");
+    if (pr->mode != SBMT_PLAIN || (pr->format != SBMT_EXPLICIT && pr->format != SBMT_COMPACT))
+      return fail(SBMT_EINVAL, "mode/format");
+  }
   if (pr->h_num < 2 || pr->h_num > 1024 || (pr->h_num & 1) || pr->h_den < 1 || pr->h_den > 63 ||
       !(pr->h_den & 1))
     return fail(SBMT_EINVAL, "h = %d/%d outside the degeneracy-free class (even h_num <= 1024, odd h_den < 64)",
@@ -736,6 +751,172 @@ int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params
   return SBMT_OK;
 }
 
+// Alg. 3's thresholds in pixels: a, b, c are relative to the reference edge
+// sqrt(0.45) px, so each is scaled by h / sqrt(0.45); they must lie in the
+// admissible range b < a/2, c < a/sqrt2, and a < h/2
+int pre_thresholds(const sbmt_params* pr, double* A, double* B, double* C) {
+  const double h = (double)pr->h_num / (double)pr->h_den;
+  const double s = h / std::sqrt(0.45);
+  *A = pr->a * s, *B = pr->b * s, *C = pr->c * s;
+  if (!(*B < *A / 2 && *C < *A / std::sqrt(2.0) && *A < h / 2 && *A > 0 && *B >= 0 && *C >= 0))
+    return fail(SBMT_EINVAL, "thresholds (%g, %g, %g) outside the admissible range", pr->a, pr->b, pr->c);
+  return SBMT_OK;
+}
+
+// the preprocessed mesh of one image (Alg. 3), enqueued on one lane
+int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
+  int rc = check_params(img, pr, true);
+  if (rc) return rc;
+  double A, B, C;
+  if ((rc = pre_thresholds(pr, &A, &B, &C))) return rc;
+  cudaStream_t st = lane->stream;
+  CK(cudaSetDevice(ctx->device));
+  GridP g{};
+  g.W = img->width, g.H = img->height;
+  g.p = pr->h_num, g.q = pr->h_den, g.S = 6 * g.q;
+  g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
+  const Tables* tbp;
+  const i64* dt;
+  if ((rc = get_tables(ctx, lane, g, &tbp, &dt))) return rc;
+  const Tables& tb = *tbp;
+  if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 31))
+    return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
+  MeshRec* m = new MeshRec();
+  m->W = g.W, m->H = g.H, m->pre = true;
+  std::vector<void*> tmp;
+  arena_begin(lane);
+  auto bail = [&](int code) {
+    free_list(st, tmp);
+    arena_end(lane);
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    destroy_mesh(ctx, m, st);
+    return code;
+  };
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->h_info = pinned_slot(ctx);
+  }
+  if (!m->h_info) return bail(fail(SBMT_ENOMEM, "pinned info"));
+  const unsigned char* dimg;
+  i64 pitch;
+  if (img->on_device) {
+    dimg = (const unsigned char*)img->data;
+    pitch = img->pitch_bytes;
+  } else {
+    unsigned char* d;
+    pitch = (i64)img->width * img->dtype;
+    if ((rc = aalloc(lane, &d, (size_t)pitch * img->height))) return bail(rc);
+    if (cudaMemcpy2DAsync(d, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
+      return bail(fail(SBMT_ECUDA, "image upload"));
+    dimg = d;
+  }
+  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
+  g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
+  g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
+  g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
+  g.lrow = (const int*)(dt + 3 * nrows + 3 * nvr);
+  g.ncells = tb.ncells, g.nverts = tb.nverts;
+  // counters: the PSLG vertex count (u64), then the six status words
+  u32* zero;
+  if ((rc = aalloc(lane, &zero, 16))) return bail(rc);
+  CK(cudaMemsetAsync(zero, 0, 16 * sizeof(u32), st));
+  unsigned long long* cnt64 = (unsigned long long*)zero;
+  const int W = g.W, H = g.H;
+  const int wpr = (W + 1 + 31) / 32, wpc = (H + 1 + 31) / 32;
+  u32 *vrow, *vcol;
+  if ((rc = aalloc(lane, &vrow, (size_t)wpr * (H + 1)))) return bail(rc);
+  if ((rc = aalloc(lane, &vcol, (size_t)wpc * (W + 1)))) return bail(rc);
+  TRACE(KN_CORNER, launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64, st));
+  unsigned long long h64 = 0;
+  CK(cudaMemcpyAsync(&h64, cnt64, sizeof h64, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const u64 NP = h64, V = (u64)tb.nverts, NCELL = (u64)tb.ncells;
+  if (V + NP >= (1ull << 31) || NCELL + 2 * NP >= (1ull << 31))
+    return bail(fail(SBMT_EINVAL, "mesh too large (%llu cells)", (unsigned long long)NCELL));
+  // x of lattice vertex v(i, j) is indexed by m = 2i + j
+  i64 m_lo = 0, m_hi = -1;
+  for (i64 r = 0; r < nvr; ++r) {
+    const i64 a = 2 * tb.vlo[r] + tb.vj0 + r, b = 2 * tb.vhi[r] + tb.vj0 + r;
+    if (r == 0 || a < m_lo) m_lo = a;
+    if (r == 0 || b > m_hi) m_hi = b;
+  }
+  const u64 nm = (u64)std::max<i64>(1, m_hi - m_lo + 1);
+  const u64 nw = (u64)wpr * (H + 1), nsw = (NCELL + 31) / 32;
+  PreArgs a{};
+  a.g = g, a.img = dimg, a.pitch = pitch, a.dtype = img->dtype, a.vrow = vrow, a.wpr = wpr, a.np = (u32)NP;
+  a.m0 = m_lo, a.nm = (i64)nm;
+  u32 *wpop, *wscan, *scr;
+  const size_t scr_words =
+      std::max({scan_scratch_words((u32)nw), scan_scratch_words((u32)NP), scan_scratch_words((u32)nsw)}) + 1;
+  if ((rc = aalloc(lane, &a.tab, nm)) || (rc = aalloc(lane, &a.tabf, nm)) ||
+      (rc = aalloc(lane, &a.prow, 2 * (size_t)nrows)) || (rc = aalloc(lane, &a.xyf, V)) ||
+      (rc = aalloc(lane, &wpop, nw)) || (rc = aalloc(lane, &wscan, nw + 1)) ||
+      (rc = aalloc(lane, &a.plist, std::max<u64>(NP, 1))) || (rc = aalloc(lane, &a.appl, std::max<u64>(NP, 1))) ||
+      (rc = aalloc(lane, &a.ascan, NP + 1)) || (rc = aalloc(lane, &a.sbit, nsw + 1)) ||
+      (rc = aalloc(lane, &a.spop, nsw + 1)) || (rc = aalloc(lane, &a.wpre, nsw + 1)) ||
+      (rc = aalloc(lane, &scr, scr_words)))
+    return bail(rc);
+  char* candb;
+  if ((rc = aalloc(lane, &candb, pre_cand_bytes((u32)NP)))) return bail(rc);
+  a.cand = (PreCand*)candb;
+  a.cnt = zero + 8;
+  // thresholds and their screening radii: the float copies of the
+  // coordinates are within 2^-24 |x| < 1/256 px of the doubles, and the
+  // float evaluations within 1e-4 h of their double values
+  const double h = (double)g.p / (double)g.q;
+  const double marg = 1.0 / 64.0 + 1e-4 * h;
+  a.A = A, a.B2 = B * B, a.C = C;
+  a.ascr = (float)(A + marg), a.cscr = (float)(C + marg), a.bscr = (float)(B + marg);
+  a.bscr2 = (float)((B + marg) * (B + marg));
+  a.reach = (float)(A + B + marg);
+  a.oxf = (float)(pr->origin2x / 2), a.oyf = (float)(pr->origin2y / 2);
+  a.hf = (float)h, a.rowh = (float)(h * std::sqrt(3.0) / 2.0);
+  // outputs: at most one inserted vertex and two extra triangles per point
+  const u64 nxy = V + NP, ntr = NCELL + 2 * NP;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_tri = up(16 * nxy), off_lab = up(off_tri + 12 * ntr), off_code = up(off_lab + 2 * ntr);
+  const size_t off_st = up(off_code + 2 * ntr), off_sn = up(off_st + V), off_el = up(off_sn + 4 * V);
+  const size_t total = off_el + 12 * std::max<u64>(NP, 1) + 256;
+  if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
+    return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
+  char* ob = (char*)m->out_block;
+  m->xy = (double*)ob, m->tri = (int*)(ob + off_tri);
+  m->label = (unsigned short*)(ob + off_lab), m->code = (unsigned short*)(ob + off_code);
+  m->pstatus = (unsigned char*)(ob + off_st), m->psnap = (int*)(ob + off_sn), m->pelim = (int*)(ob + off_el);
+  a.xy = m->xy, a.tri = m->tri, a.label = m->label, a.code = m->code;
+  a.status = m->pstatus, a.snap = m->psnap, a.elim = m->pelim;
+  m->nv = (int64_t)V, m->nt = (int64_t)NCELL, m->ncells = (int64_t)NCELL, m->nvg = (int64_t)V;
+  m->thr[0] = A, m->thr[1] = B, m->thr[2] = C, m->npts = (int64_t)NP;
+  int nk = 0;
+  TRACE(KN_PRE, nk = launch_preprocess(a, nw, wpop, wscan, scr, st));
+  if (nk < 0) return bail(fail(SBMT_ECUDA, "preprocess launch"));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(m->h_info, a.cnt, 6 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  free_list(st, tmp);
+  arena_end(lane);
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->done = pool_event(ctx);
+  }
+  if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
+  CK(cudaEventRecord(m->done, st));
+  std::lock_guard<std::mutex> lk(ctx->reg);
+  m->id = ctx->next++;
+  ctx->meshes[m->id] = m;
+  *out = m->id;
+  return SBMT_OK;
+}
+
+// a preprocessed mesh's vertex and triangle counts, once its work is done
+int settle(MeshRec* m) {
+  if (!m->pre || m->settled) return SBMT_OK;
+  CK(cudaEventSynchronize(m->done));
+  m->nv = m->nvg + (int64_t)m->h_info[1];
+  m->nt = m->ncells + (int64_t)m->h_info[2];
+  m->settled = true;
+  return SBMT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -774,6 +955,32 @@ int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params,
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
   return mesh_one(ctx, &ctx->main, img, params, out, true);
+}
+
+int mesh_preprocess(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return pre_one(ctx, &ctx->main, img, params, out);
+}
+
+int mesh_preprocess_info(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_pre_info* out) {
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  MeshRec* m;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->meshes.find(mesh);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh %llu", (unsigned long long)mesh);
+    m = it->second;
+  }
+  if (!m->pre) return fail(SBMT_EINVAL, "not a preprocessed mesh");
+  if (int rc = settle(m)) return rc;
+  std::memset(out, 0, sizeof *out);
+  out->n_lattice_vertices = m->nvg, out->n_points = m->npts;
+  out->n_snapped = m->h_info[3], out->n_repelled = m->h_info[4], out->n_candidate_points = m->h_info[5];
+  out->n_eliminated = m->h_info[1], out->n_split_cells = m->h_info[2];
+  out->a_px = m->thr[0], out->b_px = m->thr[1], out->c_px = m->thr[2];
+  out->status = m->pstatus, out->snap = m->psnap, out->elim = m->pelim;
+  return SBMT_OK;
 }
 
 int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
@@ -881,8 +1088,18 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
       return SBMT_ETIMEDOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
+  int rc = settle(m);
+  if (rc) return rc;
   std::memset(out, 0, sizeof *out);
   out->n_vertices = m->nv, out->n_triangles = m->nt, out->n_cells = m->ncells;
+  if (m->pre) {
+    out->n_cut_cells = m->h_info[2], out->n_lattice_vertices = m->nvg;
+    out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;
+    out->format = SBMT_EXPLICIT;
+    out->status = m->h_info[0] == 0 ? SBMT_OK : SBMT_EINTERNAL;
+    if (out->status) fail(out->status, "device reported error bits 0x%x", m->h_info[0]);
+    return out->status;
+  }
   out->n_cut_cells = m->h_info[1], out->n_tierG_cells = m->h_info[2];
   out->n_segments = m->nseg_total, out->n_events = m->ne_total, out->n_inside_vertices = m->nc_total;
   out->n_lattice_vertices = m->nvg, out->n_tierG_triangles = m->h_info[3];
@@ -940,6 +1157,7 @@ int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out) {
     m = it->second;
   }
   if (m->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "quality needs the explicit format");
+  if (int rc0 = settle(m)) return rc0;
   CK(cudaSetDevice(ctx->device));
   std::memset(out, 0, sizeof *out);
   const u64 T = (u64)m->nt;
@@ -1034,6 +1252,7 @@ int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* 
     m = it->second;
   }
   if (m->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "projection needs the explicit format");
+  if (int rc0 = settle(m)) return rc0;
   if (field->dtype != SBMT_F32 || field->width != m->W || field->height != m->H || !field->data)
     return fail(SBMT_EINVAL, "field must be a %dx%d SBMT_F32 image", m->W, m->H);
   if (field->pitch_bytes < 4 * (int64_t)field->width || (field->pitch_bytes & 3))

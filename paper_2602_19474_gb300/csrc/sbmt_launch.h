@@ -113,6 +113,50 @@ size_t project_scratch_bytes(u64 V);
 int launch_project(const double* xy, const int* tri, u64 T, u64 V, const float* f, i64 fpitch, int W, int H,
                    float* tri_value, float* vertex_value, void* scratch, cudaStream_t st);
 
+// geometric preprocessing of the base mesh (Alg. 3, Steps 1-3), on the PSLG
+// vertex flags vrow of launch_corner_bits.  Thresholds in pixels; the *scr
+// fields are their screening radii (each plus the float rounding margin of
+// the coordinates), bscr2 = bscr^2.  Scratch: tab / tabf (nm entries, the
+// x table over m0 <= m < m0 + nm), prow (2 per strip row), xyf (float copy
+// of the moved lattice positions), plist (np boundary points), cand
+// (pre_cand_bytes(np)), appl / ascan (np and np + 1 words), sbit / spop /
+// wpre (split-cell bit-plane of ncells / 32 + 1 words, its counts and their
+// scan), cnt (6 zeroed words: error, eliminations, split cells, snapped,
+// repelled, points with a candidate).  Outputs: xy (lattice vertices, then
+// the inserted points), tri / label / code (ncells + split cells
+// triangles), status and snap per lattice vertex, elim (3 per elimination).
+struct PreCand;
+struct PreArgs {
+  GridP g;
+  const unsigned char* img;
+  i64 pitch;
+  int dtype;
+  const u32* vrow;
+  int wpr;
+  u32 np;
+  double A, B2, C;
+  float ascr, bscr, bscr2, cscr, reach;  // reach: a + b plus the margin
+  float oxf, oyf, hf, rowh;              // origin, h and the strip height in pixels
+  i64 m0, nm;
+  double* tab;
+  float* tabf;
+  int* prow;
+  float2* xyf;
+  u32* plist;
+  PreCand* cand;
+  u32 *appl, *ascan, *sbit, *spop, *wpre, *cnt;
+  double* xy;
+  int* tri;
+  unsigned short *label, *code;
+  unsigned char* status;
+  int *snap, *elim;
+};
+size_t pre_cand_bytes(u32 np);
+// nw vrow words; wpop / wscan: nw and nw + 1 words; scr: scan scratch for
+// the largest of nw, np and ncells / 32 + 1.  Returns the kernels launched,
+// -1 if a CUDA call failed.
+int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr, cudaStream_t st);
+
 // coordinates of the lattice vertices; tab: scratch of nm doubles for the x
 // values (ox + 3p m) / S, m0 <= m < m0 + nm covering 2i + j of every vertex
 int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st);
