@@ -28,11 +28,13 @@ _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (g++ -O2) if missing or stale."""
+    """Compile the oracle shared library (g++ -O2) if missing or stale.  No
+    floating-point contraction: every product and sum is rounded on its own,
+    as written, on every host (GCC fuses them by default for C++ on Arm)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
