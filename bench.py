@@ -236,6 +236,19 @@ def oracle_sample(img: np.ndarray, h: tuple, side: int) -> tuple:
     return m["n_triangles"], dt
 
 
+def oracle_pre_sample(img: np.ndarray, h: tuple, abc: tuple, side: int) -> dict:
+    """The preprocessing oracle as it stands on a side x side crop, one
+    thread: output triangles per second."""
+    from oracle import preprocess as P
+
+    crop = np.ascontiguousarray(img[:side, :side])
+    t0 = time.perf_counter()
+    o = P.preprocess(crop, h[0], h[1], *abc)
+    t = time.perf_counter() - t0
+    return {"value": len(o["tri"]) / t, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": "top-left %dx%d crop of the workload, one thread" % (side, side)}
+
+
 def _oracle_image(args):
     """One bitmap through the oracle (a worker of the batch CPU baseline)."""
     import oracle
@@ -478,6 +491,34 @@ def our_arm(args, rank: int, world: int, dist):
                           "value at every vertex, on the step's mesh; two kernels per call",
                   "ms_per_call": ms_p, "ms_triangle_means_only": ms_pt, "triangles_per_s": T / (ms_p * 1e-3),
                   "algorithmic_bytes_per_call": pbytes, "achieved_gbs": pbytes / (ms_p * 1e-3) / 1e9}
+    # geometric preprocessing (Alg. 3, Steps 1-3) of the same image, with App.
+    # I's first admissible thresholds: the preprocessed mesh on the device
+    tri_abc = (0.26, 0.125, 0.183)
+
+    def step_pre():
+        m = sb.mesh_preprocess(ctx, dimg, hn, hd, *tri_abc)
+        vv = sb.mesh_query(ctx, m, -1)
+        info = sb.mesh_preprocess_info(ctx, m)
+        sb.mesh_release(ctx, m)
+        return vv, info
+
+    for _ in range(3):
+        vq, pinfo = step_pre()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        vq, pinfo = step_pre()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_q = e0.elapsed_time(e1) / args.steps
+    qbytes = (img.nbytes + 16.0 * vq.n_vertices + 16.0 * vq.n_triangles + 5.0 * vq.n_lattice_vertices
+              + 12.0 * pinfo.n_eliminated)
+    preprocess = {"what": "Alg. 3 Steps 1-3 (snap within a, repel to c, re-fan edges within b of a boundary point) "
+                          "on the base mesh, thresholds (a, b, c) = %s relative to the edge sqrt(0.45) px" % (tri_abc,),
+                  "ms_per_call": ms_q, "triangles_per_s": vq.n_triangles / (ms_q * 1e-3),
+                  "triangles": vq.n_triangles, "boundary_points": pinfo.n_points, "snapped": pinfo.n_snapped,
+                  "repelled": pinfo.n_repelled, "eliminated": pinfo.n_eliminated,
+                  "algorithmic_bytes_per_call": qbytes, "achieved_gbs": qbytes / (ms_q * 1e-3) / 1e9}
     compact = {"what": "the same mesh in the compact format (uncut cells as a label per base cell, cut cells' "
                        "patches listed); triangles/s counts the triangles the mesh represents",
                "ms_per_step": ms_c, "value": job_rate(world, T, ms_c), "patch_triangles": vc.n_patch_triangles,
@@ -503,6 +544,7 @@ def our_arm(args, rank: int, world: int, dist):
     # CPU baseline: the oracle as it stands, one core, on a bounded crop
     side = min(2048, W, H)
     n_cpu, t_cpu = oracle_sample(img, (hn, hd), side)
+    pre_cpu = oracle_pre_sample(img, (hn, hd), tri_abc, 160)
     out = {
         "metric": "output triangles/sec", "value": value, "unit": "triangles/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -526,6 +568,8 @@ def our_arm(args, rank: int, world: int, dist):
         "e2e": {"value": e2e_value, "unit": "triangles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "compact_format": compact,
         "projection": dict(projection, peak=peak, frac=projection["achieved_gbs"] / peak),
+        "preprocess": dict(preprocess, peak=peak, frac=preprocess["achieved_gbs"] / peak,
+                           cpu_baseline=pre_cpu),
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -75,12 +75,20 @@ SBMT_DEV float seg_d2f(float px, float py, float2 u, float2 w) {
 }
 
 // Step 3's candidate test of the point (px, py) against the edge u w
+// (a float distance beyond the band dband around b decides; an end at p
+// has float coordinates equal to p's, the only case that reads doubles
+// before the band does)
 SBMT_DEV bool is_cand(const PreArgs& a, double px, double py, float pxf, float pyf, u32 u, u32 w) {
-  if (seg_d2f(pxf, pyf, a.xyf[u], a.xyf[w]) >= a.bscr2) return false;
+  const float2 fu = a.xyf[u], fw = a.xyf[w];
+  const float d2f = seg_d2f(pxf, pyf, fu, fw);
+  if (d2f > a.b_hi2) return false;
   const double2* xy = reinterpret_cast<const double2*>(a.xy);
-  const double2 du = xy[u], dw = xy[w];
-  if ((du.x == px && du.y == py) || (dw.x == px && dw.y == py)) return false;
-  return seg_d2(px, py, du, dw) < a.B2;
+  if ((fu.x == pxf && fu.y == pyf) || (fw.x == pxf && fw.y == pyf)) {
+    const double2 du = xy[u], dw = xy[w];
+    if ((du.x == px && du.y == py) || (dw.x == px && dw.y == py)) return false;
+  }
+  if (d2f < a.b_lo2) return true;
+  return seg_d2(px, py, xy[u], xy[w]) < a.B2;
 }
 
 // pixel index of the centroid coordinate ((c0 + c1) + c2) / 3: the floor of
@@ -127,31 +135,35 @@ __global__ void __launch_bounds__(256) k_pre_rows(PreArgs a) {
   }
 }
 
-// Region I: Steps 1 and 2 for every lattice vertex, one block per vertex row
+// Region I for one vertex whose neighbourhood holds a boundary edge.
+// Distances are screened in single precision: a float distance more than
+// the band dband from a threshold decides like the double one; the rest,
+// the exact argmin among near ties, and the moved position take doubles.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
-  const GridP& g = a.g;
-  const int r = blockIdx.x, W = g.W, H = g.H;
-  const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
-  const double y = row_y(g, j);
-  const float yf = __double2float_rn(y);
+SBMT_DEV void region_one(const PreArgs& a, double x, double y, float xf, float yf, double2& out, float2& outf,
+                         unsigned char& st, int& sc) {
+  const int W = a.g.W, H = a.g.H;
   const float Af = a.ascr, Cf = a.cscr;
-  const double A2 = dmul(a.A, a.A), C2 = dmul(a.C, a.C);
-  double2* xy = reinterpret_cast<double2*>(a.xy);
-  u32 nsnap = 0, nrep = 0;
-  for (i64 k = threadIdx.x; k < n; k += blockDim.x) {
-    const i64 mi = 2 * (lo + k) + j - a.m0;
-    const double x = a.tab[mi];
-    const float xf = a.tabf[mi];
-    double2 out = make_double2(x, y);
-    float2 outf = make_float2(xf, yf);
-    unsigned char st = 0;
-    int sc = -1;
-    // Step 1: the boundary point nearest to v, if closer than a; corners are
-    // visited in increasing id, so a tie keeps the smaller
-    {
-      const int x0 = max(0, (int)ceilf(xf + 0.5f - Af)), x1 = min(W, (int)floorf(xf + 0.5f + Af));
-      const int y0 = max(0, (int)ceilf(yf + 0.5f - Af)), y1 = min(H, (int)floorf(yf + 0.5f + Af));
+  // Step 1: the boundary point nearest to v, if closer than a (ties: the
+  // smaller id; corners are visited in increasing id)
+  {
+    const int x0 = max(0, (int)ceilf(xf + 0.5f - Af)), x1 = min(W, (int)floorf(xf + 0.5f + Af));
+    const int y0 = max(0, (int)ceilf(yf + 0.5f - Af)), y1 = min(H, (int)floorf(yf + 0.5f + Af));
+    int nclose = 0, fx = -1, fy = -1;
+    bool sure = false;
+    for (int cy = y0; cy <= y1; ++cy)
+      for (int cx = x0; cx <= x1; ++cx) {
+        if (!corner_flag(a, cx, cy)) continue;
+        const float dx = xf - ((float)cx - 0.5f), dy = yf - ((float)cy - 0.5f), d2f = dx * dx + dy * dy;
+        if (d2f > a.a_hi2) continue;
+        if (nclose++ == 0) fx = cx, fy = cy, sure = d2f < a.a_lo2;
+      }
+    if (nclose == 1 && sure) {
+      out = make_double2((double)fx - 0.5, (double)fy - 0.5), outf = make_float2((float)fx - 0.5f, (float)fy - 0.5f);
+      st = 1, sc = fy * (W + 1) + fx;
+      return;
+    }
+    if (nclose > 0) {
       double best = 0.0;
       int bx = -1, by = -1;
       for (int cy = y0; cy <= y1; ++cy)
@@ -160,50 +172,139 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
           const double d2 = d2of(dsub(x, (double)cx - 0.5), dsub(y, (double)cy - 0.5));
           if (bx < 0 || d2 < best) best = d2, bx = cx, by = cy;
         }
-      if (bx >= 0 && best < A2) {
-        out = make_double2((double)bx - 0.5, (double)by - 0.5);
-        outf = make_float2((float)bx - 0.5f, (float)by - 0.5f);
+      if (best < dmul(a.A, a.A)) {
+        out = make_double2((double)bx - 0.5, (double)by - 0.5), outf = make_float2((float)bx - 0.5f, (float)by - 0.5f);
         st = 1, sc = by * (W + 1) + bx;
+        return;
       }
     }
-    // Step 2: the nearest point q of the boundary pixel edges (ties to the
-    // smaller edge id), if closer than c: v moves to q + c (v - q) / |v - q|.
-    // An edge within c of v lies between two pixels of the box around v.
-    if (st == 0) {
-      const int m0 = max(-1, (int)ceilf(xf - Cf - 0.5f)), m1 = min(W, (int)floorf(xf + Cf + 0.5f));
-      const int k0 = max(-1, (int)ceilf(yf - Cf - 0.5f)), k1 = min(H, (int)floorf(yf + Cf + 0.5f));
-      double best = 0.0, bqx = 0.0, bqy = 0.0;
-      i64 bid = -1;
-      for (int kk = k0; kk <= k1; ++kk)
-        for (int m = m0; m <= m1; ++m) {
-          const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
-          // horizontal edge (m, kk): y = kk - 1/2 between pixels (m, kk - 1) and (m, kk)
-          if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
-            const double qx = fmin(fmax(x, (double)m - 0.5), (double)m + 0.5), qy = (double)kk - 0.5;
-            const double d2 = d2of(dsub(x, qx), dsub(y, qy));
-            const i64 id = (i64)kk * W + m;
-            if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
-          }
-          // vertical edge (m, kk): x = m - 1/2 between pixels (m - 1, kk) and (m, kk)
-          if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
-            const double qx = (double)m - 0.5, qy = fmin(fmax(y, (double)kk - 0.5), (double)kk + 0.5);
-            const double d2 = d2of(dsub(x, qx), dsub(y, qy));
-            const i64 id = (i64)(H + 1) * W + (i64)kk * (W + 1) + m;
-            if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
-          }
+  }
+  // Step 2: the nearest point q of the boundary pixel edges (ties: the
+  // smaller edge id), if closer than c: v moves to q + c (v - q) / |v - q|.
+  // An edge within c of v lies between two pixels of the box around v.
+  const int m0 = max(-1, (int)ceilf(xf - Cf - 0.5f)), m1 = min(W, (int)floorf(xf + Cf + 0.5f));
+  const int k0 = max(-1, (int)ceilf(yf - Cf - 0.5f)), k1 = min(H, (int)floorf(yf + Cf + 0.5f));
+  float minf = 3.0e38f;
+  for (int kk = k0; kk <= k1; ++kk)
+    for (int m = m0; m <= m1; ++m) {
+      const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
+      if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
+        const float dx = xf - fminf(fmaxf(xf, (float)m - 0.5f), (float)m + 0.5f), dy = yf - ((float)kk - 0.5f);
+        minf = fminf(minf, dx * dx + dy * dy);
+      }
+      if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
+        const float dx = xf - ((float)m - 0.5f), dy = yf - fminf(fmaxf(yf, (float)kk - 0.5f), (float)kk + 0.5f);
+        minf = fminf(minf, dx * dx + dy * dy);
+      }
+    }
+  if (minf > a.c_hi2) return;  // no boundary edge within c
+  // the edges within 2 dband of the float minimum, in doubles
+  const float lim = (sqrtf(minf) + 2.0f * a.dband) * (sqrtf(minf) + 2.0f * a.dband) * 1.0001f;
+  double best = 0.0, bqx = 0.0, bqy = 0.0;
+  i64 bid = -1;
+  for (int kk = k0; kk <= k1; ++kk)
+    for (int m = m0; m <= m1; ++m) {
+      const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
+      // horizontal edge (m, kk): y = kk - 1/2 between pixels (m, kk - 1) and (m, kk)
+      if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
+        const float dx = xf - fminf(fmaxf(xf, (float)m - 0.5f), (float)m + 0.5f), dy = yf - ((float)kk - 0.5f);
+        if (dx * dx + dy * dy <= lim) {
+          const double qx = fmin(fmax(x, (double)m - 0.5), (double)m + 0.5), qy = (double)kk - 0.5;
+          const double d2 = d2of(dsub(x, qx), dsub(y, qy));
+          const i64 id = (i64)kk * W + m;
+          if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
         }
-      if (bid >= 0 && best < C2) {
-        const double t = __ddiv_rn(a.C, __dsqrt_rn(best));
-        out = make_double2(dadd(bqx, dmul(t, dsub(x, bqx))), dadd(bqy, dmul(t, dsub(y, bqy))));
-        outf = make_float2(__double2float_rn(out.x), __double2float_rn(out.y));
-        st = 2;
+      }
+      // vertical edge (m, kk): x = m - 1/2 between pixels (m - 1, kk) and (m, kk)
+      if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
+        const float dx = xf - ((float)m - 0.5f), dy = yf - fminf(fmaxf(yf, (float)kk - 0.5f), (float)kk + 0.5f);
+        if (dx * dx + dy * dy <= lim) {
+          const double qx = (double)m - 0.5, qy = fmin(fmax(y, (double)kk - 0.5), (double)kk + 0.5);
+          const double d2 = d2of(dsub(x, qx), dsub(y, qy));
+          const i64 id = (i64)(H + 1) * W + (i64)kk * (W + 1) + m;
+          if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
+        }
       }
     }
-    xy[base + k] = out;
-    a.xyf[base + k] = outf;
-    a.status[base + k] = st;
-    a.snap[base + k] = sc;
-    nsnap += st == 1, nrep += st == 2;
+  if (bid >= 0 && best < dmul(a.C, a.C)) {
+    const double t = __ddiv_rn(a.C, __dsqrt_rn(best));
+    out = make_double2(dadd(bqx, dmul(t, dsub(x, bqx))), dadd(bqy, dmul(t, dsub(y, bqy))));
+    outf = make_float2(__double2float_rn(out.x), __double2float_rn(out.y));
+    st = 2;
+  }
+}
+
+// Region I: Steps 1 and 2 for every lattice vertex, one block per vertex
+// row.  A vertex whose nearby pixels carry one label stays; the others are
+// queued in shared memory and taken by the whole block afterwards, so that
+// the few near the boundary do not hold up warps of vertices that stay.
+constexpr int PV_CHUNK = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
+  __shared__ u32 q[PV_CHUNK];
+  __shared__ u32 nq;
+  const GridP& g = a.g;
+  const int r = blockIdx.x, W = g.W, H = g.H;
+  const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
+  const double y = row_y(g, j);
+  const float yf = __double2float_rn(y);
+  const float Af = a.ascr;
+  // pixel rows whose squares reach within a of the row
+  const int py0 = (int)ceilf(yf - Af - 0.5f), py1 = (int)floorf(yf + Af + 0.5f);
+  double2* xy = reinterpret_cast<double2*>(a.xy);
+  u32 nsnap = 0, nrep = 0;
+  for (i64 s0 = 0; s0 < n; s0 += PV_CHUNK) {
+    if (threadIdx.x == 0) nq = 0;
+    __syncthreads();
+    const int ns = (int)min((i64)PV_CHUNK, n - s0);
+    for (int e = threadIdx.x; e < ns; e += blockDim.x) {
+      const i64 k = s0 + e, mi = 2 * (lo + k) + j - a.m0;
+      const float xf = a.tabf[mi];
+      // one label over the pixels whose squares reach within a of v: no
+      // boundary edge within a (c < a), no boundary point either (a PSLG
+      // vertex's four pixels are among them), and v stays.  Boxes reaching
+      // past the image take the general path.
+      const int px0 = (int)ceilf(xf - Af - 0.5f), px1 = (int)floorf(xf + Af + 0.5f);
+      bool uniform = false;
+      if (px0 >= 0 && py0 >= 0 && px1 < W && py1 < H) {
+        const unsigned char* rowp = a.img + (i64)py0 * a.pitch;
+        const T l0 = ((const T*)rowp)[px0];
+        uniform = true;
+        for (int yy = py0; yy <= py1 && uniform; ++yy, rowp += a.pitch)
+          for (int xx = px0; xx <= px1; ++xx)
+            if (((const T*)rowp)[xx] != l0) {
+              uniform = false;
+              break;
+            }
+      }
+      if (uniform) {
+        xy[base + k] = make_double2(a.tab[mi], y);
+        a.xyf[base + k] = make_float2(xf, yf);
+        a.status[base + k] = 0;
+        a.snap[base + k] = -1;
+      } else {
+        q[atomicAdd(&nq, 1u)] = (u32)e;
+      }
+    }
+    __syncthreads();
+    const u32 nqs = nq;
+    for (u32 e = threadIdx.x; e < nqs; e += blockDim.x) {
+      const i64 k = s0 + q[e], mi = 2 * (lo + k) + j - a.m0;
+      const double x = a.tab[mi];
+      const float xf = a.tabf[mi];
+      double2 out = make_double2(x, y);
+      float2 outf = make_float2(xf, yf);
+      unsigned char st = 0;
+      int sc = -1;
+      region_one<T>(a, x, y, xf, yf, out, outf, st, sc);
+      xy[base + k] = out;
+      a.xyf[base + k] = outf;
+      a.status[base + k] = st;
+      a.snap[base + k] = sc;
+      nsnap += st == 1, nrep += st == 2;
+    }
+    __syncthreads();
   }
   nsnap = __reduce_add_sync(0xFFFFFFFFu, nsnap);
   nrep = __reduce_add_sync(0xFFFFFFFFu, nrep);
@@ -242,21 +343,24 @@ __global__ void __launch_bounds__(256) k_pre_points(PreArgs a, u64 nw, const u32
   }
 }
 
-// Step 3, first pass: every boundary point's smallest candidate edge and
-// the cells beside it.  A candidate edge's moved ends lie within a of their
-// lattice positions, so its lattice segment lies within a + b of p: the
-// cells visited are those whose lattice extent meets p's box of that
-// half-width.
-__global__ void __launch_bounds__(128) k_pre_cand(PreArgs a) {
+// Step 3, one thread per boundary point p.
+// First p's smallest candidate edge and the cells beside it: a candidate
+// edge's moved ends lie within a of their lattice positions, so its lattice
+// segment lies within a + b of p, and the cells visited are those whose
+// lattice extent meets p's box of that half-width.
+// Then the conflict test: p applies unless a smaller point has a candidate
+// on an edge of a cell beside p's edge; such a point lies within b of the
+// bounding box of those cells' moved corners.
+__global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
   const GridP& g = a.g;
   const u64 V = (u64)g.nverts;
   const float R = a.reach;
   u32 found = 0;
   for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
     const u32 p = a.plist[t];
-    const int cx = (int)(p % (u32)(g.W + 1)), cy = (int)(p / (u32)(g.W + 1));
-    const double px = (double)cx - 0.5, py = (double)cy - 0.5;
-    const float pxf = (float)cx - 0.5f, pyf = (float)cy - 0.5f;
+    const int pcx = (int)(p % (u32)(g.W + 1)), pcy = (int)(p / (u32)(g.W + 1));
+    const double px = (double)pcx - 0.5, py = (double)pcy - 0.5;
+    const float pxf = (float)pcx - 0.5f, pyf = (float)pcy - 0.5f;
     PreCand c;
     c.u = c.w = NONE, c.cell[0] = c.cell[1] = NONE, c.k[0] = c.k[1] = 0, c.n = 0;
     u64 best = ~0ull;
@@ -265,24 +369,25 @@ __global__ void __launch_bounds__(128) k_pre_cand(PreArgs a) {
     const int jlo = max(g.j0, (int)floorf(ilo - 1e-6f * fabsf(ilo) - 0.01f));
     const int jhi = min(g.j0 + g.nrows - 1, (int)floorf(ihi + 1e-6f * fabsf(ihi) + 0.01f));
     for (int jj = jlo; jj <= jhi; ++jj) {
-      const int r = jj - g.j0;
+      const int r = jj - g.j0, rv = jj - g.vj0;
+      const i64 clo = g.clo[r], vb0 = g.vbase[rv] - g.vlo[rv], vb1 = g.vbase[rv + 1] - g.vlo[rv + 1];
+      const u32 cb = (u32)g.cbase[r];
       // cell cc of the row spans 2u in [cc, cc + 2], u = (x - ox) / h - jj / 2
       const float ulo = 2.0f * ((pxf - R - a.oxf) / a.hf) - (float)jj;
       const float uhi = 2.0f * ((pxf + R - a.oxf) / a.hf) - (float)jj;
-      const i64 c0 = max(g.clo[r], (i64)floorf(ulo - 2.0f - 1e-6f * fabsf(ulo) - 0.01f));
+      const i64 c0 = max(clo, (i64)floorf(ulo - 2.0f - 1e-6f * fabsf(ulo) - 0.01f));
       const i64 c1 = min(g.chi[r], (i64)floorf(uhi + 1e-6f * fabsf(uhi) + 0.01f));
       for (i64 cc = c0; cc <= c1; ++cc) {
-        i64 ci[3], cj[3];
-        cell_corners(cc, jj, ci, cj);
-        u32 v[3];
-        float2 f[3];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) v[e] = vid(g, ci[e], cj[e]), f[e] = a.xyf[v[e]];
+        const i64 i = cc >> 1;
+        const bool down = (cc & 1) != 0;
+        const u32 v[3] = {(u32)(down ? vb0 + i + 1 : vb0 + i), (u32)(down ? vb1 + i + 1 : vb0 + i + 1),
+                          (u32)(vb1 + i)};
+        const float2 f[3] = {a.xyf[v[0]], a.xyf[v[1]], a.xyf[v[2]]};
         // the cell's moved bounding box against p's b-box
         const float bx0 = fminf(fminf(f[0].x, f[1].x), f[2].x), bx1 = fmaxf(fmaxf(f[0].x, f[1].x), f[2].x);
         const float by0 = fminf(fminf(f[0].y, f[1].y), f[2].y), by1 = fmaxf(fmaxf(f[0].y, f[1].y), f[2].y);
         if (bx0 > pxf + a.bscr || bx1 < pxf - a.bscr || by0 > pyf + a.bscr || by1 < pyf - a.bscr) continue;
-        const u32 cid = cell_id(g, cc, jj);
+        const u32 cid = cb + (u32)(cc - clo);
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
           const u32 u = v[e], w = v[e == 2 ? 0 : e + 1];
@@ -300,52 +405,47 @@ __global__ void __launch_bounds__(128) k_pre_cand(PreArgs a) {
         }
       }
     }
-    a.cand[t] = c;
-    found += c.n != 0;
-  }
-  found = __reduce_add_sync(0xFFFFFFFFu, found);
-  if ((threadIdx.x & 31) == 0 && found) atomicAdd(a.cnt + 5, found);
-}
-
-// Step 3, second pass: p applies unless a smaller point has a candidate on
-// an edge of a cell beside p's edge.  Such a point lies within b of the
-// bounding box of those cells' moved corners.
-__global__ void __launch_bounds__(128) k_pre_apply(PreArgs a) {
-  const GridP& g = a.g;
-  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
-    const PreCand c = a.cand[t];
-    if (c.n == 0) {
-      a.appl[t] = 0;
-      continue;
-    }
-    const u32 p = a.plist[t];
-    const int pcx = (int)(p % (u32)(g.W + 1)), pcy = (int)(p / (u32)(g.W + 1));
-    float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
-    for (int s = 0; s < c.n; ++s)
+    bool ok = c.n != 0;
+    found += ok;
+    if (ok) {
+      float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
+      for (int s = 0; s < c.n; ++s)
 #pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const float2 f = a.xyf[c.cv[s][e]];
-        bx0 = fminf(bx0, f.x), bx1 = fmaxf(bx1, f.x), by0 = fminf(by0, f.y), by1 = fmaxf(by1, f.y);
-      }
-    const int x0 = max(0, (int)ceilf(bx0 - a.bscr + 0.5f)), x1 = min(g.W, (int)floorf(bx1 + a.bscr + 0.5f));
-    const int y0 = max(0, (int)ceilf(by0 - a.bscr + 0.5f)), y1 = min(pcy, (int)floorf(by1 + a.bscr + 0.5f));
-    bool ok = true;
-    for (int cy = y0; cy <= y1 && ok; ++cy) {
-      const int xe = cy == pcy ? min(x1, pcx - 1) : x1;  // ids below p only
-      for (int cx = x0; cx <= xe && ok; ++cx) {
-        if (!corner_flag(a, cx, cy)) continue;
-        const double qx = (double)cx - 0.5, qy = (double)cy - 0.5;
-        const float qxf = (float)cx - 0.5f, qyf = (float)cy - 0.5f;
-        for (int s = 0; s < c.n && ok; ++s)
+        for (int e = 0; e < 3; ++e) {
+          const float2 f = a.xyf[c.cv[s][e]];
+          bx0 = fminf(bx0, f.x), bx1 = fmaxf(bx1, f.x), by0 = fminf(by0, f.y), by1 = fmaxf(by1, f.y);
+        }
+      const int x0 = max(0, (int)ceilf(bx0 - a.bscr + 0.5f)), x1 = min(g.W, (int)floorf(bx1 + a.bscr + 0.5f));
+      const int y0 = max(0, (int)ceilf(by0 - a.bscr + 0.5f)), y1 = min(pcy, (int)floorf(by1 + a.bscr + 0.5f));
+      for (int cy = y0; cy <= y1 && ok; ++cy) {
+        const int xe = cy == pcy ? min(x1, pcx - 1) : x1;  // ids below p only
+        const u32* wrow = a.vrow + (i64)cy * a.wpr;
+        for (int wx = x0 >> 5; wx <= (xe >> 5) && ok && x0 <= xe; ++wx) {
+          // the flagged corners of this word within [x0, xe]
+          u32 bits = wrow[wx];
+          const int b0 = max(x0 - 32 * wx, 0), b1 = min(xe - 32 * wx, 31);
+          bits &= (0xFFFFFFFFu << b0) & (0xFFFFFFFFu >> (31 - b1));
+          while (bits && ok) {
+            const int cx = 32 * wx + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const double qx = (double)cx - 0.5, qy = (double)cy - 0.5;
+            const float qxf = (float)cx - 0.5f, qyf = (float)cy - 0.5f;
+            for (int s = 0; s < c.n && ok; ++s)
 #pragma unroll
-          for (int e = 0; e < 3; ++e)
-            if (ok && is_cand(a, qx, qy, qxf, qyf, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
+              for (int e = 0; e < 3; ++e)
+                if (ok && is_cand(a, qx, qy, qxf, qyf, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
+          }
+        }
       }
     }
     a.appl[t] = ok ? 1u : 0u;
-    if (ok)
+    if (ok) {
+      a.cand[t] = c;
       for (int s = 0; s < c.n; ++s) atomicOr(a.sbit + (c.cell[s] >> 5), 1u << (c.cell[s] & 31));
+    }
   }
+  found = __reduce_add_sync(0xFFFFFFFFu, found);
+  if ((threadIdx.x & 31) == 0 && found) atomicAdd(a.cnt + 5, found);
 }
 
 // output triangle index of cell cid: its id plus the split cells before it
@@ -355,47 +455,48 @@ SBMT_DEV u64 out_index(const PreArgs& a, u32 cid) {
 
 // the preprocessed mesh: every cell that is not split, as its triangle
 // (A, B, C), labelled by its centroid -- exactly for a cell with three
-// unmoved corners (the column in integers, the row from the per-row table)
+// unmoved corners (the column in integers, the row from the per-row table).
+// One block per strip row at a time, its threads over the row's cells.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
   const GridP& g = a.g;
-  const u64 nc = (u64)g.ncells;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
   const double2* xy = reinterpret_cast<const double2*>(a.xy);
-  for (u64 w0 = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < nc; w0 += stride) {
-    int r = 0;
-    if (lane == 0) r = cell_row_near(g, (u32)w0);
-    r = __shfl_sync(0xFFFFFFFFu, r, 0);
-    const u64 cid = w0 + lane;
-    if (cid >= nc) continue;
-    while (r + 1 < g.nrows && g.cbase[r + 1] <= (i64)cid) ++r;
-    const u32 sw = a.sbit[cid >> 5];
-    if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
-    const u64 o = cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
-    const i64 jr = g.j0 + r, c = g.clo[r] + ((i64)cid - g.cbase[r]), i = c >> 1;
-    i64 ci[3], cj[3];
-    cell_corners(c, jr, ci, cj);
-    u32 v[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) v[e] = vid(g, ci[e], cj[e]);
-    unsigned short lab;
-    if ((a.status[v[0]] | a.status[v[1]] | a.status[v[2]]) == 0) {
-      // pixel column floor((2 xc + S) / 2S) of the centroid x = xc / S
-      const int num = (int)(2 * (g.ox + 3 * g.p * (2 * i + jr + 1 + (c & 1))) + g.S), den = (int)(2 * g.S);
-      int col = (int)floorf((float)num / (float)den);
-      while (col * den > num) --col;
-      while ((col + 1) * den <= num) ++col;
-      lab = pre_label<T>(a, col, a.prow[2 * r + (c & 1)]);
-    } else {
-      double2 pd[3];
-      float2 pf[3];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) pd[e] = xy[v[e]], pf[e] = a.xyf[v[e]];
-      lab = moved_label<T>(a, pd, pf);
+  const int den = (int)(2 * g.S);
+  const float inv_den = 1.0f / (float)den;
+  for (int r = blockIdx.x; r < g.nrows; r += gridDim.x) {
+    const i64 jr = g.j0 + (i64)r, clo = g.clo[r], nrc = g.chi[r] - clo + 1;
+    const u32 cb = (u32)g.cbase[r];
+    const int rv = (int)(jr - g.vj0);  // vertex rows rv (jr) and rv + 1 (jr + 1)
+    const i64 vb0 = g.vbase[rv] - g.vlo[rv], vb1 = g.vbase[rv + 1] - g.vlo[rv + 1];
+    const int prow0 = a.prow[2 * r], prow1 = a.prow[2 * r + 1];
+    // centroid x of cell c in units of 1/S: ox + 3p (c + jr + 1), so the
+    // pixel column's numerator 2 xc + S grows by 6p per cell
+    const i64 num0 = 2 * (g.ox + 3 * g.p * (clo + jr + 1)) + g.S;
+    for (i64 k = threadIdx.x; k < nrc; k += blockDim.x) {
+      const u32 cid = cb + (u32)k;
+      const u32 sw = a.sbit[cid >> 5];
+      if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
+      const u64 o = (u64)cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
+      const i64 c = clo + k, i = c >> 1;
+      const bool down = (c & 1) != 0;
+      const int v0 = (int)(down ? vb0 + i + 1 : vb0 + i), v1 = (int)(down ? vb1 + i + 1 : vb0 + i + 1);
+      const int v2 = (int)(vb1 + i);
+      unsigned short lab;
+      if ((a.status[v0] | a.status[v1] | a.status[v2]) == 0) {
+        // pixel column floor(num / 2S): a float estimate, corrected
+        const int num = (int)(num0 + 6 * g.p * k);
+        int col = (int)floorf((float)num * inv_den);
+        while (col * den > num) --col;
+        while ((col + 1) * den <= num) ++col;
+        lab = pre_label<T>(a, col, down ? prow1 : prow0);
+      } else {
+        const double2 pd[3] = {xy[v0], xy[v1], xy[v2]};
+        const float2 pf[3] = {a.xyf[v0], a.xyf[v1], a.xyf[v2]};
+        lab = moved_label<T>(a, pd, pf);
+      }
+      a.tri[3 * o] = v0, a.tri[3 * o + 1] = v1, a.tri[3 * o + 2] = v2;
+      a.label[o] = lab, a.code[o] = 0;
     }
-    a.tri[3 * o] = (int)v[0], a.tri[3 * o + 1] = (int)v[1], a.tri[3 * o + 2] = (int)v[2];
-    a.label[o] = lab, a.code[o] = 0;
   }
 }
 
@@ -459,17 +560,16 @@ int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr,
   // Step 3
   const u64 nsw = ((u64)g.ncells + 31) / 32;
   if (cudaMemsetAsync(a.sbit, 0, (nsw + 1) * sizeof(u32), st) != cudaSuccess) return -1;
-  k_pre_cand<<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a), ++n;
-  k_pre_apply<<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a), ++n;
+  k_pre_step3<<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a), ++n;
   n += launch_scan(a.appl, 1, a.ascan, a.np, scr, st);
   k_popc<<<grid_for(nsw, 256, 152 * 8), 256, 0, st>>>(a.sbit, nsw, 0, 0, a.spop), ++n;
   n += launch_scan(a.spop, 1, a.wpre, (u32)nsw, scr, st);
   // the preprocessed mesh
   if (a.dtype == 1) {
-    k_pre_emit<unsigned char><<<grid_for(g.ncells, 256, 152 * 16), 256, 0, st>>>(a);
+    k_pre_emit<unsigned char><<<(unsigned)std::min(g.nrows, 152 * 16), 256, 0, st>>>(a);
     k_pre_split<unsigned char><<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a);
   } else {
-    k_pre_emit<unsigned short><<<grid_for(g.ncells, 256, 152 * 16), 256, 0, st>>>(a);
+    k_pre_emit<unsigned short><<<(unsigned)std::min(g.nrows, 152 * 16), 256, 0, st>>>(a);
     k_pre_split<unsigned short><<<grid_for(a.np, 128, 152 * 16), 128, 0, st>>>(a);
   }
   n += 2;

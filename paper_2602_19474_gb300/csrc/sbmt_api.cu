@@ -860,11 +860,18 @@ int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params*
   if ((rc = aalloc(lane, &candb, pre_cand_bytes((u32)NP)))) return bail(rc);
   a.cand = (PreCand*)candb;
   a.cnt = zero + 8;
-  // thresholds and their screening radii: the float copies of the
-  // coordinates are within 2^-24 |x| < 1/256 px of the doubles, and the
-  // float evaluations within 1e-4 h of their double values
+  // thresholds and their float screens.  A float copy of a coordinate is
+  // within 2^-24 of its magnitude (at most M) of the double; a distance is
+  // 1-Lipschitz in the points, and its float evaluation adds a few 2^-24 of
+  // the local lengths (at most 2h + a + b): dband bounds the difference
+  // between a float distance and the double one, twice over
   const double h = (double)g.p / (double)g.q;
-  const double marg = 1.0 / 64.0 + 1e-4 * h;
+  const double M = std::max(W, H) + h + 2 + std::abs(pr->origin2x) / 2 + std::abs(pr->origin2y) / 2;
+  const double dband = std::ldexp(M + 1, -21) + std::ldexp(2 * h + A + B + 1, -19);
+  const double marg = dband + 1.0 / 256.0;
+  auto lo2 = [&](double r) { return r > dband ? (float)((r - dband) * (r - dband)) : -1.0f; };
+  auto hi2 = [&](double r) { return (float)((r + dband) * (r + dband)); };
+  a.dband = (float)dband, a.a_lo2 = lo2(A), a.a_hi2 = hi2(A), a.b_lo2 = lo2(B), a.b_hi2 = hi2(B), a.c_hi2 = hi2(C);
   a.A = A, a.B2 = B * B, a.C = C;
   a.ascr = (float)(A + marg), a.cscr = (float)(C + marg), a.bscr = (float)(B + marg);
   a.bscr2 = (float)((B + marg) * (B + marg));

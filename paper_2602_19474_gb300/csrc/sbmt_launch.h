@@ -136,6 +136,9 @@ struct PreArgs {
   u32 np;
   double A, B2, C;
   float ascr, bscr, bscr2, cscr, reach;  // reach: a + b plus the margin
+  // float decisions: dband bounds the error of a float distance; r_lo2 =
+  // (r - dband)^2 (or -1), r_hi2 = (r + dband)^2 for r = a, b, c
+  float dband, a_lo2, a_hi2, b_lo2, b_hi2, c_hi2;
   float oxf, oyf, hf, rowh;              // origin, h and the strip height in pixels
   i64 m0, nm;
   double* tab;
