@@ -50,6 +50,17 @@ SBMT_DEV double dsub(double a, double b) { return __dsub_rn(a, b); }
 SBMT_DEV double dmul(double a, double b) { return __dmul_rn(a, b); }
 SBMT_DEV double d2of(double dx, double dy) { return dadd(dmul(dx, dx), dmul(dy, dy)); }
 
+// (double)c - 1/2 from its bits, without the double-precision pipe
+SBMT_DEV double half_minus(int c) {
+  const int n = 2 * c - 1;  // odd, so never 0
+  const u32 m = (u32)abs(n);
+  const int e = 31 - __clz((int)m);  // m = 1.f * 2^e; the value is m / 2
+  const u64 frac = ((u64)m << (52 - e)) & ((1ull << 52) - 1);
+  const u64 bits = ((u64)(n < 0) << 63) | ((u64)(1022 + e) << 52) | frac;
+  return __longlong_as_double((long long)bits);
+}
+
+
 // y of lattice row j in pixels, (oy + 3 p j sqrt3) / S
 SBMT_DEV double row_y(const GridP& g, i64 j) {
   return __ddiv_rn(dadd((double)g.oy, dmul((double)(3 * g.p * j), SQRT3D)), (double)g.S);
@@ -78,17 +89,26 @@ SBMT_DEV float seg_d2f(float px, float py, float2 u, float2 w) {
 // (a float distance beyond the band dband around b decides; an end at p
 // has float coordinates equal to p's, the only case that reads doubles
 // before the band does)
-SBMT_DEV bool is_cand(const PreArgs& a, double px, double py, float pxf, float pyf, u32 u, u32 w) {
+// The point is the corner (pcx, pcy), at (pcx - 1/2, pcy - 1/2): exact in
+// float, so its doubles are made only where doubles decide.
+SBMT_DEV bool is_cand(const PreArgs& a, int pcx, int pcy, u32 u, u32 w) {
+  const float pxf = (float)pcx - 0.5f, pyf = (float)pcy - 0.5f;
   const float2 fu = a.xyf[u], fw = a.xyf[w];
   const float d2f = seg_d2f(pxf, pyf, fu, fw);
   if (d2f > a.b_hi2) return false;
   const double2* xy = reinterpret_cast<const double2*>(a.xy);
-  if ((fu.x == pxf && fu.y == pyf) || (fw.x == pxf && fw.y == pyf)) {
-    const double2 du = xy[u], dw = xy[w];
-    if ((du.x == px && du.y == py) || (dw.x == px && dw.y == py)) return false;
-  }
+  // an end at p: a vertex snapped to p, or (an exact coincidence) one whose
+  // double coordinates equal p's
+  const int p = pcy * (a.g.W + 1) + pcx;
+  auto at_p = [&](u32 v, float2 f) {
+    if (f.x != pxf || f.y != pyf) return false;
+    if (a.status[v] == 1) return a.snap[v] == p;
+    const double2 d = xy[v];
+    return d.x == half_minus(pcx) && d.y == half_minus(pcy);
+  };
+  if (at_p(u, fu) || at_p(w, fw)) return false;
   if (d2f < a.b_lo2) return true;
-  return seg_d2(px, py, xy[u], xy[w]) < a.B2;
+  return seg_d2(half_minus(pcx), half_minus(pcy), xy[u], xy[w]) < a.B2;
 }
 
 // pixel index of the centroid coordinate ((c0 + c1) + c2) / 3: the floor of
@@ -116,8 +136,9 @@ SBMT_DEV unsigned short moved_label(const PreArgs& a, const double2* pd, const f
   return pre_label<T>(a, col, row);
 }
 
-// x table over m = 2i + j (the x of v(i, j) depends on m only) and the pixel
-// rows of the centroids of unmoved up and down cells, per strip row
+// x table over m = 2i + j (the x of v(i, j) depends on m only), y of every
+// vertex row, and the pixel rows of the centroids of unmoved up and down
+// cells, per strip row
 __global__ void __launch_bounds__(256) k_pre_rows(PreArgs a) {
   const GridP& g = a.g;
   const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,6 +146,11 @@ __global__ void __launch_bounds__(256) k_pre_rows(PreArgs a) {
     const double x = __ddiv_rn((double)(g.ox + 3 * g.p * (a.m0 + k)), (double)g.S);
     a.tab[k] = x;
     a.tabf[k] = __double2float_rn(x);
+  }
+  for (i64 r = t0; r < g.nvrows; r += stride) {
+    const double y = row_y(g, g.vj0 + r);
+    a.ytab[r] = y;
+    a.ytabf[r] = __double2float_rn(y);
   }
   for (i64 r = t0; r < g.nrows; r += stride) {
     const i64 j = g.j0 + r;
@@ -135,131 +161,130 @@ __global__ void __launch_bounds__(256) k_pre_rows(PreArgs a) {
   }
 }
 
-// Region I for one vertex whose neighbourhood holds a boundary edge.
-// Distances are screened in single precision: a float distance more than
-// the band dband from a threshold decides like the double one; the rest,
-// the exact argmin among near ties, and the moved position take doubles.
-template <typename T>
-SBMT_DEV void region_one(const PreArgs& a, double x, double y, float xf, float yf, double2& out, float2& outf,
-                         unsigned char& st, int& sc) {
+// Step 1 for the vertex v: the boundary point nearest to v, if closer than
+// a (ties: the smaller id).  Float distances decide unless the nearest is
+// within the band of a or of the next one; then doubles do.  Returns true
+// with (bx, by) on a snap.
+SBMT_DEV bool step1(const PreArgs& a, double x, double y, float xf, float yf, int& bx, int& by) {
   const int W = a.g.W, H = a.g.H;
-  const float Af = a.ascr, Cf = a.cscr;
-  // Step 1: the boundary point nearest to v, if closer than a (ties: the
-  // smaller id; corners are visited in increasing id)
-  {
-    const int x0 = max(0, (int)ceilf(xf + 0.5f - Af)), x1 = min(W, (int)floorf(xf + 0.5f + Af));
-    const int y0 = max(0, (int)ceilf(yf + 0.5f - Af)), y1 = min(H, (int)floorf(yf + 0.5f + Af));
-    int nclose = 0, fx = -1, fy = -1;
-    bool sure = false;
-    for (int cy = y0; cy <= y1; ++cy)
-      for (int cx = x0; cx <= x1; ++cx) {
-        if (!corner_flag(a, cx, cy)) continue;
+  const float Af = a.ascr;
+  const int x0 = max(0, (int)ceilf(xf + 0.5f - Af)), x1 = min(W, (int)floorf(xf + 0.5f + Af));
+  const int y0 = max(0, (int)ceilf(yf + 0.5f - Af)), y1 = min(H, (int)floorf(yf + 0.5f + Af));
+  int nclose = 0;
+  float b1 = 3.0e38f, b2 = 3.0e38f;  // the two smallest float squared distances
+  for (int cy = y0; cy <= y1 && x0 <= x1; ++cy) {
+    const u32* wrow = a.vrow + (i64)cy * a.wpr;
+    for (int wx = x0 >> 5; wx <= (x1 >> 5); ++wx) {
+      const int lo = max(x0 - 32 * wx, 0), hi = min(x1 - 32 * wx, 31);
+      u32 bits = wrow[wx] & (0xFFFFFFFFu << lo) & (0xFFFFFFFFu >> (31 - hi));
+      while (bits) {
+        const int cx = 32 * wx + __ffs(bits) - 1;
+        bits &= bits - 1;
         const float dx = xf - ((float)cx - 0.5f), dy = yf - ((float)cy - 0.5f), d2f = dx * dx + dy * dy;
         if (d2f > a.a_hi2) continue;
-        if (nclose++ == 0) fx = cx, fy = cy, sure = d2f < a.a_lo2;
-      }
-    if (nclose == 1 && sure) {
-      out = make_double2((double)fx - 0.5, (double)fy - 0.5), outf = make_float2((float)fx - 0.5f, (float)fy - 0.5f);
-      st = 1, sc = fy * (W + 1) + fx;
-      return;
-    }
-    if (nclose > 0) {
-      double best = 0.0;
-      int bx = -1, by = -1;
-      for (int cy = y0; cy <= y1; ++cy)
-        for (int cx = x0; cx <= x1; ++cx) {
-          if (!corner_flag(a, cx, cy)) continue;
-          const double d2 = d2of(dsub(x, (double)cx - 0.5), dsub(y, (double)cy - 0.5));
-          if (bx < 0 || d2 < best) best = d2, bx = cx, by = cy;
-        }
-      if (best < dmul(a.A, a.A)) {
-        out = make_double2((double)bx - 0.5, (double)by - 0.5), outf = make_float2((float)bx - 0.5f, (float)by - 0.5f);
-        st = 1, sc = by * (W + 1) + bx;
-        return;
+        ++nclose;
+        if (d2f < b1) b2 = b1, b1 = d2f, bx = cx, by = cy;
+        else if (d2f < b2) b2 = d2f;
       }
     }
   }
-  // Step 2: the nearest point q of the boundary pixel edges (ties: the
-  // smaller edge id), if closer than c: v moves to q + c (v - q) / |v - q|.
-  // An edge within c of v lies between two pixels of the box around v.
-  const int m0 = max(-1, (int)ceilf(xf - Cf - 0.5f)), m1 = min(W, (int)floorf(xf + Cf + 0.5f));
-  const int k0 = max(-1, (int)ceilf(yf - Cf - 0.5f)), k1 = min(H, (int)floorf(yf + Cf + 0.5f));
-  float minf = 3.0e38f;
-  for (int kk = k0; kk <= k1; ++kk)
-    for (int m = m0; m <= m1; ++m) {
-      const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
-      if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
-        const float dx = xf - fminf(fmaxf(xf, (float)m - 0.5f), (float)m + 0.5f), dy = yf - ((float)kk - 0.5f);
-        minf = fminf(minf, dx * dx + dy * dy);
-      }
-      if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
-        const float dx = xf - ((float)m - 0.5f), dy = yf - fminf(fmaxf(yf, (float)kk - 0.5f), (float)kk + 0.5f);
-        minf = fminf(minf, dx * dx + dy * dy);
-      }
+  if (nclose == 0) return false;
+  if (b1 < a.a_lo2 && (nclose == 1 || sqrtf(b2) - sqrtf(b1) > 2.5f * a.dband)) return true;
+  // doubles, in increasing corner id
+  double best = 0.0;
+  bx = -1;
+  for (int cy = y0; cy <= y1; ++cy)
+    for (int cx = x0; cx <= x1; ++cx) {
+      if (!corner_flag(a, cx, cy)) continue;
+      const double d2 = d2of(dsub(x, half_minus(cx)), dsub(y, half_minus(cy)));
+      if (bx < 0 || d2 < best) best = d2, bx = cx, by = cy;
     }
-  if (minf > a.c_hi2) return;  // no boundary edge within c
-  // the edges within 2 dband of the float minimum, in doubles
-  const float lim = (sqrtf(minf) + 2.0f * a.dband) * (sqrtf(minf) + 2.0f * a.dband) * 1.0001f;
-  double best = 0.0, bqx = 0.0, bqy = 0.0;
-  i64 bid = -1;
-  for (int kk = k0; kk <= k1; ++kk)
-    for (int m = m0; m <= m1; ++m) {
-      const int l = pix<T>(a.img, a.pitch, W, H, m, kk);
-      // horizontal edge (m, kk): y = kk - 1/2 between pixels (m, kk - 1) and (m, kk)
-      if (kk > k0 && m >= 0 && m < W && l != pix<T>(a.img, a.pitch, W, H, m, kk - 1)) {
-        const float dx = xf - fminf(fmaxf(xf, (float)m - 0.5f), (float)m + 0.5f), dy = yf - ((float)kk - 0.5f);
-        if (dx * dx + dy * dy <= lim) {
-          const double qx = fmin(fmax(x, (double)m - 0.5), (double)m + 0.5), qy = (double)kk - 0.5;
-          const double d2 = d2of(dsub(x, qx), dsub(y, qy));
-          const i64 id = (i64)kk * W + m;
-          if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
-        }
-      }
-      // vertical edge (m, kk): x = m - 1/2 between pixels (m - 1, kk) and (m, kk)
-      if (m > m0 && kk >= 0 && kk < H && l != pix<T>(a.img, a.pitch, W, H, m - 1, kk)) {
-        const float dx = xf - ((float)m - 0.5f), dy = yf - fminf(fmaxf(yf, (float)kk - 0.5f), (float)kk + 0.5f);
-        if (dx * dx + dy * dy <= lim) {
-          const double qx = (double)m - 0.5, qy = fmin(fmax(y, (double)kk - 0.5), (double)kk + 0.5);
-          const double d2 = d2of(dsub(x, qx), dsub(y, qy));
-          const i64 id = (i64)(H + 1) * W + (i64)kk * (W + 1) + m;
-          if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
-        }
-      }
-    }
-  if (bid >= 0 && best < dmul(a.C, a.C)) {
-    const double t = __ddiv_rn(a.C, __dsqrt_rn(best));
-    out = make_double2(dadd(bqx, dmul(t, dsub(x, bqx))), dadd(bqy, dmul(t, dsub(y, bqy))));
-    outf = make_float2(__double2float_rn(out.x), __double2float_rn(out.y));
-    st = 2;
-  }
+  return best < dmul(a.A, a.A);
 }
 
-// Region I: Steps 1 and 2 for every lattice vertex, one block per vertex
-// row.  A vertex whose nearby pixels carry one label stays; the others are
-// queued in shared memory and taken by the whole block afterwards, so that
-// the few near the boundary do not hold up warps of vertices that stay.
-constexpr int PV_CHUNK = 1024;
+// Step 2's candidate edges: the boundary pixel edges between two pixels of
+// the box m0..m1 x k0..k1 (pixel labels from get(m, kk)).  Horizontal edge
+// (m, kk) at y = kk - 1/2 lies between pixels (m, kk - 1) and (m, kk), id
+// kk W + m; vertical edge (m, kk) at x = m - 1/2 between (m - 1, kk) and
+// (m, kk), id (H + 1) W + kk (W + 1) + m.  visit(horizontal, m, kk).
+template <class G, class F>
+SBMT_DEV void box_edges(int W, int H, int m0, int m1, int k0, int k1, G&& get, F&& visit) {
+  for (int kk = k0; kk <= k1; ++kk)
+    for (int m = m0; m <= m1; ++m) {
+      const int l = get(m, kk);
+      if (kk > k0 && m >= 0 && m < W && l != get(m, kk - 1)) visit(true, m, kk);
+      if (m > m0 && kk >= 0 && kk < H && l != get(m - 1, kk)) visit(false, m, kk);
+    }
+}
 
+// Step 2 for the vertex v: the nearest point q of the boundary pixel edges
+// (ties: the smaller edge id); if it is closer than c, v moves to
+// q + c (v - q) / |v - q|.  An edge within c of v lies between two pixels
+// of the box around v.  With only_screen, returns whether the float
+// distances leave a move possible (the nearest edge within the band of c);
+// otherwise decides in doubles among the edges within two bands of the
+// float minimum and returns whether v moved (to out).
+template <typename T>
+SBMT_DEV bool step2(const PreArgs& a, double x, double y, float xf, float yf, bool only_screen, double2& out) {
+  const int W = a.g.W, H = a.g.H;
+  const float Cf = a.cscr;
+  const int m0 = max(-1, (int)ceilf(xf - Cf - 0.5f)), m1 = min(W, (int)floorf(xf + Cf + 0.5f));
+  const int k0 = max(-1, (int)ceilf(yf - Cf - 0.5f)), k1 = min(H, (int)floorf(yf + Cf + 0.5f));
+  auto fdist = [&](bool hor, int m, int kk) {
+    const float dx = hor ? xf - fminf(fmaxf(xf, (float)m - 0.5f), (float)m + 0.5f) : xf - ((float)m - 0.5f);
+    const float dy = hor ? yf - ((float)kk - 0.5f) : yf - fminf(fmaxf(yf, (float)kk - 0.5f), (float)kk + 0.5f);
+    return dx * dx + dy * dy;
+  };
+  float minf = 3.0e38f;
+  auto fvisit = [&](bool hor, int m, int kk) { minf = fminf(minf, fdist(hor, m, kk)); };
+  double best = 0.0, bqx = 0.0, bqy = 0.0;
+  i64 bid = -1;
+  float lim = 0.0f;
+  auto dvisit = [&](bool hor, int m, int kk) {
+    if (fdist(hor, m, kk) > lim) return;
+    const double qx = hor ? fmin(fmax(x, half_minus(m)), half_minus(m + 1)) : half_minus(m);
+    const double qy = hor ? half_minus(kk) : fmin(fmax(y, half_minus(kk)), half_minus(kk + 1));
+    const double d2 = d2of(dsub(x, qx), dsub(y, qy));
+    const i64 id = hor ? (i64)kk * W + m : (i64)(H + 1) * W + (i64)kk * (W + 1) + m;
+    if (bid < 0 || d2 < best || (d2 == best && id < bid)) best = d2, bid = id, bqx = qx, bqy = qy;
+  };
+  auto get = [&](int m, int kk) { return pix<T>(a.img, a.pitch, W, H, m, kk); };
+  box_edges(W, H, m0, m1, k0, k1, get, fvisit);
+  if (minf > a.c_hi2) return false;  // no boundary edge within c
+  if (only_screen) return true;
+  lim = (sqrtf(minf) + 2.0f * a.dband) * (sqrtf(minf) + 2.0f * a.dband) * 1.0001f;
+  box_edges(W, H, m0, m1, k0, k1, get, dvisit);
+  if (bid < 0 || !(best < dmul(a.C, a.C))) return false;
+  const double t = __ddiv_rn(a.C, __dsqrt_rn(best));
+  out = make_double2(dadd(bqx, dmul(t, dsub(x, bqx))), dadd(bqy, dmul(t, dsub(y, bqy))));
+  return true;
+}
+
+// Region I, first pass: one block per vertex row.  A vertex whose nearby
+// pixels carry one label stays; the others are queued in the row's own part
+// of the queue (the row's vertex ids) for the second pass, which takes them
+// densely, so that the few near the boundary do not hold up warps of
+// vertices that stay.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
-  __shared__ u32 q[PV_CHUNK];
-  __shared__ u32 nq;
+  __shared__ u32 nslow;
+  if (threadIdx.x == 0) nslow = 0;
+  __syncthreads();
   const GridP& g = a.g;
   const int r = blockIdx.x, W = g.W, H = g.H;
   const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
-  const double y = row_y(g, j);
-  const float yf = __double2float_rn(y);
+  const double y = a.ytab[r];
+  const float yf = a.ytabf[r];
   const float Af = a.ascr;
   // pixel rows whose squares reach within a of the row
   const int py0 = (int)ceilf(yf - Af - 0.5f), py1 = (int)floorf(yf + Af + 0.5f);
   double2* xy = reinterpret_cast<double2*>(a.xy);
-  u32 nsnap = 0, nrep = 0;
-  for (i64 s0 = 0; s0 < n; s0 += PV_CHUNK) {
-    if (threadIdx.x == 0) nq = 0;
-    __syncthreads();
-    const int ns = (int)min((i64)PV_CHUNK, n - s0);
-    for (int e = threadIdx.x; e < ns; e += blockDim.x) {
-      const i64 k = s0 + e, mi = 2 * (lo + k) + j - a.m0;
+  const int lane = threadIdx.x & 31;
+  for (i64 k0 = 0; k0 < n; k0 += blockDim.x) {  // whole warps in every iteration
+    const i64 k = k0 + threadIdx.x;
+    bool slow = false;
+    if (k < n) {
+      const i64 mi = 2 * (lo + k) + j - a.m0;
       const float xf = a.tabf[mi];
       // one label over the pixels whose squares reach within a of v: no
       // boundary edge within a (c < a), no boundary point either (a PSLG
@@ -283,35 +308,99 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
         a.xyf[base + k] = make_float2(xf, yf);
         a.status[base + k] = 0;
         a.snap[base + k] = -1;
-      } else {
-        q[atomicAdd(&nq, 1u)] = (u32)e;
       }
+      slow = !uniform;
     }
-    __syncthreads();
-    const u32 nqs = nq;
-    for (u32 e = threadIdx.x; e < nqs; e += blockDim.x) {
-      const i64 k = s0 + q[e], mi = 2 * (lo + k) + j - a.m0;
-      const double x = a.tab[mi];
-      const float xf = a.tabf[mi];
-      double2 out = make_double2(x, y);
-      float2 outf = make_float2(xf, yf);
-      unsigned char st = 0;
-      int sc = -1;
-      region_one<T>(a, x, y, xf, yf, out, outf, st, sc);
-      xy[base + k] = out;
-      a.xyf[base + k] = outf;
-      a.status[base + k] = st;
-      a.snap[base + k] = sc;
-      nsnap += st == 1, nrep += st == 2;
+    const u32 m = __ballot_sync(0xFFFFFFFFu, slow);
+    if (m) {
+      u32 q0 = 0;
+      if (lane == 0) q0 = atomicAdd(&nslow, (u32)__popc(m));
+      q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
+      if (slow) a.vq[base + q0 + __popc(m & ((1u << lane) - 1u))] = (u32)(base + k);
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.vqn[r] = nslow;
+}
+
+// Region I, second pass: the queued vertices, one block per vertex row at a
+// time.  Step 1 in full; Step 2 only screened here: a vertex the float
+// distances leave within reach of c goes to the third pass, so that the
+// double-precision work of the moves runs in full warps.
+constexpr int PR_CHUNK = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_pre_region1(PreArgs a) {
+  __shared__ u32 rq[PR_CHUNK];
+  __shared__ u32 nrq, rq0;
+  const GridP& g = a.g;
+  double2* xy = reinterpret_cast<double2*>(a.xy);
+  u32 nsnap = 0;
+  for (int r = blockIdx.x; r < g.nvrows; r += gridDim.x) {
+    const u32 nq = a.vqn[r];
+    const i64 base = g.vbase[r], j = g.vj0 + r, lo = g.vlo[r];
+    const double y = a.ytab[r];
+    const float yf = a.ytabf[r];
+    for (u32 c0 = 0; c0 < nq; c0 += PR_CHUNK) {
+      if (threadIdx.x == 0) nrq = 0;
+      __syncthreads();
+      const u32 c1 = min(nq, c0 + PR_CHUNK);
+      for (u32 e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+        const i64 v = a.vq[base + e], mi = 2 * (lo + (v - base)) + j - a.m0;
+        const double x = a.tab[mi];
+        const float xf = a.tabf[mi];
+        int bx = -1, by = -1;
+        if (step1(a, x, y, xf, yf, bx, by)) {
+          xy[v] = make_double2(half_minus(bx), half_minus(by));
+          a.xyf[v] = make_float2((float)bx - 0.5f, (float)by - 0.5f);
+          a.status[v] = 1;
+          a.snap[v] = by * (g.W + 1) + bx;
+          ++nsnap;
+          continue;
+        }
+        double2 dummy;
+        xy[v] = make_double2(x, y);
+        a.xyf[v] = make_float2(xf, yf);
+        a.status[v] = 0;
+        a.snap[v] = -1;
+        if (step2<T>(a, x, y, xf, yf, true, dummy)) rq[atomicAdd(&nrq, 1u)] = (u32)v;
+      }
+      __syncthreads();
+      const u32 n = nrq;
+      if (threadIdx.x == 0 && n) rq0 = atomicAdd(a.cnt + 6, n);
+      __syncthreads();
+      for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+        a.rq[rq0 + e] = make_uint2(rq[e], (u32)r);
+      }
+      __syncthreads();
+    }
   }
   nsnap = __reduce_add_sync(0xFFFFFFFFu, nsnap);
-  nrep = __reduce_add_sync(0xFFFFFFFFu, nrep);
-  if ((threadIdx.x & 31) == 0) {
-    if (nsnap) atomicAdd(a.cnt + 3, nsnap);
-    if (nrep) atomicAdd(a.cnt + 4, nrep);
+  if ((threadIdx.x & 31) == 0 && nsnap) atomicAdd(a.cnt + 3, nsnap);
+}
+
+// Region I, third pass: Step 2 in doubles for the vertices the float
+// screen left within reach of c
+template <typename T>
+__global__ void __launch_bounds__(128) k_pre_repel(PreArgs a) {
+  const GridP& g = a.g;
+  const u32 n = a.cnt[6];
+  double2* xy = reinterpret_cast<double2*>(a.xy);
+  u32 nrep = 0;
+  for (u32 e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const uint2 qe = a.rq[e];
+    const int r = (int)qe.y;
+    const i64 v = qe.x, mi = 2 * (g.vlo[r] + (v - g.vbase[r])) + (g.vj0 + r) - a.m0;
+    double2 out;
+    if (step2<T>(a, a.tab[mi], a.ytab[r], a.tabf[mi], a.ytabf[r], false, out)) {
+      xy[v] = out;
+      a.xyf[v] = make_float2(__double2float_rn(out.x), __double2float_rn(out.y));
+      a.status[v] = 2;
+      ++nrep;
+    }
   }
+  nrep = __reduce_add_sync(0xFFFFFFFFu, nrep);
+  if ((threadIdx.x & 31) == 0 && nrep) atomicAdd(a.cnt + 4, nrep);
 }
 
 // population counts of a bit-plane; with wpr > 0 the plane has rows of wpr
@@ -351,7 +440,7 @@ __global__ void __launch_bounds__(256) k_pre_points(PreArgs a, u64 nw, const u32
 // Then the conflict test: p applies unless a smaller point has a candidate
 // on an edge of a cell beside p's edge; such a point lies within b of the
 // bounding box of those cells' moved corners.
-__global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
+__global__ void __launch_bounds__(128, 4) k_pre_step3(PreArgs a) {
   const GridP& g = a.g;
   const u64 V = (u64)g.nverts;
   const float R = a.reach;
@@ -359,7 +448,6 @@ __global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
   for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < a.np; t += gridDim.x * blockDim.x) {
     const u32 p = a.plist[t];
     const int pcx = (int)(p % (u32)(g.W + 1)), pcy = (int)(p / (u32)(g.W + 1));
-    const double px = (double)pcx - 0.5, py = (double)pcy - 0.5;
     const float pxf = (float)pcx - 0.5f, pyf = (float)pcy - 0.5f;
     PreCand c;
     c.u = c.w = NONE, c.cell[0] = c.cell[1] = NONE, c.k[0] = c.k[1] = 0, c.n = 0;
@@ -375,8 +463,8 @@ __global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
       // cell cc of the row spans 2u in [cc, cc + 2], u = (x - ox) / h - jj / 2
       const float ulo = 2.0f * ((pxf - R - a.oxf) / a.hf) - (float)jj;
       const float uhi = 2.0f * ((pxf + R - a.oxf) / a.hf) - (float)jj;
-      const i64 c0 = max(clo, (i64)floorf(ulo - 2.0f - 1e-6f * fabsf(ulo) - 0.01f));
-      const i64 c1 = min(g.chi[r], (i64)floorf(uhi + 1e-6f * fabsf(uhi) + 0.01f));
+      const i64 c0 = max(clo, (i64)(int)floorf(ulo - 2.0f - 1e-6f * fabsf(ulo) - 0.01f));
+      const i64 c1 = min(g.chi[r], (i64)(int)floorf(uhi + 1e-6f * fabsf(uhi) + 0.01f));
       for (i64 cc = c0; cc <= c1; ++cc) {
         const i64 i = cc >> 1;
         const bool down = (cc & 1) != 0;
@@ -391,7 +479,7 @@ __global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
           const u32 u = v[e], w = v[e == 2 ? 0 : e + 1];
-          if (!is_cand(a, px, py, pxf, pyf, u, w)) continue;
+          if (!is_cand(a, pcx, pcy, u, w)) continue;
           const u32 lo = min(u, w), hi = max(u, w);
           const u64 key = (u64)lo * V + hi;
           if (key < best) {
@@ -428,12 +516,10 @@ __global__ void __launch_bounds__(128) k_pre_step3(PreArgs a) {
           while (bits && ok) {
             const int cx = 32 * wx + __ffs(bits) - 1;
             bits &= bits - 1;
-            const double qx = (double)cx - 0.5, qy = (double)cy - 0.5;
-            const float qxf = (float)cx - 0.5f, qyf = (float)cy - 0.5f;
             for (int s = 0; s < c.n && ok; ++s)
 #pragma unroll
               for (int e = 0; e < 3; ++e)
-                if (ok && is_cand(a, qx, qy, qxf, qyf, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
+                if (ok && is_cand(a, cx, cy, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
           }
         }
       }
@@ -456,7 +542,10 @@ SBMT_DEV u64 out_index(const PreArgs& a, u32 cid) {
 // the preprocessed mesh: every cell that is not split, as its triangle
 // (A, B, C), labelled by its centroid -- exactly for a cell with three
 // unmoved corners (the column in integers, the row from the per-row table).
-// One block per strip row at a time, its threads over the row's cells.
+// One block per strip row at a time, each thread over four of the row's
+// cells at once (their loads issued together).
+constexpr int PE_CELLS = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
   const GridP& g = a.g;
@@ -464,38 +553,59 @@ __global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
   const int den = (int)(2 * g.S);
   const float inv_den = 1.0f / (float)den;
   for (int r = blockIdx.x; r < g.nrows; r += gridDim.x) {
-    const i64 jr = g.j0 + (i64)r, clo = g.clo[r], nrc = g.chi[r] - clo + 1;
+    const i64 jr = g.j0 + (i64)r, clo = g.clo[r];
+    const int nrc = (int)(g.chi[r] - clo + 1);
     const u32 cb = (u32)g.cbase[r];
     const int rv = (int)(jr - g.vj0);  // vertex rows rv (jr) and rv + 1 (jr + 1)
-    const i64 vb0 = g.vbase[rv] - g.vlo[rv], vb1 = g.vbase[rv + 1] - g.vlo[rv + 1];
+    const int vb0 = (int)(g.vbase[rv] - g.vlo[rv]), vb1 = (int)(g.vbase[rv + 1] - g.vlo[rv + 1]);
     const int prow0 = a.prow[2 * r], prow1 = a.prow[2 * r + 1];
+    const int i0 = (int)(clo >> 1), par = (int)(clo & 1);
     // centroid x of cell c in units of 1/S: ox + 3p (c + jr + 1), so the
     // pixel column's numerator 2 xc + S grows by 6p per cell
-    const i64 num0 = 2 * (g.ox + 3 * g.p * (clo + jr + 1)) + g.S;
-    for (i64 k = threadIdx.x; k < nrc; k += blockDim.x) {
-      const u32 cid = cb + (u32)k;
-      const u32 sw = a.sbit[cid >> 5];
-      if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
-      const u64 o = (u64)cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
-      const i64 c = clo + k, i = c >> 1;
-      const bool down = (c & 1) != 0;
-      const int v0 = (int)(down ? vb0 + i + 1 : vb0 + i), v1 = (int)(down ? vb1 + i + 1 : vb0 + i + 1);
-      const int v2 = (int)(vb1 + i);
-      unsigned short lab;
-      if ((a.status[v0] | a.status[v1] | a.status[v2]) == 0) {
+    const int num0 = (int)(2 * (g.ox + 3 * g.p * (clo + jr + 1)) + g.S), dnum = (int)(6 * g.p);
+    for (int kb = 0; kb < nrc; kb += PE_CELLS * blockDim.x) {
+      int v0[PE_CELLS], v1[PE_CELLS], v2[PE_CELLS], praw[PE_CELLS];
+      unsigned char mv[PE_CELLS];
+      u32 o[PE_CELLS];
+      bool act[PE_CELLS];
+#pragma unroll
+      for (int q = 0; q < PE_CELLS; ++q) {
+        const int k = kb + (int)threadIdx.x + q * (int)blockDim.x;
+        act[q] = false, v0[q] = v1[q] = v2[q] = 0, praw[q] = 0, mv[q] = 0, o[q] = 0;
+        if (k >= nrc) continue;
+        const u32 cid = cb + (u32)k;
+        const u32 sw = a.sbit[cid >> 5];
+        if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
+        act[q] = true;
+        o[q] = cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
+        const int c = par + k, i = i0 + (c >> 1);  // c: the cell index relative to 2 i0
+        const bool down = (c & 1) != 0;
+        v0[q] = down ? vb0 + i + 1 : vb0 + i;
+        v1[q] = down ? vb1 + i + 1 : vb0 + i + 1;
+        v2[q] = vb1 + i;
+        mv[q] = a.status[v0[q]] | a.status[v1[q]] | a.status[v2[q]];
         // pixel column floor(num / 2S): a float estimate, corrected
-        const int num = (int)(num0 + 6 * g.p * k);
+        const int num = num0 + dnum * k;
         int col = (int)floorf((float)num * inv_den);
         while (col * den > num) --col;
         while ((col + 1) * den <= num) ++col;
-        lab = pre_label<T>(a, col, down ? prow1 : prow0);
-      } else {
-        const double2 pd[3] = {xy[v0], xy[v1], xy[v2]};
-        const float2 pf[3] = {a.xyf[v0], a.xyf[v1], a.xyf[v2]};
-        lab = moved_label<T>(a, pd, pf);
+        praw[q] = pix<T>(a.img, a.pitch, g.W, g.H, col, down ? prow1 : prow0);
       }
-      a.tri[3 * o] = v0, a.tri[3 * o + 1] = v1, a.tri[3 * o + 2] = v2;
-      a.label[o] = lab, a.code[o] = 0;
+#pragma unroll
+      for (int q = 0; q < PE_CELLS; ++q) {
+        if (!act[q]) continue;
+        unsigned short lab;
+        if (mv[q] == 0) {
+          lab = praw[q] == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)praw[q];
+        } else {
+          const double2 pd[3] = {xy[v0[q]], xy[v1[q]], xy[v2[q]]};
+          const float2 pf[3] = {a.xyf[v0[q]], a.xyf[v1[q]], a.xyf[v2[q]]};
+          lab = moved_label<T>(a, pd, pf);
+        }
+        const u64 oo = o[q];
+        a.tri[3 * oo] = v0[q], a.tri[3 * oo + 1] = v1[q], a.tri[3 * oo + 2] = v2[q];
+        a.label[oo] = lab, a.code[oo] = 0;
+      }
     }
   }
 }
@@ -549,10 +659,17 @@ unsigned grid_for(u64 n, int threads, unsigned cap) {
 int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr, cudaStream_t st) {
   int n = 0;
   const GridP& g = a.g;
-  k_pre_rows<<<grid_for((u64)std::max<i64>(a.nm, g.nrows), 256, 1024), 256, 0, st>>>(a), ++n;
-  if (a.dtype == 1) k_pre_vertex<unsigned char><<<g.nvrows, 256, 0, st>>>(a);
-  else k_pre_vertex<unsigned short><<<g.nvrows, 256, 0, st>>>(a);
-  ++n;
+  k_pre_rows<<<grid_for((u64)std::max<i64>(a.nm, std::max(g.nrows, g.nvrows)), 256, 1024), 256, 0, st>>>(a), ++n;
+  if (a.dtype == 1) {
+    k_pre_vertex<unsigned char><<<g.nvrows, 256, 0, st>>>(a);
+    k_pre_region1<unsigned char><<<(unsigned)std::min(g.nvrows, 152 * 16), 128, 0, st>>>(a);
+    k_pre_repel<unsigned char><<<152 * 8, 128, 0, st>>>(a);
+  } else {
+    k_pre_vertex<unsigned short><<<g.nvrows, 256, 0, st>>>(a);
+    k_pre_region1<unsigned short><<<(unsigned)std::min(g.nvrows, 152 * 16), 128, 0, st>>>(a);
+    k_pre_repel<unsigned short><<<152 * 8, 128, 0, st>>>(a);
+  }
+  n += 3;
   // the boundary points, in corner-id order
   k_popc<<<grid_for(nw, 256, 152 * 8), 256, 0, st>>>(a.vrow, nw, a.wpr, g.W, wpop), ++n;
   n += launch_scan(wpop, 1, wscan, (u32)nw, scr, st);

@@ -854,7 +854,9 @@ int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params*
       (rc = aalloc(lane, &a.plist, std::max<u64>(NP, 1))) || (rc = aalloc(lane, &a.appl, std::max<u64>(NP, 1))) ||
       (rc = aalloc(lane, &a.ascan, NP + 1)) || (rc = aalloc(lane, &a.sbit, nsw + 1)) ||
       (rc = aalloc(lane, &a.spop, nsw + 1)) || (rc = aalloc(lane, &a.wpre, nsw + 1)) ||
-      (rc = aalloc(lane, &scr, scr_words)))
+      (rc = aalloc(lane, &scr, scr_words)) || (rc = aalloc(lane, &a.ytab, (size_t)nvr)) ||
+      (rc = aalloc(lane, &a.ytabf, (size_t)nvr)) || (rc = aalloc(lane, &a.vq, std::max<u64>(V, 1))) ||
+      (rc = aalloc(lane, &a.vqn, (size_t)nvr)) || (rc = aalloc(lane, &a.rq, std::max<u64>(V, 1))))
     return bail(rc);
   char* candb;
   if ((rc = aalloc(lane, &candb, pre_cand_bytes((u32)NP)))) return bail(rc);

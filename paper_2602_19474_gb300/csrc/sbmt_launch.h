@@ -121,8 +121,9 @@ int launch_project(const double* xy, const int* tri, u64 T, u64 V, const float* 
 // of the moved lattice positions), plist (np boundary points), cand
 // (pre_cand_bytes(np)), appl / ascan (np and np + 1 words), sbit / spop /
 // wpre (split-cell bit-plane of ncells / 32 + 1 words, its counts and their
-// scan), cnt (6 zeroed words: error, eliminations, split cells, snapped,
-// repelled, points with a candidate).  Outputs: xy (lattice vertices, then
+// scan), ytab / ytabf / vqn (one per vertex row), vq / rq (nverts), cnt
+// (7 zeroed words: error, eliminations, split cells, snapped, repelled,
+// points with a candidate, the Step 2 queue length).  Outputs: xy (lattice vertices, then
 // the inserted points), tri / label / code (ncells + split cells
 // triangles), status and snap per lattice vertex, elim (3 per elimination).
 struct PreCand;
@@ -143,6 +144,11 @@ struct PreArgs {
   i64 m0, nm;
   double* tab;
   float* tabf;
+  double* ytab;  // y of every vertex row, and its float copy
+  float* ytabf;
+  u32* vq;       // Region I queue: vertex ids, in each row's own id range
+  u32* vqn;      // queued vertices per vertex row
+  uint2* rq;     // Step 2 queue: (vertex id, vertex row), nverts entries
   int* prow;
   float2* xyf;
   u32* plist;
