@@ -511,6 +511,16 @@ def our_arm(args, rank: int, world: int, dist):
     e1.record(st)
     torch.cuda.synchronize()
     ms_q = e0.elapsed_time(e1) / args.steps
+    # the preprocessed mesh's smallest angle and area against the bounds of
+    # the minimal-angle and minimal-area theorems (thresholds in pixels)
+    m = sb.mesh_preprocess(ctx, dimg, hn, hd, *tri_abc)
+    qq = sb.mesh_quality(ctx, m)
+    qi = sb.mesh_preprocess_info(ctx, m)
+    sb.mesh_release(ctx, m)
+    ap, bp, cp, e_ = qi.a_px, qi.b_px, qi.c_px, hn / hd
+    theta = min(math.atan(bp / (e_ + ap - math.sqrt(ap * ap - bp * bp))), math.atan(cp / (e_ + ap)))
+    pre_bounds = {"min_angle_deg": qq["min_angle_deg"], "angle_bound_deg": math.degrees(theta),
+                  "min_area": qq["min_area"], "area_bound": 0.5 * bp * cp}
     qbytes = (img.nbytes + 16.0 * vq.n_vertices + 16.0 * vq.n_triangles + 5.0 * vq.n_lattice_vertices
               + 12.0 * pinfo.n_eliminated)
     preprocess = {"what": "Alg. 3 Steps 1-3 (snap within a, repel to c, re-fan edges within b of a boundary point) "
@@ -518,7 +528,8 @@ def our_arm(args, rank: int, world: int, dist):
                   "ms_per_call": ms_q, "triangles_per_s": vq.n_triangles / (ms_q * 1e-3),
                   "triangles": vq.n_triangles, "boundary_points": pinfo.n_points, "snapped": pinfo.n_snapped,
                   "repelled": pinfo.n_repelled, "eliminated": pinfo.n_eliminated,
-                  "algorithmic_bytes_per_call": qbytes, "achieved_gbs": qbytes / (ms_q * 1e-3) / 1e9}
+                  "algorithmic_bytes_per_call": qbytes, "achieved_gbs": qbytes / (ms_q * 1e-3) / 1e9,
+                  "quality_vs_bounds": pre_bounds}
     compact = {"what": "the same mesh in the compact format (uncut cells as a label per base cell, cut cells' "
                        "patches listed); triangles/s counts the triangles the mesh represents",
                "ms_per_step": ms_c, "value": job_rate(world, T, ms_c), "patch_triangles": vc.n_patch_triangles,

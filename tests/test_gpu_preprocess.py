@@ -101,6 +101,24 @@ def test_thresholds_outside_the_admissible_range_are_rejected():
     assert e.value.code == sb.SBMT_EPROTO
 
 
+def test_angle_and_area_bounds_on_the_preprocessed_mesh():
+    # the minimal-angle and minimal-area theorems' bounds, with the
+    # thresholds in pixels, hold on the preprocessed mesh of these inputs
+    import math
+
+    for img, hn, hd in [(synth.voronoi_labels(size=256, nseeds=40), 2, 1),
+                        (synth.noise_bitmap(synth.rng_for(21), 128, 96, 2.0), 2, 3)]:
+        c = ctx()
+        m = sb.mesh_preprocess(c, img, hn, hd)
+        q = sb.mesh_quality(c, m)
+        info = sb.mesh_preprocess_info(c, m)
+        sb.mesh_release(c, m)
+        A, B, C, e = info.a_px, info.b_px, info.c_px, hn / hd
+        theta = min(math.atan(B / (e + A - math.sqrt(A * A - B * B))), math.atan(C / (e + A)))
+        assert q["min_angle_deg"] > math.degrees(theta), (q["min_angle_deg"], math.degrees(theta))
+        assert q["min_area"] > 0.5 * B * C, (q["min_area"], 0.5 * B * C)
+
+
 def test_quality_and_projection_accept_the_preprocessed_mesh():
     img = synth.voronoi_labels(size=96, nseeds=12)
     c = ctx()
