@@ -265,6 +265,8 @@ SBMT_DEV bool step2(const PreArgs& a, double x, double y, float xf, float yf, bo
 // of the queue (the row's vertex ids) for the second pass, which takes them
 // densely, so that the few near the boundary do not hold up warps of
 // vertices that stay.
+constexpr int PV_U = 1;  // vertices per thread per iteration (2 measured slower)
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
   __shared__ u32 nslow;
@@ -278,45 +280,69 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
   const float Af = a.ascr;
   // pixel rows whose squares reach within a of the row
   const int py0 = (int)ceilf(yf - Af - 0.5f), py1 = (int)floorf(yf + Af + 0.5f);
+  const float invS = 1.0f / (float)g.S;
   double2* xy = reinterpret_cast<double2*>(a.xy);
   const int lane = threadIdx.x & 31;
-  for (i64 k0 = 0; k0 < n; k0 += blockDim.x) {  // whole warps in every iteration
-    const i64 k = k0 + threadIdx.x;
-    bool slow = false;
-    if (k < n) {
-      const i64 mi = 2 * (lo + k) + j - a.m0;
-      const float xf = a.tabf[mi];
-      // one label over the pixels whose squares reach within a of v: no
-      // boundary edge within a (c < a), no boundary point either (a PSLG
-      // vertex's four pixels are among them), and v stays.  Boxes reaching
-      // past the image take the general path.
-      const int px0 = (int)ceilf(xf - Af - 0.5f), px1 = (int)floorf(xf + Af + 0.5f);
-      bool uniform = false;
-      if (px0 >= 0 && py0 >= 0 && px1 < W && py1 < H) {
-        const unsigned char* rowp = a.img + (i64)py0 * a.pitch;
-        const T l0 = ((const T*)rowp)[px0];
-        uniform = true;
-        for (int yy = py0; yy <= py1 && uniform; ++yy, rowp += a.pitch)
-          for (int xx = px0; xx <= px1; ++xx)
-            if (((const T*)rowp)[xx] != l0) {
-              uniform = false;
-              break;
-            }
-      }
-      if (uniform) {
+  // one label over the pixels whose squares reach within a of v: no boundary
+  // edge within a (c < a), no boundary point either (a PSLG vertex's four
+  // pixels are among them), and v stays.  Boxes reaching past the image take
+  // the general path.
+  auto uniform_at = [&](i64 mi) {
+    // x of v for the box: the exact numerator times 1/S in float (within a
+    // few float roundings of the table's value; the box's margin covers them)
+    const float xq = (float)(int)(g.ox + 3 * g.p * (a.m0 + mi)) * invS;
+    const int px0 = (int)ceilf(xq - Af - 0.5f), px1 = (int)floorf(xq + Af + 0.5f);
+    if (px0 < 0 || py0 < 0 || px1 >= W || py1 >= H) return false;
+    const unsigned char* rowp = a.img + (i64)py0 * a.pitch;
+    const T l0 = ((const T*)rowp)[px0];
+    bool uniform = true;
+    if (py1 - py0 < 3 && px1 - px0 < 4) {
+      // a box of at most 3 x 4 pixels: all loads issued at once
+      T pv[3][4];
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          pv[rr][c] = (rr <= py1 - py0 && c <= px1 - px0) ? ((const T*)(rowp + rr * a.pitch))[px0 + c] : l0;
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) uniform &= pv[rr][c] == l0;
+    } else {
+      for (int yy = py0; yy <= py1 && uniform; ++yy, rowp += a.pitch)
+        for (int xx = px0; xx <= px1; ++xx)
+          if (((const T*)rowp)[xx] != l0) {
+            uniform = false;
+            break;
+          }
+    }
+    return uniform;
+  };
+  // the screen's loads before any store; whole warps in every iteration
+  for (i64 k0 = 0; k0 < n; k0 += PV_U * blockDim.x) {
+    bool slow[PV_U];
+#pragma unroll
+    for (int u = 0; u < PV_U; ++u) {
+      const i64 k = k0 + threadIdx.x + u * blockDim.x;
+      slow[u] = k < n && !uniform_at(2 * (lo + k) + j - a.m0);
+    }
+#pragma unroll
+    for (int u = 0; u < PV_U; ++u) {
+      const i64 k = k0 + threadIdx.x + u * blockDim.x;
+      if (k < n && !slow[u]) {
+        const i64 mi = 2 * (lo + k) + j - a.m0;
         xy[base + k] = make_double2(a.tab[mi], y);
-        a.xyf[base + k] = make_float2(xf, yf);
+        a.xyf[base + k] = make_float2(a.tabf[mi], yf);
         a.status[base + k] = 0;
         a.snap[base + k] = -1;
       }
-      slow = !uniform;
-    }
-    const u32 m = __ballot_sync(0xFFFFFFFFu, slow);
-    if (m) {
-      u32 q0 = 0;
-      if (lane == 0) q0 = atomicAdd(&nslow, (u32)__popc(m));
-      q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
-      if (slow) a.vq[base + q0 + __popc(m & ((1u << lane) - 1u))] = (u32)(base + k);
+      const u32 m = __ballot_sync(0xFFFFFFFFu, slow[u]);
+      if (m) {
+        u32 q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&nslow, (u32)__popc(m));
+        q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
+        if (slow[u]) a.vq[base + q0 + __popc(m & ((1u << lane) - 1u))] = (u32)(base + k);
+      }
     }
   }
   __syncthreads();
@@ -547,7 +573,7 @@ SBMT_DEV u64 out_index(const PreArgs& a, u32 cid) {
 constexpr int PE_CELLS = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
+__global__ void __launch_bounds__(256, 6) k_pre_emit(PreArgs a) {
   const GridP& g = a.g;
   const double2* xy = reinterpret_cast<const double2*>(a.xy);
   const int den = (int)(2 * g.S);
@@ -568,16 +594,17 @@ __global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
       unsigned char mv[PE_CELLS];
       u32 o[PE_CELLS];
       bool act[PE_CELLS];
+      // every load of the four cells first (a cell past the row's end reads
+      // the row's last cell), then the split test and the writes
+      u32 sw[PE_CELLS], wp[PE_CELLS], cidq[PE_CELLS];
 #pragma unroll
       for (int q = 0; q < PE_CELLS; ++q) {
-        const int k = kb + (int)threadIdx.x + q * (int)blockDim.x;
-        act[q] = false, v0[q] = v1[q] = v2[q] = 0, praw[q] = 0, mv[q] = 0, o[q] = 0;
-        if (k >= nrc) continue;
+        const int k0q = kb + (int)threadIdx.x + q * (int)blockDim.x;
+        act[q] = k0q < nrc;
+        const int k = act[q] ? k0q : nrc - 1;
         const u32 cid = cb + (u32)k;
-        const u32 sw = a.sbit[cid >> 5];
-        if ((sw >> (cid & 31)) & 1u) continue;  // split: the split kernel writes it
-        act[q] = true;
-        o[q] = cid + a.wpre[cid >> 5] + __popc(sw & ((1u << (cid & 31)) - 1u));
+        cidq[q] = cid;
+        sw[q] = a.sbit[cid >> 5], wp[q] = a.wpre[cid >> 5];
         const int c = par + k, i = i0 + (c >> 1);  // c: the cell index relative to 2 i0
         const bool down = (c & 1) != 0;
         v0[q] = down ? vb0 + i + 1 : vb0 + i;
@@ -590,6 +617,12 @@ __global__ void __launch_bounds__(256) k_pre_emit(PreArgs a) {
         while (col * den > num) --col;
         while ((col + 1) * den <= num) ++col;
         praw[q] = pix<T>(a.img, a.pitch, g.W, g.H, col, down ? prow1 : prow0);
+      }
+#pragma unroll
+      for (int q = 0; q < PE_CELLS; ++q) {
+        const u32 cid = cidq[q];
+        if ((sw[q] >> (cid & 31)) & 1u) act[q] = false;  // split: the split kernel writes it
+        o[q] = cid + wp[q] + __popc(sw[q] & ((1u << (cid & 31)) - 1u));
       }
 #pragma unroll
       for (int q = 0; q < PE_CELLS; ++q) {
