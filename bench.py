@@ -530,6 +530,44 @@ def our_arm(args, rank: int, world: int, dist):
                   "repelled": pinfo.n_repelled, "eliminated": pinfo.n_eliminated,
                   "algorithmic_bytes_per_call": qbytes, "achieved_gbs": qbytes / (ms_q * 1e-3) / 1e9,
                   "quality_vs_bounds": pre_bounds}
+    # heat diffusion (App. H) on the step's mesh: the region of the most
+    # frequent label, a Gaussian pulse at the image centre, alpha = 500 px^2/s,
+    # backward Euler with dt = 0.01 s, conjugate gradients to 1e-10
+    Lh = int(np.bincount(img.ravel()).argmax())
+    m = sb.mesh_bitmap(ctx, dimg, hn, hd)
+    vh = sb.mesh_query(ctx, m, -1)
+    th = sb.view_tensors(vh)
+    in_l = th["label"].view(torch.int16) == (Lh if Lh < 32768 else Lh - 65536)
+    tri_l = th["tri"][in_l].long()
+    mark = torch.zeros(vh.n_vertices, dtype=torch.int8, device=dev)
+    mark[th["tri"][~in_l].long().ravel()] = 2
+    mark[tri_l.ravel()] |= 1
+    n_free = int((mark == 1).sum())
+    n_rtri = int(tri_l.shape[0])
+    del th, in_l, tri_l, mark
+    uh = torch.empty(vh.n_vertices, dtype=torch.float64, device=dev)
+    sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, 2, W / 2.0, H / 2.0, 127.0, u=uh)
+    hsteps = 10
+    torch.cuda.synchronize()
+    e0.record(st)
+    _, hpeaks, hits = sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, hsteps, W / 2.0, H / 2.0, 127.0, u=uh)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_h = e0.elapsed_time(e1)
+    sb.mesh_release(ctx, m)
+    del uh
+    cg_its = sum(hits)
+    # bytes per CG iteration: the triangle pass reads a 40-byte record and
+    # gathers and adds three doubles per region triangle; the vector kernels
+    # move about 16 doubles per free vertex
+    it_bytes = 88.0 * n_rtri + 128.0 * n_free
+    heat = {"what": "App. H heat diffusion on the mesh region of label %d: cotangent stiffness, lumped mass, "
+                    "backward Euler (dt 0.01, alpha 500 px^2/s), preconditioned CG to 1e-10, %d steps from a "
+                    "Gaussian pulse (sigma 127 px) at the image centre" % (Lh, hsteps),
+            "ms_per_step": ms_h / hsteps, "cg_iterations_per_step": cg_its / hsteps,
+            "ms_per_cg_iteration": ms_h / max(cg_its, 1), "region_triangles": n_rtri, "free_vertices": n_free,
+            "peak_after": hpeaks[-1], "bytes_per_cg_iteration": it_bytes,
+            "achieved_gbs": it_bytes * cg_its / (ms_h * 1e-3) / 1e9}
     compact = {"what": "the same mesh in the compact format (uncut cells as a label per base cell, cut cells' "
                        "patches listed); triangles/s counts the triangles the mesh represents",
                "ms_per_step": ms_c, "value": job_rate(world, T, ms_c), "patch_triangles": vc.n_patch_triangles,
@@ -579,6 +617,7 @@ def our_arm(args, rank: int, world: int, dist):
         "e2e": {"value": e2e_value, "unit": "triangles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "compact_format": compact,
         "projection": dict(projection, peak=peak, frac=projection["achieved_gbs"] / peak),
+        "heat": dict(heat, peak=peak, frac=heat["achieved_gbs"] / peak),
         "preprocess": dict(preprocess, peak=peak, frac=preprocess["achieved_gbs"] / peak,
                            cpu_baseline=pre_cpu),
         "gpu_launches": launches,

@@ -285,6 +285,42 @@ int mesh_quality(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_quality* out);
  * or a mesh of 2^32 triangles or more. */
 int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* tri_value, float* vertex_value);
 
+/* Transient heat diffusion on a label region of a finished mesh (App. H:
+ * du/dt = alpha Lap u on the region, u = 0 on its boundary, from a centred
+ * Gaussian pulse).  The region is the set of triangles of label `label`; its
+ * boundary vertices (those also on a triangle of another label, 0xFFFF
+ * outside the image included) stay at 0, and the other vertices of the
+ * region are free.  Linear finite elements (the paper names no scheme):
+ *  - K, the cotangent stiffness: a triangle with angle theta_k at corner k
+ *    adds -cot(theta_k)/2 to K_ij and K_ji for the opposite edge ij and
+ *    cot(theta_k)/2 to K_ii and K_jj;
+ *  - M, the lumped mass: a third of the area of each region triangle at a
+ *    vertex;
+ *  - backward Euler: (M + alpha dt K) u_{n+1} = M u_n on the free vertices.
+ * Each step is solved by conjugate gradients with the diagonal as
+ * preconditioner, started from u_n, until |r| <= tol |b|, in double
+ * precision.
+ *  u0 = amplitude exp(-|x - (x0, y0)|^2 / (2 sigma^2)) at the free vertices
+ *  (pixel units; alpha in px^2 per unit time).
+ *  u           device, n_vertices doubles: u after `steps` steps (0 outside
+ *              the region and on its boundary);
+ *  peaks       host, `steps` doubles, or NULL: the maximum of u after each
+ *              step;
+ *  iterations  host, `steps` int32, or NULL: the CG iterations of each step.
+ * Explicit meshes only (SBMT_EINVAL otherwise, or for bad parameters).
+ * SBMT_ETIMEDOUT if a step does not converge within max_iterations.  Runs on
+ * the context's stream after the mesh and returns when done. */
+typedef struct {
+  int32_t label;
+  double alpha, dt;
+  int32_t steps;
+  double x0, y0, sigma, amplitude;
+  double tol;
+  int32_t max_iterations;
+} sbmt_heat_params;
+int mesh_heat(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_heat_params* params, double* u, double* peaks,
+              int32_t* iterations);
+
 /* Per-kernel device time, for tracing and roofline accounting (no
  * counterpart in the paper, which reports no timings).  With enable != 0
  * every kernel launch of the context is bracketed by two CUDA events on the

@@ -37,7 +37,7 @@ SBMT_KEEP_STAGES = 1
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
            "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
-           "mesh_preprocess_info", "sbmt_last_error")
+           "mesh_preprocess_info", "mesh_heat", "sbmt_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -76,6 +76,13 @@ class sbmt_pre_info(ctypes.Structure):
                 ("n_eliminated", ctypes.c_int64), ("n_split_cells", ctypes.c_int64), ("a_px", ctypes.c_double),
                 ("b_px", ctypes.c_double), ("c_px", ctypes.c_double), ("status", ctypes.c_void_p),
                 ("snap", ctypes.c_void_p), ("elim", ctypes.c_void_p)]
+
+
+class sbmt_heat_params(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_int32), ("alpha", ctypes.c_double), ("dt", ctypes.c_double),
+                ("steps", ctypes.c_int32), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("amplitude", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iterations", ctypes.c_int32)]
 
 
 class SbmtError(RuntimeError):
@@ -119,10 +126,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mesh_preprocess.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params),
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_preprocess_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_pre_info)]
+    lib.mesh_heat.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_heat_params), vp, vp, vp]
     lib.sbmt_last_error.restype = ctypes.c_char_p
     for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
               "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
-              "mesh_preprocess_info"):
+              "mesh_preprocess_info", "mesh_heat"):
         getattr(lib, f).restype = ctypes.c_int
     del i32
     _lib = lib
@@ -298,6 +306,23 @@ def mesh_project(ctx: int, mesh: int, field, tri_value=None, vertex_value=None) 
 
     _check(load().mesh_project(ctx, mesh, ctypes.byref(fi), ptr(tri_value), ptr(vertex_value)))
     del keep
+
+
+def mesh_heat(ctx: int, mesh: int, label: int, alpha: float, dt: float, steps: int, x0: float, y0: float,
+              sigma: float, amplitude: float = 100.0, tol: float = 1e-10, max_iterations: int = 10000, u=None):
+    """Heat diffusion on the triangles of one label (App. H); returns (u as a
+    CUDA float64 tensor over the mesh's vertices, peaks per step, CG
+    iterations per step)."""
+    import torch
+
+    v = mesh_query(ctx, mesh, -1)
+    if u is None:
+        u = torch.empty(v.n_vertices, dtype=torch.float64, device="cuda")
+    pr = sbmt_heat_params(label, alpha, dt, steps, x0, y0, sigma, amplitude, tol, max_iterations)
+    peaks = (ctypes.c_double * max(steps, 1))()
+    its = (ctypes.c_int32 * max(steps, 1))()
+    _check(load().mesh_heat(ctx, mesh, ctypes.byref(pr), ctypes.c_void_p(u.data_ptr()), peaks, its))
+    return u, [peaks[k] for k in range(steps)], [its[k] for k in range(steps)]
 
 
 def mesh_profile(ctx: int, enable: bool) -> None:

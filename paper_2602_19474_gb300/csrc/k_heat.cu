@@ -1,0 +1,336 @@
+// k_heat.cu -- transient heat diffusion on a label region of a finished mesh
+// (App. H): du/dt = alpha Lap u on the triangles of one label, u = 0 on the
+// region's boundary, from a Gaussian pulse.
+//
+// Linear finite elements: the cotangent stiffness K (a triangle with angle
+// theta_k at corner k couples the ends i, j of the opposite edge with
+// -cot(theta_k) / 2 and adds cot(theta_k) / 2 to both diagonals), the lumped
+// mass M (a third of each incident triangle's area), backward Euler in time:
+// (M + alpha dt K) u_{n+1} = M u_n on the free vertices (those of the region
+// not on a triangle of another label).  Each step is solved by conjugate
+// gradients with the diagonal as preconditioner, matrix-free: the operator
+// is one pass over the region's triangles.  Double precision throughout; the
+// region's records are built once per call.
+#include <algorithm>
+#include <vector>
+
+#include "sbmt_dev.cuh"
+#include "sbmt_launch.h"
+
+namespace sbmt {
+
+namespace {
+
+constexpr int HB = 256;  // threads per block
+
+// one region triangle: its corners and the weights cot(theta_k) / 2 of the
+// edges opposite each corner
+struct HeatTri {
+  int v[3];
+  int pad;
+  double w[3];
+};
+
+__global__ void __launch_bounds__(HB) k_heat_flags(const int* tri, const unsigned short* label, u64 T, int L,
+                                                   u32* flag) {
+  for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (u64)gridDim.x * blockDim.x) {
+    const u32 f = label[t] == (unsigned short)L ? 1u : 2u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicOr(flag + tri[3 * t + k], f);
+  }
+}
+
+// free vertices (flag 1) as 0/1 for the scan that numbers them
+__global__ void __launch_bounds__(HB) k_heat_free(u64 V, u32* flag) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
+    flag[v] = flag[v] == 1u ? 1u : 0u;
+}
+
+// the free vertices in id order (fidx: exclusive scan of the 0/1 flags)
+__global__ void __launch_bounds__(HB) k_heat_list(u64 V, const u32* free01, const u32* fidx, u32* list) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
+    if (free01[v]) list[fidx[v]] = (u32)v;
+}
+
+// the region's triangles: records (corners as free indices, -1 for
+// boundary vertices), lumped mass and the stiffness diagonal per free vertex
+__global__ void __launch_bounds__(HB) k_heat_setup(const double* xy, const int* tri, const unsigned short* label,
+                                                   u64 T, int L, const u32* free01, const u32* fidx, HeatTri* rec,
+                                                   u32* nrec, double* mass, double* kdiag) {
+  const double2* p = reinterpret_cast<const double2*>(xy);
+  const int lane = threadIdx.x & 31;
+  for (u64 t0 = (u64)blockIdx.x * blockDim.x; t0 < T; t0 += (u64)gridDim.x * blockDim.x) {
+    const u64 t = t0 + threadIdx.x;
+    const bool in = t < T && label[t] == (unsigned short)L;
+    const u32 m = __ballot_sync(0xFFFFFFFFu, in);
+    u32 base = 0;
+    if (lane == 0 && m) base = atomicAdd(nrec, (u32)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (!in) continue;
+    HeatTri h;
+    double2 c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int v = tri[3 * t + k];
+      c[k] = p[v];
+      h.v[k] = free01[v] ? (int)fidx[v] : -1;
+    }
+    h.pad = 0;
+    const double cross = fabs((c[1].x - c[0].x) * (c[2].y - c[0].y) - (c[1].y - c[0].y) * (c[2].x - c[0].x));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double2 a = c[k], b = c[(k + 1) % 3], d = c[(k + 2) % 3];
+      const double dot = (b.x - a.x) * (d.x - a.x) + (b.y - a.y) * (d.y - a.y);
+      h.w[k] = 0.5 * dot / cross;  // cot(theta_k) / 2 = (u . v) / (2 |u x v|)
+    }
+    rec[base + __popc(m & ((1u << lane) - 1u))] = h;
+    const double third = cross / 6.0;  // a third of the area |u x v| / 2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (h.v[k] >= 0) atomicAdd(mass + h.v[k], third);
+      // the edge opposite corner k joins corners k + 1 and k + 2
+      const int i = h.v[(k + 1) % 3], j = h.v[(k + 2) % 3];
+      if (i >= 0) atomicAdd(kdiag + i, h.w[k]);
+      if (j >= 0) atomicAdd(kdiag + j, h.w[k]);
+    }
+  }
+}
+
+// block sum of v into *out (one double atomic per block)
+__device__ __forceinline__ void block_add(double v, double* out) {
+  __shared__ double s[HB / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < blockDim.x / 32 ? s[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (threadIdx.x == 0 && v != 0.0) atomicAdd(out, v);
+  }
+  __syncthreads();
+}
+
+// the free vertices: the pulse, the operator's inverse diagonal
+__global__ void __launch_bounds__(HB) k_heat_init(const double* xy, u32 n, const u32* list, const double* mass,
+                                                  const double* kdiag, double tau, double x0, double y0,
+                                                  double s2, double amp, double* x, double* dinv) {
+  const double2* p = reinterpret_cast<const double2*>(xy);
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double2 c = p[list[i]];
+    const double dx = c.x - x0, dy = c.y - y0;
+    x[i] = amp * exp(-(dx * dx + dy * dy) / (2.0 * s2));
+    dinv[i] = 1.0 / (mass[i] + tau * kdiag[i]);
+  }
+}
+
+// q = M x
+__global__ void __launch_bounds__(HB) k_heat_mass(u32 n, const double* mass, const double* x, double* q) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) q[i] = mass[i] * x[i];
+}
+
+// q += tau K x, one thread per region triangle; boundary vertices (index
+// -1) hold 0 and get no row
+__global__ void __launch_bounds__(HB) k_heat_stiff(const HeatTri* rec, u32 n, double tau, const double* x,
+                                                   double* q) {
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const HeatTri h = rec[t];
+    double xs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xs[k] = h.v[k] >= 0 ? x[h.v[k]] : 0.0;
+    double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int i = (k + 1) % 3, j = (k + 2) % 3;
+      const double f = tau * h.w[k] * (xs[i] - xs[j]);
+      acc[i] += f, acc[j] -= f;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (h.v[k] >= 0) atomicAdd(q + h.v[k], acc[k]);
+  }
+}
+
+// u over the mesh: 0, then the free values at their vertices
+__global__ void __launch_bounds__(HB) k_heat_zero(u64 V, double* u) {
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x) u[v] = 0.0;
+}
+__global__ void __launch_bounds__(HB) k_heat_put(u32 n, const u32* list, const double* x, double* u) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) u[list[i]] = x[i];
+}
+
+// CG scalars per iteration it: s[4 it + 0] = p.q, s[4 it + 1] = r.z,
+// s[4 it + 2] = r.r (all zeroed before the solve)
+__global__ void __launch_bounds__(HB) k_heat_dot(u64 V, const double* a, const double* b, double* out) {
+  double acc = 0.0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
+    acc += a[v] * b[v];
+  block_add(acc, out);
+}
+
+// r = b - q (q = A x), z = D^-1 r, p = z; r.z into rz, r.r into rr
+__global__ void __launch_bounds__(HB) k_heat_start(u64 V, const double* b, const double* q, const double* dinv,
+                                                   double* r, double* z, double* p, double* rz, double* rr) {
+  double a1 = 0.0, a2 = 0.0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x) {
+    const double rv = dinv[v] != 0.0 ? b[v] - q[v] : 0.0, zv = rv * dinv[v];
+    r[v] = rv, z[v] = zv, p[v] = zv;
+    a1 += rv * zv, a2 += rv * rv;
+  }
+  block_add(a1, rz);
+  block_add(a2, rr);
+}
+
+// x += alpha p, r -= alpha q, z = D^-1 r, with alpha = rz / pq; the new
+// r.z and r.r
+__global__ void __launch_bounds__(HB) k_heat_update(u64 V, const double* sc, double* x, double* r, double* z,
+                                                    const double* p, const double* q, const double* dinv,
+                                                    double* rz_next, double* rr_next) {
+  const double al = sc[0] != 0.0 ? sc[1] / sc[0] : 0.0;  // sc: {p.q, r.z} of this iteration
+  double a1 = 0.0, a2 = 0.0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x) {
+    x[v] += al * p[v];
+    const double rv = r[v] - al * q[v], zv = rv * dinv[v];
+    r[v] = rv, z[v] = zv;
+    a1 += rv * zv, a2 += rv * rv;
+  }
+  block_add(a1, rz_next);
+  block_add(a2, rr_next);
+}
+
+// p = z + beta p, beta = rz_next / rz
+__global__ void __launch_bounds__(HB) k_heat_dir(u64 V, const double* rz, const double* rz_next, const double* z,
+                                                 double* p) {
+  const double be = *rz != 0.0 ? *rz_next / *rz : 0.0;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
+    p[v] = z[v] + be * p[v];
+}
+
+// per-block maxima of u (the host takes the largest)
+__global__ void __launch_bounds__(HB) k_heat_max(u64 V, const double* u, double* out) {
+  __shared__ double s[HB / 32];
+  double m = -1.0e308;
+  for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
+    m = fmax(m, u[v]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmax(m, s[w]);
+    out[blockIdx.x] = m;
+  }
+}
+
+unsigned grid_v(u64 n) { return (unsigned)std::max<u64>(1, std::min<u64>((n + HB - 1) / HB, 152 * 8)); }
+
+}  // namespace
+
+size_t heat_scratch_bytes(u64 T, u64 V, int maxit) {
+  return 256 * 20 + T * sizeof(HeatTri) + V * (4 + 4 + 4 + 8 * 9) + 8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 +
+         4 * scan_scratch_words((u32)std::min<u64>(V, 0xFFFFFFFFu));
+}
+
+int heat_solve(const double* xy, const int* tri, const unsigned short* label, u64 T, u64 V, int L, double alpha,
+               double dt, int nsteps, double x0, double y0, double sigma, double amp, double tol, int maxit,
+               double* u, double* peaks, int* iters, void* scratch, cudaStream_t st) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* s = (char*)scratch;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = s + off;
+    off = up(off + bytes);
+    return p;
+  };
+  u32* nrec = (u32*)take(16);
+  HeatTri* rec = (HeatTri*)take(T * sizeof(HeatTri));
+  u32* flag = (u32*)take(4 * V);
+  u32* fidx = (u32*)take(4 * (V + 1));
+  u32* list = (u32*)take(4 * V);
+  double* mass = (double*)take(8 * V);
+  double* kdiag = (double*)take(8 * V);
+  double* dinv = (double*)take(8 * V);
+  double* x = (double*)take(8 * V);
+  double* b = (double*)take(8 * V);
+  double* q = (double*)take(8 * V);
+  double* r = (double*)take(8 * V);
+  double* z = (double*)take(8 * V);
+  double* p = (double*)take(8 * V);
+  double* sc = (double*)take(8 * 4 * (size_t)(maxit + 1));  // 4 per iteration
+  double* bmax = (double*)take(8 * 152 * 8);
+  u32* sscr = (u32*)take(4 * scan_scratch_words((u32)V) + 4);
+  const unsigned gt = grid_v(T);
+  const double tau = alpha * dt;
+  int launches = 0;
+  if (cudaMemsetAsync(nrec, 0, 16, st) || cudaMemsetAsync(flag, 0, 4 * V, st)) return -1;
+  k_heat_flags<<<gt, HB, 0, st>>>(tri, label, T, L, flag);
+  k_heat_free<<<grid_v(V), HB, 0, st>>>(V, flag);
+  launches += 2 + launch_scan(flag, 1, fidx, (u32)V, sscr, st);
+  k_heat_list<<<grid_v(V), HB, 0, st>>>(V, flag, fidx, list);
+  u32 n = 0;
+  if (cudaMemcpyAsync(&n, fidx + V, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
+  if (cudaMemsetAsync(mass, 0, 8 * (size_t)std::max<u32>(n, 1), st) ||
+      cudaMemsetAsync(kdiag, 0, 8 * (size_t)std::max<u32>(n, 1), st))
+    return -1;
+  k_heat_setup<<<gt, HB, 0, st>>>(xy, tri, label, T, L, flag, fidx, rec, nrec, mass, kdiag);
+  const unsigned gv = grid_v(n);
+  k_heat_init<<<gv, HB, 0, st>>>(xy, n, list, mass, kdiag, tau, x0, y0, sigma * sigma, amp, x, dinv);
+  u32 nr = 0;
+  if (cudaMemcpyAsync(&nr, nrec, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
+  const unsigned gr = grid_v(nr);
+  launches += 3;
+  bool converged = true;
+  if (n == 0)
+    for (int step = 0; step < nsteps; ++step) {
+      if (iters) iters[step] = 0;
+      if (peaks) peaks[step] = 0.0;
+    }
+  for (int step = 0; step < nsteps && n > 0; ++step) {
+    // b = M x_n; start from x_n: r = b - A x_n
+    if (cudaMemsetAsync(sc, 0, 8 * 4 * (size_t)(maxit + 1), st)) return -1;
+    k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, b);
+    k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, q);
+    k_heat_stiff<<<gr, HB, 0, st>>>(rec, nr, tau, x, q);
+    k_heat_start<<<gv, HB, 0, st>>>(n, b, q, dinv, r, z, p, sc + 1, sc + 2);
+    k_heat_dot<<<gv, HB, 0, st>>>(n, b, b, sc + 3);
+    launches += 5;
+    double h2[2];
+    if (cudaMemcpyAsync(h2, sc + 2, 16, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
+    const double stop = tol * tol * h2[1];
+    double rr = h2[0];
+    int it = 0;
+    while (rr > stop && it < maxit) {
+      double* s0 = sc + 4 * it;  // {p.q, r.z, r.r, -} of iteration it; the next iteration's at s0 + 4
+      k_heat_mass<<<gv, HB, 0, st>>>(n, mass, p, q);
+      k_heat_stiff<<<gr, HB, 0, st>>>(rec, nr, tau, p, q);
+      k_heat_dot<<<gv, HB, 0, st>>>(n, p, q, s0);
+      k_heat_update<<<gv, HB, 0, st>>>(n, s0, x, r, z, p, q, dinv, s0 + 5, s0 + 6);
+      k_heat_dir<<<gv, HB, 0, st>>>(n, s0 + 1, s0 + 5, z, p);
+      launches += 5;
+      ++it;
+      // the residual, read back every eighth iteration
+      if ((it & 7) == 0 || it == maxit) {
+        if (cudaMemcpyAsync(&rr, sc + 4 * it + 2, 8, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+          return -1;
+      }
+    }
+    if (iters) iters[step] = it;
+    if (peaks) {
+      k_heat_max<<<gv, HB, 0, st>>>(n, x, bmax);
+      ++launches;
+      std::vector<double> hb(gv);
+      if (cudaMemcpyAsync(hb.data(), bmax, 8 * gv, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
+        return -1;
+      peaks[step] = std::max(0.0, *std::max_element(hb.begin(), hb.end()));
+    }
+    if (rr > stop) {
+      converged = false;
+      break;
+    }
+  }
+  k_heat_zero<<<grid_v(V), HB, 0, st>>>(V, u);
+  k_heat_put<<<std::max(gv, 1u), HB, 0, st>>>(n, list, x, u);
+  launches += 2;
+  if (!converged) return -2;
+  return launches;
+}
+
+}  // namespace sbmt

@@ -168,11 +168,12 @@ enum {
   KN_TIERG,
   KN_XY,
   KN_PRE,
+  KN_HEAT,
   KN_COUNT
 };
 const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_seg_count", "k_scan",
                                             "k_walk", "k_rank", "k_sort", "k_cutcells", "k_emit",
-                                            "k_tierg", "k_lattice_xy", "k_preprocess"};
+                                            "k_tierg", "k_lattice_xy", "k_preprocess", "k_heat"};
 
 // One stream of work: the context's own stream, or one of the extra streams
 // a batch spreads its images over.  Each lane has its own scratch arena and
@@ -1304,6 +1305,45 @@ int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* 
   if (e != cudaSuccess) return fail(SBMT_ECUDA, "projection launch: %s", cudaGetErrorString(e));
   // the mesh's completion now includes the projection
   CK(cudaEventRecord(m->done, st));
+  return SBMT_OK;
+}
+
+int mesh_heat(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_heat_params* hp, double* u, double* peaks,
+              int32_t* iterations) {
+  if (!ctx || !hp || !u) return fail(SBMT_EINVAL, "null argument");
+  if (hp->steps < 0 || !(hp->dt > 0) || !(hp->alpha >= 0) || !(hp->sigma > 0) || !(hp->tol > 0) ||
+      hp->max_iterations < 1 || hp->label < 0 || hp->label > 0xFFFF)
+    return fail(SBMT_EINVAL, "heat parameters");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  MeshRec* m;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    auto it = ctx->meshes.find(mesh);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+    m = it->second;
+  }
+  if (m->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "heat diffusion needs the explicit format");
+  if (int rc0 = settle(m)) return rc0;
+  if (m->nt >= (1ll << 32) || m->nv >= (1ll << 31)) return fail(SBMT_EINVAL, "mesh too large");
+  CK(cudaSetDevice(ctx->device));
+  Lane* lane = &ctx->main;
+  cudaStream_t st = lane->stream;
+  CK(cudaStreamWaitEvent(st, m->done, 0));
+  arena_begin(lane);
+  char* scratch;
+  int rc = aalloc(lane, &scratch, heat_scratch_bytes((u64)m->nt, (u64)m->nv, hp->max_iterations));
+  if (rc) {
+    arena_end(lane);
+    return rc;
+  }
+  int n = 0;
+  TRACE(KN_HEAT, n = heat_solve(m->xy, m->tri, m->label, (u64)m->nt, (u64)m->nv, hp->label, hp->alpha, hp->dt,
+                                hp->steps, hp->x0, hp->y0, hp->sigma, hp->amplitude, hp->tol, hp->max_iterations, u,
+                                peaks, iterations, scratch, st));
+  arena_end(lane);
+  if (n == -2) return fail(SBMT_ETIMEDOUT, "a step did not reach the residual within %d iterations", hp->max_iterations);
+  if (n < 0) return fail(SBMT_ECUDA, "heat solve: %s", cudaGetErrorString(cudaGetLastError()));
+  CK(cudaGetLastError());
   return SBMT_OK;
 }
 

@@ -166,6 +166,19 @@ size_t pre_cand_bytes(u32 np);
 // -1 if a CUDA call failed.
 int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr, cudaStream_t st);
 
+// heat diffusion on the triangles of label L (backward Euler, cotangent
+// stiffness, lumped mass, preconditioned conjugate gradients to relative
+// residual tol, at most maxit iterations per step): u (device, V doubles)
+// receives the solution; peaks / iters (host, nsteps each, or null) the
+// maximum of u and the iterations after each step.  scratch holds
+// heat_scratch_bytes(T, V, maxit) bytes (256-byte aligned).  Synchronises
+// with the device a few times per step; returns the kernels launched, -1 if
+// a CUDA call failed, -2 if a step did not converge.
+size_t heat_scratch_bytes(u64 T, u64 V, int maxit);
+int heat_solve(const double* xy, const int* tri, const unsigned short* label, u64 T, u64 V, int L, double alpha,
+               double dt, int nsteps, double x0, double y0, double sigma, double amp, double tol, int maxit,
+               double* u, double* peaks, int* iters, void* scratch, cudaStream_t st);
+
 // coordinates of the lattice vertices; tab: scratch of nm doubles for the x
 // values (ox + 3p m) / S, m0 <= m < m0 + nm covering 2i + j of every vertex
 int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st);

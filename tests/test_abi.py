@@ -40,7 +40,7 @@ def test_struct_layouts_match_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = (sb.sbmt_image, sb.sbmt_params, sb.sbmt_mesh_view, sb.sbmt_quality, sb.sbmt_pre_info)
+    structs = (sb.sbmt_image, sb.sbmt_params, sb.sbmt_mesh_view, sb.sbmt_quality, sb.sbmt_pre_info, sb.sbmt_heat_params)
     lines = []
     for st in structs:
         n = st.__name__
@@ -68,4 +68,5 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mesh_destroy(None) == sb.SBMT_EINVAL
     assert lib.mesh_preprocess(None, None, None, None) == sb.SBMT_EINVAL
     assert lib.mesh_preprocess_info(None, 1, None) == sb.SBMT_EINVAL
+    assert lib.mesh_heat(None, 1, None, None, None, None) == sb.SBMT_EINVAL
     assert isinstance(lib.sbmt_last_error(), bytes)
