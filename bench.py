@@ -544,6 +544,9 @@ def our_arm(args, rank: int, world: int, dist):
     mark[tri_l.ravel()] |= 1
     n_free = int((mark == 1).sum())
     n_rtri = int(tri_l.shape[0])
+    fr = mark[tri_l] == 1  # (n_rtri, 3): which corners are free
+    nnz = 2 * int((fr[:, [0, 1, 2]] & fr[:, [1, 2, 0]]).sum())  # two entries per edge with both ends free
+    del fr
     del th, in_l, tri_l, mark
     uh = torch.empty(vh.n_vertices, dtype=torch.float64, device=dev)
     sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, 2, W / 2.0, H / 2.0, 127.0, u=uh)
@@ -557,15 +560,17 @@ def our_arm(args, rank: int, world: int, dist):
     sb.mesh_release(ctx, m)
     del uh
     cg_its = sum(hits)
-    # bytes per CG iteration: the triangle pass reads a 40-byte record and
-    # gathers and adds three doubles per region triangle; the vector kernels
-    # move about 16 doubles per free vertex
-    it_bytes = 88.0 * n_rtri + 128.0 * n_free
+    # bytes per CG iteration: the sparse product reads the row offset, the
+    # diagonal, x and writes q per free vertex, and a column, a value and a
+    # gathered x per entry; the update and the new direction move 11 doubles
+    # per free vertex
+    it_bytes = 28.0 * n_free + 20.0 * nnz + 88.0 * n_free
     heat = {"what": "App. H heat diffusion on the mesh region of label %d: cotangent stiffness, lumped mass, "
                     "backward Euler (dt 0.01, alpha 500 px^2/s), preconditioned CG to 1e-10, %d steps from a "
                     "Gaussian pulse (sigma 127 px) at the image centre" % (Lh, hsteps),
             "ms_per_step": ms_h / hsteps, "cg_iterations_per_step": cg_its / hsteps,
             "ms_per_cg_iteration": ms_h / max(cg_its, 1), "region_triangles": n_rtri, "free_vertices": n_free,
+            "matrix_entries": nnz,
             "peak_after": hpeaks[-1], "bytes_per_cg_iteration": it_bytes,
             "achieved_gbs": it_bytes * cg_its / (ms_h * 1e-3) / 1e9}
     compact = {"what": "the same mesh in the compact format (uncut cells as a label per base cell, cut cells' "

@@ -8,9 +8,10 @@
 // mass M (a third of each incident triangle's area), backward Euler in time:
 // (M + alpha dt K) u_{n+1} = M u_n on the free vertices (those of the region
 // not on a triangle of another label).  Each step is solved by conjugate
-// gradients with the diagonal as preconditioner, matrix-free: the operator
-// is one pass over the region's triangles.  Double precision throughout; the
-// region's records are built once per call.
+// gradients with the diagonal as preconditioner.  The operator is assembled
+// once per call into sparse rows over the free vertices (from one record per
+// region triangle), so that each product is a gather with no atomics.
+// Double precision throughout.
 #include <algorithm>
 #include <vector>
 
@@ -113,13 +114,14 @@ __device__ __forceinline__ void block_add(double v, double* out) {
 // the free vertices: the pulse, the operator's inverse diagonal
 __global__ void __launch_bounds__(HB) k_heat_init(const double* xy, u32 n, const u32* list, const double* mass,
                                                   const double* kdiag, double tau, double x0, double y0,
-                                                  double s2, double amp, double* x, double* dinv) {
+                                                  double s2, double amp, double* x, double* dg, double* dinv) {
   const double2* p = reinterpret_cast<const double2*>(xy);
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double2 c = p[list[i]];
     const double dx = c.x - x0, dy = c.y - y0;
     x[i] = amp * exp(-(dx * dx + dy * dy) / (2.0 * s2));
-    dinv[i] = 1.0 / (mass[i] + tau * kdiag[i]);
+    dg[i] = mass[i] + tau * kdiag[i];
+    dinv[i] = 1.0 / dg[i];
   }
 }
 
@@ -128,26 +130,50 @@ __global__ void __launch_bounds__(HB) k_heat_mass(u32 n, const double* mass, con
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) q[i] = mass[i] * x[i];
 }
 
-// q += tau K x, one thread per region triangle; boundary vertices (index
-// -1) hold 0 and get no row
-__global__ void __launch_bounds__(HB) k_heat_stiff(const HeatTri* rec, u32 n, double tau, const double* x,
-                                                   double* q) {
+// the operator as sparse rows over the free vertices: two entries per
+// region-triangle edge with both ends free (an edge shared by two region
+// triangles gives two entries for the same neighbour; they are summed by the
+// product), -tau cot/2 each; the diagonal is kept apart
+__global__ void __launch_bounds__(HB) k_heat_rowcount(const HeatTri* rec, u32 n, u32* cnt) {
   for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const HeatTri h = rec[t];
-    double xs[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) xs[k] = h.v[k] >= 0 ? x[h.v[k]] : 0.0;
-    double acc[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const int i = (k + 1) % 3, j = (k + 2) % 3;
-      const double f = tau * h.w[k] * (xs[i] - xs[j]);
-      acc[i] += f, acc[j] -= f;
+      const int i = h.v[(k + 1) % 3], j = h.v[(k + 2) % 3];
+      if (i >= 0 && j >= 0) atomicAdd(cnt + i, 1u), atomicAdd(cnt + j, 1u);
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      if (h.v[k] >= 0) atomicAdd(q + h.v[k], acc[k]);
   }
+}
+__global__ void __launch_bounds__(HB) k_heat_fill(const HeatTri* rec, u32 n, double tau, u32* cur, u32* col,
+                                                  double* val) {
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const HeatTri h = rec[t];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int i = h.v[(k + 1) % 3], j = h.v[(k + 2) % 3];
+      if (i < 0 || j < 0) continue;
+      const double w = -tau * h.w[k];
+      const u32 a = atomicAdd(cur + i, 1u), b = atomicAdd(cur + j, 1u);
+      col[a] = (u32)j, val[a] = w;
+      col[b] = (u32)i, val[b] = w;
+    }
+  }
+}
+
+// q = (M + tau K) x over the free rows (dg: the diagonal M + tau diag K),
+// and x . q added into *xq
+__global__ void __launch_bounds__(HB) k_heat_apply(u32 n, const u32* rowptr, const u32* col, const double* val,
+                                                   const double* dg, const double* x, double* q, double* xq) {
+  double acc = 0.0;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double xi = x[i];
+    double y = dg[i] * xi;
+    const u32 e1 = rowptr[i + 1];
+    for (u32 e = rowptr[i]; e < e1; ++e) y += val[e] * x[col[e]];
+    q[i] = y;
+    acc += xi * y;
+  }
+  block_add(acc, xq);
 }
 
 // u over the mesh: 0, then the free values at their vertices
@@ -225,7 +251,8 @@ unsigned grid_v(u64 n) { return (unsigned)std::max<u64>(1, std::min<u64>((n + HB
 }  // namespace
 
 size_t heat_scratch_bytes(u64 T, u64 V, int maxit) {
-  return 256 * 20 + T * sizeof(HeatTri) + V * (4 + 4 + 4 + 8 * 9) + 8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 +
+  return 256 * 24 + T * (sizeof(HeatTri) + 6 * (4 + 8)) + V * (4 + 4 + 4 + 4 + 8 * 10) +
+         8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 +
          4 * scan_scratch_words((u32)std::min<u64>(V, 0xFFFFFFFFu));
 }
 
@@ -248,6 +275,10 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
   double* mass = (double*)take(8 * V);
   double* kdiag = (double*)take(8 * V);
   double* dinv = (double*)take(8 * V);
+  double* dg = (double*)take(8 * V);
+  u32* rowptr = (u32*)take(4 * (V + 1));
+  u32* col = (u32*)take(4 * 6 * T);
+  double* val = (double*)take(8 * 6 * T);
   double* x = (double*)take(8 * V);
   double* b = (double*)take(8 * V);
   double* q = (double*)take(8 * V);
@@ -272,11 +303,21 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     return -1;
   k_heat_setup<<<gt, HB, 0, st>>>(xy, tri, label, T, L, flag, fidx, rec, nrec, mass, kdiag);
   const unsigned gv = grid_v(n);
-  k_heat_init<<<gv, HB, 0, st>>>(xy, n, list, mass, kdiag, tau, x0, y0, sigma * sigma, amp, x, dinv);
+  k_heat_init<<<gv, HB, 0, st>>>(xy, n, list, mass, kdiag, tau, x0, y0, sigma * sigma, amp, x, dg, dinv);
   u32 nr = 0;
   if (cudaMemcpyAsync(&nr, nrec, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
   const unsigned gr = grid_v(nr);
   launches += 3;
+  // the rows: counts (in flag, free now), their scan, then the entries at
+  // cursors starting from the row offsets
+  if (n > 0) {
+    if (cudaMemsetAsync(flag, 0, 4 * (size_t)n, st)) return -1;
+    k_heat_rowcount<<<gr, HB, 0, st>>>(rec, nr, flag);
+    launches += 1 + launch_scan(flag, 1, rowptr, n, sscr, st);
+    if (cudaMemcpyAsync(flag, rowptr, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st)) return -1;
+    k_heat_fill<<<gr, HB, 0, st>>>(rec, nr, tau, flag, col, val);
+    ++launches;
+  }
   bool converged = true;
   if (n == 0)
     for (int step = 0; step < nsteps; ++step) {
@@ -287,11 +328,10 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     // b = M x_n; start from x_n: r = b - A x_n
     if (cudaMemsetAsync(sc, 0, 8 * 4 * (size_t)(maxit + 1), st)) return -1;
     k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, b);
-    k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, q);
-    k_heat_stiff<<<gr, HB, 0, st>>>(rec, nr, tau, x, q);
+    k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, col, val, dg, x, q, bmax);
     k_heat_start<<<gv, HB, 0, st>>>(n, b, q, dinv, r, z, p, sc + 1, sc + 2);
     k_heat_dot<<<gv, HB, 0, st>>>(n, b, b, sc + 3);
-    launches += 5;
+    launches += 4;
     double h2[2];
     if (cudaMemcpyAsync(h2, sc + 2, 16, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
     const double stop = tol * tol * h2[1];
@@ -299,12 +339,10 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     int it = 0;
     while (rr > stop && it < maxit) {
       double* s0 = sc + 4 * it;  // {p.q, r.z, r.r, -} of iteration it; the next iteration's at s0 + 4
-      k_heat_mass<<<gv, HB, 0, st>>>(n, mass, p, q);
-      k_heat_stiff<<<gr, HB, 0, st>>>(rec, nr, tau, p, q);
-      k_heat_dot<<<gv, HB, 0, st>>>(n, p, q, s0);
+      k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, col, val, dg, p, q, s0);
       k_heat_update<<<gv, HB, 0, st>>>(n, s0, x, r, z, p, q, dinv, s0 + 5, s0 + 6);
       k_heat_dir<<<gv, HB, 0, st>>>(n, s0 + 1, s0 + 5, z, p);
-      launches += 5;
+      launches += 3;
       ++it;
       // the residual, read back every eighth iteration
       if ((it & 7) == 0 || it == maxit) {
