@@ -90,6 +90,16 @@ def test_small_and_degenerate_images():
             assert_same_pre(gpu_pre(img, hn, hd), P.preprocess(img, hn, hd, *TRIPLET))
 
 
+def test_extreme_grid_sizes():
+    # h = 2/63 px (about 1.4e5 lattice vertices over a 12 x 10 image: the
+    # finest grid), h = 64 px (snapping radius near 25 px: the general paths
+    # of the neighbourhood screens), and h = 6/5
+    for img, hn, hd in [(synth.noise_bitmap(synth.rng_for(13), 12, 10, 1.0), 2, 63),
+                        (synth.voronoi_labels(size=300, nseeds=6), 64, 1),
+                        (synth.voronoi_labels(size=70, nseeds=7), 6, 5)]:
+        assert_same_pre(gpu_pre(img, hn, hd), P.preprocess(img, hn, hd, *TRIPLET))
+
+
 def test_thresholds_outside_the_admissible_range_are_rejected():
     img = synth.disk()
     for a, b, c in [(0.24, 0.115, 0.17), (0.26, 0.13, 0.1), (0.4, 0.1, 0.1), (0.0, 0.0, 0.0)]:
