@@ -544,9 +544,12 @@ def our_arm(args, rank: int, world: int, dist):
     mark[tri_l.ravel()] |= 1
     n_free = int((mark == 1).sum())
     n_rtri = int(tri_l.shape[0])
-    fr = mark[tri_l] == 1  # (n_rtri, 3): which corners are free
-    nnz = 2 * int((fr[:, [0, 1, 2]] & fr[:, [1, 2, 0]]).sum())  # two entries per edge with both ends free
-    del fr
+    # the operator's entries: two per distinct edge with both ends free
+    ea, eb = tri_l[:, [0, 1, 2]].reshape(-1), tri_l[:, [1, 2, 0]].reshape(-1)
+    both = (mark[ea] == 1) & (mark[eb] == 1)
+    keys = torch.minimum(ea, eb)[both] * vh.n_vertices + torch.maximum(ea, eb)[both]
+    nnz = 2 * int(torch.unique(keys).numel())
+    del ea, eb, both, keys
     del th, in_l, tri_l, mark
     uh = torch.empty(vh.n_vertices, dtype=torch.float64, device=dev)
     sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, 2, W / 2.0, H / 2.0, 127.0, u=uh)

@@ -131,9 +131,9 @@ __global__ void __launch_bounds__(HB) k_heat_mass(u32 n, const double* mass, con
 }
 
 // the operator as sparse rows over the free vertices: two entries per
-// region-triangle edge with both ends free (an edge shared by two region
-// triangles gives two entries for the same neighbour; they are summed by the
-// product), -tau cot/2 each; the diagonal is kept apart
+// region-triangle edge with both ends free, -tau cot/2 each (an edge shared
+// by two region triangles gives two entries for the same neighbour, merged
+// afterwards); the diagonal is kept apart
 __global__ void __launch_bounds__(HB) k_heat_rowcount(const HeatTri* rec, u32 n, u32* cnt) {
   for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const HeatTri h = rec[t];
@@ -160,16 +160,39 @@ __global__ void __launch_bounds__(HB) k_heat_fill(const HeatTri* rec, u32 n, dou
   }
 }
 
+// each row's entries of one column summed, in place at the row's start;
+// mcnt: the merged counts
+__global__ void __launch_bounds__(HB) k_heat_merge(u32 n, const u32* rowptr, u32* col, double* val, u32* mcnt) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const u32 e0 = rowptr[i], e1 = rowptr[i + 1];
+    u32 m = 0;
+    for (u32 e = e0; e < e1; ++e) {
+      const u32 c = col[e];
+      const double v = val[e];
+      u32 k = 0;
+      while (k < m && col[e0 + k] != c) ++k;
+      if (k < m) {
+        val[e0 + k] += v;
+      } else {
+        col[e0 + m] = c, val[e0 + m] = v;
+        ++m;
+      }
+    }
+    mcnt[i] = m;
+  }
+}
+
 // q = (M + tau K) x over the free rows (dg: the diagonal M + tau diag K),
 // and x . q added into *xq
-__global__ void __launch_bounds__(HB) k_heat_apply(u32 n, const u32* rowptr, const u32* col, const double* val,
-                                                   const double* dg, const double* x, double* q, double* xq) {
+__global__ void __launch_bounds__(HB) k_heat_apply(u32 n, const u32* rowptr, const u32* mcnt, const u32* col,
+                                                   const double* val, const double* dg, const double* x, double* q,
+                                                   double* xq) {
   double acc = 0.0;
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double xi = x[i];
     double y = dg[i] * xi;
-    const u32 e1 = rowptr[i + 1];
-    for (u32 e = rowptr[i]; e < e1; ++e) y += val[e] * x[col[e]];
+    const u32 e0 = rowptr[i], e1 = e0 + mcnt[i];
+    for (u32 e = e0; e < e1; ++e) y += val[e] * x[col[e]];
     q[i] = y;
     acc += xi * y;
   }
@@ -251,7 +274,7 @@ unsigned grid_v(u64 n) { return (unsigned)std::max<u64>(1, std::min<u64>((n + HB
 }  // namespace
 
 size_t heat_scratch_bytes(u64 T, u64 V, int maxit) {
-  return 256 * 24 + T * (sizeof(HeatTri) + 6 * (4 + 8)) + V * (4 + 4 + 4 + 4 + 8 * 10) +
+  return 256 * 25 + T * (sizeof(HeatTri) + 6 * (4 + 8)) + V * (4 + 4 + 4 + 4 + 4 + 8 * 10) +
          8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 +
          4 * scan_scratch_words((u32)std::min<u64>(V, 0xFFFFFFFFu));
 }
@@ -277,6 +300,7 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
   double* dinv = (double*)take(8 * V);
   double* dg = (double*)take(8 * V);
   u32* rowptr = (u32*)take(4 * (V + 1));
+  u32* mcnt = (u32*)take(4 * V);
   u32* col = (u32*)take(4 * 6 * T);
   double* val = (double*)take(8 * 6 * T);
   double* x = (double*)take(8 * V);
@@ -316,7 +340,8 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     launches += 1 + launch_scan(flag, 1, rowptr, n, sscr, st);
     if (cudaMemcpyAsync(flag, rowptr, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st)) return -1;
     k_heat_fill<<<gr, HB, 0, st>>>(rec, nr, tau, flag, col, val);
-    ++launches;
+    k_heat_merge<<<gv, HB, 0, st>>>(n, rowptr, col, val, mcnt);
+    launches += 2;
   }
   bool converged = true;
   if (n == 0)
@@ -328,7 +353,7 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     // b = M x_n; start from x_n: r = b - A x_n
     if (cudaMemsetAsync(sc, 0, 8 * 4 * (size_t)(maxit + 1), st)) return -1;
     k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, b);
-    k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, col, val, dg, x, q, bmax);
+    k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, x, q, bmax);
     k_heat_start<<<gv, HB, 0, st>>>(n, b, q, dinv, r, z, p, sc + 1, sc + 2);
     k_heat_dot<<<gv, HB, 0, st>>>(n, b, b, sc + 3);
     launches += 4;
@@ -339,7 +364,7 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     int it = 0;
     while (rr > stop && it < maxit) {
       double* s0 = sc + 4 * it;  // {p.q, r.z, r.r, -} of iteration it; the next iteration's at s0 + 4
-      k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, col, val, dg, p, q, s0);
+      k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, p, q, s0);
       k_heat_update<<<gv, HB, 0, st>>>(n, s0, x, r, z, p, q, dinv, s0 + 5, s0 + 6);
       k_heat_dir<<<gv, HB, 0, st>>>(n, s0 + 1, s0 + 5, z, p);
       launches += 3;
