@@ -3,7 +3,8 @@ admissible range, a single pixel worked by hand, a constant image whose
 border distances have a closed form, and on label images: every snap to the
 nearest boundary point (a k-d tree query), every repelled vertex at distance
 c from the boundary (dense sampling of the boundary), every elimination
-within b, and the re-fanned mesh's triangle count and orientation."""
+within b, and the re-fanned mesh's triangle count, orientation and area
+(that of the moved base mesh)."""
 import math
 
 import numpy as np
@@ -126,3 +127,8 @@ def test_steps_on_label_images(name, img, hn, hd):
     p3 = r["xy"][r["tri"]]
     area = (p3[:, 1, 0] - p3[:, 0, 0]) * (p3[:, 2, 1] - p3[:, 0, 1]) - (p3[:, 1, 1] - p3[:, 0, 1]) * (p3[:, 2, 0] - p3[:, 0, 0])
     assert (area > 0).all()
+    # re-fanning two triangles around a point of their common quadrilateral
+    # keeps the area: T covers what the moved base mesh covers
+    q3 = r["xy"][:V][cells]
+    area0 = (q3[:, 1, 0] - q3[:, 0, 0]) * (q3[:, 2, 1] - q3[:, 0, 1]) - (q3[:, 1, 1] - q3[:, 0, 1]) * (q3[:, 2, 0] - q3[:, 0, 0])
+    assert abs(area.sum() - area0.sum()) <= 1e-9 * area0.sum()
