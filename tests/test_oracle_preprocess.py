@@ -108,9 +108,11 @@ def test_steps_on_label_images(name, img, hn, hd):
     kept = r["status"] == 0
     assert (before[rep] < C + 1e-3).all() and (before[kept] >= C - 1e-3).all()
     assert np.abs(after[rep] - C).max() <= 2e-3
-    # Step 3: every elimination point is within b of its edge (after Steps 1-2)
-    for p, u, w in r["eliminations"]:
+    # Step 3: every elimination point is within b of its edge (after Steps 1-2),
+    # and is the inserted vertex of its rank, at the pixel corner
+    for k, (p, u, w) in enumerate(r["eliminations"]):
         q = ppos[np.searchsorted(pid, p)]
+        assert tuple(r["xy"][V + k]) == (p % (img.shape[1] + 1) - 0.5, p // (img.shape[1] + 1) - 0.5)
         a_, b_ = r["xy"][u], r["xy"][w]
         t = np.clip(np.dot(q - a_, b_ - a_) / np.dot(b_ - a_, b_ - a_), 0, 1)
         assert np.linalg.norm(q - (a_ + t * (b_ - a_))) < B
