@@ -1376,9 +1376,9 @@ int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t
   auto it = ctx->meshes.find(mesh);
   if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
   MeshRec* m = it->second;
-  if (stage == 4) {  // cells over the Tier-G limit, for every mesh
+  if (stage == 4) {  // cells over the Tier-G limit, for every mesh (none in a preprocessed one)
     CK(cudaEventSynchronize(m->done));
-    const u32 cnt = m->h_info[4], kept = std::min<u32>(cnt, OVER_CAP);
+    const u32 cnt = m->pre ? 0u : m->h_info[4], kept = std::min<u32>(cnt, OVER_CAP);
     std::vector<u32> ids(kept);
     if (kept) CK(cudaMemcpy(ids.data(), m->over_cells, kept * sizeof(u32), cudaMemcpyDeviceToHost));
     std::sort(ids.begin(), ids.end());

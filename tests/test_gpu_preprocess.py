@@ -129,6 +129,16 @@ def test_angle_and_area_bounds_on_the_preprocessed_mesh():
         assert q["min_area"] > 0.5 * B * C, (q["min_area"], 0.5 * B * C)
 
 
+def test_stage_records_of_a_preprocessed_mesh():
+    # no Tier-G cells (stage 4 is empty); the kept stages of meshing do not exist
+    c = ctx()
+    m = sb.mesh_preprocess(c, synth.disk(), 2, 1)
+    assert len(sb.mesh_stage(c, m, 4)) == 0
+    with pytest.raises(sb.SbmtError):
+        sb.mesh_stage(c, m, 1)
+    sb.mesh_release(c, m)
+
+
 def test_quality_and_projection_accept_the_preprocessed_mesh():
     img = synth.voronoi_labels(size=96, nseeds=12)
     c = ctx()
