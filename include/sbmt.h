@@ -232,7 +232,8 @@ int mesh_destroy(sbmt_ctx* ctx);
  *  stage 4 the cells whose local boundary graph has more vertices than the
  *          per-cell limit of the Tier-G rule (64), the reason for the status
  *          SBMT_ECAPACITY: their ids in increasing order, 1 int64 each, the
- *          first 1024 of them; *n is their total number.
+ *          first 1024 of them; *n is their total number (0 for a mesh made
+ *          by mesh_preprocess, which has no stages 1-3).
  * Writes min(n, cap) records to host_out and the total count to *n. */
 int mesh_stage(sbmt_ctx* ctx, sbmt_mesh mesh, int stage, void* host_out, int64_t cap, int64_t* n);
 
