@@ -83,3 +83,43 @@ def test_gaussian_pulse_peak():
     t = n * dt
     free_space = 100.0 * sigma ** 2 / (sigma ** 2 + 2 * alpha * t)
     assert abs(peaks[-1] - free_space) <= 0.02 * free_space
+
+
+def _wrong_corner_stiffness(xy, tri, nv):
+    import scipy.sparse as sp
+
+    tri = np.asarray(tri)
+    cot = H.cotangents(xy, tri)
+    rows, cols, vals = [], [], []
+    for k in range(3):
+        i, j = tri[:, (k + 1) % 3], tri[:, (k + 2) % 3]
+        w = 0.5 * cot[:, (k + 1) % 3]  # planted: the angle at the wrong corner
+        rows += [i, j, i, j]
+        cols += [j, i, i, j]
+        vals += [-w, -w, w, w]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nv, nv))
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch):
+    img = rect_image()
+    m = oracle.mesh_bitmap(img, 2, 1)
+    xy = m["xy"]
+    sel, free, _ = H.region(m["tri"], m["label"], 1)
+    lin = 3.0 * xy[:, 0] - 2.0 * xy[:, 1] + 5.0
+    # the cotangent of the wrong corner: linear functions are no longer in the kernel
+    K = _wrong_corner_stiffness(xy, m["tri"][sel], len(xy))
+    assert np.abs((K @ lin)[free]).max() > 1.0
+    # half instead of a third of the area: the label area is missed
+    bad_mass = 1.5 * H.lumped_mass(xy, m["tri"][sel], len(xy))
+    assert abs(bad_mass.sum() - (img == 1).sum()) > 100
+    # the stiffness with the wrong sign: the eigenmode grows instead of decaying
+    good = H.stiffness
+    monkeypatch.setattr(H, "stiffness", lambda a, b, c: -good(a, b, c))
+    Lx, Ly, xa, ya = 60.0, 40.0, 9.5, 9.5
+    u0 = np.sin(math.pi * (xy[:, 0] - xa) / Lx) * np.sin(math.pi * (xy[:, 1] - ya) / Ly)
+    try:
+        u, peaks = H.heat(xy, m["tri"], m["label"], 1, 500.0, 0.01, 3, 0.0, 0.0, 1.0, u0=u0)
+        decayed = all(b < a for a, b in zip(peaks, peaks[1:])) and peaks[-1] < u0.max()
+    except Exception:  # an indefinite system may not even solve
+        decayed = False
+    assert not decayed
