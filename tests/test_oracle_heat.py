@@ -123,3 +123,19 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     except Exception:  # an indefinite system may not even solve
         decayed = False
     assert not decayed
+
+
+def test_energy_decreases():
+    # backward Euler with a symmetric positive semi-definite K: the M-norm of
+    # u cannot grow from one step to the next
+    img = synth.voronoi_labels(size=96, nseeds=9)
+    m = oracle.mesh_bitmap(img, 2, 3)
+    L = int(np.bincount(img.ravel()).argmax())
+    sel, free, _ = H.region(m["tri"], m["label"], L)
+    M = H.lumped_mass(m["xy"], m["tri"][sel], len(m["xy"]))
+    u = np.where(free, H.pulse(m["xy"], 40.0, 50.0, 15.0, 100.0), 0.0)
+    e = [float(u @ (M * u))]
+    for _ in range(4):
+        u, _ = H.heat(m["xy"], m["tri"], m["label"], L, 20.0, 0.05, 1, 0.0, 0.0, 1.0, u0=u)
+        e.append(float(u @ (M * u)))
+    assert all(b < a for a, b in zip(e, e[1:])), e
