@@ -59,7 +59,8 @@ enum { SBMT_KEEP_STAGES = 1 }; /* sbmt_params.flags: keep intermediate arrays fo
 
 /* A label image.  width, height in 1..32768; pitch_bytes >= width * dtype
  * bytes; data is a host pointer (on_device = 0) or a device pointer of the
- * context's device (on_device = 1). */
+ * context's device (on_device = 1).  A device u16 image needs an even pitch
+ * and an even address (SBMT_EINVAL otherwise). */
 typedef struct {
   int32_t width, height;
   int64_t pitch_bytes;
@@ -349,7 +350,13 @@ int mesh_profile_read(sbmt_ctx* ctx, int reset, int cap, const char** names, dou
  *              reversed << 31, label below/left | label above/right << 16
  *              (0xFFFF outside the image); records come in no fixed order;
  *  d_count     device u32 receiving the number of segments (it may exceed
- *              capacity, then only `capacity` records are written).
+ *              capacity, then only `capacity` records are written), or
+ *              0xFFFFFFFF when the extraction met an inconsistency (a run
+ *              with no end vertex; never for a valid image).
+ * A u16 image needs an even pitch and an even address (SBMT_EINVAL
+ * otherwise).  Launch errors are read with cudaGetLastError, which also
+ * returns, and clears, an error still pending from the caller's earlier
+ * work on this thread.
  * Working memory is one 8 MiB array of static device storage held by every
  * GPU that loads the library until the process exits; the call allocates
  * and frees nothing.  The first call on a device looks up the array's device

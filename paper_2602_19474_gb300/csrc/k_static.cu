@@ -30,6 +30,10 @@ unsigned int* g_static_ptr[kMaxDevices] = {};
 
 thread_local char g_static_err[256];
 
+__global__ void k_static_count(const u32* nseg, const u32* err, u32* d_count) {
+  if (threadIdx.x == 0) *d_count = *err ? NONE : *nseg;
+}
+
 int static_fail(int code, const char* msg) {
   std::snprintf(g_static_err, sizeof g_static_err, "%s", msg);
   return code;
@@ -45,6 +49,10 @@ extern "C" int sbmt_extract_segments_static(const void* d_image, int32_t width, 
   if (!d_image || !d_segments || !d_count || width < 1 || height < 1 || (dtype != SBMT_U8 && dtype != SBMT_U16) ||
       pitch_bytes < (int64_t)width * dtype)
     return static_fail(SBMT_EINVAL, "bad arguments");
+  // u16 pixels are read with 2-byte loads: an odd pitch or address would be
+  // a misaligned access
+  if (dtype == SBMT_U16 && ((pitch_bytes & 1) || ((uintptr_t)d_image & 1)))
+    return static_fail(SBMT_EINVAL, "a u16 image needs an even pitch and an even address");
   const size_t wpr = ((size_t)width + 1 + 31) / 32, wpc = ((size_t)height + 1 + 31) / 32;
   const size_t need = 4 + wpr * ((size_t)height + 1) + wpc * ((size_t)width + 1);
   if (width > 4096 || height > 4096 || need > kStaticWords)
@@ -78,8 +86,9 @@ extern "C" int sbmt_extract_segments_static(const void* d_image, int32_t width, 
                      (int)wpc, nvtx, st);
   launch_segments((const unsigned char*)d_image, pitch_bytes, dtype, width, height, vrow, (int)wpr, vcol, (int)wpc,
                   (Seg*)d_segments, capacity, nseg, err, st);
-  if (cudaMemcpyAsync(d_count, nseg, sizeof(u32), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return static_fail(SBMT_ECUDA, "copying the count failed");
+  // the count, or NONE when the extraction met an inconsistency (a run
+  // without an end vertex: never for a valid image)
+  k_static_count<<<1, 32, 0, st>>>(nseg, err, d_count);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(SBMT_ECUDA, cudaGetErrorString(e));
   return SBMT_OK;

@@ -471,6 +471,11 @@ int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false)
     return fail(SBMT_EINVAL, "image size %dx%d outside 1..32768", img->width, img->height);
   if (img->dtype != SBMT_U8 && img->dtype != SBMT_U16) return fail(SBMT_EINVAL, "dtype %d", img->dtype);
   if (img->pitch_bytes < (int64_t)img->width * img->dtype) return fail(SBMT_EINVAL, "pitch too small");
+  // the kernels read a device image in place with 2-byte loads for u16
+  // pixels: an odd pitch or base address would be a misaligned access (a
+  // host image is copied into an aligned buffer first)
+  if (img->on_device && img->dtype == SBMT_U16 && ((img->pitch_bytes & 1) || ((uintptr_t)img->data & 1)))
+    return fail(SBMT_EINVAL, "a device u16 image needs an even pitch and an even address");
   if (pre) {
     if (pr->mode != SBMT_PREPROCESS || pr->format != SBMT_EXPLICIT)
       return fail(SBMT_EINVAL, "mesh_preprocess takes mode SBMT_PREPROCESS and the explicit format");

@@ -58,3 +58,29 @@ def test_batch_error_fails_whole_batch():
     assert len(ids) == 3
     for m in ids:
         sb.mesh_release(c, m)
+
+
+def test_noise512_batch_sampled_images_match_oracle():
+    """The 512-bitmap batch (sides 131..2038 px, h = 2) through one
+    mesh_batch call from device-resident images, as the bench runs it; 16
+    meshes spread over the size range, the largest included, against the
+    oracle in full."""
+    import torch
+
+    c = ctx()
+    specs = synth.noise_batch_specs()
+    imgs = [synth.noise_batch_item(sp) for sp in specs]
+    dev = [torch.from_numpy(im).cuda() for im in imgs]
+    ids = sb.mesh_batch(c, dev, 2)
+    order = sorted(range(len(imgs)), key=lambda i: imgs[i].size)
+    pick = sorted(set([order[(k * (len(order) - 1)) // 15] for k in range(16)]))
+    assert order[-1] in pick and len(pick) == 16
+    views = {}
+    for k, m in enumerate(ids):
+        if k in pick:
+            views[k] = _fetch(c, m)
+        else:
+            sb.mesh_release(c, m)
+    for k in pick:
+        o = oracle.mesh_bitmap(imgs[k], 2, 1)
+        assert_same_mesh(views[k], o, 2.0, W=imgs[k].shape[1])

@@ -46,6 +46,27 @@ def test_sizes_past_the_limits_are_rejected():
         sb.mesh_bitmap(c, np.zeros((4, 4), np.uint8), 2, 65)
 
 
+def test_misaligned_device_u16_image_is_rejected():
+    """A device u16 image is read in place with 2-byte loads, so an odd pitch
+    or an odd address is refused before any launch."""
+    import ctypes
+
+    import torch
+
+    c = ctx()
+    lib = sb.load()
+    t = torch.zeros((8, 18), dtype=torch.int16, device="cuda")
+    pr = sb._params(2)
+    out = ctypes.c_uint64()
+    for ptr, pitch in ((t.data_ptr(), 33), (t.data_ptr() + 1, 36)):
+        im = sb.sbmt_image(16, 8, pitch, 2, ptr, 1)
+        assert lib.mesh_bitmap(c, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)) == sb.SBMT_EINVAL
+    # the context stays usable
+    m = sb.mesh_bitmap(c, t, 2)
+    assert sb.mesh_query(c, m, -1).n_triangles > 0
+    sb.mesh_release(c, m)
+
+
 def _device_window_triangles(t, lo, hi, chunk=1 << 26):
     """Triangles of a device-resident mesh with every vertex inside the box
     [lo, hi]: their vertex coordinates (n, 3, 2), labels and codes on the host."""

@@ -137,19 +137,18 @@ def test_steps_on_label_images(name, img, hn, hd):
 
 
 def test_planted_mistakes_fail_the_pins(monkeypatch):
+    """Each planted mistake makes a committed pin fail when that pin runs
+    under it."""
     # ties going to the larger id: the hand-worked pixel snaps elsewhere
     def nearest_larger(vals, ids):
         m = vals.min(axis=1, keepdims=True)
         cand = np.where(vals == m, ids[None, :], -1)
         return np.argmax(cand, axis=1)
 
-    img = np.ones((1, 1), np.uint8)
     good = P._nearest
     monkeypatch.setattr(P, "_nearest", nearest_larger)
-    r = P.preprocess(img, 2, 1, *TRIPLET)
-    xy0, _ = oracle.base_mesh(1, 1, 2, 1)
-    k = int(np.nonzero((xy0 == [0.0, 0.0]).all(1))[0][0])
-    assert r["snap"][k] != 0
+    with pytest.raises(AssertionError):
+        test_single_pixel_by_hand()
     monkeypatch.setattr(P, "_nearest", good)
     # repelled vertices moved the wrong way: the closed-form border positions fail
     real = P.region_one
@@ -161,22 +160,5 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
         return out, status, snap
 
     monkeypatch.setattr(P, "region_one", wrong_way)
-    H_, W_ = 9, 13
-    img = np.full((H_, W_), 3, np.uint8)
-    _, _, C = P.thresholds_px(*TRIPLET, h=2.0)
-    r = P.preprocess(img, 2, 1, *TRIPLET)
-    xy0, _ = oracle.base_mesh(W_, H_, 2, 1)
-    lo, hi = np.array([-0.5, -0.5]), np.array([W_ - 0.5, H_ - 0.5])
-    bad = 0
-    for kk in np.nonzero(r["status"] == 2)[0]:
-        v = xy0[kk]
-        q = np.clip(v, lo, hi)
-        inside = (v > lo).all() and (v < hi).all()
-        if inside:
-            ds = np.array([v[0] - lo[0], hi[0] - v[0], v[1] - lo[1], hi[1] - v[1]])
-            s = int(np.argmin(ds))
-            q = v.copy()
-            q[s // 2] = lo[s // 2] if s % 2 == 0 else hi[s // 2]
-        d = np.linalg.norm(v - q)
-        bad += not np.allclose(r["xy"][kk], q + C * (v - q) / d, rtol=0, atol=1e-12)
-    assert bad > 0
+    with pytest.raises(AssertionError):
+        test_constant_image_border_in_closed_form()

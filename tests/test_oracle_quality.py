@@ -60,3 +60,31 @@ def test_constant_image_lattice():
     assert np.allclose(ar[uncut_tris], 2 / S3, rtol=1e-12)
     # the in-image triangles tile the image rectangle exactly
     assert abs(area[m["label"] != 0xFFFF].sum() - 160 * 160) < 1e-6
+
+
+def test_area_mean_and_population_variance_closed_form():
+    # right triangles of areas 1, 2 and 6: mean 3, population variance
+    # ((1-3)^2 + (2-3)^2 + (6-3)^2) / 3 = 14/3 (the sample variance would be 7)
+    pts = [(0, 0), (2, 0), (0, 1), (10, 0), (12, 0), (10, 2), (20, 0), (23, 0), (20, 4)]
+    r = q_of(pts, [(0, 1, 2), (3, 4, 5), (6, 7, 8)])
+    assert abs(r["area_mean"] - 3.0) < 1e-15
+    assert abs(r["area_var"] - 14.0 / 3.0) < 1e-14
+    assert abs(r["min_area"] - 1.0) < 1e-15
+
+
+def test_area_mean_over_every_triangle_of_a_mesh():
+    # the patches tile their cells, so the areas of all T triangles (those
+    # outside the image included) add up to n_cells equilateral cells of
+    # area sqrt(3) h^2 / 4
+    from paper_2602_19474_gb300 import synth
+
+    img = synth.noise_batch(n=2, lo=60, hi=90, first=2)[1]
+    for hn in (2, 4):
+        m = oracle.mesh_bitmap(img, hn, 1)
+        r = Q.quality(m["xy"], m["tri"])
+        cell = S3 * hn * hn / 4.0
+        assert abs(r["area_mean"] * r["triangles"] - m["n_cells"] * cell) < 1e-9 * m["n_cells"] * cell
+        # variance from the closed-form second moment of the same areas
+        _, area, _, _ = Q.triangle_measures(m["xy"], m["tri"])
+        mean = m["n_cells"] * cell / len(area)
+        assert abs(r["area_var"] - (np.sum(area * area) / len(area) - mean * mean)) < 1e-9 * cell * cell

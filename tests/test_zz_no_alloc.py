@@ -3,14 +3,14 @@ allocate device memory (for example a host application that owns the whole
 device budget, or a latency-critical path where an allocation could block or
 fail).  Its working memory is a static device array, so this test calls it
 twice in a row on different images and compares each result with the
-segments mesh_bitmap extracts for the same image."""
+boundary segments of the CPU oracle for the same image."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2602_19474_gb300 as sb
-from gpu_util import gpu_mesh
 from paper_2602_19474_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -52,14 +52,39 @@ def _canon(a):
     return a[np.lexsort(a.T[::-1])]
 
 
-def test_static_extraction_matches_mesh_bitmap_on_consecutive_calls():
+def _oracle_segments(img):
+    """The oracle's segments as (x, y, dir, len, label left/below, label
+    right/above, reversed), the outside label written as 0xFFFF."""
+    seg = oracle.mesh_bitmap(img, 2)["seg"][:, :7].astype(np.int64)
+    lab = seg[:, 4:6]
+    lab[lab == 0x10000] = 0xFFFF
+    return seg
+
+
+def test_static_extraction_matches_the_oracle_on_consecutive_calls():
     lib = _lib()
-    images = [synth.voronoi_labels(size=640, nseeds=90, nlabels=7), synth.disk()]
+    images = [synth.voronoi_labels(size=640, nseeds=90, nlabels=7), synth.disk(),
+              synth.noise_batch(n=3, lo=300, hi=900, first=3)[2]]
     for img in images:
         got = _static_segments(lib, img)
-        ref = gpu_mesh(img, 2, 1, stages=True)["seg"][:, :7]
+        ref = _oracle_segments(img)
         assert len(got) == len(ref)
         assert np.array_equal(_canon(got), _canon(ref))
+
+
+def test_static_extraction_rejects_a_misaligned_u16_image():
+    import torch
+
+    lib = _lib()
+    t = torch.zeros((8, 18), dtype=torch.int16, device="cuda")
+    out = torch.empty((16, 4), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # odd pitch: rejected before any launch
+    rc = lib.sbmt_extract_segments_static(t.data_ptr(), 16, 8, 33, 2, out.data_ptr(), 16, cnt.data_ptr(), None)
+    assert rc == sb.SBMT_EINVAL
+    # odd address: rejected before any launch
+    rc = lib.sbmt_extract_segments_static(t.data_ptr() + 1, 16, 8, 36, 2, out.data_ptr(), 16, cnt.data_ptr(), None)
+    assert rc == sb.SBMT_EINVAL
 
 
 def test_static_extraction_rejects_images_above_its_limit():
