@@ -631,29 +631,29 @@ def our_arm(args, rank: int, world: int, dist):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    print(json.dumps(out), flush=True)
     sb.mesh_destroy(ctx)
+    if world == 1 and not args.no_extras:
+        # the batched and serving forms on the same GPU, measured by the same run
+        out["batch"] = measure_batch(sb, torch, dev, local, None, 1, "noise512", 5, 3)
+        out["serving"] = measure_serving(sb, torch, dev, local, [1000.0, 5000.0, 20000.0], 300, 50,
+                                         compare_rates=[20000.0])
+    print(json.dumps(out), flush=True)
 
 
-def batch_arm(args, rank: int, world: int, dist):
+def measure_batch(sb, torch, dev, local, dist, world, name: str, steps: int, warmup: int, autotune: bool = True,
+                  cpu_sample: int = 0) -> dict:
     """The batched workload: every step meshes the whole batch with one
-    mesh_batch call (images on several streams at once); a loop of
-    mesh_bitmap calls over the same device-resident images is timed beside
-    it, and the two must give the same meshes."""
-    import torch
-
-    import paper_2602_19474_gb300 as sb
-
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    b = BATCH_WORKLOADS[args.workload]
+    mesh_batch call (every stage one launch over all images, the emission
+    phase as the tuner chose); a loop of mesh_bitmap calls over the same
+    device-resident images is timed beside it, and the two must give the
+    same meshes."""
+    b = BATCH_WORKLOADS[name]
     hn, hd = b["h"]
-    imgs = load_batch(args.workload)
+    imgs = load_batch(name)
     # one stream for torch and the context, so that events recorded on it
-    # bracket the library's work (the legacy default stream has handle 0, for
-    # which the context would create a stream of its own)
+    # bracket the library's work
     st = torch.cuda.Stream(dev)
+    prev = torch.cuda.current_stream(dev)
     torch.cuda.set_stream(st)
     ctx = sb.mesh_create(local, 0, st.cuda_stream)
     dimgs = [torch.from_numpy(i).to(dev) for i in imgs]
@@ -686,48 +686,48 @@ def batch_arm(args, rank: int, world: int, dist):
             sb.mesh_release(ctx, m)
         return tris, d
 
-    def timed(fn, steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier_sync()
-        e0.record(st)
-        for _ in range(steps):
-            tris = fn()[0]
-        e1.record(st)
-        torch.cuda.synchronize()
-        return max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev), tris
-
     def barrier_sync():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier_sync()
+        gc.disable()
+        e0.record(st)
+        for _ in range(n):
+            tris = fn()[0]
+        e1.record(st)
+        torch.cuda.synchronize()
+        gc.enable()
+        return max_over_ranks(e0.elapsed_time(e1) / n, dist, dev), tris
+
     _, d_batch = batch_step(check=True)
     _, d_loop = loop_step(check=True)
     identical = d_batch == d_loop
-    for _ in range(max(0, args.warmup - 1)):
+    if autotune:
+        sb.mesh_autotune(ctx, dimgs, hn, hd, repeats=1)
+    tuning = sb.mesh_tuning(ctx, dimgs, hn, hd)
+    for _ in range(max(0, warmup - 1)):
         batch_step()
     clk = ClockSampler(local)
     clk.start()
-    ms, (T, V) = timed(batch_step, args.steps)
+    ms, (T, V) = timed(batch_step, steps)
     clocks = clk.stop()
-    loop_steps = max(1, min(3, args.steps))
-    ms_loop, _ = timed(loop_step, loop_steps)
-    if rank != 0:
-        sb.mesh_destroy(ctx)
-        return
+    ms_loop, _ = timed(loop_step, max(1, min(3, steps)))
+    sb.mesh_destroy(ctx)
+    torch.cuda.set_stream(prev)
     peak, peak_kind = measured_peak()
     path_bytes = float(px) + 16.0 * T + 16.0 * V
-    ntri_cpu, nimg_cpu, t_cpu, cores = oracle_batch_sample(imgs, (hn, hd), 128)
     out = {
         "metric": "output triangles/sec", "value": job_rate(world, T, ms), "unit": "triangles/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + b["desc"], "images": len(imgs), "pixels": px,
+        "ms_per_step": ms, "bitmaps_per_s": world * len(imgs) / (ms * 1e-3),
+        "config": {"workload": name + ": " + b["desc"], "images": len(imgs), "pixels": px,
                    "h": hn / hd, "triangles_per_step": T, "vertices_per_step": V,
                    "l2": "inputs and outputs larger than L2 (%d MB of images, ~%d MB of meshes per step)"
-                         % (px >> 20, int(24 * T) >> 20),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "bitmaps_per_s": world * len(imgs) / (ms * 1e-3),
+                         % (px >> 20, int(24 * T) >> 20)},
+        "tuning": tuning,
         "loop": {"ms_per_step": ms_loop, "bitmaps_per_s": world * len(imgs) / (ms_loop * 1e-3),
                  "what": "the same images, one mesh_bitmap call each on one stream"},
         "batch_over_loop": ms_loop / ms,
@@ -735,40 +735,83 @@ def batch_arm(args, rank: int, world: int, dist):
         "roofline_path": {"achieved": path_bytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                           "frac": path_bytes / (ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                           "algorithmic_bytes_per_step": path_bytes},
-        "cpu_baseline": {"value": ntri_cpu / t_cpu, "unit": "triangles/s", "cores": cores, "kind": "oracle",
-                         "bitmaps_per_s": nimg_cpu / t_cpu,
-                         "sample": "the first %d bitmaps of the batch, one per task over %d host cores"
-                                   % (nimg_cpu, cores)},
         "clocks": clocks,
     }
-    print(json.dumps(out), flush=True)
-    sb.mesh_destroy(ctx)
+    if cpu_sample:
+        ntri_cpu, nimg_cpu, t_cpu, cores = oracle_batch_sample(imgs, (hn, hd), cpu_sample)
+        out["cpu_baseline"] = {"value": ntri_cpu / t_cpu, "unit": "triangles/s", "cores": cores, "kind": "oracle",
+                               "bitmaps_per_s": nimg_cpu / t_cpu,
+                               "sample": "the first %d bitmaps of the batch, one per task over %d host cores"
+                                         % (nimg_cpu, cores)}
+    return out
 
 
-def serving_arm(args, rank: int, world: int):
-    """Open-loop serving: Poisson arrivals at each rate, FIFO over worker
-    threads (one context and stream each); latency = mesh ready - arrival."""
-    import queue
-
+def batch_arm(args, rank: int, world: int, dist):
     import torch
 
     import paper_2602_19474_gb300 as sb
 
-    if rank != 0:
-        return
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    r = measure_batch(sb, torch, dev, local, dist, world, args.workload, args.steps, args.warmup,
+                      cpu_sample=128 if rank == 0 else 0)
+    if rank != 0:
+        return
+    out = {
+        "metric": r["metric"], "value": r["value"], "unit": r["unit"], "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(r["config"], parallelism="replicas" if world > 1 else "single GPU"),
+    }
+    out.update({k: v for k, v in r.items() if k not in out})
+    print(json.dumps(out), flush=True)
+
+
+def measure_serving(sb, torch, dev, local, rates, requests: int, warm: int, workers: int = 2,
+                    compare_rates=()) -> dict:
+    """Open-loop serving through the library's request loop (server_*):
+    Poisson arrivals at each rate from one submitting thread, requests drawn
+    from a pool of device-resident bitmaps, each with its own h; latency =
+    mesh found ready - scheduled arrival.  At compare_rates the same stream
+    of requests is also served the plain way: `workers` host threads, each
+    with its own context, one mesh_bitmap call per request."""
     pool = load_serving_pool()
     dimgs = [(torch.from_numpy(img).to(dev), h) for img, h in pool]
     torch.cuda.synchronize()
-    rates = [float(r) for r in args.rates.split(",")]
     rng = np.random.default_rng(260219474 + 5)
-    ctxs = [sb.mesh_create(local) for _ in range(args.workers)]
 
-    def serve(rate: float, n: int) -> list:
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
-        picks = rng.integers(0, len(dimgs), n)
+    def plan(rate, n):
+        return np.cumsum(rng.exponential(1.0 / rate, n)), rng.integers(0, len(dimgs), n)
+
+    def served(srv, rate, n):
+        arrivals, picks = plan(rate, n)
+        ids, late = [None] * n, [0.0] * n
+        t0 = time.perf_counter() + 0.005
+        for i in range(n):
+            while True:
+                d = t0 + arrivals[i] - time.perf_counter()
+                if d <= 0:
+                    break
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            late[i] = (time.perf_counter() - (t0 + arrivals[i])) * 1e3
+            img, h = dimgs[picks[i]]
+            ids[i] = sb.server_submit(srv, img, h)
+        lat, sizes = [], []
+        for i, rid in enumerate(ids):
+            _, info = sb.server_wait(srv, rid, -1)
+            lat.append(info["total_ms"] + late[i])
+            sizes.append(info["batch_size"])
+            sb.server_release(srv, rid)
+        span = max(arrivals[-1], 1e-9) + max(lat) * 1e-3
+        return lat, sizes, n / span
+
+    def plain(rate, n):
+        import queue
+
+        arrivals, picks = plan(rate, n)
+        ctxs = [sb.mesh_create(local) for _ in range(workers)]
         q = queue.Queue()
         for i in range(n):
             q.put(i)
@@ -788,7 +831,7 @@ def serving_arm(args, rank: int, world: int):
                 img, h = dimgs[picks[i]]
                 m = sb.mesh_bitmap(c, img, h, 1)
                 sb.mesh_query(c, m, -1)
-                lat[i] = time.perf_counter() - (t0 + arrivals[i])
+                lat[i] = (time.perf_counter() - (t0 + arrivals[i])) * 1e3
                 sb.mesh_release(c, m)
 
         ths = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
@@ -796,26 +839,55 @@ def serving_arm(args, rank: int, world: int):
             t.start()
         for t in ths:
             t.join()
-        return lat
+        for c in ctxs:
+            sb.mesh_destroy(c)
+        return lat[warm:]
 
-    serve(200.0, max(8, args.warmup * 8))  # warm the contexts (table caches, scratch arenas)
+    srv = sb.server_create(local)
+    served(srv, 200.0, 64)  # warm the workers (table caches, scratch arenas)
     res = []
     for r in rates:
-        lat = serve(r, args.requests + args.warm_requests)[args.warm_requests:]
-        ms = np.array(lat) * 1e3
+        lat, sizes, thr = served(srv, r, requests + warm)
+        ms = np.array(lat[warm:])
         res.append({"rate_per_s": r, "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-                    "mean_ms": float(ms.mean()), "requests": len(ms)})
-    for c in ctxs:
-        sb.mesh_destroy(c)
-    out = {
-        "metric": "p99 latency", "value": res[-1]["p99_ms"], "unit": "ms", "n_gpus": 1,
-        "higher_is_better": False, "data": "synthetic",
+                    "mean_ms": float(ms.mean()), "requests": len(ms), "throughput_per_s": thr,
+                    "mean_batch": float(np.mean(sizes[warm:]))})
+    stats = sb.server_stats(srv)
+    sb.server_destroy(srv)
+    cmp = []
+    for r in compare_rates:
+        ms = np.array(plain(r, requests + warm))
+        cmp.append({"rate_per_s": r, "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                    "requests": len(ms)})
+    return {"latency": res, "per_request_launches": cmp, "server": {
+        "batches": stats["batches"], "completed": stats["completed"], "failed": stats["failed"],
+        "peak_reserved_bytes": stats["peak_reserved_bytes"], "budget_bytes": stats["budget_bytes"]},
         "config": {"workload": "serving: pool of 128 square u8 noise bitmaps, side log-uniform in [256, 4096], "
-                               "h from {2, 4, 8}, Poisson arrivals, FIFO over %d worker threads" % args.workers,
-                   "rates_per_s": rates, "requests_per_rate": args.requests,
-                   "warmup_requests_per_rate": args.warm_requests},
-        "latency": res,
+                               "h from {2, 4, 8}, device-resident, Poisson arrivals; library request loop "
+                               "(admission by device memory, continuous batching over 2 workers)",
+                   "rates_per_s": list(rates), "requests_per_rate": requests, "warmup_requests_per_rate": warm,
+                   "per_request_launches": "%d host threads, one context each, one mesh_bitmap per request"
+                                           % workers}}
+
+
+def serving_arm(args, rank: int, world: int):
+    import torch
+
+    import paper_2602_19474_gb300 as sb
+
+    if rank != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rates = [float(r) for r in args.rates.split(",")]
+    r = measure_serving(sb, torch, dev, local, rates, args.requests, args.warm_requests, args.workers,
+                        compare_rates=[rates[-1]])
+    out = {
+        "metric": "p99 latency", "value": r["latency"][-1]["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "data": "synthetic", "config": r["config"],
     }
+    out.update({k: v for k, v in r.items() if k != "config"})
     print(json.dumps(out), flush=True)
 
 
@@ -831,7 +903,10 @@ def main():
                     help="serving: arrival rates per second")
     ap.add_argument("--requests", type=int, default=400, help="serving: measured requests per rate")
     ap.add_argument("--warm-requests", type=int, default=50, help="serving: unmeasured requests per rate")
-    ap.add_argument("--workers", type=int, default=4, help="serving: worker threads (one context each)")
+    ap.add_argument("--workers", type=int, default=4,
+                    help="serving: host threads of the per-request comparison (one context each)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: leave out the batch and serving measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -47,7 +47,8 @@ extern "C" {
 #define SBMT_EPROTO (-6)    /* requested mode is not available (SBMT_PREPROCESS in mesh_bitmap) */
 #define SBMT_ECUDA (-7)     /* a CUDA call failed (message in sbmt_last_error) */
 #define SBMT_EINTERNAL (-8) /* a device-side consistency check failed */
-#define SBMT_ENOENT (-9)    /* unknown mesh handle */
+#define SBMT_ENOENT (-9)    /* unknown mesh handle or request */
+#define SBMT_ECANCELED (-10) /* serving: the request was cancelled */
 
 typedef struct sbmt_ctx sbmt_ctx;
 typedef uint64_t sbmt_mesh;
@@ -55,7 +56,13 @@ typedef uint64_t sbmt_mesh;
 enum { SBMT_U8 = 1, SBMT_U16 = 2, SBMT_F32 = 4 }; /* SBMT_F32: fields for mesh_project only */
 enum { SBMT_PLAIN = 0, SBMT_PREPROCESS = 1 };
 enum { SBMT_EXPLICIT = 0, SBMT_COMPACT = 1 };
-enum { SBMT_KEEP_STAGES = 1 }; /* sbmt_params.flags: keep intermediate arrays for mesh_stage */
+/* sbmt_params.flags: SBMT_KEEP_STAGES keeps intermediate arrays for
+ * mesh_stage; SBMT_DEBUG_STALL_SCAN is a test of the bound on device waits:
+ * one tile of the counting scan withholds its sums, so that the wait of the
+ * tile after it runs out (about one second) and the call returns
+ * SBMT_ETIMEDOUT, leaving the context usable (for an image with at least
+ * 4096 boundary segments; set on the first image of a batch). */
+enum { SBMT_KEEP_STAGES = 1, SBMT_DEBUG_STALL_SCAN = 2 };
 
 /* A label image.  width, height in 1..32768; pitch_bytes >= width * dtype
  * bytes; data is a host pointer (on_device = 0) or a device pointer of the
@@ -145,9 +152,11 @@ typedef struct {
 int mesh_create(sbmt_ctx** ctx, int device, size_t pool_bytes, void* cuda_stream);
 
 /* Mesh one image (Sec. 3.3 grid, Alg. 1 classification, Alg. 2 lookup).
- * Enqueues the work on the context's stream and returns a handle; the
- * call synchronises with the device twice to size its buffers.  The mesh
- * is complete when mesh_query returns SBMT_OK. */
+ * Enqueues the work on the context's stream and returns a handle; the call
+ * synchronises with the device once, after counting the image's boundary
+ * segments and their grid crossings, to size its buffers.  The mesh is
+ * complete when mesh_query returns SBMT_OK.  SBMT_ETIMEDOUT: a bounded
+ * device wait ran out (see SBMT_DEBUG_STALL_SCAN). */
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out);
 
 /* Geometric preprocessing of the base mesh (Alg. 3, Steps 1-3): the mesh T
@@ -203,10 +212,51 @@ typedef struct {
 } sbmt_pre_info;
 int mesh_preprocess_info(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_pre_info* out);
 
-/* Mesh n images; params points to n parameter sets, or to one shared by
- * all (n_params = 1).  out receives n handles. */
+/* Mesh n images of any sizes together (the batched form of the data-parallel
+ * path, Sec. 3.5's corollary: every cell's patch is independent); params
+ * points to n parameter sets, or to one shared by all (n_params = 1).  out
+ * receives n handles.  Every stage runs as one launch over all n images:
+ * a counting phase, one host synchronisation for the whole batch, and an
+ * emission phase whose variable-size stages (cut cells, Tier-G cells, the
+ * registry's large buckets) are persistent kernels over batch-wide work
+ * queues, the Tier-G cells of all images ordered by size.  The emission
+ * phase runs as a CUDA graph when the tuning of the batch's size class says
+ * so (mesh_autotune).  Each mesh is identical to the one mesh_bitmap makes
+ * for its image.  A failing image fails the whole batch (no handles).  The
+ * meshes of a batch share one device block, freed with the last of them. */
 int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
                sbmt_mesh* out);
+
+/* Tune the batched path for the size class of this batch (image count and
+ * total pixels, each log2, and the largest h, log2 rounded): mesh the batch
+ * repeatedly (1 + repeats runs per candidate, meshes released) under
+ * candidate launch parameters -- persistent blocks per SM of the cut-cell
+ * kernel (4..16) and of the Tier-G kernel (8..32), Tier-G on side streams or
+ * not, the emission phase as a CUDA graph or not -- by coordinate descent
+ * from the defaults, and keep the fastest for the class, in the context and
+ * appended to the tuning file (environment SBMT_TUNE_FILE, else
+ * $HOME/.cache/sbmt_tune.txt) that every context reads on its first batch.
+ * No counterpart in the paper (which has no parallel implementation). */
+int mesh_autotune(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                  int repeats);
+/* The launch parameters mesh_batch would use for this batch: cut-cell
+ * blocks per SM, Tier-G blocks per SM, fork (0/1), graph (0/1). */
+int mesh_tuning(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                int32_t* out4);
+/* Set, for this context only, the launch parameters of this batch's size
+ * class (the four values of mesh_tuning; SBMT_EINVAL outside cut-cell
+ * blocks 1..16, Tier-G blocks 1..32, fork and graph 0/1). */
+int mesh_set_tuning(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                    const int32_t* in4);
+
+/* Check an image and its parameters as mesh_bitmap does, with no device
+ * work: SBMT_OK, SBMT_EINVAL or SBMT_EPROTO. */
+int mesh_check(const sbmt_image* img, const sbmt_params* params);
+
+/* The device bytes a mesh holds until it is released (its outputs, and its
+ * kept stages with SBMT_KEEP_STAGES); known as soon as mesh_bitmap or
+ * mesh_batch returns. */
+int mesh_footprint(sbmt_ctx* ctx, sbmt_mesh mesh, size_t* bytes);
 
 /* Wait up to wait_ms milliseconds (0 = poll, < 0 = no limit) for a mesh and
  * fill *out.  Returns SBMT_EPENDING / SBMT_ETIMEDOUT while unfinished, or
@@ -368,6 +418,77 @@ int sbmt_extract_segments_static(const void* d_image, int32_t width, int32_t hei
                                  int32_t dtype, void* d_segments, uint32_t capacity, uint32_t* d_count,
                                  void* cuda_stream);
 const char* sbmt_static_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop for meshing requests of different sizes (no
+ * counterpart in the paper, whose prototype meshes one image at a time; the
+ * independence of every cell's patch, Sec. 3.5's corollary, is what makes a
+ * request's mesh the same alone and among others).
+ *
+ * server_submit queues a request and returns at once.  Requests are admitted
+ * in arrival order by device memory: before its boundary is counted a
+ * request reserves an upper bound of the device bytes meshing it can hold,
+ * computed from its width, height and h alone (every pixel edge a boundary
+ * edge crossing as many grid edges as its length allows); once its batch's
+ * counting phase is done the reservation becomes the exact size of its mesh
+ * (mesh_footprint), held until server_release.  A request is admitted when
+ * the reservations stay within the budget and its bound fits the device's
+ * free memory; one whose bound exceeds the budget fails with SBMT_ENOMEM.
+ * Admitted requests are meshed in batches (mesh_batch: every stage one
+ * launch over the batch).  Continuous batching: each worker (a context with
+ * its own stream and host thread) takes the next batch as soon as its
+ * previous batch's counting phase is done, so requests that arrive while
+ * others are on the GPU join the next launch, and the workers' batches
+ * overlap on the device.  Bitmaps passed as device pointers (which must stay
+ * valid until the request is done) and every finished mesh stay on the
+ * device.  A request's mesh is identical to mesh_bitmap's for its image,
+ * whatever it was batched with.
+ * ------------------------------------------------------------------------ */
+typedef struct sbmt_server sbmt_server;
+typedef struct {
+  size_t hbm_budget;  /* device bytes reservations may hold; 0 = 90% of the free memory at creation */
+  int32_t max_batch;  /* requests per batch (0 = 64) */
+  int32_t workers;    /* contexts taking batches in turn (0 = 2) */
+  int32_t oom_every;  /* fault injection on the host: every k-th admission check sees no free memory (0 = off) */
+} sbmt_server_config;
+typedef struct {
+  int32_t status;     /* SBMT_OK, or the request's error (SBMT_ECANCELED, SBMT_ENOMEM, ...) */
+  int32_t batch_size; /* requests meshed in the same batch */
+  double queued_ms;   /* submit to admission into a batch */
+  double total_ms;    /* submit to the mesh found finished by the server */
+} sbmt_request_info;
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, batches, queued;
+  int64_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+} sbmt_server_stats;
+
+/* The reservation of a request before its boundary is counted: an upper
+ * bound of the device bytes meshing this image can hold (its outputs and
+ * the path's working memory), from its width, height, dtype and h alone --
+ * every pixel edge a boundary edge, every corner a boundary vertex, and
+ * every boundary edge crossing as many grid edges as its length allows (a
+ * unit pixel edge meets at most 3 + 2.31/h of them). */
+int mesh_bound(const sbmt_image* img, const sbmt_params* params, size_t* bytes);
+/* Start a server on a device (cfg may be NULL for the defaults). */
+int server_create(sbmt_server** srv, int device, const sbmt_server_config* cfg);
+/* Queue a request (checked as by mesh_check first: SBMT_EINVAL or
+ * SBMT_EPROTO and no request for a malformed one).  A host image is copied
+ * before the call returns. */
+int server_submit(sbmt_server* srv, const sbmt_image* img, const sbmt_params* params, uint64_t* request);
+/* Wait up to wait_ms milliseconds (0 = poll, < 0 = no limit) for a request:
+ * SBMT_EPENDING / SBMT_ETIMEDOUT while unfinished, else its status; view
+ * (device pointers, valid until server_release) and info may be NULL. */
+int server_wait(sbmt_server* srv, uint64_t request, int wait_ms, sbmt_mesh_view* view, sbmt_request_info* info);
+/* Cancel a request: a queued one finishes at once with SBMT_ECANCELED; a
+ * running one is released (and forgotten) when its batch is done. */
+int server_cancel(sbmt_server* srv, uint64_t request);
+/* Free a finished request's mesh and forget the request. */
+int server_release(sbmt_server* srv, uint64_t request);
+int server_stats(sbmt_server* srv, sbmt_server_stats* out);
+/* Stop the server: queued requests are dropped, running ones finished, and
+ * every mesh freed. */
+int server_destroy(sbmt_server* srv);
+const char* sbmt_server_last_error(void);
 
 /* Message of the last failing call on this thread (never NULL). */
 const char* sbmt_last_error(void);

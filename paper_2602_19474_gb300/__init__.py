@@ -30,14 +30,18 @@ SBMT_EPROTO = -6
 SBMT_ECUDA = -7
 SBMT_EINTERNAL = -8
 SBMT_ENOENT = -9
+SBMT_ECANCELED = -10
 SBMT_U8, SBMT_U16, SBMT_F32 = 1, 2, 4
 SBMT_PLAIN, SBMT_PREPROCESS = 0, 1
 SBMT_EXPLICIT, SBMT_COMPACT = 0, 1
 SBMT_KEEP_STAGES = 1
+SBMT_DEBUG_STALL_SCAN = 2
 
-EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage",
-           "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
-           "mesh_preprocess_info", "mesh_heat", "sbmt_last_error")
+EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_autotune", "mesh_tuning", "mesh_set_tuning",
+           "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project",
+           "mesh_preprocess", "mesh_preprocess_info", "mesh_heat", "mesh_check", "mesh_footprint", "mesh_bound", "server_create",
+           "server_submit", "server_wait", "server_cancel", "server_release", "server_stats", "server_destroy",
+           "sbmt_last_error", "sbmt_server_last_error")
 
 
 class sbmt_image(ctypes.Structure):
@@ -85,6 +89,23 @@ class sbmt_heat_params(ctypes.Structure):
                 ("max_iterations", ctypes.c_int32)]
 
 
+class sbmt_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("workers", ctypes.c_int32),
+                ("oom_every", ctypes.c_int32)]
+
+
+class sbmt_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("queued_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class sbmt_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("batches", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("reserved_bytes", ctypes.c_int64), ("peak_reserved_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64)]
+
+
 class SbmtError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("sbmt error %d: %s" % (code, msg))
@@ -113,6 +134,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_batch.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_int, ctypes.POINTER(sbmt_params),
                                ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mesh_autotune.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_int, ctypes.POINTER(sbmt_params),
+                                  ctypes.c_int, ctypes.c_int]
+    lib.mesh_tuning.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_int, ctypes.POINTER(sbmt_params),
+                                ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+    lib.mesh_set_tuning.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_int, ctypes.POINTER(sbmt_params),
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
     lib.mesh_query.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(sbmt_mesh_view)]
     lib.mesh_release.argtypes = [vp, ctypes.c_uint64]
     lib.mesh_destroy.argtypes = [vp]
@@ -127,8 +154,25 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_preprocess_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_pre_info)]
     lib.mesh_heat.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_heat_params), vp, vp, vp]
+    lib.mesh_check.argtypes = [ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params)]
+    lib.mesh_footprint.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mesh_bound.argtypes = [ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params), ctypes.POINTER(ctypes.c_size_t)]
+    lib.server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(sbmt_server_config)]
+    lib.server_submit.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params),
+                                  ctypes.POINTER(ctypes.c_uint64)]
+    lib.server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(sbmt_mesh_view),
+                                ctypes.POINTER(sbmt_request_info)]
+    lib.server_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.server_release.argtypes = [vp, ctypes.c_uint64]
+    lib.server_stats.argtypes = [vp, ctypes.POINTER(sbmt_server_stats)]
+    lib.server_destroy.argtypes = [vp]
+    for f in ("mesh_check", "mesh_footprint", "mesh_bound", "server_create", "server_submit", "server_wait", "server_cancel",
+              "server_release", "server_stats", "server_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.sbmt_server_last_error.restype = ctypes.c_char_p
     lib.sbmt_last_error.restype = ctypes.c_char_p
-    for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_query", "mesh_release", "mesh_destroy",
+    for f in ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_autotune", "mesh_tuning", "mesh_set_tuning",
+              "mesh_query", "mesh_release", "mesh_destroy",
               "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project", "mesh_preprocess",
               "mesh_preprocess_info", "mesh_heat"):
         getattr(lib, f).restype = ctypes.c_int
@@ -178,9 +222,10 @@ def mesh_create(device: int = 0, pool_bytes: int = 0, stream: int | None = None)
 
 
 def mesh_bitmap(ctx: int, img, h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0,
-                keep_stages: bool = False, mode: int = SBMT_PLAIN, format: int = SBMT_EXPLICIT) -> int:
+                keep_stages: bool = False, mode: int = SBMT_PLAIN, format: int = SBMT_EXPLICIT, flags: int = 0) -> int:
     im, keep = _image(img)
     pr = _params(h_num, h_den, origin2x, origin2y, keep_stages, mode, format)
+    pr.flags |= flags
     out = ctypes.c_uint64()
     _check(load().mesh_bitmap(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
     del keep
@@ -224,7 +269,7 @@ def pre_info_numpy(info: sbmt_pre_info) -> dict:
     }
 
 
-def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False, format: int = SBMT_EXPLICIT) -> list[int]:
+def _batch_args(imgs, h_num, h_den, keep_stages=False, format=SBMT_EXPLICIT, flags=0):
     n = len(imgs)
     ims, keeps = zip(*[_image(i) for i in imgs]) if n else ((), ())
     arr = (sbmt_image * max(n, 1))(*ims)
@@ -232,10 +277,44 @@ def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False, format
     hd = list(h_den) if isinstance(h_den, (list, tuple, np.ndarray)) else [h_den] * len(hn)
     prs = (sbmt_params * len(hn))(*[_params(int(a), int(b), keep_stages=keep_stages, format=format)
                                        for a, b in zip(hn, hd)])
+    for p in prs:
+        p.flags |= flags
+    return n, arr, prs, len(hn), keeps
+
+
+def mesh_batch(ctx: int, imgs, h_num, h_den=1, keep_stages: bool = False, format: int = SBMT_EXPLICIT,
+               flags: int = 0) -> list[int]:
+    n, arr, prs, npr, keeps = _batch_args(imgs, h_num, h_den, keep_stages, format, flags)
     out = (ctypes.c_uint64 * max(n, 1))()
-    _check(load().mesh_batch(ctx, arr, n, prs, len(hn), out))
+    _check(load().mesh_batch(ctx, arr, n, prs, npr, out))
     del keeps
     return [out[k] for k in range(n)]
+
+
+def mesh_autotune(ctx: int, imgs, h_num, h_den=1, repeats: int = 2) -> None:
+    """Tune the batched path for the size class of this batch (persists to
+    the tuning file); the meshes it makes are released."""
+    n, arr, prs, npr, keeps = _batch_args(imgs, h_num, h_den)
+    _check(load().mesh_autotune(ctx, arr, n, prs, npr, repeats))
+    del keeps
+
+
+def mesh_tuning(ctx: int, imgs, h_num, h_den=1) -> dict:
+    """The launch parameters mesh_batch uses for this batch."""
+    n, arr, prs, npr, keeps = _batch_args(imgs, h_num, h_den)
+    o = (ctypes.c_int32 * 4)()
+    _check(load().mesh_tuning(ctx, arr, n, prs, npr, o))
+    del keeps
+    return {"cut_blocks_per_sm": o[0], "tierg_blocks_per_sm": o[1], "fork": o[2], "graph": o[3]}
+
+
+def mesh_set_tuning(ctx: int, imgs, h_num, h_den=1, cut_blocks_per_sm: int = 8, tierg_blocks_per_sm: int = 24,
+                    fork: int = 1, graph: int = 0) -> None:
+    """Set the launch parameters of this batch's size class (this context only)."""
+    n, arr, prs, npr, keeps = _batch_args(imgs, h_num, h_den)
+    v = (ctypes.c_int32 * 4)(cut_blocks_per_sm, tierg_blocks_per_sm, fork, graph)
+    _check(load().mesh_set_tuning(ctx, arr, n, prs, npr, v))
+    del keeps
 
 
 def mesh_query(ctx: int, mesh: int, wait_ms: int = -1) -> sbmt_mesh_view:
@@ -431,3 +510,85 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def _scheck(rc: int):
+    if rc != SBMT_OK:
+        raise SbmtError(rc, load().sbmt_server_last_error().decode())
+
+
+def mesh_check(img, h_num: int, h_den: int = 1) -> int:
+    """SBMT_OK, or the code mesh_bitmap would return for bad arguments."""
+    im, keep = _image(img)
+    pr = _params(h_num, h_den)
+    rc = load().mesh_check(ctypes.byref(im), ctypes.byref(pr))
+    del keep
+    return rc
+
+
+def mesh_bound(img, h_num: int, h_den: int = 1) -> int:
+    """A request's reservation before its boundary is counted (bytes)."""
+    im, keep = _image(img)
+    pr = _params(h_num, h_den)
+    b = ctypes.c_size_t(0)
+    _scheck(load().mesh_bound(ctypes.byref(im), ctypes.byref(pr), ctypes.byref(b)))
+    del keep
+    return b.value
+
+
+def mesh_footprint(ctx: int, mesh: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().mesh_footprint(ctx, mesh, ctypes.byref(b)))
+    return b.value
+
+
+def server_create(device: int = 0, hbm_budget: int = 0, max_batch: int = 0, workers: int = 0,
+                  oom_every: int = 0) -> int:
+    srv = ctypes.c_void_p()
+    cfg = sbmt_server_config(hbm_budget, max_batch, workers, oom_every)
+    _scheck(load().server_create(ctypes.byref(srv), device, ctypes.byref(cfg)))
+    return srv.value
+
+
+def server_submit(srv: int, img, h_num: int, h_den: int = 1) -> int:
+    """Queue one request; a CUDA tensor image must stay alive until the
+    request is done (a numpy image is copied)."""
+    im, keep = _image(img)
+    pr = _params(h_num, h_den)
+    rid = ctypes.c_uint64()
+    _scheck(load().server_submit(srv, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(rid)))
+    del keep
+    return rid.value
+
+
+def server_wait(srv: int, rid: int, wait_ms: int = -1):
+    """(view or None while pending, info dict); raises on a failed request."""
+    v, info = sbmt_mesh_view(), sbmt_request_info()
+    rc = load().server_wait(srv, rid, wait_ms, ctypes.byref(v), ctypes.byref(info))
+    if rc in (SBMT_EPENDING, SBMT_ETIMEDOUT):
+        return None, None
+    d = {"status": info.status, "batch_size": info.batch_size, "queued_ms": info.queued_ms,
+         "total_ms": info.total_ms}
+    _scheck(rc)
+    return v, d
+
+
+def server_cancel(srv: int, rid: int) -> None:
+    _scheck(load().server_cancel(srv, rid))
+
+
+def server_release(srv: int, rid: int) -> None:
+    _scheck(load().server_release(srv, rid))
+
+
+def server_stats(srv: int) -> dict:
+    st = sbmt_server_stats()
+    _scheck(load().server_stats(srv, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in sbmt_server_stats._fields_}
+
+
+def server_destroy(srv: int) -> None:
+    _scheck(load().server_destroy(srv))

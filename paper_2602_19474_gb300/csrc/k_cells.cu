@@ -241,14 +241,23 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
 // pairs are counting-sorted by cell in shared memory (histogram, scan,
 // scatter); each cut cell gets a record, in cell order, in a dense range of
 // recs drawn from a counter (bbase[b], bcut[b] records).
-__global__ void __launch_bounds__(256) k_sort(const Pair* pairs, Pair* sorted, const u32* poff, CutRec* recs,
-                                              u32* nrec, u32* bcut, u32* bbase) {
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_sort_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                const u32* __restrict__ bpre, int njobs) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB], s_off[NB], s_cur[NB];
   __shared__ unsigned short s_cut[NB];
   __shared__ u32 s_sh[8];
   __shared__ u32 s_base;
-  const u32 b = blockIdx.x, lo = poff[b], n = poff[b + 1] - lo;
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const Pair* pairs = J.pairs;
+  Pair* sorted = J.raw;
+  const u32* poff = J.poff;
+  CutRec* recs = J.recs;
+  u32* nrec = jc(J, JC_NREC);
+  u32* bcut = J.bcut;
+  u32* bbase = J.bbase;
+  const u32 b = lb, lo = poff[b], n = poff[b + 1] - lo;
   const i64 c0 = (i64)b << CB_LOG;
   if (n == 0) {
     if (threadIdx.x == 0) bcut[b] = 0, bbase[b] = 0;
@@ -391,36 +400,102 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 // totals, for a Tier-T cell its staged patch, and a Tier-G cell counted
 // (cells in ngcell, triangles in ngtri, cells per local vertex count in
 // gcnt, counts above TIERG_TN pooled at TIERG_TN + 1).
-__global__ void __launch_bounds__(128, 8) k_cutcells(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                                  const Pair* sorted, const Seg* segs, const Event* ev, CutRec* recs,
-                                                  const u32* nrec, u32* bextra, u32* bchain, TStage* stg,
-                                                  u32* ngcell, u32* ngtri, u32* gcnt, u32* err) {
-  const u32 total = *nrec;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    CutRec rec = recs[i];
+// The records of every job form one work queue, handed out in chunks of
+// CUT_CHUNK records of one job (recpre[njobs + 1 + k]: the chunks before job
+// k), so that a block works for one job at a time with its descriptor in
+// shared memory; the Tier-G size counts are batch-wide, so that the Tier-G
+// kernels take the largest cells of the whole batch first.
+template <bool ONE>
+__global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                       int njobs, BatchDev* bd) {
+  __shared__ Job sJ;
+  const u32* cpre = bd->recpre + njobs + 1;
+  const u32 nchunks = ONE ? (*jc(one, JC_NREC) + CUT_CHUNK - 1) / CUT_CHUNK : cpre[njobs];
+  int cur = -1;
+  for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const Job* jp = &one;
+    u32 c0 = 0;
+    if constexpr (!ONE) {
+      const int jk = job_of(cpre, njobs, c);
+      if (jk != cur) {
+        __syncthreads();
+        load_job(jobs, jk, &sJ);
+        cur = jk;
+      }
+      jp = &sJ;
+      c0 = cpre[jk];
+    }
+    const Job& J = *jp;
+    const u32 ri = (c - c0) * CUT_CHUNK + threadIdx.x;
+    if (ri >= *jc(J, JC_NREC)) continue;
+    const GridP& g = J.g;
+    u32* err = jc(J, JC_ERR);
+    CutRec rec = J.recs[ri];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
-    const Pair* P = sorted + rec.pair_lo;
-    const Klass kl = classify_cell(g, cg, P, rec.npairs, segs, ev, err);
+    const Pair* P = J.raw + rec.pair_lo;
+    const Klass kl = classify_cell(g, cg, P, rec.npairs, J.segs, J.ev, err);
     rec.code = kl.code | (kl.tierG ? (1u << 16) : 0u);
     rec.ntri = kl.ntri, rec.nchain = kl.nchain;
     // until emission, a Tier-T record keeps P's pixel corner in tri_off
-    if (!kl.tierG) rec.tri_off = stage_tier_t(g, cg, rec, P, segs, ev, img, pitch, dtype, stg + i, err);
-    recs[i] = rec;
+    if (!kl.tierG)
+      rec.tri_off = stage_tier_t(g, cg, rec, P, J.segs, J.ev, J.img, J.pitch, J.dtype, J.stg + ri, err);
+    J.recs[ri] = rec;
     const u32 b = rec.cell >> CB_LOG;
-    atomicAdd(&bextra[b], kl.ntri - 1);
-    if (kl.nchain) atomicAdd(&bchain[b], kl.nchain);
+    atomicAdd(&j_bextra(J)[b], kl.ntri - 1);
+    if (kl.nchain) atomicAdd(&j_bchain(J)[b], kl.nchain);
     if (kl.tierG) {
-      // one atomic per warp for the cell and triangle counts, one per
-      // distinct size for the per-size counts (n = ntri + 2 - n_i)
+      // one atomic per warp for the job's cell and triangle counts, one per
+      // distinct size for the batch's per-size counts (n = ntri + 2 - n_i)
       const unsigned act = __activemask();
       const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
       const u32 t = __reduce_add_sync(act, kl.ntri);
-      if (lane == lead) atomicAdd(ngcell, (u32)__popc(act)), atomicAdd(ngtri, t);
+      if (lane == lead) atomicAdd(jc(J, JC_NGCELL), (u32)__popc(act)), atomicAdd(jc(J, JC_NGTRI), t);
       const u32 n = kl.ntri + 2 - kl.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
       const unsigned peers = __match_any_sync(act, key);
-      if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[key], (u32)__popc(peers));
+      if (lane == __ffs(peers) - 1) atomicAdd(&bd->gcnt[key], (u32)__popc(peers));
     }
   }
+}
+
+// the jobs' record counts into the batch's prefix (one block)
+__global__ void __launch_bounds__(1024) k_rec_prefix(const Job* __restrict__ jobs, int njobs, BatchDev* bd) {
+  __shared__ u32 sh[1024];
+  u32 carry = 0;
+  for (int base = 0; base < njobs; base += 1024) {
+    const int k = base + (int)threadIdx.x;
+    const u32 v = k < njobs ? *jc(jobs[k], JC_NREC) : 0u;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const u32 x = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
+      __syncthreads();
+      sh[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (k < njobs) bd->recpre[k] = carry + sh[threadIdx.x] - v;
+    carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bd->recpre[njobs] = carry;
+  // the same over the jobs' chunks of CUT_CHUNK records
+  u32* cpre = bd->recpre + njobs + 1;
+  carry = 0;
+  for (int base = 0; base < njobs; base += 1024) {
+    const int k = base + (int)threadIdx.x;
+    const u32 v = k < njobs ? (*jc(jobs[k], JC_NREC) + CUT_CHUNK - 1) / CUT_CHUNK : 0u;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const u32 x = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
+      __syncthreads();
+      sh[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (k < njobs) cpre[k] = carry + sh[threadIdx.x] - v;
+    carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cpre[njobs] = carry;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,18 +506,34 @@ __global__ void __launch_bounds__(128, 8) k_cutcells(GridP g, const unsigned cha
 // to the Tier-G kernels, which run beside this one and take their output
 // ranges from the same scans.  The bucket's other triangles are written by
 // one block.
-__global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                              CutRec* recs, const u32* bcut, const u32* bbase,
-                                              const u32* extra_scan, const u32* chain_scan, const TStage* stg,
-                                              u32 NVg, u32 NE, int* tri, unsigned short* label,
-                                              unsigned short* code, double* xy, CompactOut cp) {
+template <bool ONE>
+__global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job one,
+                                                           const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                           int njobs) {
   constexpr int NB = 1 << CB_LOG;
   __shared__ u32 s_cnt[NB];
   __shared__ u32 s_off[NB];
   __shared__ u32 s_cb[NB];
   __shared__ u32 s_sh[8];
   __shared__ int s_row0;
-  const u32 b = blockIdx.x;
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const GridP& g = J.g;
+  const unsigned char* img = J.img;
+  const i64 pitch = J.pitch;
+  const int dtype = J.dtype;
+  const CutRec* const& recs = J.recs;
+  const u32* const& bcut = J.bcut;
+  const u32* const& bbase = J.bbase;
+  const u32* const& extra_scan = J.extra_scan;
+  const u32* const& chain_scan = J.chain_scan;
+  const TStage* const& stg = J.stg;
+  const u32 &NVg = J.NVg, &NE = J.NE, &nbc = J.nbc;
+  int* const& tri = J.tri;
+  unsigned short* const& label = J.label;
+  unsigned short* const& code = J.code;
+  double* const& xy = J.xy;
+  const CompactOut& cp = J.cp;
+  const u32 b = lb;
   const i64 c0 = (i64)b << CB_LOG;
   const int nc = (int)min((i64)NB, g.ncells - c0);
   const u32 ncut = bcut[b], rec0 = bbase[b];
@@ -594,26 +685,32 @@ __global__ void __launch_bounds__(256) k_emit(GridP g, const unsigned char* img,
       reinterpret_cast<double2*>(xy)[cb - cp.xy0] = v;
     }
   }
-  if (cp.on && b == gridDim.x - 1 && threadIdx.x == 0)
-    cp.patch_off[cp.cut_scan[gridDim.x]] = extra_scan[gridDim.x] + cp.cut_scan[gridDim.x];
+  if (cp.on && b == nbc - 1 && threadIdx.x == 0) cp.patch_off[cp.cut_scan[nbc]] = extra_scan[nbc] + cp.cut_scan[nbc];
 }
 
 // lattice vertex coordinates.  Vertex v(i, j) has x = (ox + 3p m) / S with
 // m = 2i + j, so every row reads its x values from one table over the m the
 // image uses (the double arithmetic is done once per m, not per vertex;
 // this part has little FP64 throughput); one block per vertex row.
-__global__ void __launch_bounds__(256) k_lattice_tab(GridP g, double* tab, i64 m0, i64 nm) {
-  const double invS = 1.0 / (double)g.S;
-  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += (i64)gridDim.x * blockDim.x)
-    tab[k] = (double)(g.ox + 3 * g.p * (m0 + k)) * invS;
+__global__ void __launch_bounds__(256) k_lattice_tab_b(const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                       int njobs) {
+  const int jk = job_of(bpre, njobs, blockIdx.x);
+  const Job& J = jobs[jk];
+  const double invS = 1.0 / (double)J.g.S;
+  const i64 k = (i64)(blockIdx.x - bpre[jk]) * blockDim.x + threadIdx.x;
+  if (k < J.nm) J.xtab[k] = (double)(J.g.ox + 3 * J.g.p * (J.m_lo + k)) * invS;
 }
 
-__global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy, const double* tab, i64 m0) {
-  const int r = blockIdx.x;
+__global__ void __launch_bounds__(256) k_lattice_xy_b(const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                      int njobs) {
+  const int jk = job_of(bpre, njobs, blockIdx.x);
+  const Job& J = jobs[jk];
+  const GridP& g = J.g;
+  const int r = (int)(blockIdx.x - bpre[jk]);
   const i64 j = g.vj0 + r, lo = g.vlo[r], n = g.vhi[r] - lo + 1, base = g.vbase[r];
   const double y = zdouble(zq(g.oy, 3 * g.p * j)) * (1.0 / (double)g.S);
-  const double* tx = tab + (2 * lo + j - m0);
-  double2* out = reinterpret_cast<double2*>(xy) + base;
+  const double* tx = J.xtab + (2 * lo + j - J.m_lo);
+  double2* out = reinterpret_cast<double2*>(J.xy) + base;
   for (i64 k = threadIdx.x; k < n; k += blockDim.x) {
     double2 v;
     v.x = tx[2 * k];
@@ -624,36 +721,37 @@ __global__ void __launch_bounds__(256) k_lattice_xy(GridP g, double* xy, const d
 
 }  // namespace
 
-int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
-                 u32* bbase, cudaStream_t st) {
-  if (nbc == 0) return 0;
-  k_sort<<<nbc, 256, 0, st>>>(pairs, sorted, poff, recs, nrec, bcut, bbase);
+int launch_sort_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_sort_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_sort_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
   return 1;
 }
 
-int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                     const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* ngcell, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st) {
-  k_cutcells<<<152 * 24, 128, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, nrec, bextra, bchain, stg,
-                                       ngcell, ngtri, gcnt, err);
-  return 1;
-}
-
-int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
-                 const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
-                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, const CompactOut& cp,
-                 cudaStream_t st) {
-  if (nbc == 0) return 0;
-  k_emit<<<nbc, 256, 0, st>>>(g, img, pitch, dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, NVg, NE, tri,
-                              label, code, xy, cp);
-  return 1;
-}
-
-int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st) {
-  if (g.nverts == 0) return 0;
-  k_lattice_tab<<<(unsigned)std::min<i64>((nm + 255) / 256, 1024), 256, 0, st>>>(g, tab, m0, nm);
-  k_lattice_xy<<<g.nvrows, 256, 0, st>>>(g, xy, tab, m0);
+int launch_cutcells_b(const Job* one, const Job* jobs, int njobs, const BatchPtrs& bp, int blocks_per_sm,
+                      cudaStream_t st) {
+  if (one) {
+    k_cutcells_b<true><<<152 * blocks_per_sm, 128, 0, st>>>(*one, jobs, njobs, bp.bd);
+    return 1;
+  }
+  k_rec_prefix<<<1, 1024, 0, st>>>(jobs, njobs, bp.bd);
+  k_cutcells_b<false><<<152 * blocks_per_sm, 128, 0, st>>>(Job{}, jobs, njobs, bp.bd);
   return 2;
+}
+
+int launch_emit_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_emit_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_emit_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  return 1;
+}
+
+int launch_lattice_b(const Job* jobs, const u32* bpre_tab, u32 nb_tab, const u32* bpre_xy, u32 nb_xy, int njobs,
+                     cudaStream_t st) {
+  int n = 0;
+  if (nb_tab) k_lattice_tab_b<<<nb_tab, 256, 0, st>>>(jobs, bpre_tab, njobs), ++n;
+  if (nb_xy) k_lattice_xy_b<<<nb_xy, 256, 0, st>>>(jobs, bpre_xy, njobs), ++n;
+  return n;
 }
 
 }  // namespace sbmt

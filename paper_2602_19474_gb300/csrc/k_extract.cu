@@ -12,6 +12,7 @@
 // memory), so that K1b finds the end of every run with find-first-set over
 // 32-bit words instead of walking pixel by pixel.
 #include "sbmt_launch.h"
+#include "sbmt_walk.cuh"
 
 namespace sbmt {
 
@@ -63,13 +64,12 @@ SBMT_DEV void load8(const unsigned char* img, i64 pitch, int W, int H, int x0, i
 // 8 consecutive corners of 4 rows.  Vertex flags go to shared memory as one
 // byte per (row, 8 corners), then out as row words and transposed column words.
 template <typename T>
-__global__ void __launch_bounds__(256) k_corner_bits(const unsigned char* img, i64 pitch, int W, int H, u32* vrow,
-                                                     int wpr, u32* vcol, int wpc, unsigned long long* nvtx) {
-  __shared__ unsigned char fl[32][33];
-  __shared__ unsigned int cnt;
+SBMT_DEV void corner_bits_tile(const unsigned char* img, i64 pitch, int W, int H, u32* vrow, int wpr, u32* vcol,
+                               int wpc, unsigned long long* nvtx, int bx, int by, unsigned char (*fl)[33],
+                               unsigned int& cnt) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int x0 = blockIdx.x * 256 + lane * 8;  // first corner column of this thread
-  const int r0 = blockIdx.y * 32;
+  const int x0 = bx * 256 + lane * 8;  // first corner column of this thread
+  const int r0 = by * 32;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   u32 mycnt = 0;
@@ -104,17 +104,41 @@ __global__ void __launch_bounds__(256) k_corner_bits(const unsigned char* img, i
     const int r = threadIdx.x >> 3, k = threadIdx.x & 7, cy = r0 + r;
     const u32 word = (u32)fl[r][4 * k] | ((u32)fl[r][4 * k + 1] << 8) | ((u32)fl[r][4 * k + 2] << 16) |
                      ((u32)fl[r][4 * k + 3] << 24);
-    const int wx = blockIdx.x * 8 + k;
+    const int wx = bx * 8 + k;
     if (cy <= H && wx < wpr) vrow[(i64)cy * wpr + wx] = word;
   }
   // column words: corner column c of the block, rows r0 .. r0+31
   {
-    const int c = threadIdx.x, cx = blockIdx.x * 256 + c;
+    const int c = threadIdx.x, cx = bx * 256 + c;
     u32 word = 0;
     for (int r = 0; r < 32; ++r) word |= (u32)((fl[r][c >> 3] >> (c & 7)) & 1u) << r;
-    if (cx <= W) vcol[(i64)cx * wpc + blockIdx.y] = word;
+    if (cx <= W) vcol[(i64)cx * wpc + by] = word;
   }
   if (threadIdx.x == 0 && cnt) atomicAdd(nvtx, (unsigned long long)cnt);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_corner_bits(const unsigned char* img, i64 pitch, int W, int H, u32* vrow,
+                                                     int wpr, u32* vcol, int wpc, unsigned long long* nvtx) {
+  __shared__ unsigned char fl[32][33];
+  __shared__ unsigned int cnt;
+  corner_bits_tile<T>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx, blockIdx.x, blockIdx.y, fl, cnt);
+}
+
+// batched: job k's tiles are its blocks, row-major over (256-column, 32-row) tiles
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_corner_bits_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                       const u32* __restrict__ bpre, int njobs) {
+  __shared__ unsigned char fl[32][33];
+  __shared__ unsigned int cnt;
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const int W = J.g.W, H = J.g.H, gx = (W + 1 + 255) / 256;
+  const int bx = (int)(lb % (u32)gx), by = (int)(lb / (u32)gx);
+  unsigned long long* nvtx = (unsigned long long*)J.zero;
+  if (J.dtype == 1)
+    corner_bits_tile<unsigned char>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt);
+  else
+    corner_bits_tile<unsigned short>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt);
 }
 
 // first set bit at index >= from in a packed bit-plane line of nwords words;
@@ -134,10 +158,17 @@ SBMT_DEV u32 lab16(int l) { return l == OUTSIDE ? 0xFFFFu : (u32)l; }
 
 // K1b: one thread per 32-corner word of a row bit-plane; every vertex starts
 // its +x and +y runs.  Output slots are taken one atomic per warp.
+// the number of grid cells a segment visits (its pairs), for the batched
+// path; the single-image extraction passes no grid
+struct PairCount {
+  const GridP* g;
+  u32* npairs;
+};
+
 template <typename T>
-__global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, const u32* vrow, int wpr,
-                           const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err) {
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+SBMT_DEV void segments_word(const unsigned char* img, i64 pitch, int W, int H, const u32* vrow, int wpr,
+                            const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, i64 t,
+                            PairCount pc = PairCount{nullptr, nullptr}) {
   const bool in = t < (i64)(H + 1) * wpr;
   const int cy = in ? (int)(t / wpr) : 0, w = in ? (int)(t % wpr) : 0;
   const u32 bits = in ? vrow[t] : 0u;
@@ -158,9 +189,8 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
   u32 wbase = 0;
   if (lane == 31 && wtot) wbase = atomicAdd(nseg, wtot);
   wbase = __shfl_sync(0xffffffffu, wbase, 31);
-  if (!cnt) return;
   u32 slot = wbase + x - cnt;
-  for (u32 b = bits; b; b &= b - 1) {
+  for (u32 b = cnt ? bits : 0u; b; b &= b - 1) {
     const int cx = (w << 5) + __ffs(b) - 1;
     const int m = corner_mask<T>(img, pitch, W, H, cx, cy);
     if (m & BE_E) {
@@ -171,7 +201,8 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
         const int l0 = pix<T>(img, pitch, W, H, cx, cy - 1), l1 = pix<T>(img, pitch, W, H, cx, cy);
         // going +x the left side is above: forward when the upper label is lower
         const u32 rev = l1 < l0 ? 0u : 1u;
-        segs[slot] = Seg{cx, cy, (u32)(end - cx) | (rev << 31), lab16(l0) | (lab16(l1) << 16)};
+        const Seg sg{cx, cy, (u32)(end - cx) | (rev << 31), lab16(l0) | (lab16(l1) << 16)};
+        segs[slot] = sg;
       }
       ++slot;
     }
@@ -183,11 +214,44 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
         const int l0 = pix<T>(img, pitch, W, H, cx - 1, cy), l1 = pix<T>(img, pitch, W, H, cx, cy);
         // going +y the left side is -x: forward when the left label is lower
         const u32 rev = l0 < l1 ? 0u : 1u;
-        segs[slot] = Seg{cx, cy, (u32)(end - cy) | (1u << 30) | (rev << 31), lab16(l0) | (lab16(l1) << 16)};
+        const Seg sg{cx, cy, (u32)(end - cy) | (1u << 30) | (rev << 31), lab16(l0) | (lab16(l1) << 16)};
+        segs[slot] = sg;
       }
       ++slot;
     }
   }
+  if (pc.g) {
+    // the pair counts of the warp's segments, one lane per segment: the
+    // walk setup runs densely instead of once per segment-writing lane
+    __syncwarp();
+    for (u32 i = (u32)lane; i < wtot; i += 32) {
+      const u32 sl = wbase + i;
+      if (sl < cap) pc.npairs[sl] = seg_pairs(*pc.g, segs[sl]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, const u32* vrow, int wpr,
+                           const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err) {
+  segments_word<T>(img, pitch, W, H, vrow, wpr, vcol, wpc, segs, cap, nseg, err,
+                   (i64)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(256, 4) k_segments_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                       const u32* __restrict__ bpre, int njobs) {
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const i64 t = (i64)lb * blockDim.x + threadIdx.x;
+  u32* cnt = J.zero;
+  const GridP& g = J.g;
+  const PairCount pc{&g, J.npairs};
+  if (J.dtype == 1)
+    segments_word<unsigned char>(J.img, J.pitch, g.W, g.H, J.vrow, J.wpr, J.vcol, J.wpc, J.segs, J.seg_cap,
+                                 cnt + JC_NSEG, cnt + JC_ERR, t, pc);
+  else
+    segments_word<unsigned short>(J.img, J.pitch, g.W, g.H, J.vrow, J.wpr, J.vcol, J.wpc, J.segs, J.seg_cap,
+                                  cnt + JC_NSEG, cnt + JC_ERR, t, pc);
 }
 
 }  // namespace
@@ -211,6 +275,20 @@ int launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H
     k_segments<unsigned char><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, segs, cap, nseg, err);
   else
     k_segments<unsigned short><<<grd, blk, 0, st>>>(img, pitch, W, H, vrow, wpr, vcol, wpc, segs, cap, nseg, err);
+  return 1;
+}
+
+int launch_corner_bits_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_corner_bits_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_corner_bits_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  return 1;
+}
+
+int launch_segments_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_segments_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_segments_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
   return 1;
 }
 

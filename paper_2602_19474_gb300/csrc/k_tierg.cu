@@ -27,7 +27,6 @@ namespace sbmt {
 namespace {
 
 constexpr int TN = TIERG_TN;  // thread path: local vertices per cell (16-bit vertex sets)
-constexpr int TG_BLOCKS_PER_SM = 24;  // thread path: as many 64-thread blocks as fit (latency bound)
 constexpr int WN = 64;  // warp path
 constexpr int WWARPS = 4;
 
@@ -517,155 +516,179 @@ SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, i
 SBMT_DEV int local_count(const CutRec& rec) { return (int)(rec.ntri + 2 - rec.nchain); }
 SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 * rec.nchain); }
 
-// Tier-G cells ordered by local vertex count, largest first, so that the
-// lanes of a warp run cells of one size; cells above TN vertices go to the
-// warp kernel.  gcnt[n] holds the number of Tier-G cells with n vertices
-// (n > TN pooled at index TN + 1).  One warp per cell bucket scans the
-// bucket's records (in cell order) and gives each Tier-G cell its output
-// range from the scans the emission kernel uses: its triangles follow those
-// of the bucket's earlier cells (one each when uncut, ntri each when cut)
-// and its inside vertices those of the bucket's earlier cut cells.  In the
-// compact format only the cut cells' triangles are listed.
-__global__ void __launch_bounds__(256) k_gorder(CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
-                                                const u32* gcnt, u32* gcur, u32* olist, u32* nolist, u32* wlist,
-                                                u32* nwlist, const u32* extra_scan, const u32* chain_scan,
-                                                const u32* cut_scan, u32 CB0) {
+// Tier-G cells of the whole batch ordered by local vertex count, largest
+// first, so that the lanes of a warp run cells of one size; cells above TN
+// vertices go to the warp kernel.  bd->gcnt[n] holds the batch's number of
+// Tier-G cells with n vertices (n > TN pooled at index TN + 1).  One warp per
+// cell bucket scans the bucket's records (in cell order) and gives each
+// Tier-G cell its output range from the scans the emission kernel uses: its
+// triangles follow those of the bucket's earlier cells (one each when uncut,
+// ntri each when cut) and its inside vertices those of the bucket's earlier
+// cut cells.  In the compact format only the cut cells' triangles are listed.
+// The lists hold (job, record) pairs.
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                  const u32* __restrict__ bpre, int njobs, BatchDev* bd, uint2* olist,
+                                                  uint2* wlist) {
   __shared__ u32 s_base[TN + 2];
   if (threadIdx.x == 0) {
     u32 run = 0;
-    for (int n = TN; n >= 0; --n) s_base[n] = run, run += gcnt[n];
+    for (int n = TN; n >= 0; --n) s_base[n] = run, run += bd->gcnt[n];
     s_base[TN + 1] = 0;
-    if (blockIdx.x == 0) *nolist = run;
+    if (blockIdx.x == 0) bd->nolist = run;
   }
-  __syncthreads();
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const int lane = threadIdx.x & 31;
-  const u32 nwarps = gridDim.x * (blockDim.x >> 5);
-  for (u32 b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nbc; b += nwarps) {
-    const u32 n = bcut[b], rec0 = bbase[b];
-    u32 ct = 0, cc = 0;  // the bucket's earlier records: sum of (ntri - 1), of nchain
-    for (u32 base = 0; base < n; base += 32) {
-      const u32 r = base + (u32)lane;
-      const bool valid = r < n;
-      CutRec rec{};
-      if (valid) rec = recs[rec0 + r];
-      const u32 vt = valid ? rec.ntri - 1u : 0u, vc = valid ? rec.nchain : 0u;
-      u32 it = vt, ic = vc;
+  const u32 b = lb * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= J.nbc) return;
+  CutRec* recs = J.recs;
+  const u32* extra_scan = J.extra_scan;
+  const u32* cut_scan = J.cp.on ? J.cp.cut_scan : nullptr;
+  const u32 CB0 = J.NVg + J.NE;
+  const u32 n = J.bcut[b], rec0 = J.bbase[b];
+  u32 ct = 0, cc = 0;  // the bucket's earlier records: sum of (ntri - 1), of nchain
+  for (u32 base = 0; base < n; base += 32) {
+    const u32 r = base + (u32)lane;
+    const bool valid = r < n;
+    CutRec rec{};
+    if (valid) rec = recs[rec0 + r];
+    const u32 vt = valid ? rec.ntri - 1u : 0u, vc = valid ? rec.nchain : 0u;
+    u32 it = vt, ic = vc;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 t = __shfl_up_sync(0xffffffffu, it, o), c = __shfl_up_sync(0xffffffffu, ic, o);
-        if (lane >= o) it += t, ic += c;
-      }
-      const u32 pt = ct + it - vt, pc = cc + ic - vc;
-      ct += __shfl_sync(0xffffffffu, it, 31), cc += __shfl_sync(0xffffffffu, ic, 31);
-      const bool tg = valid && (rec.code & (1u << 16));
-      const unsigned tmask = __ballot_sync(0xffffffffu, tg);
-      if (!tg) continue;
-      recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
-      recs[rec0 + r].chain_base = CB0 + chain_scan[b] + pc;
-      const int nv = local_count(rec);
-      const int key = nv > TN ? TN + 1 : nv;
-      // one atomic per distinct size in the warp
-      const unsigned peers = __match_any_sync(tmask, key);
-      const int leader = __ffs(peers) - 1;
-      u32 at = 0;
-      if (lane == leader) at = atomicAdd(key > TN ? nwlist : &gcur[key], (u32)__popc(peers));
-      at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
-      if (key > TN) wlist[at] = rec0 + r;
-      else olist[s_base[key] + at] = rec0 + r;
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 t = __shfl_up_sync(0xffffffffu, it, o), c = __shfl_up_sync(0xffffffffu, ic, o);
+      if (lane >= o) it += t, ic += c;
     }
+    const u32 pt = ct + it - vt, pc = cc + ic - vc;
+    ct += __shfl_sync(0xffffffffu, it, 31), cc += __shfl_sync(0xffffffffu, ic, 31);
+    const bool tg = valid && (rec.code & (1u << 16));
+    const unsigned tmask = __ballot_sync(0xffffffffu, tg);
+    if (!tg) continue;
+    recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
+    recs[rec0 + r].chain_base = CB0 + J.chain_scan[b] + pc;
+    const int nv = local_count(rec);
+    const int key = nv > TN ? TN + 1 : nv;
+    // one atomic per distinct size in the warp
+    const unsigned peers = __match_any_sync(tmask, key);
+    const int leader = __ffs(peers) - 1;
+    u32 at = 0;
+    if (lane == leader) at = atomicAdd(key > TN ? &bd->nwlist : &bd->gcur[key], (u32)__popc(peers));
+    at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
+    const uint2 e = make_uint2((u32)jk, rec0 + r);
+    if (key > TN) wlist[at] = e;
+    else olist[s_base[key] + at] = e;
   }
 }
 
+SBMT_DEV void tierg_over(const Job& J, u32 cell) {
+  atomicOr(jc(J, JC_ERR), ERR_CAPACITY);
+  const u32 slot = atomicAdd(jc(J, JC_NOVER), 1u);
+  if (slot < OVER_CAP) J.over[slot] = cell;
+}
+
 // one thread per Tier-G cell of at most TN vertices, in the order above
-__global__ void __launch_bounds__(64) k_tierg_thread(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                                      const Pair* sorted, const Seg* segs, const Event* ev,
-                                                      const CutRec* recs, const u32* olist, const u32* nolist,
-                                                      int* tri, unsigned short* label, unsigned short* code,
-                                                      double* xy, u32 xy0, u32* err, u32* nover, u32* over) {
-  const u32 total = *nolist;
+template <bool ONE>
+__global__ void __launch_bounds__(64, 12) k_tierg_thread_b(const __grid_constant__ Job one,
+                                                           const Job* __restrict__ jobs, const BatchDev* bd,
+                                                           const uint2* olist) {
+  const u32 total = bd->nolist;
   for (u32 item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
-    const CutRec rec = recs[olist[item]];
+    const uint2 e = olist[item];
+    const Job& J = ONE ? one : jobs[e.x];
+    const GridP g = J.g;
+    const CutRec rec = J.recs[e.y];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
     GStore<TN> s;
-    build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
+    build_local(g, cg, rec, J.raw + rec.pair_lo, J.segs, J.ev, s);
     if (!s.ok) {
-      atomicOr(err, ERR_CAPACITY);
-      const u32 slot = atomicAdd(nover, 1u);
-      if (slot < OVER_CAP) over[slot] = rec.cell;
+      tierg_over(J, rec.cell);
       continue;
     }
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
     const float M = (float)(6 * g.p);
     greedy_faces_sets<TN>(s, boundary_count(rec), 1e-4f * M * M, 8e-6f * M * M);
-    write_patch<1, TN>(g, img, pitch, dtype, cg, rec, s, 0, tri, label, code, xy, xy0, err);
+    write_patch<1, TN>(g, J.img, J.pitch, J.dtype, cg, rec, s, 0, J.tri, J.label, J.code, J.xy, J.cp.xy0,
+                       jc(J, JC_ERR));
   }
 }
 
-__global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp(GridP g, const unsigned char* img, i64 pitch, int dtype,
-                                                            const Pair* sorted, const Seg* segs, const Event* ev,
-                                                            const CutRec* recs, const u32* wlist, const u32* nwlist,
-                                                            int* tri, unsigned short* label, unsigned short* code,
-                                                            double* xy, u32 xy0, u32* err, u32* nover,
-                                                            u32* over) {
+template <bool ONE>
+__global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp_b(const __grid_constant__ Job one,
+                                                              const Job* __restrict__ jobs, const BatchDev* bd,
+                                                              const uint2* wlist) {
   __shared__ GStore<WN> sm[WWARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   GStore<WN>& s = sm[w];
-  const u32 total = *nwlist;
+  const u32 total = bd->nwlist;
   for (u32 item = blockIdx.x * WWARPS + w; item < total; item += gridDim.x * WWARPS) {
-    const CutRec rec = recs[wlist[item]];
+    const uint2 e = wlist[item];
+    const Job& J = ONE ? one : jobs[e.x];
+    const GridP g = J.g;
+    const CutRec rec = J.recs[e.y];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
-    if (lane == 0) build_local(g, cg, rec, sorted + rec.pair_lo, segs, ev, s);
+    if (lane == 0) build_local(g, cg, rec, J.raw + rec.pair_lo, J.segs, J.ev, s);
     __syncwarp();
     if (!s.ok) {
-      if (lane == 0) {
-        atomicOr(err, ERR_CAPACITY);
-        const u32 slot = atomicAdd(nover, 1u);
-        if (slot < OVER_CAP) over[slot] = rec.cell;
-      }
+      if (lane == 0) tierg_over(J, rec.cell);
       __syncwarp();
       continue;
     }
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
     const float M = (float)(6 * g.p);
     greedy_faces<32, WN>(s, lane, boundary_count(rec), OriFiltered<WN>{&s, 8e-6f * M * M}, 1e-4f * M * M);
-    write_patch<32, WN>(g, img, pitch, dtype, cg, rec, s, lane, tri, label, code, xy, xy0, err);
+    write_patch<32, WN>(g, J.img, J.pitch, J.dtype, cg, rec, s, lane, J.tri, J.label, J.code, J.xy, J.cp.xy0,
+                        jc(J, JC_ERR));
     __syncwarp();
   }
 }
 
+// the status words of every job (error bits, cut cells, Tier-G cells, Tier-G
+// triangles, cells over the Tier-G limit) into its mapped host slot
+__global__ void k_status_b(const Job* __restrict__ jobs, int njobs, const BatchDev* bd) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < njobs; k += gridDim.x * blockDim.x) {
+    const Job& J = jobs[k];
+    for (int w = 0; w < 5; ++w) J.hinfo[w] = *jc(J, JC_ERR + w);
+  }
+  __threadfence_system();
+}
+
 }  // namespace
 
-int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
-                  const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32 xy0, u32* err, u32* nover, u32* over, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
-                  cudaEvent_t ev_warp) {
-  // gcnt: TN + 2 counts, then TN + 2 cursors, then the ordered count
-  u32* gcur = gcnt + (TN + 2);
-  u32* nolist = gcnt + 2 * (TN + 2);
-  if (nbc == 0) return 0;
-  const u32 gblocks = std::min<u32>((nbc + 7) / 8, 152 * 8);
-  k_gorder<<<gblocks, 256, 0, st>>>(recs, bcut, bbase, nbc, gcnt, gcur, olist, nolist, wlist, nwlist, extra_scan,
-                                    chain_scan, cut_scan, CB0);
-  // each thread keeps a cell's state in local memory: give L1 the most room
-  static const bool carve = [] {
-    cudaFuncSetAttribute(k_tierg_thread, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    return true;
-  }();
-  (void)carve;
-  k_tierg_thread<<<152 * TG_BLOCKS_PER_SM, 64, 0, st>>>(g, img, pitch, dtype, sorted, segs, events, recs, olist,
-                                                        nolist, tri, label, code, xy, xy0, err, nover, over);
+int launch_tierg_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, const BatchPtrs& bp,
+                   int thread_blocks_per_sm, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
+                   cudaEvent_t ev_warp) {
+  if (nblocks == 0) return 0;
+  const Job none{};
+  const Job& oj = one ? *one : none;
+  if (one) k_gorder_b<true><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.wlist);
+  else k_gorder_b<false><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.wlist);
+  if (one) k_tierg_thread_b<true><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
+  else k_tierg_thread_b<false><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
   // the warp kernel on its own stream when given one, beside the thread kernel
   if (st2) {
     if (cudaEventRecord(ev_order, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_order, 0) != cudaSuccess) return -1;
   }
-  k_tierg_warp<<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(g, img, pitch, dtype, sorted, segs, events, recs, wlist,
-                                                            nwlist, tri, label, code, xy, xy0, err, nover, over);
+  if (one) k_tierg_warp_b<true><<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(oj, jobs, bp.bd, bp.wlist);
+  else k_tierg_warp_b<false><<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(oj, jobs, bp.bd, bp.wlist);
   if (st2) {
     if (cudaEventRecord(ev_warp, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_warp, 0) != cudaSuccess) return -1;
   }
   return 3;
+}
+
+int tierg_init() {
+  // each thread of the thread path keeps a cell's state in local memory:
+  // give L1 the most room
+  const bool ok = cudaFuncSetAttribute(k_tierg_thread_b<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0) ==
+                      cudaSuccess &&
+                  cudaFuncSetAttribute(k_tierg_thread_b<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0) ==
+                      cudaSuccess;
+  return ok ? 0 : -1;
+}
+
+int launch_status_b(const Job* jobs, int njobs, const BatchPtrs& bp, cudaStream_t st) {
+  k_status_b<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, njobs, bp.bd);
+  return 1;
 }
 
 }  // namespace sbmt

@@ -18,6 +18,7 @@
 // atomics and no tolerance.
 #include "sbmt_cell.cuh"
 #include "sbmt_launch.h"
+#include "sbmt_walk.cuh"
 
 namespace sbmt {
 
@@ -27,65 +28,6 @@ SBMT_DEV bool vid_ok(const GridP& g, i64 i, i64 j) {
   if (j < g.vj0 || j >= g.vj0 + g.nvrows) return false;
   const int r = (int)(j - g.vj0);
   return i >= g.vlo[r] && i <= g.vhi[r];
-}
-
-// Closed-form walk of one segment.  The walk runs from the segment's lower
-// end along +x / +y; pair k is the k-th cell it visits and crossing k the
-// k-th grid edge it crosses (between pair k and pair k + 1).  Both are O(1)
-// for any k, so a segment can be walked in independent chunks.
-struct SegWalk {
-  i64 X, Y, X0, X1, Y0, Y1, U;  // scaled end coordinates; U = (Y - oy) / 3 for horizontal runs
-  i64 j, j1, c0;                // strip (first strip) and first cell index
-  int dir, s0;                  // vertical: the first strip's slanted crossing lies above the start
-  u32 ncross;
-};
-
-SBMT_DEV i64 strip_ab(const GridP& g, i64 X, i64 j) { return ifloordiv(X - g.ox - 3 * g.p * j, 6 * g.p); }
-
-// slanted crossing of x = X inside strip j: its height, grid edge and the
-// cell above it (the cell below is up(ab, j) = 2 ab)
-SBMT_DEV void strip_slant(const GridP& g, i64 X, i64 j, Zq* ys, i64* ei, i64* ej, int* fam, i64* upper) {
-  const i64 p = g.p, ab = strip_ab(g, X, j), xab = g.ox + 3 * p * (2 * ab + j);
-  if (X - xab < 3 * p) {  // left of the apex: the 60-degree edge from v(ab, j)
-    *ys = zq(g.oy, 3 * p * j + (X - xab));
-    *ei = ab, *ej = j, *fam = 1, *upper = 2 * ab - 1;
-  } else {  // right of it: the 120-degree edge from v(ab + 1, j)
-    *ys = zq(g.oy, 3 * p * j + (xab + 6 * p - X));
-    *ei = ab + 1, *ej = j, *fam = 2, *upper = 2 * ab + 1;
-  }
-}
-
-SBMT_DEV SegWalk seg_setup(const GridP& g, const Seg& s) {
-  SegWalk w;
-  const i64 q = g.q, P6 = 6 * g.p, L = seg_len(s);
-  w.dir = seg_dir(s);
-  if (w.dir == 0) {
-    w.Y = 6 * q * s.cy - 3 * q;
-    w.X0 = 6 * q * s.cx - 3 * q, w.X1 = w.X0 + 6 * q * L;
-    w.j = strip_of(g, zq(w.Y));
-    // at height Y the 60-degree lines sit at ox + 6p i + U sqrt3 and the
-    // 120-degree lines at ox + 6p (k + j) - U sqrt3; the cell index is the
-    // number of lines of both families left of x
-    w.U = (w.Y - g.oy) / 3;
-    w.c0 = zfloordiv(zq(w.X0 - g.ox, -w.U), P6) + zfloordiv(zq(w.X0 - g.ox - P6 * w.j, w.U), P6);
-    const i64 c1 = zfloordiv(zq(w.X1 - g.ox, -w.U), P6) + zfloordiv(zq(w.X1 - g.ox - P6 * w.j, w.U), P6);
-    w.ncross = (u32)(c1 - w.c0);
-    return w;
-  }
-  w.X = 6 * q * s.cx - 3 * q;
-  w.Y0 = 6 * q * s.cy - 3 * q, w.Y1 = w.Y0 + 6 * q * L;
-  w.j = strip_of(g, zq(w.Y0)), w.j1 = strip_of(g, zq(w.Y1));
-  Zq ys;
-  i64 ei, ej, up;
-  int fam;
-  strip_slant(g, w.X, w.j, &ys, &ei, &ej, &fam, &up);
-  w.s0 = zcmp(ys, zq(w.Y0)) > 0 ? 1 : 0;
-  strip_slant(g, w.X, w.j1, &ys, &ei, &ej, &fam, &up);
-  const int e1 = zcmp(ys, zq(w.Y1)) < 0 ? 1 : 0;
-  // virtual sequence S_j0, H_j0+1, S_j0+1, ..., S_j1; the first and last
-  // slanted crossings count only when they lie inside (Y0, Y1)
-  w.ncross = (u32)(2 * (w.j1 - w.j) + 1 - (1 - w.s0) - (1 - e1));
-  return w;
 }
 
 // cell (c, j) of pair k
@@ -134,10 +76,18 @@ SBMT_DEV void walk_cross(const GridP& g, const SegWalk& w, u32 k, i64* ei, i64* 
   }
 }
 
-__global__ void k_seg_count(GridP g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs) {
-  const u32 n = min(*nseg, cap);
-  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += gridDim.x * blockDim.x)
-    npairs[s] = s < n ? seg_setup(g, segs[s]).ncross + 1u : 0u;
+// the counting phase's results per job: PSLG vertices (u64), segments, error
+// bits, pairs, into mapped host memory (8 words per job)
+__global__ void k_counts_b(const Job* __restrict__ jobs, int njobs, u32* out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < njobs; k += gridDim.x * blockDim.x) {
+    const Job& J = jobs[k];
+    const unsigned long long nv = *(const unsigned long long*)J.zero;
+    out[8 * k + 0] = (u32)nv, out[8 * k + 1] = (u32)(nv >> 32);
+    out[8 * k + 2] = *jc(J, JC_NSEG);
+    out[8 * k + 3] = *jc(J, JC_ERR);
+    out[8 * k + 4] = J.pbase[min(*jc(J, JC_NSEG), J.seg_cap)];
+  }
+  __threadfence_system();
 }
 
 constexpr u32 CH = 8;  // pairs per thread in the chunked walks
@@ -156,12 +106,14 @@ SBMT_DEV u32 warp_inc(u32* cur, u32 key) {
 
 // first segment of every chunk of CH pairs: chunk c starts in the segment s
 // with pbase[s] <= c CH < pbase[s + 1] (every segment has at least one pair)
-__global__ void k_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart) {
-  const u32 n = min(*nseg, cap);
-  for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const u32 a = pbase[s], b = pbase[s + 1];
-    for (u32 c = (a + CH - 1) / CH; c * CH < b; ++c) cstart[c] = s;
-  }
+__global__ void __launch_bounds__(256) k_chunk_map_b(const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                     int njobs) {
+  const int k = job_of(bpre, njobs, blockIdx.x);
+  const Job& J = jobs[k];
+  const u32 s = (blockIdx.x - bpre[k]) * blockDim.x + threadIdx.x;
+  if (s >= J.nseg) return;
+  const u32 a = J.pbase[s], b = J.pbase[s + 1];
+  for (u32 c = (a + CH - 1) / CH; c * CH < b; ++c) J.cstart[c] = s;
 }
 
 // Chunked walk over the global pair index range, done once: every pair is
@@ -169,9 +121,8 @@ __global__ void k_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cst
 // event base + k), and the pairs per cell bucket and events per event bucket
 // are counted (one atomic per run of equal buckets).  k_scatter then places
 // pairs and event indices into their buckets.
-__global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u32* pbase, const u32* cstart,
-                                              u32 NP, u32* pbk, u32* ebk, Pair* raw, Event* ev, u32* err) {
-  const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+SBMT_DEV void walk_chunk(const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk,
+                        u32* ebk, Pair* raw, Event* ev, u32* err, u64 t) {
   const u64 p0 = t * CH;
   if (p0 >= NP) return;
   const u32 p1 = (u32)((p0 + CH < (u64)NP) ? p0 + CH : (u64)NP);
@@ -221,18 +172,27 @@ __global__ void __launch_bounds__(256) k_walk(GridP g, const Seg* segs, const u3
   if (en) atomicAdd(ebk + eb, en);
 }
 
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_walk_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                const u32* __restrict__ bpre, int njobs) {
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const GridP& g = J.g;
+  walk_chunk(g, J.segs, J.pbase, J.cstart, J.NP, j_pcnt(J), j_ecnt(J), J.raw, J.ev, jc(J, JC_ERR),
+             (u64)lb * blockDim.x + threadIdx.x);
+}
+
 // pairs into their cell buckets and event indices into their event buckets
 // (pcur / ecur: bucket cursors, the exclusive scans of the counts)
-__global__ void __launch_bounds__(256) k_scatter(const Pair* raw, u32 NP, const Event* ev, u32 NE, u32* pcur,
-                                                 u32* ecur, Pair* pairs, u32* eidx) {
-  const u32 n = max(NP, NE);
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i < NP) {
-      const Pair pr = raw[i];
-      pairs[warp_inc(pcur, pr.cell >> CB_LOG)] = pr;
-    }
-    if (i < NE) eidx[warp_inc(ecur, ev[i].edge >> EB_LOG)] = i;
+__global__ void __launch_bounds__(256) k_scatter_b(const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                   int njobs) {
+  const int k = job_of(bpre, njobs, blockIdx.x);
+  const Job& J = jobs[k];
+  const u32 i = (blockIdx.x - bpre[k]) * blockDim.x + threadIdx.x;
+  if (i < J.NP) {
+    const Pair pr = J.raw[i];
+    J.pairs[warp_inc(J.pcur, pr.cell >> CB_LOG)] = pr;
   }
+  if (i < J.NE) J.eidx[warp_inc(J.ecur, J.ev[i].edge >> EB_LOG)] = i;
 }
 
 SBMT_DEV Zq event_t(const Event& e) {
@@ -248,12 +208,9 @@ SBMT_DEV Zq event_t(const Event& e) {
 // The registry, small buckets (at most RANK_SMALL events, nearly all of
 // them): a 64-thread block per bucket, each event ranked by a count over
 // the bucket's events held in shared memory.
-constexpr u32 RANK_SMALL = 256;
-__global__ void __launch_bounds__(64) k_rank_small(GridP g, Event* ev, const u32* eidx, const u32* eoff, u32 NVg,
-                                                   double* xy, u32 xy0) {
-  __shared__ u32 s_edge[RANK_SMALL];
-  __shared__ int s_ta[RANK_SMALL], s_tb[RANK_SMALL];
-  const u32 lo = eoff[blockIdx.x], n = eoff[blockIdx.x + 1] - lo;
+SBMT_DEV void rank_small_bucket(const GridP& g, Event* ev, const u32* eidx, const u32* eoff, u32 bucket, u32 NVg,
+                                double* xy, u32 xy0, u32* s_edge, int* s_ta, int* s_tb) {
+  const u32 lo = eoff[bucket], n = eoff[bucket + 1] - lo;
   if (n == 0 || n > RANK_SMALL) return;
   const double invS = 1.0 / (double)g.S;
   u32 me[RANK_SMALL / 64];
@@ -289,19 +246,27 @@ __global__ void __launch_bounds__(64) k_rank_small(GridP g, Event* ev, const u32
   }
 }
 
+template <bool ONE>
+__global__ void __launch_bounds__(64) k_rank_small_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                     const u32* __restrict__ bpre, int njobs) {
+  __shared__ u32 s_edge[RANK_SMALL];
+  __shared__ int s_ta[RANK_SMALL], s_tb[RANK_SMALL];
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const GridP& g = J.g;
+  rank_small_bucket(g, J.ev, J.eidx, J.eoff, lb, J.NVg, J.xy, J.cp.xy0, s_edge, s_ta, s_tb);
+}
+
 // The registry, large buckets (grid-edge buckets along the image border
 // collect thousands of events): a counting sort of the bucket's events by
 // grid edge, then each event ranked among those of its own edge.  A short
 // grid walks over all buckets and skips the small ones.
-__global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eidx, u32* elist, const u32* eoff,
-                                              u32 nbe, u32 NVg, double* xy, u32 xy0) {
-  constexpr int NEB = 1 << EB_LOG;
-  __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
-  __shared__ u32 s_sh[8];
+constexpr int NEB = 1 << EB_LOG;
+SBMT_DEV void rank_large_bucket(const GridP& g, Event* ev, const u32* eidx, u32* elist, const u32* eoff, u32 b,
+                                u32 NVg, double* xy, u32 xy0, u32* s_cnt, u32* s_off, u32* s_cur, u32* s_sh) {
   const double invS = 1.0 / (double)g.S;
-  for (u32 b = blockIdx.x; b < nbe; b += gridDim.x) {
+  {
     const u32 lo = eoff[b], n = eoff[b + 1] - lo;
-    if (n <= RANK_SMALL) continue;
+    if (n <= RANK_SMALL) return;
     const u32 e0 = b << EB_LOG;
     for (int k = threadIdx.x; k < NEB; k += blockDim.x) s_cnt[k] = 0;
     __syncthreads();
@@ -343,50 +308,70 @@ __global__ void __launch_bounds__(256) k_rank(GridP g, Event* ev, const u32* eid
   }
 }
 
+// the large buckets of every job, from the batch's list (filled by the scan
+// of the event bucket counts)
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_rank_big_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                    const BatchDev* bd, const uint2* big) {
+  __shared__ u32 s_cnt[NEB], s_off[NEB], s_cur[NEB];
+  __shared__ u32 s_sh[8];
+  __shared__ Job sJ;
+  const u32 n = bd->nbig;
+  for (u32 it = blockIdx.x; it < n; it += gridDim.x) {
+    const uint2 e = big[it];
+    const Job* jp = &one;
+    if constexpr (!ONE) {
+      __syncthreads();
+      load_job(jobs, (int)e.x, &sJ);
+      jp = &sJ;
+    }
+    const Job& J = *jp;
+    const GridP& g = J.g;
+    rank_large_bucket(g, J.ev, J.eidx, J.elist, J.eoff, e.y, J.NVg, J.xy, J.cp.xy0, s_cnt, s_off, s_cur, s_sh);
+  }
+}
+
 }  // namespace
-
-int launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st) {
-  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
-  k_seg_count<<<grd, 256, 0, st>>>(g, segs, nseg, cap, npairs);
-  return 1;
-}
-
-int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st) {
-  const unsigned grd = (unsigned)std::max<u64>(1, std::min<u64>((cap + 255) / 256, 152u * 64u));
-  k_chunk_map<<<grd, 256, 0, st>>>(pbase, nseg, cap, cstart);
-  return 1;
-}
 
 size_t walk_chunks(u32 NP) { return (NP + CH - 1) / CH; }
 
-int launch_walk(const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk, u32* ebk,
-                Pair* raw, Event* events, u32* err, cudaStream_t st) {
-  const u64 threads = walk_chunks(NP);
-  if (threads == 0) return 0;
-  const unsigned grd = (unsigned)((threads + 255) / 256);
-  k_walk<<<grd, 256, 0, st>>>(g, segs, pbase, cstart, NP, pbk, ebk, raw, events, err);
+int launch_counts_b(const Job* jobs, int njobs, u32* out, cudaStream_t st) {
+  k_counts_b<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, njobs, out);
   return 1;
 }
 
-int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pcur, u32* ecur, Pair* pairs,
-                   u32* eidx, cudaStream_t st) {
-  const u32 n = std::max(NP, NE);
-  if (n == 0) return 0;
-  const unsigned grd = (unsigned)std::min<u64>((n + 255) / 256, 152u * 16u);
-  k_scatter<<<grd, 256, 0, st>>>(raw, NP, events, NE, pcur, ecur, pairs, eidx);
+int launch_chunk_map_b(const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  k_chunk_map_b<<<nblocks, 256, 0, st>>>(jobs, bpre, njobs);
   return 1;
 }
 
-int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, u32 xy0, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
-                        cudaEvent_t ev_b) {
-  if (nbe == 0) return 0;
-  // the large buckets on st2 beside the small ones when given (disjoint buckets)
+int launch_walk_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_walk_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_walk_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  return 1;
+}
+
+int launch_scatter_b(const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  k_scatter_b<<<nblocks, 256, 0, st>>>(jobs, bpre, njobs);
+  return 1;
+}
+
+int launch_rank_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, const BatchPtrs& bp,
+                  cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a, cudaEvent_t ev_b) {
+  if (nblocks == 0) return 0;
   if (st2) {
     if (cudaEventRecord(ev_a, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_a, 0) != cudaSuccess) return -1;
   }
-  k_rank<<<152 * 2, 256, 0, st2 ? st2 : st>>>(g, events, eidx, elist, eoff, nbe, NVg, xy, xy0);
-  k_rank_small<<<nbe, 64, 0, st>>>(g, events, eidx, eoff, NVg, xy, xy0);
+  if (one) {
+    k_rank_big_b<true><<<152 * 2, 256, 0, st2 ? st2 : st>>>(*one, jobs, bp.bd, bp.big);
+    k_rank_small_b<true><<<nblocks, 64, 0, st>>>(*one, jobs, bpre, njobs);
+  } else {
+    k_rank_big_b<false><<<152 * 2, 256, 0, st2 ? st2 : st>>>(Job{}, jobs, bp.bd, bp.big);
+    k_rank_small_b<false><<<nblocks, 64, 0, st>>>(Job{}, jobs, bpre, njobs);
+  }
   if (st2) {
     if (cudaEventRecord(ev_b, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_b, 0) != cudaSuccess) return -1;
   }

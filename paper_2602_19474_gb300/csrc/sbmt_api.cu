@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <sys/stat.h>
+
 #include "sbmt.h"
 #include "sbmt_launch.h"
 
@@ -112,15 +114,27 @@ int build_tables(const GridP& g, Tables& t) {
   return SBMT_OK;
 }
 
+// device memory or an event shared by the meshes of one batch, released
+// with the last of them
+struct Shared {
+  void* ptr = nullptr;
+  cudaEvent_t ev = nullptr;
+  int refs = 0;
+};
+
 struct MeshRec {
   sbmt_mesh id = 0;
-  cudaEvent_t done = nullptr;
-  void* out_block = nullptr;
+  cudaEvent_t done = nullptr;   // completion of the mesh's work
+  Shared* done_sh = nullptr;    // the batch's completion event (done is its event)
+  bool own_done = false;        // done is this mesh's own pooled event
+  Shared* out_sh = nullptr;     // the batch's output block holding this mesh
+  void* out_block = nullptr;    // this mesh's own output block (preprocessed meshes)
   double* xy = nullptr;
   int* tri = nullptr;
   unsigned short* label = nullptr;
   unsigned short* code = nullptr;
   int64_t nv = 0, nt = 0, ncells = 0, nseg_total = 0, ne_total = 0, nc_total = 0, nvg = 0;
+  size_t bytes = 0;  // device bytes of the mesh's outputs (and kept stages)
   // SBMT_COMPACT: per-cell labels and codes, the cut cells' patch list
   int format = SBMT_EXPLICIT;
   unsigned short* cell_label = nullptr;
@@ -154,7 +168,7 @@ struct MeshRec {
 
 }  // namespace
 
-// kernels of the hot path, in launch order (for the per-kernel timing)
+// stages of the hot path, in launch order (for the per-stage timing)
 enum {
   KN_CORNER,
   KN_SEG,
@@ -175,19 +189,30 @@ const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_se
                                             "k_walk", "k_rank", "k_sort", "k_cutcells", "k_emit",
                                             "k_tierg", "k_lattice_xy", "k_preprocess", "k_heat"};
 
-// One stream of work: the context's own stream, or one of the extra streams
-// a batch spreads its images over.  Each lane has its own scratch arena and
-// its own tracing events, so lanes run on separate host threads.
+// The context's stream of work with its side streams, scratch arena, staging
+// buffers and tracing events.
 struct Lane {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  // the Tier-G kernels run on a second stream beside the emission kernel,
-  // forked from and joined back into the lane's stream
+  // the Tier-G kernels (and the registry's large buckets) run on side
+  // streams beside the main kernels, forked from and joined back into the
+  // lane's stream
   cudaStream_t side = nullptr, side2 = nullptr;  // side2: the Tier-G warp kernel
   cudaEvent_t fork = nullptr, join = nullptr, order = nullptr, warp = nullptr;
   // per-call scratch: bump allocation in stream-ordered chunks
   std::vector<std::pair<char*, size_t>> chunks;
   size_t chunk_used = 0, call_bytes = 0;
+  // pinned staging of the job tables, reused once its last copy is done
+  char* stage = nullptr;
+  size_t stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  // mapped pinned memory receiving the counting phase's results
+  u32* cnt_h = nullptr;
+  u32* cnt_d = nullptr;
+  size_t cnt_cap = 0;
+  // the emission phase as a CUDA graph (updated in place call to call)
+  cudaGraphExec_t gexec = nullptr;
+  bool capturing = false;
   // tracing: events around each kernel launch, resolved lazily
   struct Mark {
     int k, kernels;
@@ -197,43 +222,44 @@ struct Lane {
   std::vector<Mark> pending;
 };
 
-// images a batch meshes at once, each on its own lane (SBMT_BATCH_LANES
-// overrides, 1..32)
-int batch_lanes() {
-  static const int n = [] {
-    const char* e = std::getenv("SBMT_BATCH_LANES");
-    const int v = e ? std::atoi(e) : 0;
-    return v >= 1 && v <= 32 ? v : 12;
-  }();
-  return n;
-}
+// launch parameters of the batched path (chosen per size class by the tuner)
+struct Tune {
+  int cut_blocks_per_sm = 8;     // persistent cut-cell kernel, 128 threads a block
+  int tierg_blocks_per_sm = 24;  // persistent Tier-G thread kernel, 64 threads a block
+  int fork = 1;                  // Tier-G and the large registry buckets on side streams
+  int graph = 0;                 // the emission phase captured into a CUDA graph
+};
 
 struct sbmt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::mutex mu;   // one API call at a time
-  std::mutex reg;  // meshes, ids, events, pinned slots, tables: shared by the lanes of a batch
+  std::mutex reg;  // meshes, ids, events, pinned slots, tables
   std::map<sbmt_mesh, MeshRec*> meshes;
   sbmt_mesh next = 1;
   Lane main;
-  std::vector<Lane*> extra;
-  bool in_batch = false;  // lanes share the tables: no eviction while set
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[KN_COUNT] = {};
   int64_t prof_n[KN_COUNT] = {};
-  // grid tables per (W, H, h, origin), kept on the device
+  // grid tables per (W, H, h, origin), kept on the device; entries uploaded
+  // together share one device block
   struct TableEntry {
     Tables host;
     i64* dev = nullptr;
-    cudaEvent_t ready = nullptr;  // recorded after the upload
+    Shared* block = nullptr;
     uint64_t last_use = 0;
   };
   std::map<std::array<i64, 6>, TableEntry> tables;
   uint64_t tick = 0;
-  // pinned slots for the per-mesh status words
-  std::vector<u32*> pinned_slabs;
+  // pinned slots for the per-mesh status words (mapped: kernels write them)
+  std::vector<std::pair<u32*, u32*>> pinned_slabs;  // host, device
   std::vector<u32*> pinned_free;
+  // tuning: the launch parameters in use, and per size class those chosen
+  // by mesh_autotune (also read from and written to the tuning file)
+  Tune tune;
+  std::map<std::string, Tune> tuned;
+  bool tuned_loaded = false;
 };
 
 namespace {
@@ -262,19 +288,17 @@ void prof_collect_lane(sbmt_ctx* c, Lane* L) {
   }
   L->pending.clear();
 }
-void prof_collect(sbmt_ctx* c) {
-  prof_collect_lane(c, &c->main);
-  for (Lane* L : c->extra) prof_collect_lane(c, L);
-}
+void prof_collect(sbmt_ctx* c) { prof_collect_lane(c, &c->main); }
 
-// brackets one kernel launch with events on the lane's stream when tracing
+// brackets one launcher call with events on the lane's stream when tracing
+// (not while the lane's stream is being captured into a graph)
 struct ProfScope {
   Lane* L;
   cudaStream_t s;
   int k, kernels = 0;
   cudaEvent_t a = nullptr;
   ProfScope(sbmt_ctx* c, Lane* L_, int k_, cudaStream_t s_) : L(L_), s(s_), k(k_) {
-    if (c->prof && (a = take_event(L->ev_pool))) cudaEventRecord(a, s);
+    if (c->prof && !L->capturing && (a = take_event(L->ev_pool))) cudaEventRecord(a, s);
   }
   ~ProfScope() {
     if (!a) return;
@@ -332,10 +356,13 @@ void lane_release(Lane* L) {
   cudaStreamSynchronize(L->stream);
   for (cudaEvent_t e : L->ev_pool) cudaEventDestroy(e);
   L->ev_pool.clear();
+  if (L->gexec) cudaGraphExecDestroy(L->gexec), L->gexec = nullptr;
+  if (L->stage) cudaFreeHost(L->stage), L->stage = nullptr;
+  if (L->cnt_h) cudaFreeHost(L->cnt_h), L->cnt_h = nullptr;
   if (L->own_stream) cudaStreamDestroy(L->stream);
   if (L->side) cudaStreamSynchronize(L->side), cudaStreamDestroy(L->side);
   if (L->side2) cudaStreamSynchronize(L->side2), cudaStreamDestroy(L->side2);
-  for (cudaEvent_t e : {L->fork, L->join, L->order, L->warp})
+  for (cudaEvent_t e : {L->fork, L->join, L->order, L->warp, L->stage_ev})
     if (e) cudaEventDestroy(e);
 }
 
@@ -358,12 +385,50 @@ int lane_side(Lane* L) {
   return SBMT_OK;
 }
 
+// pinned staging of `bytes` for a host-to-device copy on the lane's stream;
+// waits until the previous copy from it is done
+int stage_begin(Lane* L, size_t bytes, char** out) {
+  if (!L->stage_ev && cudaEventCreateWithFlags(&L->stage_ev, cudaEventDisableTiming) != cudaSuccess)
+    return fail(SBMT_ECUDA, "staging event");
+  if (cudaEventSynchronize(L->stage_ev) != cudaSuccess) return fail(SBMT_ECUDA, "staging wait");
+  if (bytes > L->stage_cap) {
+    if (L->stage) cudaFreeHost(L->stage), L->stage = nullptr, L->stage_cap = 0;
+    const size_t want = std::max<size_t>(bytes, (size_t)1 << 20) * 2;
+    if (cudaMallocHost(&L->stage, want) != cudaSuccess) return fail(SBMT_ENOMEM, "pinned staging of %zu bytes", want);
+    L->stage_cap = want;
+  }
+  *out = L->stage;
+  return SBMT_OK;
+}
+int stage_copy(Lane* L, void* dst, size_t bytes) {
+  if (cudaMemcpyAsync(dst, L->stage, bytes, cudaMemcpyHostToDevice, L->stream) != cudaSuccess ||
+      cudaEventRecord(L->stage_ev, L->stream) != cudaSuccess)
+    return fail(SBMT_ECUDA, "job table upload");
+  return SBMT_OK;
+}
+// mapped pinned words for the counting phase's results
+int lane_counts(Lane* L, size_t words) {
+  if (words <= L->cnt_cap) return SBMT_OK;
+  if (L->cnt_h) cudaFreeHost(L->cnt_h), L->cnt_h = nullptr, L->cnt_cap = 0;
+  const size_t want = std::max<size_t>(words, 4096) * 2;
+  if (cudaHostAlloc(&L->cnt_h, want * sizeof(u32), cudaHostAllocMapped) != cudaSuccess)
+    return fail(SBMT_ENOMEM, "pinned counts");
+  if (cudaHostGetDevicePointer(&L->cnt_d, L->cnt_h, 0) != cudaSuccess) return fail(SBMT_ECUDA, "mapped counts");
+  L->cnt_cap = want;
+  return SBMT_OK;
+}
+
 // callers hold ctx->reg
 u32* pinned_slot(sbmt_ctx* ctx) {
   if (ctx->pinned_free.empty()) {
     u32* slab = nullptr;
-    if (cudaMallocHost(&slab, 1024 * 8 * sizeof(u32)) != cudaSuccess) return nullptr;
-    ctx->pinned_slabs.push_back(slab);
+    u32* dslab = nullptr;
+    if (cudaHostAlloc(&slab, 1024 * 8 * sizeof(u32), cudaHostAllocMapped) != cudaSuccess) return nullptr;
+    if (cudaHostGetDevicePointer(&dslab, slab, 0) != cudaSuccess) {
+      cudaFreeHost(slab);
+      return nullptr;
+    }
+    ctx->pinned_slabs.push_back({slab, dslab});
     for (int k = 1023; k >= 0; --k) ctx->pinned_free.push_back(slab + 8 * k);
   }
   u32* p = ctx->pinned_free.back();
@@ -371,71 +436,123 @@ u32* pinned_slot(sbmt_ctx* ctx) {
   std::memset(p, 0, 8 * sizeof(u32));
   return p;
 }
+// the device address of a pinned slot; callers hold ctx->reg
+u32* pinned_dev(sbmt_ctx* ctx, u32* host) {
+  for (auto& s : ctx->pinned_slabs)
+    if (host >= s.first && host < s.first + 1024 * 8) return s.second + (host - s.first);
+  return nullptr;
+}
 
-// grid tables for one configuration, built once and kept on the device.
-// The host build and the upload run outside ctx->reg, so the lanes of a
-// batch build different tables at once; a lane that finds an entry another
-// lane is still uploading waits for its event.  An evicted entry may still be
-// read by work in flight on any lane, so eviction waits for the device, and
-// is put off while a batch runs.
-int get_tables(sbmt_ctx* ctx, Lane* lane, const GridP& g, const Tables** host, const i64** dev) {
-  const std::array<i64, 6> key{g.W, g.H, g.p, g.q, g.ox, g.oy};
+// grid tables for a batch of configurations, built once and kept on the
+// device.  The entries a call adds are built on the host and uploaded
+// together, in one block shared by them.  An evicted entry may still be
+// read by work in flight, so eviction waits for the device; entries the
+// call uses are never evicted by it.
+int get_tables_many(sbmt_ctx* ctx, Lane* lane, const std::vector<GridP>& G, std::vector<const Tables*>& host,
+                    std::vector<const i64*>& dev) {
+  const size_t n = G.size();
+  host.assign(n, nullptr), dev.assign(n, nullptr);
+  std::vector<std::array<i64, 6>> keys(n);
+  std::vector<size_t> missing;
+  std::map<std::array<i64, 6>, size_t> first_missing;
   {
     std::lock_guard<std::mutex> lk(ctx->reg);
-    auto it = ctx->tables.find(key);
-    if (it != ctx->tables.end()) {
-      it->second.last_use = ++ctx->tick;
-      *host = &it->second.host;
-      *dev = it->second.dev;
-      if (cudaStreamWaitEvent(lane->stream, it->second.ready, 0) != cudaSuccess)
-        return fail(SBMT_ECUDA, "table wait");
-      return SBMT_OK;
+    ++ctx->tick;
+    for (size_t k = 0; k < n; ++k) {
+      const GridP& g = G[k];
+      keys[k] = {g.W, g.H, g.p, g.q, g.ox, g.oy};
+      auto it = ctx->tables.find(keys[k]);
+      if (it != ctx->tables.end()) {
+        it->second.last_use = ctx->tick;
+      } else if (!first_missing.count(keys[k])) {
+        first_missing[keys[k]] = k;
+        missing.push_back(k);
+      }
     }
-    if (ctx->tables.size() >= 1024 && !ctx->in_batch) {  // evict the least recently used entry
-      auto old = ctx->tables.begin();
-      for (auto jt = ctx->tables.begin(); jt != ctx->tables.end(); ++jt)
-        if (jt->second.last_use < old->second.last_use) old = jt;
+    if (ctx->tables.size() + missing.size() > 1024) {  // evict the least recently used entries
       cudaDeviceSynchronize();
-      cudaFree(old->second.dev);
-      cudaEventDestroy(old->second.ready);
-      ctx->tables.erase(old);
+      std::vector<std::pair<uint64_t, std::array<i64, 6>>> age;
+      for (auto& kv : ctx->tables)
+        if (kv.second.last_use != ctx->tick) age.push_back({kv.second.last_use, kv.first});
+      std::sort(age.begin(), age.end());
+      for (size_t a = 0; a < age.size() && ctx->tables.size() + missing.size() > 1024; ++a) {
+        auto it = ctx->tables.find(age[a].second);
+        Shared* b = it->second.block;
+        if (--b->refs == 0) cudaFree(b->ptr), delete b;
+        ctx->tables.erase(it);
+      }
     }
   }
-  sbmt_ctx::TableEntry te;
-  int rc = build_tables(g, te.host);
-  if (rc) return rc;
-  const Tables& tb = te.host;
-  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
-  std::vector<i64> all;
-  all.insert(all.end(), tb.clo.begin(), tb.clo.end());
-  all.insert(all.end(), tb.chi.begin(), tb.chi.end());
-  all.insert(all.end(), tb.cbase.begin(), tb.cbase.end());
-  all.insert(all.end(), tb.vlo.begin(), tb.vlo.end());
-  all.insert(all.end(), tb.vhi.begin(), tb.vhi.end());
-  all.insert(all.end(), tb.vbase.begin(), tb.vbase.end());
-  const size_t nl = all.size();
-  all.resize(nl + nrows);
-  std::memcpy(all.data() + nl, tb.lrow.data(), tb.lrow.size() * sizeof(int));
-  (void)nvr;
-  if (cudaMallocAsync(&te.dev, all.size() * sizeof(i64), lane->stream) != cudaSuccess)
-    return fail(SBMT_ENOMEM, "table allocation");
-  // from pageable memory the copy has read `all` when the call returns
-  if (cudaMemcpyAsync(te.dev, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, lane->stream) ||
-      cudaEventCreateWithFlags(&te.ready, cudaEventDisableTiming) || cudaEventRecord(te.ready, lane->stream))
-    return fail(SBMT_ECUDA, "table upload");
-  std::lock_guard<std::mutex> lk(ctx->reg);
-  auto ins = ctx->tables.try_emplace(key, std::move(te));
-  auto it = ins.first;
-  if (!ins.second) {
-    // another lane built the same tables meanwhile: use those
-    cudaFreeAsync(te.dev, lane->stream);
-    cudaEventDestroy(te.ready);
-    if (cudaStreamWaitEvent(lane->stream, it->second.ready, 0) != cudaSuccess) return fail(SBMT_ECUDA, "table wait");
+  if (!missing.empty()) {
+    std::vector<Tables> built(missing.size());
+    std::vector<size_t> off(missing.size());
+    size_t words = 0;
+    for (size_t u = 0; u < missing.size(); ++u) {
+      if (int rc = build_tables(G[missing[u]], built[u])) return rc;
+      const Tables& tb = built[u];
+      off[u] = words;
+      words += (6 * tb.clo.size() + 3 * tb.vlo.size()) + (tb.lrow.size() + 1) / 2;
+      words = (words + 7) & ~(size_t)7;
+    }
+    std::vector<i64> all(std::max<size_t>(words, 1));
+    for (size_t u = 0; u < missing.size(); ++u) {
+      const Tables& tb = built[u];
+      i64* o = all.data() + off[u];
+      for (const std::vector<i64>* v : {&tb.clo, &tb.chi, &tb.cbase, &tb.vlo, &tb.vhi, &tb.vbase}) {
+        std::copy(v->begin(), v->end(), o);
+        o += v->size();
+      }
+      std::memcpy(o, tb.lrow.data(), tb.lrow.size() * sizeof(int));
+    }
+    Shared* blk = new Shared();
+    if (cudaMallocAsync(&blk->ptr, all.size() * sizeof(i64), lane->stream) != cudaSuccess) {
+      delete blk;
+      return fail(SBMT_ENOMEM, "table allocation");
+    }
+    // from pageable memory the copy has read `all` when the call returns
+    if (cudaMemcpyAsync(blk->ptr, all.data(), all.size() * sizeof(i64), cudaMemcpyHostToDevice, lane->stream) !=
+        cudaSuccess) {
+      cudaFreeAsync(blk->ptr, lane->stream);
+      delete blk;
+      return fail(SBMT_ECUDA, "table upload");
+    }
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    for (size_t u = 0; u < missing.size(); ++u) {
+      sbmt_ctx::TableEntry te;
+      te.host = std::move(built[u]);
+      te.dev = (i64*)blk->ptr + off[u];
+      te.block = blk;
+      te.last_use = ctx->tick;
+      blk->refs++;
+      ctx->tables.emplace(keys[missing[u]], std::move(te));
+    }
   }
-  it->second.last_use = ++ctx->tick;
-  *host = &it->second.host;
-  *dev = it->second.dev;
+  std::lock_guard<std::mutex> lk(ctx->reg);
+  for (size_t k = 0; k < n; ++k) {
+    auto it = ctx->tables.find(keys[k]);
+    host[k] = &it->second.host;
+    dev[k] = it->second.dev;
+  }
   return SBMT_OK;
+}
+
+int get_tables(sbmt_ctx* ctx, Lane* lane, const GridP& g, const Tables** host, const i64** dev) {
+  std::vector<GridP> G{g};
+  std::vector<const Tables*> h;
+  std::vector<const i64*> d;
+  if (int rc = get_tables_many(ctx, lane, G, h, d)) return rc;
+  *host = h[0], *dev = d[0];
+  return SBMT_OK;
+}
+
+// the device tables of one configuration into its grid
+void set_grid_tables(GridP& g, const Tables& tb, const i64* dt) {
+  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
+  g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
+  g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
+  g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
+  g.lrow = (const int*)(dt + 3 * nrows + 3 * nvr);
+  g.ncells = tb.ncells, g.nverts = tb.nverts;
 }
 
 template <typename T>
@@ -460,7 +577,9 @@ void destroy_mesh(sbmt_ctx* ctx, MeshRec* m, cudaStream_t st) {
   if (m->done) cudaEventSynchronize(m->done);
   free_list(st, m->scratch);
   if (m->out_block) cudaFreeAsync(m->out_block, st);
-  if (m->done) ctx->ev_pool.push_back(m->done);
+  if (m->out_sh && --m->out_sh->refs == 0) cudaFreeAsync(m->out_sh->ptr, st), delete m->out_sh;
+  if (m->own_done && m->done) ctx->ev_pool.push_back(m->done);
+  if (m->done_sh && --m->done_sh->refs == 0) ctx->ev_pool.push_back(m->done_sh->ev), delete m->done_sh;
   if (m->h_info) ctx->pinned_free.push_back(m->h_info);
   delete m;
 }
@@ -494,267 +613,514 @@ int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false)
   return SBMT_OK;
 }
 
-// the whole path for one image, enqueued on one lane
-// fork: run the Tier-G kernels on the lane's second stream beside the
-// emission (single meshes; a batch's lanes already fill the device)
-int mesh_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out, bool fork) {
-  int rc = check_params(img, pr);
-  if (rc) return rc;
-  cudaStream_t st = lane->stream;
-  CK(cudaSetDevice(ctx->device));
+GridP grid_of(const sbmt_image& img, const sbmt_params& pr) {
   GridP g{};
-  g.W = img->width, g.H = img->height;
-  g.p = pr->h_num, g.q = pr->h_den, g.S = 6 * g.q;
-  g.ox = 3 * g.q * (i64)pr->origin2x, g.oy = 3 * g.q * (i64)pr->origin2y;
-  const Tables* tbp;
-  const i64* dt;
-  if ((rc = get_tables(ctx, lane, g, &tbp, &dt))) return rc;
-  const Tables& tb = *tbp;
-  if (tb.ncells >= (1ll << 31) || 3 * tb.nverts >= (1ll << 32))
-    return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)tb.ncells);
-  MeshRec* m = new MeshRec();
-  m->W = g.W, m->H = g.H;
-  m->keep = (pr->flags & SBMT_KEEP_STAGES) != 0;
-  std::vector<void*> tmp;  // device memory freed at the end of the call
+  g.W = img.width, g.H = img.height;
+  g.p = pr.h_num, g.q = pr.h_den, g.S = 6 * g.q;
+  g.ox = 3 * g.q * (i64)pr.origin2x, g.oy = 3 * g.q * (i64)pr.origin2y;
+  return g;
+}
+
+// room for the boundary segments of an image before they are counted: a
+// quarter of its pixel corners (real images hold a few percent), at most the
+// bound of two per corner; an image with more is counted exactly and redone
+u32 seg_cap_guess(int W, int H) {
+  const u64 corners = (u64)(W + 1) * (u64)(H + 1);
+  return (u32)std::min<u64>(2 * corners, corners / 4 + 4096);
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct RunOpts {
+  bool fork = true;    // Tier-G and the large registry buckets on side streams
+  bool graph = false;  // the emission phase captured into a CUDA graph
+  bool stall = false;  // test of the device wait bound (SBMT_DEBUG_STALL_SCAN)
+  int cut_blocks_per_sm = 8, tierg_blocks_per_sm = 24;
+};
+
+// per-stage block prefix over the jobs
+template <class F>
+std::vector<u32> prefix_of(int n, F blocks) {
+  std::vector<u32> p(n + 1, 0);
+  for (int k = 0; k < n; ++k) p[k + 1] = p[k] + (u32)blocks(k);
+  return p;
+}
+
+// The whole path for a batch of images (one image is a batch of one), on
+// one lane: a counting phase (segments and pairs per image, one launch per
+// stage over all images), one host synchronisation to size the buffers, and
+// an emission phase (one launch per stage, the variable-size stages
+// persistent over batch-wide work queues), optionally as a CUDA graph.
+int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbmt_params* prs, int nprs,
+             sbmt_mesh* out, const RunOpts& opt) {
+  if (n == 0) return SBMT_OK;
+  for (int k = 0; k < n; ++k)
+    if (int rc = check_params(imgs + k, prs + (nprs == 1 ? 0 : k))) return rc;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = lane->stream;
+  std::vector<GridP> G(n);
+  for (int k = 0; k < n; ++k) G[k] = grid_of(imgs[k], prs[nprs == 1 ? 0 : k]);
+  std::vector<const Tables*> TB;
+  std::vector<const i64*> DT;
+  if (int rc = get_tables_many(ctx, lane, G, TB, DT)) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (TB[k]->ncells >= (1ll << 31) || 3 * TB[k]->nverts >= (1ll << 32))
+      return fail(SBMT_EINVAL, "mesh too large (%lld cells)", (long long)TB[k]->ncells);
+    set_grid_tables(G[k], *TB[k], DT[k]);
+  }
+  std::vector<MeshRec*> M(n, nullptr);
   arena_begin(lane);
   auto bail = [&](int code) {
-    free_list(st, tmp);
     arena_end(lane);
     std::lock_guard<std::mutex> lk(ctx->reg);
-    destroy_mesh(ctx, m, st);
+    for (MeshRec* m : M)
+      if (m) destroy_mesh(ctx, m, st);
     return code;
   };
+  std::vector<Job> J(n);
   {
     std::lock_guard<std::mutex> lk(ctx->reg);
-    m->h_info = pinned_slot(ctx);
-  }
-  if (!m->h_info) return bail(fail(SBMT_ENOMEM, "pinned info"));
-  // image on the device
-  const unsigned char* dimg;
-  i64 pitch;
-  if (img->on_device) {
-    dimg = (const unsigned char*)img->data;
-    pitch = img->pitch_bytes;
-  } else {
-    unsigned char* d;
-    pitch = (i64)img->width * img->dtype;
-    if ((rc = aalloc(lane, &d, (size_t)pitch * img->height))) return bail(rc);
-    if (cudaMemcpy2DAsync(d, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
-      return bail(fail(SBMT_ECUDA, "image upload"));
-    dimg = d;
-  }
-  const i64 nrows = (i64)tb.clo.size(), nvr = (i64)tb.vlo.size();
-  g.j0 = (int)tb.j0, g.nrows = (int)nrows, g.vj0 = (int)tb.vj0, g.nvrows = (int)nvr;
-  g.clo = dt, g.chi = dt + nrows, g.cbase = dt + 2 * nrows;
-  g.vlo = dt + 3 * nrows, g.vhi = dt + 3 * nrows + nvr, g.vbase = dt + 3 * nrows + 2 * nvr;
-  g.lrow = (const int*)(dt + 3 * nrows + 3 * nvr);
-  g.ncells = tb.ncells, g.nverts = tb.nverts;
-
-  // every counter of the call, zeroed by one memset: the vertex count (u64),
-  // the u32 counters (err, cut cells, Tier-G cells and their triangles next
-  // to each other: the mesh's status words), the bucket counts of pairs and
-  // events, the buckets' extra triangles and inside vertices, the Tier-G
-  // per-size counts
-  const u32 nbc = (u32)((tb.ncells + (1 << CB_LOG) - 1) >> CB_LOG);
-  const u32 nbe = (u32)((3 * tb.nverts + (1 << EB_LOG) - 1) >> EB_LOG);
-  const size_t zwords = 16 + (nbc + 1) + (nbe + 1) + 2 * ((size_t)nbc + 1) + 3 * (TIERG_TN + 2);
-  u32* zero;
-  if ((rc = aalloc(lane, &zero, zwords))) return bail(rc);
-  CK(cudaMemsetAsync(zero, 0, zwords * sizeof(u32), st));
-  unsigned long long* cnt64 = (unsigned long long*)zero;
-  u32* cnt32 = zero + 8;
-  u32 *nseg = cnt32 + 0, *nwlist = cnt32 + 1, *err = cnt32 + 2, *nrec = cnt32 + 3, *nglist = cnt32 + 4,
-      *ngtri = cnt32 + 5, *nover = cnt32 + 6;
-  u32* pcnt = zero + 16;
-  u32* ecnt = pcnt + nbc + 1;
-  u32* bextra = ecnt + nbe + 1;
-  u32* bchain = bextra + nbc + 1;
-  u32* gcnt = bchain + nbc + 1;
-
-  // K1a
-  const int W = g.W, H = g.H;
-  const int wpr = (W + 1 + 31) / 32, wpc = (H + 1 + 31) / 32;
-  u32 *vrow, *vcol;
-  if ((rc = aalloc(lane, &vrow, (size_t)wpr * (H + 1)))) return bail(rc);
-  if ((rc = aalloc(lane, &vcol, (size_t)wpc * (W + 1)))) return bail(rc);
-  TRACE(KN_CORNER, launch_corner_bits(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, cnt64 + 0, st));
-  unsigned long long h64[4];
-  CK(cudaMemcpyAsync(h64, cnt64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const u64 NC = h64[0];
-  // K1b: every vertex starts at most two runs (+x and +y)
-  const u32 seg_cap = (u32)std::max<u64>(2 * NC, 1);
-  Seg* segs;
-  if ((rc = m->keep ? dalloc(lane, &segs, seg_cap, m->scratch) : aalloc(lane, &segs, seg_cap))) return bail(rc);
-  TRACE(KN_SEG, launch_segments(dimg, pitch, img->dtype, W, H, vrow, wpr, vcol, wpc, segs, seg_cap, nseg, err, st));
-  // K2: pairs per segment in closed form and their scan -> fixed pair and
-  // event indices of every segment
-  u32 *npairs, *pbase, *sscr;
-  const size_t scr_words = std::max({scan_scratch_words(seg_cap), scan_scratch_words(nbc), scan_scratch_words(nbe)});
-  if ((rc = aalloc(lane, &npairs, seg_cap))) return bail(rc);
-  if ((rc = aalloc(lane, &pbase, (size_t)seg_cap + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &sscr, scr_words + 1))) return bail(rc);
-  TRACE(KN_TCOUNT, launch_seg_count(g, segs, nseg, seg_cap, npairs, st));
-  TRACE(KN_SCAN, launch_scan(npairs, 1, pbase, seg_cap, sscr, st));
-  u32 h32[4];
-  CK(cudaMemcpyAsync(h32, cnt32, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h32 + 3, pbase + seg_cap, sizeof(u32), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (h32[2]) return bail(fail(SBMT_EINTERNAL, "device check failed during extraction (0x%x)", h32[2]));
-  const u32 nsegs = h32[0];
-  if (nsegs > seg_cap) return bail(fail(SBMT_EINTERNAL, "segment count %u above bound %u", nsegs, seg_cap));
-  const u64 NP = h32[3], NE = NP - nsegs;
-  const u64 NVg = (u64)tb.nverts;
-  const u64 V = NVg + NE + NC, T = (u64)tb.ncells + 2 * NC + 2 * NE;
-  if (V >= (1ull << 31) || T >= (1ull << 31) || NP >= (1ull << 31))
-    return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T));
-  // buckets: pairs by cell id, events by grid-edge id
-  u32 *poff, *eoff, *pcur, *ecur;
-  if ((rc = aalloc(lane, &poff, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &eoff, nbe + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &pcur, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &ecur, nbe + 1))) return bail(rc);
-  Pair *pairs, *sorted;
-  Event* ev;
-  CutRec* recs;
-  u32 *bcut, *bbase, *extra_scan, *chain_scan, *olist, *wlist, *elist, *eidx;
-  TStage* stg;
-  u32* cstart;
-  if ((rc = aalloc(lane, &cstart, walk_chunks((u32)NP) + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &pairs, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &sorted, NP))) return bail(rc);
-  if ((rc = m->keep ? dalloc(lane, &ev, NE, m->scratch) : aalloc(lane, &ev, NE))) return bail(rc);
-  if ((rc = aalloc(lane, &eidx, NE))) return bail(rc);
-  // K2: one walk (pairs in their global order, in the sorted buffer for now;
-  // events at their fixed indices; bucket counts), then the bucket scans and
-  // the scatter into buckets
-  TRACE(KN_TCOUNT, launch_chunk_map(pbase, nseg, seg_cap, cstart, st));
-  TRACE(KN_TEMIT, launch_walk(g, segs, pbase, cstart, (u32)NP, pcnt, ecnt, sorted, ev, err, st));
-  if (nbc <= SCAN_ONE && nbe <= SCAN_ONE) {
-    TRACE(KN_SCAN, launch_scan_pair(pcnt, poff, pcur, nbc, ecnt, eoff, ecur, nbe, st));
-  } else {
-    TRACE(KN_SCAN, launch_scan(pcnt, 1, poff, nbc, sscr, st));
-    TRACE(KN_SCAN, launch_scan(ecnt, 1, eoff, nbe, sscr, st));
-    CK(cudaMemcpyAsync(pcur, poff, (nbc + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(ecur, eoff, (nbe + 1) * sizeof(u32), cudaMemcpyDeviceToDevice, st));
-  }
-  TRACE(KN_TEMIT, launch_scatter(sorted, (u32)NP, ev, (u32)NE, pcur, ecur, pairs, eidx, st));
-  if ((rc = m->keep ? dalloc(lane, &recs, NP, m->scratch) : aalloc(lane, &recs, NP))) return bail(rc);
-  if ((rc = m->keep ? dalloc(lane, &bcut, nbc + 1, m->scratch) : aalloc(lane, &bcut, nbc + 1))) return bail(rc);
-  if ((rc = m->keep ? dalloc(lane, &bbase, nbc + 1, m->scratch) : aalloc(lane, &bbase, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &extra_scan, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &chain_scan, nbc + 1))) return bail(rc);
-  if ((rc = aalloc(lane, &stg, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &wlist, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &olist, NP))) return bail(rc);
-  if ((rc = aalloc(lane, &elist, NE))) return bail(rc);
-  // outputs.  The compact format stores the vertices after the lattice, the
-  // per-cell label and code, and the patch triangles of the cut cells (at
-  // most the extra triangles plus one per cut cell, and cut cells <= pairs).
-  const bool compact = pr->format == SBMT_COMPACT;
-  m->format = pr->format;
-  const u64 nxy = compact ? V - NVg : V, ntr = compact ? (T - (u64)tb.ncells) + NP : T;
-  const size_t bxy = 16 * nxy, btri = 12 * ntr, blab = 2 * ntr, bcode = 2 * ntr;
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t off_tri = up(bxy), off_lab = up(off_tri + btri), off_code = up(off_lab + blab);
-  const size_t off_cl = up(off_code + bcode), off_cc = up(off_cl + (compact ? 2 * (size_t)tb.ncells : 0));
-  const size_t off_pc = up(off_cc + (compact ? 2 * (size_t)tb.ncells : 0));
-  const size_t off_po = up(off_pc + (compact ? 4 * NP : 0));
-  const size_t off_ov = up(off_po + (compact ? 4 * (NP + 1) : 0));
-  const size_t total = off_ov + 4 * (size_t)OVER_CAP + 256;
-  if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
-    return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
-  char* ob = (char*)m->out_block;
-  m->xy = (double*)ob;
-  m->tri = (int*)(ob + off_tri);
-  m->label = (unsigned short*)(ob + off_lab);
-  m->code = (unsigned short*)(ob + off_code);
-  m->over_cells = (u32*)(ob + off_ov);
-  CompactOut cp{0, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
-  u32* cut_scan = nullptr;
-  if (compact) {
-    m->cell_label = (unsigned short*)(ob + off_cl), m->cell_code = (unsigned short*)(ob + off_cc);
-    m->patch_cell = (u32*)(ob + off_pc), m->patch_off = (u32*)(ob + off_po);
-    if ((rc = aalloc(lane, &cut_scan, nbc + 1))) return bail(rc);
-    cp = CompactOut{1, (u32)NVg, m->cell_label, m->cell_code, m->patch_cell, m->patch_off, cut_scan};
-    if (nbc == 0) CK(cudaMemsetAsync(m->patch_off, 0, sizeof(u32), st));
-  }
-  m->nv = (int64_t)V, m->nt = (int64_t)T, m->ncells = tb.ncells;
-  m->nseg_total = nsegs, m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NC, m->nvg = (int64_t)NVg;
-  // registry, K3, scans, K4, K4-G, lattice coordinates
-  if (fork && (rc = lane_side(lane))) return bail(rc);
-  int nrk = 0;
-  TRACE(KN_RANK, nrk = launch_rank_events(g, ev, eidx, elist, eoff, nbe, (u32)NVg, m->xy, cp.xy0, st,
-                                          fork ? lane->side : nullptr, lane->fork, lane->join));
-  if (nrk < 0) return bail(fail(SBMT_ECUDA, "registry stream events"));
-  TRACE(KN_SORT, launch_sort(pairs, sorted, poff, nbc, recs, nrec, bcut, bbase, st));
-  TRACE(KN_CUTCELLS, launch_cutcells(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, nrec, bextra, bchain, stg,
-                                     nglist, ngtri, gcnt, err, st));
-  if (nbc <= SCAN_ONE) {
-    TRACE(KN_SCAN, launch_scan_pair(bextra, extra_scan, nullptr, nbc, bchain, chain_scan, nullptr, nbc, st));
-  } else {
-    TRACE(KN_SCAN, launch_scan(bextra, 1, extra_scan, nbc, sscr, st));
-    TRACE(KN_SCAN, launch_scan(bchain, 1, chain_scan, nbc, sscr, st));
-  }
-  if (compact) {
-    if (nbc <= SCAN_ONE) {
-      TRACE(KN_SCAN, launch_scan_pair(bcut, cut_scan, nullptr, nbc, nullptr, nullptr, nullptr, 0, st));
-    } else {
-      TRACE(KN_SCAN, launch_scan(bcut, 1, cut_scan, nbc, sscr, st));
+    for (int k = 0; k < n; ++k) {
+      const sbmt_params& pr = prs[nprs == 1 ? 0 : k];
+      MeshRec* m = M[k] = new MeshRec();
+      m->W = G[k].W, m->H = G[k].H, m->keep = (pr.flags & SBMT_KEEP_STAGES) != 0, m->format = pr.format;
+      m->h_info = pinned_slot(ctx);
+      if (!m->h_info) break;
+      std::memset(&J[k], 0, sizeof(Job));
+      J[k].hinfo = pinned_dev(ctx, m->h_info);
     }
   }
+  for (int k = 0; k < n; ++k)
+    if (!M[k] || !M[k]->h_info) return bail(fail(SBMT_ENOMEM, "pinned status words"));
+  int rc;
+  // images on the device, grids, bucket counts
+  for (int k = 0; k < n; ++k) {
+    const sbmt_image& img = imgs[k];
+    Job& j = J[k];
+    j.g = G[k], j.dtype = img.dtype;
+    if (img.on_device) {
+      j.img = (const unsigned char*)img.data, j.pitch = img.pitch_bytes;
+    } else {
+      unsigned char* d;
+      j.pitch = (i64)img.width * img.dtype;
+      if ((rc = aalloc(lane, &d, (size_t)j.pitch * img.height))) return bail(rc);
+      if (cudaMemcpy2DAsync(d, j.pitch, img.data, img.pitch_bytes, j.pitch, img.height, cudaMemcpyHostToDevice, st))
+        return bail(fail(SBMT_ECUDA, "image upload"));
+      j.img = d;
+    }
+    j.wpr = (G[k].W + 1 + 31) / 32, j.wpc = (G[k].H + 1 + 31) / 32;
+    j.nbc = (u32)((G[k].ncells + (1 << CB_LOG) - 1) >> CB_LOG);
+    j.nbe = (u32)((3 * G[k].nverts + (1 << EB_LOG) - 1) >> EB_LOG);
+    j.NVg = (u32)G[k].nverts;
+  }
+  // ---------------- counting phase ----------------
+  std::vector<u32> cap(n);
+  for (int k = 0; k < n; ++k) cap[k] = seg_cap_guess(G[k].W, G[k].H);
+  if ((rc = lane_counts(lane, 8 * (size_t)n))) return bail(rc);
+  for (int attempt = 0;; ++attempt) {
+    std::vector<size_t> zoff(n);
+    size_t zw = 0;
+    for (int k = 0; k < n; ++k) zoff[k] = zw, zw += (job_zero_words(J[k].nbc, J[k].nbe) + 63) & ~(size_t)63;
+    const std::vector<u32> tpre = prefix_of(n, [&](int k) { return mscan_tiles(cap[k]); });
+    const u32 ntiles = tpre[n];
+    u32* zero;
+    const size_t zall = zw + 2 * (size_t)ntiles + 64;
+    if ((rc = aalloc(lane, &zero, zall))) return bail(rc);
+    CK(cudaMemsetAsync(zero, 0, zall * sizeof(u32), st));
+    unsigned long long* flags = (unsigned long long*)(zero + zw);
+    u32* ticket = zero + zw + 2 * (size_t)ntiles;
+    std::vector<ScanJob> sj(n);
+    for (int k = 0; k < n; ++k) {
+      Job& j = J[k];
+      MeshRec* m = M[k];
+      const int W = G[k].W, H = G[k].H;
+      j.zero = zero + zoff[k];
+      if ((rc = aalloc(lane, &j.vrow, (size_t)j.wpr * (H + 1)))) return bail(rc);
+      if ((rc = aalloc(lane, &j.vcol, (size_t)j.wpc * (W + 1)))) return bail(rc);
+      free_list(st, m->scratch);
+      if ((rc = m->keep ? dalloc(lane, &j.segs, cap[k], m->scratch) : aalloc(lane, &j.segs, cap[k]))) return bail(rc);
+      if ((rc = aalloc(lane, &j.npairs, cap[k])) || (rc = aalloc(lane, &j.pbase, (size_t)cap[k] + 1))) return bail(rc);
+      j.seg_cap = cap[k];
+      sj[k] = ScanJob{j.npairs, j.pbase, nullptr, cap[k], j.zero + JC_NSEG, k, 0, nullptr, nullptr, j.zero + JC_ERR};
+    }
+    const std::vector<u32> pc = prefix_of(n, [&](int k) {
+      return (u32)(((G[k].W + 1 + 255) / 256) * ((G[k].H + 1 + 31) / 32));
+    });
+    const std::vector<u32> ps = prefix_of(n, [&](int k) {
+      return (u32)(((i64)(G[k].H + 1) * J[k].wpr + 255) / 256);
+    });
+    // the job table, the scan jobs and the block prefixes in one upload
+    const size_t b_jobs = up256(n * sizeof(Job)), b_sj = up256(n * sizeof(ScanJob)), b_pre = up256((n + 1) * 4);
+    const size_t bytes = b_jobs + b_sj + 3 * b_pre;
+    char *hs, *ds;
+    if ((rc = aalloc(lane, &ds, bytes)) || (rc = stage_begin(lane, bytes, &hs))) return bail(rc);
+    std::memcpy(hs, J.data(), n * sizeof(Job));
+    std::memcpy(hs + b_jobs, sj.data(), n * sizeof(ScanJob));
+    std::memcpy(hs + b_jobs + b_sj, pc.data(), (n + 1) * 4);
+    std::memcpy(hs + b_jobs + b_sj + b_pre, ps.data(), (n + 1) * 4);
+    std::memcpy(hs + b_jobs + b_sj + 2 * b_pre, tpre.data(), (n + 1) * 4);
+    if ((rc = stage_copy(lane, ds, bytes))) return bail(rc);
+    const Job* djobs = (const Job*)ds;
+    const ScanJob* dsj = (const ScanJob*)(ds + b_jobs);
+    const u32* dpc = (const u32*)(ds + b_jobs + b_sj);
+    const u32* dps = (const u32*)(ds + b_jobs + b_sj + b_pre);
+    const u32* dtp = (const u32*)(ds + b_jobs + b_sj + 2 * b_pre);
+    // the test of the wait bound: the second tile of the first image's scan
+    // withholds its sums, so that the third tile's wait runs out
+    const u32 stall = (opt.stall && tpre[1] >= 3) ? 1u : NONE;
+    // a single image's job goes to the kernels as a parameter
+    const Job* one_a = n == 1 ? &J[0] : nullptr;
+    TRACE(KN_CORNER, launch_corner_bits_b(one_a, djobs, dpc, n, pc[n], st));
+    TRACE(KN_SEG, launch_segments_b(one_a, djobs, dps, n, ps[n], st));
+    TRACE(KN_SCAN, launch_mscan(dsj, dtp, n, ntiles, flags, ticket, stall, st));
+    TRACE(KN_TCOUNT, launch_counts_b(djobs, n, lane->cnt_d, st));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    bool redo = false;
+    for (int k = 0; k < n; ++k) {
+      const u32 err = lane->cnt_h[8 * k + 3], ns = lane->cnt_h[8 * k + 2];
+      if (err & ERR_TIMEOUT) return bail(fail(SBMT_ETIMEDOUT, "a device wait ran out while counting (image %d)", k));
+      if (err) return bail(fail(SBMT_EINTERNAL, "device check failed during extraction (0x%x, image %d)", err, k));
+      if (ns > cap[k]) cap[k] = ns, redo = true;
+    }
+    if (!redo) break;
+    if (attempt > 0) return bail(fail(SBMT_EINTERNAL, "segment count above its exact size"));
+  }
+  // ---------------- sizes ----------------
+  std::vector<u64> T(n), V(n);
+  u64 np_all = 0, nbe_all = 0;
+  for (int k = 0; k < n; ++k) {
+    Job& j = J[k];
+    const u32* c = lane->cnt_h + 8 * k;
+    const u64 NC = (u64)c[0] | ((u64)c[1] << 32), NP = c[4];
+    j.nseg = c[2], j.NP = (u32)NP, j.NE = (u32)(NP - c[2]);
+    V[k] = (u64)j.NVg + j.NE + NC, T[k] = (u64)G[k].ncells + 2 * NC + 2 * (u64)j.NE;
+    if (V[k] >= (1ull << 31) || T[k] >= (1ull << 31) || NP >= (1ull << 31))
+      return bail(fail(SBMT_EINVAL, "mesh too large (%llu triangles)", (unsigned long long)T[k]));
+    MeshRec* m = M[k];
+    m->nv = (int64_t)V[k], m->nt = (int64_t)T[k], m->ncells = G[k].ncells;
+    m->nseg_total = j.nseg, m->ne_total = j.NE, m->nc_total = (int64_t)NC, m->nvg = j.NVg;
+    np_all += NP, nbe_all += j.nbe;
+  }
+  // ---------------- emission-phase buffers ----------------
+  std::vector<size_t> ooff(n);
+  size_t obytes = 0;
+  struct OutLay {
+    size_t tri, lab, code, cl, cc, pc, po, ov;
+  };
+  std::vector<OutLay> L(n);
+  for (int k = 0; k < n; ++k) {
+    Job& j = J[k];
+    MeshRec* m = M[k];
+    const bool compact = m->format == SBMT_COMPACT;
+    const u64 NP = j.NP, nxy = compact ? V[k] - j.NVg : V[k], ntr = compact ? (T[k] - (u64)G[k].ncells) + NP : T[k];
+    OutLay& l = L[k];
+    l.tri = up256(16 * nxy), l.lab = up256(l.tri + 12 * ntr), l.code = up256(l.lab + 2 * ntr);
+    l.cl = up256(l.code + 2 * ntr), l.cc = up256(l.cl + (compact ? 2 * (size_t)G[k].ncells : 0));
+    l.pc = up256(l.cc + (compact ? 2 * (size_t)G[k].ncells : 0));
+    l.po = up256(l.pc + (compact ? 4 * NP : 0));
+    l.ov = up256(l.po + (compact ? 4 * (NP + 1) : 0));
+    ooff[k] = obytes;
+    obytes += up256(l.ov + 4 * (size_t)OVER_CAP);
+    m->bytes = up256(l.ov + 4 * (size_t)OVER_CAP);
+  }
+  Shared* osh = new Shared();
+  if (cudaMallocAsync(&osh->ptr, std::max<size_t>(obytes, 256), st) != cudaSuccess) {
+    delete osh;
+    return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", obytes));
+  }
+  osh->refs = n;
+  for (int k = 0; k < n; ++k) M[k]->out_sh = osh;
+  for (int k = 0; k < n; ++k) {
+    Job& j = J[k];
+    MeshRec* m = M[k];
+    char* ob = (char*)osh->ptr + ooff[k];
+    const OutLay& l = L[k];
+    m->xy = (double*)ob, m->tri = (int*)(ob + l.tri), m->label = (unsigned short*)(ob + l.lab);
+    m->code = (unsigned short*)(ob + l.code), m->over_cells = (u32*)(ob + l.ov);
+    j.xy = m->xy, j.tri = m->tri, j.label = m->label, j.code = m->code, j.over = m->over_cells;
+    const u32 NP = j.NP, NE = j.NE, nbc = j.nbc, nbe = j.nbe;
+    if ((rc = aalloc(lane, &j.cstart, walk_chunks(NP) + 1)) || (rc = aalloc(lane, &j.raw, NP)) ||
+        (rc = aalloc(lane, &j.pairs, NP)) || (rc = aalloc(lane, &j.eidx, NE)) || (rc = aalloc(lane, &j.elist, NE)) ||
+        (rc = aalloc(lane, &j.poff, nbc + 1)) || (rc = aalloc(lane, &j.eoff, nbe + 1)) ||
+        (rc = aalloc(lane, &j.pcur, nbc + 1)) || (rc = aalloc(lane, &j.ecur, nbe + 1)) ||
+        (rc = aalloc(lane, &j.extra_scan, nbc + 1)) || (rc = aalloc(lane, &j.chain_scan, nbc + 1)) ||
+        (rc = aalloc(lane, &j.stg, NP)))
+      return bail(rc);
+    if (m->keep) {
+      if ((rc = dalloc(lane, &j.ev, NE, m->scratch)) || (rc = dalloc(lane, &j.recs, NP, m->scratch)) ||
+          (rc = dalloc(lane, &j.bcut, nbc + 1, m->scratch)) || (rc = dalloc(lane, &j.bbase, nbc + 1, m->scratch)))
+        return bail(rc);
+    } else {
+      if ((rc = aalloc(lane, &j.ev, NE)) || (rc = aalloc(lane, &j.recs, NP)) || (rc = aalloc(lane, &j.bcut, nbc + 1)) ||
+          (rc = aalloc(lane, &j.bbase, nbc + 1)))
+        return bail(rc);
+    }
+    j.cp = CompactOut{0, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (m->format == SBMT_COMPACT) {
+      m->cell_label = (unsigned short*)(ob + l.cl), m->cell_code = (unsigned short*)(ob + l.cc);
+      m->patch_cell = (u32*)(ob + l.pc), m->patch_off = (u32*)(ob + l.po);
+      if ((rc = aalloc(lane, &j.cut_scan, nbc + 1))) return bail(rc);
+      j.cp = CompactOut{1, j.NVg, m->cell_label, m->cell_code, m->patch_cell, m->patch_off, j.cut_scan};
+      if (nbc == 0) CK(cudaMemsetAsync(m->patch_off, 0, sizeof(u32), st));
+    }
+    // x of lattice vertex v(i, j) is indexed by m = 2i + j
+    const Tables& tb = *TB[k];
+    i64 m_lo = 0, m_hi = -1;
+    for (size_t r = 0; r < tb.vlo.size(); ++r) {
+      const i64 a = 2 * tb.vlo[r] + tb.vj0 + (i64)r, b = 2 * tb.vhi[r] + tb.vj0 + (i64)r;
+      if (r == 0 || a < m_lo) m_lo = a;
+      if (r == 0 || b > m_hi) m_hi = b;
+    }
+    j.m_lo = m_lo, j.nm = std::max<i64>(1, m_hi - m_lo + 1);
+    if ((rc = aalloc(lane, &j.xtab, (size_t)j.nm))) return bail(rc);
+    if (m->keep) {
+      m->segs = j.segs, m->nseg = j.nseg, m->ev = j.ev, m->ne = j.NE, m->recs = j.recs, m->bcut = j.bcut;
+      m->bbase = j.bbase, m->nbc = nbc;
+    }
+  }
+  // batch-wide state, work lists and the scans' flags
+  BatchPtrs bp{};
+  if ((rc = aalloc(lane, &bp.olist, std::max<u64>(np_all, 1))) || (rc = aalloc(lane, &bp.wlist, std::max<u64>(np_all, 1))) ||
+      (rc = aalloc(lane, &bp.big, std::max<u64>(nbe_all, 1))))
+    return bail(rc);
+  std::vector<ScanJob> sj1(2 * n), sj2;
+  const size_t bdw = (batch_dev_words(n) + 63) & ~(size_t)63;
+  std::vector<u32> t1pre(2 * n + 1, 0), t2pre;
+  for (int k = 0; k < n; ++k) {
+    t1pre[2 * k + 1] = t1pre[2 * k] + mscan_tiles(J[k].nbc);
+    t1pre[2 * k + 2] = t1pre[2 * k + 1] + mscan_tiles(J[k].nbe);
+  }
+  std::vector<int> sj2_job;
+  for (int k = 0; k < n; ++k) {
+    const int per = M[k]->format == SBMT_COMPACT ? 3 : 2;
+    for (int u = 0; u < per; ++u) sj2_job.push_back(k);
+  }
+  const int n2 = (int)sj2_job.size();
+  t2pre.assign(n2 + 1, 0);
+  for (int u = 0; u < n2; ++u) t2pre[u + 1] = t2pre[u] + mscan_tiles(J[sj2_job[u]].nbc);
+  const u32 nt1 = t1pre[2 * n], nt2 = t2pre[n2];
+  u32* zb;
+  const size_t zball = bdw + 2 * ((size_t)nt1 + nt2) + 64;
+  if ((rc = aalloc(lane, &zb, zball))) return bail(rc);
+  CK(cudaMemsetAsync(zb, 0, zball * sizeof(u32), st));
+  bp.bd = (BatchDev*)zb;
+  unsigned long long* flags1 = (unsigned long long*)(zb + bdw);
+  unsigned long long* flags2 = flags1 + nt1;
+  u32* tickets = zb + bdw + 2 * ((size_t)nt1 + nt2);
+  for (int k = 0; k < n; ++k) {
+    Job& j = J[k];
+    u32* z = j.zero;
+    u32* pcnt = z + JC_BUCKETS;
+    u32* ecnt = pcnt + j.nbc + 1;
+    sj1[2 * k] = ScanJob{pcnt, j.poff, j.pcur, j.nbc, nullptr, k, 0, nullptr, nullptr, z + JC_ERR};
+    sj1[2 * k + 1] = ScanJob{ecnt, j.eoff, j.ecur, j.nbe, nullptr, k, RANK_SMALL, bp.big, &bp.bd->nbig, z + JC_ERR};
+  }
+  for (int u = 0, k = -1, w = 0; u < n2; ++u) {
+    if (sj2_job[u] != k) k = sj2_job[u], w = 0;
+    Job& j = J[k];
+    u32* z = j.zero;
+    u32* bextra = z + JC_BUCKETS + (j.nbc + 1) + (j.nbe + 1);  // after pcnt and ecnt
+    u32* bchain = bextra + j.nbc + 1;
+    if (w == 0) sj2.push_back(ScanJob{bextra, j.extra_scan, nullptr, j.nbc, nullptr, k, 0, nullptr, nullptr, z + JC_ERR});
+    else if (w == 1) sj2.push_back(ScanJob{bchain, j.chain_scan, nullptr, j.nbc, nullptr, k, 0, nullptr, nullptr, z + JC_ERR});
+    else sj2.push_back(ScanJob{j.bcut, j.cut_scan, nullptr, j.nbc, nullptr, k, 0, nullptr, nullptr, z + JC_ERR});
+    ++w;
+  }
+  // block prefixes of the emission phase
+  const std::vector<u32> p_cm = prefix_of(n, [&](int k) { return (J[k].nseg + 255) / 256; });
+  const std::vector<u32> p_walk = prefix_of(n, [&](int k) { return (u32)((walk_chunks(J[k].NP) + 255) / 256); });
+  const std::vector<u32> p_sc = prefix_of(n, [&](int k) { return (std::max(J[k].NP, J[k].NE) + 255) / 256; });
+  const std::vector<u32> p_rk = prefix_of(n, [&](int k) { return J[k].nbe; });
+  const std::vector<u32> p_so = prefix_of(n, [&](int k) { return J[k].nbc; });
+  const std::vector<u32> p_go = prefix_of(n, [&](int k) { return (J[k].nbc + 7) / 8; });
+  const std::vector<u32> p_lt = prefix_of(n, [&](int k) {
+    return M[k]->format == SBMT_COMPACT ? 0u : (u32)((J[k].nm + 255) / 256);
+  });
+  const std::vector<u32> p_lx = prefix_of(n, [&](int k) {
+    return M[k]->format == SBMT_COMPACT ? 0u : (u32)G[k].nvrows;
+  });
+  // upload: jobs, scan jobs of both scans, and the prefixes
+  const std::vector<const std::vector<u32>*> pres = {&p_cm, &p_walk, &p_sc, &p_rk, &p_so, &p_go, &p_lt, &p_lx,
+                                                    &t1pre, &t2pre};
+  const size_t b_jobs = up256(n * sizeof(Job)), b_s1 = up256(sj1.size() * sizeof(ScanJob)),
+               b_s2 = up256(std::max<size_t>(sj2.size(), 1) * sizeof(ScanJob));
+  std::vector<size_t> poffs;
+  size_t bytes = b_jobs + b_s1 + b_s2;
+  for (auto* p : pres) poffs.push_back(bytes), bytes += up256(p->size() * 4);
+  char *hs, *ds;
+  if ((rc = aalloc(lane, &ds, bytes)) || (rc = stage_begin(lane, bytes, &hs))) return bail(rc);
+  std::memcpy(hs, J.data(), n * sizeof(Job));
+  std::memcpy(hs + b_jobs, sj1.data(), sj1.size() * sizeof(ScanJob));
+  if (!sj2.empty()) std::memcpy(hs + b_jobs + b_s1, sj2.data(), sj2.size() * sizeof(ScanJob));
+  for (size_t u = 0; u < pres.size(); ++u) std::memcpy(hs + poffs[u], pres[u]->data(), pres[u]->size() * 4);
+  if ((rc = stage_copy(lane, ds, bytes))) return bail(rc);
+  const Job* dj = (const Job*)ds;
+  const ScanJob* ds1 = (const ScanJob*)(ds + b_jobs);
+  const ScanJob* ds2 = (const ScanJob*)(ds + b_jobs + b_s1);
+  auto dpre = [&](int u) { return (const u32*)(ds + poffs[u]); };
+  // ---------------- emission phase ----------------
+  const Job* one = n == 1 ? &J[0] : nullptr;
+  const bool fork = opt.fork;
+  if (fork && (rc = lane_side(lane))) return bail(rc);
+  cudaGraph_t graph = nullptr;
+  if (opt.graph) {
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return bail(fail(SBMT_ECUDA, "graph capture"));
+    lane->capturing = true;
+  }
+  int kerr = 0;
+  TRACE(KN_TCOUNT, launch_chunk_map_b(dj, dpre(0), n, p_cm[n], st));
+  TRACE(KN_TEMIT, launch_walk_b(one, dj, dpre(1), n, p_walk[n], st));
+  TRACE(KN_SCAN, launch_mscan(ds1, dpre(8), 2 * n, nt1, flags1, tickets, NONE, st));
+  TRACE(KN_TEMIT, launch_scatter_b(dj, dpre(2), n, p_sc[n], st));
+  int nrk = 0;
+  TRACE(KN_RANK, nrk = launch_rank_b(one, dj, dpre(3), n, p_rk[n], bp, st, fork ? lane->side : nullptr, lane->fork,
+                                     lane->join));
+  if (nrk < 0) kerr = 1;
+  TRACE(KN_SORT, launch_sort_b(one, dj, dpre(4), n, p_so[n], st));
+  TRACE(KN_CUTCELLS, launch_cutcells_b(one, dj, n, bp, opt.cut_blocks_per_sm, st));
+  TRACE(KN_SCAN, launch_mscan(ds2, dpre(9), n2, nt2, flags2, tickets + 1, NONE, st));
   // Tier-G beside the emission: both read the scans and the records, and
   // write disjoint parts of the output
   cudaStream_t gst = st;
   if (fork) {
-    if ((rc = lane_side(lane))) return bail(rc);
-    CK(cudaEventRecord(lane->fork, st));
-    CK(cudaStreamWaitEvent(lane->side, lane->fork, 0));
+    if (cudaEventRecord(lane->fork, st) != cudaSuccess || cudaStreamWaitEvent(lane->side, lane->fork, 0) != cudaSuccess)
+      kerr = 1;
     gst = lane->side;
   }
   int ntg = 0;
   TRACE_ON(KN_TIERG, gst,
-           ntg = launch_tierg(g, dimg, pitch, img->dtype, sorted, segs, ev, recs, bcut, bbase, nbc, gcnt, olist, wlist,
-                        nwlist, extra_scan, chain_scan, compact ? cut_scan : nullptr, (u32)(NVg + NE), m->tri,
-                        m->label, m->code, m->xy, cp.xy0, err, nover, m->over_cells, gst,
-                        fork ? lane->side2 : nullptr, lane->order, lane->warp));
-  if (ntg < 0) return bail(fail(SBMT_ECUDA, "Tier-G stream events"));
-  if (fork) CK(cudaEventRecord(lane->join, lane->side));
-  TRACE(KN_EMIT, launch_emit(g, dimg, pitch, img->dtype, recs, bcut, bbase, extra_scan, chain_scan, stg, nbc,
-                             (u32)NVg, (u32)NE, m->tri, m->label, m->code, m->xy, cp, st));
-  // x of lattice vertex v(i, j) is indexed by m = 2i + j
-  i64 m_lo = 0, m_hi = -1;
-  for (i64 r = 0; r < nvr; ++r) {
-    const i64 a = 2 * tb.vlo[r] + tb.vj0 + r, b = 2 * tb.vhi[r] + tb.vj0 + r;
-    if (r == 0 || a < m_lo) m_lo = a;
-    if (r == 0 || b > m_hi) m_hi = b;
+           ntg = launch_tierg_b(one, dj, dpre(5), n, p_go[n], bp, opt.tierg_blocks_per_sm, gst,
+                                fork ? lane->side2 : nullptr, lane->order, lane->warp));
+  if (ntg < 0) kerr = 1;
+  if (fork && cudaEventRecord(lane->join, lane->side) != cudaSuccess) kerr = 1;
+  TRACE(KN_EMIT, launch_emit_b(one, dj, dpre(4), n, p_so[n], st));
+  TRACE(KN_XY, launch_lattice_b(dj, dpre(6), p_lt[n], dpre(7), p_lx[n], n, st));
+  if (fork && cudaStreamWaitEvent(st, lane->join, 0) != cudaSuccess) kerr = 1;
+  launch_status_b(dj, n, bp, st);
+  if (opt.graph) {
+    lane->capturing = false;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess || kerr) {
+      if (graph) cudaGraphDestroy(graph);
+      return bail(fail(SBMT_ECUDA, "graph capture: %s", cudaGetErrorString(ce)));
+    }
+    bool ok = false;
+    if (lane->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(lane->gexec, graph, &info) == cudaSuccess;
+      if (!ok) cudaGetLastError(), cudaGraphExecDestroy(lane->gexec), lane->gexec = nullptr;
+    }
+    if (!ok && cudaGraphInstantiate(&lane->gexec, graph, 0) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      lane->gexec = nullptr;
+      return bail(fail(SBMT_ECUDA, "graph instantiation"));
+    }
+    cudaGraphDestroy(graph);
+    CK(cudaGraphLaunch(lane->gexec, st));
   }
-  double* xtab;
-  if ((rc = aalloc(lane, &xtab, (size_t)std::max<i64>(1, m_hi - m_lo + 1)))) return bail(rc);
-  if (!compact) TRACE(KN_XY, launch_lattice_xy(g, m->xy, xtab, m_lo, m_hi - m_lo + 1, st));
-  if (fork) CK(cudaStreamWaitEvent(st, lane->join, 0));
+  if (kerr) return bail(fail(SBMT_ECUDA, "stream events"));
   CK(cudaGetLastError());
-  // the status words: err, cut cells, Tier-G cells, Tier-G triangles, cells
-  // over the Tier-G limit
-  CK(cudaMemcpyAsync(m->h_info, err, 5 * sizeof(u32), cudaMemcpyDeviceToHost, st));
-  if (m->keep) {
-    // sorted pairs are needed by nobody after emission; keep what mesh_stage reads
-    m->segs = segs, m->nseg = nsegs, m->ev = ev, m->ne = (u32)NE, m->recs = recs, m->bcut = bcut;
-    m->bbase = bbase, m->nbc = nbc;
-  }
-  free_list(st, tmp);
   arena_end(lane);
-  {
-    std::lock_guard<std::mutex> lk(ctx->reg);
-    m->done = pool_event(ctx);
-  }
-  if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
-  CK(cudaEventRecord(m->done, st));
   std::lock_guard<std::mutex> lk(ctx->reg);
-  m->id = ctx->next++;
-  ctx->meshes[m->id] = m;
-  *out = m->id;
+  Shared* dsh = new Shared();
+  dsh->ev = pool_event(ctx);
+  if (!dsh->ev || cudaEventRecord(dsh->ev, st) != cudaSuccess) {
+    if (dsh->ev) ctx->ev_pool.push_back(dsh->ev);
+    delete dsh;
+    for (MeshRec* m : M) destroy_mesh(ctx, m, st);
+    return fail(SBMT_ECUDA, "event record");
+  }
+  dsh->refs = n;
+  for (int k = 0; k < n; ++k) {
+    MeshRec* m = M[k];
+    m->done_sh = dsh, m->done = dsh->ev;
+    m->id = ctx->next++;
+    ctx->meshes[m->id] = m;
+    out[k] = m->id;
+  }
   return SBMT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning of the batched path.  A batch's size class is its image count,
+// total pixels (both log2) and largest grid edge h (log2, rounded).  For a
+// class, mesh_autotune times the path under candidate launch parameters
+// (persistent blocks per SM of the cut-cell and Tier-G kernels, Tier-G on
+// side streams or not, the emission phase as a CUDA graph or not) by
+// coordinate descent from the defaults, keeps the fastest and appends it to
+// the tuning file (SBMT_TUNE_FILE, else $HOME/.cache/sbmt_tune.txt), which
+// later contexts read.  Meshes are identical under every choice: only
+// launch shapes and stream placement change.
+// ---------------------------------------------------------------------------
+std::string size_class(const sbmt_image* imgs, int n, const sbmt_params* prs, int nprs) {
+  u64 px = 0;
+  double hmax = 0;
+  for (int k = 0; k < n; ++k) {
+    const sbmt_params& pr = prs[nprs == 1 ? 0 : k];
+    px += (u64)imgs[k].width * (u64)imgs[k].height;
+    hmax = std::max(hmax, (double)pr.h_num / (double)std::max(1, pr.h_den));
+  }
+  auto lg = [](u64 v) {
+    int l = 0;
+    while (v > 1) v >>= 1, ++l;
+    return l;
+  };
+  char buf[64];
+  std::snprintf(buf, sizeof buf, "n%d_p%d_h%d", lg((u64)std::max(n, 1)), lg(std::max<u64>(px, 1)),
+                (int)std::lround(std::log2(std::max(hmax, 1e-9))));
+  return buf;
+}
+
+std::string tune_path() {
+  if (const char* e = std::getenv("SBMT_TUNE_FILE")) return e;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/sbmt_tune.txt";
+}
+
+void tune_load(sbmt_ctx* ctx) {
+  if (ctx->tuned_loaded) return;
+  ctx->tuned_loaded = true;
+  FILE* f = std::fopen(tune_path().c_str(), "r");
+  if (!f) return;
+  char key[64];
+  Tune t;
+  while (std::fscanf(f, "%63s %d %d %d %d", key, &t.cut_blocks_per_sm, &t.tierg_blocks_per_sm, &t.fork, &t.graph) ==
+         5) {
+    const bool ok = t.cut_blocks_per_sm >= 1 && t.cut_blocks_per_sm <= 16 && t.tierg_blocks_per_sm >= 1 &&
+                    t.tierg_blocks_per_sm <= 32 && (t.fork == 0 || t.fork == 1) && (t.graph == 0 || t.graph == 1);
+    if (ok) ctx->tuned[key] = t;  // later lines win
+  }
+  std::fclose(f);
+}
+
+void tune_save(const std::string& key, const Tune& t) {
+  const std::string path = tune_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) {
+    // the cache directory, made when missing (one level)
+    mkdir(path.substr(0, slash).c_str(), 0755);
+  }
+  if (FILE* f = std::fopen(path.c_str(), "a")) {
+    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.cut_blocks_per_sm, t.tierg_blocks_per_sm, t.fork, t.graph);
+    std::fclose(f);
+  }
+}
+
+// launch parameters for a batch: the tuned ones of its size class, else the
+// context's defaults; callers hold ctx->mu
+Tune tune_for(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* prs, int nprs) {
+  tune_load(ctx);
+  auto it = ctx->tuned.find(size_class(imgs, n, prs, nprs));
+  return it != ctx->tuned.end() ? it->second : ctx->tune;
+}
+
+RunOpts opts_of(const Tune& t) {
+  RunOpts o;
+  o.fork = t.fork != 0, o.graph = t.graph != 0;
+  o.cut_blocks_per_sm = t.cut_blocks_per_sm, o.tierg_blocks_per_sm = t.tierg_blocks_per_sm;
+  return o;
 }
 
 // Alg. 3's thresholds in pixels: a, b, c are relative to the reference edge
@@ -892,6 +1258,7 @@ int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params*
   const size_t off_tri = up(16 * nxy), off_lab = up(off_tri + 12 * ntr), off_code = up(off_lab + 2 * ntr);
   const size_t off_st = up(off_code + 2 * ntr), off_sn = up(off_st + V), off_el = up(off_sn + 4 * V);
   const size_t total = off_el + 12 * std::max<u64>(NP, 1) + 256;
+  m->bytes = total;
   if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
     return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
   char* ob = (char*)m->out_block;
@@ -912,6 +1279,7 @@ int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params*
   {
     std::lock_guard<std::mutex> lk(ctx->reg);
     m->done = pool_event(ctx);
+    m->own_done = true;
   }
   if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
   CK(cudaEventRecord(m->done, st));
@@ -944,6 +1312,7 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
   if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(SBMT_ECUDA, "no CUDA device");
   if (device < 0 || device >= n) return fail(SBMT_EINVAL, "device %d of %d", device, n);
   CK(cudaSetDevice(device));
+  if (tierg_init()) return fail(SBMT_ECUDA, "kernel attributes");
   sbmt_ctx* ctx = new sbmt_ctx();
   ctx->device = device;
   if (cuda_stream) {
@@ -967,9 +1336,11 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
 }
 
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
-  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  if (!ctx || !out || !params) return fail(SBMT_EINVAL, "null ctx, params or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  return mesh_one(ctx, &ctx->main, img, params, out, true);
+  RunOpts o = opts_of(tune_for(ctx, img, 1, params, 1));
+  o.stall = (params->flags & SBMT_DEBUG_STALL_SCAN) != 0;
+  return mesh_run(ctx, &ctx->main, img, 1, params, 1, out, o);
 }
 
 int mesh_preprocess(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
@@ -1003,83 +1374,104 @@ int mesh_batch(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* 
   if (!ctx || !imgs || !params || !out || n < 0 || (n_params != 1 && n_params != n))
     return fail(SBMT_EINVAL, "bad batch arguments");
   std::lock_guard<std::mutex> lk(ctx->mu);
-  CK(cudaSetDevice(ctx->device));
-  const int K = std::min(n, batch_lanes());
-  while ((int)ctx->extra.size() < K - 1) {
-    Lane* L = new Lane();
-    if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete L;
-      return fail(SBMT_ECUDA, "stream create");
-    }
-    L->own_stream = true;
-    ctx->extra.push_back(L);
-  }
-  std::vector<Lane*> lanes{&ctx->main};
-  for (int k = 0; k < K - 1; ++k) lanes.push_back(ctx->extra[k]);
-  // the extra lanes start after the work already on the context stream
-  cudaEvent_t start;
-  {
-    std::lock_guard<std::mutex> rl(ctx->reg);
-    start = pool_event(ctx);
-  }
-  CK(cudaEventRecord(start, ctx->stream));
-  for (int k = 1; k < K; ++k) CK(cudaStreamWaitEvent(lanes[k]->stream, start, 0));
-  // largest images first, each lane taking the next image when it is free
-  std::vector<int> order(n);
-  for (int k = 0; k < n; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return (i64)imgs[a].width * imgs[a].height > (i64)imgs[b].width * imgs[b].height;
-  });
-  std::vector<char> made(n, 0);
-  std::atomic<int> next{0};
-  std::atomic<int> first_rc{0};
-  std::mutex msg_mu;
-  std::string msg;
-  ctx->in_batch = true;
-  auto work = [&](Lane* L) {
-    cudaSetDevice(ctx->device);
-    for (int i; (i = next.fetch_add(1)) < n;) {
-      if (first_rc.load()) break;
-      const int k = order[i];
-      const int rc = mesh_one(ctx, L, imgs + k, params + (n_params == 1 ? 0 : k), out + k, false);
-      if (rc) {
-        std::lock_guard<std::mutex> ml(msg_mu);
-        if (!first_rc.load()) first_rc = rc, msg = sbmt_last_error();
-        break;
+  RunOpts o = opts_of(tune_for(ctx, imgs, n, params, n_params));
+  o.stall = n > 0 && (params[0].flags & SBMT_DEBUG_STALL_SCAN) != 0;
+  return mesh_run(ctx, &ctx->main, imgs, n, params, n_params, out, o);
+}
+
+int mesh_autotune(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                  int repeats) {
+  if (!ctx || !imgs || !params || n < 1 || (n_params != 1 && n_params != n) || repeats < 1)
+    return fail(SBMT_EINVAL, "bad autotune arguments");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  tune_load(ctx);
+  std::vector<sbmt_mesh> ids(n);
+  // the wall time of the call and its device work, best of `repeats`
+  auto time_of = [&](const Tune& t, double* best) -> int {
+    *best = 1e30;
+    for (int r = 0; r <= repeats; ++r) {  // the first run warms the tables and the arena
+      const auto t0 = std::chrono::steady_clock::now();
+      int rc = mesh_run(ctx, &ctx->main, imgs, n, params, n_params, ids.data(), opts_of(t));
+      if (rc) return rc;
+      if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(SBMT_ECUDA, "autotune run");
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      {
+        std::lock_guard<std::mutex> rl(ctx->reg);
+        for (sbmt_mesh id : ids) {
+          auto it = ctx->meshes.find(id);
+          if (it != ctx->meshes.end()) destroy_mesh(ctx, it->second, ctx->stream), ctx->meshes.erase(it);
+        }
       }
-      made[k] = 1;
+      if (r > 0) *best = std::min(*best, ms);
     }
+    return SBMT_OK;
   };
-  std::vector<std::thread> threads;
-  for (int k = 1; k < K; ++k) threads.emplace_back(work, lanes[k]);
-  work(lanes[0]);
-  for (auto& t : threads) t.join();
-  ctx->in_batch = false;
-  // later work on the context stream sees every mesh of the batch
-  for (int k = 1; k < K; ++k) {
-    cudaEvent_t e;
-    {
-      std::lock_guard<std::mutex> rl(ctx->reg);
-      e = pool_event(ctx);
+  Tune cur = ctx->tune;
+  double cur_ms;
+  if (int rc = time_of(cur, &cur_ms)) return rc;
+  const std::vector<int> cut_c = {4, 8, 12, 16}, tg_c = {8, 16, 24, 32};
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int axis = 0; axis < 4; ++axis) {
+      std::vector<Tune> cands;
+      if (axis == 0)
+        for (int v : cut_c) cands.push_back(cur), cands.back().cut_blocks_per_sm = v;
+      if (axis == 1)
+        for (int v : tg_c) cands.push_back(cur), cands.back().tierg_blocks_per_sm = v;
+      if (axis == 2) cands.push_back(cur), cands.back().fork ^= 1;
+      if (axis == 3) cands.push_back(cur), cands.back().graph ^= 1;
+      for (const Tune& t : cands) {
+        if (t.cut_blocks_per_sm == cur.cut_blocks_per_sm && t.tierg_blocks_per_sm == cur.tierg_blocks_per_sm &&
+            t.fork == cur.fork && t.graph == cur.graph)
+          continue;
+        double ms;
+        if (int rc = time_of(t, &ms)) return rc;
+        if (ms < 0.97 * cur_ms) cur = t, cur_ms = ms;
+      }
     }
-    CK(cudaEventRecord(e, lanes[k]->stream));
-    CK(cudaStreamWaitEvent(ctx->stream, e, 0));
-    std::lock_guard<std::mutex> rl(ctx->reg);
-    ctx->ev_pool.push_back(e);
   }
-  {
-    std::lock_guard<std::mutex> rl(ctx->reg);
-    ctx->ev_pool.push_back(start);
-  }
-  if (first_rc.load()) {
-    std::lock_guard<std::mutex> rl(ctx->reg);
-    for (int k = 0; k < n; ++k) {
-      if (!made[k]) continue;
-      auto it = ctx->meshes.find(out[k]);
-      if (it != ctx->meshes.end()) destroy_mesh(ctx, it->second, ctx->stream), ctx->meshes.erase(it);
-    }
-    return fail(first_rc.load(), "%s", msg.c_str());
-  }
+  const std::string key = size_class(imgs, n, params, n_params);
+  ctx->tuned[key] = cur;
+  tune_save(key, cur);
+  return SBMT_OK;
+}
+
+int mesh_tuning(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                int32_t* out4) {
+  if (!ctx || !imgs || !params || !out4 || n < 1 || (n_params != 1 && n_params != n))
+    return fail(SBMT_EINVAL, "bad arguments");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  const Tune t = tune_for(ctx, imgs, n, params, n_params);
+  out4[0] = t.cut_blocks_per_sm, out4[1] = t.tierg_blocks_per_sm, out4[2] = t.fork, out4[3] = t.graph;
+  return SBMT_OK;
+}
+
+int mesh_set_tuning(sbmt_ctx* ctx, const sbmt_image* imgs, int n, const sbmt_params* params, int n_params,
+                    const int32_t* in4) {
+  if (!ctx || !imgs || !params || !in4 || n < 1 || (n_params != 1 && n_params != n))
+    return fail(SBMT_EINVAL, "bad arguments");
+  if (in4[0] < 1 || in4[0] > 16 || in4[1] < 1 || in4[1] > 32 || (in4[2] != 0 && in4[2] != 1) ||
+      (in4[3] != 0 && in4[3] != 1))
+    return fail(SBMT_EINVAL, "tuning values out of range");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  tune_load(ctx);
+  Tune t;
+  t.cut_blocks_per_sm = in4[0], t.tierg_blocks_per_sm = in4[1], t.fork = in4[2], t.graph = in4[3];
+  ctx->tuned[size_class(imgs, n, params, n_params)] = t;
+  return SBMT_OK;
+}
+
+int mesh_check(const sbmt_image* img, const sbmt_params* params) { return check_params(img, params); }
+
+int mesh_footprint(sbmt_ctx* ctx, sbmt_mesh mesh, size_t* bytes) {
+  if (!ctx || !bytes) return fail(SBMT_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->meshes.find(mesh);
+  if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh");
+  const MeshRec* m = it->second;
+  size_t b = m->bytes;
+  if (m->keep) b += (size_t)m->nseg * sizeof(Seg) + (size_t)m->ne * sizeof(Event) + 8 * ((size_t)m->nbc + 1) +
+                    (size_t)(m->nseg_total + m->ne_total) * sizeof(CutRec);
+  *bytes = b;
   return SBMT_OK;
 }
 
@@ -1087,7 +1479,9 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   MeshRec* m;
   {
-    std::lock_guard<std::mutex> lk(ctx->mu);
+    // the registry lock only: a query does not wait for another thread's
+    // call in progress on the same context
+    std::lock_guard<std::mutex> lk(ctx->reg);
     auto it = ctx->meshes.find(mesh);
     if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh %llu", (unsigned long long)mesh);
     m = it->second;
@@ -1152,10 +1546,13 @@ int mesh_destroy(sbmt_ctx* ctx) {
     cudaDeviceSynchronize();
     prof_collect(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    for (auto& kv : ctx->tables) cudaFreeAsync(kv.second.dev, ctx->stream), cudaEventDestroy(kv.second.ready);
-    for (Lane* L : ctx->extra) lane_release(L), delete L;
+    for (auto& kv : ctx->tables) {
+      Shared* b = kv.second.block;
+      if (--b->refs == 0) cudaFreeAsync(b->ptr, ctx->stream), delete b;
+    }
+    ctx->tables.clear();
     lane_release(&ctx->main);
-    for (u32* slab : ctx->pinned_slabs) cudaFreeHost(slab);
+    for (auto& slab : ctx->pinned_slabs) cudaFreeHost(slab.first);
   }
   delete ctx;
   return SBMT_OK;
@@ -1308,7 +1705,14 @@ int mesh_project(sbmt_ctx* ctx, sbmt_mesh mesh, const sbmt_image* field, float* 
   const cudaError_t e = cudaGetLastError();
   arena_end(lane);
   if (e != cudaSuccess) return fail(SBMT_ECUDA, "projection launch: %s", cudaGetErrorString(e));
-  // the mesh's completion now includes the projection
+  // the mesh's completion now includes the projection (an event of its own:
+  // a batch's meshes share their completion event)
+  if (!m->own_done) {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    cudaEvent_t e = pool_event(ctx);
+    if (!e) return fail(SBMT_ECUDA, "event create");
+    m->done = e, m->own_done = true;
+  }
   CK(cudaEventRecord(m->done, st));
   return SBMT_OK;
 }

@@ -25,6 +25,7 @@ constexpr int CB_LOG = 10;        // base cells per cell bucket (2^10)
 constexpr int EB_LOG = 11;        // grid-edge ids per event bucket (2^11)
 constexpr int TIERG_TN = 9;      // Tier-G cells up to this many local vertices run one thread each
 constexpr u32 OVER_CAP = 1024;   // ids of cells over the Tier-G vertex limit kept per mesh
+constexpr u32 RANK_SMALL = 256;  // event buckets up to this size are ranked by one small block each
 
 // device error bits (reported through mesh_query)
 enum : u32 {
@@ -32,6 +33,7 @@ enum : u32 {
   ERR_CAPACITY = 2u,   // a Tier-G cell exceeded the per-cell vertex limit (ids listed, OVER_CAP at most)
   ERR_COUNT = 4u,      // a patch did not have the expected triangle count
   ERR_SEGBUF = 8u,     // segment buffer too small (retried by the host)
+  ERR_TIMEOUT = 16u,   // a bounded device wait ran out (reported as SBMT_ETIMEDOUT)
 };
 
 // ---------------------------------------------------------------------------

@@ -8,6 +8,178 @@
 
 namespace sbmt {
 
+// ---------------------------------------------------------------------------
+// Batched launches.  A batch of images (one image is a batch of one) runs
+// every stage of the path as one launch over a job table: job k is image k
+// with its grid, its image and its buffers.  The blocks of a launch are split
+// among the jobs by a prefix of per-job block counts (bpre, njobs + 1
+// entries); block b works for the job k with bpre[k] <= b < bpre[k + 1].
+// The stages whose work is only known on the device (cut cells, Tier-G
+// cells, the large registry buckets) are persistent kernels that pull items
+// from batch-wide work queues.
+// ---------------------------------------------------------------------------
+// counters of one job, in its zeroed block (words): the PSLG vertex count
+// (u64 at 0), the status words at 8.. (see JC_*), then the per-bucket counts
+constexpr int JC_NSEG = 8, JC_ERR = 10, JC_NREC = 11, JC_NGCELL = 12, JC_NGTRI = 13, JC_NOVER = 14;
+constexpr int JC_BUCKETS = 16;
+struct __align__(16) Job {
+  GridP g;
+  const unsigned char* img;
+  i64 pitch;
+  int dtype;
+  int wpr, wpc;
+  u32* vrow;
+  u32* vcol;
+  u32* zero;  // counters (JC_*), then pcnt (nbc + 1), ecnt (nbe + 1), bextra (nbc + 1), bchain (nbc + 1)
+  Seg* segs;
+  u32 seg_cap;
+  u32* npairs;  // seg_cap values
+  u32* pbase;   // seg_cap + 1 values
+  // known after the counting phase
+  u32 nseg, NP, NE, NVg, nbc, nbe;
+  u32* cstart;
+  Pair* raw;     // pairs in walk order, later sorted by cell
+  Pair* pairs;   // pairs in cell buckets
+  Event* ev;
+  u32* eidx;
+  u32* elist;
+  u32 *poff, *eoff, *pcur, *ecur;
+  CutRec* recs;
+  u32 *bcut, *bbase, *extra_scan, *chain_scan, *cut_scan;
+  TStage* stg;
+  int* tri;
+  unsigned short* label;
+  unsigned short* code;
+  double* xy;
+  CompactOut cp;
+  double* xtab;
+  i64 m_lo, nm;
+  u32* over;   // ids of cells over the Tier-G limit (OVER_CAP)
+  u32* hinfo;  // host status words (mapped pinned memory), written at the end
+};
+SBMT_DEV u32* jc(const Job& J, int k) { return J.zero + k; }
+SBMT_DEV u32* j_pcnt(const Job& J) { return J.zero + JC_BUCKETS; }
+SBMT_DEV u32* j_ecnt(const Job& J) { return J.zero + JC_BUCKETS + J.nbc + 1; }
+SBMT_DEV u32* j_bextra(const Job& J) { return J.zero + JC_BUCKETS + J.nbc + 1 + J.nbe + 1; }
+SBMT_DEV u32* j_bchain(const Job& J) { return J.zero + JC_BUCKETS + 2 * (J.nbc + 1) + J.nbe + 1; }
+inline size_t job_zero_words(u32 nbc, u32 nbe) { return JC_BUCKETS + 3 * ((size_t)nbc + 1) + (nbe + 1); }
+
+// the job of a block-uniform kernel, copied once into shared memory so that
+// its fields do not occupy registers for the whole kernel
+SBMT_DEV void load_job(const Job* jobs, int k, Job* sj) {
+  const int4* src = reinterpret_cast<const int4*>(jobs + k);
+  int4* dst = reinterpret_cast<int4*>(sj);
+  for (int i = threadIdx.x; i < (int)(sizeof(Job) / 16); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// The job of a block-uniform kernel.  A launch for one image (ONE) takes its
+// job as a kernel parameter, whose fields the kernel reads as constant-bank
+// operands; a batched launch finds the block's job from the block prefix
+// and copies it into shared memory.  Declares J (the job), jk (its index)
+// and lb (the block's index within the job).
+#define SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)  \
+  __shared__ Job sJ_;                                 \
+  int jk = 0;                                         \
+  u32 lb = blockIdx.x;                                \
+  const Job* jp_ = &one;                              \
+  if constexpr (!ONE) {                               \
+    jk = job_of(bpre, njobs, blockIdx.x);             \
+    load_job(jobs, jk, &sJ_);                         \
+    jp_ = &sJ_;                                       \
+    lb = blockIdx.x - bpre[jk];                       \
+  }                                                   \
+  const Job& J = *jp_;
+
+// the job of block b: the last k with bpre[k] <= b
+SBMT_DEV int job_of(const u32* bpre, int njobs, u32 b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(bpre + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// batch-wide state of the persistent stages
+struct BatchDev {
+  u32 gcnt[TIERG_TN + 2];  // Tier-G cells per local vertex count (above TIERG_TN pooled)
+  u32 gcur[TIERG_TN + 2];  // cursors while ordering
+  u32 nolist, nwlist, nbig, err;
+  u32 recpre[1];           // 2 (njobs + 1) entries: prefix of the jobs' cut-cell records, then of
+                           // their chunks of CUT_CHUNK records
+};
+inline size_t batch_dev_words(int njobs) { return sizeof(BatchDev) / 4 + 2 * ((size_t)njobs + 1); }
+constexpr u32 CUT_CHUNK = 128;  // records per block and turn of the persistent cut-cell kernel
+struct BatchPtrs {
+  BatchDev* bd;
+  uint2* olist;  // (job, record) of Tier-G cells of at most TIERG_TN vertices, largest first
+  uint2* wlist;  // (job, record) of larger Tier-G cells
+  uint2* big;    // (job, event bucket) of registry buckets above RANK_SMALL events
+};
+
+// one prefix sum of a batched scan: out[i] = sum of in[0..i), out[n] = total,
+// also into out2 when given; with big, the indices of values above big_thr
+// are listed as (img, index) in big (count in *nbig)
+struct ScanJob {
+  const u32* in;
+  u32* out;
+  u32* out2;
+  u32 n;             // values (the tiles cover n + 1 outputs)
+  const u32* n_dev;  // or null: the number of values is min(*n_dev, n), known on the device only
+  int img;
+  u32 big_thr;
+  uint2* big;
+  u32* nbig;
+  u32* err;  // the image's error word (ERR_TIMEOUT when a wait ran out)
+};
+constexpr int MSCAN_TILE = 2048;
+inline u32 mscan_tiles(u32 n) { return (n + 1 + MSCAN_TILE - 1) / MSCAN_TILE; }
+// single-pass scans of every job in one launch (tpre: prefix of the jobs'
+// tiles; flags: tpre[nsj] words of zeroed scratch for the tiles' published
+// sums, ticket: one zeroed word).  Each tile waits for its predecessor's
+// prefix with a bounded wait (about one second), after which it records
+// ERR_TIMEOUT and publishes an error mark.  stall_tile (NONE normally)
+// names a tile that withholds its sums, so that the wait of its successor
+// runs out -- the test of the bound.
+int launch_mscan(const ScanJob* sj, const u32* tpre, int nsj, u32 ntiles, unsigned long long* flags, u32* ticket,
+                 u32 stall_tile, cudaStream_t st);
+
+// batched stages (jobs and the block prefix bpre in device memory; nblocks =
+// bpre[njobs]); each returns the kernels it launched.  `one` is the host
+// copy of the job when the launch has a single job (then passed as a kernel
+// parameter), else null.
+int launch_corner_bits_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+int launch_segments_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+// per job {PSLG vertices (2 words), segments, error, pairs} into out (mapped
+// host memory).  launch_segments_b also writes each segment's pair count
+// (cells visited) into npairs at the segment's slot.
+int launch_counts_b(const Job* jobs, int njobs, u32* out, cudaStream_t st);
+int launch_chunk_map_b(const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+int launch_walk_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+int launch_scatter_b(const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+// registry: small buckets one block each (bpre over nbe), large ones from
+// the batch's list on st2 (or st) beside them
+int launch_rank_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, const BatchPtrs& bp,
+                  cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a, cudaEvent_t ev_b);
+int launch_sort_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+// cut-cell classification, persistent over every job's records
+int launch_cutcells_b(const Job* one, const Job* jobs, int njobs, const BatchPtrs& bp, int blocks_per_sm,
+                      cudaStream_t st);
+int launch_emit_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+int launch_lattice_b(const Job* jobs, const u32* bpre_tab, u32 nb_tab, const u32* bpre_xy, u32 nb_xy, int njobs,
+                     cudaStream_t st);
+// Tier-G: ordering (bpre over warps of buckets), then the persistent thread
+// and warp kernels over the batch's lists (warp kernel on st2 when given)
+int launch_tierg_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, const BatchPtrs& bp,
+                   int thread_blocks_per_sm, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
+                   cudaEvent_t ev_warp);
+// kernel attributes set once per device (outside any stream capture)
+int tierg_init();
+// status words of every job into its mapped host slot
+int launch_status_b(const Job* jobs, int njobs, const BatchPtrs& bp, cudaStream_t st);
+
 // K1a: vertex flags of every pixel corner, bit-packed per corner row (vrow)
 // and per corner column (vcol); counts the PSLG vertices into *nvtx.
 int launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, int H, u32* vrow, int wpr,
@@ -17,84 +189,15 @@ int launch_corner_bits(const unsigned char* img, i64 pitch, int dtype, int W, in
 int launch_segments(const unsigned char* img, i64 pitch, int dtype, int W, int H, const u32* vrow, int wpr,
                      const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, cudaStream_t st);
 
-// K2: number of pairs (cells visited = crossings + 1) of every segment, in
-// closed form; slots beyond the segment count get 0.
-int launch_seg_count(const GridP& g, const Seg* segs, const u32* nseg, u32 cap, u32* npairs, cudaStream_t st);
-
-// K2 walk, chunked over the global pair index (pbase = exclusive scan of
-// npairs; cstart = first segment of every chunk, from launch_chunk_map over
-// walk_chunks(NP) chunks): every pair at its global index in raw, every event
-// at its fixed index, pairs per cell bucket counted into pbk and events per
-// event bucket into ebk.  launch_scatter then moves the pairs into their cell
-// buckets and the event indices into their event buckets (pcur / ecur: the
-// buckets' cursors, starting at the exclusive scans of pbk / ebk).
+// K2 walk, chunked over the global pair index: walk_chunks(NP) chunks of
+// pairs, one thread each.
 size_t walk_chunks(u32 NP);
-int launch_chunk_map(const u32* pbase, const u32* nseg, u32 cap, u32* cstart, cudaStream_t st);
-int launch_walk(const GridP& g, const Seg* segs, const u32* pbase, const u32* cstart, u32 NP, u32* pbk, u32* ebk,
-                Pair* raw, Event* events, u32* err, cudaStream_t st);
-int launch_scatter(const Pair* raw, u32 NP, const Event* events, u32 NE, u32* pcur, u32* ecur, Pair* pairs,
-                   u32* eidx, cudaStream_t st);
-
-// frozen registry: rank the events of each event bucket (listed in eidx) by
-// (grid-edge id, position), assign vertex ids NVg + rank, write coordinates.
-// With st2 the few large buckets are ranked there beside the small ones
-// (ev_a, ev_b fork and join); returns the kernels launched, -1 when an
-// event call failed.
-int launch_rank_events(const GridP& g, Event* events, const u32* eidx, u32* elist, const u32* eoff, u32 nbe,
-                        u32 NVg, double* xy, u32 xy0, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_a,
-                        cudaEvent_t ev_b);
-
-// K3a: sort each cell bucket's pairs by cell into sorted; one record per cut
-// cell, in cell order, in a dense range of recs drawn from *nrec (bucket b:
-// bcut[b] records from bbase[b]).
-int launch_sort(const Pair* pairs, Pair* sorted, const u32* poff, u32 nbc, CutRec* recs, u32* nrec, u32* bcut,
-                 u32* bbase, cudaStream_t st);
-
-// K3b: classify every cut cell (key, sigma, class, Tier-T / Tier-G, triangle
-// and inside-vertex counts, added per bucket into bextra / bchain) and stage
-// the patch of every Tier-T cell in stg (same index as its record).
-int launch_cutcells(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                     const Seg* segs, const Event* events, CutRec* recs, const u32* nrec, u32* bextra, u32* bchain,
-                     TStage* stg, u32* ngcell, u32* ngtri, u32* gcnt, u32* err, cudaStream_t st);
 
 // exclusive scan of n u32 values with stride `stride` into out (n + 1
 // entries, out[n] = total); inputs above 65536 values need scratch of
 // scan_scratch_words(n) words
 size_t scan_scratch_words(u32 n);
-// exclusive scans of one or two arrays (in_b = nullptr for one) of at most
-// SCAN_ONE values each in one launch, the results also copied to out2 when
-// given (nullptr otherwise)
-constexpr u32 SCAN_ONE = 1u << 14;
-int launch_scan_pair(const u32* in_a, u32* out_a, u32* out2_a, u32 n_a, const u32* in_b, u32* out_b, u32* out2_b,
-                     u32 n_b, cudaStream_t st);
 int launch_scan(const u32* in, int stride, u32* out, u32 n, u32* scratch, cudaStream_t st);
-
-// K4: per cell bucket, emit every uncut cell's base triangle and every
-// Tier-T cell's staged patch (Alg. 2) with its inside vertex (Tier-G cells
-// are skipped: k_cutcells queued them, the Tier-G kernels place them).
-int launch_emit(const GridP& g, const unsigned char* img, i64 pitch, int dtype, CutRec* recs, const u32* bcut,
-                 const u32* bbase, const u32* extra_scan, const u32* chain_scan, const TStage* stg, u32 nbc, u32 NVg,
-                 u32 NE, int* tri, unsigned short* label, unsigned short* code, double* xy, const CompactOut& cp,
-                 cudaStream_t st);
-
-// K4-G: greedy Steiner-free triangulation of every queued Tier-G cell.  The
-// cells are first ordered by local vertex count, largest first, into olist
-// (gcnt: zeroed, 3 * (TIERG_TN + 2) words; its first TIERG_TN + 2 are the
-// per-count totals k_cutcells gathered), each cell's output range taken from
-// the scans (cut_scan for the compact format, else null; CB0 = the first
-// inside-vertex id); one thread per cell of at most TIERG_TN vertices, one
-// warp per larger cell (through wlist).  A cell over the per-cell limit
-// sets ERR_CAPACITY, counts itself in *nover and lists its id in over
-// (OVER_CAP at most).  With st2 the warp kernel runs there,
-// after ev_order (recorded on st after the ordering), and st waits for it
-// through ev_warp; without, everything runs on st.  Returns the kernels
-// launched, or -1 when an event call failed.
-int launch_tierg(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const Pair* sorted,
-                  const Seg* segs, const Event* events, CutRec* recs, const u32* bcut, const u32* bbase, u32 nbc,
-                  u32* gcnt, u32* olist, u32* wlist, u32* nwlist, const u32* extra_scan, const u32* chain_scan,
-                  const u32* cut_scan, u32 CB0, int* tri, unsigned short* label, unsigned short* code, double* xy,
-                  u32 xy0, u32* err, u32* nover, u32* over, cudaStream_t st, cudaStream_t st2,
-                  cudaEvent_t ev_order, cudaEvent_t ev_warp);
 
 // quality measures: per-triangle pass (mm: min angle, min area, max AR as
 // double bits; cnt: slivers, equilateral; part: per-block area sums; ar:
@@ -178,9 +281,5 @@ size_t heat_scratch_bytes(u64 T, u64 V, int maxit);
 int heat_solve(const double* xy, const int* tri, const unsigned short* label, u64 T, u64 V, int L, double alpha,
                double dt, int nsteps, double x0, double y0, double sigma, double amp, double tol, int maxit,
                double* u, double* peaks, int* iters, void* scratch, cudaStream_t st);
-
-// coordinates of the lattice vertices; tab: scratch of nm doubles for the x
-// values (ox + 3p m) / S, m0 <= m < m0 + nm covering 2i + j of every vertex
-int launch_lattice_xy(const GridP& g, double* xy, double* tab, i64 m0, i64 nm, cudaStream_t st);
 
 }  // namespace sbmt

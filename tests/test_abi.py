@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2602_19474_gb300 as sb
@@ -40,7 +41,8 @@ def test_struct_layouts_match_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = (sb.sbmt_image, sb.sbmt_params, sb.sbmt_mesh_view, sb.sbmt_quality, sb.sbmt_pre_info, sb.sbmt_heat_params)
+    structs = (sb.sbmt_image, sb.sbmt_params, sb.sbmt_mesh_view, sb.sbmt_quality, sb.sbmt_pre_info, sb.sbmt_heat_params,
+               sb.sbmt_server_config, sb.sbmt_request_info, sb.sbmt_server_stats)
     lines = []
     for st in structs:
         n = st.__name__
@@ -69,4 +71,27 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mesh_preprocess(None, None, None, None) == sb.SBMT_EINVAL
     assert lib.mesh_preprocess_info(None, 1, None) == sb.SBMT_EINVAL
     assert lib.mesh_heat(None, 1, None, None, None, None) == sb.SBMT_EINVAL
+    assert lib.mesh_autotune(None, None, 0, None, 1, 1) == sb.SBMT_EINVAL
+    assert lib.mesh_tuning(None, None, 0, None, 1, None) == sb.SBMT_EINVAL
+    assert lib.mesh_set_tuning(None, None, 0, None, 1, None) == sb.SBMT_EINVAL
+    assert lib.mesh_footprint(None, 1, None) == sb.SBMT_EINVAL
+    assert lib.server_create(None, 0, None) == sb.SBMT_EINVAL
+    assert lib.server_submit(None, None, None, None) == sb.SBMT_EINVAL
+    assert lib.server_wait(None, 1, 0, None, None) == sb.SBMT_EINVAL
+    assert lib.server_destroy(None) == sb.SBMT_EINVAL
     assert isinstance(lib.sbmt_last_error(), bytes)
+
+
+def test_requests_are_checked_without_a_device(lib):
+    # mesh_check (which server_submit runs first) needs no GPU
+    img = np.zeros((4, 5), np.uint8)
+    assert sb.mesh_check(img, 2) == sb.SBMT_OK
+    assert sb.mesh_check(img, 3) == sb.SBMT_EINVAL  # odd h_num: outside the degeneracy-free class
+    assert sb.mesh_check(img, 2, 2) == sb.SBMT_EINVAL  # even h_den
+    assert sb.mesh_check(np.zeros((4, 32769), np.uint8), 2) == sb.SBMT_EINVAL
+    im, _ = sb._image(img)
+    pr = sb._params(2, mode=sb.SBMT_PREPROCESS)
+    assert lib.mesh_check(ctypes.byref(im), ctypes.byref(pr)) == sb.SBMT_EPROTO
+    # the pre-count reservation grows with the image and shrinks with h
+    assert sb.mesh_bound(np.zeros((100, 100), np.uint8), 2) < sb.mesh_bound(np.zeros((200, 200), np.uint8), 2)
+    assert sb.mesh_bound(np.zeros((100, 100), np.uint8), 8) < sb.mesh_bound(np.zeros((100, 100), np.uint8), 2)
