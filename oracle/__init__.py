@@ -85,6 +85,11 @@ def _load():
         lib.oracle_base_mesh.argtypes = [ctypes.c_int32] * 6 + [ctypes.POINTER(ctypes.c_int64)] * 2 + [
             ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
         lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_check_mesh.restype = ctypes.c_int
+        lib.oracle_check_mesh.argtypes = [ctypes.c_void_p] + [ctypes.c_int32] * 4 + [ctypes.c_int64] * 2 + [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_brute.restype = ctypes.c_int64
+        lib.oracle_brute.argtypes = [ctypes.c_int32] * 4 + [ctypes.c_int64] * 2
         lib.oracle_greedy.restype = ctypes.c_int
         lib.oracle_greedy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_int32]
@@ -215,3 +220,31 @@ def base_mesh(width: int, height: int, h_num: int, h_den: int = 1, origin2x: int
     finally:
         lib.oracle_free(ctypes.cast(xy, ctypes.c_void_p))
         lib.oracle_free(ctypes.cast(tri, ctypes.c_void_p))
+
+
+def brute(width: int, height: int, h_num: int, h_den: int = 1, first: int = 0, stride: int = 1) -> int:
+    """Mesh every binary width x height bitmap (bit k of its number = pixel k,
+    row-major; from `first`, every `stride`-th) at h = h_num / h_den and check
+    each mesh against the invariants of any correct output (orientation,
+    closure, Euler characteristic, exact total and per-label areas, boundary
+    conformity).  Returns the number checked; raises on the first failure."""
+    r = _load().oracle_brute(width, height, h_num, h_den, first, stride)
+    if r < 0:
+        raise OracleError(_load().oracle_last_error().decode())
+    return r
+
+
+def check_mesh(img: np.ndarray, h_num: int, h_den: int, mesh: dict) -> int:
+    """The invariants of brute() for one mesh of a binary bitmap: 0, or the
+    number of the failed check (the message in last_error())."""
+    lib = _load()
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    xy = np.ascontiguousarray(mesh["xy"], dtype=np.float64)
+    tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32)
+    lab = np.ascontiguousarray(mesh["label"], dtype=np.uint16)
+    return lib.oracle_check_mesh(img.ctypes.data, img.shape[1], img.shape[0], h_num, h_den, mesh["n_cells"],
+                                 len(xy), xy.ctypes.data, len(tri), tri.ctypes.data, lab.ctypes.data)
+
+
+def last_error() -> str:
+    return _load().oracle_last_error().decode()

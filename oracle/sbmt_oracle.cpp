@@ -53,6 +53,7 @@
 #include <map>
 #include <set>
 #include <stdexcept>
+#include <string>
 #include <vector>
 
 typedef __int128 i128;
@@ -1112,5 +1113,132 @@ int oracle_base_mesh(int32_t width, int32_t height, int32_t h_num, int32_t h_den
 }
 
 void oracle_free(void* p) { free(p); }
+
+/* ------------------------------------------------------------------------
+ * Mesh invariants of any correct output (test infrastructure): every
+ * triangle counter-clockwise, every vertex used, each undirected edge in at
+ * most two triangles and each directed edge in at most one (closure and
+ * consistent orientation), Euler characteristic V - E + T = 1 (a disk),
+ * total area = n_cells * sqrt(3)/4 h^2 (every base cell tiled), the area of
+ * each pixel label = its pixel count and the outside area = the rest, and
+ * boundary conformity: every edge between triangles of different labels
+ * lies on a pixel line, and those edges add up to the bitmap's boundary
+ * length.  Returns 0, or the number of the failed check (message in
+ * g_err).
+ * ------------------------------------------------------------------------ */
+static int check_invariants(const uint8_t* img, int W, int H, double h, const Mesh& M) {
+  const i64 V = (i64)M.xy.size() / 2, T = (i64)M.label.size();
+  auto X = [&](i64 v) { return M.xy[2 * v]; };
+  auto Y = [&](i64 v) { return M.xy[2 * v + 1]; };
+  std::vector<char> used(V, 0);
+  double total = 0.0;
+  double lab_area[2] = {0.0, 0.0}, out_area = 0.0;
+  for (i64 t = 0; t < T; ++t) {
+    const int32_t a = M.tri[3 * t], b = M.tri[3 * t + 1], c = M.tri[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) return std::snprintf(g_err, sizeof g_err, "vertex id"), 1;
+    used[a] = used[b] = used[c] = 1;
+    const double ar = 0.5 * ((X(b) - X(a)) * (Y(c) - Y(a)) - (Y(b) - Y(a)) * (X(c) - X(a)));
+    if (!(ar > 0)) return std::snprintf(g_err, sizeof g_err, "triangle %lld not counter-clockwise", (long long)t), 2;
+    total += ar;
+    const uint16_t l = M.label[t];
+    if (l == 0xFFFF) out_area += ar;
+    else if (l < 2) lab_area[l] += ar;
+    else return std::snprintf(g_err, sizeof g_err, "label %d", (int)l), 3;
+  }
+  for (i64 v = 0; v < V; ++v)
+    if (!used[v]) return std::snprintf(g_err, sizeof g_err, "unused vertex %lld", (long long)v), 4;
+  // edges: (min, max, triangle, directed) sorted
+  std::vector<std::array<i64, 4>> e;
+  e.reserve(3 * T);
+  for (i64 t = 0; t < T; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const i64 u = M.tri[3 * t + k], w = M.tri[3 * t + (k + 1) % 3];
+      e.push_back({std::min(u, w), std::max(u, w), t, u < w ? 1 : 0});
+    }
+  std::sort(e.begin(), e.end());
+  i64 E = 0;
+  double blen = 0.0;
+  for (size_t k = 0; k < e.size();) {
+    size_t m = k + 1;
+    while (m < e.size() && e[m][0] == e[k][0] && e[m][1] == e[k][1]) ++m;
+    if (m - k > 2) return std::snprintf(g_err, sizeof g_err, "edge in three triangles"), 5;
+    if (m - k == 2) {
+      if (e[k][3] == e[k + 1][3]) return std::snprintf(g_err, sizeof g_err, "directed edge repeated"), 6;
+      if (M.label[e[k][2]] != M.label[e[k + 1][2]]) {
+        const i64 u = e[k][0], w = e[k][1];
+        const bool onh = std::fabs(Y(u) - Y(w)) < 1e-9 && std::fabs(Y(u) - std::round(Y(u) - 0.5) - 0.5) < 1e-9;
+        const bool onv = std::fabs(X(u) - X(w)) < 1e-9 && std::fabs(X(u) - std::round(X(u) - 0.5) - 0.5) < 1e-9;
+        if (!onh && !onv) return std::snprintf(g_err, sizeof g_err, "label change off the pixel lines"), 7;
+        blen += std::fabs(X(u) - X(w)) + std::fabs(Y(u) - Y(w));
+      }
+    }
+    ++E;
+    k = m;
+  }
+  if (V - E + T != 1) return std::snprintf(g_err, sizeof g_err, "Euler characteristic %lld", (long long)(V - E + T)), 8;
+  const double want = (double)M.ncells * std::sqrt(3.0) / 4.0 * h * h;
+  if (std::fabs(total - want) > 1e-9 * want + 1e-9) return std::snprintf(g_err, sizeof g_err, "total area"), 9;
+  int cnt[2] = {0, 0}, bl = 0;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int l = img[y * W + x];
+      cnt[l]++;
+      bl += (x == 0) + (y == 0) + (x == W - 1) + (y == H - 1);
+      if (x + 1 < W && img[y * W + x + 1] != l) ++bl;
+      if (y + 1 < H && img[(y + 1) * W + x] != l) ++bl;
+    }
+  for (int l = 0; l < 2; ++l)
+    if (std::fabs(lab_area[l] - cnt[l]) > 1e-9 * W * H + 1e-7)
+      return std::snprintf(g_err, sizeof g_err, "area of label %d", l), 10;
+  if (std::fabs(out_area - (want - W * H)) > 1e-9 * want + 1e-7)
+    return std::snprintf(g_err, sizeof g_err, "outside area"), 11;
+  if (std::fabs(blen - bl) > 1e-6 * std::max(1, bl))
+    return std::snprintf(g_err, sizeof g_err, "boundary length %g of %d", blen, bl), 12;
+  return 0;
+}
+
+/* The invariants above for a given mesh of a binary bitmap (W x H bytes,
+ * row-major): 0, or the number of the failed check (message in
+ * oracle_last_error). */
+int oracle_check_mesh(const uint8_t* img, int32_t W, int32_t H, int32_t h_num, int32_t h_den, int64_t ncells,
+                      int64_t V, const double* xy, int64_t T, const int32_t* tri, const uint16_t* label) {
+  g_err[0] = 0;
+  Mesh M;
+  M.xy.assign(xy, xy + 2 * V);
+  M.tri.assign(tri, tri + 3 * T);
+  M.label.assign(label, label + T);
+  M.ncells = ncells;
+  return check_invariants(img, W, H, (double)h_num / h_den, M);
+}
+
+/* Every binary bitmap of W x H <= 25 pixels (bit k of the bitmap's number =
+ * pixel k in row-major order) from `first`, every `stride`-th, meshed at
+ * h = h_num / h_den and checked against the invariants; returns the number
+ * checked, or -(1 + the first failing bitmap's number) with the message in
+ * oracle_last_error. */
+int64_t oracle_brute(int32_t W, int32_t H, int32_t h_num, int32_t h_den, int64_t first, int64_t stride) {
+  if (W < 1 || H < 1 || W * H > 25 || stride < 1 || first < 0) return -1;
+  std::vector<uint8_t> img(W * H);
+  const int64_t n = (int64_t)1 << (W * H);
+  int64_t done = 0;
+  for (int64_t b = first; b < n; b += stride) {
+    for (int k = 0; k < W * H; ++k) img[k] = (uint8_t)((b >> k) & 1);
+    try {
+      Image im{W, H, (int64_t)W, 1, img.data()};
+      Mesh M;
+      mesh_image(im, h_num, h_den, 0, 0, M);
+      if (check_invariants(img.data(), W, H, (double)h_num / h_den, M)) {
+        const std::string what = g_err;
+        std::snprintf(g_err, sizeof g_err, "bitmap %lld: %.400s", (long long)b, what.c_str());
+        return -(1 + b);
+      }
+    } catch (const std::exception& ex) {
+      std::snprintf(g_err, sizeof g_err, "bitmap %lld: %s", (long long)b, ex.what());
+      return -(1 + b);
+    }
+    ++done;
+  }
+  return done;
+}
 
 }  // extern "C"

@@ -11,7 +11,11 @@
 // gradients with the diagonal as preconditioner.  The operator is assembled
 // once per call into sparse rows over the free vertices (from one record per
 // region triangle), so that each product is a gather with no atomics.
-// Double precision throughout.
+// Double precision throughout.  The result does not depend on the order in
+// which threads run: records are placed by a scan, each free vertex's mass
+// and diagonal are gathered over its incident records in record order, the
+// rows' entries are sorted by column, and every reduction is finished by
+// the last block of its launch over the blocks' partial sums in block order.
 #include <algorithm>
 #include <vector>
 
@@ -30,6 +34,7 @@ struct HeatTri {
   int v[3];
   int pad;
   double w[3];
+  double third;  // a third of the triangle's area
 };
 
 __global__ void __launch_bounds__(HB) k_heat_flags(const int* tri, const unsigned short* label, u64 T, int L,
@@ -53,21 +58,21 @@ __global__ void __launch_bounds__(HB) k_heat_list(u64 V, const u32* free01, cons
     if (free01[v]) list[fidx[v]] = (u32)v;
 }
 
+// region triangles as 0/1 flags, for the scan that places their records
+__global__ void __launch_bounds__(HB) k_heat_tflag(const unsigned short* label, u64 T, int L, u32* tf) {
+  for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (u64)gridDim.x * blockDim.x)
+    tf[t] = label[t] == (unsigned short)L ? 1u : 0u;
+}
+
 // the region's triangles: records (corners as free indices, -1 for
-// boundary vertices), lumped mass and the stiffness diagonal per free vertex
+// boundary vertices) at their scan positions, in triangle order, and the
+// number of records at each free vertex
 __global__ void __launch_bounds__(HB) k_heat_setup(const double* xy, const int* tri, const unsigned short* label,
-                                                   u64 T, int L, const u32* free01, const u32* fidx, HeatTri* rec,
-                                                   u32* nrec, double* mass, double* kdiag) {
+                                                   u64 T, int L, const u32* free01, const u32* fidx, const u32* tpos,
+                                                   HeatTri* rec, u32* vcnt) {
   const double2* p = reinterpret_cast<const double2*>(xy);
-  const int lane = threadIdx.x & 31;
-  for (u64 t0 = (u64)blockIdx.x * blockDim.x; t0 < T; t0 += (u64)gridDim.x * blockDim.x) {
-    const u64 t = t0 + threadIdx.x;
-    const bool in = t < T && label[t] == (unsigned short)L;
-    const u32 m = __ballot_sync(0xFFFFFFFFu, in);
-    u32 base = 0;
-    if (lane == 0 && m) base = atomicAdd(nrec, (u32)__popc(m));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (!in) continue;
+  for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (u64)gridDim.x * blockDim.x) {
+    if (label[t] != (unsigned short)L) continue;
     HeatTri h;
     double2 c[3];
 #pragma unroll
@@ -84,29 +89,82 @@ __global__ void __launch_bounds__(HB) k_heat_setup(const double* xy, const int* 
       const double dot = (b.x - a.x) * (d.x - a.x) + (b.y - a.y) * (d.y - a.y);
       h.w[k] = 0.5 * dot / cross;  // cot(theta_k) / 2 = (u . v) / (2 |u x v|)
     }
-    rec[base + __popc(m & ((1u << lane) - 1u))] = h;
-    const double third = cross / 6.0;  // a third of the area |u x v| / 2
+    h.third = cross / 6.0;  // a third of the area |u x v| / 2
+    rec[tpos[t]] = h;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (h.v[k] >= 0) atomicAdd(mass + h.v[k], third);
-      // the edge opposite corner k joins corners k + 1 and k + 2
-      const int i = h.v[(k + 1) % 3], j = h.v[(k + 2) % 3];
-      if (i >= 0) atomicAdd(kdiag + i, h.w[k]);
-      if (j >= 0) atomicAdd(kdiag + j, h.w[k]);
-    }
+    for (int k = 0; k < 3; ++k)
+      if (h.v[k] >= 0) atomicAdd(vcnt + h.v[k], 1u);
   }
 }
 
-// block sum of v into *out (one double atomic per block)
-__device__ __forceinline__ void block_add(double v, double* out) {
+// each free vertex's incident records (record index * 4 + corner), placed
+// at cursors from the scan of the counts; sorted afterwards
+__global__ void __launch_bounds__(HB) k_heat_inc(const HeatTri* rec, u32 nr, u32* cur, u32* inc) {
+  for (u32 t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
+    const HeatTri h = rec[t];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (h.v[k] >= 0) inc[atomicAdd(cur + h.v[k], 1u)] = 4 * t + (u32)k;
+  }
+}
+
+// per free vertex, in record order: the lumped mass (a third of each
+// incident triangle's area |u x v| / 2) and the stiffness diagonal (the
+// weights of the two edges at the vertex)
+__global__ void __launch_bounds__(HB) k_heat_gather(const HeatTri* rec, u32 n, const u32* vptr, u32* inc,
+                                                    double* mass, double* kdiag) {
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const u32 e0 = vptr[i], e1 = vptr[i + 1];
+    for (u32 a = e0 + 1; a < e1; ++a)  // insertion sort: a vertex has few records
+      for (u32 b = a; b > e0 && inc[b] < inc[b - 1]; --b) {
+        const u32 t = inc[b];
+        inc[b] = inc[b - 1], inc[b - 1] = t;
+      }
+    double m = 0.0, d = 0.0;
+    for (u32 e = e0; e < e1; ++e) {
+      const HeatTri h = rec[inc[e] >> 2];
+      const int c = (int)(inc[e] & 3u);
+      m += h.third;
+      // the edges at corner c are those opposite corners c + 1 and c + 2
+      d += h.w[(c + 1) % 3];
+      d += h.w[(c + 2) % 3];
+    }
+    mass[i] = m;
+    kdiag[i] = d;
+  }
+}
+
+// A reduction slot: the blocks' partial sums and a counter of finished
+// blocks (zeroed once; the last block resets it).
+struct Red {
+  double* part;
+  u32* done;
+};
+
+// block sum of v into *out: each block writes its partial sum, and the last
+// block to finish adds the partials in block order (the same sum on every
+// run, whatever order the blocks ran in)
+__device__ __forceinline__ void block_add(double v, double* out, Red red) {
   __shared__ double s[HB / 32];
+  __shared__ bool last;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    v = threadIdx.x < blockDim.x / 32 ? s[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if (threadIdx.x == 0 && v != 0.0) atomicAdd(out, v);
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) b += s[w];
+    red.part[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(red.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* pv = red.part;
+    double t = 0.0;
+    for (u32 k = 0; k < gridDim.x; ++k) t += pv[k];
+    *out = t;
+    *red.done = 0;
   }
   __syncthreads();
 }
@@ -178,6 +236,14 @@ __global__ void __launch_bounds__(HB) k_heat_merge(u32 n, const u32* rowptr, u32
         ++m;
       }
     }
+    // the row's entries by column, so that each product sums them in one order
+    for (u32 a = 1; a < m; ++a)
+      for (u32 b = a; b > 0 && col[e0 + b] < col[e0 + b - 1]; --b) {
+        const u32 tc = col[e0 + b];
+        col[e0 + b] = col[e0 + b - 1], col[e0 + b - 1] = tc;
+        const double tv = val[e0 + b];
+        val[e0 + b] = val[e0 + b - 1], val[e0 + b - 1] = tv;
+      }
     mcnt[i] = m;
   }
 }
@@ -186,7 +252,7 @@ __global__ void __launch_bounds__(HB) k_heat_merge(u32 n, const u32* rowptr, u32
 // and x . q added into *xq
 __global__ void __launch_bounds__(HB) k_heat_apply(u32 n, const u32* rowptr, const u32* mcnt, const u32* col,
                                                    const double* val, const double* dg, const double* x, double* q,
-                                                   double* xq) {
+                                                   double* xq, Red red) {
   double acc = 0.0;
   for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double xi = x[i];
@@ -196,7 +262,7 @@ __global__ void __launch_bounds__(HB) k_heat_apply(u32 n, const u32* rowptr, con
     q[i] = y;
     acc += xi * y;
   }
-  block_add(acc, xq);
+  block_add(acc, xq, red);
 }
 
 // u over the mesh: 0, then the free values at their vertices
@@ -209,31 +275,32 @@ __global__ void __launch_bounds__(HB) k_heat_put(u32 n, const u32* list, const d
 
 // CG scalars per iteration it: s[4 it + 0] = p.q, s[4 it + 1] = r.z,
 // s[4 it + 2] = r.r (all zeroed before the solve)
-__global__ void __launch_bounds__(HB) k_heat_dot(u64 V, const double* a, const double* b, double* out) {
+__global__ void __launch_bounds__(HB) k_heat_dot(u64 V, const double* a, const double* b, double* out, Red red) {
   double acc = 0.0;
   for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x)
     acc += a[v] * b[v];
-  block_add(acc, out);
+  block_add(acc, out, red);
 }
 
 // r = b - q (q = A x), z = D^-1 r, p = z; r.z into rz, r.r into rr
 __global__ void __launch_bounds__(HB) k_heat_start(u64 V, const double* b, const double* q, const double* dinv,
-                                                   double* r, double* z, double* p, double* rz, double* rr) {
+                                                   double* r, double* z, double* p, double* rz, double* rr, Red r1,
+                                                   Red r2) {
   double a1 = 0.0, a2 = 0.0;
   for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x) {
     const double rv = dinv[v] != 0.0 ? b[v] - q[v] : 0.0, zv = rv * dinv[v];
     r[v] = rv, z[v] = zv, p[v] = zv;
     a1 += rv * zv, a2 += rv * rv;
   }
-  block_add(a1, rz);
-  block_add(a2, rr);
+  block_add(a1, rz, r1);
+  block_add(a2, rr, r2);
 }
 
 // x += alpha p, r -= alpha q, z = D^-1 r, with alpha = rz / pq; the new
 // r.z and r.r
 __global__ void __launch_bounds__(HB) k_heat_update(u64 V, const double* sc, double* x, double* r, double* z,
                                                     const double* p, const double* q, const double* dinv,
-                                                    double* rz_next, double* rr_next) {
+                                                    double* rz_next, double* rr_next, Red r1, Red r2) {
   const double al = sc[0] != 0.0 ? sc[1] / sc[0] : 0.0;  // sc: {p.q, r.z} of this iteration
   double a1 = 0.0, a2 = 0.0;
   for (u64 v = (u64)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (u64)gridDim.x * blockDim.x) {
@@ -242,8 +309,8 @@ __global__ void __launch_bounds__(HB) k_heat_update(u64 V, const double* sc, dou
     r[v] = rv, z[v] = zv;
     a1 += rv * zv, a2 += rv * rv;
   }
-  block_add(a1, rz_next);
-  block_add(a2, rr_next);
+  block_add(a1, rz_next, r1);
+  block_add(a2, rr_next, r2);
 }
 
 // p = z + beta p, beta = rz_next / rz
@@ -273,10 +340,12 @@ unsigned grid_v(u64 n) { return (unsigned)std::max<u64>(1, std::min<u64>((n + HB
 
 }  // namespace
 
+constexpr int RED_BLOCKS = 152 * 8;  // the most blocks of a reducing launch (grid_v)
+
 size_t heat_scratch_bytes(u64 T, u64 V, int maxit) {
-  return 256 * 25 + T * (sizeof(HeatTri) + 6 * (4 + 8)) + V * (4 + 4 + 4 + 4 + 4 + 8 * 10) +
-         8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 +
-         4 * scan_scratch_words((u32)std::min<u64>(V, 0xFFFFFFFFu));
+  return 256 * 32 + T * (sizeof(HeatTri) + 6 * (4 + 8) + 4 + 4 + 12) + V * (4 + 4 + 4 + 4 + 4 + 4 + 4 + 8 * 10) +
+         8 * 4 * (size_t)(maxit + 1) + 8 * 152 * 8 + 8 * 2 * RED_BLOCKS + 16 +
+         4 * scan_scratch_words((u32)std::min<u64>(std::max(T, V), 0xFFFFFFFFu));
 }
 
 int heat_solve(const double* xy, const int* tri, const unsigned short* label, u64 T, u64 V, int L, double alpha,
@@ -290,11 +359,15 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     off = up(off + bytes);
     return p;
   };
-  u32* nrec = (u32*)take(16);
   HeatTri* rec = (HeatTri*)take(T * sizeof(HeatTri));
   u32* flag = (u32*)take(4 * V);
   u32* fidx = (u32*)take(4 * (V + 1));
   u32* list = (u32*)take(4 * V);
+  u32* tf = (u32*)take(4 * T);          // region triangles as 0/1
+  u32* tpos = (u32*)take(4 * (T + 1));  // their scan: record positions
+  u32* vcnt = (u32*)take(4 * V);        // records per free vertex
+  u32* vptr = (u32*)take(4 * (V + 1));  // their scan
+  u32* inc = (u32*)take(4 * 3 * T);     // incident records per free vertex
   double* mass = (double*)take(8 * V);
   double* kdiag = (double*)take(8 * V);
   double* dinv = (double*)take(8 * V);
@@ -311,27 +384,38 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
   double* p = (double*)take(8 * V);
   double* sc = (double*)take(8 * 4 * (size_t)(maxit + 1));  // 4 per iteration
   double* bmax = (double*)take(8 * 152 * 8);
-  u32* sscr = (u32*)take(4 * scan_scratch_words((u32)V) + 4);
+  double* part = (double*)take(8 * 2 * RED_BLOCKS);
+  u32* rdone = (u32*)take(16);
+  u32* sscr = (u32*)take(4 * scan_scratch_words((u32)std::max(T, V)) + 4);
+  const Red r1{part, rdone}, r2{part + RED_BLOCKS, rdone + 1};
   const unsigned gt = grid_v(T);
   const double tau = alpha * dt;
   int launches = 0;
-  if (cudaMemsetAsync(nrec, 0, 16, st) || cudaMemsetAsync(flag, 0, 4 * V, st)) return -1;
+  if (cudaMemsetAsync(flag, 0, 4 * V, st) || cudaMemsetAsync(rdone, 0, 16, st)) return -1;
   k_heat_flags<<<gt, HB, 0, st>>>(tri, label, T, L, flag);
   k_heat_free<<<grid_v(V), HB, 0, st>>>(V, flag);
   launches += 2 + launch_scan(flag, 1, fidx, (u32)V, sscr, st);
   k_heat_list<<<grid_v(V), HB, 0, st>>>(V, flag, fidx, list);
-  u32 n = 0;
-  if (cudaMemcpyAsync(&n, fidx + V, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
-  if (cudaMemsetAsync(mass, 0, 8 * (size_t)std::max<u32>(n, 1), st) ||
-      cudaMemsetAsync(kdiag, 0, 8 * (size_t)std::max<u32>(n, 1), st))
+  k_heat_tflag<<<gt, HB, 0, st>>>(label, T, L, tf);
+  launches += 2 + launch_scan(tf, 1, tpos, (u32)T, sscr, st);
+  u32 n = 0, nr = 0;
+  if (cudaMemcpyAsync(&n, fidx + V, 4, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(&nr, tpos + T, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
     return -1;
-  k_heat_setup<<<gt, HB, 0, st>>>(xy, tri, label, T, L, flag, fidx, rec, nrec, mass, kdiag);
+  if (cudaMemsetAsync(vcnt, 0, 4 * (size_t)std::max<u32>(n, 1), st)) return -1;
+  k_heat_setup<<<gt, HB, 0, st>>>(xy, tri, label, T, L, flag, fidx, tpos, rec, vcnt);
   const unsigned gv = grid_v(n);
-  k_heat_init<<<gv, HB, 0, st>>>(xy, n, list, mass, kdiag, tau, x0, y0, sigma * sigma, amp, x, dg, dinv);
-  u32 nr = 0;
-  if (cudaMemcpyAsync(&nr, nrec, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
   const unsigned gr = grid_v(nr);
-  launches += 3;
+  launches += 1;
+  if (n > 0) {
+    // the free vertices' incident records, sorted, then their mass and diagonal
+    launches += launch_scan(vcnt, 1, vptr, n, sscr, st);
+    if (cudaMemcpyAsync(mcnt, vptr, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st)) return -1;
+    k_heat_inc<<<gr, HB, 0, st>>>(rec, nr, mcnt, inc);
+    k_heat_gather<<<gv, HB, 0, st>>>(rec, n, vptr, inc, mass, kdiag);
+    k_heat_init<<<gv, HB, 0, st>>>(xy, n, list, mass, kdiag, tau, x0, y0, sigma * sigma, amp, x, dg, dinv);
+    launches += 3;
+  }
   // the rows: counts (in flag, free now), their scan, then the entries at
   // cursors starting from the row offsets
   if (n > 0) {
@@ -353,9 +437,9 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     // b = M x_n; start from x_n: r = b - A x_n
     if (cudaMemsetAsync(sc, 0, 8 * 4 * (size_t)(maxit + 1), st)) return -1;
     k_heat_mass<<<gv, HB, 0, st>>>(n, mass, x, b);
-    k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, x, q, bmax);
-    k_heat_start<<<gv, HB, 0, st>>>(n, b, q, dinv, r, z, p, sc + 1, sc + 2);
-    k_heat_dot<<<gv, HB, 0, st>>>(n, b, b, sc + 3);
+    k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, x, q, bmax, r1);
+    k_heat_start<<<gv, HB, 0, st>>>(n, b, q, dinv, r, z, p, sc + 1, sc + 2, r1, r2);
+    k_heat_dot<<<gv, HB, 0, st>>>(n, b, b, sc + 3, r1);
     launches += 4;
     double h2[2];
     if (cudaMemcpyAsync(h2, sc + 2, 16, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st)) return -1;
@@ -364,8 +448,8 @@ int heat_solve(const double* xy, const int* tri, const unsigned short* label, u6
     int it = 0;
     while (rr > stop && it < maxit) {
       double* s0 = sc + 4 * it;  // {p.q, r.z, r.r, -} of iteration it; the next iteration's at s0 + 4
-      k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, p, q, s0);
-      k_heat_update<<<gv, HB, 0, st>>>(n, s0, x, r, z, p, q, dinv, s0 + 5, s0 + 6);
+      k_heat_apply<<<gv, HB, 0, st>>>(n, rowptr, mcnt, col, val, dg, p, q, s0, r1);
+      k_heat_update<<<gv, HB, 0, st>>>(n, s0, x, r, z, p, q, dinv, s0 + 5, s0 + 6, r1, r2);
       k_heat_dir<<<gv, HB, 0, st>>>(n, s0 + 1, s0 + 5, z, p);
       launches += 3;
       ++it;

@@ -105,3 +105,18 @@ def test_full_size_residual():
     rhs = (M * u0)[free]
     assert np.linalg.norm(res) <= 2e-10 * np.linalg.norm(rhs), np.linalg.norm(res) / np.linalg.norm(rhs)
     assert free.sum() > 100000 and 0 < peaks[0] <= 100.0
+
+
+def test_runs_are_bit_identical():
+    """The assembly and the solver's reductions sum in fixed orders (records
+    placed by a scan, each vertex's mass and diagonal gathered in record
+    order, rows sorted by column, block partials added in block order), so
+    two runs give the same bits."""
+    img = synth.voronoi_labels(size=700, nseeds=40)
+    L = int(np.bincount(img.ravel()).argmax())
+    cx = ctx()
+    m = sb.mesh_bitmap(cx, img, 2, 1)
+    a = run_gpu(m, L, 500.0, 0.01, 4, 350.0, 350.0, 60.0)
+    b = run_gpu(m, L, 500.0, 0.01, 4, 350.0, 350.0, 60.0)
+    sb.mesh_release(cx, m)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
