@@ -118,7 +118,7 @@ def load_serving_pool() -> list:
 
 # stage -> source files whose hash the committed DRAM capture records
 STAGE_SOURCES = {
-    "k_corner_bits": ["k_extract.cu"], "k_segments": ["k_extract.cu"], "k_seg_count": ["k_traverse.cu"],
+    "k_corner_bits": ["k_extract.cu"], "k_segments": ["k_extract.cu"], "k_seg_count": ["k_extract.cu", "k_traverse.cu"],
     "k_walk": ["k_traverse.cu"], "k_rank": ["k_traverse.cu"], "k_sort": ["k_cells.cu"],
     "k_cutcells": ["k_cells.cu"], "k_emit": ["k_cells.cu"], "k_tierg": ["k_tierg.cu"],
     "k_lattice_xy": ["k_cells.cu"], "k_scan": ["k_scan.cu"],
@@ -132,7 +132,7 @@ def stage_source_hash(stage: str) -> str | None:
     if not files:
         return None
     hsh = hashlib.sha256()
-    for f in files + ["sbmt_dev.cuh", "sbmt_cell.cuh"]:
+    for f in files + ["sbmt_dev.cuh", "sbmt_cell.cuh", "sbmt_launch.h", "sbmt_walk.cuh"]:
         with open(os.path.join(ROOT, "paper_2602_19474_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]

@@ -410,8 +410,10 @@ __global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ J
                                                        int njobs, BatchDev* bd) {
   __shared__ Job sJ;
   const u32* cpre = bd->recpre + njobs + 1;
-  const u32 nchunks = ONE ? (*jc(one, JC_NREC) + CUT_CHUNK - 1) / CUT_CHUNK : cpre[njobs];
+  const u32 nrec_one = ONE ? *jc(one, JC_NREC) : 0u;
+  const u32 nchunks = ONE ? (nrec_one + CUT_CHUNK - 1) / CUT_CHUNK : cpre[njobs];
   int cur = -1;
+  u32 nrec = nrec_one;
   for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const Job* jp = &one;
     u32 c0 = 0;
@@ -421,13 +423,14 @@ __global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ J
         __syncthreads();
         load_job(jobs, jk, &sJ);
         cur = jk;
+        nrec = *jc(sJ, JC_NREC);
       }
       jp = &sJ;
       c0 = cpre[jk];
     }
     const Job& J = *jp;
     const u32 ri = (c - c0) * CUT_CHUNK + threadIdx.x;
-    if (ri >= *jc(J, JC_NREC)) continue;
+    if (ri >= nrec) continue;
     const GridP& g = J.g;
     u32* err = jc(J, JC_ERR);
     CutRec rec = J.recs[ri];
@@ -499,159 +502,214 @@ __global__ void __launch_bounds__(1024) k_rec_prefix(const Job* __restrict__ job
 }
 
 // ---------------------------------------------------------------------------
-// K4: emission, one block per cell bucket
+// K4: emission, one block per cell bucket (1024 consecutive cell ids)
 // ---------------------------------------------------------------------------
-// Every uncut cell writes its base triangle; every Tier-T cell its staged
-// patch at its offset, with P's id and coordinates.  Tier-G cells are left
-// to the Tier-G kernels, which run beside this one and take their output
+// Every uncut cell writes its base triangle (A, B, C); every Tier-T cell its
+// staged patch at its offset, with P's id and coordinates.  Tier-G cells are
+// left to the Tier-G kernels, which run beside this one and take their output
 // ranges from the same scans.  The bucket's other triangles are written by
-// one block.
+// one block, a thread taking four consecutive cells.
+//
+// Two uncut cells sharing an edge carry one label: a boundary crossing the
+// edge would cut both cells, and none lies along it.  So a maximal run of
+// uncut cells within a strip row takes the label of its first cell, and one
+// pixel is read per run (a block max-scan gives every cell its run's first
+// cell).
+
+// exclusive sums of a and b over the block's earlier threads, and the
+// largest m over them (-1 when none), for 256 threads; sh holds 24 words
+SBMT_DEV void block_scan3(u32 a, u32 b, int m, u32* ea, u32* eb, int* em, u32* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  u32 xa = a, xb = b;
+  int xm = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+    const int ym = __shfl_up_sync(0xffffffffu, xm, o);
+    if (lane >= o) xa += ya, xb += yb, xm = max(xm, ym);
+  }
+  const int prev_m = __shfl_up_sync(0xffffffffu, xm, 1);
+  if (lane == 31) sh[w] = xa, sh[8 + w] = xb, sh[16 + w] = (u32)xm;
+  __syncthreads();
+  if (w == 0) {
+    u32 sa = lane < 8 ? sh[lane] : 0u, sb = lane < 8 ? sh[8 + lane] : 0u;
+    int sm = lane < 8 ? (int)sh[16 + lane] : -1;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const u32 ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
+      const int ym = __shfl_up_sync(0xffffffffu, sm, o);
+      if (lane >= o) sa += ya, sb += yb, sm = max(sm, ym);
+    }
+    if (lane < 8) sh[lane] = sa, sh[8 + lane] = sb, sh[16 + lane] = (u32)sm;
+  }
+  __syncthreads();
+  *ea = (w ? sh[w - 1] : 0u) + xa - a;
+  *eb = (w ? sh[8 + w - 1] : 0u) + xb - b;
+  *em = max(w ? (int)sh[16 + w - 1] : -1, lane ? prev_m : -1);
+}
+
 template <bool ONE>
 __global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job one,
-                                                           const Job* __restrict__ jobs, const u32* __restrict__ bpre,
-                                                           int njobs) {
+                                                   const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                   int njobs) {
   constexpr int NB = 1 << CB_LOG;
-  __shared__ u32 s_cnt[NB];
-  __shared__ u32 s_off[NB];
-  __shared__ u32 s_cb[NB];
-  __shared__ u32 s_sh[8];
+  static_assert(NB == 4 * 256, "four cells per thread");
+  __shared__ __align__(16) u32 s_off[NB];  // triangles per cell, then the bucket's exclusive scan of them
+  __shared__ __align__(16) u32 s_cb[NB];   // inside vertices per record, then their exclusive scan
+  __shared__ unsigned short s_lab[NB];   // the label of each run's first cell
+  __shared__ unsigned short s_head[NB];  // each uncut cell's run's first cell, | 0x8000; 0 for cut cells
+  __shared__ unsigned short s_rowd[NB];  // each cell's strip row, relative to the bucket's first
+  __shared__ u32 s_sh[24];
   __shared__ int s_row0;
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const GridP& g = J.g;
-  const unsigned char* img = J.img;
-  const i64 pitch = J.pitch;
-  const int dtype = J.dtype;
-  const CutRec* const& recs = J.recs;
-  const u32* const& bcut = J.bcut;
-  const u32* const& bbase = J.bbase;
-  const u32* const& extra_scan = J.extra_scan;
-  const u32* const& chain_scan = J.chain_scan;
-  const TStage* const& stg = J.stg;
-  const u32 &NVg = J.NVg, &NE = J.NE, &nbc = J.nbc;
-  int* const& tri = J.tri;
-  unsigned short* const& label = J.label;
-  unsigned short* const& code = J.code;
-  double* const& xy = J.xy;
   const CompactOut& cp = J.cp;
   const u32 b = lb;
   const i64 c0 = (i64)b << CB_LOG;
   const int nc = (int)min((i64)NB, g.ncells - c0);
-  const u32 ncut = bcut[b], rec0 = bbase[b];
+  const u32 ncut = J.bcut[b], rec0 = J.bbase[b];
+  const int t4 = 4 * (int)threadIdx.x;
   if (threadIdx.x == 0) s_row0 = cell_row_near(g, (u32)c0);
-  for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = k < nc ? 1u : 0u;
+  reinterpret_cast<uint4*>(s_off)[threadIdx.x] =
+      make_uint4(t4 < nc ? 1u : 0u, t4 + 1 < nc ? 1u : 0u, t4 + 2 < nc ? 1u : 0u, t4 + 3 < nc ? 1u : 0u);
+  reinterpret_cast<uint4*>(s_cb)[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
-    const CutRec rec = recs[rec0 + r];
-    s_cnt[rec.cell - c0] = rec.ntri;
+    const CutRec rec = J.recs[rec0 + r];
+    s_off[rec.cell - c0] = rec.ntri;  // at least 3: a cut cell is never one triangle
+    s_cb[r] = rec.nchain;
   }
   __syncthreads();
-  // exclusive scan of the bucket's triangle counts (4 cells per thread) and
-  // of the records' inside-vertex counts
+  // this thread's cells: counts, cut flags, strip rows, run starts
+  u32 v[4], ch[4];
+  bool cut[4];
+  int r = s_row0;
+  i64 rs = g.cbase[r], re = r + 1 < g.nrows ? g.cbase[r + 1] : g.ncells;  // the row's cell ids [rs, re)
+  int rowu[4];
+  bool rstart[4];
+  int m = -1;
+  bool prevcut = t4 == 0 || s_off[t4 - 1] != 1u;
   {
-    const int k0 = threadIdx.x * 4;
-    u32 v[4], s = 0;
-    for (int u = 0; u < 4; ++u) v[u] = s_cnt[k0 + u], s += v[u];
-    u32 tot;
-    u32 run = block_exscan256(s, &tot, s_sh);
-    for (int u = 0; u < 4; ++u) s_off[k0 + u] = run, run += v[u];
+    const uint4 a = reinterpret_cast<const uint4*>(s_off)[threadIdx.x];
+    const uint4 c = reinterpret_cast<const uint4*>(s_cb)[threadIdx.x];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+    ch[0] = c.x, ch[1] = c.y, ch[2] = c.z, ch[3] = c.w;
   }
-  {
-    u32 carry = 0;
-    for (u32 base = 0; base < ncut; base += blockDim.x) {
-      const u32 r = base + threadIdx.x;
-      const u32 v = r < ncut ? recs[rec0 + r].nchain : 0u;
-      u32 tot;
-      const u32 ex = block_exscan256(v, &tot, s_sh);
-      if (r < ncut) s_cb[r] = carry + ex;
-      carry += tot;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int k = t4 + u;
+    cut[u] = v[u] != 1u;
+    const i64 cid = c0 + k;
+    bool rowstart = false;
+    if (k < nc) {
+      while (cid >= re) rs = re, ++r, re = r + 1 < g.nrows ? g.cbase[r + 1] : g.ncells;
+      rowstart = cid == rs;
     }
+    rowu[u] = r;
+    rstart[u] = rowstart;
+    if (!cut[u] && (k == 0 || prevcut || rowstart)) m = k;
+    prevcut = cut[u];
   }
-  __syncthreads();
-  const u32 T0_ = (u32)c0 + extra_scan[b];
-  const u32 CB0 = NVg + NE + chain_scan[b];
-  const int row0 = s_row0;
-  // uncut cells: the base triangle (A, B, C), untouched.  Per strip row the
-  // corner ids are row base + i, the centroid's pixel row is tabulated, and
-  // its pixel column is an integer floor.  A thread's four cells (the block
-  // has 256 threads for 1024 cells) are set up first with their pixel loads
-  // issued, then written, so that the loads are in flight together.
-  static_assert(NB == 4 * 256, "four cells per thread");
-  int r = -1;
-  i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0, jr = 0;
-  int lr0 = 0, lr1 = 0;
+  u32 ex_t, ex_c;
+  int em;
+  block_scan3(v[0] + v[1] + v[2] + v[3], ch[0] + ch[1] + ch[2] + ch[3], m, &ex_t, &ex_c, &em, s_sh);
+  // the run start of each cell, and the scans in place
+  int head[4];
+  {
+    u32 rt = ex_t, rc = ex_c;
+    int hm = em;
+    prevcut = t4 == 0 || s_off[t4 - 1] != 1u;  // s_off still holds the counts here
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = t4 + u;
+      const bool start = !cut[u] && (k == 0 || prevcut || rstart[u]);
+      if (start) hm = k;
+      head[u] = hm;
+      prevcut = cut[u];
+      s_head[k] = cut[u] ? (unsigned short)0 : (unsigned short)(0x8000 | hm);
+      s_rowd[k] = (unsigned short)(rowu[u] - s_row0);
+    }
+    reinterpret_cast<uint4*>(s_off)[threadIdx.x] = make_uint4(rt, rt + v[0], rt + v[0] + v[1], rt + v[0] + v[1] + v[2]);
+    reinterpret_cast<uint4*>(s_cb)[threadIdx.x] = make_uint4(rc, rc + ch[0], rc + ch[0] + ch[1], rc + ch[0] + ch[1] + ch[2]);
+  }
+  // run starts read their pixel: column floor((2 xc + S) / 2S) of the
+  // centroid, xc = ox + 3p (c + j + 1) for cell index c in strip row j; row
+  // tabulated per strip row and cell parity
   const i64 twoS = 2 * g.S;
   const float inv2S = 1.0f / (float)twoS;
-  int tv0[4], tv1[4], tv2[4], traw[4];
-  u32 to[4];
-  bool tuc[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int k = (int)threadIdx.x + j * 256;
-    tuc[j] = k < nc && s_cnt[k] == 1u;
-    traw[j] = OUTSIDE, tv0[j] = tv1[j] = tv2[j] = 0, to[j] = 0;
-    if (!tuc[j]) continue;
-    const i64 cid = c0 + k;
-    if (r < 0 || cid >= cb_r + (g.chi[r] - clo_r + 1)) {
-      if (r < 0) r = row0;
-      while (r + 1 < g.nrows && g.cbase[r + 1] <= cid) ++r;
-      clo_r = g.clo[r], cb_r = g.cbase[r], jr = g.j0 + r;
-      vb0 = g.vbase[r] - g.vlo[r], vb1 = g.vbase[r + 1] - g.vlo[r + 1];
-      lr0 = g.lrow[2 * r], lr1 = g.lrow[2 * r + 1];
-    }
-    const i64 c = clo_r + (cid - cb_r), i = c >> 1;
-    to[j] = T0_ + s_off[k];
-    int prow;
-    i64 xc;
-    if ((c & 1) == 0) {
-      tv0[j] = (int)(vb0 + i), tv1[j] = (int)(vb0 + i + 1), tv2[j] = (int)(vb1 + i);
-      xc = g.ox + 3 * g.p * (2 * i + jr + 1), prow = lr0;
-    } else {
-      tv0[j] = (int)(vb0 + i + 1), tv1[j] = (int)(vb1 + i + 1), tv2[j] = (int)(vb1 + i);
-      xc = g.ox + 3 * g.p * (2 * i + jr + 2), prow = lr1;
-    }
-    // pixel column floor((2 xc + S) / 2S) in 32 bits: a float estimate, corrected
+  for (int u = 0; u < 4; ++u) {
+    const int k = t4 + u;
+    if (head[u] != k || cut[u] || k >= nc) continue;
+    const int rr = rowu[u];
+    const i64 c = g.clo[rr] + ((c0 + k) - g.cbase[rr]);
+    const i64 xc = g.ox + 3 * g.p * (c + g.j0 + rr + 1);
+    const int prow = g.lrow[2 * rr + (int)(c & 1)];
     const int num = (int)(2 * xc + g.S), den = (int)twoS;
     int pcol = (int)floorf((float)num * inv2S);
     while (pcol * den > num) --pcol;
     while ((pcol + 1) * den <= num) ++pcol;
-    traw[j] = dtype == 1 ? pix<unsigned char>(img, pitch, g.W, g.H, pcol, prow)
-                         : pix<unsigned short>(img, pitch, g.W, g.H, pcol, prow);
+    const int l = J.dtype == 1 ? pix<unsigned char>(J.img, J.pitch, g.W, g.H, pcol, prow)
+                               : pix<unsigned short>(J.img, J.pitch, g.W, g.H, pcol, prow);
+    s_lab[k] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
   }
+  __syncthreads();
+  const u32 T0_ = (u32)c0 + J.extra_scan[b];
+  // uncut cells: the base triangle (A, B, C), untouched; corner ids are the
+  // vertex row bases plus i.  Here a thread takes cells 256 apart, so that
+  // the warp's stores of neighbouring cells are adjacent.
+  int rr_prev = -1;
+  i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (!tuc[j]) continue;
-    const unsigned short lab = traw[j] == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)traw[j];
+  for (int u = 0; u < 4; ++u) {
+    const int k = (int)threadIdx.x + 256 * u;
+    const unsigned hk = s_head[k];
+    if (k >= nc || !(hk & 0x8000u)) continue;
+    const unsigned short lab = s_lab[hk & 0x3FFu];
+    const i64 cid = c0 + k;
     if (cp.on) {  // the base triangle stays implicit: its cell's label and code
-      const i64 cid = c0 + (int)threadIdx.x + j * 256;
       cp.cell_label[cid] = lab, cp.cell_code[cid] = 0;
       continue;
     }
-    const u32 o = to[j];
-    tri[3 * (i64)o] = tv0[j];
-    tri[3 * (i64)o + 1] = tv1[j];
-    tri[3 * (i64)o + 2] = tv2[j];
-    label[o] = lab;
-    code[o] = 0;
+    const int rr = s_row0 + s_rowd[k];
+    if (rr != rr_prev) {
+      rr_prev = rr;
+      clo_r = g.clo[rr], cb_r = g.cbase[rr];
+      vb0 = g.vbase[rr] - g.vlo[rr], vb1 = g.vbase[rr + 1] - g.vlo[rr + 1];
+    }
+    const i64 c = clo_r + (cid - cb_r), i = c >> 1;
+    int a0, a1, a2;
+    if ((c & 1) == 0) a0 = (int)(vb0 + i), a1 = (int)(vb0 + i + 1), a2 = (int)(vb1 + i);
+    else a0 = (int)(vb0 + i + 1), a1 = (int)(vb1 + i + 1), a2 = (int)(vb1 + i);
+    const u32 o = T0_ + s_off[k];
+    J.tri[3 * (i64)o] = a0;
+    J.tri[3 * (i64)o + 1] = a1;
+    J.tri[3 * (i64)o + 2] = a2;
+    J.label[o] = lab;
+    J.code[o] = 0;
   }
-  // cut cells
-  int row = row0;
+  // cut cells: one thread per record (a bucket has a few dozen, so they
+  // share a warp or two)
+  const u32 CB0 = J.NVg + J.NE + J.chain_scan[b];
   const double invS = 1.0 / (double)g.S;
+  int row = s_row0;
   for (u32 rr = threadIdx.x; rr < ncut; rr += blockDim.x) {
-    CutRec rec = recs[rec0 + rr];
+    const CutRec rec = J.recs[rec0 + rr];
     const u32 kl = rec.cell - (u32)c0, cb = CB0 + s_cb[rr];
     u32 off = T0_ + s_off[kl];
     if (cp.on) {
       // patch triangles before this cell: those of earlier buckets, then the
       // bucket's earlier cut cells (their extra triangles plus one each)
       const u32 gi = cp.cut_scan[b] + rr;
-      off = extra_scan[b] + cp.cut_scan[b] + rr + (s_off[kl] - kl);
+      off = J.extra_scan[b] + cp.cut_scan[b] + rr + (s_off[kl] - kl);
       cp.patch_cell[gi] = rec.cell, cp.patch_off[gi] = off;
       cp.cell_label[rec.cell] = 0xFFFF, cp.cell_code[rec.cell] = (unsigned short)(rec.code & 0xFFFFu);
     }
     if (rec.code & (1u << 16)) continue;  // Tier-G
     row = advance_row(g, row, rec.cell);
     const CellGeo cg = cell_geo(g, rec.cell, row);
-    const TStage st = stg[rec0 + rr];
+    const TStage st = J.stg[rec0 + rr];
     const unsigned long long w = g_keys.tris[(((rec.code >> 6) & 63u) - 1) * 3 + ((rec.code >> 4) & 3u)];
     const u32 ga = vid(g, cg.ci[0], cg.cj[0]), gb = vid(g, cg.ci[1], cg.cj[1]), gc = vid(g, cg.ci[2], cg.cj[2]);
     auto gid = [&](int l) -> u32 {
@@ -671,21 +729,22 @@ __global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job o
     for (int k = 0; k < 7; ++k) {
       if (k >= (int)rec.ntri) break;
       const u32 o = off + (u32)k;
-      tri[3 * (i64)o] = (int)gid(tri_label(w, k, 0));
-      tri[3 * (i64)o + 1] = (int)gid(tri_label(w, k, 1));
-      tri[3 * (i64)o + 2] = (int)gid(tri_label(w, k, 2));
-      label[o] = st.lab[k];
-      code[o] = cd;
+      J.tri[3 * (i64)o] = (int)gid(tri_label(w, k, 0));
+      J.tri[3 * (i64)o + 1] = (int)gid(tri_label(w, k, 1));
+      J.tri[3 * (i64)o + 2] = (int)gid(tri_label(w, k, 2));
+      J.label[o] = st.lab[k];
+      J.code[o] = cd;
     }
     if (rec.nchain == 1) {
       const Pq p = corner_of_id(g, rec.tri_off);
-      double2 v;
-      v.x = zdouble(p.x) * invS;
-      v.y = zdouble(p.y) * invS;
-      reinterpret_cast<double2*>(xy)[cb - cp.xy0] = v;
+      double2 vv;
+      vv.x = zdouble(p.x) * invS;
+      vv.y = zdouble(p.y) * invS;
+      reinterpret_cast<double2*>(J.xy)[cb - cp.xy0] = vv;
     }
   }
-  if (cp.on && b == nbc - 1 && threadIdx.x == 0) cp.patch_off[cp.cut_scan[nbc]] = extra_scan[nbc] + cp.cut_scan[nbc];
+  if (cp.on && b == J.nbc - 1 && threadIdx.x == 0)
+    cp.patch_off[cp.cut_scan[J.nbc]] = J.extra_scan[J.nbc] + cp.cut_scan[J.nbc];
 }
 
 // lattice vertex coordinates.  Vertex v(i, j) has x = (ox + 3p m) / S with

@@ -158,17 +158,9 @@ SBMT_DEV u32 lab16(int l) { return l == OUTSIDE ? 0xFFFFu : (u32)l; }
 
 // K1b: one thread per 32-corner word of a row bit-plane; every vertex starts
 // its +x and +y runs.  Output slots are taken one atomic per warp.
-// the number of grid cells a segment visits (its pairs), for the batched
-// path; the single-image extraction passes no grid
-struct PairCount {
-  const GridP* g;
-  u32* npairs;
-};
-
 template <typename T>
 SBMT_DEV void segments_word(const unsigned char* img, i64 pitch, int W, int H, const u32* vrow, int wpr,
-                            const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, i64 t,
-                            PairCount pc = PairCount{nullptr, nullptr}) {
+                            const u32* vcol, int wpc, Seg* segs, u32 cap, u32* nseg, u32* err, i64 t) {
   const bool in = t < (i64)(H + 1) * wpr;
   const int cy = in ? (int)(t / wpr) : 0, w = in ? (int)(t % wpr) : 0;
   const u32 bits = in ? vrow[t] : 0u;
@@ -220,15 +212,6 @@ SBMT_DEV void segments_word(const unsigned char* img, i64 pitch, int W, int H, c
       ++slot;
     }
   }
-  if (pc.g) {
-    // the pair counts of the warp's segments, one lane per segment: the
-    // walk setup runs densely instead of once per segment-writing lane
-    __syncwarp();
-    for (u32 i = (u32)lane; i < wtot; i += 32) {
-      const u32 sl = wbase + i;
-      if (sl < cap) pc.npairs[sl] = seg_pairs(*pc.g, segs[sl]);
-    }
-  }
 }
 
 template <typename T>
@@ -239,19 +222,30 @@ __global__ void k_segments(const unsigned char* img, i64 pitch, int W, int H, co
 }
 
 template <bool ONE>
-__global__ void __launch_bounds__(256, 4) k_segments_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(256) k_segments_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
                                                        const u32* __restrict__ bpre, int njobs) {
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const i64 t = (i64)lb * blockDim.x + threadIdx.x;
   u32* cnt = J.zero;
   const GridP& g = J.g;
-  const PairCount pc{&g, J.npairs};
   if (J.dtype == 1)
     segments_word<unsigned char>(J.img, J.pitch, g.W, g.H, J.vrow, J.wpr, J.vcol, J.wpc, J.segs, J.seg_cap,
-                                 cnt + JC_NSEG, cnt + JC_ERR, t, pc);
+                                 cnt + JC_NSEG, cnt + JC_ERR, t);
   else
     segments_word<unsigned short>(J.img, J.pitch, g.W, g.H, J.vrow, J.wpr, J.vcol, J.wpc, J.segs, J.seg_cap,
-                                  cnt + JC_NSEG, cnt + JC_ERR, t, pc);
+                                  cnt + JC_NSEG, cnt + JC_ERR, t);
+}
+
+// the cells each segment visits (its pairs), densely over the segments the
+// device counted: a job's blocks stride over its segments
+template <bool ONE>
+__global__ void __launch_bounds__(256) k_seg_count_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                     const u32* __restrict__ bpre, int njobs) {
+  SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const u32 nb = ONE ? gridDim.x : bpre[jk + 1] - bpre[jk];
+  const u32 n = min(*jc(J, JC_NSEG), J.seg_cap);
+  const GridP& g = J.g;
+  for (u32 s = lb * blockDim.x + threadIdx.x; s < n; s += nb * blockDim.x) J.npairs[s] = seg_pairs(g, J.segs[s]);
 }
 
 }  // namespace
@@ -289,6 +283,13 @@ int launch_segments_b(const Job* one, const Job* jobs, const u32* bpre, int njob
   if (nblocks == 0) return 0;
   if (one) k_segments_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
   else k_segments_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  return 1;
+}
+
+int launch_seg_count_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
+  if (nblocks == 0) return 0;
+  if (one) k_seg_count_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_seg_count_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
   return 1;
 }
 

@@ -749,9 +749,14 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
     const std::vector<u32> ps = prefix_of(n, [&](int k) {
       return (u32)(((i64)(G[k].H + 1) * J[k].wpr + 255) / 256);
     });
+    // the pair counts: a job's blocks stride over its segments, about 1216
+    // blocks over the batch, at least one and at most enough for its room
+    const std::vector<u32> pq = prefix_of(n, [&](int k) {
+      return std::max<u32>(1, std::min<u32>((cap[k] + 255) / 256, std::max<u32>(1, 1216 / (u32)n)));
+    });
     // the job table, the scan jobs and the block prefixes in one upload
     const size_t b_jobs = up256(n * sizeof(Job)), b_sj = up256(n * sizeof(ScanJob)), b_pre = up256((n + 1) * 4);
-    const size_t bytes = b_jobs + b_sj + 3 * b_pre;
+    const size_t bytes = b_jobs + b_sj + 4 * b_pre;
     char *hs, *ds;
     if ((rc = aalloc(lane, &ds, bytes)) || (rc = stage_begin(lane, bytes, &hs))) return bail(rc);
     std::memcpy(hs, J.data(), n * sizeof(Job));
@@ -759,12 +764,14 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
     std::memcpy(hs + b_jobs + b_sj, pc.data(), (n + 1) * 4);
     std::memcpy(hs + b_jobs + b_sj + b_pre, ps.data(), (n + 1) * 4);
     std::memcpy(hs + b_jobs + b_sj + 2 * b_pre, tpre.data(), (n + 1) * 4);
+    std::memcpy(hs + b_jobs + b_sj + 3 * b_pre, pq.data(), (n + 1) * 4);
     if ((rc = stage_copy(lane, ds, bytes))) return bail(rc);
     const Job* djobs = (const Job*)ds;
     const ScanJob* dsj = (const ScanJob*)(ds + b_jobs);
     const u32* dpc = (const u32*)(ds + b_jobs + b_sj);
     const u32* dps = (const u32*)(ds + b_jobs + b_sj + b_pre);
     const u32* dtp = (const u32*)(ds + b_jobs + b_sj + 2 * b_pre);
+    const u32* dpq = (const u32*)(ds + b_jobs + b_sj + 3 * b_pre);
     // the test of the wait bound: the second tile of the first image's scan
     // withholds its sums, so that the third tile's wait runs out
     const u32 stall = (opt.stall && tpre[1] >= 3) ? 1u : NONE;
@@ -772,6 +779,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
     const Job* one_a = n == 1 ? &J[0] : nullptr;
     TRACE(KN_CORNER, launch_corner_bits_b(one_a, djobs, dpc, n, pc[n], st));
     TRACE(KN_SEG, launch_segments_b(one_a, djobs, dps, n, ps[n], st));
+    TRACE(KN_TCOUNT, launch_seg_count_b(one_a, djobs, dpq, n, pq[n], st));
     TRACE(KN_SCAN, launch_mscan(dsj, dtp, n, ntiles, flags, ticket, stall, st));
     TRACE(KN_TCOUNT, launch_counts_b(djobs, n, lane->cnt_d, st));
     CK(cudaGetLastError());

@@ -152,9 +152,11 @@ int launch_mscan(const ScanJob* sj, const u32* tpre, int nsj, u32 ntiles, unsign
 // parameter), else null.
 int launch_corner_bits_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
 int launch_segments_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
+// each segment's pair count (cells visited) into npairs, over the segments
+// the device counted (a job's blocks stride over them)
+int launch_seg_count_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
 // per job {PSLG vertices (2 words), segments, error, pairs} into out (mapped
-// host memory).  launch_segments_b also writes each segment's pair count
-// (cells visited) into npairs at the segment's slot.
+// host memory)
 int launch_counts_b(const Job* jobs, int njobs, u32* out, cudaStream_t st);
 int launch_chunk_map_b(const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
 int launch_walk_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st);
