@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(256) k_sort_b(const __grid_constant__ Job one,
   __shared__ unsigned short s_cut[NB];
   __shared__ u32 s_sh[8];
   __shared__ u32 s_base;
+  __shared__ u32 s_kc[NCLS], s_kb[NCLS];
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const Pair* pairs = J.pairs;
   Pair* sorted = J.raw;
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(256) k_sort_b(const __grid_constant__ Job one,
     return;
   }
   for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0;
+  if (threadIdx.x < NCLS) s_kc[threadIdx.x] = 0;
   __syncthreads();
   for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[pairs[lo + i].cell - c0], 1u);
   __syncthreads();
@@ -288,10 +290,20 @@ __global__ void __launch_bounds__(256) k_sort_b(const __grid_constant__ Job one,
     sorted[lo + slot] = p;
   }
   const u32 base = s_base;
-  for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
+  // records, and their places in the class lists (the order within a class
+  // is only the classification's work order)
+  u32 slot[4], cls[4];
+  for (u32 r = threadIdx.x, u = 0; r < ncut; r += blockDim.x, ++u) {
     const int k = s_cut[r];
     recs[base + r] = CutRec{(u32)(c0 + k), lo + s_off[k], s_cnt[k], 0u, 0u, 0u, 0u, 0u};
+    cls[u] = (u32)piece_class(s_cnt[k]);
+    slot[u] = atomicAdd(&s_kc[cls[u]], 1u);
   }
+  __syncthreads();
+  if (threadIdx.x < NCLS && s_kc[threadIdx.x]) s_kb[threadIdx.x] = atomicAdd(jc(J, JC_KCNT + threadIdx.x), s_kc[threadIdx.x]);
+  __syncthreads();
+  for (u32 r = threadIdx.x, u = 0; r < ncut; r += blockDim.x, ++u)
+    J.klist[(size_t)cls[u] * J.NP + s_kb[cls[u]] + slot[u]] = base + r;
   if (threadIdx.x == 0) bcut[b] = ncut, bbase[b] = base;
 }
 
@@ -401,19 +413,26 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 // (cells in ngcell, triangles in ngtri, cells per local vertex count in
 // gcnt, counts above TIERG_TN pooled at TIERG_TN + 1).
 // The records of every job form one work queue, handed out in chunks of
-// CUT_CHUNK records of one job (recpre[njobs + 1 + k]: the chunks before job
-// k), so that a block works for one job at a time with its descriptor in
-// shared memory; the Tier-G size counts are batch-wide, so that the Tier-G
+// CUT_CHUNK records of one job and one piece class (recpre[njobs + 1 + k]:
+// the chunks before job k), so that a block works for one job at a time with
+// its descriptor in shared memory and a warp's cells have as many boundary
+// pieces; the Tier-G size counts are batch-wide, so that the Tier-G
 // kernels take the largest cells of the whole batch first.
 template <bool ONE>
 __global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
                                                        int njobs, BatchDev* bd) {
   __shared__ Job sJ;
+  __shared__ u32 s_kc[NCLS];
   const u32* cpre = bd->recpre + njobs + 1;
-  const u32 nrec_one = ONE ? *jc(one, JC_NREC) : 0u;
-  const u32 nchunks = ONE ? (nrec_one + CUT_CHUNK - 1) / CUT_CHUNK : cpre[njobs];
+  u32 nchunks = 0;
+  if constexpr (ONE) {
+    for (int q = 0; q < NCLS; ++q) nchunks += (*jc(one, JC_KCNT + q) + CUT_CHUNK - 1) / CUT_CHUNK;
+    if (threadIdx.x < NCLS) s_kc[threadIdx.x] = *jc(one, JC_KCNT + threadIdx.x);
+    __syncthreads();
+  } else {
+    nchunks = cpre[njobs];
+  }
   int cur = -1;
-  u32 nrec = nrec_one;
   for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const Job* jp = &one;
     u32 c0 = 0;
@@ -422,15 +441,25 @@ __global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ J
       if (jk != cur) {
         __syncthreads();
         load_job(jobs, jk, &sJ);
+        if (threadIdx.x < NCLS) s_kc[threadIdx.x] = *jc(sJ, JC_KCNT + threadIdx.x);
+        __syncthreads();
         cur = jk;
-        nrec = *jc(sJ, JC_NREC);
       }
       jp = &sJ;
       c0 = cpre[jk];
     }
     const Job& J = *jp;
-    const u32 ri = (c - c0) * CUT_CHUNK + threadIdx.x;
-    if (ri >= nrec) continue;
+    // the job's chunks run class by class: this chunk's class and place
+    u32 cc = c - c0;
+    int q = 0;
+    for (; q < NCLS - 1; ++q) {
+      const u32 nq = (s_kc[q] + CUT_CHUNK - 1) / CUT_CHUNK;
+      if (cc < nq) break;
+      cc -= nq;
+    }
+    const u32 pos = cc * CUT_CHUNK + threadIdx.x;
+    if (pos >= s_kc[q]) continue;
+    const u32 ri = J.klist[(size_t)q * J.NP + pos];
     const GridP& g = J.g;
     u32* err = jc(J, JC_ERR);
     CutRec rec = J.recs[ri];
@@ -485,7 +514,9 @@ __global__ void __launch_bounds__(1024) k_rec_prefix(const Job* __restrict__ job
   carry = 0;
   for (int base = 0; base < njobs; base += 1024) {
     const int k = base + (int)threadIdx.x;
-    const u32 v = k < njobs ? (*jc(jobs[k], JC_NREC) + CUT_CHUNK - 1) / CUT_CHUNK : 0u;
+    u32 v = 0;
+    if (k < njobs)
+      for (int q = 0; q < NCLS; ++q) v += (*jc(jobs[k], JC_KCNT + q) + CUT_CHUNK - 1) / CUT_CHUNK;
     sh[threadIdx.x] = v;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {

@@ -61,32 +61,69 @@ SBMT_DEV void load8(const unsigned char* img, i64 pitch, int W, int H, int x0, i
 }
 
 // K1a: a block covers 32 corner rows x 256 corner columns; each thread takes
-// 8 consecutive corners of 4 rows.  Vertex flags go to shared memory as one
-// byte per (row, 8 corners), then out as row words and transposed column words.
+// 8 consecutive corners of 4 rows.  The block's pixels (33 rows, the 256
+// columns and a 16-byte halo chunk to their left) are first staged in shared
+// memory with asynchronous 16-byte copies, every copy of the tile in flight
+// at once; chunks that leave the image or are not 16-byte aligned are read
+// pixel by pixel.  Vertex flags go to shared memory as one byte per (row, 8
+// corners), then out as row words and transposed column words.
+constexpr int CB_ROWS = 33;  // pixel rows r0 - 1 .. r0 + 31
+
+template <typename T>
+struct CornerTile {
+  static constexpr int CHUNK = 16 / (int)sizeof(T);  // pixels per 16-byte chunk
+  static constexpr int COLS = 256 + CHUNK;           // columns x0 - CHUNK .. x0 + 255
+  static constexpr int NCH = COLS / CHUNK;           // chunks per row
+  __align__(16) T px[CB_ROWS][COLS];
+};
+
+SBMT_DEV void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+SBMT_DEV void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename T>
 SBMT_DEV void corner_bits_tile(const unsigned char* img, i64 pitch, int W, int H, u32* vrow, int wpr, u32* vcol,
                                int wpc, unsigned long long* nvtx, int bx, int by, unsigned char (*fl)[33],
-                               unsigned int& cnt) {
+                               unsigned int& cnt, CornerTile<T>& tile) {
+  using TT = CornerTile<T>;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int x0 = bx * 256 + lane * 8;  // first corner column of this thread
-  const int r0 = by * 32;
+  const int xb = bx * 256, r0 = by * 32;
+  const int xs = xb - TT::CHUNK;  // first staged column
   if (threadIdx.x == 0) cnt = 0;
+  // stage rows r0 - 1 .. r0 + 31, columns xs .. xb + 255 (in-image pixels only)
+  for (int q = threadIdx.x; q < CB_ROWS * TT::NCH; q += blockDim.x) {
+    const int tr = q / TT::NCH, ch = q - tr * TT::NCH;
+    const int y = r0 - 1 + tr, x = xs + ch * TT::CHUNK;
+    if (y < 0 || y >= H) continue;
+    const T* src = (const T*)(img + (i64)y * pitch) + x;
+    T* dst = &tile.px[tr][ch * TT::CHUNK];
+    if (x >= 0 && x + TT::CHUNK <= W && (((uintptr_t)src) & 15) == 0) {
+      cp_async16(dst, src);
+    } else {
+      for (int k = 0; k < TT::CHUNK; ++k)
+        if (x + k >= 0 && x + k < W) dst[k] = src[k];
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
+  // pixel (x, y) of the tile, OUTSIDE beyond the image
+  auto P = [&](int x, int y) -> int {
+    return (x < 0 || x >= W || y < 0 || y >= H) ? OUTSIDE : (int)tile.px[y - r0 + 1][x - xs];
+  };
   u32 mycnt = 0;
+  const int x0 = xb + lane * 8;  // first corner column of this thread
   for (int rr = 0; rr < 4; ++rr) {
     const int r = w * 4 + rr, cy = r0 + r;
     int lo[9], hi[9];  // pixel rows cy-1 and cy, columns x0-1 .. x0+7
-    load8<T>(img, pitch, W, H, x0, cy - 1, lo + 1);
-    load8<T>(img, pitch, W, H, x0, cy, hi + 1);
-    // the pixel left of x0 is the previous lane's last one
-    int pl = __shfl_up_sync(0xffffffffu, lo[8], 1), ph = __shfl_up_sync(0xffffffffu, hi[8], 1);
-    if (lane == 0) {
-      const bool in = x0 - 1 >= 0 && x0 - 1 < W;
-      pl = (in && cy - 1 >= 0 && cy - 1 < H) ? (int)((const T*)(img + (i64)(cy - 1) * pitch))[x0 - 1] : OUTSIDE;
-      ph = (in && cy >= 0 && cy < H) ? (int)((const T*)(img + (i64)cy * pitch))[x0 - 1] : OUTSIDE;
-    }
-    lo[0] = pl, hi[0] = ph;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) lo[k] = P(x0 - 1 + k, cy - 1), hi[k] = P(x0 - 1 + k, cy);
     u32 bits = 0;
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
       // corner (x0 + k, cy): a = (cx-1, cy-1), b = (cx, cy-1), c = (cx-1, cy), d = (cx, cy)
       const int a = lo[k], b = lo[k + 1], c = hi[k], d = hi[k + 1];
@@ -122,7 +159,8 @@ __global__ void __launch_bounds__(256) k_corner_bits(const unsigned char* img, i
                                                      int wpr, u32* vcol, int wpc, unsigned long long* nvtx) {
   __shared__ unsigned char fl[32][33];
   __shared__ unsigned int cnt;
-  corner_bits_tile<T>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx, blockIdx.x, blockIdx.y, fl, cnt);
+  __shared__ CornerTile<T> tile;
+  corner_bits_tile<T>(img, pitch, W, H, vrow, wpr, vcol, wpc, nvtx, blockIdx.x, blockIdx.y, fl, cnt, tile);
 }
 
 // batched: job k's tiles are its blocks, row-major over (256-column, 32-row) tiles
@@ -131,14 +169,19 @@ __global__ void __launch_bounds__(256) k_corner_bits_b(const __grid_constant__ J
                                                        const u32* __restrict__ bpre, int njobs) {
   __shared__ unsigned char fl[32][33];
   __shared__ unsigned int cnt;
+  __shared__ union {
+    CornerTile<unsigned char> t8;
+    CornerTile<unsigned short> t16;
+  } tile;
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const int W = J.g.W, H = J.g.H, gx = (W + 1 + 255) / 256;
   const int bx = (int)(lb % (u32)gx), by = (int)(lb / (u32)gx);
   unsigned long long* nvtx = (unsigned long long*)J.zero;
   if (J.dtype == 1)
-    corner_bits_tile<unsigned char>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt);
+    corner_bits_tile<unsigned char>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt, tile.t8);
   else
-    corner_bits_tile<unsigned short>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt);
+    corner_bits_tile<unsigned short>(J.img, J.pitch, W, H, J.vrow, J.wpr, J.vcol, J.wpc, nvtx, bx, by, fl, cnt,
+                                     tile.t16);
 }
 
 // first set bit at index >= from in a packed bit-plane line of nwords words;

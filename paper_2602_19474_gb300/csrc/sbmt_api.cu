@@ -198,7 +198,7 @@ struct Lane {
   // streams beside the main kernels, forked from and joined back into the
   // lane's stream
   cudaStream_t side = nullptr, side2 = nullptr;  // side2: the Tier-G warp kernel
-  cudaEvent_t fork = nullptr, join = nullptr, order = nullptr, warp = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, order = nullptr, warp = nullptr, lat = nullptr;
   // per-call scratch: bump allocation in stream-ordered chunks
   std::vector<std::pair<char*, size_t>> chunks;
   size_t chunk_used = 0, call_bytes = 0;
@@ -362,7 +362,7 @@ void lane_release(Lane* L) {
   if (L->own_stream) cudaStreamDestroy(L->stream);
   if (L->side) cudaStreamSynchronize(L->side), cudaStreamDestroy(L->side);
   if (L->side2) cudaStreamSynchronize(L->side2), cudaStreamDestroy(L->side2);
-  for (cudaEvent_t e : {L->fork, L->join, L->order, L->warp, L->stage_ev})
+  for (cudaEvent_t e : {L->fork, L->join, L->order, L->warp, L->lat, L->stage_ev})
     if (e) cudaEventDestroy(e);
 }
 
@@ -377,7 +377,7 @@ int lane_side(Lane* L) {
       *s = nullptr;
       return fail(SBMT_ECUDA, "side stream");
     }
-  for (cudaEvent_t* e : {&L->fork, &L->join, &L->order, &L->warp})
+  for (cudaEvent_t* e : {&L->fork, &L->join, &L->order, &L->warp, &L->lat})
     if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
       *e = nullptr;
       return fail(SBMT_ECUDA, "fork/join events");
@@ -853,7 +853,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
         (rc = aalloc(lane, &j.poff, nbc + 1)) || (rc = aalloc(lane, &j.eoff, nbe + 1)) ||
         (rc = aalloc(lane, &j.pcur, nbc + 1)) || (rc = aalloc(lane, &j.ecur, nbe + 1)) ||
         (rc = aalloc(lane, &j.extra_scan, nbc + 1)) || (rc = aalloc(lane, &j.chain_scan, nbc + 1)) ||
-        (rc = aalloc(lane, &j.stg, NP)))
+        (rc = aalloc(lane, &j.stg, NP)) || (rc = aalloc(lane, &j.klist, (size_t)NCLS * NP)))
       return bail(rc);
     if (m->keep) {
       if ((rc = dalloc(lane, &j.ev, NE, m->scratch)) || (rc = dalloc(lane, &j.recs, NP, m->scratch)) ||
@@ -978,6 +978,14 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
     lane->capturing = true;
   }
   int kerr = 0;
+  // the lattice coordinates need only the grid: written on a side stream
+  // beside the compute-bound walk and registry (its writes are the only
+  // bandwidth-bound work there); the Tier-G join below waits for it
+  if (fork) {
+    if (cudaEventRecord(lane->lat, st) != cudaSuccess || cudaStreamWaitEvent(lane->side2, lane->lat, 0) != cudaSuccess)
+      kerr = 1;
+    TRACE_ON(KN_XY, lane->side2, launch_lattice_b(dj, dpre(6), p_lt[n], dpre(7), p_lx[n], n, lane->side2));
+  }
   TRACE(KN_TCOUNT, launch_chunk_map_b(dj, dpre(0), n, p_cm[n], st));
   TRACE(KN_TEMIT, launch_walk_b(one, dj, dpre(1), n, p_walk[n], st));
   TRACE(KN_SCAN, launch_mscan(ds1, dpre(8), 2 * n, nt1, flags1, tickets, NONE, st));
@@ -1004,7 +1012,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   if (ntg < 0) kerr = 1;
   if (fork && cudaEventRecord(lane->join, lane->side) != cudaSuccess) kerr = 1;
   TRACE(KN_EMIT, launch_emit_b(one, dj, dpre(4), n, p_so[n], st));
-  TRACE(KN_XY, launch_lattice_b(dj, dpre(6), p_lt[n], dpre(7), p_lx[n], n, st));
+  if (!fork) TRACE(KN_XY, launch_lattice_b(dj, dpre(6), p_lt[n], dpre(7), p_lx[n], n, st));
   if (fork && cudaStreamWaitEvent(st, lane->join, 0) != cudaSuccess) kerr = 1;
   launch_status_b(dj, n, bp, st);
   if (opt.graph) {

@@ -21,7 +21,11 @@ namespace sbmt {
 // counters of one job, in its zeroed block (words): the PSLG vertex count
 // (u64 at 0), the status words at 8.. (see JC_*), then the per-bucket counts
 constexpr int JC_NSEG = 8, JC_ERR = 10, JC_NREC = 11, JC_NGCELL = 12, JC_NGTRI = 13, JC_NOVER = 14;
-constexpr int JC_BUCKETS = 16;
+// cut cells by their number of boundary pieces (1, 2, 3, 4, 5 or more), so
+// that the classification's warps run cells of one shape: counts at JC_KCNT
+constexpr int NCLS = 5, JC_KCNT = 16;
+constexpr int JC_BUCKETS = 24;
+SBMT_HD int piece_class(u32 npairs) { return npairs >= (u32)NCLS ? NCLS - 1 : (int)npairs - 1; }
 struct __align__(16) Job {
   GridP g;
   const unsigned char* img;
@@ -45,6 +49,7 @@ struct __align__(16) Job {
   u32* elist;
   u32 *poff, *eoff, *pcur, *ecur;
   CutRec* recs;
+  u32* klist;  // record indices by piece class: NCLS regions of NP entries
   u32 *bcut, *bbase, *extra_scan, *chain_scan, *cut_scan;
   TStage* stg;
   int* tri;
