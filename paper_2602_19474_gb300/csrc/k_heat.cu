@@ -142,29 +142,41 @@ struct Red {
 };
 
 // block sum of v into *out: each block writes its partial sum, and the last
-// block to finish adds the partials in block order (the same sum on every
-// run, whatever order the blocks ran in)
-__device__ __forceinline__ void block_add(double v, double* out, Red red) {
-  __shared__ double s[HB / 32];
-  __shared__ bool last;
+// block to finish adds the partials in a fixed order (thread t sums partials
+// t, t + HB, ..., then a fixed tree over the threads), so the sum is the same
+// on every run, whatever order the blocks ran in
+__device__ __forceinline__ double block_sum_fixed(double v, double* s) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
   __syncthreads();
+  double b = 0.0;
+  if (threadIdx.x < 32) {
+    b = threadIdx.x < blockDim.x / 32 ? s[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+  }
+  __syncthreads();
+  return b;  // valid in thread 0
+}
+
+__device__ __forceinline__ void block_add(double v, double* out, Red red) {
+  __shared__ double s[HB / 32];
+  __shared__ bool last;
+  const double b = block_sum_fixed(v, s);
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) b += s[w];
     red.part[blockIdx.x] = b;
     __threadfence();
     last = atomicAdd(red.done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
     __threadfence();
-    const volatile double* pv = red.part;
     double t = 0.0;
-    for (u32 k = 0; k < gridDim.x; ++k) t += pv[k];
-    *out = t;
-    *red.done = 0;
+    for (u32 k = threadIdx.x; k < gridDim.x; k += blockDim.x) t += __ldcg(red.part + k);
+    t = block_sum_fixed(t, s);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *red.done = 0;
+    }
   }
   __syncthreads();
 }
