@@ -184,7 +184,9 @@ int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params,
  *          beside e.  p becomes vertex n_lattice_vertices + (its rank by id
  *          among the applied points), and each triangle (u, w, x) beside
  *          e = u w becomes (u, p, x) and (p, w, x).
- * Steps 1 and 2 read the lattice positions; every distance test is a
+ * Steps 1 and 2 read the lattice positions and leave the vertices of the
+ * base mesh's outer boundary where they are (so that T covers the same
+ * domain as the base mesh); every distance test is a
  * double-precision comparison of squared distances.  The result is an
  * explicit mesh (mesh_query): the lattice vertices in id order (moved),
  * then the inserted points; the cells in id order, a split cell's two

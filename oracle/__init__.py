@@ -12,6 +12,10 @@ Functions whose parity is pinned by the paper (see the tests): ``alg1``
 intersection points), ``local_patch`` / ``template`` (App. G triangle lists).
 The Tier-G greedy rule (``greedy``) has no counterpart in the paper; it is
 pinned only by invariants and brute force ("parity unpinned" by the paper).
+``region3`` (Region III of Alg. 3's schedule: Alg. 2 on the preprocessed
+mesh) is pinned by reproducing the plain mesh on the unmoved base mesh, by
+the invariants of an embedding, and by hand-built degenerate cells against
+App. G and Fig. "lookup_table".
 """
 from __future__ import annotations
 
@@ -90,6 +94,10 @@ def _load():
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_brute.restype = ctypes.c_int64
         lib.oracle_brute.argtypes = [ctypes.c_int32] * 4 + [ctypes.c_int64] * 2
+        lib.oracle_region3.restype = ctypes.c_int
+        lib.oracle_region3.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Mesh)]
         lib.oracle_greedy.restype = ctypes.c_int
         lib.oracle_greedy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_int32]
@@ -244,6 +252,39 @@ def check_mesh(img: np.ndarray, h_num: int, h_den: int, mesh: dict) -> int:
     lab = np.ascontiguousarray(mesh["label"], dtype=np.uint16)
     return lib.oracle_check_mesh(img.ctypes.data, img.shape[1], img.shape[0], h_num, h_den, mesh["n_cells"],
                                  len(xy), xy.ctypes.data, len(tri), tri.ctypes.data, lab.ctypes.data)
+
+
+def region3(img: np.ndarray, xy: np.ndarray, tri: np.ndarray, plant: int = 0) -> dict:
+    """Region III of Alg. 3's schedule: Alg. 2 (the template retriangulation)
+    of the counter-clockwise triangle mesh (xy (V, 2) f64, tri (C, 3)) against
+    the image's boundary, each cell on its own.  Returns the embedded mesh as
+    mesh_bitmap does (xy, tri, label, code and counts; n_events, n_inside).
+    plant != 0 plants one of the oracle's test mistakes."""
+    lib = _load()
+    img = np.ascontiguousarray(img)
+    if img.ndim != 2 or img.dtype not in (np.uint8, np.uint16):
+        raise ValueError("img must be a 2-D uint8 or uint16 array")
+    H, W = img.shape
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    m = _Mesh()
+    rc = lib.oracle_region3(img.ctypes.data, W, H, img.strides[0], img.dtype.itemsize, xy.ctypes.data, len(xy),
+                            tri.ctypes.data, len(tri), plant, ctypes.byref(m))
+    if rc != 0:
+        raise OracleError("oracle_region3 failed (%d): %s" % (rc, lib.oracle_last_error().decode()))
+    try:
+        out = dict(
+            n_vertices=m.n_vertices, n_triangles=m.n_triangles, n_cells=m.n_cells, n_cut_cells=m.n_cut_cells,
+            n_tierG_cells=m.n_tierG_cells, n_vertices_grid=m.n_vertices_grid, n_events=m.n_events,
+            n_inside=m.n_vertices - m.n_vertices_grid - m.n_events,
+            xy=_copy(m.xy, 2 * m.n_vertices, np.float64).reshape(-1, 2),
+            tri=_copy(m.tri, 3 * m.n_triangles, np.int32).reshape(-1, 3),
+            label=_copy(m.label, m.n_triangles, np.uint16),
+            code=_copy(m.code, m.n_triangles, np.uint16),
+        )
+    finally:
+        lib.oracle_mesh_free(ctypes.byref(m))
+    return out
 
 
 def last_error() -> str:

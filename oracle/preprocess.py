@@ -28,7 +28,10 @@ Readings where the paper leaves a choice open:
   nearest point of any boundary pixel edge; ties to the smaller edge id) is
   closer than c moves along q -> v to distance c from q: for q inside a
   segment that is the segment's normal.
-- Steps 1 and 2 both read the positions of T0.
+- Steps 1 and 2 both read the positions of T0, and leave the vertices of
+  T0's outer boundary (the ends of edges with one cell beside them) where
+  they are, so that T covers the same domain as T0 (a vertex outside the
+  image snapping onto a border point would uncover part of the image).
 - Step 3: a candidate is a boundary point p and an edge e of T (after
   Steps 1-2) closer to p than b, neither end of e lying at p.  It is applied
   when p is the smallest candidate point of e, e the smallest candidate
@@ -115,9 +118,23 @@ def _nearest(vals, ids):
     return np.argmin(cand, axis=1)
 
 
-def region_one(xy0, img, A, C, chunk=2048):
+def outer_vertices(cells, V):
+    """The vertices on the outer boundary of the mesh: the ends of the edges
+    that only one cell has."""
+    e = np.concatenate([cells[:, [0, 1]], cells[:, [1, 2]], cells[:, [2, 0]]]).astype(np.int64)
+    key = np.minimum(e[:, 0], e[:, 1]) * V + np.maximum(e[:, 0], e[:, 1])
+    u, cnt = np.unique(key, return_counts=True)
+    one = u[cnt == 1]
+    out = np.zeros(V, bool)
+    out[one // V] = True
+    out[one % V] = True
+    return out
+
+
+def region_one(xy0, img, A, C, fixed=None, chunk=2048):
     """Steps 1 and 2 on the lattice positions xy0: new positions, status
-    (0 kept, 1 snapped, 2 repelled) and the corner id snapped to (-1)."""
+    (0 kept, 1 snapped, 2 repelled) and the corner id snapped to (-1); the
+    vertices marked in fixed stay."""
     pid, ppos = boundary_points(img)
     eid, eseg = boundary_edges(img)
     V = len(xy0)
@@ -134,6 +151,8 @@ def region_one(xy0, img, A, C, chunk=2048):
             k = _nearest(d2, pid)
             best = d2[np.arange(len(v)), k]
             hit = best < A * A
+            if fixed is not None:
+                hit &= ~fixed[s:s + chunk]
             out[s:s + chunk][hit] = ppos[k[hit]]
             status[s:s + chunk][hit] = 1
             snap[s:s + chunk][hit] = pid[k[hit]]
@@ -150,6 +169,8 @@ def region_one(xy0, img, A, C, chunk=2048):
             r = np.arange(len(v))
             best = d2[r, k]
             rep = (~hit) & (best < C * C)
+            if fixed is not None:
+                rep &= ~fixed[s:s + chunk]
             if rep.any():
                 d = np.sqrt(best[rep])
                 t = C / d
@@ -177,7 +198,7 @@ def preprocess(img, h_num, h_den, a, b, c, origin2x=0, origin2y=0):
     A, B, C = thresholds_px(a, b, c, h)
     xy0, cells = oracle.base_mesh(W, H, h_num, h_den, origin2x, origin2y)
     V = len(xy0)
-    xy, status, snap = region_one(xy0, img, A, C)
+    xy, status, snap = region_one(xy0, img, A, C, outer_vertices(cells, V))
     # Step 3: candidates over every (boundary point, edge of T)
     pid, ppos = boundary_points(img)
     e = np.concatenate([cells[:, [0, 1]], cells[:, [1, 2]], cells[:, [2, 0]]])

@@ -38,6 +38,12 @@
  *    split by the direction of the chord nearest the cut corner;
  *  - a triangle's label is the label of the pixel holding its centroid.
  *
+ * Region III of Alg. 3's schedule (oracle_region3, at the end of this file)
+ * retriangulates an arbitrary counter-clockwise mesh, the preprocessed one,
+ * cell by cell in double precision with the same two-tier rule; it handles
+ * Alg. 1's degenerate incidences (vertex on the segment, overlap, endpoint
+ * on the edge), which the moved vertices create.
+ *
  * parity pinned: Alg. 1 by the single-segment atoms of Fig. "lookup_table";
  * intersection points by the printed coordinates of App. F; templates by the
  * printed triangle lists of App. G at the printed coordinates; the mesh by
@@ -1239,6 +1245,558 @@ int64_t oracle_brute(int32_t W, int32_t H, int32_t h_num, int32_t h_den, int64_t
     ++done;
   }
   return done;
+}
+
+}  // extern "C"
+
+/* ========================================================================= */
+/* Region III of the pipelined schedule (Alg. 3 with the corollary on        */
+/* pipelined parallel scheduling): Alg. 2, the template retriangulation, on  */
+/* an arbitrary counter-clockwise triangle mesh T (the preprocessed mesh),   */
+/* each cell on its own from its local intersection class.                   */
+/*                                                                           */
+/* T's vertices are doubles (Steps 1-2 move them off the lattice), so every  */
+/* quantity here is a double computed by one fixed formula, each operation   */
+/* rounded once (the library is built without floating-point contraction).   */
+/* Degenerate incidences are exact: a pixel line is k - 1/2, and a vertex   */
+/* snapped to a pixel corner sits on it exactly.                             */
+/*                                                                           */
+/* Readings:                                                                 */
+/*  - an event of a mesh edge e is a point of the open edge where the        */
+/*    boundary meets it: a crossing of a boundary pixel edge, or a pixel     */
+/*    corner on e with a boundary pixel edge not collinear with e (a run of  */
+/*    boundary along e itself is embedded by e: Alg. 1's overlap); an end    */
+/*    of e on the boundary (a vertex on the segment) is not an event of e;   */
+/*  - an edge's events are computed from its lower-id end P to its other    */
+/*    end Q: on the horizontal pixel line y0 the crossing is                 */
+/*    x = P.x + ((y0 - P.y) (Q.x - P.x)) / (Q.y - P.y), on the vertical line  */
+/*    x0 likewise; the two cells beside the edge see the same points;        */
+/*  - the boundary vertices inside a cell are the PSLG vertices strictly     */
+/*    inside its chord on their horizontal pixel line;                       */
+/*  - the boundary pieces in a cell are the boundary runs of each pixel line */
+/*    strictly between the cell's lowest and highest corner (resp. leftmost  */
+/*    and rightmost), cut at the cell's nodes on that line;                  */
+/*  - a cell is cut when it has an event or an inside vertex; Tier-T when,   */
+/*    as on the lattice, no piece ends at a corner of the cell and every     */
+/*    event ends exactly one piece, with no inside vertex and one or two     */
+/*    chords, or one inside vertex every piece ends at; then the App. G      */
+/*    template of its key; every other cut cell takes the greedy rule with   */
+/*    double-precision predicates;                                           */
+/*  - Alg. 1's mask: an event sets its edge, a corner on a piece sets both   */
+/*    edges at that corner (vertex on the segment), an edge lying on a       */
+/*    boundary run sets its own bit (overlap), bit 0 an inside vertex; the   */
+/*    (m, n) class from the first two pieces' popcounts;                     */
+/*  - numbering: T's vertices, then the events by owning cell (the smaller   */
+/*    of the two cells beside the edge), local edge and position from the    */
+/*    lower-id end, then the inside vertices by cell and pixel-corner id;    */
+/*    triangles by cell, then the patch order; a triangle's label is that of */
+/*    the pixel holding ((x1 + x2) + x3) / 3.                                */
+/* ========================================================================= */
+namespace {
+
+/* planted mistakes for the tests (0 = none): 1 = a pixel corner on an edge
+ * is an event even when its only boundary edges run along the edge; 2 =
+ * boundary pieces oriented the wrong way; 3 = the inside test takes the
+ * closed chord */
+int g_r3_plant = 0;
+
+struct R3Ev {
+  double x, y, s;
+  int kind;  /* 0 on horizontal line k, 1 on vertical line m, 2 at pixel corner (m, k) */
+  i64 m, k;
+};
+
+struct R3Pt {
+  double x, y;
+};
+
+bool r3_hb(const Image& im, i64 m, i64 k) { return im.at(m, k - 1) != im.at(m, k); }
+bool r3_vb(const Image& im, i64 m, i64 k) { return im.at(m - 1, k) != im.at(m, k); }
+
+/* position t on a pixel line: the pixel edge j holding it (edge j spans
+ * [j - 1/2, j + 1/2]), or the corner c with t = c - 1/2 (returns true) */
+bool r3_at_corner(double t, i64* idx) {
+  const double fl = std::floor(t), fr = t - fl;
+  if (fr == 0.5) {
+    *idx = (i64)fl + 1;
+    return true;
+  }
+  *idx = fr < 0.5 ? (i64)fl : (i64)fl + 1;
+  return false;
+}
+
+double r3_hx(const R3Pt& P, const R3Pt& Q, double y0) { return P.x + ((y0 - P.y) * (Q.x - P.x)) / (Q.y - P.y); }
+double r3_vy(const R3Pt& P, const R3Pt& Q, double x0) { return P.y + ((x0 - P.x) * (Q.y - P.y)) / (Q.x - P.x); }
+
+/* the boundary pixel edges at corner (cx, cy) not collinear with an edge
+ * that is horizontal (hz) or vertical (vt) */
+bool r3_corner_event(const Image& im, i64 cx, i64 cy, bool hz, bool vt) {
+  int m = corner_mask(im, cx, cy);
+  if (g_r3_plant == 1) return m != 0;
+  if (hz) m &= ~(CE_E | CE_W);
+  if (vt) m &= ~(CE_N | CE_S);
+  return m != 0;
+}
+
+/* events of the edge from P (its lower-id end) to Q, in order from P */
+std::vector<R3Ev> r3_edge_events(const Image& im, const R3Pt& P, const R3Pt& Q) {
+  std::vector<R3Ev> ev;
+  const double dx = Q.x - P.x, dy = Q.y - P.y;
+  const bool hz = dy == 0.0, vt = dx == 0.0;
+  const double ylo = std::min(P.y, Q.y), yhi = std::max(P.y, Q.y);
+  const double xlo = std::min(P.x, Q.x), xhi = std::max(P.x, Q.x);
+  const i64 k0 = std::max<i64>(0, (i64)std::floor(ylo + 0.5)), k1 = std::min<i64>(im.H, (i64)std::ceil(yhi + 0.5));
+  for (i64 k = k0; k <= k1; ++k) {
+    const double y0 = (double)k - 0.5;
+    if (!(ylo < y0 && y0 < yhi)) continue;
+    const double x = r3_hx(P, Q, y0);
+    i64 j;
+    if (r3_at_corner(x, &j)) {
+      if (r3_corner_event(im, j, k, hz, vt)) ev.push_back({x, y0, 0.0, 2, j, k});
+    } else if (r3_hb(im, j, k)) {
+      ev.push_back({x, y0, 0.0, 0, j, k});
+    }
+  }
+  const i64 m0 = std::max<i64>(0, (i64)std::floor(xlo + 0.5)), m1 = std::min<i64>(im.W, (i64)std::ceil(xhi + 0.5));
+  for (i64 m = m0; m <= m1; ++m) {
+    const double x0 = (double)m - 0.5;
+    if (!(xlo < x0 && x0 < xhi)) continue;
+    const double y = r3_vy(P, Q, x0);
+    i64 j;
+    if (r3_at_corner(y, &j)) {
+      bool dup = false;
+      for (auto& e : ev)
+        if (e.kind == 2 && e.m == m && e.k == j) dup = true;
+      if (!dup && r3_corner_event(im, m, j, hz, vt)) ev.push_back({x0, y, 0.0, 2, m, j});
+    } else if (r3_vb(im, m, j)) {
+      ev.push_back({x0, y, 0.0, 1, m, j});
+    }
+  }
+  const bool alongx = std::fabs(dx) >= std::fabs(dy);
+  for (auto& e : ev) e.s = alongx ? (e.x - P.x) / dx : (e.y - P.y) / dy;
+  std::sort(ev.begin(), ev.end(), [](const R3Ev& a, const R3Ev& b) {
+    if (a.s != b.s) return a.s < b.s;
+    if (a.kind != b.kind) return a.kind < b.kind;
+    if (a.k != b.k) return a.k < b.k;
+    return a.m < b.m;
+  });
+  return ev;
+}
+
+double r3_orient(const R3Pt& p, const R3Pt& q, const R3Pt& r) {
+  return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
+}
+
+/* greedy rule of the Tier-G cells with double predicates; on_edge[v] is the
+ * set of cell edges v lies on (pairs on one cell edge are never
+ * candidates: they are the cell's own boundary) */
+std::vector<Tri> r3_greedy(const std::vector<R3Pt>& v, const std::vector<int>& on_edge,
+                           const std::vector<std::pair<int, int>>& constraints) {
+  const int n = (int)v.size();
+  std::vector<std::vector<uint8_t>> adj(n, std::vector<uint8_t>(n, 0));
+  std::vector<std::pair<int, int>> edges;
+  for (auto& e : constraints) {
+    const int a = std::min(e.first, e.second), b = std::max(e.first, e.second);
+    if (!adj[a][b]) adj[a][b] = adj[b][a] = 1, edges.push_back({a, b});
+  }
+  /* candidates in order of squared length rounded to single precision,
+   * ties by local index pair: lengths that are equal in exact arithmetic
+   * (symmetric configurations) but differ by a few units of the double's
+   * last place stay tied */
+  struct Cand {
+    float key;
+    double len2;
+    int u, w;
+  };
+  std::vector<Cand> cand;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b)
+      if (!adj[a][b] && (on_edge[a] & on_edge[b]) == 0) {
+        const double dx = v[b].x - v[a].x, dy = v[b].y - v[a].y;
+        const double l2 = dx * dx + dy * dy;
+        cand.push_back({(float)l2, l2, a, b});
+      }
+  std::sort(cand.begin(), cand.end(), [](const Cand& x, const Cand& y) {
+    if (x.key != y.key) return x.key < y.key;
+    if (x.u != y.u) return x.u < y.u;
+    return x.w < y.w;
+  });
+  auto sgn = [](double o) { return o > 0.0 ? 1 : (o < 0.0 ? -1 : 0); };
+  for (auto& c : cand) {
+    bool ok = true;
+    const double ex = v[c.w].x - v[c.u].x, ey = v[c.w].y - v[c.u].y;
+    for (int k = 0; k < n && ok; ++k) {
+      if (k == c.u || k == c.w || r3_orient(v[c.u], v[c.w], v[k]) != 0.0) continue;
+      const double t = (v[k].x - v[c.u].x) * ex + (v[k].y - v[c.u].y) * ey;
+      if (t > 0.0 && t < c.len2) ok = false;
+    }
+    for (size_t t = 0; t < edges.size() && ok; ++t) {
+      const int a = edges[t].first, b = edges[t].second;
+      if (a == c.u || a == c.w || b == c.u || b == c.w) continue;
+      const int o1 = sgn(r3_orient(v[c.u], v[c.w], v[a])), o2 = sgn(r3_orient(v[c.u], v[c.w], v[b]));
+      const int o3 = sgn(r3_orient(v[a], v[b], v[c.u])), o4 = sgn(r3_orient(v[a], v[b], v[c.w]));
+      if (o1 * o2 < 0 && o3 * o4 < 0) ok = false;
+    }
+    if (ok) adj[c.u][c.w] = adj[c.w][c.u] = 1, edges.push_back({c.u, c.w});
+  }
+  std::vector<Tri> tri;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      if (!adj[a][b]) continue;
+      for (int c = b + 1; c < n; ++c) {
+        if (!adj[a][c] || !adj[b][c]) continue;
+        const int o = sgn(r3_orient(v[a], v[b], v[c]));
+        if (o == 0) continue;
+        bool empty = true;
+        for (int k = 0; k < n && empty; ++k) {
+          if (k == a || k == b || k == c) continue;
+          if (sgn(r3_orient(v[a], v[b], v[k])) == o && sgn(r3_orient(v[b], v[c], v[k])) == o &&
+              sgn(r3_orient(v[c], v[a], v[k])) == o)
+            empty = false;
+        }
+        if (empty) tri.push_back(o > 0 ? Tri{a, b, c} : Tri{a, c, b});
+      }
+    }
+  std::sort(tri.begin(), tri.end());
+  return tri;
+}
+
+struct R3Mesh {
+  std::vector<double> xy;
+  std::vector<int32_t> tri;
+  std::vector<uint16_t> label, code;
+  i64 n_cut = 0, n_tierG = 0, n_events = 0, n_inside = 0;
+};
+
+/* the cell's two chord ends on a pixel line: horizontal (vert = false,
+ * coordinate c0 = the line's y) or vertical; each end is (position along the
+ * line, source) with source = corner 0..2 or 3 + edge */
+int r3_chord(const R3Pt* K, const int* id, bool vert, double c0, double* pos, int* src) {
+  int n = 0;
+  for (int c = 0; c < 3; ++c)
+    if ((vert ? K[c].x : K[c].y) == c0) {
+      if (n == 2) return 3;
+      pos[n] = vert ? K[c].y : K[c].x, src[n++] = c;
+    }
+  for (int j = 0; j < 3; ++j) {
+    const int a = j, b = (j + 1) % 3;
+    const R3Pt& P = id[a] < id[b] ? K[a] : K[b];
+    const R3Pt& Q = id[a] < id[b] ? K[b] : K[a];
+    const double pa = vert ? P.x : P.y, pb = vert ? Q.x : Q.y;
+    if (!((pa < c0 && c0 < pb) || (pb < c0 && c0 < pa))) continue;
+    if (n == 2) return 3;
+    pos[n] = vert ? r3_vy(P, Q, c0) : r3_hx(P, Q, c0), src[n++] = 3 + j;
+  }
+  if (n == 2 && pos[1] < pos[0]) std::swap(pos[0], pos[1]), std::swap(src[0], src[1]);
+  return n;
+}
+
+void r3_mesh(const Image& im, const std::vector<R3Pt>& X, const std::vector<int32_t>& T, R3Mesh& R) {
+  const i64 nv = (i64)X.size(), nt = (i64)T.size() / 3;
+  /* edge owners: the smaller cell beside each edge */
+  std::map<std::pair<i64, i64>, std::vector<std::pair<i64, int>>> uses;
+  for (i64 c = 0; c < nt; ++c)
+    for (int j = 0; j < 3; ++j) {
+      const i64 u = T[3 * c + j], w = T[3 * c + (j + 1) % 3];
+      if (u < 0 || w < 0 || u >= nv || w >= nv || u == w) throw std::runtime_error("bad triangle");
+      uses[{std::min(u, w), std::max(u, w)}].push_back({c, j});
+    }
+  for (auto& kv : uses)
+    if (kv.second.size() > 2) throw std::runtime_error("edge in more than two cells");
+  struct CellInfo {
+    std::vector<R3Ev> ev[3]; /* in CCW order along the cell's edge j */
+    std::vector<std::pair<i64, i64>> inside; /* (corner id, cx | cy << 32) sorted */
+    std::vector<i64> evid[3];
+  };
+  std::vector<CellInfo> info(nt);
+  /* events per cell edge, and global ids by owner, edge, position */
+  i64 next = nv;
+  std::vector<double> evxy;
+  for (i64 c = 0; c < nt; ++c) {
+    R3Pt K[3];
+    int id[3];
+    for (int q = 0; q < 3; ++q) id[q] = T[3 * c + q], K[q] = X[id[q]];
+    if (!(r3_orient(K[0], K[1], K[2]) > 0.0)) throw std::runtime_error("cell not counter-clockwise");
+    for (int j = 0; j < 3; ++j) {
+      const int a = j, b = (j + 1) % 3;
+      const bool fwd = id[a] < id[b];
+      auto ev = r3_edge_events(im, fwd ? K[a] : K[b], fwd ? K[b] : K[a]);
+      const auto& us = uses[{std::min(id[a], id[b]), std::max(id[a], id[b])}];
+      i64 owner = c;
+      for (auto& u : us) owner = std::min(owner, u.first);
+      std::vector<i64> ids(ev.size(), -1);
+      if (owner == c) {
+        for (size_t t = 0; t < ev.size(); ++t) ids[t] = next++, evxy.push_back(ev[t].x), evxy.push_back(ev[t].y);
+      }
+      if (!fwd) std::reverse(ev.begin(), ev.end()), std::reverse(ids.begin(), ids.end());
+      info[c].ev[j] = ev;
+      info[c].evid[j] = ids;
+    }
+  }
+  /* the non-owners take the owner's ids */
+  for (i64 c = 0; c < nt; ++c)
+    for (int j = 0; j < 3; ++j) {
+      if (info[c].ev[j].empty() || info[c].evid[j][0] >= 0) continue;
+      const i64 u = T[3 * c + j], w = T[3 * c + (j + 1) % 3];
+      for (auto& us : uses[{std::min(u, w), std::max(u, w)}]) {
+        if (us.first == c) continue;
+        auto ids = info[us.first].evid[us.second];
+        if (ids.size() != info[c].ev[j].size()) throw std::runtime_error("the cells beside an edge disagree");
+        std::reverse(ids.begin(), ids.end());
+        info[c].evid[j] = ids;
+      }
+    }
+  R.n_events = next - nv;
+  /* inside vertices */
+  for (i64 c = 0; c < nt; ++c) {
+    R3Pt K[3];
+    int id[3];
+    for (int q = 0; q < 3; ++q) id[q] = T[3 * c + q], K[q] = X[id[q]];
+    const double ylo = std::min({K[0].y, K[1].y, K[2].y}), yhi = std::max({K[0].y, K[1].y, K[2].y});
+    const double xlo = std::min({K[0].x, K[1].x, K[2].x}), xhi = std::max({K[0].x, K[1].x, K[2].x});
+    const i64 cy0 = std::max<i64>(0, (i64)std::floor(ylo + 0.5)), cy1 = std::min<i64>(im.H, (i64)std::ceil(yhi + 0.5));
+    const i64 cx0 = std::max<i64>(0, (i64)std::floor(xlo + 0.5)), cx1 = std::min<i64>(im.W, (i64)std::ceil(xhi + 0.5));
+    for (i64 cy = cy0; cy <= cy1; ++cy) {
+      const double y0 = (double)cy - 0.5;
+      if (!(ylo < y0 && y0 < yhi)) continue;
+      double pos[2];
+      int src[2];
+      if (r3_chord(K, id, false, y0, pos, src) != 2) throw std::runtime_error("chord");
+      for (i64 cx = cx0; cx <= cx1; ++cx) {
+        const double x0 = (double)cx - 0.5;
+        if (g_r3_plant == 3 ? !(pos[0] <= x0 && x0 <= pos[1]) : !(pos[0] < x0 && x0 < pos[1])) continue;
+        if (!is_vertex(corner_mask(im, cx, cy))) continue;
+        info[c].inside.push_back({cy * (im.W + 1) + cx, cx | (cy << 32)});
+      }
+    }
+    std::sort(info[c].inside.begin(), info[c].inside.end());
+  }
+  R.xy.reserve(2 * (nv + R.n_events));
+  for (auto& p : X) R.xy.push_back(p.x), R.xy.push_back(p.y);
+  R.xy.insert(R.xy.end(), evxy.begin(), evxy.end());
+  i64 nin = 0;
+  for (i64 c = 0; c < nt; ++c)
+    for (auto& q : info[c].inside) {
+      const i64 cx = q.second & 0xFFFFFFFF, cy = q.second >> 32;
+      R.xy.push_back((double)cx - 0.5), R.xy.push_back((double)cy - 0.5);
+      ++nin;
+    }
+  R.n_inside = nin;
+  /* the cells' patches */
+  i64 inbase = nv + R.n_events;
+  auto label_of = [&](const R3Pt& a, const R3Pt& b, const R3Pt& d) {
+    const double cx = ((a.x + b.x) + d.x) / 3.0, cy = ((a.y + b.y) + d.y) / 3.0;
+    return out_label(im.at((i64)std::floor(cx + 0.5), (i64)std::floor(cy + 0.5)));
+  };
+  for (i64 c = 0; c < nt; ++c) {
+    R3Pt K[3];
+    int id[3];
+    for (int q = 0; q < 3; ++q) id[q] = T[3 * c + q], K[q] = X[id[q]];
+    const CellInfo& ci = info[c];
+    const int nev[3] = {(int)ci.ev[0].size(), (int)ci.ev[1].size(), (int)ci.ev[2].size()};
+    const int ne = nev[0] + nev[1] + nev[2], ni = (int)ci.inside.size();
+    if (ne == 0 && ni == 0) {
+      for (int q = 0; q < 3; ++q) R.tri.push_back(id[q]);
+      R.label.push_back(label_of(K[0], K[1], K[2]));
+      R.code.push_back(0);
+      continue;
+    }
+    ++R.n_cut;
+    /* local nodes */
+    std::vector<R3Pt> v;
+    std::vector<i64> gid;
+    std::vector<int> on_edge;
+    for (int q = 0; q < 3; ++q) v.push_back(K[q]), gid.push_back(id[q]), on_edge.push_back((1 << q) | (1 << ((q + 2) % 3)));
+    for (int j = 0; j < 3; ++j)
+      for (size_t t = 0; t < ci.ev[j].size(); ++t)
+        v.push_back({ci.ev[j][t].x, ci.ev[j][t].y}), gid.push_back(ci.evid[j][t]), on_edge.push_back(1 << j);
+    for (size_t t = 0; t < ci.inside.size(); ++t) {
+      const i64 cx = ci.inside[t].second & 0xFFFFFFFF, cy = ci.inside[t].second >> 32;
+      v.push_back({(double)cx - 0.5, (double)cy - 0.5}), gid.push_back(inbase + (i64)t), on_edge.push_back(0);
+    }
+    inbase += ni;
+    auto ev_local = [&](int j, bool vert, i64 line) -> int {
+      int base = 3;
+      for (int t = 0; t < j; ++t) base += nev[t];
+      for (int t = 0; t < nev[j]; ++t) {
+        const R3Ev& e = ci.ev[j][t];
+        if (e.kind == 2 ? (vert ? e.m == line : e.k == line) : (e.kind == (vert ? 1 : 0) && (vert ? e.m : e.k) == line))
+          return base + t;
+      }
+      return -1;
+    };
+    /* pieces, oriented with the lower label on the left */
+    std::vector<std::pair<int, int>> pieces;
+    const double ylo = std::min({K[0].y, K[1].y, K[2].y}), yhi = std::max({K[0].y, K[1].y, K[2].y});
+    const double xlo = std::min({K[0].x, K[1].x, K[2].x}), xhi = std::max({K[0].x, K[1].x, K[2].x});
+    for (int vert = 0; vert < 2; ++vert) {
+      const double lo = vert ? xlo : ylo, hi = vert ? xhi : yhi;
+      const i64 L0 = std::max<i64>(0, (i64)std::floor(lo + 0.5));
+      const i64 L1 = std::min<i64>(vert ? im.W : im.H, (i64)std::ceil(hi + 0.5));
+      for (i64 line = L0; line <= L1; ++line) {
+        const double c0 = (double)line - 0.5;
+        if (!(lo < c0 && c0 < hi)) continue;
+        double pos[2];
+        int src[2];
+        if (r3_chord(K, id, vert, c0, pos, src) != 2) throw std::runtime_error("chord");
+        std::vector<std::pair<double, int>> nodes;
+        auto end_node = [&](int e) {
+          if (src[e] < 3) return src[e];
+          return ev_local(src[e] - 3, vert, line);
+        };
+        const int n0 = end_node(0), n1 = end_node(1);
+        if (n0 >= 0) nodes.push_back({pos[0], n0});
+        for (int t = 0; t < ni; ++t) {
+          const i64 cx = ci.inside[t].second & 0xFFFFFFFF, cy = ci.inside[t].second >> 32;
+          if ((vert ? cx : cy) == line) nodes.push_back({vert ? (double)cy - 0.5 : (double)cx - 0.5, 3 + ne + t});
+        }
+        if (n1 >= 0) nodes.push_back({pos[1], n1});
+        std::sort(nodes.begin() + (n0 >= 0 ? 1 : 0), nodes.end() - (n1 >= 0 ? 1 : 0));
+        for (size_t t = 0; t + 1 < nodes.size(); ++t) {
+          const double mid = (nodes[t].first + nodes[t + 1].first) * 0.5;
+          i64 j;
+          r3_at_corner(mid, &j); /* at a corner: the pixel edge starting there */
+          bool bnd;
+          int32_t l0, l1;
+          if (!vert) {
+            bnd = r3_hb(im, j, line), l0 = im.at(j, line - 1), l1 = im.at(j, line);
+            /* going +x the left side is above: lower label above runs +x */
+            if (bnd) pieces.push_back(l1 < l0 ? std::make_pair(nodes[t].second, nodes[t + 1].second)
+                                              : std::make_pair(nodes[t + 1].second, nodes[t].second));
+          } else {
+            bnd = r3_vb(im, line, j), l0 = im.at(line - 1, j), l1 = im.at(line, j);
+            /* going +y the left side is -x */
+            if (bnd) pieces.push_back(l0 < l1 ? std::make_pair(nodes[t].second, nodes[t + 1].second)
+                                              : std::make_pair(nodes[t + 1].second, nodes[t].second));
+          }
+        }
+      }
+    }
+    if (g_r3_plant == 2)
+      for (auto& p : pieces) std::swap(p.first, p.second);
+    /* Alg. 1 mask and the (m, n) class */
+    auto node_bits = [&](int w) {
+      if (w < 3) return (2 << w) | (2 << ((w + 2) % 3));
+      if (w < 3 + ne) {
+        int k = w - 3;
+        for (int j = 0; j < 3; ++j) {
+          if (k < nev[j]) return 2 << j;
+          k -= nev[j];
+        }
+      }
+      return 0;
+    };
+    int mask = ni > 0 ? 1 : 0;
+    std::vector<int> pc;
+    for (auto& p : pieces) {
+      const int b = node_bits(p.first) | node_bits(p.second);
+      mask |= b;
+      pc.push_back(__builtin_popcount(b));
+    }
+    for (int j = 0; j < 3; ++j) {
+      const R3Pt &a = K[j], &b = K[(j + 1) % 3];
+      for (int vert = 0; vert < 2; ++vert) {
+        const double ca = vert ? a.x : a.y, cb = vert ? b.x : b.y;
+        i64 line;
+        if (ca != cb || !r3_at_corner(ca, &line)) continue; /* not on a pixel line */
+        const double ta = vert ? a.y : a.x, tb = vert ? b.y : b.x;
+        const double t0 = std::min(ta, tb), t1 = std::max(ta, tb);
+        for (i64 q = (i64)std::floor(t0 + 0.5) - 1; q <= (i64)std::ceil(t1 + 0.5) + 1; ++q) {
+          if (!((double)q + 0.5 > t0 && (double)q - 0.5 < t1)) continue;
+          if (vert ? r3_vb(im, line, q) : r3_hb(im, q, line)) mask |= 2 << j;
+        }
+      }
+    }
+    int klass = 0;
+    if (pieces.size() == 1) klass = class_index(0, pc[0]);
+    else if (pieces.size() == 2) klass = class_index(pc[0], pc[1]);
+    /* Tier-T or Tier-G */
+    bool tierT = ni <= 1;
+    std::vector<int> deg(v.size(), 0);
+    for (auto& p : pieces) {
+      if (p.first < 3 || p.second < 3) tierT = false;
+      deg[p.first]++, deg[p.second]++;
+    }
+    for (int w = 3; w < 3 + ne; ++w)
+      if (deg[w] != 1) tierT = false;
+    if (ni == 0 && !(pieces.size() == 1 || pieces.size() == 2)) tierT = false;
+    if (ni == 1)
+      for (auto& p : pieces)
+        if (p.first != 3 + ne && p.second != 3 + ne) tierT = false;
+    LocalResult r;
+    if (tierT) {
+      r = classify_local(nev, ni, pieces);
+      if (r.tierG) throw std::runtime_error("Tier-T cell outside the table");
+    } else {
+      std::vector<std::pair<int, int>> cons = pieces;
+      std::vector<int> cyc;
+      for (int j = 0; j < 3; ++j) {
+        cyc.push_back(j);
+        int base = 3;
+        for (int t = 0; t < j; ++t) base += nev[t];
+        for (int t = 0; t < nev[j]; ++t) cyc.push_back(base + t);
+      }
+      for (size_t t = 0; t < cyc.size(); ++t) cons.push_back({cyc[t], cyc[(t + 1) % cyc.size()]});
+      r.tri = r3_greedy(v, on_edge, cons);
+      r.tierG = 1, r.key = 63, r.sigma = 0;
+      ++R.n_tierG;
+      if ((int)r.tri.size() != 2 * ni + (3 + ne) - 2) throw std::runtime_error("greedy triangle count");
+    }
+    r.mask = mask, r.klass = klass;
+    const uint16_t code = make_code(r);
+    for (auto& t : r.tri) {
+      for (int q = 0; q < 3; ++q) R.tri.push_back((int32_t)gid[t[q]]);
+      R.label.push_back(label_of(v[t[0]], v[t[1]], v[t[2]]));
+      R.code.push_back(code);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+/* Region III: Alg. 2 on the counter-clockwise triangle mesh T (nv vertices
+ * as 2 doubles, nt cells as 3 vertex ids) against the boundary of the image;
+ * the result in out (n_cells = nt, n_vertices_grid = nv, n_events; seg, ev
+ * and cut empty).  plant != 0 plants a mistake (tests only).  0, -1 bad
+ * arguments, -2 a consistency failure. */
+int oracle_region3(const void* data, int32_t width, int32_t height, int64_t pitch_bytes, int32_t dtype,
+                   const double* xy, int64_t nv, const int32_t* tri, int64_t nt, int32_t plant, oracle_mesh* out) {
+  g_err[0] = 0;
+  g_r3_plant = plant;
+  if (!data || !out || !xy || !tri || width < 1 || height < 1 || (dtype != 1 && dtype != 2) ||
+      pitch_bytes < (int64_t)width * dtype || nv < 3 || nt < 1) {
+    std::snprintf(g_err, sizeof g_err, "invalid arguments");
+    return -1;
+  }
+  try {
+    Image im{width, height, pitch_bytes, dtype, (const uint8_t*)data};
+    std::vector<R3Pt> X((size_t)nv);
+    for (i64 v = 0; v < nv; ++v) X[v] = {xy[2 * v], xy[2 * v + 1]};
+    std::vector<int32_t> T(tri, tri + 3 * nt);
+    R3Mesh R;
+    r3_mesh(im, X, T, R);
+    std::memset(out, 0, sizeof *out);
+    out->n_vertices = (int64_t)R.xy.size() / 2;
+    out->n_triangles = (int64_t)R.label.size();
+    out->n_cells = nt;
+    out->n_cut_cells = R.n_cut;
+    out->n_tierG_cells = R.n_tierG;
+    out->n_vertices_grid = nv;
+    out->xy = dup(R.xy);
+    out->tri = dup(R.tri);
+    out->label = dup(R.label);
+    out->code = dup(R.code);
+    out->n_events = R.n_events;
+    out->seg = dup(std::vector<int32_t>());
+    out->ev = dup(std::vector<int64_t>());
+    out->cut = dup(std::vector<int64_t>());
+    return 0;
+  } catch (const std::exception& ex) {
+    std::snprintf(g_err, sizeof g_err, "%s", ex.what());
+    return -2;
+  }
 }
 
 }  // extern "C"

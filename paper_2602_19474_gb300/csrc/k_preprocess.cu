@@ -318,13 +318,21 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
     }
     return uniform;
   };
+  // the vertices of the base mesh's outer boundary (one of the six cells
+  // around v(i, j) -- up cells 2i-2 and 2i and down cell 2i-1 of strip j,
+  // down cells 2i-1 and 2i+1 and up cell 2i of strip j-1 -- is not in the
+  // mesh) stay, so that the moved mesh covers the same domain
+  auto outer = [&](i64 i) {
+    return !(cell_in(g, 2 * i - 2, j) && cell_in(g, 2 * i - 1, j) && cell_in(g, 2 * i, j) &&
+             cell_in(g, 2 * i - 1, j - 1) && cell_in(g, 2 * i, j - 1) && cell_in(g, 2 * i + 1, j - 1));
+  };
   // the screen's loads before any store; whole warps in every iteration
   for (i64 k0 = 0; k0 < n; k0 += PV_U * blockDim.x) {
     bool slow[PV_U];
 #pragma unroll
     for (int u = 0; u < PV_U; ++u) {
       const i64 k = k0 + threadIdx.x + u * blockDim.x;
-      slow[u] = k < n && !uniform_at(2 * (lo + k) + j - a.m0);
+      slow[u] = k < n && !outer(lo + k) && !uniform_at(2 * (lo + k) + j - a.m0);
     }
 #pragma unroll
     for (int u = 0; u < PV_U; ++u) {

@@ -47,11 +47,18 @@ def test_constant_image_border_in_closed_form():
     H, W = 9, 13
     img = np.full((H, W), 3, np.uint8)
     A, B, C = P.thresholds_px(*TRIPLET, h=2.0)
-    xy0, _ = oracle.base_mesh(W, H, 2, 1)
+    xy0, cells = oracle.base_mesh(W, H, 2, 1)
     r = P.preprocess(img, 2, 1, *TRIPLET)
     corners = np.array([[-0.5, -0.5], [W - 0.5, -0.5], [-0.5, H - 0.5], [W - 0.5, H - 0.5]])
     lo, hi = np.array([-0.5, -0.5]), np.array([W - 0.5, H - 0.5])
+    # a lattice vertex has six cells around it; one with fewer is on the
+    # base mesh's outer boundary, and stays
+    outer = np.bincount(cells.ravel(), minlength=len(xy0)) < 6
+    assert outer.sum() > 0
     for k, v in enumerate(xy0):
+        if outer[k]:
+            assert r["status"][k] == 0 and np.array_equal(r["xy"][k], v)
+            continue
         dc = np.sqrt(((corners - v) ** 2).sum(1))
         if dc.min() < A:  # snaps to the nearest image corner
             assert r["status"][k] == 1 and np.array_equal(r["xy"][k], corners[np.argmin(dc)])
@@ -94,10 +101,13 @@ def test_steps_on_label_images(name, img, hn, hd):
     r = P.preprocess(img, hn, hd, *TRIPLET)
     V = len(xy0)
     pid, ppos = P.boundary_points(img)
+    # the base mesh's outer boundary (vertices with fewer than six cells) stays
+    outer = np.bincount(cells.ravel(), minlength=V) < 6
+    assert (r["status"][outer] == 0).all() and np.array_equal(r["xy"][:V][outer], xy0[outer])
     # Step 1: a snap is to the nearest boundary point, closer than a
     d, _ = cKDTree(ppos).query(xy0)
     snapped = r["status"] == 1
-    assert np.array_equal(snapped, d < A)
+    assert np.array_equal(snapped, (d < A) & ~outer)
     assert np.allclose(np.sqrt(((r["xy"][:V][snapped] - xy0[snapped]) ** 2).sum(1)), d[snapped], rtol=0, atol=1e-12)
     # Step 2: a repelled vertex was closer than c to the boundary and ends at
     # distance c from it (dense samples of the boundary pixel edges)
@@ -106,7 +116,7 @@ def test_steps_on_label_images(name, img, hn, hd):
     after, _ = tree.query(r["xy"][:V])
     rep = r["status"] == 2
     kept = r["status"] == 0
-    assert (before[rep] < C + 1e-3).all() and (before[kept] >= C - 1e-3).all()
+    assert (before[rep] < C + 1e-3).all() and (before[kept & ~outer] >= C - 1e-3).all()
     assert np.abs(after[rep] - C).max() <= 2e-3
     # Step 3: every elimination point is within b of its edge (after Steps 1-2),
     # and is the inserted vertex of its rank, at the pixel corner
@@ -130,10 +140,21 @@ def test_steps_on_label_images(name, img, hn, hd):
     area = (p3[:, 1, 0] - p3[:, 0, 0]) * (p3[:, 2, 1] - p3[:, 0, 1]) - (p3[:, 1, 1] - p3[:, 0, 1]) * (p3[:, 2, 0] - p3[:, 0, 0])
     assert (area > 0).all()
     # re-fanning two triangles around a point of their common quadrilateral
-    # keeps the area: T covers what the moved base mesh covers
+    # keeps the area: T covers what the moved base mesh covers.  An edge on
+    # the outer boundary has one triangle (u, w, x); its halves (u, p, x) and
+    # (p, w, x) cover it less the triangle (u, w, p) (signed areas:
+    # A(u,w,x) = A(u,p,x) + A(p,w,x) + A(u,w,p) for any p)
     q3 = r["xy"][:V][cells]
     area0 = (q3[:, 1, 0] - q3[:, 0, 0]) * (q3[:, 2, 1] - q3[:, 0, 1]) - (q3[:, 1, 1] - q3[:, 0, 1]) * (q3[:, 2, 0] - q3[:, 0, 0])
-    assert abs(area.sum() - area0.sum()) <= 1e-9 * area0.sum()
+    ccw = {(int(c_[k]), int(c_[(k + 1) % 3])) for c_ in cells for k in range(3)}
+    lost = 0.0
+    for k, (p, u, w) in enumerate(r["eliminations"]):
+        if edges[(min(u, w), max(u, w))] != 1:
+            continue
+        a_, b_ = (u, w) if (int(u), int(w)) in ccw else (w, u)
+        pa, pb, pc = r["xy"][a_], r["xy"][b_], r["xy"][V + k]
+        lost += (pb[0] - pa[0]) * (pc[1] - pa[1]) - (pb[1] - pa[1]) * (pc[0] - pa[0])
+    assert abs(area.sum() - (area0.sum() - lost)) <= 1e-9 * area0.sum()
 
 
 def test_planted_mistakes_fail_the_pins(monkeypatch):
