@@ -81,11 +81,11 @@ typedef struct {
  * degeneracy-free class is accepted: h_num even in 2..1024, h_den odd in
  * 1..63, origin2x and origin2y even.  Under it no grid vertex lies on a
  * pixel line and no pixel corner on a grid edge, so every Alg. 1 event is a
- * proper crossing; other parameters return SBMT_EINVAL.  mode must be
- * SBMT_PLAIN for mesh_bitmap and mesh_batch (SBMT_PREPROCESS returns
- * SBMT_EPROTO there: the template retriangulation of Alg. 3's Region III is
- * not built) and SBMT_PREPROCESS for mesh_preprocess, which reads the
- * thresholds a, b, c.  format selects the storage
+ * proper crossing; other parameters return SBMT_EINVAL.  mode is
+ * SBMT_PLAIN or SBMT_PREPROCESS for mesh_bitmap (Alg. 3 in full, explicit
+ * format only: see mesh_bitmap), SBMT_PLAIN for mesh_batch (SBMT_PREPROCESS
+ * returns SBMT_EPROTO there) and SBMT_PREPROCESS for mesh_preprocess, which
+ * reads the thresholds a, b, c.  format selects the storage
  * of the mesh (see sbmt_mesh_view): SBMT_EXPLICIT lists every triangle;
  * SBMT_COMPACT keeps the untouched base mesh implicit -- the paper's
  * "preserve the base mesh" (Sec. 1, Sec. 3.3) as a storage format. */
@@ -156,8 +156,49 @@ int mesh_create(sbmt_ctx** ctx, int device, size_t pool_bytes, void* cuda_stream
  * synchronises with the device once, after counting the image's boundary
  * segments and their grid crossings, to size its buffers.  The mesh is
  * complete when mesh_query returns SBMT_OK.  SBMT_ETIMEDOUT: a bounded
- * device wait ran out (see SBMT_DEBUG_STALL_SCAN). */
+ * device wait ran out (see SBMT_DEBUG_STALL_SCAN).
+ * With params->mode = SBMT_PREPROCESS (and the explicit format) the call
+ * runs Alg. 3 in full, in the pipelined schedule of Sec. 3.5's corollary:
+ * Regions I-II (mesh_preprocess), then Region III, Alg. 2 on the
+ * preprocessed mesh T (mesh_retriangulate); the returned mesh is the
+ * embedded one, and T is released.  That path synchronises three times. */
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out);
+
+/* Region III of Alg. 3's schedule: Alg. 2, the template retriangulation,
+ * applied to the explicit counter-clockwise mesh `base` (normally one made by
+ * mesh_preprocess; any mesh whose cells are counter-clockwise and whose edges
+ * have at most two cells) against the boundary of img, each cell on its own
+ * from its local intersection class (Sec. 3.5, corollary on lookup-driven
+ * parallel retriangulation).  base stays valid; out receives a new mesh:
+ *  xy    base's vertices in their ids, then the boundary events on base's
+ *        edges ordered by owning cell (the smaller of the two cells beside
+ *        the edge), its local edge and the position from the edge's lower-id
+ *        end, then the boundary vertices inside cells by cell and
+ *        pixel-corner id;
+ *  tri   by base cell, then the patch order;
+ *  label the pixel holding ((x1 + x2) + x3) / 3, 0xFFFF outside;
+ *  code  as for mesh_bitmap: Alg. 1's bitmask (an event sets its edge, a
+ *        base vertex on a boundary piece -- a vertex on the segment -- both
+ *        edges at it, an edge lying on a boundary run -- an overlap -- its
+ *        own bit, bit 0 a boundary vertex inside), the rotation, the key (1..15
+ *        table keys, 63 greedy), the (m, n) class; 0 for cells left as they
+ *        are.
+ * An event of a base edge is a point of the open edge where the boundary
+ * meets it: a crossing of a boundary pixel edge, or a pixel corner on the
+ * edge with a boundary pixel edge not collinear with it; on the horizontal
+ * pixel line y0 it is x = P.x + ((y0 - P.y) (Q.x - P.x)) / (Q.y - P.y) with
+ * P the edge's lower-id end (vertical lines likewise), every operation
+ * rounded once in double precision.  Cells in the table's regime (no piece
+ * ending at a corner of the cell, every event ending one piece, no inside
+ * vertex and one or two chords, or one inside vertex every piece ends at)
+ * take the App. G template of their key; the others the greedy rule (vertex
+ * pairs by squared length rounded to single precision, ties by local index
+ * pair, kept when the open segment holds no vertex and crosses no kept
+ * edge).  Per-cell limits: 16 events on an edge, 16 inside vertices, 48
+ * nodes (SBMT_ECAPACITY past them).  mesh_query reports n_cut_cells,
+ * n_tierG_cells and _triangles, n_events, n_inside_vertices and, as
+ * n_lattice_vertices, base's vertex count.  Synchronises once. */
+int mesh_retriangulate(sbmt_ctx* ctx, const sbmt_image* img, sbmt_mesh base, sbmt_mesh* out);
 
 /* Geometric preprocessing of the base mesh (Alg. 3, Steps 1-3): the mesh T
  * that Alg. 3's template retriangulation starts from.  params->mode must be
@@ -181,12 +222,14 @@ int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params,
  *          neither end of e at p, is a candidate (p, e).  It applies when e
  *          is p's smallest candidate edge (by smaller end id, then larger)
  *          and no smaller point is a candidate on an edge of the triangles
- *          beside e.  p becomes vertex n_lattice_vertices + (its rank by id
- *          among the applied points), and each triangle (u, w, x) beside
- *          e = u w becomes (u, p, x) and (p, w, x).
- * Steps 1 and 2 read the lattice positions and leave the vertices of the
- * base mesh's outer boundary where they are (so that T covers the same
- * domain as the base mesh); every distance test is a
+ *          beside e, and when the halves below all stay strictly
+ *          counter-clockwise.  p becomes vertex n_lattice_vertices + (its
+ *          rank by id among the applied points), and each triangle
+ *          (u, w, x) beside e = u w becomes (u, p, x) and (p, w, x).
+ * Steps 1 and 2 read the lattice positions; a vertex of the base mesh's
+ * outer boundary snaps only onto an image corner or a border point at least
+ * h + a from both ends of its side (so that T covers the image); every
+ * distance test is a
  * double-precision comparison of squared distances.  The result is an
  * explicit mesh (mesh_query): the lattice vertices in id order (moved),
  * then the inserted points; the cells in id order, a split cell's two

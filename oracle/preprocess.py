@@ -28,16 +28,23 @@ Readings where the paper leaves a choice open:
   nearest point of any boundary pixel edge; ties to the smaller edge id) is
   closer than c moves along q -> v to distance c from q: for q inside a
   segment that is the segment's normal.
-- Steps 1 and 2 both read the positions of T0, and leave the vertices of
-  T0's outer boundary (the ends of edges with one cell beside them) where
-  they are, so that T covers the same domain as T0 (a vertex outside the
-  image snapping onto a border point would uncover part of the image).
+- Steps 1 and 2 both read the positions of T0.  A vertex of T0's outer
+  boundary (an end of an edge with one cell beside it) snaps only onto an
+  image corner or onto a point of the image border at least h + a from both
+  ends of its side; Step 2 applies to it as to any vertex.  Otherwise the
+  outer boundary could cut into the image: a neighbour O of v lies within h
+  of v, and v within a of its target p, so only a target within h + a of an
+  image corner lets an outer-boundary edge (p, O) cross the image's corner
+  region (and a target off the border would pull the boundary inside).
 - Step 3: a candidate is a boundary point p and an edge e of T (after
   Steps 1-2) closer to p than b, neither end of e lying at p.  It is applied
   when p is the smallest candidate point of e, e the smallest candidate
   edge of p (edge id = smaller vertex id * V + larger), and p the smallest
   candidate point over the edges of both triangles beside e: so no triangle
-  loses two edges and no point is inserted twice.  An applied candidate
+  loses two edges and no point is inserted twice; and when the re-fan keeps
+  every half strictly counter-clockwise (p inside the quadrilateral: a point
+  on the line of two of a cell's moved vertices, both snapped onto one
+  pixel line, would leave a degenerate half).  An applied candidate
   inserts p as a vertex and splits each triangle (u, w, x) beside e = uw
   into (u, p, x) and (p, w, x).
 - output: the lattice vertices (moved) in their ids, then the inserted
@@ -131,11 +138,23 @@ def outer_vertices(cells, V):
     return out
 
 
-def region_one(xy0, img, A, C, fixed=None, chunk=2048):
+def border_safe(pid, W, H, reach):
+    """Per boundary point: an image corner, or a point of the image border
+    at least `reach` from both ends of its side (corner id y (W+1) + x)."""
+    cx, cy = pid % (W + 1), pid // (W + 1)
+    onx, ony = (cx == 0) | (cx == W), (cy == 0) | (cy == H)
+    corner = onx & ony
+    dside = np.where(onx, np.minimum(cy, H - cy), np.minimum(cx, W - cx)).astype(np.float64)
+    return corner | ((onx | ony) & (dside >= reach))
+
+
+def region_one(xy0, img, A, C, fixed=None, reach=0.0, chunk=2048):
     """Steps 1 and 2 on the lattice positions xy0: new positions, status
-    (0 kept, 1 snapped, 2 repelled) and the corner id snapped to (-1); the
-    vertices marked in fixed stay."""
+    (0 kept, 1 snapped, 2 repelled) and the corner id snapped to (-1); a
+    vertex marked in fixed snaps only onto a point border_safe(reach)."""
     pid, ppos = boundary_points(img)
+    H, W = img.shape
+    safe = border_safe(pid, W, H, reach)
     eid, eseg = boundary_edges(img)
     V = len(xy0)
     out = xy0.copy()
@@ -152,7 +171,7 @@ def region_one(xy0, img, A, C, fixed=None, chunk=2048):
             best = d2[np.arange(len(v)), k]
             hit = best < A * A
             if fixed is not None:
-                hit &= ~fixed[s:s + chunk]
+                hit &= ~fixed[s:s + chunk] | safe[k]
             out[s:s + chunk][hit] = ppos[k[hit]]
             status[s:s + chunk][hit] = 1
             snap[s:s + chunk][hit] = pid[k[hit]]
@@ -169,8 +188,6 @@ def region_one(xy0, img, A, C, fixed=None, chunk=2048):
             r = np.arange(len(v))
             best = d2[r, k]
             rep = (~hit) & (best < C * C)
-            if fixed is not None:
-                rep &= ~fixed[s:s + chunk]
             if rep.any():
                 d = np.sqrt(best[rep])
                 t = C / d
@@ -198,7 +215,7 @@ def preprocess(img, h_num, h_den, a, b, c, origin2x=0, origin2y=0):
     A, B, C = thresholds_px(a, b, c, h)
     xy0, cells = oracle.base_mesh(W, H, h_num, h_den, origin2x, origin2y)
     V = len(xy0)
-    xy, status, snap = region_one(xy0, img, A, C, outer_vertices(cells, V))
+    xy, status, snap = region_one(xy0, img, A, C, outer_vertices(cells, V), h + A)
     # Step 3: candidates over every (boundary point, edge of T)
     pid, ppos = boundary_points(img)
     e = np.concatenate([cells[:, [0, 1]], cells[:, [1, 2]], cells[:, [2, 0]]])
@@ -235,8 +252,26 @@ def preprocess(img, h_num, h_den, a, b, c, origin2x=0, origin2y=0):
     for pp, ee in zip(cand_p, cand_e):
         if emin[ee] == pp and pmin[pp] == ukey[ee] and all(cmin[cc] == pp for cc in edge_cells[ee]):
             applied.append((pp, ee))
-    applied.sort()
     pos_of = dict(zip(pid.tolist(), map(tuple, ppos)))
+
+    def orient(a_, b_, c_):
+        return (b_[0] - a_[0]) * (c_[1] - a_[1]) - (b_[1] - a_[1]) * (c_[0] - a_[0])
+
+    def refan_ok(pp, ee):
+        # both halves (u, p, x) and (p, w, x) of every cell beside e stay
+        # counter-clockwise: p inside the quadrilateral the re-fan covers
+        q = pos_of[pp]
+        for cc in edge_cells[ee]:
+            t = [int(x_) for x_ in cells[cc]]
+            for kk in range(3):
+                u_, w_, x_ = t[kk], t[(kk + 1) % 3], t[(kk + 2) % 3]
+                if {u_, w_} == {int(eu[ee]), int(ew[ee])}:
+                    if not (orient(xy[u_], q, xy[x_]) > 0.0 and orient(q, xy[w_], xy[x_]) > 0.0):
+                        return False
+        return True
+
+    applied = [(pp, ee) for pp, ee in applied if refan_ok(pp, ee)]
+    applied.sort()
     new_id = {pp: V + r for r, (pp, _) in enumerate(applied)}
     split = {}  # cell -> (local edge k, new vertex id)
     for pp, ee in applied:

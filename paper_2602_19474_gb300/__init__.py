@@ -39,7 +39,7 @@ SBMT_DEBUG_STALL_SCAN = 2
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_autotune", "mesh_tuning", "mesh_set_tuning",
            "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project",
-           "mesh_preprocess", "mesh_preprocess_info", "mesh_heat", "mesh_check", "mesh_footprint", "mesh_bound", "server_create",
+           "mesh_preprocess", "mesh_preprocess_info", "mesh_retriangulate", "mesh_heat", "mesh_check", "mesh_footprint", "mesh_bound", "server_create",
            "server_submit", "server_wait", "server_cancel", "server_release", "server_stats", "server_destroy",
            "sbmt_last_error", "sbmt_server_last_error")
 
@@ -153,6 +153,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.mesh_preprocess.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params),
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_preprocess_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_pre_info)]
+    lib.mesh_retriangulate.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_heat.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_heat_params), vp, vp, vp]
     lib.mesh_check.argtypes = [ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params)]
     lib.mesh_footprint.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_size_t)]
@@ -166,7 +167,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.server_release.argtypes = [vp, ctypes.c_uint64]
     lib.server_stats.argtypes = [vp, ctypes.POINTER(sbmt_server_stats)]
     lib.server_destroy.argtypes = [vp]
-    for f in ("mesh_check", "mesh_footprint", "mesh_bound", "server_create", "server_submit", "server_wait", "server_cancel",
+    for f in ("mesh_check", "mesh_footprint", "mesh_bound", "mesh_retriangulate", "server_create", "server_submit", "server_wait", "server_cancel",
               "server_release", "server_stats", "server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     lib.sbmt_server_last_error.restype = ctypes.c_char_p
@@ -241,6 +242,27 @@ def mesh_preprocess(ctx: int, img, h_num: int, h_den: int = 1, a: float = 0.26, 
     pr = sbmt_params(h_num, h_den, origin2x, origin2y, SBMT_PREPROCESS, float(a), float(b), float(c), SBMT_EXPLICIT, 0)
     out = ctypes.c_uint64()
     _check(load().mesh_preprocess(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def mesh_preprocessed(ctx: int, img, h_num: int, h_den: int = 1, a: float = 0.26, b: float = 0.125, c: float = 0.183,
+                      origin2x: int = 0, origin2y: int = 0) -> int:
+    """Alg. 3 in full through mesh_bitmap (mode SBMT_PREPROCESS): Regions
+    I-II, then Region III on the preprocessed mesh; the embedded mesh."""
+    im, keep = _image(img)
+    pr = sbmt_params(h_num, h_den, origin2x, origin2y, SBMT_PREPROCESS, float(a), float(b), float(c), SBMT_EXPLICIT, 0)
+    out = ctypes.c_uint64()
+    _check(load().mesh_bitmap(ctx, ctypes.byref(im), ctypes.byref(pr), ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def mesh_retriangulate(ctx: int, img, base: int) -> int:
+    """Region III: Alg. 2 on the explicit mesh `base` against img's boundary."""
+    im, keep = _image(img)
+    out = ctypes.c_uint64()
+    _check(load().mesh_retriangulate(ctx, ctypes.byref(im), base, ctypes.byref(out)))
     del keep
     return out.value
 

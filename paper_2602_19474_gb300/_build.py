@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsbmt.so")
-SOURCES = ["k_extract.cu", "k_traverse.cu", "k_cells.cu", "k_tierg.cu", "k_scan.cu", "k_static.cu", "k_quality.cu", "k_project.cu", "k_preprocess.cu", "k_heat.cu", "sbmt_api.cu", "sbmt_server.cu"]
+SOURCES = ["k_extract.cu", "k_traverse.cu", "k_cells.cu", "k_tierg.cu", "k_scan.cu", "k_static.cu", "k_quality.cu", "k_project.cu", "k_preprocess.cu", "k_heat.cu", "k_region3.cu", "sbmt_api.cu", "sbmt_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

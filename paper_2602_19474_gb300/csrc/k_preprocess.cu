@@ -318,21 +318,13 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
     }
     return uniform;
   };
-  // the vertices of the base mesh's outer boundary (one of the six cells
-  // around v(i, j) -- up cells 2i-2 and 2i and down cell 2i-1 of strip j,
-  // down cells 2i-1 and 2i+1 and up cell 2i of strip j-1 -- is not in the
-  // mesh) stay, so that the moved mesh covers the same domain
-  auto outer = [&](i64 i) {
-    return !(cell_in(g, 2 * i - 2, j) && cell_in(g, 2 * i - 1, j) && cell_in(g, 2 * i, j) &&
-             cell_in(g, 2 * i - 1, j - 1) && cell_in(g, 2 * i, j - 1) && cell_in(g, 2 * i + 1, j - 1));
-  };
   // the screen's loads before any store; whole warps in every iteration
   for (i64 k0 = 0; k0 < n; k0 += PV_U * blockDim.x) {
     bool slow[PV_U];
 #pragma unroll
     for (int u = 0; u < PV_U; ++u) {
       const i64 k = k0 + threadIdx.x + u * blockDim.x;
-      slow[u] = k < n && !outer(lo + k) && !uniform_at(2 * (lo + k) + j - a.m0);
+      slow[u] = k < n && !uniform_at(2 * (lo + k) + j - a.m0);
     }
 #pragma unroll
     for (int u = 0; u < PV_U; ++u) {
@@ -355,6 +347,27 @@ __global__ void __launch_bounds__(256) k_pre_vertex(PreArgs a) {
   }
   __syncthreads();
   if (threadIdx.x == 0) a.vqn[r] = nslow;
+}
+
+// a vertex of the base mesh's outer boundary: one of the six cells around
+// v(i, j) -- up cells 2i-2 and 2i and down cell 2i-1 of strip j, down cells
+// 2i-1 and 2i+1 and up cell 2i of strip j-1 -- is not in the mesh.  Such a
+// vertex snaps only onto an image corner or a border point at least h + a
+// from both ends of its side: a neighbour lies within h of it and it within
+// a of the point, so only a point nearer an image corner lets the moved
+// outer boundary cut across the image's corner (and a point off the border
+// would pull it inside).  It may be repelled.
+SBMT_DEV bool outer_vertex(const GridP& g, i64 i, i64 j) {
+  return !(cell_in(g, 2 * i - 2, j) && cell_in(g, 2 * i - 1, j) && cell_in(g, 2 * i, j) &&
+           cell_in(g, 2 * i - 1, j - 1) && cell_in(g, 2 * i, j - 1) && cell_in(g, 2 * i + 1, j - 1));
+}
+SBMT_DEV bool border_safe(const PreArgs& a, int bx, int by) {
+  const GridP& g = a.g;
+  const bool onx = bx == 0 || bx == g.W, ony = by == 0 || by == g.H;
+  if (onx && ony) return true;
+  if (!onx && !ony) return false;
+  const int side = onx ? min(by, g.H - by) : min(bx, g.W - bx);
+  return (double)side >= dadd(__ddiv_rn((double)g.p, (double)g.q), a.A);
 }
 
 // Region I, second pass: the queued vertices, one block per vertex row at a
@@ -384,7 +397,7 @@ __global__ void __launch_bounds__(128) k_pre_region1(PreArgs a) {
         const double x = a.tab[mi];
         const float xf = a.tabf[mi];
         int bx = -1, by = -1;
-        if (step1(a, x, y, xf, yf, bx, by)) {
+        if (step1(a, x, y, xf, yf, bx, by) && (!outer_vertex(g, lo + (v - base), j) || border_safe(a, bx, by))) {
           xy[v] = make_double2(half_minus(bx), half_minus(by));
           a.xyf[v] = make_float2((float)bx - 0.5f, (float)by - 0.5f);
           a.status[v] = 1;
@@ -556,6 +569,20 @@ __global__ void __launch_bounds__(128, 4) k_pre_step3(PreArgs a) {
                 if (ok && is_cand(a, cx, cy, c.cv[s][e], c.cv[s][e == 2 ? 0 : e + 1])) ok = false;
           }
         }
+      }
+    }
+    if (ok) {
+      // the re-fan keeps both halves (u, p, x) and (p, w, x) of every cell
+      // beside the edge strictly counter-clockwise
+      const double2* X = reinterpret_cast<const double2*>(a.xy);
+      const double2 P = make_double2((double)pcx - 0.5, (double)pcy - 0.5);
+      auto orient = [](double2 p0, double2 p1, double2 p2) {
+        return dsub(dmul(dsub(p1.x, p0.x), dsub(p2.y, p0.y)), dmul(dsub(p1.y, p0.y), dsub(p2.x, p0.x)));
+      };
+      for (int s = 0; s < c.n && ok; ++s) {
+        const int e = c.k[s];
+        const double2 U = X[c.cv[s][e]], Wv = X[c.cv[s][e == 2 ? 0 : e + 1]], Xv = X[c.cv[s][e == 0 ? 2 : e - 1]];
+        ok = orient(U, P, Xv) > 0.0 && orient(P, Wv, Xv) > 0.0;
       }
     }
     a.appl[t] = ok ? 1u : 0u;

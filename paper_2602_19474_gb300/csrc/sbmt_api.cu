@@ -159,6 +159,9 @@ struct MeshRec {
   // (h_info: err, eliminations, split cells, snapped, repelled, points with
   // a candidate)
   bool pre = false, settled = false;
+  // Region III meshes (Alg. 2 on a preprocessed mesh): h_info holds the
+  // error bits, cut cells, Tier-G cells and Tier-G triangles
+  bool r3 = false;
   unsigned char* pstatus = nullptr;
   int* psnap = nullptr;
   int* pelim = nullptr;
@@ -183,11 +186,13 @@ enum {
   KN_XY,
   KN_PRE,
   KN_HEAT,
+  KN_R3,
   KN_COUNT
 };
 const char* const kKernelNames[KN_COUNT] = {"k_corner_bits", "k_segments", "k_seg_count", "k_scan",
                                             "k_walk", "k_rank", "k_sort", "k_cutcells", "k_emit",
-                                            "k_tierg", "k_lattice_xy", "k_preprocess", "k_heat"};
+                                            "k_tierg", "k_lattice_xy", "k_preprocess", "k_heat",
+                                            "k_region3"};
 
 // The context's stream of work with its side streams, scratch arena, staging
 // buffers and tracing events.
@@ -599,7 +604,7 @@ int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false)
     if (pr->mode != SBMT_PREPROCESS || pr->format != SBMT_EXPLICIT)
       return fail(SBMT_EINVAL, "mesh_preprocess takes mode SBMT_PREPROCESS and the explicit format");
   } else {
-    if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is not available");
+    if (pr->mode == SBMT_PREPROCESS) return fail(SBMT_EPROTO, "SBMT_PREPROCESS is available through mesh_bitmap");
     if (pr->mode != SBMT_PLAIN || (pr->format != SBMT_EXPLICIT && pr->format != SBMT_COMPACT))
       return fail(SBMT_EINVAL, "mode/format");
   }
@@ -1316,6 +1321,151 @@ int settle(MeshRec* m) {
   return SBMT_OK;
 }
 
+// Region III: Alg. 2 on the counter-clockwise mesh (txy, ttri) against the
+// boundary of the device image; registers the result in *out.  One host
+// synchronisation (the output sizes), then the emission.
+int r3_one(sbmt_ctx* ctx, Lane* lane, const unsigned char* dimg, i64 pitch, int dtype, int W, int H,
+           const double* txy, const int* ttri, i64 nv, i64 nt, sbmt_mesh* out) {
+  if (nv < 3 || nt < 1 || nv >= (1ll << 31) || 3 * nt >= (1ll << 31))
+    return fail(SBMT_EINVAL, "mesh of %lld vertices and %lld cells", (long long)nv, (long long)nt);
+  cudaStream_t st = lane->stream;
+  MeshRec* m = new MeshRec();
+  m->W = W, m->H = H, m->r3 = true;
+  std::vector<void*> tmp;
+  arena_begin(lane);
+  auto bail = [&](int code) {
+    free_list(st, tmp);
+    arena_end(lane);
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    destroy_mesh(ctx, m, st);
+    return code;
+  };
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->h_info = pinned_slot(ctx);
+  }
+  if (!m->h_info) return bail(fail(SBMT_ENOMEM, "pinned info"));
+  int rc;
+  R3Args a{};
+  a.img = dimg, a.pitch = pitch, a.dtype = dtype, a.W = W, a.H = H;
+  a.txy = txy, a.ttri = ttri, a.nv = (u32)nv, a.nt = (u64)nt;
+  u32 *cnt, *scr;
+  const size_t scr_words = std::max(scan_scratch_words((u32)nv), scan_scratch_words((u32)nt)) + 1;
+  if ((rc = aalloc(lane, &a.deg, nv)) || (rc = aalloc(lane, &a.vptr, nv + 1)) || (rc = aalloc(lane, &a.inc, 3 * nt)) ||
+      (rc = aalloc(lane, &a.ntri, nt)) || (rc = aalloc(lane, &a.nown, nt)) || (rc = aalloc(lane, &a.nin, nt)) ||
+      (rc = aalloc(lane, &a.own3, nt)) || (rc = aalloc(lane, &a.toff, nt + 1)) || (rc = aalloc(lane, &a.eoff, nt + 1)) ||
+      (rc = aalloc(lane, &a.ioff, nt + 1)) || (rc = aalloc(lane, &a.glist, nt)) || (rc = aalloc(lane, &cnt, 8)) ||
+      (rc = aalloc(lane, &scr, scr_words)))
+    return bail(rc);
+  a.err = cnt, a.ncut = cnt + 1, a.ng = cnt + 2, a.ngtri = cnt + 3;
+  CK(cudaMemsetAsync(a.deg, 0, sizeof(u32) * (size_t)nv, st));
+  CK(cudaMemsetAsync(cnt, 0, 8 * sizeof(u32), st));
+  int nk = 0;
+  TRACE(KN_R3, nk = launch_r3_adjacency(a, scr, st));
+  TRACE(KN_R3, nk = launch_r3_count(a, st));
+  TRACE(KN_R3, nk = launch_scan(a.ntri, 1, a.toff, (u32)nt, scr, st));
+  TRACE(KN_R3, nk = launch_scan(a.nown, 1, a.eoff, (u32)nt, scr, st));
+  TRACE(KN_R3, nk = launch_scan(a.nin, 1, a.ioff, (u32)nt, scr, st));
+  (void)nk;
+  CK(cudaGetLastError());
+  u32* h = m->h_info;
+  CK(cudaMemcpyAsync(h + 4, a.toff + nt, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 5, a.eoff + nt, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 6, a.ioff + nt, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h, cnt, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h[0]) {
+    const u32 e = h[0];
+    return bail(fail((e & R3_CAPACITY) ? SBMT_ECAPACITY : SBMT_EINTERNAL,
+                     "retriangulation: %s (error bits 0x%x)",
+                     (e & R3_CAPACITY) ? "a cell over the per-cell limits (16 events per edge, 16 boundary "
+                                         "vertices, 48 nodes)"
+                                       : "an inconsistent mesh (a cell not counter-clockwise, an edge in three cells)",
+                     e));
+  }
+  const u64 NT = h[4], NE = h[5], NI = h[6], NV = (u64)nv + NE + NI;
+  if (NV >= (1ull << 31) || NT >= (1ull << 31)) return bail(fail(SBMT_EINVAL, "mesh too large"));
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_tri = up(16 * NV), off_lab = up(off_tri + 12 * NT), off_code = up(off_lab + 2 * NT);
+  const size_t total = off_code + 2 * NT + 256;
+  m->bytes = total;
+  if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
+    return bail(fail(SBMT_ENOMEM, "output allocation of %zu bytes", total));
+  char* ob = (char*)m->out_block;
+  m->xy = (double*)ob, m->tri = (int*)(ob + off_tri);
+  m->label = (unsigned short*)(ob + off_lab), m->code = (unsigned short*)(ob + off_code);
+  CK(cudaMemcpyAsync(m->xy, txy, 16 * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+  a.ne_total = (u32)NE;
+  a.xy = m->xy, a.tri = m->tri, a.label = m->label, a.code = m->code;
+  TRACE(KN_R3, nk = launch_r3_emit(a, st));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h, cnt, 4 * sizeof(u32), cudaMemcpyDeviceToHost, st));
+  free_list(st, tmp);
+  arena_end(lane);
+  m->nv = (int64_t)NV, m->nt = (int64_t)NT, m->ncells = nt, m->nvg = nv;
+  m->ne_total = (int64_t)NE, m->nc_total = (int64_t)NI;
+  {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    m->done = pool_event(ctx);
+    m->own_done = true;
+  }
+  if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
+  CK(cudaEventRecord(m->done, st));
+  std::lock_guard<std::mutex> lk(ctx->reg);
+  m->id = ctx->next++;
+  ctx->meshes[m->id] = m;
+  *out = m->id;
+  return SBMT_OK;
+}
+
+// the image on the device for a call that reads it twice: a device image as
+// it is, a host image uploaded into *owned (freed by the caller on st)
+int device_image(const sbmt_image* img, cudaStream_t st, sbmt_image* dev, void** owned) {
+  *dev = *img;
+  *owned = nullptr;
+  if (img->on_device) return SBMT_OK;
+  const size_t pitch = (size_t)img->width * img->dtype;
+  if (cudaMallocAsync(owned, pitch * img->height, st) != cudaSuccess) return fail(SBMT_ENOMEM, "image upload");
+  if (cudaMemcpy2DAsync(*owned, pitch, img->data, img->pitch_bytes, pitch, img->height, cudaMemcpyHostToDevice, st))
+    return fail(SBMT_ECUDA, "image upload");
+  dev->data = *owned, dev->pitch_bytes = (int64_t)pitch, dev->on_device = 1;
+  return SBMT_OK;
+}
+
+// Alg. 3 in full: Regions I-II (mesh_preprocess), the barrier, Region III
+int preprocess_mesh(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
+  int rc = check_params(img, pr, true);
+  if (rc) return rc;
+  Lane* lane = &ctx->main;
+  cudaStream_t st = lane->stream;
+  CK(cudaSetDevice(ctx->device));
+  sbmt_image dev;
+  void* owned = nullptr;
+  if ((rc = device_image(img, st, &dev, &owned))) {
+    if (owned) cudaFreeAsync(owned, st);
+    return rc;
+  }
+  sbmt_mesh tid = 0;
+  rc = pre_one(ctx, lane, &dev, pr, &tid);
+  MeshRec* tm = nullptr;
+  if (rc == SBMT_OK) {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    tm = ctx->meshes[tid];
+  }
+  if (rc == SBMT_OK && (rc = settle(tm)) == SBMT_OK && tm->h_info[0])
+    rc = fail(SBMT_EINTERNAL, "preprocessing reported error bits 0x%x", tm->h_info[0]);
+  if (rc == SBMT_OK)
+    rc = r3_one(ctx, lane, (const unsigned char*)dev.data, dev.pitch_bytes, dev.dtype, dev.width, dev.height, tm->xy,
+                tm->tri, tm->nv, tm->nt, out);
+  if (tm) {
+    std::lock_guard<std::mutex> lk(ctx->reg);
+    ctx->meshes.erase(tid);
+    destroy_mesh(ctx, tm, st);
+  }
+  if (owned) cudaFreeAsync(owned, st);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1354,6 +1504,7 @@ int mesh_create(sbmt_ctx** out, int device, size_t pool_bytes, void* cuda_stream
 int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params, sbmt_mesh* out) {
   if (!ctx || !out || !params) return fail(SBMT_EINVAL, "null ctx, params or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (params->mode == SBMT_PREPROCESS) return preprocess_mesh(ctx, img, params, out);
   RunOpts o = opts_of(tune_for(ctx, img, 1, params, 1));
   o.stall = (params->flags & SBMT_DEBUG_STALL_SCAN) != 0;
   return mesh_run(ctx, &ctx->main, img, 1, params, 1, out, o);
@@ -1363,6 +1514,37 @@ int mesh_preprocess(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* par
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
   return pre_one(ctx, &ctx->main, img, params, out);
+}
+
+int mesh_retriangulate(sbmt_ctx* ctx, const sbmt_image* img, sbmt_mesh base, sbmt_mesh* out) {
+  if (!ctx || !out || !img || !img->data) return fail(SBMT_EINVAL, "null ctx, image or out");
+  if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768 ||
+      (img->dtype != SBMT_U8 && img->dtype != SBMT_U16) || img->pitch_bytes < (int64_t)img->width * img->dtype)
+    return fail(SBMT_EINVAL, "image");
+  if (img->on_device && img->dtype == SBMT_U16 && ((img->pitch_bytes & 1) || ((uintptr_t)img->data & 1)))
+    return fail(SBMT_EINVAL, "a device u16 image needs an even pitch and an even address");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  MeshRec* tm;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    auto it = ctx->meshes.find(base);
+    if (it == ctx->meshes.end()) return fail(SBMT_ENOENT, "unknown mesh %llu", (unsigned long long)base);
+    tm = it->second;
+  }
+  if (tm->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "the base mesh must be explicit");
+  CK(cudaSetDevice(ctx->device));
+  Lane* lane = &ctx->main;
+  cudaStream_t st = lane->stream;
+  CK(cudaStreamWaitEvent(st, tm->done, 0));
+  if (int rc = settle(tm)) return rc;
+  sbmt_image dev;
+  void* owned = nullptr;
+  int rc = device_image(img, st, &dev, &owned);
+  if (rc == SBMT_OK)
+    rc = r3_one(ctx, lane, (const unsigned char*)dev.data, dev.pitch_bytes, dev.dtype, dev.width, dev.height, tm->xy,
+                tm->tri, tm->nv, tm->nt, out);
+  if (owned) cudaFreeAsync(owned, st);
+  return rc;
 }
 
 int mesh_preprocess_info(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_pre_info* out) {
@@ -1517,6 +1699,16 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
   if (rc) return rc;
   std::memset(out, 0, sizeof *out);
   out->n_vertices = m->nv, out->n_triangles = m->nt, out->n_cells = m->ncells;
+  if (m->r3) {
+    out->n_cut_cells = m->h_info[1], out->n_tierG_cells = m->h_info[2], out->n_tierG_triangles = m->h_info[3];
+    out->n_events = m->ne_total, out->n_inside_vertices = m->nc_total, out->n_lattice_vertices = m->nvg;
+    out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;
+    out->format = SBMT_EXPLICIT;
+    const u32 e = m->h_info[0];
+    out->status = e == 0 ? SBMT_OK : (e & R3_CAPACITY) ? SBMT_ECAPACITY : SBMT_EINTERNAL;
+    if (out->status) fail(out->status, "device reported error bits 0x%x", e);
+    return out->status;
+  }
   if (m->pre) {
     out->n_cut_cells = m->h_info[2], out->n_lattice_vertices = m->nvg;
     out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;

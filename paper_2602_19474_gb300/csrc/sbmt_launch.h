@@ -276,6 +276,36 @@ size_t pre_cand_bytes(u32 np);
 // -1 if a CUDA call failed.
 int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr, cudaStream_t st);
 
+// Region III (Alg. 2 on an arbitrary counter-clockwise mesh T, the
+// preprocessed one): the image, T (nv vertices as double pairs, nt cells as
+// vertex-id triples), the per-vertex cell lists (deg: nv counts, vptr:
+// nv + 1 offsets, inc: 3 nt cell ids), per cell the triangle count, the
+// events on the edges it owns (the smaller cell beside an edge), the inside
+// vertices and the owned events per local edge (8 bits each), their
+// exclusive scans (nt + 1 each), the output mesh, the Tier-G queue (nt
+// entries) and its length, and the error word.
+enum : u32 { R3_CAPACITY = 1u, R3_GEOMETRY = 2u, R3_COUNT = 4u };
+struct R3Args {
+  const unsigned char* img;
+  i64 pitch;
+  int dtype, W, H;
+  const double* txy;
+  const int* ttri;
+  u32 nv;
+  u64 nt;
+  u32 *deg, *vptr, *inc;
+  u32 *ntri, *nown, *nin, *own3;
+  u32 *toff, *eoff, *ioff;
+  u32 ne_total;
+  double* xy;
+  int* tri;
+  unsigned short *label, *code;
+  u32 *glist, *ng, *err, *ncut, *ngtri;
+};
+int launch_r3_adjacency(const R3Args& a, u32* scr, cudaStream_t st);
+int launch_r3_count(const R3Args& a, cudaStream_t st);
+int launch_r3_emit(const R3Args& a, cudaStream_t st);
+
 // heat diffusion on the triangles of label L (backward Euler, cotangent
 // stiffness, lumped mass, preconditioned conjugate gradients to relative
 // residual tol, at most maxit iterations per step): u (device, V doubles)

@@ -70,6 +70,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mesh_destroy(None) == sb.SBMT_EINVAL
     assert lib.mesh_preprocess(None, None, None, None) == sb.SBMT_EINVAL
     assert lib.mesh_preprocess_info(None, 1, None) == sb.SBMT_EINVAL
+    assert lib.mesh_retriangulate(None, None, 1, None) == sb.SBMT_EINVAL
     assert lib.mesh_heat(None, 1, None, None, None, None) == sb.SBMT_EINVAL
     assert lib.mesh_autotune(None, None, 0, None, 1, 1) == sb.SBMT_EINVAL
     assert lib.mesh_tuning(None, None, 0, None, 1, None) == sb.SBMT_EINVAL

@@ -106,9 +106,9 @@ def test_thresholds_outside_the_admissible_range_are_rejected():
         with pytest.raises(sb.SbmtError) as e:
             sb.mesh_preprocess(ctx(), img, 2, 1, a, b, c)
         assert e.value.code == sb.SBMT_EINVAL
-    with pytest.raises(sb.SbmtError) as e:  # the full pipeline's Region III is not built
+    with pytest.raises(sb.SbmtError) as e:  # mesh_bitmap's full Alg. 3 checks them too
         sb.mesh_bitmap(ctx(), img, 2, 1, mode=sb.SBMT_PREPROCESS)
-    assert e.value.code == sb.SBMT_EPROTO
+    assert e.value.code == sb.SBMT_EINVAL
 
 
 def test_angle_and_area_bounds_on_the_preprocessed_mesh():

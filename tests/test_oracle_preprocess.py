@@ -51,14 +51,9 @@ def test_constant_image_border_in_closed_form():
     r = P.preprocess(img, 2, 1, *TRIPLET)
     corners = np.array([[-0.5, -0.5], [W - 0.5, -0.5], [-0.5, H - 0.5], [W - 0.5, H - 0.5]])
     lo, hi = np.array([-0.5, -0.5]), np.array([W - 0.5, H - 0.5])
-    # a lattice vertex has six cells around it; one with fewer is on the
-    # base mesh's outer boundary, and stays
-    outer = np.bincount(cells.ravel(), minlength=len(xy0)) < 6
-    assert outer.sum() > 0
+    # the only boundary points are the image corners, onto which the base
+    # mesh's outer boundary snaps too
     for k, v in enumerate(xy0):
-        if outer[k]:
-            assert r["status"][k] == 0 and np.array_equal(r["xy"][k], v)
-            continue
         dc = np.sqrt(((corners - v) ** 2).sum(1))
         if dc.min() < A:  # snaps to the nearest image corner
             assert r["status"][k] == 1 and np.array_equal(r["xy"][k], corners[np.argmin(dc)])
@@ -78,6 +73,35 @@ def test_constant_image_border_in_closed_form():
             assert np.allclose(r["xy"][k], q + C * (v - q) / d, rtol=0, atol=1e-12)
         else:
             assert r["status"][k] == 0 and np.array_equal(r["xy"][k], v)
+
+
+# a label boundary meeting the right border 1 px below the image corner:
+# vertices outside the image lie within a of that border point, too near the
+# corner to snap onto it
+BORDER_BAND = np.zeros((10, 33), np.uint8)
+BORDER_BAND[9:, :] = 1
+
+
+def test_outer_boundary_snaps_only_far_from_image_corners():
+    """Step 1 on BORDER_BAND: two vertices outside the image lie within a of
+    the border point 1 px below the image corner and do not snap; every other
+    vertex within a of a boundary point snaps onto the nearest."""
+    from scipy.spatial import cKDTree
+
+    img, h = BORDER_BAND, 2.0
+    H, W = img.shape
+    A, B, C = P.thresholds_px(*TRIPLET, h=h)
+    xy0, cells = oracle.base_mesh(W, H, 2, 1)
+    r = P.preprocess(img, 2, 1, *TRIPLET)
+    outer = np.bincount(cells.ravel(), minlength=len(xy0)) < 6
+    pid, ppos = P.boundary_points(img)
+    d, near = cKDTree(ppos).query(xy0)
+    pcx, pcy = ppos[near, 0] + 0.5, ppos[near, 1] + 0.5
+    onx, ony = (pcx == 0) | (pcx == W), (pcy == 0) | (pcy == H)
+    side = np.where(onx, np.minimum(pcy, H - pcy), np.minimum(pcx, W - pcx))
+    safe = (onx & ony) | ((onx | ony) & (side >= h + A))
+    assert ((d < A) & outer & ~safe).sum() == 2
+    assert np.array_equal(r["status"] == 1, (d < A) & (~outer | safe))
 
 
 def _sampled_boundary(img, step=1e-3):
@@ -101,13 +125,19 @@ def test_steps_on_label_images(name, img, hn, hd):
     r = P.preprocess(img, hn, hd, *TRIPLET)
     V = len(xy0)
     pid, ppos = P.boundary_points(img)
-    # the base mesh's outer boundary (vertices with fewer than six cells) stays
+    # Step 1: a snap is to the nearest boundary point, closer than a; a
+    # vertex of the base mesh's outer boundary (fewer than six cells around
+    # it) snaps only onto an image corner or a border point at least h + a
+    # from the ends of its side
     outer = np.bincount(cells.ravel(), minlength=V) < 6
-    assert (r["status"][outer] == 0).all() and np.array_equal(r["xy"][:V][outer], xy0[outer])
-    # Step 1: a snap is to the nearest boundary point, closer than a
-    d, _ = cKDTree(ppos).query(xy0)
+    d, near = cKDTree(ppos).query(xy0)
+    H, W = img.shape
+    pcx, pcy = ppos[near, 0] + 0.5, ppos[near, 1] + 0.5
+    onx, ony = (pcx == 0) | (pcx == W), (pcy == 0) | (pcy == H)
+    side = np.where(onx, np.minimum(pcy, H - pcy), np.minimum(pcx, W - pcx))
+    safe = (onx & ony) | ((onx | ony) & (side >= h + A))
     snapped = r["status"] == 1
-    assert np.array_equal(snapped, (d < A) & ~outer)
+    assert np.array_equal(snapped, (d < A) & (~outer | safe))
     assert np.allclose(np.sqrt(((r["xy"][:V][snapped] - xy0[snapped]) ** 2).sum(1)), d[snapped], rtol=0, atol=1e-12)
     # Step 2: a repelled vertex was closer than c to the boundary and ends at
     # distance c from it (dense samples of the boundary pixel edges)
@@ -116,7 +146,7 @@ def test_steps_on_label_images(name, img, hn, hd):
     after, _ = tree.query(r["xy"][:V])
     rep = r["status"] == 2
     kept = r["status"] == 0
-    assert (before[rep] < C + 1e-3).all() and (before[kept & ~outer] >= C - 1e-3).all()
+    assert (before[rep] < C + 1e-3).all() and (before[kept] >= C - 1e-3).all()
     assert np.abs(after[rep] - C).max() <= 2e-3
     # Step 3: every elimination point is within b of its edge (after Steps 1-2),
     # and is the inserted vertex of its rank, at the pixel corner
@@ -174,8 +204,8 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     # repelled vertices moved the wrong way: the closed-form border positions fail
     real = P.region_one
 
-    def wrong_way(xy0_, img_, A, C, chunk=2048):
-        out, status, snap = real(xy0_, img_, A, C, chunk)
+    def wrong_way(xy0_, img_, A, C, *rest, **kw):
+        out, status, snap = real(xy0_, img_, A, C, *rest, **kw)
         rep = status == 2
         out[rep] = 2 * xy0_[rep] - out[rep]
         return out, status, snap
@@ -183,3 +213,9 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     monkeypatch.setattr(P, "region_one", wrong_way)
     with pytest.raises(AssertionError):
         test_constant_image_border_in_closed_form()
+    monkeypatch.setattr(P, "region_one", real)
+    # the outer boundary snapping anywhere (no border rule): the Step 1 pin
+    # on a Voronoi image fails
+    monkeypatch.setattr(P, "border_safe", lambda pid, W, H, reach: np.ones(len(pid), bool))
+    with pytest.raises(AssertionError):
+        test_outer_boundary_snaps_only_far_from_image_corners()

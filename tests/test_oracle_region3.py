@@ -24,6 +24,9 @@ from oracle import preprocess as P
 from paper_2602_19474_gb300 import synth
 
 TRIPLET = (0.26, 0.125, 0.183)
+# a label boundary meeting the right border 1 px below the image corner
+BORDER_BAND = np.zeros((10, 33), np.uint8)
+BORDER_BAND[9:, :] = 1
 _ELL = synth.ellipses(256, 20, 2, 5.0, 40.0)
 
 
@@ -115,6 +118,7 @@ def test_every_3x3_bitmap_on_the_base_mesh():
     ("noise_h4", synth.noise_bitmap(synth.rng_for(31), 36, 30, 1.5), 4, 1),
     ("noise_third", synth.noise_bitmap(synth.rng_for(32), 28, 24, 1.5), 2, 3),
     ("pixels_h2", (np.random.default_rng(5).random((20, 26)) < 0.5).astype(np.uint8), 2, 1),
+    ("border_band", BORDER_BAND, 2, 1),
 ])
 def test_preprocessed_mesh_invariants(name, img, hn, hd):
     img = np.ascontiguousarray(img)
@@ -122,6 +126,9 @@ def test_preprocessed_mesh_invariants(name, img, hn, hd):
     R = oracle.region3(img, T["xy"], T["tri"])
     assert R["n_vertices_grid"] == len(T["xy"]) and R["n_cells"] == len(T["tri"])
     check_embedded(img, T, R)
+    # every event lies on an edge between two cells, and a cut cell has
+    # 2 n_i + n_b - 2 triangles
+    assert len(R["tri"]) == len(T["tri"]) + 2 * R["n_inside"] + 2 * R["n_events"]
     # the degenerate incidences occur: snapped vertices sit on the boundary
     assert (T["status"] == 1).sum() > 0
 
@@ -198,3 +205,26 @@ def test_planted_mistakes_fail_the_pins():
     T = P.preprocess(im, 2, 1, *TRIPLET)
     with pytest.raises((AssertionError, oracle.OracleError)):
         check_embedded(im, T, oracle.region3(im, T["xy"], T["tri"], plant=3))
+
+
+def _corner_noise():
+    # a 33 x 10 noise bitmap whose boundary meets the right border 1 px below
+    # the top-right corner
+    rng = np.random.default_rng(3)
+    W, H = rng.integers(8, 40, 2)
+    rng.integers(0, 3, (H // 3 + 1, W // 3 + 1))
+    return (rng.random((H, W)) < 0.5).astype(np.uint8)
+
+
+def test_the_preprocessed_mesh_must_cover_the_image(monkeypatch):
+    """With the outer boundary snapping onto any border point, a vertex
+    outside the image moves onto the right border 1 px below the corner and
+    the corner is left uncovered: the per-label area pin fails."""
+    img = _corner_noise()
+    assert img.shape == (10, 33)
+    T = P.preprocess(img, 2, 1, *TRIPLET)
+    check_embedded(img, T, oracle.region3(img, T["xy"], T["tri"]))
+    monkeypatch.setattr(P, "border_safe", lambda pid, W, H, reach: np.ones(len(pid), bool))
+    T = P.preprocess(img, 2, 1, *TRIPLET)
+    with pytest.raises(AssertionError):
+        check_embedded(img, T, oracle.region3(img, T["xy"], T["tri"]))
