@@ -530,6 +530,79 @@ def our_arm(args, rank: int, world: int, dist):
                   "repelled": pinfo.n_repelled, "eliminated": pinfo.n_eliminated,
                   "algorithmic_bytes_per_call": qbytes, "achieved_gbs": qbytes / (ms_q * 1e-3) / 1e9,
                   "quality_vs_bounds": pre_bounds}
+    # Alg. 3 in full (mesh_bitmap with SBMT_PREPROCESS): Regions I-II, the
+    # barrier, Region III (Alg. 2 on the preprocessed mesh); and Region III
+    # alone (mesh_retriangulate on a preprocessed mesh)
+    def step_full():
+        m = sb.mesh_preprocessed(ctx, dimg, hn, hd, *tri_abc)
+        vv = sb.mesh_query(ctx, m, -1)
+        sb.mesh_release(ctx, m)
+        return vv
+
+    for _ in range(3):
+        vf = step_full()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        vf = step_full()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1) / args.steps
+    mt = sb.mesh_preprocess(ctx, dimg, hn, hd, *tri_abc)
+    vt = sb.mesh_query(ctx, mt, -1)
+
+    def step_r3():
+        m = sb.mesh_retriangulate(ctx, dimg, mt)
+        vv = sb.mesh_query(ctx, m, -1)
+        sb.mesh_release(ctx, m)
+        return vv
+
+    for _ in range(3):
+        step_r3()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        vr = step_r3()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_r3 = e0.elapsed_time(e1) / args.steps
+    # the embedded mesh's Tier-T sub-triangles against the two theorems'
+    # bounds (at h = 2 px the boundary's 1-px runs are shorter than the edge,
+    # outside the length constraint the theorems assume: reported, not held)
+    mr = sb.mesh_retriangulate(ctx, dimg, mt)
+    vr = sb.mesh_query(ctx, mr, -1)
+    tr_ = sb.view_tensors(vr)
+    key = (tr_["code"].view(torch.int16).to(torch.int32) & 0xFFFF) >> 6 & 63
+    tt = (key >= 1) & (key <= 15)
+    p3 = tr_["xy"][tr_["tri"][tt].long()]
+    ea = (p3[:, 1] - p3[:, 2]).norm(dim=1)
+    eb = (p3[:, 2] - p3[:, 0]).norm(dim=1)
+    ec = (p3[:, 0] - p3[:, 1]).norm(dim=1)
+    area = 0.5 * ((p3[:, 1, 0] - p3[:, 0, 0]) * (p3[:, 2, 1] - p3[:, 0, 1])
+                  - (p3[:, 1, 1] - p3[:, 0, 1]) * (p3[:, 2, 0] - p3[:, 0, 0]))
+    # smallest angle: opposite the shortest edge, sin = 2 area / (product of the other two)
+    emin = torch.minimum(torch.minimum(ea, eb), ec)
+    emax = torch.maximum(torch.maximum(ea, eb), ec)
+    emid = ea + eb + ec - emin - emax
+    min_ang = torch.rad2deg(torch.asin(torch.clamp(2 * area / (emid * emax), max=1.0)))
+    full_bounds = {"tierT_triangles": int(tt.sum()), "min_angle_deg": float(min_ang.min()),
+                   "angle_bound_deg": math.degrees(theta), "min_area": float(area.min()), "area_bound": 0.5 * bp * cp,
+                   "note": "h = 2 px is outside the length constraint the theorems assume; at the paper's edge "
+                           "(h = 2/3 px) the bounds hold on Tier-T cells (tests/test_gpu_region3.py)"}
+    del tr_, p3, ea, eb, ec, area, emin, emax, emid, min_ang, key, tt
+    sb.mesh_release(ctx, mr)
+    sb.mesh_release(ctx, mt)
+    rbytes = (img.nbytes + 16.0 * vt.n_vertices + 12.0 * vt.n_triangles + 16.0 * vr.n_vertices
+              + 16.0 * vr.n_triangles)
+    preprocess["alg3_full"] = {
+        "what": "Alg. 3 in full through mesh_bitmap with SBMT_PREPROCESS: Regions I-II, then Region III (Alg. 2 on "
+                "the preprocessed mesh, cell by cell)",
+        "ms_per_call": ms_f, "triangles_per_s": vf.n_triangles / (ms_f * 1e-3), "triangles": vf.n_triangles,
+        "cut_cells": vf.n_cut_cells, "tierG_cells": vf.n_tierG_cells, "events": vf.n_events,
+        "inside_vertices": vf.n_inside_vertices,
+        "region3_ms_per_call": ms_r3, "region3_algorithmic_bytes": rbytes,
+        "region3_achieved_gbs": rbytes / (ms_r3 * 1e-3) / 1e9,
+        "tierT_quality_vs_bounds": full_bounds}
     # heat diffusion (App. H) on the step's mesh: the region of the most
     # frequent label, a Gaussian pulse at the image centre, alpha = 500 px^2/s,
     # backward Euler with dt = 0.01 s, conjugate gradients to 1e-10
@@ -627,6 +700,8 @@ def our_arm(args, rank: int, world: int, dist):
         "projection": dict(projection, peak=peak, frac=projection["achieved_gbs"] / peak),
         "heat": dict(heat, peak=peak, frac=heat["achieved_gbs"] / peak),
         "preprocess": dict(preprocess, peak=peak, frac=preprocess["achieved_gbs"] / peak,
+                           alg3_full=dict(preprocess["alg3_full"],
+                                          region3_frac=preprocess["alg3_full"]["region3_achieved_gbs"] / peak),
                            cpu_baseline=pre_cpu),
         "gpu_launches": launches,
         "clocks": clocks,

@@ -34,11 +34,14 @@
 //    rounded to single precision (ties by local index pair), kept when the
 //    open segment holds no vertex and crosses no kept edge.
 //
-// Kernels: k_r3_deg / k_r3_fill (cells around each vertex), k_r3_count (per
-// cell: triangles, events on the edges it owns -- the smaller of the two
-// cells beside an edge -- and inside vertices), three scans, k_r3_emit (uncut
-// and Tier-T cells; Tier-G cells queued), k_r3_tierg (one warp per Tier-G
-// cell).
+// Kernels: k_r3_deg / k_r3_fill (cells around each vertex); k_r3_screen
+// (every cell: a cell whose pixel box carries one label is uncut and takes
+// that label, with no double-precision work; the others are listed);
+// k_r3_count (the listed cells: triangles, events on the edges each owns --
+// the smaller of the two cells beside an edge -- and inside vertices); three
+// scans; k_r3_emit_uncut; k_r3_emit (the listed cells: Tier-T patches, the
+// greedy rule for Tier-G cells of at most 12 nodes, larger ones queued);
+// k_r3_tierg (one warp per queued cell).
 #include "sbmt_cell.cuh"
 #include "sbmt_keys.cuh"
 #include "sbmt_launch.h"
@@ -210,16 +213,18 @@ SBMT_DEV R3Cell r3_load(const R3Args& a, u32 c) {
   return C;
 }
 
-// one label over the pixels touching the cell's bounding box (widened by one
-// pixel for rounding): no boundary pixel edge meets the cell
-SBMT_DEV bool r3_uniform(const R3Args& a, const R3Cell& C) {
-  const i64 x0 = (i64)floor(dsb(C.xlo, 0.5)), x1 = (i64)ceil(dad(C.xhi, 0.5));
-  const i64 y0 = (i64)floor(dsb(C.ylo, 0.5)), y1 = (i64)ceil(dad(C.yhi, 0.5));
+// one label over the pixels touching the cell's bounding box (the box grown
+// by 1e-6 px for the rounding of its ends): no boundary pixel edge meets the
+// cell, and every pixel the cell covers has that label (returned, OUTSIDE
+// as 0xFFFF), or -1
+SBMT_DEV int r3_uniform(const R3Args& a, const R3Cell& C) {
+  const i64 x0 = (i64)ceil(dsb(dsb(C.xlo, 0.5), 1e-6)), x1 = (i64)floor(dad(dad(C.xhi, 0.5), 1e-6));
+  const i64 y0 = (i64)ceil(dsb(dsb(C.ylo, 0.5), 1e-6)), y1 = (i64)floor(dad(dad(C.yhi, 0.5), 1e-6));
   const int l0 = r3_px(a, x0, y0);
   for (i64 y = y0; y <= y1; ++y)
     for (i64 x = x0; x <= x1; ++x)
-      if (r3_px(a, x, y) != l0) return false;
-  return true;
+      if (r3_px(a, x, y) != l0) return -1;
+  return l0 == R3_OUTSIDE ? 0xFFFF : l0;
 }
 
 // the boundary vertices strictly inside the cell, as corner ids y (W+1) + x
@@ -298,43 +303,69 @@ __global__ void __launch_bounds__(256) k_r3_fill(R3Args a) {
 }
 
 // ---------------------------------------------------------------------------
-// per cell: triangles, events on owned edges, inside vertices
+// screen: every cell; a cell whose pixel box carries one label is uncut (its
+// label is the box's); the others go to the candidate list
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_r3_screen(R3Args a) {
+  const int lane = threadIdx.x & 31;
+  for (u64 c0 = (u64)blockIdx.x * blockDim.x; c0 < a.nt; c0 += (u64)gridDim.x * blockDim.x) {
+    const u64 c = c0 + threadIdx.x;
+    bool cand = false;
+    if (c < a.nt) {
+      const R3Cell C = r3_load(a, (u32)c);
+      int l = -1;
+      if (!(r3_orient(C.K[0], C.K[1], C.K[2]) > 0.0)) atomicOr(a.err, R3_GEOMETRY);
+      else l = r3_uniform(a, C);
+      cand = l < 0;
+      a.ntri[c] = 1, a.nown[c] = 0, a.nin[c] = 0, a.own3[c] = 0;
+      a.ulab[c] = (unsigned short)(cand ? 0 : l);
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, cand);
+    // a warp's 32 cells fill one word of the candidate bit-plane
+    const u64 w0 = c0 + (threadIdx.x & ~31u);
+    if (lane == 0 && w0 < a.nt) a.cmark[w0 >> 5] = m;
+    if (m) {
+      u32 base = 0;
+      if (lane == 0) base = atomicAdd(a.ncand, (u32)__popc(m));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (cand) a.cand[base + __popc(m & ((1u << lane) - 1u))] = (u32)c;
+    }
+  }
+}
+
+// the candidates: events on the edges, inside vertices, the cells beside
+// the edges that carry events
 __global__ void __launch_bounds__(128) k_r3_count(R3Args a) {
   R3Ev ev[R3_MAXE];
-  for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < a.nt; c += (u64)gridDim.x * blockDim.x) {
-    const R3Cell C = r3_load(a, (u32)c);
-    u32 ntri = 1, nown = 0, nin = 0, own3 = 0;
-    if (!(r3_orient(C.K[0], C.K[1], C.K[2]) > 0.0)) {
-      atomicOr(a.err, R3_GEOMETRY);
-    } else if (!r3_uniform(a, C)) {
-      int ne = 0, cnt[3];
-      bool bad = false;
-      for (int j = 0; j < 3; ++j) {
-        const int u = j, w = j == 2 ? 0 : j + 1;
-        const bool fwd = C.id[u] < C.id[w];
-        cnt[j] = r3_edge_events(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], ev);
-        if (cnt[j] < 0) bad = true;
-        else ne += cnt[j];
-      }
-      const int ni = bad ? 0 : r3_inside(a, C, nullptr);
-      if (bad || ni == -1 || 3 + ne + ni > R3_MAXN) {
-        atomicOr(a.err, R3_CAPACITY);
-      } else if (ni < 0) {
-        atomicOr(a.err, R3_GEOMETRY);
-      } else if (ne + ni > 0) {
-        atomicAdd(a.ncut, 1u);
-        ntri = (u32)(2 * ni + 3 + ne - 2);
-        nin = (u32)ni;
-        for (int j = 0; j < 3; ++j) {
-          if (cnt[j] == 0) continue;
-          const int nb = r3_neighbour(a, (u32)c, C, j);
-          if (nb == -2) atomicOr(a.err, R3_GEOMETRY);
-          if (nb < 0 || (u64)nb > c) nown += (u32)cnt[j], own3 |= (u32)cnt[j] << (8 * j);
-        }
-      }
+  const u32 n = *a.ncand;
+  for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const u32 c = a.cand[q];
+    const R3Cell C = r3_load(a, c);
+    int ne = 0, cnt[3];
+    bool bad = false;
+    for (int j = 0; j < 3; ++j) {
+      const int u = j, w = j == 2 ? 0 : j + 1;
+      const bool fwd = C.id[u] < C.id[w];
+      cnt[j] = r3_edge_events(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], ev);
+      if (cnt[j] < 0) bad = true;
+      else ne += cnt[j];
     }
-    a.ntri[c] = ntri, a.nown[c] = nown, a.nin[c] = nin, a.own3[c] = own3;
+    const int ni = bad ? 0 : r3_inside(a, C, nullptr);
+    if (bad || ni == -1 || 3 + ne + ni > R3_MAXN) {
+      atomicOr(a.err, R3_CAPACITY);
+    } else if (ni < 0) {
+      atomicOr(a.err, R3_GEOMETRY);
+    } else if (ne + ni > 0) {
+      atomicAdd(a.ncut, 1u);
+      u32 nown = 0, own3 = 0;
+      for (int j = 0; j < 3; ++j) {
+        if (cnt[j] == 0) continue;
+        const int nb = r3_neighbour(a, c, C, j);
+        if (nb == -2) atomicOr(a.err, R3_GEOMETRY);
+        if (nb < 0 || (u32)nb > c) nown += (u32)cnt[j], own3 |= (u32)cnt[j] << (8 * j);
+      }
+      a.ntri[c] = (u32)(2 * ni + 3 + ne - 2), a.nin[c] = (u32)ni, a.nown[c] = nown, a.own3[c] = own3;
+    }
   }
 }
 
@@ -588,7 +619,146 @@ SBMT_DEV int r3_tier_t(const R3Local& L, int* sigma_out) {
 }
 
 // ---------------------------------------------------------------------------
-// uncut and Tier-T cells; Tier-G cells queued for the warp kernel
+// the greedy rule for a small cell (n <= R3_SMALL nodes) in one thread:
+// candidate pairs by (squared length rounded to single precision, u, w),
+// each kept when its open segment holds no node and it crosses no kept edge;
+// the faces (3-cycles with no node inside, smallest index first,
+// counter-clockwise) in sorted order.  Returns the face count, -1 past the
+// limits.
+// ---------------------------------------------------------------------------
+constexpr int R3_SMALL = 12;
+
+// Orientation signs with a single-precision filter.  The nodes' coordinates
+// relative to the first corner, rounded once to float, are within
+// 2^-24 M (1 + 2^-23) of the exact differences (M: the largest of them);
+// a float orientation of three such points is then within 48 2^-24 M^2 of
+// the exact orientation of the doubles, and the double-precision formula
+// within 32 2^-53 M^2 of it.  Outside 80 2^-24 M^2 the float sign is the
+// sign the double formula gives; inside it the double formula decides.
+struct R3Filt {
+  float2 l[R3_SMALL];
+  float T;
+};
+SBMT_DEV void r3_filt_init(const R3Local& L, R3Filt& F) {
+  float M = 0.0f;
+  for (int k = 0; k < L.n; ++k) {
+    F.l[k] = make_float2(__double2float_rn(dsb(L.v[k].x, L.v[0].x)), __double2float_rn(dsb(L.v[k].y, L.v[0].y)));
+    M = fmaxf(M, fmaxf(fabsf(F.l[k].x), fabsf(F.l[k].y)));
+  }
+  F.T = 80.0f * 5.9604645e-8f * M * M * 1.0001f;  // 80 2^-24 M^2, rounded up
+}
+SBMT_DEV int r3_osgn(const R3Local& L, const R3Filt& F, int p, int q, int r) {
+  const float2 a = F.l[p], b = F.l[q], c = F.l[r];
+  const float o = __fsub_rn(__fmul_rn(__fsub_rn(b.x, a.x), __fsub_rn(c.y, a.y)),
+                            __fmul_rn(__fsub_rn(b.y, a.y), __fsub_rn(c.x, a.x)));
+  if (o > F.T) return 1;
+  if (o < -F.T) return -1;
+  return r3_sgn(r3_orient(L.v[p], L.v[q], L.v[r]));
+}
+
+SBMT_DEV int r3_greedy_small(const R3Local& L, int* face) {
+  const int n = L.n;
+  R3Filt F;
+  r3_filt_init(L, F);
+  unsigned short adj[R3_SMALL];
+  unsigned char ea[3 * R3_SMALL], eb[3 * R3_SMALL];
+  int ne = 0;
+  for (int w = 0; w < n; ++w) adj[w] = 0;
+  auto add = [&](int p, int q) {
+    if ((adj[p] >> q) & 1) return;
+    adj[p] |= (unsigned short)(1 << q), adj[q] |= (unsigned short)(1 << p);
+    if (ne < 3 * R3_SMALL) ea[ne] = (unsigned char)p, eb[ne] = (unsigned char)q;
+    ++ne;
+  };
+  for (int t = 0; t < L.np; ++t) add(L.pa[t], L.pb[t]);
+  {
+    int prev = 0, b = 3;
+    for (int j = 0; j < 3; ++j) {
+      if (j) add(prev, j), prev = j;
+      for (int t = 0; t < L.nev[j]; ++t) add(prev, b + t), prev = b + t;
+      b += L.nev[j];
+    }
+    add(prev, 0);
+  }
+  // candidates, insertion-sorted by (key, u, w)
+  float key[R3_SMALL * (R3_SMALL - 1) / 2];
+  unsigned char pr[R3_SMALL * (R3_SMALL - 1) / 2];
+  int nc = 0;
+  for (int u = 0; u < n; ++u)
+    for (int w = u + 1; w < n; ++w) {
+      if (((adj[u] >> w) & 1) || (L.on_edge[u] & L.on_edge[w])) continue;
+      const double dx = dsb(L.v[w].x, L.v[u].x), dy = dsb(L.v[w].y, L.v[u].y);
+      const float k = __double2float_rn(dad(dml(dx, dx), dml(dy, dy)));
+      const unsigned char code = (unsigned char)(u << 4 | w);
+      int t = nc++;
+      while (t > 0 && (key[t - 1] > k || (key[t - 1] == k && pr[t - 1] > code))) key[t] = key[t - 1], pr[t] = pr[t - 1], --t;
+      key[t] = k, pr[t] = code;
+    }
+  for (int r = 0; r < nc; ++r) {
+    const int u = pr[r] >> 4, w = pr[r] & 15;
+    const double2 pu = L.v[u], pw = L.v[w];
+    const double ex = dsb(pw.x, pu.x), ey = dsb(pw.y, pu.y), len2 = dad(dml(ex, ex), dml(ey, ey));
+    bool bad = false;
+    for (int k = 0; k < n && !bad; ++k) {
+      if (k == u || k == w || r3_osgn(L, F, u, w, k) != 0) continue;
+      const double t = dad(dml(dsb(L.v[k].x, pu.x), ex), dml(dsb(L.v[k].y, pu.y), ey));
+      if (t > 0.0 && t < len2) bad = true;
+    }
+    for (int t = 0; t < ne && t < 3 * R3_SMALL && !bad; ++t) {
+      const int p = ea[t], q = eb[t];
+      if (p == u || p == w || q == u || q == w) continue;
+      const int o1 = r3_osgn(L, F, u, w, p), o2 = r3_osgn(L, F, u, w, q);
+      if (o1 * o2 >= 0) continue;
+      const int o3 = r3_osgn(L, F, p, q, u), o4 = r3_osgn(L, F, p, q, w);
+      if (o3 * o4 < 0) bad = true;
+    }
+    if (!bad) add(u, w);
+  }
+  if (ne > 3 * R3_SMALL) return -1;
+  int nf = 0;
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) {
+      if (!((adj[p] >> q) & 1)) continue;
+      for (int r = q + 1; r < n; ++r) {
+        if (!((adj[p] >> r) & 1) || !((adj[q] >> r) & 1)) continue;
+        const int o = r3_osgn(L, F, p, q, r);
+        if (o == 0) continue;
+        bool empty = true;
+        for (int k = 0; k < n && empty; ++k) {
+          if (k == p || k == q || k == r) continue;
+          if (r3_osgn(L, F, p, q, k) == o && r3_osgn(L, F, q, r, k) == o && r3_osgn(L, F, r, p, k) == o)
+            empty = false;
+        }
+        if (!empty) continue;
+        if (nf == 2 * R3_SMALL) return -1;
+        const int f = o > 0 ? (p << 12 | q << 6 | r) : (p << 12 | r << 6 | q);
+        int t = nf++;
+        while (t > 0 && face[t - 1] > f) face[t] = face[t - 1], --t;
+        face[t] = f;
+      }
+    }
+  return nf;
+}
+
+// ---------------------------------------------------------------------------
+// uncut cells of one label: the cell as it is, labelled by its pixel box
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_r3_emit_uncut(R3Args a) {
+  for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < a.nt; c += (u64)gridDim.x * blockDim.x) {
+    const u32 t0 = a.toff[c];
+    if (a.toff[c + 1] - t0 != 1) continue;
+    const int* t = a.ttri + 3 * c;
+    if ((a.cmark[c >> 5] >> (c & 31)) & 1u) continue;  // a candidate: k_r3_emit's
+    reinterpret_cast<int3*>(a.tri)[t0] = make_int3(t[0], t[1], t[2]);
+    a.label[t0] = a.ulab[c];
+    a.code[t0] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the candidates: cells touched only at a corner stay; Tier-T cells take
+// their template; small Tier-G cells the greedy rule here, larger ones are
+// queued for the warp kernel
 // ---------------------------------------------------------------------------
 struct R3EvBuf {
   R3Ev e[3][R3_MAXE];
@@ -598,28 +768,25 @@ struct R3EvBuf {
 __global__ void __launch_bounds__(128) k_r3_emit(R3Args a) {
   R3EvBuf ev;
   R3Local L;
-  for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < a.nt; c += (u64)gridDim.x * blockDim.x) {
-    const R3Cell C = r3_load(a, (u32)c);
+  const u32 n = *a.ncand;
+  for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const u32 c = a.cand[q];
+    const R3Cell C = r3_load(a, c);
     const u32 t0 = a.toff[c];
     int3* tri = reinterpret_cast<int3*>(a.tri);
-    if (a.ntri[c] == 1 && a.nin[c] == 0 && a.toff[c + 1] - t0 == 1 && r3_uniform(a, C)) {
+    if (a.toff[c + 1] - t0 == 1) {  // touches only: the cell stays
       tri[t0] = make_int3(C.id[0], C.id[1], C.id[2]);
       a.label[t0] = r3_label(a, C.K[0], C.K[1], C.K[2]);
       a.code[t0] = 0;
       continue;
     }
-    const u32 e = r3_build(a, (u32)c, C, L, ev, true);
+    const u32 e = r3_build(a, c, C, L, ev, true);
     if (e) {
       atomicOr(a.err, e);
       continue;
     }
-    if (L.ne + L.ni == 0) {  // touches only: the cell stays
-      tri[t0] = make_int3(C.id[0], C.id[1], C.id[2]);
-      a.label[t0] = r3_label(a, C.K[0], C.K[1], C.K[2]);
-      a.code[t0] = 0;
-      continue;
-    }
-    if ((u32)(2 * L.ni + 3 + L.ne - 2) != a.toff[c + 1] - t0) {
+    const int nt = 2 * L.ni + 3 + L.ne - 2;
+    if ((u32)nt != a.toff[c + 1] - t0) {
       atomicOr(a.err, R3_COUNT);
       continue;
     }
@@ -630,21 +797,38 @@ __global__ void __launch_bounds__(128) k_r3_emit(R3Args a) {
       continue;
     }
     if (key == 0) {
-      a.glist[atomicAdd(a.ng, 1u)] = (u32)c;
+      if (L.n > R3_SMALL) {
+        a.glist[atomicAdd(a.ng, 1u)] = c;
+        continue;
+      }
+      int face[2 * R3_SMALL];
+      const int nf = r3_greedy_small(L, face);
+      if (nf != nt) {
+        atomicOr(a.err, nf < 0 ? R3_CAPACITY : R3_COUNT);
+        continue;
+      }
+      const unsigned short code = (unsigned short)((L.mask & 15) | (63 << 6) | (L.klass << 12));
+      atomicAdd(a.ngtri, (u32)nf);
+      atomicAdd(a.ngsmall, 1u);
+      for (int i = 0; i < nf; ++i) {
+        const int f = face[i], p = f >> 12, r2 = (f >> 6) & 63, s2 = f & 63;
+        tri[t0 + i] = make_int3((int)L.gid[p], (int)L.gid[r2], (int)L.gid[s2]);
+        a.label[t0 + i] = r3_label(a, L.v[p], L.v[r2], L.v[s2]);
+        a.code[t0 + i] = code;
+      }
       continue;
     }
     const unsigned long long w = g_keys.tris[(key - 1) * 3 + sigma];
-    const int nt = 2 * L.ni + 3 + L.ne - 2;
     const unsigned short code =
         (unsigned short)((L.mask & 15) | (sigma << 4) | (key << 6) | (L.klass << 12));
     for (int k = 0; k < nt; ++k) {
-      int q[3];
+      int q3[3];
       for (int u = 0; u < 3; ++u) {
         const int l = tri_label(w, k, u);
-        q[u] = l == 7 ? 3 + L.ne : l;
+        q3[u] = l == 7 ? 3 + L.ne : l;
       }
-      tri[t0 + k] = make_int3((int)L.gid[q[0]], (int)L.gid[q[1]], (int)L.gid[q[2]]);
-      a.label[t0 + k] = r3_label(a, L.v[q[0]], L.v[q[1]], L.v[q[2]]);
+      tri[t0 + k] = make_int3((int)L.gid[q3[0]], (int)L.gid[q3[1]], (int)L.gid[q3[2]]);
+      a.label[t0 + k] = r3_label(a, L.v[q3[0]], L.v[q3[1]], L.v[q3[2]]);
       a.code[t0 + k] = code;
     }
   }
@@ -845,16 +1029,18 @@ int launch_r3_adjacency(const R3Args& a, u32* scr, cudaStream_t st) {
 }
 
 int launch_r3_count(const R3Args& a, cudaStream_t st) {
-  const unsigned g = (unsigned)std::min<u64>((a.nt + 127) / 128, 152 * 16);
-  k_r3_count<<<std::max(g, 1u), 128, 0, st>>>(a);
-  return 1;
+  const unsigned g = (unsigned)std::min<u64>((a.nt + 255) / 256, 152 * 16);
+  k_r3_screen<<<std::max(g, 1u), 256, 0, st>>>(a);
+  k_r3_count<<<152 * 16, 128, 0, st>>>(a);
+  return 2;
 }
 
 int launch_r3_emit(const R3Args& a, cudaStream_t st) {
-  const unsigned g = (unsigned)std::min<u64>((a.nt + 127) / 128, 152 * 16);
-  k_r3_emit<<<std::max(g, 1u), 128, 0, st>>>(a);
+  const unsigned g = (unsigned)std::min<u64>((a.nt + 255) / 256, 152 * 16);
+  k_r3_emit_uncut<<<std::max(g, 1u), 256, 0, st>>>(a);
+  k_r3_emit<<<152 * 16, 128, 0, st>>>(a);
   k_r3_tierg<<<152 * 8, 32 * R3G_WARPS, 0, st>>>(a);
-  return 2;
+  return 3;
 }
 
 }  // namespace sbmt

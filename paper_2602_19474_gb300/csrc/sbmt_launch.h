@@ -283,7 +283,7 @@ int launch_preprocess(const PreArgs& a, u64 nw, u32* wpop, u32* wscan, u32* scr,
 // events on the edges it owns (the smaller cell beside an edge), the inside
 // vertices and the owned events per local edge (8 bits each), their
 // exclusive scans (nt + 1 each), the output mesh, the Tier-G queue (nt
-// entries) and its length, and the error word.
+// entries) and its length, the error word and counters.
 enum : u32 { R3_CAPACITY = 1u, R3_GEOMETRY = 2u, R3_COUNT = 4u };
 struct R3Args {
   const unsigned char* img;
@@ -301,6 +301,10 @@ struct R3Args {
   int* tri;
   unsigned short *label, *code;
   u32 *glist, *ng, *err, *ncut, *ngtri;
+  unsigned short* ulab;  // per cell: the label of an uncut cell's pixel box
+  u32* cmark;            // candidate bit-plane, (nt + 31) / 32 words
+  u32 *cand, *ncand;     // the candidates (nt entries) and their count
+  u32* ngsmall;          // Tier-G cells done by one thread
 };
 int launch_r3_adjacency(const R3Args& a, u32* scr, cudaStream_t st);
 int launch_r3_count(const R3Args& a, cudaStream_t st);
