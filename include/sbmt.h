@@ -77,11 +77,18 @@ typedef struct {
 } sbmt_image;
 
 /* Meshing parameters.  h = h_num / h_den pixels (Sec. 3.3's edge length);
- * the grid origin is (origin2x / 2, origin2y / 2).  Only the
- * degeneracy-free class is accepted: h_num even in 2..1024, h_den odd in
- * 1..63, origin2x and origin2y even.  Under it no grid vertex lies on a
- * pixel line and no pixel corner on a grid edge, so every Alg. 1 event is a
- * proper crossing; other parameters return SBMT_EINVAL.  mode is
+ * the grid origin is (origin2x / 2, origin2y / 2).  h_num is even in
+ * 2..1024 and h_den odd in 1..63 (else SBMT_EINVAL).  With origin2x and
+ * origin2y even (the degeneracy-free class) no grid vertex lies on a pixel
+ * line and no pixel corner on a grid edge, so every Alg. 1 event is a proper
+ * crossing: the lattice path.  An odd one puts the origin on a pixel line
+ * (a degenerate origin, e.g. (-1/2, -1/2) with origin2x = origin2y = -1):
+ * grid vertices then lie on pixel lines and grid edges on the image
+ * border, and mesh_bitmap meshes it by the general path -- the unmoved base
+ * mesh, then the per-cell retriangulation of mesh_retriangulate, which takes
+ * Alg. 1's vertex-on-segment and overlap incidences (explicit format; the
+ * mesh numbered and coded as mesh_retriangulate's).  mesh_batch and
+ * mesh_preprocess take even origins only.  mode is
  * SBMT_PLAIN or SBMT_PREPROCESS for mesh_bitmap (Alg. 3 in full, explicit
  * format only: see mesh_bitmap), SBMT_PLAIN for mesh_batch (SBMT_PREPROCESS
  * returns SBMT_EPROTO there) and SBMT_PREPROCESS for mesh_preprocess, which

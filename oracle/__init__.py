@@ -98,6 +98,8 @@ def _load():
         lib.oracle_region3.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Mesh)]
+        lib.oracle_brute_general.restype = ctypes.c_int64
+        lib.oracle_brute_general.argtypes = [ctypes.c_int32] * 6 + [ctypes.c_int64] * 2
         lib.oracle_greedy.restype = ctypes.c_int
         lib.oracle_greedy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_int32]
@@ -285,6 +287,27 @@ def region3(img: np.ndarray, xy: np.ndarray, tri: np.ndarray, plant: int = 0) ->
     finally:
         lib.oracle_mesh_free(ctypes.byref(m))
     return out
+
+
+def mesh_general(img: np.ndarray, h_num: int, h_den: int = 1, origin2x: int = 0, origin2y: int = 0) -> dict:
+    """The general path, for any integer origin (an odd origin2x / origin2y
+    puts the lattice on pixel lines): the base mesh, then Region III."""
+    H, W = img.shape
+    xy0, cells = base_mesh(W, H, h_num, h_den, origin2x, origin2y)
+    out = region3(img, xy0, cells)
+    out["base_xy"], out["base_tri"] = xy0, cells
+    return out
+
+
+def brute_general(width: int, height: int, h_num: int, h_den: int = 1, origin2x: int = -1, origin2y: int = -1,
+                  first: int = 0, stride: int = 1) -> int:
+    """brute() for the general path at the given origin: every binary bitmap
+    (from first, every stride-th) meshed as mesh_general does and checked
+    against the invariants.  Returns the number checked; raises on a failure."""
+    r = _load().oracle_brute_general(width, height, h_num, h_den, origin2x, origin2y, first, stride)
+    if r < 0:
+        raise OracleError(_load().oracle_last_error().decode())
+    return r
 
 
 def last_error() -> str:

@@ -1083,13 +1083,14 @@ int oracle_greedy(const int64_t* pts4, int32_t n, const int32_t* cons, int32_t n
 /* The base mesh T0 of Sec. 3.3 (the lattice cells meeting the closed image
  * rectangle, no boundary embedded), the input of the preprocessing of
  * Alg. 3: lattice vertex coordinates (2 doubles each, vertex-id order) and
- * the cells' corners A, B, C (3 vertex ids each, cell-id order).  Free the
- * two arrays with oracle_free. */
+ * the cells' corners A, B, C (3 vertex ids each, cell-id order).  Any
+ * integer origin2x, origin2y: an odd one puts the origin on a pixel line
+ * (the degenerate origins).  Free the two arrays with oracle_free. */
 int oracle_base_mesh(int32_t width, int32_t height, int32_t h_num, int32_t h_den, int32_t origin2x, int32_t origin2y,
                      int64_t* nverts, int64_t* ncells, double** xy, int32_t** tri) {
   g_err[0] = 0;
   if (!nverts || !ncells || !xy || !tri || width < 1 || height < 1 || h_num < 1 || h_den < 1 || (h_num % 2) != 0 ||
-      (h_den % 2) != 1 || (origin2x % 2) != 0 || (origin2y % 2) != 0) {
+      (h_den % 2) != 1) {
     std::snprintf(g_err, sizeof g_err, "invalid arguments");
     return -1;
   }
@@ -1168,6 +1169,15 @@ static int check_invariants(const uint8_t* img, int W, int H, double h, const Me
     size_t m = k + 1;
     while (m < e.size() && e[m][0] == e[k][0] && e[m][1] == e[k][1]) ++m;
     if (m - k > 2) return std::snprintf(g_err, sizeof g_err, "edge in three triangles"), 5;
+    if (m - k == 1 && M.label[e[k][2]] != 0xFFFF) {
+      // an outer edge of the mesh with an image label inside: it must lie
+      // on the image border (a lattice row on the border line)
+      const i64 u = e[k][0], w = e[k][1];
+      const bool onh = Y(u) == Y(w) && (Y(u) == -0.5 || Y(u) == H - 0.5);
+      const bool onv = X(u) == X(w) && (X(u) == -0.5 || X(u) == W - 0.5);
+      if (!onh && !onv) return std::snprintf(g_err, sizeof g_err, "an image label on the mesh's outer boundary"), 13;
+      blen += std::fabs(X(u) - X(w)) + std::fabs(Y(u) - Y(w));
+    }
     if (m - k == 2) {
       if (e[k][3] == e[k + 1][3]) return std::snprintf(g_err, sizeof g_err, "directed edge repeated"), 6;
       if (M.label[e[k][2]] != M.label[e[k + 1][2]]) {
@@ -1752,9 +1762,67 @@ void r3_mesh(const Image& im, const std::vector<R3Pt>& X, const std::vector<int3
   }
 }
 
+/* the base mesh T0 as arrays: lattice vertices in id order, cells' corners */
+void base_mesh_arrays(i64 W, i64 H, i64 p, i64 q, i64 o2x, i64 o2y, std::vector<R3Pt>& X, std::vector<int32_t>& T,
+                      i64* ncells) {
+  Grid g;
+  build_grid(g, W, H, p, q, o2x, o2y);
+  X.clear(), T.clear();
+  for (i64 j = g.vj0; j <= g.vj1; ++j)
+    for (i64 i = g.vlo[j - g.vj0]; i <= g.vhi[j - g.vj0]; ++i) {
+      const Pt v = g.vtx(i, j);
+      X.push_back({to_double(v.x) / (double)g.S, to_double(v.y) / (double)g.S});
+    }
+  for (i64 j = g.j0; j <= g.j1; ++j)
+    for (i64 c = g.clo[j - g.j0]; c <= g.chi[j - g.j0]; ++c) {
+      i64 ci[3], cj[3];
+      g.corners(c, j, ci, cj);
+      for (int k = 0; k < 3; ++k) T.push_back((int32_t)g.vid(ci[k], cj[k]));
+    }
+  *ncells = g.ncells;
+}
+
 }  // namespace
 
 extern "C" {
+
+/* Every binary W x H <= 25 bitmap (bit k = pixel k, row-major; from first,
+ * every stride-th) meshed by the general path -- the base mesh at origin
+ * (o2x/2, o2y/2), any integer o2x, o2y, then Region III -- and checked
+ * against the invariants of any correct output.  Returns the number checked,
+ * or -(1 + the first failing bitmap) with the message in oracle_last_error. */
+int64_t oracle_brute_general(int32_t W, int32_t H, int32_t h_num, int32_t h_den, int32_t o2x, int32_t o2y,
+                             int64_t first, int64_t stride) {
+  g_err[0] = 0;
+  if (W < 1 || H < 1 || W * H > 25 || stride < 1 || first < 0) return -1;
+  std::vector<uint8_t> img(W * H);
+  const int64_t n = (int64_t)1 << (W * H);
+  int64_t done = 0;
+  std::vector<R3Pt> X;
+  std::vector<int32_t> T;
+  for (int64_t b = first; b < n; b += stride) {
+    for (int k = 0; k < W * H; ++k) img[k] = (uint8_t)((b >> k) & 1);
+    try {
+      Image im{W, H, (int64_t)W, 1, img.data()};
+      i64 ncells = 0;
+      base_mesh_arrays(W, H, h_num, h_den, o2x, o2y, X, T, &ncells);
+      R3Mesh R;
+      r3_mesh(im, X, T, R);
+      Mesh M;
+      M.xy = R.xy, M.tri = R.tri, M.label = R.label, M.ncells = ncells;
+      if (check_invariants(img.data(), W, H, (double)h_num / h_den, M)) {
+        const std::string what = g_err;
+        std::snprintf(g_err, sizeof g_err, "bitmap %lld: %.400s", (long long)b, what.c_str());
+        return -(1 + b);
+      }
+    } catch (const std::exception& ex) {
+      std::snprintf(g_err, sizeof g_err, "bitmap %lld: %s", (long long)b, ex.what());
+      return -(1 + b);
+    }
+    ++done;
+  }
+  return done;
+}
 
 /* Region III: Alg. 2 on the counter-clockwise triangle mesh T (nv vertices
  * as 2 doubles, nt cells as 3 vertex ids) against the boundary of the image;

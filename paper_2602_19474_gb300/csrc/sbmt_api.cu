@@ -589,7 +589,9 @@ void destroy_mesh(sbmt_ctx* ctx, MeshRec* m, cudaStream_t st) {
   delete m;
 }
 
-int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false) {
+// pre: mesh_preprocess's parameters; base: the general path's base mesh
+// (any integer origin, no thresholds)
+int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false, bool base = false) {
   if (!img || !pr || !img->data) return fail(SBMT_EINVAL, "null image or params");
   if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768)
     return fail(SBMT_EINVAL, "image size %dx%d outside 1..32768", img->width, img->height);
@@ -600,7 +602,9 @@ int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false)
   // host image is copied into an aligned buffer first)
   if (img->on_device && img->dtype == SBMT_U16 && ((img->pitch_bytes & 1) || ((uintptr_t)img->data & 1)))
     return fail(SBMT_EINVAL, "a device u16 image needs an even pitch and an even address");
-  if (pre) {
+  if (base) {
+    if (pr->format != SBMT_EXPLICIT) return fail(SBMT_EINVAL, "a degenerate origin is meshed in the explicit format");
+  } else if (pre) {
     if (pr->mode != SBMT_PREPROCESS || pr->format != SBMT_EXPLICIT)
       return fail(SBMT_EINVAL, "mesh_preprocess takes mode SBMT_PREPROCESS and the explicit format");
   } else {
@@ -612,9 +616,11 @@ int check_params(const sbmt_image* img, const sbmt_params* pr, bool pre = false)
       !(pr->h_den & 1))
     return fail(SBMT_EINVAL, "h = %d/%d outside the degeneracy-free class (even h_num <= 1024, odd h_den < 64)",
                 pr->h_num, pr->h_den);
-  if ((pr->origin2x & 1) || (pr->origin2y & 1) || pr->origin2x < -65536 || pr->origin2x > 65536 ||
-      pr->origin2y < -65536 || pr->origin2y > 65536)
-    return fail(SBMT_EINVAL, "origin must be integer pixels within +-32768");
+  if (pr->origin2x < -65536 || pr->origin2x > 65536 || pr->origin2y < -65536 || pr->origin2y > 65536)
+    return fail(SBMT_EINVAL, "origin outside +-32768 px");
+  if (!base && ((pr->origin2x & 1) || (pr->origin2y & 1)))
+    return fail(SBMT_EINVAL, "origin (%d/2, %d/2) on a pixel line: mesh_bitmap meshes it (the general path); "
+                "mesh_batch and mesh_preprocess take integer origins", pr->origin2x, pr->origin2y);
   return SBMT_OK;
 }
 
@@ -1157,11 +1163,14 @@ int pre_thresholds(const sbmt_params* pr, double* A, double* B, double* C) {
 }
 
 // the preprocessed mesh of one image (Alg. 3), enqueued on one lane
-int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
-  int rc = check_params(img, pr, true);
+// base_only: the unmoved base mesh (no thresholds: nothing snaps, moves or
+// splits), for the general path
+int pre_one(sbmt_ctx* ctx, Lane* lane, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out,
+            bool base_only = false) {
+  int rc = check_params(img, pr, !base_only, base_only);
   if (rc) return rc;
-  double A, B, C;
-  if ((rc = pre_thresholds(pr, &A, &B, &C))) return rc;
+  double A = 0.0, B = 0.0, C = 0.0;
+  if (!base_only && (rc = pre_thresholds(pr, &A, &B, &C))) return rc;
   cudaStream_t st = lane->stream;
   CK(cudaSetDevice(ctx->device));
   GridP g{};
@@ -1433,9 +1442,13 @@ int device_image(const sbmt_image* img, cudaStream_t st, sbmt_image* dev, void**
   return SBMT_OK;
 }
 
-// Alg. 3 in full: Regions I-II (mesh_preprocess), the barrier, Region III
-int preprocess_mesh(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out) {
-  int rc = check_params(img, pr, true);
+// Alg. 3 in full: Regions I-II (mesh_preprocess), the barrier, Region III.
+// base_only: the general path of a degenerate origin -- the unmoved base
+// mesh, then Region III (Alg. 2 cell by cell, with Alg. 1's vertex-on-segment
+// and overlap incidences that a lattice on the pixel lines creates)
+int preprocess_mesh(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr, sbmt_mesh* out,
+                    bool base_only = false) {
+  int rc = check_params(img, pr, !base_only, base_only);
   if (rc) return rc;
   Lane* lane = &ctx->main;
   cudaStream_t st = lane->stream;
@@ -1447,7 +1460,7 @@ int preprocess_mesh(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* pr,
     return rc;
   }
   sbmt_mesh tid = 0;
-  rc = pre_one(ctx, lane, &dev, pr, &tid);
+  rc = pre_one(ctx, lane, &dev, pr, &tid, base_only);
   MeshRec* tm = nullptr;
   if (rc == SBMT_OK) {
     std::lock_guard<std::mutex> lk(ctx->reg);
@@ -1506,6 +1519,8 @@ int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params,
   if (!ctx || !out || !params) return fail(SBMT_EINVAL, "null ctx, params or out");
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (params->mode == SBMT_PREPROCESS) return preprocess_mesh(ctx, img, params, out);
+  if (params->mode == SBMT_PLAIN && ((params->origin2x & 1) || (params->origin2y & 1)))
+    return preprocess_mesh(ctx, img, params, out, true);
   RunOpts o = opts_of(tune_for(ctx, img, 1, params, 1));
   o.stall = (params->flags & SBMT_DEBUG_STALL_SCAN) != 0;
   return mesh_run(ctx, &ctx->main, img, 1, params, 1, out, o);

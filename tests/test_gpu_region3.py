@@ -192,3 +192,53 @@ def test_full_size_windows():
     del t
     sb.mesh_release(c, m)
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# degenerate origins: mesh_bitmap's general path against the oracle's
+# ---------------------------------------------------------------------------
+def gpu_general(img, hn, hd, ox, oy):
+    cx = ctx()
+    m = sb.mesh_bitmap(cx, img, hn, hd, ox, oy)
+    v = sb.mesh_query(cx, m, -1)
+    out = sb.view_numpy(v)
+    out.update(n_cut=v.n_cut_cells, n_tierG=v.n_tierG_cells, n_events=v.n_events, n_inside=v.n_inside_vertices,
+               n_base=v.n_lattice_vertices, n_cells=v.n_cells, n_tierG_triangles=v.n_tierG_triangles)
+    sb.mesh_release(cx, m)
+    return out
+
+
+@pytest.mark.parametrize("ox,oy", [(-1, -1), (1, 0), (0, 3), (-1, 5)])
+def test_degenerate_origins_match_the_oracle(ox, oy):
+    rng = np.random.default_rng(200 + ox + 7 * oy)
+    for hn, hd in [(2, 1), (4, 1), (2, 3)]:
+        W, H = (int(x) for x in rng.integers(6, 40, 2))
+        img = np.ascontiguousarray(rng.integers(0, 3, (H, W)).astype(np.uint8))
+        assert_same(gpu_general(img, hn, hd, ox, oy), oracle.mesh_general(img, hn, hd, ox, oy))
+    img = synth.voronoi_labels(size=96, nseeds=12)
+    assert_same(gpu_general(img, 2, 1, ox, oy), oracle.mesh_general(img, 2, 1, ox, oy))
+
+
+def test_every_3x3_bitmap_at_origin_minus_half():
+    for b in range(512):
+        img = np.array([(b >> k) & 1 for k in range(9)], np.uint8).reshape(3, 3)
+        assert_same(gpu_general(img, 2, 1, -1, -1), oracle.mesh_general(img, 2, 1, -1, -1))
+
+
+def test_4x4_bitmaps_at_origin_minus_half():
+    """Every 16th binary 4x4 bitmap at origin (-1/2, -1/2), h = 2 and 2/3."""
+    for hn, hd in [(2, 1), (2, 3)]:
+        for b in range(0, 65536, 16):
+            img = np.array([(b >> k) & 1 for k in range(16)], np.uint8).reshape(4, 4)
+            assert_same(gpu_general(img, hn, hd, -1, -1), oracle.mesh_general(img, hn, hd, -1, -1))
+
+
+def test_degenerate_origin_refused_where_not_meshed():
+    img = synth.disk()
+    c = ctx()
+    with pytest.raises(sb.SbmtError) as e:
+        sb.mesh_bitmap(c, img, 2, 1, -1, -1, format=sb.SBMT_COMPACT)
+    assert e.value.code == sb.SBMT_EINVAL
+    with pytest.raises(sb.SbmtError) as e:
+        sb.mesh_preprocess(c, img, 2, 1, 0.26, 0.125, 0.183, -1, -1)
+    assert e.value.code == sb.SBMT_EINVAL

@@ -228,3 +228,42 @@ def test_the_preprocessed_mesh_must_cover_the_image(monkeypatch):
     T = P.preprocess(img, 2, 1, *TRIPLET)
     with pytest.raises(AssertionError):
         check_embedded(img, T, oracle.region3(img, T["xy"], T["tri"]))
+
+
+# ---------------------------------------------------------------------------
+# degenerate origins: the general path (base mesh, then Region III)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("hn,hd,stride", [(2, 1, 1), (4, 1, 1), (2, 3, 3)])
+def test_every_4x4_bitmap_at_origin_minus_half(hn, hd, stride):
+    """At origin (-1/2, -1/2) the lattice's row 0 lies on the image border and
+    the vertices of every even row on vertical pixel lines: every cell the
+    boundary meets is degenerate.  Every binary 4x4 bitmap (every third at
+    h = 2/3) meshes to a correct embedding (the invariants of brute())."""
+    n = oracle.brute_general(4, 4, hn, hd, -1, -1, 0, stride)
+    assert n == (65536 + stride - 1) // stride
+
+
+@pytest.mark.parametrize("ox,oy", [(-1, -1), (1, 0), (0, 3), (-1, 5)])
+def test_degenerate_origins_on_label_images(ox, oy):
+    rng = np.random.default_rng(100 + ox + 7 * oy)
+    for hn, hd in [(2, 1), (4, 1), (2, 3)]:
+        W, H = (int(x) for x in rng.integers(6, 24, 2))
+        img = np.ascontiguousarray(rng.integers(0, 3, (H, W)).astype(np.uint8))
+        R = oracle.mesh_general(img, hn, hd, ox, oy)
+        check_embedded(img, dict(xy=R["base_xy"], tri=R["base_tri"]), R)
+        # the degeneracy is there: lattice vertices exactly on pixel lines
+        on_line = ((R["base_xy"] + 0.5) % 1.0 == 0.0).any(axis=1)
+        assert on_line.any()
+        # an event on an edge of the outer boundary (a lattice row on the
+        # image border) adds one triangle, not two
+        assert len(R["base_tri"]) + 2 * R["n_inside"] + R["n_events"] <= len(R["tri"])
+        assert len(R["tri"]) <= len(R["base_tri"]) + 2 * R["n_inside"] + 2 * R["n_events"]
+
+
+def test_general_path_at_an_integer_origin_is_the_plain_mesh():
+    """At an integer origin the general path is the lattice path."""
+    img = np.ascontiguousarray(synth.voronoi_labels(64, 12, 16))
+    o = oracle.mesh_bitmap(img, 2, 1, 2, -4)
+    g = oracle.mesh_general(img, 2, 1, 2, -4)
+    assert np.abs(g["xy"][g["tri"]] - o["xy"][o["tri"]]).max() <= 1e-9
+    assert np.array_equal(g["label"], o["label"]) and np.array_equal(g["code"], o["code"])
