@@ -55,6 +55,7 @@ struct GStore {
   unsigned short cand[NCANDP];
   u32 tri[2 * N];
   float fx[N], fy[N];  // the values rounded once from double, for the fast filters
+  unsigned char em[N];  // the cell edges a vertex lies on (bit k: edge k)
   int n, nev, nedge, ntri, ok;
 };
 template <int N>
@@ -202,6 +203,7 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
   }
   s.n = n, s.nev = ne;
   for (int k = 0; k < n; ++k) {
+    s.em[k] = k < 3 ? (unsigned char)((1 << k) | (1 << (k == 0 ? 2 : k - 1))) : k < 3 + ne ? (unsigned char)(1 << ek[k]) : 0;
     s.adj[k] = 0;
     s.fx[k] = (float)zdouble(zq(s.xa[k], s.xb[k]));
     s.fy[k] = (float)zdouble(zq(s.ya[k], s.yb[k]));
@@ -415,17 +417,28 @@ SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
     if ((Zset(u, v) >> w) & 1u) return 0;
     return ((Lset(u, v) >> w) & 1u) ? 1 : -1;
   };
-  // candidates in order of exact length, then (u, v)
+  // candidates in order of exact length, then (u, v).  A pair on one cell
+  // edge that is not a cycle edge always has a vertex between its ends, so
+  // it is left out; each candidate's single-precision key is taken once.
   int m = 0;
+  float key[NPAIR];
   for (int u = 0; u < n; ++u)
     for (int v = u + 1; v < n; ++v)
-      if (!((s.adj[u] >> v) & 1ull)) s.cand[m++] = (unsigned short)((u << 8) | v);
-  for (int a = 1; a < m; ++a) {
-    const unsigned short x = s.cand[a];
-    int b = a;
-    while (b > 0 && cand_less_fast(s, x, s.cand[b - 1], tolc)) s.cand[b] = s.cand[b - 1], --b;
-    s.cand[b] = x;
-  }
+      if (!((s.adj[u] >> v) & 1ull) && !(s.em[u] & s.em[v])) {
+        const unsigned short x = (unsigned short)((u << 8) | v);
+        const float dx = sfx(s, v) - sfx(s, u), dy = sfy(s, v) - sfy(s, u);
+        const float kx = dx * dx + dy * dy;
+        int b = m++;
+        // insertion: the same order as cand_less_fast, with the keys kept
+        while (b > 0) {
+          const float ky = key[b - 1];
+          const float tol = 1e-5f * (kx + ky) + tolc;
+          const bool less = kx < ky - tol ? true : kx > ky + tol ? false : cand_less(s, x, s.cand[b - 1]);
+          if (!less) break;
+          s.cand[b] = s.cand[b - 1], key[b] = key[b - 1], --b;
+        }
+        s.cand[b] = x, key[b] = kx;
+      }
   const int max_edges = 3 * n - nb - 3;
   for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
     const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
