@@ -117,19 +117,36 @@ SBMT_DEV void corner_bits_tile(const unsigned char* img, i64 pitch, int W, int H
   };
   u32 mycnt = 0;
   const int x0 = xb + lane * 8;  // first corner column of this thread
+  // a tile whose pixels (rows r0 - 1 .. r0 + 31, columns xb - 1 .. xb + 255)
+  // all lie in the image reads them without bounds checks
+  const bool interior = xb >= 1 && xb + 255 < W && r0 >= 1 && r0 + 31 < H;
   for (int rr = 0; rr < 4; ++rr) {
     const int r = w * 4 + rr, cy = r0 + r;
     int lo[9], hi[9];  // pixel rows cy-1 and cy, columns x0-1 .. x0+7
+    if (interior) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) lo[k] = P(x0 - 1 + k, cy - 1), hi[k] = P(x0 - 1 + k, cy);
-    u32 bits = 0;
+      for (int k = 0; k < 9; ++k) lo[k] = tile.px[r][x0 - 1 + k - xs], hi[k] = tile.px[r + 1][x0 - 1 + k - xs];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) lo[k] = P(x0 - 1 + k, cy - 1), hi[k] = P(x0 - 1 + k, cy);
+    }
+    // the eight corners' masks as bit vectors: corner (x0 + k, cy) has pixels
+    // a = lo[k], b = lo[k+1], c = hi[k], d = hi[k+1]; its E edge is b != d,
+    // W a != c, N c != d, S a != b
+    u32 vv = 0, nn = 0, ss = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vv |= (lo[k] != hi[k] ? 1u : 0u) << k;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      // corner (x0 + k, cy): a = (cx-1, cy-1), b = (cx, cy-1), c = (cx-1, cy), d = (cx, cy)
-      const int a = lo[k], b = lo[k + 1], c = hi[k], d = hi[k + 1];
-      const int m = (b != d ? BE_E : 0) | (a != c ? BE_W : 0) | (c != d ? BE_N : 0) | (a != b ? BE_S : 0);
-      const bool v = vertex_mask(m) && x0 + k <= W && cy <= H;
-      bits |= (v ? 1u : 0u) << k;
+      nn |= (hi[k] != hi[k + 1] ? 1u : 0u) << k;
+      ss |= (lo[k] != lo[k + 1] ? 1u : 0u) << k;
+    }
+    const u32 ee = vv >> 1, ww = vv & 0xFFu;
+    // a vertex: some boundary edge, and not exactly two collinear ones
+    u32 bits = (ee | ww | nn | ss) & ~(ee & ww & ~nn & ~ss) & ~(nn & ss & ~ee & ~ww) & 0xFFu;
+    if (!interior) {
+      const int room = W - x0 + 1;  // corners x0 + k <= W
+      bits &= cy <= H ? (room >= 8 ? 0xFFu : room > 0 ? (1u << room) - 1u : 0u) : 0u;
     }
     fl[r][lane] = (unsigned char)bits;
     mycnt += __popc(bits);

@@ -90,7 +90,7 @@ __global__ void k_counts_b(const Job* __restrict__ jobs, int njobs, u32* out) {
   __threadfence_system();
 }
 
-constexpr u32 CH = 8;  // pairs per thread in the chunked walks
+constexpr u32 CH = 2;  // pairs per thread in the chunked walks
 
 // atomicAdd(&cur[key], 1) for each active lane, one atomic per distinct key
 // among them (neighbouring lanes mostly fill the same bucket)
