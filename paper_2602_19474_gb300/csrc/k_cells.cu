@@ -126,74 +126,86 @@ SBMT_DEV Klass classify_cell(const GridP& g, const CellGeo& cg, const Pair* P, u
   return r;
 }
 
-// K3a: one block per cell bucket (1024 consecutive cell ids).  The bucket's
-// pairs are counting-sorted by cell in shared memory (histogram, scan,
-// scatter); each cut cell gets a record, in cell order, in a dense range of
-// recs drawn from a counter (bbase[b], bcut[b] records).
+// K3a: one warp per cell bucket (1024 consecutive cell ids), four buckets
+// to a block.  The bucket's pairs are counting-sorted by cell in the warp's
+// shared memory -- a histogram, a scan over the 1024 cells in 32 rounds of
+// the warp, a scatter -- and each cut cell gets a record, in cell order, in
+// a dense range of recs drawn from a counter (bbase[b], bcut[b] records).
+// The warp's one array holds the counts, then their exclusive scan, then
+// (after the scatter's increments) each cell's end, which is the next cell's
+// start.  No block barrier: a bucket holds a few dozen pairs, and the warps
+// of a block do not wait for one another.
+constexpr int SORT_W = 4;  // buckets (warps) per block
 template <bool ONE>
-__global__ void __launch_bounds__(256) k_sort_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
-                                                const u32* __restrict__ bpre, int njobs) {
+__global__ void __launch_bounds__(32 * SORT_W) k_sort_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
+                                                       const u32* __restrict__ bpre, int njobs) {
   constexpr int NB = 1 << CB_LOG;
-  __shared__ u32 s_cnt[NB], s_off[NB], s_cur[NB];
-  __shared__ unsigned short s_cut[NB];
-  __shared__ u32 s_sh[8];
-  __shared__ u32 s_base;
-  __shared__ u32 s_kc[NCLS], s_kb[NCLS];
+  __shared__ __align__(16) u32 s_c[SORT_W][NB];
+  __shared__ unsigned short s_cut[SORT_W][NB];
+  __shared__ u32 s_kc[SORT_W][NCLS], s_kc2[SORT_W][NCLS], s_kb[SORT_W][NCLS];
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 b = lb * SORT_W + (u32)w;
+  if (b >= J.nbc) return;
   const Pair* pairs = J.pairs;
   Pair* sorted = J.raw;
-  const u32* poff = J.poff;
-  CutRec* recs = J.recs;
-  u32* nrec = jc(J, JC_NREC);
-  u32* bcut = J.bcut;
-  u32* bbase = J.bbase;
-  const u32 b = lb, lo = poff[b], n = poff[b + 1] - lo;
+  u32* c = s_c[w];
+  unsigned short* cut = s_cut[w];
+  const u32 lo = J.poff[b], n = J.poff[b + 1] - lo;
   const i64 c0 = (i64)b << CB_LOG;
   if (n == 0) {
-    if (threadIdx.x == 0) bcut[b] = 0, bbase[b] = 0;
+    if (lane == 0) J.bcut[b] = 0, J.bbase[b] = 0;
     return;
   }
-  for (int k = threadIdx.x; k < NB; k += blockDim.x) s_cnt[k] = 0;
-  if (threadIdx.x < NCLS) s_kc[threadIdx.x] = 0;
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[pairs[lo + i].cell - c0], 1u);
-  __syncthreads();
-  u32 ncut;
-  {
-    const int k0 = threadIdx.x * 4;
-    u32 v[4], s = 0, c = 0;
-    for (int u = 0; u < 4; ++u) v[u] = s_cnt[k0 + u], s += v[u], c += v[u] ? 1u : 0u;
-    u32 tot;
-    u32 run = block_exscan256(s, &tot, s_sh);
-    u32 crun = block_exscan256(c, &ncut, s_sh);
-    for (int u = 0; u < 4; ++u) {
-      s_off[k0 + u] = run, s_cur[k0 + u] = run, run += v[u];
-      if (v[u]) s_cut[crun++] = (unsigned short)(k0 + u);
+  for (int k = lane; k < NB / 4; k += 32) reinterpret_cast<uint4*>(c)[k] = make_uint4(0u, 0u, 0u, 0u);
+  if (lane < NCLS) s_kc[w][lane] = 0, s_kc2[w][lane] = 0;
+  __syncwarp();
+  for (u32 i = lane; i < n; i += 32) atomicAdd(&c[pairs[lo + i].cell - c0], 1u);
+  __syncwarp();
+  // exclusive scan of the counts, and the cut cells in order
+  u32 carry = 0, ncut = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < NB / 32; ++r) {
+    const u32 v = c[r * 32 + lane];
+    u32 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += y;
     }
+    c[r * 32 + lane] = carry + inc - v;
+    carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, v != 0u);
+    if (v) cut[ncut + __popc(m & lt)] = (unsigned short)(r * 32 + lane);
+    ncut += __popc(m);
   }
-  if (threadIdx.x == 0) s_base = atomicAdd(nrec, ncut);
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+  u32 base = 0;
+  if (lane == 0) base = atomicAdd(jc(J, JC_NREC), ncut);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  __syncwarp();
+  for (u32 i = lane; i < n; i += 32) {
     const Pair p = pairs[lo + i];
-    const u32 slot = atomicAdd(&s_cur[p.cell - c0], 1u);
-    sorted[lo + slot] = p;
+    sorted[lo + atomicAdd(&c[p.cell - c0], 1u)] = p;
   }
-  const u32 base = s_base;
-  // records, and their places in the class lists (the order within a class
+  __syncwarp();
+  // records (a cell's start is the previous cell's end), and their class
+  // counts; then their places in the class lists (the order within a class
   // is only the classification's work order)
-  u32 slot[4], cls[4];
-  for (u32 r = threadIdx.x, u = 0; r < ncut; r += blockDim.x, ++u) {
-    const int k = s_cut[r];
-    recs[base + r] = CutRec{(u32)(c0 + k), lo + s_off[k], s_cnt[k], 0u, 0u, 0u, 0u, 0u};
-    cls[u] = (u32)piece_class(s_cnt[k]);
-    slot[u] = atomicAdd(&s_kc[cls[u]], 1u);
+  for (u32 r = lane; r < ncut; r += 32) {
+    const int k = cut[r];
+    const u32 st = k == 0 ? 0u : c[k - 1], cnt = c[k] - st;
+    J.recs[base + r] = CutRec{(u32)(c0 + k), lo + st, cnt, 0u, 0u, 0u, 0u, 0u};
+    atomicAdd(&s_kc[w][piece_class(cnt)], 1u);
   }
-  __syncthreads();
-  if (threadIdx.x < NCLS && s_kc[threadIdx.x]) s_kb[threadIdx.x] = atomicAdd(jc(J, JC_KCNT + threadIdx.x), s_kc[threadIdx.x]);
-  __syncthreads();
-  for (u32 r = threadIdx.x, u = 0; r < ncut; r += blockDim.x, ++u)
-    J.klist[(size_t)cls[u] * J.NP + s_kb[cls[u]] + slot[u]] = base + r;
-  if (threadIdx.x == 0) bcut[b] = ncut, bbase[b] = base;
+  __syncwarp();
+  if (lane < NCLS && s_kc[w][lane]) s_kb[w][lane] = atomicAdd(jc(J, JC_KCNT + lane), s_kc[w][lane]);
+  __syncwarp();
+  for (u32 r = lane; r < ncut; r += 32) {
+    const int k = cut[r];
+    const u32 st = k == 0 ? 0u : c[k - 1], cls = (u32)piece_class(c[k] - st);
+    J.klist[(size_t)cls * J.NP + s_kb[w][cls] + atomicAdd(&s_kc2[w][cls], 1u)] = base + r;
+  }
+  if (lane == 0) J.bcut[b] = ncut, J.bbase[b] = base;
 }
 
 // ---------------------------------------------------------------------------
@@ -702,8 +714,8 @@ __global__ void __launch_bounds__(256) k_lattice_xy_b(const Job* __restrict__ jo
 
 int launch_sort_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
   if (nblocks == 0) return 0;
-  if (one) k_sort_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
-  else k_sort_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  if (one) k_sort_b<true><<<nblocks, 32 * SORT_W, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_sort_b<false><<<nblocks, 32 * SORT_W, 0, st>>>(Job{}, jobs, bpre, njobs);
   return 1;
 }
 

@@ -952,6 +952,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   const std::vector<u32> p_sc = prefix_of(n, [&](int k) { return (std::max(J[k].NP, J[k].NE) + 255) / 256; });
   const std::vector<u32> p_rk = prefix_of(n, [&](int k) { return J[k].nbe; });
   const std::vector<u32> p_so = prefix_of(n, [&](int k) { return J[k].nbc; });
+  const std::vector<u32> p_sw = prefix_of(n, [&](int k) { return (J[k].nbc + 3) / 4; });  // the sort: 4 buckets a block
   const std::vector<u32> p_go = prefix_of(n, [&](int k) { return (J[k].nbc + 7) / 8; });
   const std::vector<u32> p_lt = prefix_of(n, [&](int k) {
     return M[k]->format == SBMT_COMPACT ? 0u : (u32)((J[k].nm + 255) / 256);
@@ -961,7 +962,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   });
   // upload: jobs, scan jobs of both scans, and the prefixes
   const std::vector<const std::vector<u32>*> pres = {&p_cm, &p_walk, &p_sc, &p_rk, &p_so, &p_go, &p_lt, &p_lx,
-                                                    &t1pre, &t2pre};
+                                                    &t1pre, &t2pre, &p_sw};
   const size_t b_jobs = up256(n * sizeof(Job)), b_s1 = up256(sj1.size() * sizeof(ScanJob)),
                b_s2 = up256(std::max<size_t>(sj2.size(), 1) * sizeof(ScanJob));
   std::vector<size_t> poffs;
@@ -1005,7 +1006,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   TRACE(KN_RANK, nrk = launch_rank_b(one, dj, dpre(3), n, p_rk[n], bp, st, fork ? lane->side : nullptr, lane->fork,
                                      lane->join));
   if (nrk < 0) kerr = 1;
-  TRACE(KN_SORT, launch_sort_b(one, dj, dpre(4), n, p_so[n], st));
+  TRACE(KN_SORT, launch_sort_b(one, dj, dpre(10), n, p_sw[n], st));
   TRACE(KN_CUTCELLS, launch_cutcells_b(one, dj, n, bp, opt.cut_blocks_per_sm, st));
   TRACE(KN_SCAN, launch_mscan(ds2, dpre(9), n2, nt2, flags2, tickets + 1, NONE, st));
   // Tier-G beside the emission: both read the scans and the records, and
