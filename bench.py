@@ -361,22 +361,48 @@ def our_arm(args, rank: int, world: int, dist):
     # on the host between its launches, so host pauses show in its time)
     gc.collect()
     gc.disable()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # a workload whose image and mesh fit in twice the L2 (129 MB) has L2
+    # flushed (a 256 MB write) before each timed iteration, and each
+    # iteration timed on its own; a larger one streams through L2 anyway and
+    # is timed as one loop
+    small = img.nbytes + 16 * (v.n_vertices + v.n_triangles) < (256 << 20)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
+
+    def timed(fn, n):
+        """Milliseconds per call of fn on the context's stream over n calls."""
+        if flush_buf is None:
+            e0.record(st)
+            for _ in range(n):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n
+        tot = 0.0
+        for _ in range(n):
+            flush_buf.fill_(1)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / n
     # device-resident timed region
     sb.mesh_profile(ctx, True)
     sb.mesh_profile_read(ctx, reset=True)
     clk = ClockSampler(local)
     clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        v = step(dimg)
-    e1.record(st)
-    torch.cuda.synchronize()
+    last = [v]
+
+    def main_step():
+        last[0] = step(dimg)
+
+    ms = timed(main_step, args.steps)
+    v = last[0]
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     prof = sb.mesh_profile_read(ctx, reset=True)
     sb.mesh_profile(ctx, False)
     T = v.n_triangles
@@ -408,13 +434,9 @@ def our_arm(args, rank: int, world: int, dist):
         e2e_step()
     barrier()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(st)
-    torch.cuda.synchronize()
+    ms_e2e = timed(e2e_step, e2e_steps)
     barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
+    ms_e2e = max_over_ranks(ms_e2e, dist, dev)
     e2e_value = job_rate(world, T, ms_e2e)
     h2d = img.nbytes
     d2h = 16 * v.n_vertices + 16 * T
@@ -431,12 +453,7 @@ def our_arm(args, rank: int, world: int, dist):
         vc = step_compact()
     barrier()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        vc = step_compact()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_c = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    ms_c = max_over_ranks(timed(step_compact, args.steps), dist, dev)
     m = sb.mesh_bitmap(ctx, dimg, hn, hd, format=sb.SBMT_COMPACT)
     pins = {k: torch.empty(t.shape, dtype=t.dtype).pin_memory() for k, t in sb.view_tensors(sb.mesh_query(ctx, m, -1)).items()}
     sb.mesh_release(ctx, m)
@@ -453,13 +470,9 @@ def our_arm(args, rank: int, world: int, dist):
         e2e_compact()
     barrier()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(e2e_steps):
-        e2e_compact()
-    e1.record(st)
-    torch.cuda.synchronize()
+    ms_ce = timed(e2e_compact, e2e_steps)
     barrier()
-    ms_ce = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
+    ms_ce = max_over_ranks(ms_ce, dist, dev)
     # projection of a scalar pixel field onto the mesh (per-triangle means and
     # bilinear vertex values): a smooth synthetic intensity of the image's size
     m = sb.mesh_bitmap(ctx, dimg, hn, hd)
@@ -472,18 +485,8 @@ def our_arm(args, rank: int, world: int, dist):
     for _ in range(3):
         sb.mesh_project(ctx, m, field, tv, vv)
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        sb.mesh_project(ctx, m, field, tv, vv)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1) / args.steps
-    e0.record(st)
-    for _ in range(args.steps):
-        sb.mesh_project(ctx, m, field, tv, None)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_pt = e0.elapsed_time(e1) / args.steps
+    ms_p = timed(lambda: sb.mesh_project(ctx, m, field, tv, vv), args.steps)
+    ms_pt = timed(lambda: sb.mesh_project(ctx, m, field, tv, None), args.steps)
     sb.mesh_release(ctx, m)
     del field
     pbytes = 12.0 * T + 16.0 * vp.n_vertices + 4.0 * W * H + 4.0 * T + 4.0 * vp.n_vertices
@@ -505,12 +508,7 @@ def our_arm(args, rank: int, world: int, dist):
     for _ in range(3):
         vq, pinfo = step_pre()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        vq, pinfo = step_pre()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_q = e0.elapsed_time(e1) / args.steps
+    ms_q = timed(step_pre, args.steps)
     # the preprocessed mesh's smallest angle and area against the bounds of
     # the minimal-angle and minimal-area theorems (thresholds in pixels)
     m = sb.mesh_preprocess(ctx, dimg, hn, hd, *tri_abc)
@@ -542,12 +540,7 @@ def our_arm(args, rank: int, world: int, dist):
     for _ in range(3):
         vf = step_full()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        vf = step_full()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_f = e0.elapsed_time(e1) / args.steps
+    ms_f = timed(step_full, args.steps)
     mt = sb.mesh_preprocess(ctx, dimg, hn, hd, *tri_abc)
     vt = sb.mesh_query(ctx, mt, -1)
 
@@ -560,12 +553,7 @@ def our_arm(args, rank: int, world: int, dist):
     for _ in range(3):
         step_r3()
     torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        vr = step_r3()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_r3 = e0.elapsed_time(e1) / args.steps
+    ms_r3 = timed(step_r3, args.steps)
     # the embedded mesh's Tier-T sub-triangles against the two theorems'
     # bounds (at h = 2 px the boundary's 1-px runs are shorter than the edge,
     # outside the length constraint the theorems assume: reported, not held)
@@ -628,11 +616,9 @@ def our_arm(args, rank: int, world: int, dist):
     sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, 2, W / 2.0, H / 2.0, 127.0, u=uh)
     hsteps = 10
     torch.cuda.synchronize()
-    e0.record(st)
-    _, hpeaks, hits = sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, hsteps, W / 2.0, H / 2.0, 127.0, u=uh)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_h = e0.elapsed_time(e1)
+    hres = []
+    ms_h = timed(lambda: hres.append(sb.mesh_heat(ctx, m, Lh, 500.0, 0.01, hsteps, W / 2.0, H / 2.0, 127.0, u=uh)), 1)
+    _, hpeaks, hits = hres[-1]
     sb.mesh_release(ctx, m)
     del uh
     cg_its = sum(hits)
@@ -681,7 +667,9 @@ def our_arm(args, rank: int, world: int, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload + ": " + wl["desc"], "image": [W, H], "h": hn / hd,
                    "triangles_per_step": T, "vertices_per_step": v.n_vertices,
-                   "l2": "inputs larger than L2: %d MB image and %d MB mesh per step" % (img.nbytes >> 20,
+                   "l2": ("L2 flushed (a 256 MB write) before each timed step, each step timed on its own: %d MB "
+                          "image and %d MB mesh per step" if small else
+                          "inputs larger than L2: %d MB image and %d MB mesh per step") % (img.nbytes >> 20,
                                                                                     (16 * (T + v.n_vertices)) >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "bitmaps_per_s": world / (ms_max * 1e-3),
@@ -707,6 +695,12 @@ def our_arm(args, rank: int, world: int, dist):
         "clocks": clocks,
     }
     sb.mesh_destroy(ctx)
+    if world == 1 and not args.no_extras and args.workload == "voronoi8192":
+        # C2 (ellipses2048 at h = 4, where the Tier-G cells set the pace) on the
+        # same GPU, measured by the same run
+        c2 = measure_single(sb, torch, dev, local, "ellipses2048", 20, 5)
+        c2["roofline_path"].update(peak=peak, unit="GB/s", frac=c2["roofline_path"]["achieved"] / peak)
+        out["c2"] = c2
     if world == 1 and not args.no_extras:
         # the batched and serving forms on the same GPU, measured by the same run
         out["batch"] = measure_batch(sb, torch, dev, local, None, 1, "noise512", 5, 3)
@@ -819,6 +813,67 @@ def measure_batch(sb, torch, dev, local, dist, world, name: str, steps: int, war
                                "sample": "the first %d bitmaps of the batch, one per task over %d host cores"
                                          % (nimg_cpu, cores)}
     return out
+
+
+def measure_single(sb, torch, dev, local, name: str, steps: int, warmup: int) -> dict:
+    """One workload's device-resident step (mesh_bitmap) on this GPU: ms per
+    step, triangles/s and the stage shares, with L2 flushed (a 256 MB write)
+    before each timed step when the image and mesh fit in twice the L2."""
+    wl = WORKLOADS[name]
+    img = load_workload(name, 0, lambda: None)
+    H, W = img.shape
+    hn, hd = wl["h"]
+    st = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(st)
+    ctx = sb.mesh_create(local, 0, st.cuda_stream)
+    dimg = torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).to(dev)
+
+    def step():
+        m = sb.mesh_bitmap(ctx, dimg, hn, hd)
+        v = sb.mesh_query(ctx, m, -1)
+        sb.mesh_release(ctx, m)
+        return v
+
+    for _ in range(warmup):
+        v = step()
+    small = img.nbytes + 16 * (v.n_vertices + v.n_triangles) < (256 << 20)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sb.mesh_profile(ctx, True)
+    sb.mesh_profile_read(ctx, reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    torch.cuda.synchronize()
+    tot = 0.0
+    if flush_buf is None:
+        e0.record(st)
+        for _ in range(steps):
+            v = step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        tot = e0.elapsed_time(e1)
+    else:
+        for _ in range(steps):
+            flush_buf.fill_(1)
+            e0.record(st)
+            v = step()
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+    clocks = clk.stop()
+    ms = tot / steps
+    prof = sb.mesh_profile_read(ctx, reset=True)
+    sb.mesh_profile(ctx, False)
+    sb.mesh_destroy(ctx)
+    pt = sum(t for t, _ in prof.values()) or 1.0
+    pbytes = img.nbytes + 16.0 * v.n_vertices + 16.0 * v.n_triangles
+    return {"workload": name + ": " + wl["desc"], "ms_per_step": ms, "value": v.n_triangles / (ms * 1e-3),
+            "unit": "triangles/s", "bitmaps_per_s": 1e3 / ms, "triangles_per_step": v.n_triangles,
+            "tierG_cells": v.n_tierG_cells, "cut_cells": v.n_cut_cells,
+            "kernel_share": {k: round(t / pt, 4) for k, (t, _) in prof.items() if t > 0},
+            "roofline_path": {"achieved": pbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes_per_step": pbytes},
+            "l2": ("flushed (a 256 MB write) before each timed step" if small else "inputs larger than L2"),
+            "steps": steps, "warmup": warmup, "clocks": clocks}
 
 
 def batch_arm(args, rank: int, world: int, dist):
