@@ -207,6 +207,23 @@ int mesh_bitmap(sbmt_ctx* ctx, const sbmt_image* img, const sbmt_params* params,
  * n_lattice_vertices, base's vertex count.  Synchronises once. */
 int mesh_retriangulate(sbmt_ctx* ctx, const sbmt_image* img, sbmt_mesh base, sbmt_mesh* out);
 
+/* A mesh of the caller's own as an explicit mesh handle, e.g. the base mesh
+ * of mesh_retriangulate (Alg. 2 applies to any conforming counter-clockwise
+ * triangulation, Sec. 3.5).  xy: 2 * n_vertices doubles (x, y in pixel
+ * coordinates, pixel (i, j) covering [i - 1/2, i + 1/2] x [j - 1/2, j + 1/2]),
+ * tri: 3 * n_triangles vertex ids; both HOST arrays, copied before the call
+ * returns (the caller keeps ownership).  The handle's labels are 0xFFFF and
+ * its codes 0; mesh_query reports n_cells = n_triangles and
+ * n_lattice_vertices = n_vertices, its other counts 0.  SBMT_EINVAL
+ * (checked on the host before ctx is used): a null array, fewer than 3
+ * vertices or 1 triangle, 2^31 or more vertices or triangle ids, a
+ * coordinate that is not finite or beyond 2^24 px, an id outside
+ * [0, n_vertices) or repeated in a triangle.  Orientation and edge
+ * manifoldness are mesh_retriangulate's checks (SBMT_EINTERNAL).
+ * Synchronises once. */
+int mesh_import(sbmt_ctx* ctx, const double* xy, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,
+                sbmt_mesh* out);
+
 /* Geometric preprocessing of the base mesh (Alg. 3, Steps 1-3): the mesh T
  * that Alg. 3's template retriangulation starts from.  params->mode must be
  * SBMT_PREPROCESS and params->format SBMT_EXPLICIT.  The thresholds a, b, c

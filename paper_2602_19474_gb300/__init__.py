@@ -39,7 +39,7 @@ SBMT_DEBUG_STALL_SCAN = 2
 
 EXPORTS = ("mesh_create", "mesh_bitmap", "mesh_batch", "mesh_autotune", "mesh_tuning", "mesh_set_tuning",
            "mesh_query", "mesh_release", "mesh_destroy", "mesh_stage", "mesh_profile", "mesh_profile_read", "mesh_quality", "mesh_project",
-           "mesh_preprocess", "mesh_preprocess_info", "mesh_retriangulate", "mesh_heat", "mesh_check", "mesh_footprint", "mesh_bound", "server_create",
+           "mesh_preprocess", "mesh_preprocess_info", "mesh_retriangulate", "mesh_import", "mesh_heat", "mesh_check", "mesh_footprint", "mesh_bound", "server_create",
            "server_submit", "server_wait", "server_cancel", "server_release", "server_stats", "server_destroy",
            "sbmt_last_error", "sbmt_server_last_error")
 
@@ -154,6 +154,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_preprocess_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_pre_info)]
     lib.mesh_retriangulate.argtypes = [vp, ctypes.POINTER(sbmt_image), ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mesh_import.argtypes = [vp, vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
     lib.mesh_heat.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(sbmt_heat_params), vp, vp, vp]
     lib.mesh_check.argtypes = [ctypes.POINTER(sbmt_image), ctypes.POINTER(sbmt_params)]
     lib.mesh_footprint.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_size_t)]
@@ -167,7 +168,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.server_release.argtypes = [vp, ctypes.c_uint64]
     lib.server_stats.argtypes = [vp, ctypes.POINTER(sbmt_server_stats)]
     lib.server_destroy.argtypes = [vp]
-    for f in ("mesh_check", "mesh_footprint", "mesh_bound", "mesh_retriangulate", "server_create", "server_submit", "server_wait", "server_cancel",
+    for f in ("mesh_check", "mesh_footprint", "mesh_bound", "mesh_retriangulate", "mesh_import", "server_create", "server_submit", "server_wait", "server_cancel",
               "server_release", "server_stats", "server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     lib.sbmt_server_last_error.restype = ctypes.c_char_p
@@ -264,6 +265,15 @@ def mesh_retriangulate(ctx: int, img, base: int) -> int:
     out = ctypes.c_uint64()
     _check(load().mesh_retriangulate(ctx, ctypes.byref(im), base, ctypes.byref(out)))
     del keep
+    return out.value
+
+
+def mesh_import(ctx: int, xy, tri) -> int:
+    """An explicit mesh handle from host arrays xy (n, 2) and tri (m, 3)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+    out = ctypes.c_uint64()
+    _check(load().mesh_import(ctx, xy.ctypes.data, len(xy), tri.ctypes.data, len(tri), ctypes.byref(out)))
     return out.value
 
 

@@ -221,8 +221,10 @@ SBMT_DEV int r3_uniform(const R3Args& a, const R3Cell& C) {
   const i64 x0 = (i64)ceil(dsb(dsb(C.xlo, 0.5), 1e-6)), x1 = (i64)floor(dad(dad(C.xhi, 0.5), 1e-6));
   const i64 y0 = (i64)ceil(dsb(dsb(C.ylo, 0.5), 1e-6)), y1 = (i64)floor(dad(dad(C.yhi, 0.5), 1e-6));
   const int l0 = r3_px(a, x0, y0);
-  for (i64 y = y0; y <= y1; ++y)
-    for (i64 x = x0; x <= x1; ++x)
+  // every pixel beyond the image reads OUTSIDE, like those of the one-pixel
+  // margin kept: the scan stops there without changing its answer
+  for (i64 y = max(y0, (i64)-1), ye = min(y1, (i64)a.H); y <= ye; ++y)
+    for (i64 x = max(x0, (i64)-1), xe = min(x1, (i64)a.W); x <= xe; ++x)
       if (r3_px(a, x, y) != l0) return -1;
   return l0 == R3_OUTSIDE ? 0xFFFF : l0;
 }

@@ -1564,6 +1564,71 @@ int mesh_retriangulate(sbmt_ctx* ctx, const sbmt_image* img, sbmt_mesh base, sbm
   return rc;
 }
 
+int mesh_import(sbmt_ctx* ctx, const double* xy, int64_t n_vertices, const int32_t* tri, int64_t n_triangles,
+                sbmt_mesh* out) {
+  // the arrays first (host logic only), then the context
+  if (!xy || !tri) return fail(SBMT_EINVAL, "null xy or tri");
+  if (n_vertices < 3 || n_triangles < 1 || n_vertices >= (1ll << 31) || 3 * n_triangles >= (1ll << 31))
+    return fail(SBMT_EINVAL, "mesh of %lld vertices and %lld triangles", (long long)n_vertices,
+                (long long)n_triangles);
+  constexpr double kMaxCoord = 16777216.0;  // 2^24 px: every pixel-line index fits an int
+  for (int64_t i = 0; i < 2 * n_vertices; ++i)
+    if (!(std::fabs(xy[i]) <= kMaxCoord))
+      return fail(SBMT_EINVAL, "vertex %lld: coordinate not finite or beyond 2^24 px", (long long)(i / 2));
+  for (int64_t t = 0; t < n_triangles; ++t) {
+    const int32_t u = tri[3 * t], v = tri[3 * t + 1], w = tri[3 * t + 2];
+    if (u < 0 || v < 0 || w < 0 || u >= n_vertices || v >= n_vertices || w >= n_vertices)
+      return fail(SBMT_EINVAL, "triangle %lld: vertex id out of range", (long long)t);
+    if (u == v || v == w || w == u) return fail(SBMT_EINVAL, "triangle %lld: repeated vertex id", (long long)t);
+  }
+  if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->main.stream;
+  MeshRec* m = new MeshRec();
+  auto bail = [&](int code) {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    destroy_mesh(ctx, m, st);
+    return code;
+  };
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    m->h_info = pinned_slot(ctx);
+  }
+  if (!m->h_info) return bail(fail(SBMT_ENOMEM, "pinned info"));
+  std::memset(m->h_info, 0, 8 * sizeof(u32));
+  const size_t NV = (size_t)n_vertices, NT = (size_t)n_triangles;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_tri = up(16 * NV), off_lab = up(off_tri + 12 * NT), off_code = up(off_lab + 2 * NT);
+  const size_t total = off_code + 2 * NT + 256;
+  if (cudaMallocAsync(&m->out_block, total, st) != cudaSuccess)
+    return bail(fail(SBMT_ENOMEM, "mesh allocation of %zu bytes", total));
+  char* ob = (char*)m->out_block;
+  m->xy = (double*)ob, m->tri = (int*)(ob + off_tri);
+  m->label = (unsigned short*)(ob + off_lab), m->code = (unsigned short*)(ob + off_code);
+  if (cudaMemcpyAsync(m->xy, xy, 16 * NV, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(m->tri, tri, 12 * NT, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(m->label, 0xFF, 2 * NT, st) != cudaSuccess || cudaMemsetAsync(m->code, 0, 2 * NT, st) != cudaSuccess)
+    return bail(fail(SBMT_ECUDA, "mesh upload"));
+  m->bytes = total;
+  m->nv = m->nvg = (int64_t)NV, m->nt = m->ncells = (int64_t)NT;
+  {
+    std::lock_guard<std::mutex> rl(ctx->reg);
+    m->done = pool_event(ctx);
+    m->own_done = true;
+  }
+  if (!m->done) return bail(fail(SBMT_ECUDA, "event create"));
+  CK(cudaEventRecord(m->done, st));
+  // the caller's arrays may be pinned (a truly asynchronous copy): done
+  // with them before returning
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(SBMT_ECUDA, "mesh upload"));
+  std::lock_guard<std::mutex> rl(ctx->reg);
+  m->id = ctx->next++;
+  ctx->meshes[m->id] = m;
+  *out = m->id;
+  return SBMT_OK;
+}
+
 int mesh_preprocess_info(sbmt_ctx* ctx, sbmt_mesh mesh, sbmt_pre_info* out) {
   if (!ctx || !out) return fail(SBMT_EINVAL, "null ctx or out");
   MeshRec* m;

@@ -236,3 +236,26 @@ WORKLOADS = {
     "ellipses2048": (lambda: ellipses(), 4, 1),
     "voronoi8192": (lambda: voronoi_labels(), 2, 1),
 }
+
+
+def delaunay_mesh(width: int, height: int, n: int = 900, seed_k: int = 7, spacing: float = 2.0):
+    """A conforming counter-clockwise triangle mesh of the image rectangle
+    [-1/2, W - 1/2] x [-1/2, H - 1/2] that is no lattice: the Delaunay
+    triangulation of the rectangle's corners, points every `spacing` px along
+    its sides (edges lying on the border's pixel lines) and n seeded points.
+    Returns (xy (m, 2) float64, tri (t, 3) int32)."""
+    from scipy.spatial import Delaunay
+
+    rng = rng_for(seed_k)
+    sx = np.arange(-0.5 + spacing, width - 0.5, spacing)
+    sy = np.arange(-0.5 + spacing, height - 0.5, spacing)
+    pts = np.concatenate([
+        [[-0.5, -0.5], [width - 0.5, -0.5], [width - 0.5, height - 0.5], [-0.5, height - 0.5]],
+        np.stack([sx, np.full_like(sx, -0.5)], 1), np.stack([sx, np.full_like(sx, height - 0.5)], 1),
+        np.stack([np.full_like(sy, -0.5), sy], 1), np.stack([np.full_like(sy, width - 0.5), sy], 1),
+        rng.uniform([-0.5, -0.5], [width - 0.5, height - 0.5], (n, 2))])
+    tri = Delaunay(pts).simplices.astype(np.int32)
+    P = pts[tri]
+    o = (P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0])
+    tri[o < 0] = tri[o < 0][:, [0, 2, 1]]
+    return pts, np.ascontiguousarray(tri)

@@ -96,3 +96,26 @@ def test_requests_are_checked_without_a_device(lib):
     # the pre-count reservation grows with the image and shrinks with h
     assert sb.mesh_bound(np.zeros((100, 100), np.uint8), 2) < sb.mesh_bound(np.zeros((200, 200), np.uint8), 2)
     assert sb.mesh_bound(np.zeros((100, 100), np.uint8), 8) < sb.mesh_bound(np.zeros((100, 100), np.uint8), 2)
+
+
+def test_mesh_import_checks_the_arrays_before_the_context(lib):
+    """mesh_import's array checks are host logic: each bad mesh is refused
+    with its own reason before the (null) context is looked at."""
+    def call(xy, tri, nv=None, nt=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        rc = lib.mesh_import(None, xy.ctypes.data, len(xy) if nv is None else nv, tri.ctypes.data,
+                             len(tri) if nt is None else nt, None)
+        return rc, lib.sbmt_last_error().decode()
+
+    xy = [[0.0, 0.0], [2.0, 0.0], [0.0, 2.0]]
+    assert call(xy, [[0, 1, 2]]) == (sb.SBMT_EINVAL, "null ctx or out")
+    assert "vertex id out of range" in call(xy, [[0, 1, 3]])[1]
+    assert "vertex id out of range" in call(xy, [[0, -1, 2]])[1]
+    assert "repeated vertex id" in call(xy, [[0, 1, 1]])[1]
+    assert "coordinate" in call([[0.0, 0.0], [np.nan, 0.0], [0.0, 2.0]], [[0, 1, 2]])[1]
+    assert "coordinate" in call([[0.0, 0.0], [2.0, np.inf], [0.0, 2.0]], [[0, 1, 2]])[1]
+    assert "coordinate" in call([[0.0, 0.0], [2.0 ** 25, 0.0], [0.0, 2.0]], [[0, 1, 2]])[1]
+    assert "mesh of" in call(xy[:2], [[0, 1, 2]], nv=2)[1]
+    assert "mesh of" in call(xy, [[0, 1, 2]], nt=0)[1]
+    assert lib.mesh_import(None, None, 3, None, 1, None) == sb.SBMT_EINVAL

@@ -242,3 +242,70 @@ def test_degenerate_origin_refused_where_not_meshed():
     with pytest.raises(sb.SbmtError) as e:
         sb.mesh_preprocess(c, img, 2, 1, 0.26, 0.125, 0.183, -1, -1)
     assert e.value.code == sb.SBMT_EINVAL
+
+
+def _imported(img, xy, tri):
+    """mesh_retriangulate on the caller's own mesh (mesh_import)."""
+    c = ctx()
+    b = sb.mesh_import(c, xy, tri)
+    r = sb.mesh_retriangulate(c, img, b)
+    v = sb.mesh_query(c, r, -1)
+    g = sb.view_numpy(v)
+    g.update(n_cut=v.n_cut_cells, n_tierG=v.n_tierG_cells, n_events=v.n_events, n_inside=v.n_inside_vertices,
+             n_base=v.n_lattice_vertices, n_cells=v.n_cells, n_tierG_triangles=v.n_tierG_triangles)
+    base = sb.view_numpy(sb.mesh_query(c, b, -1))
+    assert np.array_equal(base["xy"], np.asarray(xy, np.float64)) and np.array_equal(base["tri"], np.asarray(tri))
+    sb.mesh_release(c, r)
+    sb.mesh_release(c, b)
+    return g
+
+
+def _quadrant(n, x0, y0):
+    img = np.zeros((n, n), np.uint8)
+    img[y0:, x0:] = 1
+    return img
+
+
+def _wedge():
+    img = np.zeros((6, 7), np.uint8)
+    img[1:3, 3:] = 1
+    return img
+
+
+def _overlap():
+    img = np.zeros((6, 6), np.uint8)
+    img[2:, :3] = 1
+    return img
+
+
+# single cells of App. G's cases that only Alg. 1's degenerate incidences
+# reach (vertex on a segment, overlap, endpoint on an edge), the oracle's
+# pins of the same cells stating the expected patches
+APP_G_CELLS = [
+    ("22_a1", lambda: _quadrant(8, 3, 2), [[4.5, 1.5], [2.5, 3.5], [1.0, 0.0]]),
+    ("12_a1", lambda: _quadrant(8, 3, 2), [[1.0, 0.5], [4.0, 0.0], [2.5, 3.5]]),
+    ("13", _wedge, [[4.0, 0.75], [2.5, 2.5], [1.0, 0.25]]),
+    ("23_c1", lambda: _quadrant(6, 2, 2), [[1.5, 1.5], [4.2, 1.1], [2.3, 4.1]]),
+    ("overlap", _overlap, [[0.5, 1.5], [4.5, 1.5], [3.2, 4.0]]),
+    ("glancing", lambda: _quadrant(6, 2, 2), [[1.5, 1.5], [0.3, 0.4], [1.4, 0.3]]),
+]
+
+
+@pytest.mark.parametrize("name,make,xy", APP_G_CELLS, ids=[c[0] for c in APP_G_CELLS])
+def test_app_g_degenerate_cells_match_the_oracle(name, make, xy):
+    img = np.ascontiguousarray(make())
+    tri = np.array([[0, 1, 2]], np.int32)
+    g = _imported(img, np.array(xy), tri)
+    assert_same(g, oracle.region3(img, np.array(xy, np.float64), tri))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_retriangulate_a_delaunay_mesh(seed):
+    """Alg. 2 on a mesh that is no lattice and was never preprocessed: every
+    cell classified and retriangulated as the oracle does, bit for bit."""
+    img = np.ascontiguousarray(synth.voronoi_labels(size=64, nseeds=7))
+    xy, tri = synth.delaunay_mesh(64, 64, 900, seed)
+    g = _imported(img, xy, tri)
+    o = oracle.region3(img, xy, tri)
+    assert_same(g, o)
+    assert o["n_cut_cells"] > 100 and o["n_events"] > 100

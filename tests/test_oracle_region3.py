@@ -267,3 +267,64 @@ def test_general_path_at_an_integer_origin_is_the_plain_mesh():
     g = oracle.mesh_general(img, 2, 1, 2, -4)
     assert np.abs(g["xy"][g["tri"]] - o["xy"][o["tri"]]).max() <= 1e-9
     assert np.array_equal(g["label"], o["label"]) and np.array_equal(g["code"], o["code"])
+
+
+def _cell(img, xy):
+    return oracle.region3(np.ascontiguousarray(img), np.array(xy, dtype=np.float64), np.array([[0, 1, 2]]))
+
+
+def test_app_g_case_22_a1_star_from_the_inside_vertex():
+    """App. G (2,2) case (a1): the inside vertex P2 with two boundary segments
+    leaving it through two corners (each a vertex on the segment, counted twice
+    by Alg. 1): the patch is the star from P2 over A, B, C, and the class is
+    (2,2)."""
+    img = _quadrant(8, 3, 2)  # boundary turns at (2.5, 1.5), runs +x and +y
+    R = _cell(img, [[4.5, 1.5], [2.5, 3.5], [1.0, 0.0]])  # A, B on the two runs
+    assert R["n_events"] == 0 and R["n_inside"] == 1 and np.array_equal(R["xy"][3], [2.5, 1.5])
+    assert sorted(map(tuple, R["tri"].tolist())) == [(0, 1, 3), (0, 3, 2), (1, 2, 3)]  # A B P2, C A P2, B C P2
+    code = int(R["code"][0])
+    assert (code & 15) == 1 | 2 | 4 | 8 and code >> 12 == 6  # mask, class (2,2)
+
+
+def test_app_g_case_12_a1_star_with_an_event():
+    """App. G (1,2) case (a1): P2 inside, one segment leaving through Q on BC
+    (one intersection), the other through corner C (two): the star from P2 over
+    A, B, Q, C; class (1,2)."""
+    img = _quadrant(8, 3, 2)
+    R = _cell(img, [[1.0, 0.5], [4.0, 0.0], [2.5, 3.5]])  # C on the vertical run
+    qx = 4.0 + ((1.5 - 0.0) * (2.5 - 4.0)) / (3.5 - 0.0)  # from the lower-id end B
+    assert R["n_events"] == 1 and np.array_equal(R["xy"][3], [qx, 1.5]) and np.array_equal(R["xy"][4], [2.5, 1.5])
+    A, B, C, Q, P = 0, 1, 2, 3, 4
+    assert sorted(map(tuple, R["tri"].tolist())) == [(A, B, P), (A, P, C), (B, Q, P), (C, P, Q)]
+    code = int(R["code"][0])
+    assert (code & 15) == 1 | 4 | 8 and code >> 12 == 5  # class (1,2)
+
+
+def test_app_g_case_13_vertex_to_an_endpoint_on_the_opposite_edge():
+    """App. G's (1,3) case: a segment from corner B (a vertex on the segment)
+    to the PSLG vertex P2 on edge CA (an endpoint on the edge), where a second
+    segment only touches the cell: triangles A B P2 and P2 B C.  The class
+    counts the pieces inside the cell (reading): the touching segment has none,
+    so the cell reports (0,3) where the paper, counting every segment meeting
+    the cell, names (1,3)."""
+    img = np.zeros((6, 7), np.uint8)
+    img[1:3, 3:] = 1  # left side x = 2.5 for y in [0.5, 2.5], turning at both ends
+    R = _cell(img, [[4.0, 0.75], [2.5, 2.5], [1.0, 0.25]])  # CA passes through (2.5, 0.5)
+    assert R["n_events"] == 1 and np.array_equal(R["xy"][3], [2.5, 0.5])
+    A, B, C, P2 = 0, 1, 2, 3
+    assert sorted(map(tuple, R["tri"].tolist())) == [(A, B, P2), (B, C, P2)]
+    code = int(R["code"][0])
+    assert (code & 15) == 2 | 4 | 8 and code >> 12 == 3  # class (0,3)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_embedding_into_a_delaunay_mesh(seed):
+    """Alg. 2 applies to any conforming mesh (Sec. 3.5): on a Delaunay mesh
+    of random points, never preprocessed, the boundary is embedded with the
+    same invariants (areas per label, label changes on pixel lines, boundary
+    length)."""
+    img = np.ascontiguousarray(synth.voronoi_labels(size=64, nseeds=7))
+    xy, tri = synth.delaunay_mesh(64, 64, 900, seed)
+    R = oracle.region3(img, xy, tri)
+    check_embedded(img, {"xy": xy, "tri": tri}, R)
+    assert R["n_cut_cells"] > 100 and R["n_events"] > 100
