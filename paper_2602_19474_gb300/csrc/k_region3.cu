@@ -213,13 +213,24 @@ SBMT_DEV R3Cell r3_load(const R3Args& a, u32 c) {
   return C;
 }
 
-// one label over the pixels touching the cell's bounding box (the box grown
-// by 1e-6 px for the rounding of its ends): no boundary pixel edge meets the
-// cell, and every pixel the cell covers has that label (returned, OUTSIDE
-// as 0xFFFF), or -1
-SBMT_DEV int r3_uniform(const R3Args& a, const R3Cell& C) {
-  const i64 x0 = (i64)ceil(dsb(dsb(C.xlo, 0.5), 1e-6)), x1 = (i64)floor(dad(dad(C.xhi, 0.5), 1e-6));
-  const i64 y0 = (i64)ceil(dsb(dsb(C.ylo, 0.5), 1e-6)), y1 = (i64)floor(dad(dad(C.yhi, 0.5), 1e-6));
+// one label over the pixels touching the cell's bounding box: no boundary
+// pixel edge meets the cell, and every pixel the cell covers has that label
+// (returned, OUTSIDE as 0xFFFF), or -1.  The box is the double-precision one
+// grown by 1e-6 px, or any box holding it: a larger box finds a cell of one
+// label at most where the exact one does, and a cell it misses becomes a
+// candidate with no event and no inside vertex, emitted as it is with the
+// label of the pixel holding its centroid, a pixel of the exact box -- the
+// same output.  Here the box comes from single precision: each coordinate
+// converted rounding down (lower ends) or up (upper ends), the ends moved by
+// 2e-6 px more, the arithmetic rounded outwards, so that it holds the exact
+// box at every magnitude.
+SBMT_DEV int r3_uniform(const R3Args& a, const double2* K) {
+  const float xlo = fminf(fminf(__double2float_rd(K[0].x), __double2float_rd(K[1].x)), __double2float_rd(K[2].x));
+  const float ylo = fminf(fminf(__double2float_rd(K[0].y), __double2float_rd(K[1].y)), __double2float_rd(K[2].y));
+  const float xhi = fmaxf(fmaxf(__double2float_ru(K[0].x), __double2float_ru(K[1].x)), __double2float_ru(K[2].x));
+  const float yhi = fmaxf(fmaxf(__double2float_ru(K[0].y), __double2float_ru(K[1].y)), __double2float_ru(K[2].y));
+  const i64 x0 = (i64)ceilf(__fsub_rd(__fsub_rd(xlo, 0.5f), 2e-6f)), x1 = (i64)floorf(__fadd_ru(__fadd_ru(xhi, 0.5f), 2e-6f));
+  const i64 y0 = (i64)ceilf(__fsub_rd(__fsub_rd(ylo, 0.5f), 2e-6f)), y1 = (i64)floorf(__fadd_ru(__fadd_ru(yhi, 0.5f), 2e-6f));
   const int l0 = r3_px(a, x0, y0);
   // every pixel beyond the image reads OUTSIDE, like those of the one-pixel
   // margin kept: the scan stops there without changing its answer
@@ -227,6 +238,28 @@ SBMT_DEV int r3_uniform(const R3Args& a, const R3Cell& C) {
     for (i64 x = max(x0, (i64)-1), xe = min(x1, (i64)a.W); x <= xe; ++x)
       if (r3_px(a, x, y) != l0) return -1;
   return l0 == R3_OUTSIDE ? 0xFFFF : l0;
+}
+
+// counter-clockwise (a positive orientation of the doubles), with a
+// single-precision filter: the corners rounded to float are within 2^-24 E
+// of the doubles (E: the largest coordinate magnitude), so the float
+// orientation of the rounded corners is within 16 2^-24 (E D + D^2) of the
+// exact orientation (D: the largest coordinate difference), and the double
+// formula within 2^-50 D^2 of it; above that bound the float sign decides,
+// below it the double formula
+SBMT_DEV bool r3_ccw(const double2* K) {
+  const float2 p = make_float2(__double2float_rn(K[0].x), __double2float_rn(K[0].y));
+  const float2 q = make_float2(__double2float_rn(K[1].x), __double2float_rn(K[1].y));
+  const float2 r = make_float2(__double2float_rn(K[2].x), __double2float_rn(K[2].y));
+  const float ax = __fsub_rn(q.x, p.x), ay = __fsub_rn(q.y, p.y), bx = __fsub_rn(r.x, p.x), by = __fsub_rn(r.y, p.y);
+  const float o = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+  const float E = fmaxf(fmaxf(fmaxf(fabsf(p.x), fabsf(p.y)), fmaxf(fabsf(q.x), fabsf(q.y))), fmaxf(fabsf(r.x), fabsf(r.y)));
+  const float D = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fmaxf(fabsf(bx), fabsf(by)), fabsf(__fsub_rn(r.x, q.x))));
+  const float Dy = fmaxf(D, fabsf(__fsub_rn(r.y, q.y))) + 1e-30f;
+  const float T = 32.0f * 5.9604645e-8f * (E * Dy + Dy * Dy);  // twice the bound, rounding included
+  if (o > T) return true;
+  if (o < -T) return false;
+  return r3_orient(K[0], K[1], K[2]) > 0.0;
 }
 
 // the boundary vertices strictly inside the cell, as corner ids y (W+1) + x
@@ -314,10 +347,12 @@ __global__ void __launch_bounds__(256) k_r3_screen(R3Args a) {
     const u64 c = c0 + threadIdx.x;
     bool cand = false;
     if (c < a.nt) {
-      const R3Cell C = r3_load(a, (u32)c);
+      const int* t = a.ttri + 3 * c;
+      double2 K[3];
+      for (int q = 0; q < 3; ++q) K[q] = reinterpret_cast<const double2*>(a.txy)[t[q]];
       int l = -1;
-      if (!(r3_orient(C.K[0], C.K[1], C.K[2]) > 0.0)) atomicOr(a.err, R3_GEOMETRY);
-      else l = r3_uniform(a, C);
+      if (!r3_ccw(K)) atomicOr(a.err, R3_GEOMETRY);
+      else l = r3_uniform(a, K);
       cand = l < 0;
       a.ntri[c] = 1, a.nown[c] = 0, a.nin[c] = 0, a.own3[c] = 0;
       a.ulab[c] = (unsigned short)(cand ? 0 : l);
@@ -358,7 +393,13 @@ __global__ void __launch_bounds__(128) k_r3_count(R3Args a) {
     } else if (ni < 0) {
       atomicOr(a.err, R3_GEOMETRY);
     } else if (ne + ni > 0) {
-      atomicAdd(a.ncut, 1u);
+      // the cut cells' list for the emission, one atomic per group of lanes
+      const unsigned act = __activemask();
+      const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
+      u32 base = 0;
+      if (lane == lead) base = atomicAdd(a.ncut, (u32)__popc(act));
+      base = __shfl_sync(act, base, lead);
+      a.cutl[base + __popc(act & ((1u << lane) - 1u))] = c;
       u32 nown = 0, own3 = 0;
       for (int j = 0; j < 3; ++j) {
         if (cnt[j] == 0) continue;
@@ -649,13 +690,16 @@ SBMT_DEV void r3_filt_init(const R3Local& L, R3Filt& F) {
   }
   F.T = 80.0f * 5.9604645e-8f * M * M * 1.0001f;  // 80 2^-24 M^2, rounded up
 }
+__device__ __noinline__ int r3_osgn_exact(const R3Local& L, int p, int q, int r) {
+  return r3_sgn(r3_orient(L.v[p], L.v[q], L.v[r]));
+}
 SBMT_DEV int r3_osgn(const R3Local& L, const R3Filt& F, int p, int q, int r) {
   const float2 a = F.l[p], b = F.l[q], c = F.l[r];
   const float o = __fsub_rn(__fmul_rn(__fsub_rn(b.x, a.x), __fsub_rn(c.y, a.y)),
                             __fmul_rn(__fsub_rn(b.y, a.y), __fsub_rn(c.x, a.x)));
   if (o > F.T) return 1;
   if (o < -F.T) return -1;
-  return r3_sgn(r3_orient(L.v[p], L.v[q], L.v[r]));
+  return r3_osgn_exact(L, p, q, r);  // within the filter's bound: the double formula
 }
 
 SBMT_DEV int r3_greedy_small(const R3Local& L, int* face) {
@@ -743,25 +787,37 @@ SBMT_DEV int r3_greedy_small(const R3Local& L, int* face) {
 }
 
 // ---------------------------------------------------------------------------
-// uncut cells of one label: the cell as it is, labelled by its pixel box
+// the cells left as they are: uncut cells of one label, labelled by their
+// pixel box, and candidates the boundary only touches (at a corner or along
+// an edge), labelled by the pixel holding the centroid
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_r3_emit_uncut(R3Args a) {
   for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < a.nt; c += (u64)gridDim.x * blockDim.x) {
     const u32 t0 = a.toff[c];
     if (a.toff[c + 1] - t0 != 1) continue;
     const int* t = a.ttri + 3 * c;
-    if ((a.cmark[c >> 5] >> (c & 31)) & 1u) continue;  // a candidate: k_r3_emit's
-    reinterpret_cast<int3*>(a.tri)[t0] = make_int3(t[0], t[1], t[2]);
-    a.label[t0] = a.ulab[c];
+    const int3 tv = make_int3(t[0], t[1], t[2]);
+    unsigned short lab;
+    if ((a.cmark[c >> 5] >> (c & 31)) & 1u) {
+      const double2* K = reinterpret_cast<const double2*>(a.txy);
+      lab = r3_label(a, K[tv.x], K[tv.y], K[tv.z]);
+    } else {
+      lab = a.ulab[c];
+    }
+    reinterpret_cast<int3*>(a.tri)[t0] = tv;
+    a.label[t0] = lab;
     a.code[t0] = 0;
   }
 }
 
 // ---------------------------------------------------------------------------
-// the candidates: cells touched only at a corner stay; Tier-T cells take
-// their template; small Tier-G cells the greedy rule here, larger ones are
-// queued for the warp kernel
+// the cut cells (k_r3_count's list): Tier-T cells take their template;
+// Tier-G cells are queued (those over R3_SMALL nodes
+// flagged) for the greedy kernels, so that this kernel's warps stay on the
+// short template path and the greedy runs in warps of Tier-G cells only
 // ---------------------------------------------------------------------------
+constexpr u32 R3_BIG = 0x80000000u;  // a queued cell over R3_SMALL nodes (cell ids stay below 2^31)
+
 struct R3EvBuf {
   R3Ev e[3][R3_MAXE];
   SBMT_DEV R3Ev* operator[](int j) { return e[j]; }
@@ -770,18 +826,12 @@ struct R3EvBuf {
 __global__ void __launch_bounds__(128) k_r3_emit(R3Args a) {
   R3EvBuf ev;
   R3Local L;
-  const u32 n = *a.ncand;
+  const u32 n = *a.ncut;
   for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const u32 c = a.cand[q];
+    const u32 c = a.cutl[q];
     const R3Cell C = r3_load(a, c);
     const u32 t0 = a.toff[c];
     int3* tri = reinterpret_cast<int3*>(a.tri);
-    if (a.toff[c + 1] - t0 == 1) {  // touches only: the cell stays
-      tri[t0] = make_int3(C.id[0], C.id[1], C.id[2]);
-      a.label[t0] = r3_label(a, C.K[0], C.K[1], C.K[2]);
-      a.code[t0] = 0;
-      continue;
-    }
     const u32 e = r3_build(a, c, C, L, ev, true);
     if (e) {
       atomicOr(a.err, e);
@@ -799,25 +849,13 @@ __global__ void __launch_bounds__(128) k_r3_emit(R3Args a) {
       continue;
     }
     if (key == 0) {
-      if (L.n > R3_SMALL) {
-        a.glist[atomicAdd(a.ng, 1u)] = c;
-        continue;
-      }
-      int face[2 * R3_SMALL];
-      const int nf = r3_greedy_small(L, face);
-      if (nf != nt) {
-        atomicOr(a.err, nf < 0 ? R3_CAPACITY : R3_COUNT);
-        continue;
-      }
-      const unsigned short code = (unsigned short)((L.mask & 15) | (63 << 6) | (L.klass << 12));
-      atomicAdd(a.ngtri, (u32)nf);
-      atomicAdd(a.ngsmall, 1u);
-      for (int i = 0; i < nf; ++i) {
-        const int f = face[i], p = f >> 12, r2 = (f >> 6) & 63, s2 = f & 63;
-        tri[t0 + i] = make_int3((int)L.gid[p], (int)L.gid[r2], (int)L.gid[s2]);
-        a.label[t0 + i] = r3_label(a, L.v[p], L.v[r2], L.v[s2]);
-        a.code[t0 + i] = code;
-      }
+      // one queue slot per lane, one atomic per group of lanes here
+      const unsigned act = __activemask();
+      const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
+      u32 base = 0;
+      if (lane == lead) base = atomicAdd(a.ng, (u32)__popc(act));
+      base = __shfl_sync(act, base, lead);
+      a.glist[base + __popc(act & ((1u << lane) - 1u))] = c | (L.n > R3_SMALL ? R3_BIG : 0u);
       continue;
     }
     const unsigned long long w = g_keys.tris[(key - 1) * 3 + sigma];
@@ -832,6 +870,44 @@ __global__ void __launch_bounds__(128) k_r3_emit(R3Args a) {
       tri[t0 + k] = make_int3((int)L.gid[q3[0]], (int)L.gid[q3[1]], (int)L.gid[q3[2]]);
       a.label[t0 + k] = r3_label(a, L.v[q3[0]], L.v[q3[1]], L.v[q3[2]]);
       a.code[t0 + k] = code;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tier-G cells of at most R3_SMALL nodes: one thread per queued cell, the
+// local graph rebuilt (the event and inside-vertex coordinates are written
+// by k_r3_emit), the greedy rule, the faces written in sorted order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_r3_gsmall(R3Args a) {
+  R3EvBuf ev;
+  R3Local L;
+  const u32 n = *a.ng;
+  for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const u32 c = a.glist[q];
+    if (c & R3_BIG) continue;
+    const R3Cell C = r3_load(a, c);
+    const u32 e = r3_build(a, c, C, L, ev, false);
+    if (e) {
+      atomicOr(a.err, e);
+      continue;
+    }
+    const u32 t0 = a.toff[c];
+    int face[2 * R3_SMALL];
+    const int nf = r3_greedy_small(L, face);
+    if (nf != (int)(a.toff[c + 1] - t0)) {
+      atomicOr(a.err, nf < 0 ? R3_CAPACITY : R3_COUNT);
+      continue;
+    }
+    const unsigned short code = (unsigned short)((L.mask & 15) | (63 << 6) | (L.klass << 12));
+    atomicAdd(a.ngtri, (u32)nf);
+    atomicAdd(a.ngsmall, 1u);
+    int3* tri = reinterpret_cast<int3*>(a.tri);
+    for (int i = 0; i < nf; ++i) {
+      const int f = face[i], p = f >> 12, r2 = (f >> 6) & 63, s2 = f & 63;
+      tri[t0 + i] = make_int3((int)L.gid[p], (int)L.gid[r2], (int)L.gid[s2]);
+      a.label[t0 + i] = r3_label(a, L.v[p], L.v[r2], L.v[s2]);
+      a.code[t0 + i] = code;
     }
   }
 }
@@ -869,7 +945,8 @@ __global__ void __launch_bounds__(32 * R3G_WARPS) k_r3_tierg(R3Args a) {
   R3GShared& S = sh[wid];
   const u32 ng = *a.ng;
   for (u32 g = blockIdx.x * R3G_WARPS + wid; g < ng; g += gridDim.x * R3G_WARPS) {
-    const u32 c = a.glist[g];
+    const u32 c = a.glist[g] & ~R3_BIG;
+    if (!(a.glist[g] & R3_BIG)) continue;  // k_r3_gsmall's (the whole warp reads one entry)
     if (lane == 0) {
       const R3Cell C = r3_load(a, c);
       R3SharedEv ev{S.ev};
@@ -1041,8 +1118,9 @@ int launch_r3_emit(const R3Args& a, cudaStream_t st) {
   const unsigned g = (unsigned)std::min<u64>((a.nt + 255) / 256, 152 * 16);
   k_r3_emit_uncut<<<std::max(g, 1u), 256, 0, st>>>(a);
   k_r3_emit<<<152 * 16, 128, 0, st>>>(a);
+  k_r3_gsmall<<<152 * 16, 128, 0, st>>>(a);
   k_r3_tierg<<<152 * 8, 32 * R3G_WARPS, 0, st>>>(a);
-  return 3;
+  return 4;
 }
 
 }  // namespace sbmt

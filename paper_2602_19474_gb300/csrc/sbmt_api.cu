@@ -1366,7 +1366,8 @@ int r3_one(sbmt_ctx* ctx, Lane* lane, const unsigned char* dimg, i64 pitch, int 
       (rc = aalloc(lane, &a.own3, nt)) || (rc = aalloc(lane, &a.toff, nt + 1)) || (rc = aalloc(lane, &a.eoff, nt + 1)) ||
       (rc = aalloc(lane, &a.ioff, nt + 1)) || (rc = aalloc(lane, &a.glist, nt)) || (rc = aalloc(lane, &cnt, 8)) ||
       (rc = aalloc(lane, &scr, scr_words)) || (rc = aalloc(lane, &a.ulab, nt)) ||
-      (rc = aalloc(lane, &a.cmark, (nt + 31) / 32)) || (rc = aalloc(lane, &a.cand, nt)))
+      (rc = aalloc(lane, &a.cmark, (nt + 31) / 32)) || (rc = aalloc(lane, &a.cand, nt)) ||
+      (rc = aalloc(lane, &a.cutl, nt)))
     return bail(rc);
   a.err = cnt, a.ncut = cnt + 1, a.ng = cnt + 2, a.ngtri = cnt + 3, a.ncand = cnt + 4, a.ngsmall = cnt + 5;
   CK(cudaMemsetAsync(a.deg, 0, sizeof(u32) * (size_t)nv, st));
@@ -1782,9 +1783,9 @@ int mesh_query(sbmt_ctx* ctx, sbmt_mesh mesh, int wait_ms, sbmt_mesh_view* out) 
   std::memset(out, 0, sizeof *out);
   out->n_vertices = m->nv, out->n_triangles = m->nt, out->n_cells = m->ncells;
   if (m->r3) {
-    // h_info: error bits, cut cells, queued Tier-G cells, Tier-G triangles,
-    // candidates, Tier-G cells done by one thread
-    out->n_cut_cells = m->h_info[1], out->n_tierG_cells = (int64_t)m->h_info[2] + m->h_info[5];
+    // h_info: error bits, cut cells, Tier-G cells (all queued), Tier-G
+    // triangles, candidates, Tier-G cells done by one thread
+    out->n_cut_cells = m->h_info[1], out->n_tierG_cells = m->h_info[2];
     out->n_tierG_triangles = m->h_info[3];
     out->n_events = m->ne_total, out->n_inside_vertices = m->nc_total, out->n_lattice_vertices = m->nvg;
     out->xy = m->xy, out->tri = m->tri, out->label = m->label, out->code = m->code;

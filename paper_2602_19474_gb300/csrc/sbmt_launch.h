@@ -300,11 +300,12 @@ struct R3Args {
   double* xy;
   int* tri;
   unsigned short *label, *code;
-  u32 *glist, *ng, *err, *ncut, *ngtri;
+  u32 *glist, *ng, *err, *ncut, *ngtri;  // glist: the Tier-G cells (bit 31: over 12 nodes), ng of them
   unsigned short* ulab;  // per cell: the label of an uncut cell's pixel box
   u32* cmark;            // candidate bit-plane, (nt + 31) / 32 words
   u32 *cand, *ncand;     // the candidates (nt entries) and their count
   u32* ngsmall;          // Tier-G cells done by one thread
+  u32* cutl;             // the cut cells (nt entries), ncut of them
 };
 int launch_r3_adjacency(const R3Args& a, u32* scr, cudaStream_t st);
 int launch_r3_count(const R3Args& a, cudaStream_t st);
