@@ -117,9 +117,356 @@ SBMT_DEV bool r3_corner_event(const R3Args& a, i64 cx, i64 cy, bool hz, bool vt)
   return m != 0;
 }
 
-// events of the edge from P (its lower-id end) to Q, in order from P; the
-// count, or -1 past R3_MAXE
-SBMT_DEV int r3_edge_events(const R3Args& a, double2 P, double2 Q, R3Ev* ev) {
+// ---------------------------------------------------------------------------
+// single-precision filters for the positions on pixel lines.  The double
+// formulas above are the definition (the oracle's arithmetic); a float
+// computation decides where a proven bound allows, the double formula
+// where it does not, so that every decision is the double formula's.
+// ---------------------------------------------------------------------------
+// This GPU converts from double to float, from 64-bit integers to double
+// and from float to 64-bit integers at about the rate of its FP64
+// arithmetic (a few per clock per SM, against about a hundred for float
+// arithmetic and for integer to float conversions), so the filters take
+// doubles apart with integer instructions.
+//
+// v (|v| <= 2^24) as a 64-bit fixed-point number with 36 fraction bits:
+// floor(v 2^36), exactly, and whether v 2^36 was not an integer (*inexact)
+SBMT_DEV i64 r3_fix36(double v, bool* inexact) {
+  const u64 b = (u64)__double_as_longlong(v);
+  const bool neg = (b >> 63) != 0;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const u64 frac = b & 0xFFFFFFFFFFFFFull;
+  i64 f;
+  bool lost;
+  if (e == 0) {
+    lost = frac != 0;  // zero, or a denormal (below one unit)
+    f = (neg && lost) ? 1 : 0;
+  } else {
+    const i64 m = (i64)(frac | (1ull << 52));
+    const int sh = e - 1039;  // v = m 2^(e - 1075), so v 2^36 = m 2^(e - 1039); sh <= 8 up to 2^24
+    if (sh >= 0) {
+      f = m << sh, lost = false;
+    } else if (sh > -63) {
+      lost = (m & ((1ll << -sh) - 1)) != 0;
+      f = (m >> -sh) + ((neg && lost) ? 1 : 0);  // magnitude rounded towards the floor
+    } else {
+      f = neg ? 1 : 0, lost = true;
+    }
+  }
+  *inexact = lost;
+  return neg ? -f : f;
+}
+// the float of an integer |n| < 2^22, exactly: n in the mantissa of 1.5 2^23 + n
+SBMT_DEV float r3_i2f(int n) { return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f); }
+// the nearest integer to a float |z| < 2^22, and the floor
+SBMT_DEV int r3_fint(float z) { return __float_as_int(__fadd_rn(z, 12582912.0f)) - 0x4B400000; }
+SBMT_DEV int r3_ffloor(float z) {
+  const int n = r3_fint(z);
+  return r3_i2f(n) > z ? n - 1 : n;
+}
+// A coordinate v as an integer i = floor(v) and f: the remainder v - i (in
+// [0, 1), exact in double) truncated to a multiple of 2^-23, so that
+// v - i - 2^-23 - 2^-36 < f <= v - i.
+struct R3Split {
+  i64 i, fx;
+  float f;
+  bool inexact;
+};
+SBMT_DEV R3Split r3_split(double v) {
+  R3Split s;
+  s.fx = r3_fix36(v, &s.inexact);
+  s.i = s.fx >> 36;
+  const int n23 = (int)((s.fx & ((1ll << 36) - 1)) >> 13);
+  s.f = __fmul_rn(__fsub_rn(__int_as_float(0x4B000000 | n23), 8388608.0f), 1.1920928955078125e-7f);  // n23 2^-23
+  return s;
+}
+// v against the pixel line k - 1/2, exactly, from fx = floor(v 2^36):
+// below iff fx < (k - 1/2) 2^36; above iff fx is greater, or equal with
+// bits dropped
+SBMT_DEV i64 r3_line36(i64 k) { return (k << 36) - (1ll << 35); }
+SBMT_DEV bool r3_lt(const R3Split& v, i64 k) { return v.fx < r3_line36(k); }
+SBMT_DEV bool r3_gt(const R3Split& v, i64 k) {
+  const i64 t = r3_line36(k);
+  return v.fx > t || (v.fx == t && v.inexact);
+}
+// the float of a coordinate difference from the fixed-point values (within
+// 2^-35 + 2^-24 |d| of the double difference's real value; integer to
+// float conversions run at the float rate)
+SBMT_DEV float r3_fdiff(const R3Split& q, const R3Split& p) {
+  return __fmul_rn((float)(q.fx - p.fx), 1.4551915228366852e-11f);
+}
+
+// The crossing of the edge from P (its lower-id end) with the line at
+// coordinate c0 = k - 1/2 across it, as w = (position along the line) - B,
+// B the integer part of P's coordinate along the line.  With A = c0 - P (in
+// the crossing direction: k - 1/2 - Pi - Pr, the integer part exact) and
+// s = the edge's slope in float, w = Pr + A s.  The remainders are within
+// 2^-22 of their values, the differences within 2^-35 + 2^-23 |d|, the
+// slope within 5 2^-24 |s| relatively, so the float w is within
+// 2^-24 (8 + 8|s| + 7 D + |w|) of the real w of the double inputs (D: the
+// edge's larger extent; |A| is below the extent across the line, |A s|
+// below the extent along it), and the double formula within
+// 2^-53 (|position| + 3 D) of that real value; T (below) is above their
+// sum at every coordinate up to 2^24.
+SBMT_DEV float r3_cross_tol(float D, float s, float w) {
+  return 6.0e-7f * (D + fabsf(s) + 2.0f * fabsf(w) + 3.0f) + 1.5e-8f;
+}
+// the double formula's crossing with the line c0 (vert: x = c0, giving y):
+// its pixel edge or corner index in *j, *corner set
+__device__ __noinline__ void r3_cross_exact(double2 P, double2 Q, double c0, bool vert, i64* j, bool* corner) {
+  *corner = r3_at_corner(vert ? r3_vy(P, Q, c0) : r3_hx(P, Q, c0), j);
+}
+
+// the number of events of the edge from P (its lower-id end) to Q, or -1
+// past R3_MAXE, through the filters (the count pass's form: positions are
+// not needed there); ev receives the events' kinds and pixel indices, for
+// the corner found on both line families to count once
+SBMT_DEV int r3_edge_count(const R3Args& a, double2 P, double2 Q, R3Ev* ev) {
+  int n = 0;
+  const bool hz = P.y == Q.y, vt = P.x == Q.x;
+  const R3Split px = r3_split(P.x), py = r3_split(P.y), qx = r3_split(Q.x), qy = r3_split(Q.y);
+  const float dxf = r3_fdiff(qx, px), dyf = r3_fdiff(qy, py);
+  const float D = fmaxf(fabsf(dxf), fabsf(dyf));
+  if (!hz) {
+    // horizontal lines y = k - 1/2 strictly between P.y and Q.y
+    const float sl = __fdiv_rn(dxf, dyf);
+    const i64 k0 = max((i64)0, min(py.i, qy.i) - 1), k1 = min((i64)a.H, max(py.i, qy.i) + 3);
+    for (i64 k = k0; k <= k1; ++k) {
+      if (!((r3_lt(py, k) && r3_gt(qy, k)) || (r3_lt(qy, k) && r3_gt(py, k)))) continue;
+      const float hp = r3_i2f((int)(k - py.i)) - 0.5f;
+      const float w = __fadd_rn(px.f, __fmul_rn(__fsub_rn(hp, py.f), sl));
+      const float z = __fadd_rn(w, 0.5f);
+      const int zi = r3_ffloor(z);
+      const float fr = __fsub_rn(z, r3_i2f(zi)), T = r3_cross_tol(D, sl, w);
+      i64 j;
+      bool corner = false;
+      if (fr > T && fr < 1.0f - T) j = px.i + zi;
+      else r3_cross_exact(P, Q, (double)k - 0.5, false, &j, &corner);
+      if (corner ? r3_corner_event(a, j, k, hz, vt) : r3_hb(a, j, k)) {
+        if (n == R3_MAXE) return -1;
+        ev[n].kind = corner ? 2 : 0, ev[n].m = (int)j, ev[n].k = (int)k;
+        ++n;
+      }
+    }
+  }
+  if (!vt) {
+    // vertical lines x = m - 1/2 strictly between P.x and Q.x
+    const float sl = __fdiv_rn(dyf, dxf);
+    const i64 m0 = max((i64)0, min(px.i, qx.i) - 1), m1 = min((i64)a.W, max(px.i, qx.i) + 3);
+    for (i64 m = m0; m <= m1; ++m) {
+      if (!((r3_lt(px, m) && r3_gt(qx, m)) || (r3_lt(qx, m) && r3_gt(px, m)))) continue;
+      const float hp = r3_i2f((int)(m - px.i)) - 0.5f;
+      const float w = __fadd_rn(py.f, __fmul_rn(__fsub_rn(hp, px.f), sl));
+      const float z = __fadd_rn(w, 0.5f);
+      const int zi = r3_ffloor(z);
+      const float fr = __fsub_rn(z, r3_i2f(zi)), T = r3_cross_tol(D, sl, w);
+      i64 j;
+      bool corner = false;
+      if (fr > T && fr < 1.0f - T) j = py.i + zi;
+      else r3_cross_exact(P, Q, (double)m - 0.5, true, &j, &corner);
+      if (corner) {
+        bool dup = false;
+        for (int t = 0; t < n; ++t)
+          if (ev[t].kind == 2 && ev[t].m == (int)m && ev[t].k == (int)j) dup = true;
+        if (dup || !r3_corner_event(a, m, j, hz, vt)) continue;
+      } else if (!r3_vb(a, m, j)) {
+        continue;
+      }
+      if (n == R3_MAXE) return -1;
+      ev[n].kind = corner ? 2 : 1, ev[n].m = (int)m, ev[n].k = (int)j;
+      ++n;
+    }
+  }
+  return n;
+}
+
+// the cell's two chord ends on a pixel line (vert: the vertical line x = c0,
+// else the horizontal y = c0): (position along the line, source = corner 0..2
+// or 3 + edge); the number of ends found (2 for a proper cell)
+SBMT_DEV int r3_chord(const double2* K, const int* id, bool vert, double c0, double* pos, int* src) {
+  int n = 0;
+  for (int c = 0; c < 3; ++c)
+    if ((vert ? K[c].x : K[c].y) == c0) {
+      if (n == 2) return 3;
+      pos[n] = vert ? K[c].y : K[c].x, src[n++] = c;
+    }
+  for (int j = 0; j < 3; ++j) {
+    const int u = j, w = j == 2 ? 0 : j + 1;
+    const double2 P = id[u] < id[w] ? K[u] : K[w], Q = id[u] < id[w] ? K[w] : K[u];
+    const double pa = vert ? P.x : P.y, pb = vert ? Q.x : Q.y;
+    if (!((pa < c0 && c0 < pb) || (pb < c0 && c0 < pa))) continue;
+    if (n == 2) return 3;
+    pos[n] = vert ? r3_vy(P, Q, c0) : r3_hx(P, Q, c0), src[n++] = 3 + j;
+  }
+  if (n == 2 && pos[1] < pos[0]) {
+    const double t = pos[0];
+    pos[0] = pos[1], pos[1] = t;
+    const int s = src[0];
+    src[0] = src[1], src[1] = s;
+  }
+  return n;
+}
+
+struct R3Cell {
+  double2 K[3];
+  int id[3];
+  double ylo, yhi, xlo, xhi;
+};
+// the corners alone (the bounding box left unset)
+SBMT_DEV R3Cell r3_load_k(const R3Args& a, u32 c) {
+  R3Cell C;
+  const int* t = a.ttri + 3 * (u64)c;
+  for (int q = 0; q < 3; ++q) C.id[q] = t[q], C.K[q] = reinterpret_cast<const double2*>(a.txy)[C.id[q]];
+  return C;
+}
+SBMT_DEV R3Cell r3_load(const R3Args& a, u32 c) {
+  R3Cell C;
+  const int* t = a.ttri + 3 * (u64)c;
+  for (int q = 0; q < 3; ++q) C.id[q] = t[q], C.K[q] = reinterpret_cast<const double2*>(a.txy)[C.id[q]];
+  C.ylo = fmin(fmin(C.K[0].y, C.K[1].y), C.K[2].y), C.yhi = fmax(fmax(C.K[0].y, C.K[1].y), C.K[2].y);
+  C.xlo = fmin(fmin(C.K[0].x, C.K[1].x), C.K[2].x), C.xhi = fmax(fmax(C.K[0].x, C.K[1].x), C.K[2].x);
+  return C;
+}
+
+// one label over the pixels touching the cell's bounding box: no boundary
+// pixel edge meets the cell, and every pixel the cell covers has that label
+// (returned, OUTSIDE as 0xFFFF), or -1.  The box is the double-precision one
+// grown by 1e-6 px, or any box holding it: a larger box finds a cell of one
+// label at most where the exact one does, and a cell it misses becomes a
+// candidate with no event and no inside vertex, emitted as it is with the
+// label of the pixel holding its centroid, a pixel of the exact box -- the
+// same output.  Here the box comes from the corners' fixed-point values
+// (within 2^-36 of the doubles), its ends moved outwards by 2^-36 and
+// 2e-6 px, all in integer arithmetic.
+SBMT_DEV int r3_uniform(const R3Args& a, const i64* X, const i64* Y) {
+  constexpr i64 HALF = 1ll << 35, GROW = 137439 + 1;  // 1/2 and 2e-6 (rounded up) plus 2^-36, in 2^-36 units
+  const i64 xlo = min(min(X[0], X[1]), X[2]), xhi = max(max(X[0], X[1]), X[2]);
+  const i64 ylo = min(min(Y[0], Y[1]), Y[2]), yhi = max(max(Y[0], Y[1]), Y[2]);
+  // ceil(lo - 1/2 - grow) and floor(hi + 1/2 + grow) in pixels
+  const i64 x0 = -((-(xlo - HALF - GROW)) >> 36), x1 = (xhi + HALF + GROW) >> 36;
+  const i64 y0 = -((-(ylo - HALF - GROW)) >> 36), y1 = (yhi + HALF + GROW) >> 36;
+  const int l0 = r3_px(a, x0, y0);
+  // every pixel beyond the image reads OUTSIDE, like those of the one-pixel
+  // margin kept: the scan stops there without changing its answer
+  for (i64 y = max(y0, (i64)-1), ye = min(y1, (i64)a.H); y <= ye; ++y)
+    for (i64 x = max(x0, (i64)-1), xe = min(x1, (i64)a.W); x <= xe; ++x)
+      if (r3_px(a, x, y) != l0) return -1;
+  return l0 == R3_OUTSIDE ? 0xFFFF : l0;
+}
+
+// counter-clockwise (a positive orientation of the doubles), with a
+// single-precision filter: the coordinate differences from the fixed-point
+// values are within 2^-35 + 2^-24 |d| of the doubles' (D: the largest), so
+// the float orientation is within 2^-33 D + 7 2^-24 D^2 of the exact one,
+// and the double formula within 2^-50 D^2 of it; beyond twice that the
+// float sign decides, else the double formula
+SBMT_DEV bool r3_ccw(const double2* K, const i64* X, const i64* Y) {
+  constexpr float S36 = 1.4551915228366852e-11f;  // 2^-36
+  const float ax = __fmul_rn((float)(X[1] - X[0]), S36), ay = __fmul_rn((float)(Y[1] - Y[0]), S36);
+  const float bx = __fmul_rn((float)(X[2] - X[0]), S36), by = __fmul_rn((float)(Y[2] - Y[0]), S36);
+  const float o = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+  const float D = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by))) + 5.9604645e-8f;
+  const float T = 4.7e-10f * D + 1.4e-6f * D * D;
+  if (o > T) return true;
+  if (o < -T) return false;
+  return r3_orient(K[0], K[1], K[2]) > 0.0;
+}
+
+// the boundary vertices strictly inside the cell, as corner ids y (W+1) + x
+// in id order; the count, -1 past R3_MAXI, -2 for a row the cell meets in
+// other than two points.  Rows strictly inside the cell's y-range; on each,
+// the chord's two ends (a corner on the row, or an edge crossing it, as in
+// r3_chord): a corner compared with the pixel corners exactly through its
+// fixed-point value, a crossing as a float interval around the double
+// formula's position (the crossing filter's bound), the double formula
+// taken only where the interval holds the pixel corner compared with.
+struct R3End {
+  i64 b;     // integer base of the position
+  float w, T;
+  int src;   // corner 0..2, or 3 + edge
+};
+// the sign of (an edge end's position) - (cx - 1/2), from the double formula
+__device__ __noinline__ int r3_end_cmp_exact(const R3Cell& C, int src, i64 cx, double c0) {
+  const int j = src - 3, u = j, v = j == 2 ? 0 : j + 1;
+  const bool fwd = C.id[u] < C.id[v];
+  const double p = r3_hx(fwd ? C.K[u] : C.K[v], fwd ? C.K[v] : C.K[u], c0);
+  const double x0 = dsb((double)cx, 0.5);
+  return p < x0 ? -1 : (p > x0 ? 1 : 0);
+}
+// the end's position below x0 = cx - 1/2: a corner's exactly from its
+// fixed-point value, a crossing's from the float interval or the double
+// formula
+SBMT_DEV bool r3_end_below(const R3Cell& C, const R3Split* sx, const R3End& e, i64 cx, double c0) {
+  if (e.src < 3) return r3_lt(sx[e.src], cx);
+  const float h = r3_i2f((int)(cx - e.b)) - 0.5f;
+  if (__fsub_rn(h, e.w) > e.T) return true;
+  if (__fsub_rn(e.w, h) > e.T) return false;
+  return r3_end_cmp_exact(C, e.src, cx, c0) < 0;
+}
+SBMT_DEV bool r3_end_above(const R3Cell& C, const R3Split* sx, const R3End& e, i64 cx, double c0) {
+  if (e.src < 3) return r3_gt(sx[e.src], cx);
+  const float h = r3_i2f((int)(cx - e.b)) - 0.5f;
+  if (__fsub_rn(e.w, h) > e.T) return true;
+  if (__fsub_rn(h, e.w) > e.T) return false;
+  return r3_end_cmp_exact(C, e.src, cx, c0) > 0;
+}
+SBMT_DEV int r3_inside(const R3Args& a, const R3Cell& C, u32* out) {
+  R3Split sx[3], sy[3];
+  for (int q = 0; q < 3; ++q) sx[q] = r3_split(C.K[q].x), sy[q] = r3_split(C.K[q].y);
+  float sl[3], D[3];
+  for (int j = 0; j < 3; ++j) {
+    const int u = j, v = j == 2 ? 0 : j + 1;
+    const int P = C.id[u] < C.id[v] ? u : v, Q = P == u ? v : u;
+    const float dxf = r3_fdiff(sx[Q], sx[P]), dyf = r3_fdiff(sy[Q], sy[P]);
+    sl[j] = __fdiv_rn(dxf, dyf), D[j] = fmaxf(fabsf(dxf), fabsf(dyf));
+  }
+  const i64 cy0 = max((i64)0, min(min(sy[0].i, sy[1].i), sy[2].i) - 1);
+  const i64 cy1 = min((i64)a.H, max(max(sy[0].i, sy[1].i), sy[2].i) + 3);
+  const i64 cx0 = max((i64)0, min(min(sx[0].i, sx[1].i), sx[2].i) - 1);
+  const i64 cx1 = min((i64)a.W, max(max(sx[0].i, sx[1].i), sx[2].i) + 3);
+  int n = 0;
+  for (i64 cy = cy0; cy <= cy1; ++cy) {
+    bool below = false, above = false, lt[3], gt[3];
+    for (int q = 0; q < 3; ++q) {
+      lt[q] = r3_lt(sy[q], cy), gt[q] = r3_gt(sy[q], cy);
+      below |= lt[q], above |= gt[q];
+    }
+    if (!(below && above)) continue;
+    const double c0 = (double)cy - 0.5;
+    R3End e[2];
+    int ne = 0;
+    for (int q = 0; q < 3; ++q)
+      if (!lt[q] && !gt[q]) {  // the corner lies on the row
+        if (ne == 2) return -2;
+        e[ne++] = R3End{sx[q].i, sx[q].f, 0.0f, q};  // compared exactly
+      }
+    for (int j = 0; j < 3; ++j) {
+      const int u = j, v = j == 2 ? 0 : j + 1;
+      if (!((lt[u] && gt[v]) || (lt[v] && gt[u]))) continue;
+      if (ne == 2) return -2;
+      const int P = C.id[u] < C.id[v] ? u : v;
+      const float hP = r3_i2f((int)(cy - sy[P].i)) - 0.5f;
+      const float w = __fadd_rn(sx[P].f, __fmul_rn(__fsub_rn(hP, sy[P].f), sl[j]));
+      e[ne++] = R3End{sx[P].i, w, r3_cross_tol(D[j], sl[j], w), 3 + j};
+    }
+    if (ne != 2) return -2;
+    for (i64 cx = cx0; cx <= cx1; ++cx) {
+      const bool inside = (r3_end_below(C, sx, e[0], cx, c0) && r3_end_above(C, sx, e[1], cx, c0)) ||
+                          (r3_end_below(C, sx, e[1], cx, c0) && r3_end_above(C, sx, e[0], cx, c0));
+      if (!inside) continue;
+      if (!r3_is_vertex(r3_cmask(a, cx, cy))) continue;
+      if (n == R3_MAXI) return -1;
+      if (out) out[n] = (u32)(cy * (a.W + 1) + cx);
+      ++n;
+    }
+  }
+  return n;
+}
+
+// events of the edge from P (its lower-id end) to Q, in order from P, with
+// their coordinates, all in the double formulas (the emission's form: every
+// event's position is needed there); the count, or -1 past R3_MAXE
+SBMT_DEV int r3_edge_events_d(const R3Args& a, double2 P, double2 Q, R3Ev* ev) {
   int n = 0;
   const double dx = dsb(Q.x, P.x), dy = dsb(Q.y, P.y);
   const bool hz = dy == 0.0, vt = dx == 0.0;
@@ -172,99 +519,10 @@ SBMT_DEV int r3_edge_events(const R3Args& a, double2 P, double2 Q, R3Ev* ev) {
   return n;
 }
 
-// the cell's two chord ends on a pixel line (vert: the vertical line x = c0,
-// else the horizontal y = c0): (position along the line, source = corner 0..2
-// or 3 + edge); the number of ends found (2 for a proper cell)
-SBMT_DEV int r3_chord(const double2* K, const int* id, bool vert, double c0, double* pos, int* src) {
-  int n = 0;
-  for (int c = 0; c < 3; ++c)
-    if ((vert ? K[c].x : K[c].y) == c0) {
-      if (n == 2) return 3;
-      pos[n] = vert ? K[c].y : K[c].x, src[n++] = c;
-    }
-  for (int j = 0; j < 3; ++j) {
-    const int u = j, w = j == 2 ? 0 : j + 1;
-    const double2 P = id[u] < id[w] ? K[u] : K[w], Q = id[u] < id[w] ? K[w] : K[u];
-    const double pa = vert ? P.x : P.y, pb = vert ? Q.x : Q.y;
-    if (!((pa < c0 && c0 < pb) || (pb < c0 && c0 < pa))) continue;
-    if (n == 2) return 3;
-    pos[n] = vert ? r3_vy(P, Q, c0) : r3_hx(P, Q, c0), src[n++] = 3 + j;
-  }
-  if (n == 2 && pos[1] < pos[0]) {
-    const double t = pos[0];
-    pos[0] = pos[1], pos[1] = t;
-    const int s = src[0];
-    src[0] = src[1], src[1] = s;
-  }
-  return n;
-}
-
-struct R3Cell {
-  double2 K[3];
-  int id[3];
-  double ylo, yhi, xlo, xhi;
-};
-SBMT_DEV R3Cell r3_load(const R3Args& a, u32 c) {
-  R3Cell C;
-  const int* t = a.ttri + 3 * (u64)c;
-  for (int q = 0; q < 3; ++q) C.id[q] = t[q], C.K[q] = reinterpret_cast<const double2*>(a.txy)[C.id[q]];
-  C.ylo = fmin(fmin(C.K[0].y, C.K[1].y), C.K[2].y), C.yhi = fmax(fmax(C.K[0].y, C.K[1].y), C.K[2].y);
-  C.xlo = fmin(fmin(C.K[0].x, C.K[1].x), C.K[2].x), C.xhi = fmax(fmax(C.K[0].x, C.K[1].x), C.K[2].x);
-  return C;
-}
-
-// one label over the pixels touching the cell's bounding box: no boundary
-// pixel edge meets the cell, and every pixel the cell covers has that label
-// (returned, OUTSIDE as 0xFFFF), or -1.  The box is the double-precision one
-// grown by 1e-6 px, or any box holding it: a larger box finds a cell of one
-// label at most where the exact one does, and a cell it misses becomes a
-// candidate with no event and no inside vertex, emitted as it is with the
-// label of the pixel holding its centroid, a pixel of the exact box -- the
-// same output.  Here the box comes from single precision: each coordinate
-// converted rounding down (lower ends) or up (upper ends), the ends moved by
-// 2e-6 px more, the arithmetic rounded outwards, so that it holds the exact
-// box at every magnitude.
-SBMT_DEV int r3_uniform(const R3Args& a, const double2* K) {
-  const float xlo = fminf(fminf(__double2float_rd(K[0].x), __double2float_rd(K[1].x)), __double2float_rd(K[2].x));
-  const float ylo = fminf(fminf(__double2float_rd(K[0].y), __double2float_rd(K[1].y)), __double2float_rd(K[2].y));
-  const float xhi = fmaxf(fmaxf(__double2float_ru(K[0].x), __double2float_ru(K[1].x)), __double2float_ru(K[2].x));
-  const float yhi = fmaxf(fmaxf(__double2float_ru(K[0].y), __double2float_ru(K[1].y)), __double2float_ru(K[2].y));
-  const i64 x0 = (i64)ceilf(__fsub_rd(__fsub_rd(xlo, 0.5f), 2e-6f)), x1 = (i64)floorf(__fadd_ru(__fadd_ru(xhi, 0.5f), 2e-6f));
-  const i64 y0 = (i64)ceilf(__fsub_rd(__fsub_rd(ylo, 0.5f), 2e-6f)), y1 = (i64)floorf(__fadd_ru(__fadd_ru(yhi, 0.5f), 2e-6f));
-  const int l0 = r3_px(a, x0, y0);
-  // every pixel beyond the image reads OUTSIDE, like those of the one-pixel
-  // margin kept: the scan stops there without changing its answer
-  for (i64 y = max(y0, (i64)-1), ye = min(y1, (i64)a.H); y <= ye; ++y)
-    for (i64 x = max(x0, (i64)-1), xe = min(x1, (i64)a.W); x <= xe; ++x)
-      if (r3_px(a, x, y) != l0) return -1;
-  return l0 == R3_OUTSIDE ? 0xFFFF : l0;
-}
-
-// counter-clockwise (a positive orientation of the doubles), with a
-// single-precision filter: the corners rounded to float are within 2^-24 E
-// of the doubles (E: the largest coordinate magnitude), so the float
-// orientation of the rounded corners is within 16 2^-24 (E D + D^2) of the
-// exact orientation (D: the largest coordinate difference), and the double
-// formula within 2^-50 D^2 of it; above that bound the float sign decides,
-// below it the double formula
-SBMT_DEV bool r3_ccw(const double2* K) {
-  const float2 p = make_float2(__double2float_rn(K[0].x), __double2float_rn(K[0].y));
-  const float2 q = make_float2(__double2float_rn(K[1].x), __double2float_rn(K[1].y));
-  const float2 r = make_float2(__double2float_rn(K[2].x), __double2float_rn(K[2].y));
-  const float ax = __fsub_rn(q.x, p.x), ay = __fsub_rn(q.y, p.y), bx = __fsub_rn(r.x, p.x), by = __fsub_rn(r.y, p.y);
-  const float o = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
-  const float E = fmaxf(fmaxf(fmaxf(fabsf(p.x), fabsf(p.y)), fmaxf(fabsf(q.x), fabsf(q.y))), fmaxf(fabsf(r.x), fabsf(r.y)));
-  const float D = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fmaxf(fabsf(bx), fabsf(by)), fabsf(__fsub_rn(r.x, q.x))));
-  const float Dy = fmaxf(D, fabsf(__fsub_rn(r.y, q.y))) + 1e-30f;
-  const float T = 32.0f * 5.9604645e-8f * (E * Dy + Dy * Dy);  // twice the bound, rounding included
-  if (o > T) return true;
-  if (o < -T) return false;
-  return r3_orient(K[0], K[1], K[2]) > 0.0;
-}
-
 // the boundary vertices strictly inside the cell, as corner ids y (W+1) + x
-// in id order; the count, or -1 past R3_MAXI (ids written when out != null)
-SBMT_DEV int r3_inside(const R3Args& a, const R3Cell& C, u32* out) {
+// in id order, in the double formulas (the emission's form); the count, or
+// -1 past R3_MAXI (ids written when out != null)
+SBMT_DEV int r3_inside_d(const R3Args& a, const R3Cell& C, u32* out) {
   int n = 0;
   const i64 cy0 = max((i64)0, r3_lo(C.ylo)), cy1 = min((i64)a.H, r3_hi(C.yhi));
   const i64 cx0 = max((i64)0, r3_lo(C.xlo)), cx1 = min((i64)a.W, r3_hi(C.xhi));
@@ -349,10 +607,15 @@ __global__ void __launch_bounds__(256) k_r3_screen(R3Args a) {
     if (c < a.nt) {
       const int* t = a.ttri + 3 * c;
       double2 K[3];
-      for (int q = 0; q < 3; ++q) K[q] = reinterpret_cast<const double2*>(a.txy)[t[q]];
+      i64 X[3], Y[3];
+      for (int q = 0; q < 3; ++q) {
+        K[q] = reinterpret_cast<const double2*>(a.txy)[t[q]];
+        bool ix, iy;
+        X[q] = r3_fix36(K[q].x, &ix), Y[q] = r3_fix36(K[q].y, &iy);
+      }
       int l = -1;
-      if (!r3_ccw(K)) atomicOr(a.err, R3_GEOMETRY);
-      else l = r3_uniform(a, K);
+      if (!r3_ccw(K, X, Y)) atomicOr(a.err, R3_GEOMETRY);
+      else l = r3_uniform(a, X, Y);
       cand = l < 0;
       a.ntri[c] = 1, a.nown[c] = 0, a.nin[c] = 0, a.own3[c] = 0;
       a.ulab[c] = (unsigned short)(cand ? 0 : l);
@@ -377,13 +640,13 @@ __global__ void __launch_bounds__(128) k_r3_count(R3Args a) {
   const u32 n = *a.ncand;
   for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const u32 c = a.cand[q];
-    const R3Cell C = r3_load(a, c);
+    const R3Cell C = r3_load_k(a, c);
     int ne = 0, cnt[3];
     bool bad = false;
     for (int j = 0; j < 3; ++j) {
       const int u = j, w = j == 2 ? 0 : j + 1;
       const bool fwd = C.id[u] < C.id[w];
-      cnt[j] = r3_edge_events(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], ev);
+      cnt[j] = r3_edge_count(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], ev);
       if (cnt[j] < 0) bad = true;
       else ne += cnt[j];
     }
@@ -447,7 +710,7 @@ SBMT_DEV u32 r3_build(const R3Args& a, u32 c, const R3Cell& C, R3Local& L, EvBuf
     const int u = j, w = j == 2 ? 0 : j + 1;
     const bool fwd = C.id[u] < C.id[w];
     R3Ev* e = ev[j];
-    const int n = r3_edge_events(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], e);
+    const int n = r3_edge_events_d(a, fwd ? C.K[u] : C.K[w], fwd ? C.K[w] : C.K[u], e);
     if (n < 0 || L.n + n > R3_MAXN) return R3_CAPACITY;
     L.nev[j] = n;
     if (n == 0) continue;
@@ -478,7 +741,7 @@ SBMT_DEV u32 r3_build(const R3Args& a, u32 c, const R3Cell& C, R3Local& L, EvBuf
   }
   // inside vertices
   u32 ins[R3_MAXI];
-  const int ni = r3_inside(a, C, ins);
+  const int ni = r3_inside_d(a, C, ins);
   if (ni == -1 || L.n + ni > R3_MAXN) return R3_CAPACITY;
   if (ni < 0) return R3_GEOMETRY;
   L.ni = ni;
