@@ -309,3 +309,43 @@ def test_retriangulate_a_delaunay_mesh(seed):
     o = oracle.region3(img, xy, tri)
     assert_same(g, o)
     assert o["n_cut_cells"] > 100 and o["n_events"] > 100
+
+
+def _near_lines(W, H, seed):
+    """A Delaunay mesh whose points sit on pixel lines and corners or just
+    off them: offsets below the device filters' fixed-point resolution
+    (2^-37), near it (1e-13, 3e-11) and well above (1e-7), on both sides,
+    so that the exact paths of the pixel-line tests and of the crossing
+    filter decide."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    base, _ = synth.delaunay_mesh(W, H, 500, seed)
+    pts = base.copy()
+    offs = np.array([0.0, 2.0 ** -37, -2.0 ** -37, 1e-13, -1e-13, 3e-11, -3e-11, 1e-7, -1e-7])
+    inner = np.arange(4 + 4 * ((W - 1) // 2), len(pts))
+    pick = rng.choice(inner, size=len(inner) // 2, replace=False)
+    for k, i in enumerate(pick):
+        ax = k % 3  # x on a line, y on a line, or both (a corner)
+        if ax in (0, 2):
+            pts[i, 0] = np.floor(pts[i, 0]) + 0.5 + offs[rng.integers(len(offs))]
+        if ax in (1, 2):
+            pts[i, 1] = np.floor(pts[i, 1]) + 0.5 + offs[rng.integers(len(offs))]
+    pts = np.clip(pts, -0.5, [W - 0.5, H - 0.5])
+    _, keep = np.unique(np.round(pts, 6), axis=0, return_index=True)
+    pts = pts[np.sort(keep)]
+    tri = Delaunay(pts).simplices.astype(np.int32)
+    P = pts[tri]
+    o = (P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0])
+    tri[o < 0] = tri[o < 0][:, [0, 2, 1]]
+    return pts, np.ascontiguousarray(tri[np.abs(o) > 1e-9])
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_retriangulate_points_on_and_near_pixel_lines(seed):
+    img = np.ascontiguousarray(synth.voronoi_labels(size=48, nseeds=9))
+    xy, tri = _near_lines(48, 48, seed)
+    o = oracle.region3(img, xy, tri)
+    g = _imported(img, xy, tri)
+    assert_same(g, o)
+    assert o["n_cut_cells"] > 50
