@@ -312,7 +312,7 @@ SBMT_DEV u32 stage_tier_t(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 // Tier-T / Tier-G, triangle and inside-vertex counts) added to the bucket's
 // totals, for a Tier-T cell its staged patch, and a Tier-G cell counted
 // (cells in ngcell, triangles in ngtri, cells per local vertex count in
-// gcnt, counts above TIERG_TN pooled at TIERG_TN + 1).
+// gcnt, counts above TIERG_WN pooled at TIERG_WN + 1).
 // The records of every job form one work queue, handed out in chunks of
 // CUT_CHUNK records of one job and one piece class (recpre[njobs + 1 + k]:
 // the chunks before job k), so that a block works for one job at a time with
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(128, 8) k_cutcells_b(const __grid_constant__ J
       const int lane = threadIdx.x & 31, lead = __ffs(act) - 1;
       const u32 t = __reduce_add_sync(act, kl.ntri);
       if (lane == lead) atomicAdd(jc(J, JC_NGCELL), (u32)__popc(act)), atomicAdd(jc(J, JC_NGTRI), t);
-      const u32 n = kl.ntri + 2 - kl.nchain, key = n > TIERG_TN ? TIERG_TN + 1 : n;
+      const u32 n = kl.ntri + 2 - kl.nchain, key = n > TIERG_WN ? TIERG_WN + 1 : n;
       const unsigned peers = __match_any_sync(act, key);
       if (lane == __ffs(peers) - 1) atomicAdd(&bd->gcnt[key], (u32)__popc(peers));
     }
@@ -434,215 +434,197 @@ __global__ void __launch_bounds__(1024) k_rec_prefix(const Job* __restrict__ job
 }
 
 // ---------------------------------------------------------------------------
-// K4: emission, one block per cell bucket (1024 consecutive cell ids)
+// K4: emission, one warp per cell bucket (1024 consecutive cell ids), four
+// buckets to a block with no block barrier
 // ---------------------------------------------------------------------------
 // Every uncut cell writes its base triangle (A, B, C); every Tier-T cell its
 // staged patch at its offset, with P's id and coordinates.  Tier-G cells are
 // left to the Tier-G kernels, which run beside this one and take their output
-// ranges from the same scans.  The bucket's other triangles are written by
-// one block, a thread taking four consecutive cells.
+// ranges from the same scans.
 //
-// Two uncut cells sharing an edge carry one label: a boundary crossing the
-// edge would cut both cells, and none lies along it.  So a maximal run of
-// uncut cells within a strip row takes the label of its first cell, and one
-// pixel is read per run (a block max-scan gives every cell its run's first
-// cell).
-
-// exclusive sums of a and b over the block's earlier threads, and the
-// largest m over them (-1 when none), for 256 threads; sh holds 24 words
-SBMT_DEV void block_scan3(u32 a, u32 b, int m, u32* ea, u32* eb, int* em, u32* sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  u32 xa = a, xb = b;
-  int xm = m;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u32 ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
-    const int ym = __shfl_up_sync(0xffffffffu, xm, o);
-    if (lane >= o) xa += ya, xb += yb, xm = max(xm, ym);
-  }
-  const int prev_m = __shfl_up_sync(0xffffffffu, xm, 1);
-  if (lane == 31) sh[w] = xa, sh[8 + w] = xb, sh[16 + w] = (u32)xm;
-  __syncthreads();
-  if (w == 0) {
-    u32 sa = lane < 8 ? sh[lane] : 0u, sb = lane < 8 ? sh[8 + lane] : 0u;
-    int sm = lane < 8 ? (int)sh[16 + lane] : -1;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      const u32 ya = __shfl_up_sync(0xffffffffu, sa, o), yb = __shfl_up_sync(0xffffffffu, sb, o);
-      const int ym = __shfl_up_sync(0xffffffffu, sm, o);
-      if (lane >= o) sa += ya, sb += yb, sm = max(sm, ym);
-    }
-    if (lane < 8) sh[lane] = sa, sh[8 + lane] = sb, sh[16 + lane] = (u32)sm;
-  }
-  __syncthreads();
-  *ea = (w ? sh[w - 1] : 0u) + xa - a;
-  *eb = (w ? sh[8 + w - 1] : 0u) + xb - b;
-  *em = max(w ? (int)sh[16 + w - 1] : -1, lane ? prev_m : -1);
-}
+// A cell's first triangle is T0 + k + (the extra triangles, ntri - 1, of the
+// bucket's cut cells before it), k its index in the bucket.  Two uncut cells
+// sharing an edge carry one label: a boundary crossing the edge would cut
+// both cells, and none lies along it.  So a maximal run of uncut cells within
+// a strip row takes the label of its first cell, and one pixel is read per
+// run.  The warp's steps:
+//  1. the bucket's cut-cell records give each cell its extra triangles (a
+//     word per cell in shared memory, 0 for an uncut cell);
+//  2. lane l takes cells 32 l .. 32 l + 31: their cut and row-start bit
+//     masks give the run starts, whose pixel loads are all issued before any
+//     label is stored (the label goes into the run start's word);
+//  3. 32 turns over chunks of 32 consecutive cells, lane l writing cell
+//     32 t + l: the chunk's scan of extra triangles gives the offsets, the
+//     latest run start at or before the cell (else the one carried from
+//     earlier chunks) the label, so the warp's stores of neighbouring cells
+//     are adjacent;
+//  4. the cut cells, a lane per record, offsets from a scan over the records.
+constexpr int EMIT_W = 4;  // buckets (warps) per block
 
 template <bool ONE>
-__global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job one,
-                                                   const Job* __restrict__ jobs, const u32* __restrict__ bpre,
-                                                   int njobs) {
+__global__ void __launch_bounds__(32 * EMIT_W, 8) k_emit_b(const __grid_constant__ Job one,
+                                                           const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                           int njobs) {
   constexpr int NB = 1 << CB_LOG;
-  static_assert(NB == 4 * 256, "four cells per thread");
-  __shared__ __align__(16) u32 s_off[NB];  // triangles per cell, then the bucket's exclusive scan of them
-  __shared__ __align__(16) u32 s_cb[NB];   // inside vertices per record, then their exclusive scan
-  __shared__ unsigned short s_lab[NB];   // the label of each run's first cell
-  __shared__ unsigned short s_head[NB];  // each uncut cell's run's first cell, | 0x8000; 0 for cut cells
-  __shared__ unsigned short s_rowd[NB];  // each cell's strip row, relative to the bucket's first
-  __shared__ u32 s_sh[24];
-  __shared__ int s_row0;
+  static_assert(NB == 32 * 32, "a lane's range is one 32-bit mask");
+  __shared__ __align__(16) u32 s_x[EMIT_W][NB];  // extra triangles per cell; a run start's label after step 2
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 b = lb * EMIT_W + (u32)w;
+  if (b >= J.nbc) return;
+  constexpr unsigned FULL = 0xFFFFFFFFu;
   const GridP& g = J.g;
   const CompactOut& cp = J.cp;
-  const u32 b = lb;
+  u32* xs = s_x[w];
   const i64 c0 = (i64)b << CB_LOG;
   const int nc = (int)min((i64)NB, g.ncells - c0);
   const u32 ncut = J.bcut[b], rec0 = J.bbase[b];
-  const int t4 = 4 * (int)threadIdx.x;
-  if (threadIdx.x == 0) s_row0 = cell_row_near(g, (u32)c0);
-  reinterpret_cast<uint4*>(s_off)[threadIdx.x] =
-      make_uint4(t4 < nc ? 1u : 0u, t4 + 1 < nc ? 1u : 0u, t4 + 2 < nc ? 1u : 0u, t4 + 3 < nc ? 1u : 0u);
-  reinterpret_cast<uint4*>(s_cb)[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
-  for (u32 r = threadIdx.x; r < ncut; r += blockDim.x) {
+  const int row0 = cell_row_near(g, (u32)c0);
+  // 1. extra triangles per cell
+  for (int k = lane; k < NB / 4; k += 32) reinterpret_cast<uint4*>(xs)[k] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  for (u32 r = lane; r < ncut; r += 32) {
     const CutRec rec = J.recs[rec0 + r];
-    s_off[rec.cell - c0] = rec.ntri;  // at least 3: a cut cell is never one triangle
-    s_cb[r] = rec.nchain;
+    xs[rec.cell - c0] = rec.ntri - 1u;  // at least 2: a cut cell is never one triangle
   }
-  __syncthreads();
-  // this thread's cells: counts, cut flags, strip rows, run starts
-  u32 v[4], ch[4];
-  bool cut[4];
-  int r = s_row0;
-  i64 rs = g.cbase[r], re = r + 1 < g.nrows ? g.cbase[r + 1] : g.ncells;  // the row's cell ids [rs, re)
-  int rowu[4];
-  bool rstart[4];
-  int m = -1;
-  bool prevcut = t4 == 0 || s_off[t4 - 1] != 1u;
+  __syncwarp();
+  // 2. this lane's cells: cut, valid and row-start masks, run starts, labels
+  const int k0 = 32 * lane;
+  u32 cutm = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint4 v = reinterpret_cast<const uint4*>(xs + k0)[i];
+    cutm |= (v.x ? 1u : 0u) << (4 * i) | (v.y ? 2u : 0u) << (4 * i) | (v.z ? 4u : 0u) << (4 * i) |
+            (v.w ? 8u : 0u) << (4 * i);
+  }
+  const int nv = max(0, min(32, nc - k0));
+  const u32 validm = nv >= 32 ? FULL : (1u << nv) - 1u;
+  int r = row0;  // strip row of the lane's first cell, then of each run start
+  u32 rowm = 0;
+  if (nv > 0) {
+    const i64 cfirst = c0 + k0;
+    r = advance_row(g, row0, (u32)cfirst);
+    if (g.cbase[r] == cfirst) rowm |= 1u;
+    for (int q = r + 1; q < g.nrows && g.cbase[q] < cfirst + nv; ++q) rowm |= 1u << (int)(g.cbase[q] - cfirst);
+  }
+  const u32 prev_last = __shfl_up_sync(FULL, cutm, 1) >> 31;
+  const u32 prevm = (cutm << 1) | (lane == 0 ? 1u : prev_last);  // the bucket's first cell starts a run
+  const u32 startm = ~cutm & validm & (prevm | rowm);
   {
-    const uint4 a = reinterpret_cast<const uint4*>(s_off)[threadIdx.x];
-    const uint4 c = reinterpret_cast<const uint4*>(s_cb)[threadIdx.x];
-    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-    ch[0] = c.x, ch[1] = c.y, ch[2] = c.z, ch[3] = c.w;
-  }
+    const i64 twoS = 2 * g.S;
+    const float inv2S = 1.0f / (float)twoS;
+    // four run starts at a time: their loads are in flight together
+    for (u32 m = startm; m;) {
+      int kk[4], lab[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int k = t4 + u;
-    cut[u] = v[u] != 1u;
+      for (int q = 0; q < 4; ++q) {
+        kk[q] = -1;
+        if (!m) continue;
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        const i64 cid = c0 + k0 + i;
+        r = advance_row(g, r, (u32)cid);
+        const i64 c = g.clo[r] + (cid - g.cbase[r]);
+        const i64 xc = g.ox + 3 * g.p * (c + g.j0 + r + 1);
+        const int prow = g.lrow[2 * r + (int)(c & 1)];
+        const int num = (int)(2 * xc + g.S), den = (int)twoS;
+        int pcol = (int)floorf((float)num * inv2S);
+        while (pcol * den > num) --pcol;
+        while ((pcol + 1) * den <= num) ++pcol;
+        kk[q] = k0 + i;
+        lab[q] = J.dtype == 1 ? pix<unsigned char>(J.img, J.pitch, g.W, g.H, pcol, prow)
+                              : pix<unsigned short>(J.img, J.pitch, g.W, g.H, pcol, prow);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (kk[q] >= 0) xs[kk[q]] = lab[q] == OUTSIDE ? 0xFFFFu : (u32)lab[q];
+    }
+  }
+  __syncwarp();
+  // 3. uncut cells, lane l writing cell 32 t + l of chunk t
+  const u32 T0 = (u32)c0 + J.extra_scan[b];
+  u32 extra = 0;           // extra triangles of the cut cells before the chunk
+  u32 lab_carry = 0;       // label of the latest run start before the chunk
+  int rr = row0;           // strip row of this lane's cell, advanced chunk by chunk
+  i64 rnext = rr + 1 < g.nrows ? g.cbase[rr + 1] : g.ncells;
+  i64 clo_r = g.clo[rr], cb_r = g.cbase[rr];
+  i64 vb0 = g.vbase[rr] - g.vlo[rr], vb1 = g.vbase[rr + 1] - g.vlo[rr + 1];
+  for (int t = 0; t * 32 < nc; ++t) {
+    const int k = 32 * t + lane;
+    const u32 cm = __shfl_sync(FULL, cutm, t), sm = __shfl_sync(FULL, startm, t);
+    const u32 xv = xs[k];
+    const bool cut = (cm >> lane) & 1u;
+    const u32 ex = cut ? xv : 0u;
+    u32 inc = ex;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const u32 off = T0 + (u32)k + extra + inc - ex;
+    extra += __shfl_sync(FULL, inc, 31);
+    const u32 upto = sm & (lane == 31 ? FULL : (2u << lane) - 1u);
+    const int src = upto ? 31 - __clz(upto) : 0;
+    const u32 lv = __shfl_sync(FULL, xv, src);
+    const u32 lab = upto ? lv : lab_carry;
+    if (sm) lab_carry = __shfl_sync(FULL, xv, 31 - __clz(sm));
+    if (cut || k >= nc) continue;
     const i64 cid = c0 + k;
-    bool rowstart = false;
-    if (k < nc) {
-      while (cid >= re) rs = re, ++r, re = r + 1 < g.nrows ? g.cbase[r + 1] : g.ncells;
-      rowstart = cid == rs;
-    }
-    rowu[u] = r;
-    rstart[u] = rowstart;
-    if (!cut[u] && (k == 0 || prevcut || rowstart)) m = k;
-    prevcut = cut[u];
-  }
-  u32 ex_t, ex_c;
-  int em;
-  block_scan3(v[0] + v[1] + v[2] + v[3], ch[0] + ch[1] + ch[2] + ch[3], m, &ex_t, &ex_c, &em, s_sh);
-  // the run start of each cell, and the scans in place
-  int head[4];
-  {
-    u32 rt = ex_t, rc = ex_c;
-    int hm = em;
-    prevcut = t4 == 0 || s_off[t4 - 1] != 1u;  // s_off still holds the counts here
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = t4 + u;
-      const bool start = !cut[u] && (k == 0 || prevcut || rstart[u]);
-      if (start) hm = k;
-      head[u] = hm;
-      prevcut = cut[u];
-      s_head[k] = cut[u] ? (unsigned short)0 : (unsigned short)(0x8000 | hm);
-      s_rowd[k] = (unsigned short)(rowu[u] - s_row0);
-    }
-    reinterpret_cast<uint4*>(s_off)[threadIdx.x] = make_uint4(rt, rt + v[0], rt + v[0] + v[1], rt + v[0] + v[1] + v[2]);
-    reinterpret_cast<uint4*>(s_cb)[threadIdx.x] = make_uint4(rc, rc + ch[0], rc + ch[0] + ch[1], rc + ch[0] + ch[1] + ch[2]);
-  }
-  // run starts read their pixel: column floor((2 xc + S) / 2S) of the
-  // centroid, xc = ox + 3p (c + j + 1) for cell index c in strip row j; row
-  // tabulated per strip row and cell parity
-  const i64 twoS = 2 * g.S;
-  const float inv2S = 1.0f / (float)twoS;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int k = t4 + u;
-    if (head[u] != k || cut[u] || k >= nc) continue;
-    const int rr = rowu[u];
-    const i64 c = g.clo[rr] + ((c0 + k) - g.cbase[rr]);
-    const i64 xc = g.ox + 3 * g.p * (c + g.j0 + rr + 1);
-    const int prow = g.lrow[2 * rr + (int)(c & 1)];
-    const int num = (int)(2 * xc + g.S), den = (int)twoS;
-    int pcol = (int)floorf((float)num * inv2S);
-    while (pcol * den > num) --pcol;
-    while ((pcol + 1) * den <= num) ++pcol;
-    const int l = J.dtype == 1 ? pix<unsigned char>(J.img, J.pitch, g.W, g.H, pcol, prow)
-                               : pix<unsigned short>(J.img, J.pitch, g.W, g.H, pcol, prow);
-    s_lab[k] = l == OUTSIDE ? (unsigned short)0xFFFF : (unsigned short)l;
-  }
-  __syncthreads();
-  const u32 T0_ = (u32)c0 + J.extra_scan[b];
-  // uncut cells: the base triangle (A, B, C), untouched; corner ids are the
-  // vertex row bases plus i.  Here a thread takes cells 256 apart, so that
-  // the warp's stores of neighbouring cells are adjacent.
-  int rr_prev = -1;
-  i64 clo_r = 0, cb_r = 0, vb0 = 0, vb1 = 0;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int k = (int)threadIdx.x + 256 * u;
-    const unsigned hk = s_head[k];
-    if (k >= nc || !(hk & 0x8000u)) continue;
-    const unsigned short lab = s_lab[hk & 0x3FFu];
-    const i64 cid = c0 + k;
-    if (cp.on) {  // the base triangle stays implicit: its cell's label and code
-      cp.cell_label[cid] = lab, cp.cell_code[cid] = 0;
-      continue;
-    }
-    const int rr = s_row0 + s_rowd[k];
-    if (rr != rr_prev) {
-      rr_prev = rr;
+    if (cid >= rnext) {
+      while (cid >= rnext) ++rr, rnext = rr + 1 < g.nrows ? g.cbase[rr + 1] : g.ncells;
       clo_r = g.clo[rr], cb_r = g.cbase[rr];
       vb0 = g.vbase[rr] - g.vlo[rr], vb1 = g.vbase[rr + 1] - g.vlo[rr + 1];
+    }
+    if (cp.on) {  // the base triangle stays implicit: its cell's label and code
+      cp.cell_label[cid] = (unsigned short)lab, cp.cell_code[cid] = 0;
+      continue;
     }
     const i64 c = clo_r + (cid - cb_r), i = c >> 1;
     int a0, a1, a2;
     if ((c & 1) == 0) a0 = (int)(vb0 + i), a1 = (int)(vb0 + i + 1), a2 = (int)(vb1 + i);
     else a0 = (int)(vb0 + i + 1), a1 = (int)(vb1 + i + 1), a2 = (int)(vb1 + i);
-    const u32 o = T0_ + s_off[k];
-    J.tri[3 * (i64)o] = a0;
-    J.tri[3 * (i64)o + 1] = a1;
-    J.tri[3 * (i64)o + 2] = a2;
-    J.label[o] = lab;
-    J.code[o] = 0;
+    J.tri[3 * (i64)off] = a0;
+    J.tri[3 * (i64)off + 1] = a1;
+    J.tri[3 * (i64)off + 2] = a2;
+    J.label[off] = (unsigned short)lab;
+    J.code[off] = 0;
   }
-  // cut cells: one thread per record (a bucket has a few dozen, so they
-  // share a warp or two)
+  // 4. cut cells, a lane per record: offsets and inside-vertex ids from
+  // scans over the records (in cell order)
   const u32 CB0 = J.NVg + J.NE + J.chain_scan[b];
   const double invS = 1.0 / (double)g.S;
-  int row = s_row0;
-  for (u32 rr = threadIdx.x; rr < ncut; rr += blockDim.x) {
-    const CutRec rec = J.recs[rec0 + rr];
-    const u32 kl = rec.cell - (u32)c0, cb = CB0 + s_cb[rr];
-    u32 off = T0_ + s_off[kl];
+  u32 ex_carry = 0, ch_carry = 0;
+  int row = row0;
+  for (u32 base = 0; base < ncut; base += 32) {
+    const u32 ri = base + (u32)lane;
+    const bool valid = ri < ncut;
+    CutRec rec{};
+    if (valid) rec = J.recs[rec0 + ri];
+    const u32 ex = valid ? rec.ntri - 1u : 0u, ch = valid ? rec.nchain : 0u;
+    u32 ie = ex, ic = ch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 ye = __shfl_up_sync(FULL, ie, o), yc = __shfl_up_sync(FULL, ic, o);
+      if (lane >= o) ie += ye, ic += yc;
+    }
+    const u32 pe = ex_carry + ie - ex, cb = CB0 + ch_carry + ic - ch;
+    ex_carry += __shfl_sync(FULL, ie, 31), ch_carry += __shfl_sync(FULL, ic, 31);
+    if (!valid) continue;
+    const u32 kl = rec.cell - (u32)c0;
+    u32 off = T0 + kl + pe;
     if (cp.on) {
       // patch triangles before this cell: those of earlier buckets, then the
       // bucket's earlier cut cells (their extra triangles plus one each)
-      const u32 gi = cp.cut_scan[b] + rr;
-      off = J.extra_scan[b] + cp.cut_scan[b] + rr + (s_off[kl] - kl);
+      const u32 gi = cp.cut_scan[b] + ri;
+      off = J.extra_scan[b] + cp.cut_scan[b] + ri + pe;
       cp.patch_cell[gi] = rec.cell, cp.patch_off[gi] = off;
       cp.cell_label[rec.cell] = 0xFFFF, cp.cell_code[rec.cell] = (unsigned short)(rec.code & 0xFFFFu);
     }
     if (rec.code & (1u << 16)) continue;  // Tier-G
     row = advance_row(g, row, rec.cell);
     const CellGeo cg = cell_geo(g, rec.cell, row);
-    const TStage st = J.stg[rec0 + rr];
-    const unsigned long long w = g_keys.tris[(((rec.code >> 6) & 63u) - 1) * 3 + ((rec.code >> 4) & 3u)];
+    const TStage st = J.stg[rec0 + ri];
+    const unsigned long long wk = g_keys.tris[(((rec.code >> 6) & 63u) - 1) * 3 + ((rec.code >> 4) & 3u)];
     const u32 ga = vid(g, cg.ci[0], cg.cj[0]), gb = vid(g, cg.ci[1], cg.cj[1]), gc = vid(g, cg.ci[2], cg.cj[2]);
     auto gid = [&](int l) -> u32 {
       switch (l) {
@@ -658,13 +640,13 @@ __global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job o
     };
     const unsigned short cd = (unsigned short)(rec.code & 0xFFFFu);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      if (k >= (int)rec.ntri) break;
-      const u32 o = off + (u32)k;
-      J.tri[3 * (i64)o] = (int)gid(tri_label(w, k, 0));
-      J.tri[3 * (i64)o + 1] = (int)gid(tri_label(w, k, 1));
-      J.tri[3 * (i64)o + 2] = (int)gid(tri_label(w, k, 2));
-      J.label[o] = st.lab[k];
+    for (int q = 0; q < 7; ++q) {
+      if (q >= (int)rec.ntri) break;
+      const u32 o = off + (u32)q;
+      J.tri[3 * (i64)o] = (int)gid(tri_label(wk, q, 0));
+      J.tri[3 * (i64)o + 1] = (int)gid(tri_label(wk, q, 1));
+      J.tri[3 * (i64)o + 2] = (int)gid(tri_label(wk, q, 2));
+      J.label[o] = st.lab[q];
       J.code[o] = cd;
     }
     if (rec.nchain == 1) {
@@ -675,7 +657,7 @@ __global__ void __launch_bounds__(256, 6) k_emit_b(const __grid_constant__ Job o
       reinterpret_cast<double2*>(J.xy)[cb - cp.xy0] = vv;
     }
   }
-  if (cp.on && b == J.nbc - 1 && threadIdx.x == 0)
+  if (cp.on && b == J.nbc - 1 && lane == 0)
     cp.patch_off[cp.cut_scan[J.nbc]] = J.extra_scan[J.nbc] + cp.cut_scan[J.nbc];
 }
 
@@ -732,8 +714,8 @@ int launch_cutcells_b(const Job* one, const Job* jobs, int njobs, const BatchPtr
 
 int launch_emit_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, cudaStream_t st) {
   if (nblocks == 0) return 0;
-  if (one) k_emit_b<true><<<nblocks, 256, 0, st>>>(*one, jobs, bpre, njobs);
-  else k_emit_b<false><<<nblocks, 256, 0, st>>>(Job{}, jobs, bpre, njobs);
+  if (one) k_emit_b<true><<<nblocks, 32 * EMIT_W, 0, st>>>(*one, jobs, bpre, njobs);
+  else k_emit_b<false><<<nblocks, 32 * EMIT_W, 0, st>>>(Job{}, jobs, bpre, njobs);
   return 1;
 }
 

@@ -27,8 +27,10 @@ namespace sbmt {
 namespace {
 
 constexpr int TN = TIERG_TN;  // thread path: local vertices per cell (16-bit vertex sets)
-constexpr int WN = 64;  // warp path
+constexpr int WN = 64;  // warp path, large state
+constexpr int WS = TIERG_WN;  // warp path, small state (16-bit vertex sets)
 constexpr int WWARPS = 4;
+constexpr int SW_BLOCKS = 6;  // small-state warp kernel: blocks per SM
 
 SBMT_DEV constexpr int pow2_at_least(int x) {
   int m = 1;
@@ -36,34 +38,34 @@ SBMT_DEV constexpr int pow2_at_least(int x) {
   return m;
 }
 
-// The state of one Tier-G cell.  The thread path (N <= 16) keeps it in
-// local memory and small -- 16-bit vertex sets, no edge list; the warp path
-// (N = 64) keeps it in shared memory.  Cell-local coordinates keep full 32-bit
+// The state of one Tier-G cell.  The thread path (L false, N <= 16) keeps it
+// in local memory and small -- 16-bit vertex sets, no edge list; the warp
+// path (L true; N = 16 or 64) keeps it in shared memory, with the kept edges
+// listed.  Cell-local coordinates keep full 32-bit
 // components: a value near the cell can have components of order the image
 // size (a point on a slanted grid edge has x = a + b sqrt3 with both large).
-template <int N>
+template <int N, bool L>
 struct GStore {
-  static constexpr bool SMALL = N <= 16;
   static constexpr int NCAND = N * (N - 1) / 2;
-  static constexpr int NCANDP = SMALL ? NCAND : pow2_at_least(NCAND);
-  using Adj = typename std::conditional<SMALL, unsigned short, u64>::type;
+  static constexpr int NCANDP = L ? pow2_at_least(NCAND) : NCAND;
+  using Adj = typename std::conditional<(N <= 16), unsigned short, u64>::type;
   int xa[N], xb[N], ya[N], yb[N];  // cell-local exact coordinates (a + b sqrt3)
   u32 gid[N];
   u32 ref[N];  // event index (events) or pixel-corner id (inside vertices) while building
   Adj adj[N];
-  unsigned short edge[SMALL ? 1 : 3 * N];  // kept edges, warp path only
+  unsigned short edge[L ? 3 * N : 1];  // kept edges, warp path only (L)
   unsigned short cand[NCANDP];
   u32 tri[2 * N];
   float fx[N], fy[N];  // the values rounded once from double, for the fast filters
   unsigned char em[N];  // the cell edges a vertex lies on (bit k: edge k)
   int n, nev, nedge, ntri, ok;
 };
-template <int N>
-SBMT_DEV float sfx(const GStore<N>& s, int k) {
+template <int N, bool L>
+SBMT_DEV float sfx(const GStore<N, L>& s, int k) {
   return s.fx[k];
 }
-template <int N>
-SBMT_DEV float sfy(const GStore<N>& s, int k) {
+template <int N, bool L>
+SBMT_DEV float sfy(const GStore<N, L>& s, int k) {
   return s.fy[k];
 }
 
@@ -77,19 +79,19 @@ SBMT_DEV void g_sync() {
   if constexpr (G == 32) __syncwarp();
 }
 
-template <int N>
-SBMT_DEV Pq lpt(const GStore<N>& s, int k) {
+template <int N, bool L>
+SBMT_DEV Pq lpt(const GStore<N, L>& s, int k) {
   return Pq{zq(s.xa[k], s.xb[k]), zq(s.ya[k], s.yb[k])};
 }
-template <int N>
-SBMT_DEV Zq len2(const GStore<N>& s, int u, int v) {
+template <int N, bool L>
+SBMT_DEV Zq len2(const GStore<N, L>& s, int u, int v) {
   const Zq dx = zq((i64)s.xa[v] - s.xa[u], (i64)s.xb[v] - s.xb[u]);
   const Zq dy = zq((i64)s.ya[v] - s.ya[u], (i64)s.yb[v] - s.yb[u]);
   return dx * dx + dy * dy;
 }
 // candidate order: exact squared length, then the packed pair (u << 8 | v)
-template <int N>
-SBMT_DEV bool cand_less(const GStore<N>& s, unsigned short x, unsigned short y) {
+template <int N, bool L>
+SBMT_DEV bool cand_less(const GStore<N, L>& s, unsigned short x, unsigned short y) {
   if (x == 0xFFFFu) return false;
   if (y == 0xFFFFu) return true;
   const int c = zcmp(len2(s, x >> 8, x & 255), len2(s, y >> 8, y & 255));
@@ -104,8 +106,8 @@ SBMT_DEV Zq dot3(const Pq& o, const Pq& p, const Pq& q) {
 // are far apart and exactly otherwise.  Coordinates are rounded from their
 // exact values (error below |coordinate| 2^-24), so a key's error stays far
 // below tol for cells of extent E (scaled units).
-template <int N>
-SBMT_DEV bool cand_less_fast(const GStore<N>& s, unsigned short x, unsigned short y, float tolc) {
+template <int N, bool L>
+SBMT_DEV bool cand_less_fast(const GStore<N, L>& s, unsigned short x, unsigned short y, float tolc) {
   const int xu = x >> 8, xv = x & 255, yu = y >> 8, yv = y & 255;
   const float dx0 = sfx(s, xv) - sfx(s, xu), dy0 = sfy(s, xv) - sfy(s, xu);
   const float dx1 = sfx(s, yv) - sfx(s, yu), dy1 = sfy(s, yv) - sfy(s, yu);
@@ -117,19 +119,21 @@ SBMT_DEV bool cand_less_fast(const GStore<N>& s, unsigned short x, unsigned shor
 }
 
 // cand_less_fast with the sort's padding entries (0xFFFF) last
-template <int N>
-SBMT_DEV bool cand_less_sent(const GStore<N>& s, unsigned short x, unsigned short y, float tolc) {
+template <int N, bool L>
+SBMT_DEV bool cand_less_sent(const GStore<N, L>& s, unsigned short x, unsigned short y, float tolc) {
   if (x == 0xFFFFu) return false;
   if (y == 0xFFFFu) return true;
   return cand_less_fast(s, x, y, tolc);
 }
 
+SBMT_DEV void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // Build the local boundary graph (one thread): corners A, B, C; the events
 // on AB, BC, CA in counter-clockwise order; the inside vertices by pixel-
 // corner id; constraint edges = boundary cycle + one piece per pair.
-template <int N>
+template <int N, bool L>
 SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, const Pair* P, const Seg* segs,
-                          const Event* ev, GStore<N>& s) {
+                          const Event* ev, GStore<N, L>& s) {
   s.ok = 0;
   s.nedge = 0;
   const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
@@ -220,7 +224,7 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
       return;
     }
     s.adj[u] |= 1ull << v, s.adj[v] |= 1ull << u;
-    if constexpr (!GStore<N>::SMALL) s.edge[s.nedge] = (unsigned short)((u << 8) | v);
+    if constexpr (L) s.edge[s.nedge] = (unsigned short)((u << 8) | v);
     ++s.nedge;
   };
   {  // boundary cycle A, events on AB, B, events on BC, C, events on CA
@@ -253,8 +257,8 @@ SBMT_DEV void build_local(const GridP& g, const CellGeo& cg, const CutRec& rec, 
 
 // The greedy completion and face listing by a group of G lanes (G = 1: one
 // thread; G = 32: a warp with the store in shared memory).
-template <int G, int N, class O>
-SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float tolc) {
+template <int G, int N, bool L, class O>
+SBMT_DEV void greedy_faces(GStore<N, L>& s, int lane, int nb, const O& ori, float tolc) {
   const int n = s.n;
   // candidate pairs not joined by a constraint edge
   int m = 0;
@@ -273,7 +277,9 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
     for (int u = 0; u < n; ++u)
       for (int vb = u + 1; vb < n; vb += 32) {
         const int v = vb + lane;
-        const bool ok = v < n && !((s.adj[u] >> v) & 1ull);
+        // a pair on one cell edge that is not a cycle edge has a vertex
+        // between its ends and is always rejected: left out
+        const bool ok = v < n && !((s.adj[u] >> v) & 1ull) && !(s.em[u] & s.em[v]);
         const u32 bal = __ballot_sync(0xffffffffu, ok);
         if (ok) s.cand[m + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)((u << 8) | v);
         m += __popc(bal);
@@ -346,13 +352,30 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
     }
   }
   g_sync<G>();
-  if (lane == 0) {
-    const int nt = min(s.ntri, 2 * N);
+  const int nt = min(s.ntri, 2 * N);
+  if constexpr (G == 1) {
     for (int a = 1; a < nt; ++a)
       for (int b = a; b > 0 && s.tri[b] < s.tri[b - 1]; --b) {
         const u32 t = s.tri[b];
         s.tri[b] = s.tri[b - 1], s.tri[b - 1] = t;
       }
+  } else {
+    // by rank, the lanes together: the keys are distinct (each face once)
+    constexpr int R = (2 * N + G - 1) / G;
+    u32 key[R];
+    int rank[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int k = lane + q * G;
+      key[q] = k < nt ? s.tri[k] : 0u;
+      rank[q] = 0;
+      if (k < nt)
+        for (int j = 0; j < nt; ++j) rank[q] += s.tri[j] < key[q] ? 1 : 0;
+    }
+    g_sync<G>();
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (lane + q * G < nt) s.tri[rank[q]] = key[q];
   }
   g_sync<G>();
 }
@@ -365,28 +388,30 @@ SBMT_DEV void greedy_faces(GStore<N>& s, int lane, int nb, const O& ori, float t
 // its ends or by a kept edge with one end on each side whose own line
 // separates the candidate's ends; a 3-cycle is a face when no vertex lies on
 // the inner side of all three of its edges.
-template <int N>
-SBMT_DEV int ori_filtered(const GStore<N>& s, int a, int b, int c, float tol) {
+template <int N, bool L>
+SBMT_DEV int ori_filtered(const GStore<N, L>& s, int a, int b, int c, float tol) {
   const float fxa = sfx(s, a), fya = sfy(s, a);
   const float dx1 = sfx(s, b) - fxa, dy1 = sfy(s, b) - fya;
   const float dx2 = sfx(s, c) - fxa, dy2 = sfy(s, c) - fya;
   const float d = dx1 * dy2 - dy1 * dx2;
   if (d > tol) return 1;
   if (d < -tol) return -1;
+  // three points of one cell edge (an exact line) need no exact test
+  if (s.em[a] & s.em[b] & s.em[c]) return 0;
   return orient3(lpt(s, a), lpt(s, b), lpt(s, c));
 }
 
 // orientation decided in single precision when clear, exactly otherwise
-template <int N>
+template <int N, bool L>
 struct OriFiltered {
-  const GStore<N>* s;
+  const GStore<N, L>* s;
   float tol;
   SBMT_DEV int operator()(int u, int v, int w) const { return ori_filtered(*s, u, v, w, tol); }
 };
 
-template <int N>
-SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
-  static_assert(N <= 16, "vertex sets are 16 bits wide");
+template <int N, bool L>
+SBMT_DEV void greedy_faces_sets(GStore<N, L>& s, int nb, float tolc, float tolo) {
+  static_assert(N <= 16 && !L, "vertex sets are 16 bits wide");
   constexpr int NPAIR = N * (N - 1) / 2;
   const int n = s.n;
   unsigned short Lm[NPAIR], Zm[NPAIR];
@@ -494,9 +519,9 @@ SBMT_DEV void greedy_faces_sets(GStore<N>& s, int nb, float tolc, float tolo) {
     }
 }
 
-template <int G, int N>
+template <int G, int N, bool L>
 SBMT_DEV void write_patch(const GridP& g, const unsigned char* img, i64 pitch, int dtype, const CellGeo& cg,
-                          const CutRec& rec, const GStore<N>& s, int lane, int* tri, unsigned short* label,
+                          const CutRec& rec, const GStore<N, L>& s, int lane, int* tri, unsigned short* label,
                           unsigned short* code, double* xy, u32 xy0, u32* err) {
   const Pq A = lattice_pt(g, cg.ci[0], cg.cj[0]);
   const int nt = min(s.ntri, 2 * N);
@@ -530,9 +555,15 @@ SBMT_DEV int local_count(const CutRec& rec) { return (int)(rec.ntri + 2 - rec.nc
 SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 * rec.nchain); }
 
 // Tier-G cells of the whole batch ordered by local vertex count, largest
-// first, so that the lanes of a warp run cells of one size; cells above TN
-// vertices go to the warp kernel.  bd->gcnt[n] holds the batch's number of
-// Tier-G cells with n vertices (n > TN pooled at index TN + 1).  One warp per
+// first.  bd->gcnt[n] holds the batch's number of Tier-G cells with n
+// vertices (n > WS pooled at index WS + 1).  The cells of at most WS vertices
+// form one order: those above TN run one warp each with the small state
+// (slist), the others one thread each (olist), so that the lanes of a warp
+// run cells of one size.  (Moving more of the largest cells to the warp
+// kernel measured no faster on any workload tried, from 10^4 to 2 x 10^5
+// Tier-G cells: a warp's greedy pass takes about as long per cell as a
+// thread's.)  Cells above WS vertices go to the
+// large-state warp kernel (wlist).  One warp per
 // cell bucket scans the bucket's records (in cell order) and gives each
 // Tier-G cell its output range from the scans the emission kernel uses: its
 // triangles follow those of the bucket's earlier cells (one each when uncut,
@@ -542,14 +573,20 @@ SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 *
 template <bool ONE>
 __global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
                                                   const u32* __restrict__ bpre, int njobs, BatchDev* bd, uint2* olist,
-                                                  uint2* wlist) {
-  __shared__ u32 s_base[TN + 2];
+                                                  uint2* slist, uint2* wlist) {
+  __shared__ u32 s_base[WS + 2];
+  __shared__ u32 s_kw;
   if (threadIdx.x == 0) {
-    u32 run = 0;
-    for (int n = TN; n >= 0; --n) s_base[n] = run, run += bd->gcnt[n];
-    s_base[TN + 1] = 0;
-    if (blockIdx.x == 0) bd->nolist = run;
+    u32 run = 0, big = 0;
+    for (int n = WS; n >= 0; --n) {
+      s_base[n] = run, run += bd->gcnt[n];
+      if (n == TN + 1) big = run;  // the cells above TN
+    }
+    s_base[WS + 1] = 0;
+    s_kw = big;
+    if (blockIdx.x == 0) bd->nolist = run - big, bd->nslist = big;
   }
+  __syncthreads();
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
   const int lane = threadIdx.x & 31;
   const u32 b = lb * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -559,6 +596,7 @@ __global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job on
   const u32* cut_scan = J.cp.on ? J.cp.cut_scan : nullptr;
   const u32 CB0 = J.NVg + J.NE;
   const u32 n = J.bcut[b], rec0 = J.bbase[b];
+  const u32 kw = s_kw;
   u32 ct = 0, cc = 0;  // the bucket's earlier records: sum of (ntri - 1), of nchain
   for (u32 base = 0; base < n; base += 32) {
     const u32 r = base + (u32)lane;
@@ -580,16 +618,21 @@ __global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job on
     recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
     recs[rec0 + r].chain_base = CB0 + J.chain_scan[b] + pc;
     const int nv = local_count(rec);
-    const int key = nv > TN ? TN + 1 : nv;
+    const int key = nv > WS ? WS + 1 : nv;
     // one atomic per distinct size in the warp
     const unsigned peers = __match_any_sync(tmask, key);
     const int leader = __ffs(peers) - 1;
     u32 at = 0;
-    if (lane == leader) at = atomicAdd(key > TN ? &bd->nwlist : &bd->gcur[key], (u32)__popc(peers));
+    if (lane == leader) at = atomicAdd(key > WS ? &bd->nwlist : &bd->gcur[key], (u32)__popc(peers));
     at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
     const uint2 e = make_uint2((u32)jk, rec0 + r);
-    if (key > TN) wlist[at] = e;
-    else olist[s_base[key] + at] = e;
+    if (key > WS) {
+      wlist[at] = e;
+    } else {
+      const u32 pos = s_base[key] + at;  // place in the order, largest first
+      if (pos < kw) slist[pos] = e;
+      else olist[pos - kw] = e;
+    }
   }
 }
 
@@ -611,7 +654,7 @@ __global__ void __launch_bounds__(64, 12) k_tierg_thread_b(const __grid_constant
     const GridP g = J.g;
     const CutRec rec = J.recs[e.y];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
-    GStore<TN> s;
+    GStore<TN, false> s;
     build_local(g, cg, rec, J.raw + rec.pair_lo, J.segs, J.ev, s);
     if (!s.ok) {
       tierg_over(J, rec.cell);
@@ -620,26 +663,38 @@ __global__ void __launch_bounds__(64, 12) k_tierg_thread_b(const __grid_constant
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
     const float M = (float)(6 * g.p);
     greedy_faces_sets<TN>(s, boundary_count(rec), 1e-4f * M * M, 8e-6f * M * M);
-    write_patch<1, TN>(g, J.img, J.pitch, J.dtype, cg, rec, s, 0, J.tri, J.label, J.code, J.xy, J.cp.xy0,
+    write_patch<1, TN, false>(g, J.img, J.pitch, J.dtype, cg, rec, s, 0, J.tri, J.label, J.code, J.xy, J.cp.xy0,
                        jc(J, JC_ERR));
   }
 }
 
-template <bool ONE>
+// one warp per Tier-G cell, the state (N vertices at most) in shared memory
+template <bool ONE, int N>
 __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp_b(const __grid_constant__ Job one,
-                                                              const Job* __restrict__ jobs, const BatchDev* bd,
-                                                              const uint2* wlist) {
-  __shared__ GStore<WN> sm[WWARPS];
+                                                              const Job* __restrict__ jobs, const u32* count,
+                                                              const uint2* list) {
+  __shared__ GStore<N, true> sm[WWARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  GStore<WN>& s = sm[w];
-  const u32 total = bd->nwlist;
+  GStore<N, true>& s = sm[w];
+  const u32 total = *count;
   for (u32 item = blockIdx.x * WWARPS + w; item < total; item += gridDim.x * WWARPS) {
-    const uint2 e = wlist[item];
+    const uint2 e = list[item];
     const Job& J = ONE ? one : jobs[e.x];
     const GridP g = J.g;
     const CutRec rec = J.recs[e.y];
     const CellGeo cg = cell_geo(g, rec.cell, cell_row_near(g, rec.cell));
-    if (lane == 0) build_local(g, cg, rec, J.raw + rec.pair_lo, J.segs, J.ev, s);
+    // the lanes request the cell's pair records, events and segments into
+    // L1 together, so that the one lane building the local graph finds them
+    // there instead of waiting on each in turn
+    const Pair* P = J.raw + rec.pair_lo;
+    for (u32 k = (u32)lane; k < rec.npairs; k += 32) {
+      const Pair pr = P[k];
+      if (pr.ev_in != NONE) prefetch_l1(J.ev + pr.ev_in);
+      if (pr.ev_out != NONE) prefetch_l1(J.ev + pr.ev_out);
+      prefetch_l1(J.segs + pr.seg);
+    }
+    __syncwarp();
+    if (lane == 0) build_local(g, cg, rec, P, J.segs, J.ev, s);
     __syncwarp();
     if (!s.ok) {
       if (lane == 0) tierg_over(J, rec.cell);
@@ -648,9 +703,9 @@ __global__ void __launch_bounds__(32 * WWARPS) k_tierg_warp_b(const __grid_const
     }
     // cell-local coordinates are bounded by the cell extent M = 6p scaled units
     const float M = (float)(6 * g.p);
-    greedy_faces<32, WN>(s, lane, boundary_count(rec), OriFiltered<WN>{&s, 8e-6f * M * M}, 1e-4f * M * M);
-    write_patch<32, WN>(g, J.img, J.pitch, J.dtype, cg, rec, s, lane, J.tri, J.label, J.code, J.xy, J.cp.xy0,
-                        jc(J, JC_ERR));
+    greedy_faces<32, N, true>(s, lane, boundary_count(rec), OriFiltered<N, true>{&s, 8e-6f * M * M}, 1e-4f * M * M);
+    write_patch<32, N, true>(g, J.img, J.pitch, J.dtype, cg, rec, s, lane, J.tri, J.label, J.code, J.xy, J.cp.xy0,
+                             jc(J, JC_ERR));
     __syncwarp();
   }
 }
@@ -673,20 +728,27 @@ int launch_tierg_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, 
   if (nblocks == 0) return 0;
   const Job none{};
   const Job& oj = one ? *one : none;
-  if (one) k_gorder_b<true><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.wlist);
-  else k_gorder_b<false><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.wlist);
+  if (one) k_gorder_b<true><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
+  else k_gorder_b<false><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
   if (one) k_tierg_thread_b<true><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
   else k_tierg_thread_b<false><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
-  // the warp kernel on its own stream when given one, beside the thread kernel
+  // the warp kernels on their own stream when given one, beside the thread
+  // kernel: the large-state cells (the largest of all) first
   if (st2) {
     if (cudaEventRecord(ev_order, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_order, 0) != cudaSuccess) return -1;
   }
-  if (one) k_tierg_warp_b<true><<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(oj, jobs, bp.bd, bp.wlist);
-  else k_tierg_warp_b<false><<<152 * 2, 32 * WWARPS, 0, st2 ? st2 : st>>>(oj, jobs, bp.bd, bp.wlist);
+  cudaStream_t ws = st2 ? st2 : st;
+  if (one) {
+    k_tierg_warp_b<true, WN><<<152 * 2, 32 * WWARPS, 0, ws>>>(oj, jobs, &bp.bd->nwlist, bp.wlist);
+    k_tierg_warp_b<true, WS><<<152 * SW_BLOCKS, 32 * WWARPS, 0, ws>>>(oj, jobs, &bp.bd->nslist, bp.slist);
+  } else {
+    k_tierg_warp_b<false, WN><<<152 * 2, 32 * WWARPS, 0, ws>>>(oj, jobs, &bp.bd->nwlist, bp.wlist);
+    k_tierg_warp_b<false, WS><<<152 * SW_BLOCKS, 32 * WWARPS, 0, ws>>>(oj, jobs, &bp.bd->nslist, bp.slist);
+  }
   if (st2) {
     if (cudaEventRecord(ev_warp, st2) != cudaSuccess || cudaStreamWaitEvent(st, ev_warp, 0) != cudaSuccess) return -1;
   }
-  return 3;
+  return 4;
 }
 
 int tierg_init() {

@@ -900,7 +900,8 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   }
   // batch-wide state, work lists and the scans' flags
   BatchPtrs bp{};
-  if ((rc = aalloc(lane, &bp.olist, std::max<u64>(np_all, 1))) || (rc = aalloc(lane, &bp.wlist, std::max<u64>(np_all, 1))) ||
+  if ((rc = aalloc(lane, &bp.olist, std::max<u64>(np_all, 1))) || (rc = aalloc(lane, &bp.slist, std::max<u64>(np_all, 1))) ||
+      (rc = aalloc(lane, &bp.wlist, std::max<u64>(np_all, 1))) ||
       (rc = aalloc(lane, &bp.big, std::max<u64>(nbe_all, 1))))
     return bail(rc);
   std::vector<ScanJob> sj1(2 * n), sj2;
@@ -951,7 +952,7 @@ int mesh_run(sbmt_ctx* ctx, Lane* lane, const sbmt_image* imgs, int n, const sbm
   const std::vector<u32> p_walk = prefix_of(n, [&](int k) { return (u32)((walk_chunks(J[k].NP) + 255) / 256); });
   const std::vector<u32> p_sc = prefix_of(n, [&](int k) { return (std::max(J[k].NP, J[k].NE) + 255) / 256; });
   const std::vector<u32> p_rk = prefix_of(n, [&](int k) { return J[k].nbe; });
-  const std::vector<u32> p_so = prefix_of(n, [&](int k) { return J[k].nbc; });
+  const std::vector<u32> p_so = prefix_of(n, [&](int k) { return (J[k].nbc + 3) / 4; });  // the emission: 4 buckets a block
   const std::vector<u32> p_sw = prefix_of(n, [&](int k) { return (J[k].nbc + 3) / 4; });  // the sort: 4 buckets a block
   const std::vector<u32> p_go = prefix_of(n, [&](int k) { return (J[k].nbc + 7) / 8; });
   const std::vector<u32> p_lt = prefix_of(n, [&](int k) {

@@ -23,7 +23,8 @@ constexpr u32 NONE = 0xFFFFFFFFu;
 constexpr int OUTSIDE = 0x10000;  // label outside the image: above every pixel label
 constexpr int CB_LOG = 10;        // base cells per cell bucket (2^10)
 constexpr int EB_LOG = 11;        // grid-edge ids per event bucket (2^11)
-constexpr int TIERG_TN = 9;      // Tier-G cells up to this many local vertices run one thread each
+constexpr int TIERG_TN = 9;      // Tier-G cells up to this many local vertices may run one thread each
+constexpr int TIERG_WN = 16;     // Tier-G cells up to this many local vertices fit the warp path's small state
 constexpr u32 OVER_CAP = 1024;   // ids of cells over the Tier-G vertex limit kept per mesh
 constexpr u32 RANK_SMALL = 256;  // event buckets up to this size are ranked by one small block each
 

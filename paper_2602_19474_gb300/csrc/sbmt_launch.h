@@ -109,9 +109,10 @@ SBMT_DEV int job_of(const u32* bpre, int njobs, u32 b) {
 
 // batch-wide state of the persistent stages
 struct BatchDev {
-  u32 gcnt[TIERG_TN + 2];  // Tier-G cells per local vertex count (above TIERG_TN pooled)
-  u32 gcur[TIERG_TN + 2];  // cursors while ordering
+  u32 gcnt[TIERG_WN + 2];  // Tier-G cells per local vertex count (above TIERG_WN pooled)
+  u32 gcur[TIERG_WN + 2];  // cursors while ordering
   u32 nolist, nwlist, nbig, err;
+  u32 nslist;              // cells of the small-state warp list
   u32 recpre[1];           // 2 (njobs + 1) entries: prefix of the jobs' cut-cell records, then of
                            // their chunks of CUT_CHUNK records
 };
@@ -120,7 +121,8 @@ constexpr u32 CUT_CHUNK = 128;  // records per block and turn of the persistent 
 struct BatchPtrs {
   BatchDev* bd;
   uint2* olist;  // (job, record) of Tier-G cells of at most TIERG_TN vertices, largest first
-  uint2* wlist;  // (job, record) of larger Tier-G cells
+  uint2* slist;  // (job, record) of Tier-G cells of TIERG_TN + 1 .. TIERG_WN vertices, largest first
+  uint2* wlist;  // (job, record) of Tier-G cells above TIERG_WN vertices
   uint2* big;    // (job, event bucket) of registry buckets above RANK_SMALL events
 };
 
@@ -178,7 +180,9 @@ int launch_emit_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u
 int launch_lattice_b(const Job* jobs, const u32* bpre_tab, u32 nb_tab, const u32* bpre_xy, u32 nb_xy, int njobs,
                      cudaStream_t st);
 // Tier-G: ordering (bpre over warps of buckets), then the persistent thread
-// and warp kernels over the batch's lists (warp kernel on st2 when given)
+// and warp kernels over the batch's lists (warp kernels on st2 when given).
+// Cells of at most TIERG_TN vertices run one thread each, larger ones one warp
+// each (a small-state kernel up to TIERG_WN vertices, a large-state one above).
 int launch_tierg_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, u32 nblocks, const BatchPtrs& bp,
                    int thread_blocks_per_sm, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_order,
                    cudaEvent_t ev_warp);
