@@ -490,13 +490,22 @@ __global__ void __launch_bounds__(32 * EMIT_W, 8) k_emit_b(const __grid_constant
   __syncwarp();
   // 2. this lane's cells: cut, valid and row-start masks, run starts, labels
   const int k0 = 32 * lane;
-  u32 cutm = 0;
+  u32 cutm = 0, xsum = 0;  // cut cells, and their extra triangles
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const uint4 v = reinterpret_cast<const uint4*>(xs + k0)[i];
     cutm |= (v.x ? 1u : 0u) << (4 * i) | (v.y ? 2u : 0u) << (4 * i) | (v.z ? 4u : 0u) << (4 * i) |
             (v.w ? 8u : 0u) << (4 * i);
+    xsum += v.x + v.y + v.z + v.w;
   }
+  // the extra triangles of the cut cells before this lane's range
+  u32 xinc = xsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u32 y = __shfl_up_sync(FULL, xinc, o);
+    if (lane >= o) xinc += y;
+  }
+  const u32 xex = xinc - xsum;
   const int nv = max(0, min(32, nc - k0));
   const u32 validm = nv >= 32 ? FULL : (1u << nv) - 1u;
   int r = row0;  // strip row of the lane's first cell, then of each run start
@@ -541,17 +550,28 @@ __global__ void __launch_bounds__(32 * EMIT_W, 8) k_emit_b(const __grid_constant
     }
   }
   __syncwarp();
-  // 3. uncut cells, lane l writing cell 32 t + l of chunk t
+  // the label of the latest run start before this lane's range (every uncut
+  // cell has a run start at or before it in the bucket)
+  u32 carry;
+  {
+    const u32 mylast = startm ? xs[k0 + 31 - __clz(startm)] : 0u;
+    const u32 below = __ballot_sync(FULL, startm != 0u) & ((1u << lane) - 1u);
+    const u32 v = __shfl_sync(FULL, mylast, below ? 31 - __clz(below) : 0);
+    carry = below ? v : 0u;
+  }
+  // 3. uncut cells, lane l writing cell 32 t + l of chunk t; a chunk's
+  // extra triangles before it and its carried label come from lane t, so the
+  // chunks do not wait on one another
   const u32 T0 = (u32)c0 + J.extra_scan[b];
-  u32 extra = 0;           // extra triangles of the cut cells before the chunk
-  u32 lab_carry = 0;       // label of the latest run start before the chunk
   int rr = row0;           // strip row of this lane's cell, advanced chunk by chunk
   i64 rnext = rr + 1 < g.nrows ? g.cbase[rr + 1] : g.ncells;
   i64 clo_r = g.clo[rr], cb_r = g.cbase[rr];
   i64 vb0 = g.vbase[rr] - g.vlo[rr], vb1 = g.vbase[rr + 1] - g.vlo[rr + 1];
+#pragma unroll 4
   for (int t = 0; t * 32 < nc; ++t) {
     const int k = 32 * t + lane;
     const u32 cm = __shfl_sync(FULL, cutm, t), sm = __shfl_sync(FULL, startm, t);
+    const u32 ext = __shfl_sync(FULL, xex, t), ct = __shfl_sync(FULL, carry, t);
     const u32 xv = xs[k];
     const bool cut = (cm >> lane) & 1u;
     const u32 ex = cut ? xv : 0u;
@@ -561,13 +581,10 @@ __global__ void __launch_bounds__(32 * EMIT_W, 8) k_emit_b(const __grid_constant
       const u32 y = __shfl_up_sync(FULL, inc, o);
       if (lane >= o) inc += y;
     }
-    const u32 off = T0 + (u32)k + extra + inc - ex;
-    extra += __shfl_sync(FULL, inc, 31);
+    const u32 off = T0 + (u32)k + ext + inc - ex;
     const u32 upto = sm & (lane == 31 ? FULL : (2u << lane) - 1u);
-    const int src = upto ? 31 - __clz(upto) : 0;
-    const u32 lv = __shfl_sync(FULL, xv, src);
-    const u32 lab = upto ? lv : lab_carry;
-    if (sm) lab_carry = __shfl_sync(FULL, xv, 31 - __clz(sm));
+    const u32 lv = __shfl_sync(FULL, xv, upto ? 31 - __clz(upto) : 0);
+    const u32 lab = upto ? lv : ct;
     if (cut || k >= nc) continue;
     const i64 cid = c0 + k;
     if (cid >= rnext) {

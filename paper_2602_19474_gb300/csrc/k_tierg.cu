@@ -54,7 +54,7 @@ struct GStore {
   u32 ref[N];  // event index (events) or pixel-corner id (inside vertices) while building
   Adj adj[N];
   unsigned short edge[L ? 3 * N : 1];  // kept edges, warp path only (L)
-  unsigned short cand[NCANDP];
+  unsigned short cand[L ? NCANDP : 1];  // candidate order, warp path only (the thread path keeps it with the keys)
   u32 tri[2 * N];
   float fx[N], fy[N];  // the values rounded once from double, for the fast filters
   unsigned char em[N];  // the cell edges a vertex lies on (bit k: edge k)
@@ -416,23 +416,33 @@ SBMT_DEV void greedy_faces_sets(GStore<N, L>& s, int nb, float tolc, float tolo)
   const int n = s.n;
   unsigned short Lm[NPAIR], Zm[NPAIR];
   auto pid = [](int u, int v) { return v * (v - 1) / 2 + u; };  // u < v
-  for (int k = 0; k < n * (n - 1) / 2; ++k) Lm[k] = 0, Zm[k] = 0;
-  for (int c = 2; c < n; ++c)
-    for (int b = 1; b < c; ++b)
-      for (int a = 0; a < b; ++a) {
-        const int o = ori_filtered(s, a, b, c, tolo);
-        // ori(a,b,c) = ori(b,c,a) = -ori(a,c,b)
-        if (o > 0) {
-          Lm[pid(a, b)] |= (unsigned short)(1u << c);
-          Lm[pid(b, c)] |= (unsigned short)(1u << a);
-        } else if (o < 0) {
-          Lm[pid(a, c)] |= (unsigned short)(1u << b);
-        } else {
-          Zm[pid(a, b)] |= (unsigned short)(1u << c);
-          Zm[pid(a, c)] |= (unsigned short)(1u << b);
-          Zm[pid(b, c)] |= (unsigned short)(1u << a);
-        }
+  // Per pair u < v, the vertices left of u -> v and those on its line,
+  // gathered in registers and stored once (the coordinates of every w in
+  // registers too).  Each orientation comes out exact whichever way round its
+  // triple is taken (the filter decides only outside its rounding bound), so
+  // deciding a triple once per pair gives the sets of deciding it once.
+  float fxr[N], fyr[N];
+#pragma unroll
+  for (int w = 0; w < N; ++w) fxr[w] = w < n ? sfx(s, w) : 0.f, fyr[w] = w < n ? sfy(s, w) : 0.f;
+  for (int v = 1; v < n; ++v)
+    for (int u = 0; u < v; ++u) {
+      const float xu = sfx(s, u), yu = sfy(s, u), dx1 = sfx(s, v) - xu, dy1 = sfy(s, v) - yu;
+      unsigned lm = 0, zm = 0, und = 0;
+#pragma unroll
+      for (int w = 0; w < N; ++w) {
+        if (w >= n || w == u || w == v) continue;
+        const float d = dx1 * (fyr[w] - yu) - dy1 * (fxr[w] - xu);
+        if (d > tolo) lm |= 1u << w;
+        else if (!(d < -tolo)) und |= 1u << w;
       }
+      for (; und; und &= und - 1) {  // within the rounding bound: exactly
+        const int w = __ffs(und) - 1;
+        const int o = (s.em[u] & s.em[v] & s.em[w]) ? 0 : orient3(lpt(s, u), lpt(s, v), lpt(s, w));
+        if (o > 0) lm |= 1u << w;
+        else if (o == 0) zm |= 1u << w;
+      }
+      Lm[pid(u, v)] = (unsigned short)lm, Zm[pid(u, v)] = (unsigned short)zm;
+    }
   const unsigned valid = (1u << n) - 1u;
   auto Zset = [&](int u, int v) -> unsigned { return u < v ? Zm[pid(u, v)] : Zm[pid(v, u)]; };
   auto Lset = [&](int u, int v) -> unsigned {
@@ -446,7 +456,7 @@ SBMT_DEV void greedy_faces_sets(GStore<N, L>& s, int nb, float tolc, float tolo)
   // edge that is not a cycle edge always has a vertex between its ends, so
   // it is left out; each candidate's single-precision key is taken once.
   int m = 0;
-  float key[NPAIR];
+  u64 kc[NPAIR];  // the key's bits above the candidate (u << 8 | v): one word moves per shift
   for (int u = 0; u < n; ++u)
     for (int v = u + 1; v < n; ++v)
       if (!((s.adj[u] >> v) & 1ull) && !(s.em[u] & s.em[v])) {
@@ -456,17 +466,19 @@ SBMT_DEV void greedy_faces_sets(GStore<N, L>& s, int nb, float tolc, float tolo)
         int b = m++;
         // insertion: the same order as cand_less_fast, with the keys kept
         while (b > 0) {
-          const float ky = key[b - 1];
+          const u64 y = kc[b - 1];
+          const float ky = __uint_as_float((u32)(y >> 32));
           const float tol = 1e-5f * (kx + ky) + tolc;
-          const bool less = kx < ky - tol ? true : kx > ky + tol ? false : cand_less(s, x, s.cand[b - 1]);
+          const bool less =
+              kx < ky - tol ? true : kx > ky + tol ? false : cand_less(s, x, (unsigned short)(y & 0xFFFFu));
           if (!less) break;
-          s.cand[b] = s.cand[b - 1], key[b] = key[b - 1], --b;
+          kc[b] = y, --b;
         }
-        s.cand[b] = x, key[b] = kx;
+        kc[b] = (u64)__float_as_uint(kx) << 32 | x;
       }
   const int max_edges = 3 * n - nb - 3;
   for (int ci = 0; ci < m && s.nedge < max_edges; ++ci) {
-    const int u = s.cand[ci] >> 8, v = s.cand[ci] & 255;
+    const int u = (int)((kc[ci] >> 8) & 255u), v = (int)(kc[ci] & 255u);
     bool bad = false;
     const unsigned zu = Zset(u, v);
     for (unsigned zc = zu & ~((1u << u) | (1u << v)); zc && !bad; zc &= zc - 1) {
