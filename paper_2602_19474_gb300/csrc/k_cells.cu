@@ -574,17 +574,26 @@ __global__ void __launch_bounds__(32 * EMIT_W, 8) k_emit_b(const __grid_constant
     const u32 ext = __shfl_sync(FULL, xex, t), ct = __shfl_sync(FULL, carry, t);
     const u32 xv = xs[k];
     const bool cut = (cm >> lane) & 1u;
-    const u32 ex = cut ? xv : 0u;
-    u32 inc = ex;
+    // a chunk without cut cells (most of them) needs no scan, one without
+    // run starts no label from a lane
+    u32 exinc = 0;  // the extra triangles of the chunk's cut cells before this cell
+    if (cm) {
+      const u32 ex = cut ? xv : 0u;
+      u32 inc = ex;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const u32 y = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+      }
+      exinc = inc - ex;
     }
-    const u32 off = T0 + (u32)k + ext + inc - ex;
-    const u32 upto = sm & (lane == 31 ? FULL : (2u << lane) - 1u);
-    const u32 lv = __shfl_sync(FULL, xv, upto ? 31 - __clz(upto) : 0);
-    const u32 lab = upto ? lv : ct;
+    const u32 off = T0 + (u32)k + ext + exinc;
+    u32 lab = ct;
+    if (sm) {
+      const u32 upto = sm & (lane == 31 ? FULL : (2u << lane) - 1u);
+      const u32 lv = __shfl_sync(FULL, xv, upto ? 31 - __clz(upto) : 0);
+      if (upto) lab = lv;
+    }
     if (cut || k >= nc) continue;
     const i64 cid = c0 + k;
     if (cid >= rnext) {
