@@ -986,7 +986,13 @@ def measure_serving(sb, torch, dev, local, rates, requests: int, warm: int, work
         return lat[warm:]
 
     srv = sb.server_create(local)
-    served(srv, 200.0, 64)  # warm the workers (table caches, scratch arenas)
+    # warm the workers (table caches, scratch arenas): every pool image once,
+    # one after another, so that no image meets a cold arena in a timed rate
+    for img, h in dimgs:
+        rid = sb.server_submit(srv, img, h)
+        sb.server_wait(srv, rid, -1)
+        sb.server_release(srv, rid)
+    served(srv, 200.0, 64)
     res = []
     for r in rates:
         lat, sizes, thr = served(srv, r, requests + warm)

@@ -31,6 +31,7 @@ constexpr int WN = 64;  // warp path, large state
 constexpr int WS = TIERG_WN;  // warp path, small state (16-bit vertex sets)
 constexpr int WWARPS = 4;
 constexpr int SW_BLOCKS = 6;  // small-state warp kernel: blocks per SM
+constexpr int GORDER_W = 8;   // ordering kernel: cell buckets (warps) per block
 
 SBMT_DEV constexpr int pow2_at_least(int x) {
   int m = 1;
@@ -583,11 +584,14 @@ SBMT_DEV int boundary_count(const CutRec& rec) { return (int)(rec.ntri + 2 - 2 *
 // cut cells.  In the compact format only the cut cells' triangles are listed.
 // The lists hold (job, record) pairs.
 template <bool ONE>
-__global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job one, const Job* __restrict__ jobs,
-                                                  const u32* __restrict__ bpre, int njobs, BatchDev* bd, uint2* olist,
-                                                  uint2* slist, uint2* wlist) {
+__global__ void __launch_bounds__(32 * GORDER_W) k_gorder_b(const __grid_constant__ Job one,
+                                                            const Job* __restrict__ jobs, const u32* __restrict__ bpre,
+                                                            int njobs, BatchDev* bd, uint2* olist, uint2* slist,
+                                                            uint2* wlist) {
   __shared__ u32 s_base[WS + 2];
   __shared__ u32 s_kw;
+  __shared__ u32 s_wc[GORDER_W][WS + 2];  // per warp: its cells per size, then its first place among the block's
+  __shared__ u32 s_blk[WS + 2];           // the block's first place per size (one atomic per size and block)
   if (threadIdx.x == 0) {
     u32 run = 0, big = 0;
     for (int n = WS; n >= 0; --n) {
@@ -598,16 +602,45 @@ __global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job on
     s_kw = big;
     if (blockIdx.x == 0) bd->nolist = run - big, bd->nslist = big;
   }
+  for (int i = threadIdx.x; i < GORDER_W * (WS + 2); i += blockDim.x) (&s_wc[0][0])[i] = 0u;
   __syncthreads();
   SBMT_BLOCK_JOB(ONE, one, jobs, bpre, njobs)
-  const int lane = threadIdx.x & 31;
-  const u32 b = lb * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= J.nbc) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u32 b = lb * GORDER_W + (u32)w;
+  const bool live = b < J.nbc;  // a warp past the job's buckets still meets the block's barriers
   CutRec* recs = J.recs;
+  const u32 n = live ? J.bcut[b] : 0u, rec0 = live ? J.bbase[b] : 0u;
+  // the warp's Tier-G cells per size
+  for (u32 base = 0; base < n; base += 32) {
+    const u32 r = base + (u32)lane;
+    CutRec rec{};
+    if (r < n) rec = recs[rec0 + r];
+    const bool tg = r < n && (rec.code & (1u << 16));
+    const unsigned tmask = __ballot_sync(0xffffffffu, tg);
+    if (tg) {
+      const int nv = local_count(rec);
+      const int key = nv > WS ? WS + 1 : nv;
+      const unsigned peers = __match_any_sync(tmask, key);
+      if (lane == __ffs(peers) - 1) s_wc[w][key] += (u32)__popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // per size: the warps' places within the block, and one atomic for the block
+  if (threadIdx.x < WS + 2) {
+    const int key = (int)threadIdx.x;
+    u32 tot = 0;
+    for (int q = 0; q < GORDER_W; ++q) {
+      const u32 c = s_wc[q][key];
+      s_wc[q][key] = tot, tot += c;
+    }
+    s_blk[key] = tot ? atomicAdd(key > WS ? &bd->nwlist : &bd->gcur[key], tot) : 0u;
+  }
+  __syncthreads();
+  if (!live) return;
   const u32* extra_scan = J.extra_scan;
   const u32* cut_scan = J.cp.on ? J.cp.cut_scan : nullptr;
   const u32 CB0 = J.NVg + J.NE;
-  const u32 n = J.bcut[b], rec0 = J.bbase[b];
   const u32 kw = s_kw;
   u32 ct = 0, cc = 0;  // the bucket's earlier records: sum of (ntri - 1), of nchain
   for (u32 base = 0; base < n; base += 32) {
@@ -626,25 +659,27 @@ __global__ void __launch_bounds__(256) k_gorder_b(const __grid_constant__ Job on
     ct += __shfl_sync(0xffffffffu, it, 31), cc += __shfl_sync(0xffffffffu, ic, 31);
     const bool tg = valid && (rec.code & (1u << 16));
     const unsigned tmask = __ballot_sync(0xffffffffu, tg);
-    if (!tg) continue;
-    recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
-    recs[rec0 + r].chain_base = CB0 + J.chain_scan[b] + pc;
-    const int nv = local_count(rec);
-    const int key = nv > WS ? WS + 1 : nv;
-    // one atomic per distinct size in the warp
-    const unsigned peers = __match_any_sync(tmask, key);
-    const int leader = __ffs(peers) - 1;
-    u32 at = 0;
-    if (lane == leader) at = atomicAdd(key > WS ? &bd->nwlist : &bd->gcur[key], (u32)__popc(peers));
-    at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
-    const uint2 e = make_uint2((u32)jk, rec0 + r);
-    if (key > WS) {
-      wlist[at] = e;
-    } else {
-      const u32 pos = s_base[key] + at;  // place in the order, largest first
-      if (pos < kw) slist[pos] = e;
-      else olist[pos - kw] = e;
+    if (tg) {
+      recs[rec0 + r].tri_off = cut_scan ? extra_scan[b] + cut_scan[b] + r + pt : rec.cell + extra_scan[b] + pt;
+      recs[rec0 + r].chain_base = CB0 + J.chain_scan[b] + pc;
+      const int nv = local_count(rec);
+      const int key = nv > WS ? WS + 1 : nv;
+      // the cells of one size take consecutive places, in the warp's order
+      const unsigned peers = __match_any_sync(tmask, key);
+      const int leader = __ffs(peers) - 1;
+      u32 at = 0;
+      if (lane == leader) at = s_blk[key] + s_wc[w][key], s_wc[w][key] += (u32)__popc(peers);
+      at = __shfl_sync(peers, at, leader) + (u32)__popc(peers & ((1u << lane) - 1u));
+      const uint2 e = make_uint2((u32)jk, rec0 + r);
+      if (key > WS) {
+        wlist[at] = e;
+      } else {
+        const u32 pos = s_base[key] + at;  // place in the order, largest first
+        if (pos < kw) slist[pos] = e;
+        else olist[pos - kw] = e;
+      }
     }
+    __syncwarp();
   }
 }
 
@@ -740,8 +775,10 @@ int launch_tierg_b(const Job* one, const Job* jobs, const u32* bpre, int njobs, 
   if (nblocks == 0) return 0;
   const Job none{};
   const Job& oj = one ? *one : none;
-  if (one) k_gorder_b<true><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
-  else k_gorder_b<false><<<nblocks, 256, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
+  if (one)
+    k_gorder_b<true><<<nblocks, 32 * GORDER_W, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
+  else
+    k_gorder_b<false><<<nblocks, 32 * GORDER_W, 0, st>>>(oj, jobs, bpre, njobs, bp.bd, bp.olist, bp.slist, bp.wlist);
   if (one) k_tierg_thread_b<true><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
   else k_tierg_thread_b<false><<<152 * thread_blocks_per_sm, 64, 0, st>>>(oj, jobs, bp.bd, bp.olist);
   // the warp kernels on their own stream when given one, beside the thread
