@@ -15,8 +15,8 @@
 //
 // The cells are first ordered by vertex count, largest first.  Cells with at
 // most TN vertices (nearly all of them at h = 2 px) run one thread each, on
-// per-pair vertex sets (orientations decided once per triple); larger cells
-// run one warp each with the state in shared memory.
+// per-pair vertex sets; larger cells run one warp each with the state in
+// shared memory (a small state up to WS vertices, a large one above).
 #include <type_traits>
 
 #include "sbmt_cell.cuh"
@@ -383,9 +383,9 @@ SBMT_DEV void greedy_faces(GStore<N, L>& s, int lane, int nb, const O& ori, floa
 
 // The same greedy rule for one thread, on vertex sets.  For every pair u < v
 // two 16-bit sets record the vertices strictly left of the directed line
-// u -> v and those on it; each triple's orientation is decided once, in
-// single precision when the determinant is clear of its rounding bound and
-// exactly otherwise.  A candidate is blocked by a collinear vertex between
+// u -> v and those on it; each orientation is decided in single precision
+// when the determinant is clear of its rounding bound and exactly otherwise,
+// so that it is the exact one.  A candidate is blocked by a collinear vertex between
 // its ends or by a kept edge with one end on each side whose own line
 // separates the candidate's ends; a 3-cycle is a face when no vertex lies on
 // the inner side of all three of its edges.
