@@ -129,6 +129,12 @@ STAGE_SOURCES = {
 LATENCY_STAGES = ("k_tierg",)
 
 
+def roofline_stage(prof: dict):
+    """(name, (ms, launches)) of the stage the HBM roofline entry describes:
+    the one with the most device time among those whose bytes bound them."""
+    return max(((k, x) for k, x in prof.items() if k not in LATENCY_STAGES), key=lambda kv: kv[1][0])
+
+
 def stage_source_hash(stage: str) -> str | None:
     import hashlib
 
@@ -658,8 +664,7 @@ def our_arm(args, rank: int, world: int, dist):
     # stream, so that the two event times cover one interval: the HBM
     # roofline takes the dominant stage among the others, and the Tier-G
     # stage is reported beside it
-    dom = max(((k, x) for k, x in prof.items() if k not in LATENCY_STAGES), key=lambda kv: kv[1][0])
-    dname, (dms, dn) = dom
+    dname, (dms, dn) = roofline_stage(prof)
     lat_stages = {k: {"bound": "latency", "ms_per_launch": t / args.steps,
                       "algorithmic_bytes_per_launch": kernel_bytes(k, v, img.nbytes, W, H)}
                   for k, (t, _) in prof.items() if k in LATENCY_STAGES and t > 0}

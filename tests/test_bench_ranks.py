@@ -66,3 +66,15 @@ def test_reference_arm_prints_on_rank_zero_only(tmp_path):
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_roofline_stage_skips_the_latency_bound_tier_g_stage():
+    """The Tier-G stage runs beside the emission and is bound by latency:
+    the HBM roofline entry describes the busiest byte-bound stage even when
+    the Tier-G stage's event time is the longest."""
+    import bench
+
+    prof = {"k_emit": (13.1, 20), "k_tierg": (13.5, 80), "k_walk": (4.0, 40)}
+    assert bench.roofline_stage(prof)[0] == "k_emit"
+    prof = {"k_emit": (3.0, 20), "k_tierg": (13.5, 80), "k_cutcells": (4.5, 20)}
+    assert bench.roofline_stage(prof)[0] == "k_cutcells"
